@@ -1,0 +1,216 @@
+"""Pins of the CPU oracle against facts it does not compute itself:
+published generator outputs, closed-form gate identities, brute-force
+Kronecker products, normalisation, exact slicing and order independence."""
+import itertools
+
+import numpy as np
+import pytest
+
+import tn_inputs as I
+from oracle import circuit as C
+from oracle import gates as G
+from oracle import statevector as SV
+from oracle import tn as TN
+
+X = np.array([[0, 1], [1, 0]], dtype=complex)
+Y = np.array([[0, -1j], [1j, 0]], dtype=complex)
+
+
+# ---- SplitMix64: published outputs (Steele, Lea, Flood 2014 reference code)
+@pytest.mark.parametrize("cls", [I.SplitMix64, C._SplitMix64])
+def test_splitmix64_published_vectors(cls):
+    r = cls(0)
+    assert [r.next() for _ in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    r = cls(1234567)
+    assert [r.next() for _ in range(3)] == [6457827717110365317, 3203168211198807973, 9817491932198370423]
+
+
+# ---- gate matrices
+@pytest.mark.parametrize("U", [G.SQRT_X, G.SQRT_Y, G.SQRT_W, G.fsim(G.FSIM_THETA, G.FSIM_PHI), G.fsim(0.3, 1.1)])
+def test_gates_unitary(U):
+    assert np.allclose(U.conj().T @ U, np.eye(len(U)), atol=1e-15)
+
+
+def test_sqrt_gates_square_to_minus_i_pauli():
+    W = (X + Y) / np.sqrt(2)
+    assert np.allclose(G.SQRT_X @ G.SQRT_X, -1j * X, atol=1e-15)
+    assert np.allclose(G.SQRT_Y @ G.SQRT_Y, -1j * Y, atol=1e-15)
+    assert np.allclose(G.SQRT_W @ G.SQRT_W, -1j * W, atol=1e-15)
+
+
+def test_fsim_special_cases():
+    assert np.allclose(G.fsim(0.0, 0.0), np.eye(4))
+    F = G.fsim(np.pi / 2, 0.0)
+    e01 = np.array([0, 1, 0, 0], dtype=complex)   # |x_a=0, x_b=1>
+    assert np.allclose(F @ e01, [0, 0, -1j, 0])   # -> -i |10>
+    F = G.fsim(np.pi / 2, np.pi / 6)
+    assert np.isclose(F[3, 3], np.exp(-1j * np.pi / 6))
+    assert np.isclose(F[0, 0], 1.0)
+
+
+# ---- circuit protocol
+def test_coupler_patterns_by_hand():
+    # 3 x 4 grid, qubit (r, c) = 4r + c
+    assert C.coupler_pattern(3, 4, 0) == [(0, 1), (2, 3), (4, 5), (6, 7), (8, 9), (10, 11)]
+    assert C.coupler_pattern(3, 4, 1) == [(1, 2), (5, 6), (9, 10)]
+    assert C.coupler_pattern(3, 4, 2) == [(0, 4), (1, 5), (2, 6), (3, 7)]
+    assert C.coupler_pattern(3, 4, 3) == [(4, 8), (5, 9), (6, 10), (7, 11)]
+    # every grid edge appears in exactly one pattern
+    edges = set()
+    for p in range(4):
+        for e in C.coupler_pattern(5, 6, p):
+            assert e not in edges
+            edges.add(e)
+    assert len(edges) == 5 * 5 + 4 * 6
+
+
+def test_circuit_layout_and_no_repeat():
+    rows, cols, depth = 3, 4, 9
+    n = rows * cols
+    gs = C.random_circuit(rows, cols, depth, seed=7)
+    n_fsim = sum(len(C.coupler_pattern(rows, cols, c % 4)) for c in range(depth))
+    assert len(gs) == n * (depth + 1) + n_fsim
+    last = {}
+    for g in gs:
+        if len(g.qubits) == 1:
+            q = g.qubits[0]
+            assert last.get(q) != g.kind
+            last[q] = g.kind
+        else:
+            assert g.kind == "fsim" and g.qubits[0] < g.qubits[1]
+
+
+def test_circuit_draws_follow_splitmix64():
+    """Layer 0 kinds are KINDS[((x >> 32) * 3) >> 32] of the published stream,
+    layer 1 picks among the two other kinds with ((x >> 32) * 2) >> 32."""
+    rows, cols = 2, 3
+    n = rows * cols
+    gs = C.random_circuit(rows, cols, 1, seed=1234567)
+    r = I.SplitMix64(1234567)
+    first = [G.ONE_QUBIT_KINDS[((r.next() >> 32) * 3) >> 32] for _ in range(n)]
+    assert [g.kind for g in gs[:n]] == first
+    second = []
+    for q in range(n):
+        opts = [k for k in G.ONE_QUBIT_KINDS if k != first[q]]
+        second.append(opts[((r.next() >> 32) * 2) >> 32])
+    assert [g.kind for g in gs if len(g.qubits) == 1][n:] == second
+
+
+# ---- state vector
+def _kron_unitary(gates, n):
+    """Dense 2^n x 2^n unitary by Kronecker products (qubit 0 = LSB)."""
+    I2 = np.eye(2)
+    U = np.eye(1 << n, dtype=complex)
+    for g in gates:
+        if len(g.qubits) == 1:
+            q = g.qubits[0]
+            M = np.array([[1.0]])
+            for k in reversed(range(n)):
+                M = np.kron(M, g.matrix if k == q else I2)
+        else:
+            a, b = g.qubits
+            M = np.zeros((1 << n, 1 << n), dtype=complex)
+            for i in range(1 << n):
+                xa, xb = (i >> a) & 1, (i >> b) & 1
+                for ya, yb in itertools.product((0, 1), repeat=2):
+                    j = i & ~(1 << a) & ~(1 << b) | (ya << a) | (yb << b)
+                    M[j, i] += g.matrix[2 * ya + yb, 2 * xa + xb]
+        U = M @ U
+    return U
+
+
+@pytest.mark.parametrize("rows,cols,depth,seed", [(1, 2, 3, 1), (2, 2, 4, 2), (1, 4, 5, 3), (2, 2, 8, 4)])
+def test_statevector_matches_kronecker(rows, cols, depth, seed):
+    n = rows * cols
+    gs = C.random_circuit(rows, cols, depth, seed)
+    psi = SV.simulate(gs, n)
+    U = _kron_unitary(gs, n)
+    assert np.allclose(psi, U[:, 0], atol=1e-13)
+
+
+def test_statevector_hand_cases():
+    # sqrt(X)|0> = (|0> - i|1>)/sqrt2
+    g = C.Gate("sqrtx", (0,), matrix=G.SQRT_X)
+    psi = SV.simulate([g], 1)
+    assert np.allclose(psi, np.array([1, -1j]) / np.sqrt(2))
+    # fSim(pi/2, 0) on qubits (0, 1): |x0=0, x1=1> -> -i |x0=1, x1=0>
+    flip1 = C.Gate("mat1", (1,), matrix=X)
+    fs = C.Gate("fsim", (0, 1), np.pi / 2, 0.0, G.fsim(np.pi / 2, 0.0))
+    psi = SV.simulate([flip1, fs], 2)
+    assert np.allclose(psi, [0, -1j, 0, 0])   # index 1 = qubit 0 set
+
+
+@pytest.mark.parametrize("rows,cols,depth", [(3, 3, 8), (3, 4, 10)])
+def test_statevector_norm(rows, cols, depth):
+    psi = SV.simulate(C.random_circuit(rows, cols, depth, 5), rows * cols)
+    assert abs(np.vdot(psi, psi).real - 1.0) < 1e-12
+
+
+def test_amplitude_open_index_convention():
+    n = 3
+    psi = np.arange(8, dtype=complex)
+    a = SV.amplitudes(psi, n, [[1, 0, 0]], open_qubits=(2, 1))
+    # j bit0 -> qubit 2, bit1 -> qubit 1; qubit 0 fixed to 1
+    assert list(a[0].real) == [1, 5, 3, 7]
+
+
+# ---- tensor network
+def _rows(n, nb, seed):
+    return [I.bits_of(w, n) for w in I.bitstrings(n, nb, seed)]
+
+
+@pytest.mark.parametrize("rows,cols,depth,seed,opened", [(3, 3, 6, 1, ()), (3, 4, 8, 2, (10, 11)), (2, 5, 10, 3, (0, 9, 4))])
+def test_tn_matches_statevector(rows, cols, depth, seed, opened):
+    n = rows * cols
+    gs = C.random_circuit(rows, cols, depth, seed)
+    bits = _rows(n, 3, seed)
+    a_sv = SV.amplitudes(SV.simulate(gs, n), n, bits, opened)
+    a_tn = TN.amplitudes(gs, n, bits, opened)
+    assert np.linalg.norm(a_tn - a_sv) / np.linalg.norm(a_sv) < 1e-12
+
+
+def _random_tree(labels, seed):
+    """A random contraction tree that only joins tensors sharing an index
+    (random outer products of many tensors would blow up memory)."""
+    rng = np.random.default_rng(seed)
+    active = {i: set(l) for i, l in enumerate(labels)}
+    nid = len(labels)
+    pairs = []
+    while len(active) > 1:
+        keys = sorted(active)
+        cand = [(a, b) for x, a in enumerate(keys) for b in keys[x + 1:] if active[a] & active[b]]
+        if not cand:
+            cand = [(keys[0], keys[1])]
+        a, b = cand[rng.integers(len(cand))]
+        active[nid] = active.pop(a) ^ active.pop(b)
+        pairs.append((a, b))
+        nid += 1
+    return pairs
+
+
+def test_tn_order_independence():
+    rows, cols, depth = 2, 3, 6
+    n = rows * cols
+    gs = C.random_circuit(rows, cols, depth, 11)
+    net = TN.circuit_network(gs, n, _rows(n, 1, 11)[0], open_qubits=(5,))
+    ref = TN.contract(net)
+    for s in range(3):
+        v = TN.contract(net, _random_tree(net.labels, s))
+        assert np.linalg.norm(v - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_tn_sliced_sum_equals_unsliced():
+    rows, cols, depth = 3, 3, 8
+    n = rows * cols
+    gs = C.random_circuit(rows, cols, depth, 13)
+    net = TN.circuit_network(gs, n, _rows(n, 1, 13)[0], open_qubits=(8,))
+    ref = TN.contract(net)
+    internal = sorted({l for ls in net.labels for l in ls} - set(net.open_labels))
+    rng = np.random.default_rng(0)
+    sliced = [internal[i] for i in rng.choice(len(internal), 5, replace=False)]
+    tot = TN.contract_sliced(net, sliced)
+    assert np.linalg.norm(tot - ref) <= 1e-12 * np.linalg.norm(ref)
+    # one slice is the contraction with those wires fixed, brute force:
+    s = 19
+    fixed = TN.fix_indices(net, {lab: (s >> j) & 1 for j, lab in enumerate(sliced)})
+    assert np.allclose(TN.contract_slice(net, sliced, s), TN.contract(fixed))
