@@ -1,0 +1,257 @@
+/*
+ * tn.h -- C ABI of the GB300 random-circuit tensor-network library.
+ *
+ * The library computes output amplitudes <x|U|0...0> of a random quantum
+ * circuit U by contracting its tensor network (paper: Sec. "Existing Efforts
+ * on Simulation of RQCs", tensor approach), sliced into 2^S independent
+ * sub-networks whose results are summed (Sec. "A PEPS-based Simulation Method
+ * with an Optimized Slicing Strategy"), with a batch of 2^k amplitudes per
+ * contraction obtained by leaving k output qubits open (same section, "open
+ * batch").  Each slice runs a planned chain of pairwise contractions, each an
+ * index permutation fused into a complex GEMM (Sec. "Tensor Contraction Using
+ * Fused Permutation and Multiplication"), in one of several precisions (Sec.
+ * "A Mixed-Precision Computation Method via Adaptive Precision Scaling").
+ *
+ * Conventions used throughout:
+ *  - Qubit q of an R x C grid is (r, c) with q = r*C + c.
+ *  - Bitstrings are packed little-endian in ceil(n/64) uint64 words per
+ *    bitstring: bit q of the word array is the value of qubit q.
+ *  - Amplitude batch: output index j of a bitstring sets open qubit
+ *    open_qubits[t] to bit t of j; the bitstring's own bits for open qubits
+ *    are ignored.
+ *  - Complex numbers are interleaved (re, im).  Amplitude outputs are
+ *    complex128 (the cross-slice sum is FP64); device tensors are complex64.
+ *  - Tensor indices all have dimension 2.  A rank-r tensor with index labels
+ *    (l_0, ..., l_{r-1}) is stored row-major: element offset
+ *    sum_t x_t * 2^(r-1-t), so l_0 is the slowest index.
+ *
+ * Ownership and errors: every function returns a tn_status (TN_OK = 0).  On
+ * error a message describing the failure is available from tn_last_error()
+ * (thread-local, valid until the next call on the same thread), and output
+ * arguments are left untouched.  Handles are created and destroyed by the
+ * library; arrays passed in are owned by the caller and only read during the
+ * call.  All pointer and size arguments are validated on the host before any
+ * device work is queued.  The tn_free_* functions accept NULL.
+ */
+#ifndef TN_H
+#define TN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TN_OK = 0,
+  TN_EINVAL = 1,      /* invalid argument (null pointer, bad size, bad label) */
+  TN_ENOMEM = 2,      /* host allocation failed */
+  TN_EHBM = 3,        /* device memory needed exceeds what is free */
+  TN_ECUDA = 4,       /* a CUDA runtime call or kernel launch failed */
+  TN_ETIMEOUT = 5,    /* a bounded device or host wait expired */
+  TN_ETOOBIG = 6,     /* the plan's cost exceeds the caller's cap */
+  TN_EOVERFLOW = 7,   /* a scaled low-precision slice over/underflowed and the policy forbids recompute */
+  TN_ENOTREADY = 8,   /* a serving request has not completed yet */
+  TN_ENODEVICE = 9    /* no usable sm_103 device */
+} tn_status;
+
+/* Human-readable description of the last error on this thread. */
+const char* tn_last_error(void);
+/* Library version string, e.g. "gb300-rqc-tn 0.1". */
+const char* tn_version(void);
+
+/* ------------------------------------------------------------------ */
+/* Circuits (paper: Sec. "General Background of RQC")                  */
+/* ------------------------------------------------------------------ */
+
+enum {
+  TN_GATE_SQRTX = 0, /* (1/sqrt2)[[1,-i],[-i,1]] */
+  TN_GATE_SQRTY = 1, /* (1/sqrt2)[[1,-1],[1,1]] */
+  TN_GATE_SQRTW = 2, /* (1/sqrt2)[[1,-e^{i pi/4}],[e^{-i pi/4},1]] */
+  TN_GATE_FSIM = 3,  /* fSim(theta, phi), basis index 2*x_q0 + x_q1 */
+  TN_GATE_MAT1 = 4,  /* arbitrary 2x2 in mat[0..7] */
+  TN_GATE_MAT2 = 5   /* arbitrary 4x4 in mat[0..31], basis index 2*x_q0 + x_q1 */
+};
+
+/* One gate.  q1 = -1 for one-qubit gates; two-qubit gates need q0 != q1.
+ * mat holds a row-major complex matrix as (re, im) pairs for MAT1/MAT2 and is
+ * filled by the library for the named kinds when read back. */
+typedef struct {
+  int32_t kind;
+  int32_t q0;
+  int32_t q1;
+  int32_t reserved;
+  double theta;
+  double phi;
+  double mat[32];
+} tn_gate;
+
+typedef struct tn_circuit_s tn_circuit;
+
+/* Seeded random circuit on a rows x cols grid with depth (1+depth+1): one
+ * layer of one-qubit gates, then `depth` cycles of {fSim(pi/2, pi/6) layer on
+ * coupler pattern A,B,C,D (cycle c uses pattern c mod 4), one-qubit layer}.
+ * Patterns: A horizontal (r,c)-(r,c+1) c even; B horizontal c odd; C vertical
+ * (r,c)-(r+1,c) r even; D vertical r odd.  One-qubit kinds are drawn from
+ * {sqrtX, sqrtY, sqrtW} with SplitMix64(seed), uniform over k options via
+ * ((x >> 32) * k) >> 32; after the first layer a qubit never repeats its
+ * previous kind.  rows, cols >= 1, rows*cols <= 64, 0 <= depth <= 4096. */
+tn_status tn_random_circuit(int32_t rows, int32_t cols, int32_t depth, uint64_t seed, tn_circuit** out);
+/* Circuit from an explicit gate list (num_qubits <= 64). */
+tn_status tn_circuit_from_gates(int32_t num_qubits, int64_t num_gates, const tn_gate* gates, tn_circuit** out);
+tn_status tn_circuit_info(const tn_circuit* c, int32_t* num_qubits, int64_t* num_gates);
+/* Copies the gate list into out[0 .. num_gates-1]. */
+tn_status tn_circuit_gates(const tn_circuit* c, tn_gate* out, int64_t capacity);
+void tn_free_circuit(tn_circuit* c);
+
+/* ------------------------------------------------------------------ */
+/* Tensor network (paper: Sec. "Existing Efforts on Simulation of RQCs") */
+/* ------------------------------------------------------------------ */
+
+typedef struct tn_network_s tn_network;
+
+typedef struct {
+  int32_t num_qubits;
+  int32_t num_open;
+  int32_t num_leaves;      /* tensors after simplification */
+  int32_t num_labels;      /* distinct wire-segment indices in the leaves */
+  int32_t max_leaf_rank;   /* including closed-output indices */
+  int32_t num_closed;      /* closed output indices (fixed per bitstring) */
+} tn_network_info;
+
+/* Builds the network of <x|U|0^n> with the listed qubits left open (their
+ * order defines the amplitude-batch index, see above).  Inputs |0> are
+ * rank-1, one-qubit gates rank-2, two-qubit gates rank-4 tensors; each closed
+ * output wire becomes a "fixed" index whose value is the bitstring bit at
+ * contraction time.  Tensors of rank <= 2 (not counting fixed indices) are
+ * absorbed into a neighbour (FP64 on the host).  open_qubits may be NULL when
+ * num_open == 0; entries must be distinct and in [0, n). */
+tn_status tn_build_network(const tn_circuit* c, const int32_t* open_qubits, int32_t num_open, tn_network** out);
+tn_status tn_network_get_info(const tn_network* net, tn_network_info* info);
+/* Wire-segment name of a label: qubit q after its t-th gate (t = 0 is the
+ * input wire).  pairs_out receives 2*num_labels int32 (q, t). */
+tn_status tn_network_label_wires(const tn_network* net, int32_t* pairs_out, int64_t capacity_pairs);
+void tn_free_network(tn_network* net);
+
+/* ------------------------------------------------------------------ */
+/* Planning (paper: Secs. "A PEPS-based Simulation Method ..." and      */
+/* "Searching for Better Contraction Paths with a Reduced Complexity")  */
+/* ------------------------------------------------------------------ */
+
+typedef struct tn_plan_s tn_plan_t;  /* opaque plan handle */
+
+typedef struct {
+  int32_t num_sliced;            /* exact number of sliced indices S; -1 = as few as the width cap needs */
+  int32_t max_log2_intermediate; /* per-slice width cap (log2 elements); 0 = no cap */
+  int32_t search_trials;         /* order-search restarts; 0 = default (128) */
+  int32_t reserved;
+  uint64_t seed;                 /* search seed; equal inputs + seed give byte-identical plans */
+  double max_log2_cmac;          /* cost cap on total complex MACs (log2); 0 = none -> TN_ETOOBIG when exceeded */
+} tn_plan_opts;
+
+typedef struct {
+  int32_t num_qubits;
+  int32_t num_open;
+  int32_t num_sliced;
+  int32_t num_steps;
+  int32_t num_leaves;
+  int32_t max_log2_intermediate; /* largest per-slice tensor (log2 elements) */
+  int64_t num_slices;            /* 2^num_sliced */
+  double cmac_per_slice;         /* counted complex multiply-adds of one slice */
+  double flops_per_slice;        /* 8 real flops per complex MAC (counted, not issued) */
+  double log2_cmac_total;        /* log2(cmac_per_slice * num_slices) */
+  int64_t footprint_bytes_per_unit; /* peak live complex64 bytes of one slice */
+  uint64_t hash;                 /* FNV-1a 64 of the serialized plan */
+  int32_t num_dense_steps;       /* steps routed to the tensor-core GEMM */
+  int32_t num_vector_steps;      /* steps routed to the bandwidth kernel */
+} tn_plan_info;
+
+tn_status tn_plan(const tn_network* net, const tn_plan_opts* opts, tn_plan_t** out);
+tn_status tn_plan_get_info(const tn_plan_t* p, tn_plan_info* info);
+/* The sliced indices as (q, t) wire segments: sliced index j takes bit j of
+ * the slice id.  pairs_out receives 2*num_sliced int32. */
+tn_status tn_plan_sliced_wires(const tn_plan_t* p, int32_t* pairs_out, int64_t capacity_pairs);
+/* Serialized plan bytes; call with buf = NULL to get the length. */
+tn_status tn_plan_serialize(const tn_plan_t* p, uint8_t* buf, size_t capacity, size_t* len);
+/* Contraction tree for replay: leaf_raw receives, per leaf, the raw tensor ids
+ * it merges (-1 terminated lists, raw id g < num_gates = gate g, num_gates + q =
+ * input vector of qubit q); tree receives 2*(num_leaves-1) SSA ids (leaves
+ * 0..L-1, step i result L+i).  Sizes via tn_plan_get_info. */
+tn_status tn_plan_tree(const tn_plan_t* p, int32_t* leaf_raw, int64_t leaf_raw_capacity, int32_t* tree, int64_t tree_capacity);
+void tn_free_plan(tn_plan_t* p);
+
+/* ------------------------------------------------------------------ */
+/* Contraction (the hot path)                                          */
+/* ------------------------------------------------------------------ */
+
+enum {
+  TN_PREC_C64 = 0,          /* complex64 storage, FP32 products and sums (SIMT FFMA) */
+  TN_PREC_SPLIT_BF16 = 1,   /* complex64 storage; GEMMs as bf16 hi+lo split on tcgen05, FP32 accumulate */
+  TN_PREC_SPLIT_FP16 = 2,   /* as above with fp16 hi+lo and a per-tensor power-of-two scale */
+  TN_PREC_SCALED_FP16 = 3,  /* complex fp16 storage with per-tensor power-of-two scale, FP32 accumulate */
+  TN_PREC_SCALED_BF16 = 4   /* complex bf16 storage with per-tensor power-of-two scale, FP32 accumulate */
+};
+
+typedef struct {
+  void* stream;             /* cudaStream_t to run on; NULL = the legacy default stream */
+  int32_t precision;        /* TN_PREC_* */
+  int32_t device_io;        /* 0: bitstrings/out are host memory; 1: device memory */
+  int64_t slice_begin;      /* first slice id of the summed range */
+  int64_t slice_count;      /* number of slices summed; -1 = all from slice_begin */
+  int32_t units_per_group;  /* (bitstring, slice) units contracted together; 0 = auto */
+  int32_t overflow_policy;  /* scaled modes: 0 = recompute a flagged slice in complex64, 1 = discard it (counted) */
+  int32_t use_graph;        /* 1 = replay the per-group launch sequence as a CUDA graph */
+  int32_t reserved;
+} tn_exec_opts;
+
+typedef struct {
+  double device_ms;          /* device time of the call (CUDA events on the call's stream) */
+  double flops;              /* counted flops of the contracted units */
+  int64_t units;             /* (bitstring, slice) units contracted */
+  int64_t kernel_launches;   /* kernels launched by the call */
+  int64_t flagged_units;     /* scaled-mode units flagged for over/underflow */
+  int64_t discarded_units;   /* flagged units dropped under overflow_policy = 1 */
+  double dominant_kernel_ms; /* summed device time of the dominant kernel class (when profiled) */
+  int32_t dominant_kernel;   /* 0 gemm-simt, 1 vector, 2 tcgen05 */
+  int32_t reserved;
+} tn_report;
+
+/* Sums, over the slice range, the contraction of every bitstring's network:
+ *   out[b*2^k + j] = sum_{s in range} C_{b,s}[j]   (complex128, (re, im))
+ * bitstrings: nb * ceil(n/64) uint64 words; out: nb * 2^k complex128.  Both
+ * live on the host (device_io = 0) or the device (device_io = 1).  The call
+ * is synchronous for host I/O; for device I/O it returns once work is queued
+ * on opts->stream.  report may be NULL. */
+tn_status tn_contract_amplitudes(tn_plan_t* p, const uint64_t* bitstrings, int64_t nb, double* out,
+                                 const tn_exec_opts* opts, tn_report* report);
+
+/* ------------------------------------------------------------------ */
+/* One pairwise contraction (Sec. "Tensor Contraction Using Fused       */
+/* Permutation and Multiplication")                                    */
+/* ------------------------------------------------------------------ */
+
+enum {
+  TN_PAIR_AUTO = 0,      /* the executor's kernel choice for this shape */
+  TN_PAIR_FUSED_SIMT = 1,/* fused permute-GEMM, FP32 FFMA */
+  TN_PAIR_VECTOR = 2,    /* bandwidth kernel (small N*K) */
+  TN_PAIR_FUSED_TC = 3,  /* fused permute-GEMM on tcgen05 (split or scaled precision) */
+  TN_PAIR_UNFUSED = 4    /* permute A and B to GEMM order, GEMM, permute C (library-allocated scratch) */
+};
+
+/* C[c_labels] = sum over labels shared by A and B of A[a_labels] * B[b_labels].
+ * A, B, C: device complex64 tensors (rank <= 30 each, row-major as above).
+ * Every label of C appears in exactly one of A, B; a label shared by A and B
+ * must not appear in C; labels are distinct within a tensor.
+ * precision selects the arithmetic (TN_PREC_C64, _SPLIT_BF16, _SPLIT_FP16 on
+ * complex64 storage).  Asynchronous on `stream`. */
+tn_status tn_contract_pair(const void* A, const int32_t* a_labels, int32_t a_rank,
+                           const void* B, const int32_t* b_labels, int32_t b_rank,
+                           void* C, const int32_t* c_labels, int32_t c_rank,
+                           int32_t precision, int32_t algo, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TN_H */

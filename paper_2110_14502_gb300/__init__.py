@@ -1,0 +1,226 @@
+"""GB300 random-circuit tensor-network library: Python binding of include/tn.h.
+
+The compute path lives in libtn.so (CUDA kernels for sm_103a behind a C ABI);
+this package only marshals arguments.  See the docstrings of
+:func:`random_circuit`, :func:`build_network`, :func:`plan` and
+:meth:`Plan.contract_amplitudes`.
+"""
+import ctypes as C
+
+import numpy as np
+
+from ._abi import (PAIR_ALGO, PREC, ExecOpts, Gate, NetworkInfo, PlanInfo, PlanOpts, Report, TnError, check,
+                   i32array, lib)
+
+__all__ = ["Circuit", "Network", "Plan", "random_circuit", "circuit_from_gates", "build_network", "plan",
+           "contract_pair", "TnError", "PREC", "version"]
+
+
+def version():
+    return lib().tn_version().decode()
+
+
+def _ptr(x):
+    """Device or host pointer of a torch tensor / NumPy array (no copies)."""
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    return C.c_void_p(x.ctypes.data)
+
+
+class Circuit:
+    def __init__(self, handle):
+        self._h = handle
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().tn_free_circuit(self._h)
+            self._h = None
+
+    @property
+    def num_qubits(self):
+        n, g = C.c_int32(), C.c_int64()
+        check(lib().tn_circuit_info(self._h, C.byref(n), C.byref(g)))
+        return n.value
+
+    def gates(self):
+        """List of (kind, q0, q1, theta, phi, matrix complex128)."""
+        n, g = C.c_int32(), C.c_int64()
+        check(lib().tn_circuit_info(self._h, C.byref(n), C.byref(g)))
+        arr = (Gate * max(g.value, 1))()
+        check(lib().tn_circuit_gates(self._h, arr, g.value))
+        out = []
+        for i in range(g.value):
+            t = arr[i]
+            d = 4 if t.q1 >= 0 else 2
+            m = np.array(t.mat[: 2 * d * d]).view(np.complex128).reshape(d, d)
+            out.append((t.kind, t.q0, t.q1, t.theta, t.phi, m))
+        return out
+
+
+def random_circuit(rows, cols, depth, seed):
+    h = C.c_void_p()
+    check(lib().tn_random_circuit(rows, cols, depth, seed, C.byref(h)))
+    return Circuit(h)
+
+
+def circuit_from_gates(num_qubits, gates):
+    """gates: iterable of (kind:str|int, qubits tuple, theta, phi, matrix or None)."""
+    gates = list(gates)
+    arr = (Gate * max(len(gates), 1))()
+    for i, (kind, qs, theta, phi, mat) in enumerate(gates):
+        t = arr[i]
+        t.kind = kind if isinstance(kind, int) else {"sqrtx": 0, "sqrty": 1, "sqrtw": 2, "fsim": 3,
+                                                      "mat1": 4, "mat2": 5}[kind]
+        t.q0 = qs[0]
+        t.q1 = qs[1] if len(qs) > 1 else -1
+        t.theta, t.phi = theta, phi
+        if mat is not None:
+            flat = np.asarray(mat, dtype=np.complex128).reshape(-1).view(np.float64)
+            for e, v in enumerate(flat):
+                t.mat[e] = v
+    h = C.c_void_p()
+    check(lib().tn_circuit_from_gates(num_qubits, len(gates), arr, C.byref(h)))
+    return Circuit(h)
+
+
+class Network:
+    def __init__(self, handle, circuit):
+        self._h = handle
+        self.circuit = circuit
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().tn_free_network(self._h)
+            self._h = None
+
+    def info(self):
+        i = NetworkInfo()
+        check(lib().tn_network_get_info(self._h, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in NetworkInfo._fields_}
+
+    def label_wires(self):
+        n = self.info()["num_labels"]
+        a = np.zeros(2 * n, dtype=np.int32)
+        check(lib().tn_network_label_wires(self._h, a.ctypes.data_as(C.POINTER(C.c_int32)), n))
+        return [tuple(x) for x in a.reshape(-1, 2)]
+
+
+def build_network(circuit, open_qubits=()):
+    arr, p = i32array(open_qubits)
+    h = C.c_void_p()
+    check(lib().tn_build_network(circuit._h, p, len(arr), C.byref(h)))
+    return Network(h, circuit)
+
+
+class Plan:
+    def __init__(self, handle, network):
+        self._h = handle
+        self.network = network
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().tn_free_plan(self._h)
+            self._h = None
+
+    def info(self):
+        i = PlanInfo()
+        check(lib().tn_plan_get_info(self._h, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in PlanInfo._fields_}
+
+    def sliced_wires(self):
+        s = self.info()["num_sliced"]
+        a = np.zeros(2 * max(s, 1), dtype=np.int32)
+        check(lib().tn_plan_sliced_wires(self._h, a.ctypes.data_as(C.POINTER(C.c_int32)), s))
+        return [tuple(int(v) for v in x) for x in a[: 2 * s].reshape(-1, 2)]
+
+    def serialize(self):
+        n = C.c_size_t()
+        check(lib().tn_plan_serialize(self._h, None, 0, C.byref(n)))
+        buf = (C.c_uint8 * n.value)()
+        check(lib().tn_plan_serialize(self._h, buf, n.value, C.byref(n)))
+        return bytes(buf)
+
+    def tree(self, num_gates, num_qubits):
+        """(leaf raw-tensor lists, SSA pairs) of the contraction tree."""
+        L = self.info()["num_leaves"]
+        raw = np.zeros(num_gates + num_qubits + L + 1, dtype=np.int32)
+        tree = np.zeros(2 * max(L - 1, 1), dtype=np.int32)
+        check(lib().tn_plan_tree(self._h, raw.ctypes.data_as(C.POINTER(C.c_int32)), raw.size,
+                                 tree.ctypes.data_as(C.POINTER(C.c_int32)), tree.size))
+        leaves, cur = [], []
+        for v in raw:
+            if len(leaves) == L:
+                break
+            if v < 0:
+                leaves.append(cur)
+                cur = []
+            else:
+                cur.append(int(v))
+        return leaves, [tuple(int(x) for x in p) for p in tree[: 2 * (L - 1)].reshape(-1, 2)]
+
+    def contract_amplitudes(self, bitstrings, precision="c64", slice_begin=0, slice_count=-1,
+                            units_per_group=0, stream=None, out=None, overflow_policy=0, use_graph=0,
+                            report=False):
+        """Amplitudes of each bitstring's open batch, summed over the slice range.
+
+        bitstrings: uint64 words, shape (nb, ceil(n/64)) -- a NumPy array (host
+        I/O: result returned as complex128 NumPy (nb, 2^k)) or a CUDA torch
+        tensor (device I/O: `out` must be a CUDA float64 tensor of nb*2^k*2
+        entries; work is queued on `stream`, a torch.cuda.Stream or raw handle).
+        """
+        info = self.info()
+        k = info["num_open"]
+        o = ExecOpts()
+        o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+        o.slice_begin = slice_begin
+        o.slice_count = slice_count
+        o.units_per_group = units_per_group
+        o.overflow_policy = overflow_policy
+        o.use_graph = use_graph
+        if stream is not None:
+            o.stream = C.c_void_p(getattr(stream, "cuda_stream", stream))
+        rep = Report()
+        device = hasattr(bitstrings, "is_cuda") and bitstrings.is_cuda
+        if device:
+            nb = bitstrings.shape[0]
+            if out is None:
+                raise ValueError("device I/O needs an `out` tensor")
+            o.device_io = 1
+            check(lib().tn_contract_amplitudes(self._h, _ptr(bitstrings), nb, _ptr(out), C.byref(o), C.byref(rep)))
+            res = out
+        else:
+            b = np.ascontiguousarray(np.asarray(bitstrings, dtype=np.uint64))
+            if b.ndim == 1:
+                b = b.reshape(-1, 1)
+            nb = b.shape[0]
+            res = np.zeros((nb, 1 << k), dtype=np.complex128)
+            check(lib().tn_contract_amplitudes(self._h, _ptr(b), nb, _ptr(res), C.byref(o), C.byref(rep)))
+        if report:
+            return res, {f: getattr(rep, f) for f, _ in Report._fields_}
+        return res
+
+
+def plan(network, num_sliced=-1, max_log2_intermediate=0, search_trials=0, seed=0, max_log2_cmac=0.0):
+    o = PlanOpts()
+    o.num_sliced = num_sliced
+    o.max_log2_intermediate = max_log2_intermediate
+    o.search_trials = search_trials
+    o.seed = seed
+    o.max_log2_cmac = max_log2_cmac
+    h = C.c_void_p()
+    check(lib().tn_plan(network._h, C.byref(o), C.byref(h)))
+    return Plan(h, network)
+
+
+def contract_pair(A, a_labels, B, b_labels, Cout, c_labels, precision="c64", algo="auto", stream=None):
+    """C[c_labels] = sum over shared labels of A[a_labels] * B[b_labels] on the
+    GPU; A, B, C are CUDA complex64 torch tensors (contiguous)."""
+    la, pa = i32array(a_labels)
+    lb, pb = i32array(b_labels)
+    lc, pc = i32array(c_labels)
+    s = C.c_void_p(getattr(stream, "cuda_stream", stream) if stream is not None else None)
+    prec = PREC[precision] if isinstance(precision, str) else int(precision)
+    al = PAIR_ALGO[algo] if isinstance(algo, str) else int(algo)
+    check(lib().tn_contract_pair(_ptr(A), pa, len(la), _ptr(B), pb, len(lb), _ptr(Cout), pc, len(lc),
+                                 prec, al, s))
+    return Cout

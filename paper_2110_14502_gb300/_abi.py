@@ -1,0 +1,116 @@
+"""ctypes declarations of the C ABI in include/tn.h (argument marshalling only).
+
+Every computation happens in libtn.so; this module converts Python/NumPy/
+torch arguments to pointers and sizes and raises on a non-zero tn_status.
+Importing it fails loudly when the compiled library is missing: there is no
+CPU fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtn.so")
+
+TN_OK = 0
+STATUS = {0: "TN_OK", 1: "TN_EINVAL", 2: "TN_ENOMEM", 3: "TN_EHBM", 4: "TN_ECUDA", 5: "TN_ETIMEOUT",
+          6: "TN_ETOOBIG", 7: "TN_EOVERFLOW", 8: "TN_ENOTREADY", 9: "TN_ENODEVICE"}
+GATE_KINDS = {"sqrtx": 0, "sqrty": 1, "sqrtw": 2, "fsim": 3, "mat1": 4, "mat2": 5}
+PREC = {"c64": 0, "split_bf16": 1, "split_fp16": 2, "scaled_fp16": 3, "scaled_bf16": 4}
+PAIR_ALGO = {"auto": 0, "fused_simt": 1, "vector": 2, "fused_tc": 3, "unfused": 4}
+
+
+class TnError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Gate(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("q0", C.c_int32), ("q1", C.c_int32), ("reserved", C.c_int32),
+                ("theta", C.c_double), ("phi", C.c_double), ("mat", C.c_double * 32)]
+
+
+class NetworkInfo(C.Structure):
+    _fields_ = [("num_qubits", C.c_int32), ("num_open", C.c_int32), ("num_leaves", C.c_int32),
+                ("num_labels", C.c_int32), ("max_leaf_rank", C.c_int32), ("num_closed", C.c_int32)]
+
+
+class PlanOpts(C.Structure):
+    _fields_ = [("num_sliced", C.c_int32), ("max_log2_intermediate", C.c_int32), ("search_trials", C.c_int32),
+                ("reserved", C.c_int32), ("seed", C.c_uint64), ("max_log2_cmac", C.c_double)]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("num_qubits", C.c_int32), ("num_open", C.c_int32), ("num_sliced", C.c_int32),
+                ("num_steps", C.c_int32), ("num_leaves", C.c_int32), ("max_log2_intermediate", C.c_int32),
+                ("num_slices", C.c_int64), ("cmac_per_slice", C.c_double), ("flops_per_slice", C.c_double),
+                ("log2_cmac_total", C.c_double), ("footprint_bytes_per_unit", C.c_int64), ("hash", C.c_uint64),
+                ("num_dense_steps", C.c_int32), ("num_vector_steps", C.c_int32)]
+
+
+class ExecOpts(C.Structure):
+    _fields_ = [("stream", C.c_void_p), ("precision", C.c_int32), ("device_io", C.c_int32),
+                ("slice_begin", C.c_int64), ("slice_count", C.c_int64), ("units_per_group", C.c_int32),
+                ("overflow_policy", C.c_int32), ("use_graph", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Report(C.Structure):
+    _fields_ = [("device_ms", C.c_double), ("flops", C.c_double), ("units", C.c_int64),
+                ("kernel_launches", C.c_int64), ("flagged_units", C.c_int64), ("discarded_units", C.c_int64),
+                ("dominant_kernel_ms", C.c_double), ("dominant_kernel", C.c_int32), ("reserved", C.c_int32)]
+
+
+P = C.c_void_p
+I32P = C.POINTER(C.c_int32)
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "tn_last_error": (C.c_char_p, []),
+    "tn_version": (C.c_char_p, []),
+    "tn_random_circuit": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(P)]),
+    "tn_circuit_from_gates": (C.c_int, [C.c_int32, C.c_int64, C.POINTER(Gate), C.POINTER(P)]),
+    "tn_circuit_info": (C.c_int, [P, I32P, C.POINTER(C.c_int64)]),
+    "tn_circuit_gates": (C.c_int, [P, C.POINTER(Gate), C.c_int64]),
+    "tn_free_circuit": (None, [P]),
+    "tn_build_network": (C.c_int, [P, I32P, C.c_int32, C.POINTER(P)]),
+    "tn_network_get_info": (C.c_int, [P, C.POINTER(NetworkInfo)]),
+    "tn_network_label_wires": (C.c_int, [P, I32P, C.c_int64]),
+    "tn_free_network": (None, [P]),
+    "tn_plan": (C.c_int, [P, C.POINTER(PlanOpts), C.POINTER(P)]),
+    "tn_plan_get_info": (C.c_int, [P, C.POINTER(PlanInfo)]),
+    "tn_plan_sliced_wires": (C.c_int, [P, I32P, C.c_int64]),
+    "tn_plan_serialize": (C.c_int, [P, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "tn_plan_tree": (C.c_int, [P, I32P, C.c_int64, I32P, C.c_int64]),
+    "tn_free_plan": (None, [P]),
+    "tn_contract_amplitudes": (C.c_int, [P, C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(ExecOpts),
+                                         C.POINTER(Report)]),
+    "tn_contract_pair": (C.c_int, [C.c_void_p, I32P, C.c_int32, C.c_void_p, I32P, C.c_int32,
+                                   C.c_void_p, I32P, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
+}
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2110_14502_gb300.build.build()")
+        h = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(h, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = h
+    return _lib
+
+
+def check(status):
+    if status != TN_OK:
+        raise TnError(status, lib().tn_last_error().decode())
+
+
+def i32array(xs):
+    a = np.ascontiguousarray(np.asarray(list(xs), dtype=np.int32))
+    return a, (a.ctypes.data_as(I32P) if a.size else None)

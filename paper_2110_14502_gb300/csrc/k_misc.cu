@@ -1,0 +1,111 @@
+// Slice selection, cross-slice FP64 summation and a plain permutation kernel.
+//
+// Slice selection (paper: Sec. "A PEPS-based Simulation Method with an
+// Optimized Slicing Strategy"): each (bitstring, slice) unit fixes the sliced
+// indices to the bits of its slice id and the closed output indices to the
+// bits of its bitstring; every leaf tensor carrying such an index contributes
+// the corresponding sub-tensor.  Cross-slice sum (paper: Sec. "Scaling",
+// global reduction of the slice results): the per-unit results are added in
+// FP64 in unit order, so the sum order is fixed for a given call.
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace tn {
+
+namespace {
+
+__global__ void gather_kernel(const float2* __restrict__ store, float2* __restrict__ arena, int64_t arena_stride,
+                              const LeafGather* __restrict__ descs, const uint64_t* __restrict__ bits,
+                              GroupInfo g) {
+  const LeafGather& L = descs[blockIdx.x];
+  const int u = blockIdx.y;
+  const int64_t gu = g.unit0 + u;
+  const int64_t b = gu / g.slices;
+  const int64_t s = g.slice_begin + gu % g.slices;
+  int64_t fixed_off = L.store_off;
+  for (int f = 0; f < L.nfixed; ++f) {
+    int src = L.fixed_src[f];
+    int v;
+    if (src >= 0) v = (int)((s >> src) & 1);
+    else {
+      int q = -src - 2;
+      v = (int)((bits[b * g.words + (q >> 6)] >> (q & 63)) & 1);
+    }
+    if (v) fixed_off += L.fixed_stride[f];
+  }
+  const int sub = 1 << L.nkept;
+  float2* dst = arena + (int64_t)u * arena_stride + L.dst_off;
+  for (int e = threadIdx.x; e < sub; e += blockDim.x) {
+    int64_t o = fixed_off;
+    for (int p = 0; p < L.nkept; ++p)
+      if ((e >> (L.nkept - 1 - p)) & 1) o += L.kept_stride[p];
+    dst[e] = store[o];
+  }
+}
+
+// acc[b, j] += sum over the group's units of bitstring b (in unit order) of root_u[perm[j]].
+__global__ void accumulate_kernel(const float2* __restrict__ root, int64_t root_unit_stride,
+                                  const int64_t* __restrict__ perm, int nperm, double2* __restrict__ acc,
+                                  GroupInfo g) {
+  const int64_t b_first = g.unit0 / g.slices;
+  const int64_t b_last = (g.unit0 + g.units - 1) / g.slices;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nbl = b_last - b_first + 1;
+  if (idx >= nbl * nperm) return;
+  const int64_t b = b_first + idx / nperm;
+  const int j = (int)(idx % nperm);
+  int64_t u_lo = b * g.slices - g.unit0, u_hi = (b + 1) * g.slices - g.unit0;
+  if (u_lo < 0) u_lo = 0;
+  if (u_hi > g.units) u_hi = g.units;
+  double2 a = acc[b * nperm + j];
+  const int64_t pj = perm[j];
+  for (int64_t u = u_lo; u < u_hi; ++u) {
+    float2 v = root[u * root_unit_stride + pj];
+    a.x += (double)v.x;
+    a.y += (double)v.y;
+  }
+  acc[b * nperm + j] = a;
+}
+
+__global__ void permute_kernel(const float2* __restrict__ src, float2* __restrict__ dst, const PermDesc pd,
+                               int64_t src_unit, int64_t dst_unit) {
+  const int64_t n = int64_t(1) << pd.rank;
+  const int64_t u = blockIdx.y;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t o = 0;
+    for (int p = 0; p < pd.rank; ++p)
+      if ((e >> p) & 1) o += pd.st[p];
+    dst[u * dst_unit + e] = src[u * src_unit + o];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gather(const float2* store, float2* arena, int64_t arena_stride, const LeafGather* descs,
+                          int nleaves, const uint64_t* bits, const GroupInfo& g, cudaStream_t s) {
+  if (nleaves == 0 || g.units == 0) return cudaSuccess;
+  dim3 grid((unsigned)nleaves, (unsigned)g.units);
+  gather_kernel<<<grid, 64, 0, s>>>(store, arena, arena_stride, descs, bits, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(const float2* root, int64_t root_unit_stride, const int64_t* perm, int nperm,
+                              double2* acc, const GroupInfo& g, cudaStream_t s) {
+  const int64_t b_first = g.unit0 / g.slices;
+  const int64_t b_last = (g.unit0 + g.units - 1) / g.slices;
+  const int64_t total = (b_last - b_first + 1) * nperm;
+  const int nt = 256;
+  accumulate_kernel<<<(unsigned)((total + nt - 1) / nt), nt, 0, s>>>(root, root_unit_stride, perm, nperm, acc, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute(const float2* src, float2* dst, const PermDesc& pd, int64_t units, int64_t src_unit,
+                           int64_t dst_unit, cudaStream_t s) {
+  int64_t n = int64_t(1) << pd.rank;
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  permute_kernel<<<dim3(blocks, (unsigned)units), 256, 0, s>>>(src, dst, pd, src_unit, dst_unit);
+  return cudaGetLastError();
+}
+
+}  // namespace tn

@@ -1,0 +1,127 @@
+// Bandwidth-bound contraction for vector-like steps (N <= 16 and K <= 16).
+//
+// Paper: Sec. "Tensor Contraction Using Fused Permutation and
+// Multiplication", imbalanced case (a high-rank tensor against a rank-4 one):
+// the small operand is kept in fast memory and the large one is streamed once.
+// Here the small operand B (K x N complex) sits in shared memory, each thread
+// owns rows m of the large operand, reads its K elements and writes its N
+// outputs; consecutive threads take consecutive m, so with the step's bit
+// order (bit 0 = most contiguous index) both the stream of A and the store of
+// C coalesce.  The row offsets come from two 32-entry position tables per
+// CTA plus one CTA base (the bits of m are disjoint, so offsets add).
+#include "kernels.h"
+
+namespace tn {
+
+namespace {
+
+constexpr int NT = 256;
+constexpr int PER = 4;                 // rows per thread
+constexpr int CH_BITS = 10;            // 1024 rows per CTA
+constexpr int CH = 1 << CH_BITS;
+static_assert(NT * PER == CH, "chunk");
+
+__device__ __forceinline__ int32_t bit_offset(int64_t x, int nb, const int32_t* st) {
+  int32_t o = 0;
+  for (int i = 0; i < nb; ++i)
+    if ((x >> i) & 1) o += st[i];
+  return o;
+}
+
+template <int NK, int NN>
+__global__ void __launch_bounds__(NT) vector_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
+                                                    float2* __restrict__ C, const GemmDesc d) {
+  constexpr int K = 1 << NK, N = 1 << NN;
+  const int64_t M = int64_t(1) << d.nm;
+  const int64_t u = blockIdx.y;
+  A += u * d.a_unit;
+  B += u * d.b_unit;
+  C += u * d.c_unit;
+  __shared__ float2 Bs[K * N];
+  __shared__ int32_t kA[K], nC[N];
+  __shared__ int32_t tAlo[32], tAhi[32], tClo[32], tChi[32];
+  const int tid = threadIdx.x;
+  const int64_t base = (int64_t)blockIdx.x * CH;
+  for (int e = tid; e < K * N; e += NT) {
+    int k = e / N, n = e % N;
+    Bs[e] = B[bit_offset(k, NK, d.bk) + bit_offset(n, NN, d.bn)];
+  }
+  if (tid < K) kA[tid] = bit_offset(tid, NK, d.ak);
+  if (tid >= 64 && tid < 64 + N) nC[tid - 64] = bit_offset(tid - 64, NN, d.cn);
+  const int lb = d.nm < CH_BITS ? d.nm : CH_BITS;  // bits of m inside the chunk
+  if (tid >= 128 && tid < 160) {
+    int x = tid - 128;
+    int b0 = lb < 5 ? lb : 5;
+    tAlo[x] = x < (1 << b0) ? bit_offset(x, b0, d.am) : 0;
+    tClo[x] = x < (1 << b0) ? bit_offset(x, b0, d.cm) : 0;
+  }
+  if (tid >= 160 && tid < 192) {
+    int x = tid - 160;
+    int b1 = lb > 5 ? lb - 5 : 0;
+    tAhi[x] = x < (1 << b1) ? bit_offset(x, b1, d.am + 5) : 0;
+    tChi[x] = x < (1 << b1) ? bit_offset(x, b1, d.cm + 5) : 0;
+  }
+  // CTA base offsets from the bits of m above the chunk
+  __shared__ int32_t baseA, baseC;
+  if (tid == 0) {
+    int32_t oa = 0, oc = 0;
+    for (int i = CH_BITS; i < d.nm; ++i)
+      if ((base >> i) & 1) { oa += d.am[i]; oc += d.cm[i]; }
+    baseA = oa;
+    baseC = oc;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    int loc = tid + r * NT;
+    if (base + loc >= M) break;
+    int32_t oa = baseA + tAlo[loc & 31] + tAhi[loc >> 5];
+    int32_t oc = baseC + tClo[loc & 31] + tChi[loc >> 5];
+    float2 a[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] = __ldg(A + (int64_t)oa + kA[k]);
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        float2 b = Bs[k * N + n];
+        acc.x = fmaf(a[k].x, b.x, acc.x);
+        acc.x = fmaf(-a[k].y, b.y, acc.x);
+        acc.y = fmaf(a[k].x, b.y, acc.y);
+        acc.y = fmaf(a[k].y, b.x, acc.y);
+      }
+      C[(int64_t)oc + nC[n]] = acc;
+    }
+  }
+}
+
+template <int NK>
+cudaError_t launch_nn(const float2* A, const float2* B, float2* C, const GemmDesc& d, dim3 g, cudaStream_t s) {
+  switch (d.nn) {
+    case 0: vector_kernel<NK, 0><<<g, NT, 0, s>>>(A, B, C, d); break;
+    case 1: vector_kernel<NK, 1><<<g, NT, 0, s>>>(A, B, C, d); break;
+    case 2: vector_kernel<NK, 2><<<g, NT, 0, s>>>(A, B, C, d); break;
+    case 3: vector_kernel<NK, 3><<<g, NT, 0, s>>>(A, B, C, d); break;
+    case 4: vector_kernel<NK, 4><<<g, NT, 0, s>>>(A, B, C, d); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s) {
+  if (d.nk > 4 || d.nn > 4 || d.units > 65535) return cudaErrorInvalidValue;
+  int64_t M = int64_t(1) << d.nm;
+  dim3 g((unsigned)((M + CH - 1) / CH), (unsigned)d.units);
+  switch (d.nk) {
+    case 0: return launch_nn<0>(A, B, C, d, g, s);
+    case 1: return launch_nn<1>(A, B, C, d, g, s);
+    case 2: return launch_nn<2>(A, B, C, d, g, s);
+    case 3: return launch_nn<3>(A, B, C, d, g, s);
+    default: return launch_nn<4>(A, B, C, d, g, s);
+  }
+}
+
+}  // namespace tn

@@ -1,0 +1,72 @@
+// Device-side descriptors and kernel launchers shared by the executor and the
+// pairwise-contraction entry point.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+#include <cuda_runtime.h>
+
+namespace tn {
+
+constexpr int kMaxBits = 32;
+
+// One pairwise contraction C[m, n] = sum_k A[m, k] B[k, n] with M = 2^nm,
+// N = 2^nn, K = 2^nk, where every operand is addressed through per-bit
+// element strides: the index permutation of each operand (paper: Sec. "Tensor
+// Contraction Using Fused Permutation and Multiplication") is folded into the
+// address arithmetic instead of being materialised.  Element (m, k) of A sits
+// at sum_i bit_i(m) am[i] + sum_l bit_l(k) ak[l] (+ unit * a_unit), and
+// likewise for B (k, n) and C (m, n).  Bits are numbered so that bit 0 is the
+// operand's most contiguous index of that group.
+struct GemmDesc {
+  int nm, nn, nk;
+  int units;                 // grid extent over (bitstring, slice) units
+  int64_t a_unit, b_unit, c_unit;  // element stride between units (0 = shared operand)
+  int32_t am[kMaxBits], cm[kMaxBits];
+  int32_t bn[kMaxBits], cn[kMaxBits];
+  int32_t ak[kMaxBits], bk[kMaxBits];
+};
+
+// Variant leaf: the sub-tensor of one unit is the full leaf with its fixed
+// indices set to the unit's values (sliced index j <- bit j of the slice id;
+// closed output qubit q <- bit q of the bitstring).
+constexpr int kMaxLeafRank = 12;
+struct LeafGather {
+  int64_t store_off;         // full leaf in the leaf store
+  int64_t dst_off;           // sub-tensor in the unit arena
+  int32_t nkept, nfixed;
+  int32_t kept_stride[kMaxLeafRank];   // full-leaf stride of each kept index, slowest first
+  int32_t fixed_src[kMaxLeafRank];     // >= 0: slice bit j; <= -2: closed qubit (-src-2)
+  int32_t fixed_stride[kMaxLeafRank];
+};
+
+struct GroupInfo {
+  int64_t unit0;             // first global unit of the group
+  int64_t slices;            // slices per bitstring in this call
+  int64_t slice_begin;
+  int32_t words;             // uint64 words per bitstring
+  int32_t units;             // units in this group
+};
+
+// launchers (return cudaGetLastError())
+cudaError_t launch_gemm_simt(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s);
+cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s);
+cudaError_t launch_gather(const float2* store, float2* arena, int64_t arena_stride, const LeafGather* descs,
+                          int nleaves, const uint64_t* bits, const GroupInfo& g, cudaStream_t s);
+cudaError_t launch_accumulate(const float2* root, int64_t root_unit_stride, const int64_t* perm, int nperm,
+                              double2* acc, const GroupInfo& g, cudaStream_t s);
+// dst (dense, element e) = src[sum_p bit_p(e) * st[p]]: bit p of e is dst's
+// p-th fastest index, st[p] its element stride in src.
+struct PermDesc {
+  int rank;
+  int32_t st[kMaxBits];
+};
+cudaError_t launch_permute(const float2* src, float2* dst, const PermDesc& p, int64_t units, int64_t src_unit,
+                           int64_t dst_unit, cudaStream_t s);
+
+struct Step;
+// GEMM view (per-bit strides) of one pairwise step.
+void make_gemm_desc(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc,
+                    GemmDesc& d);
+
+}  // namespace tn

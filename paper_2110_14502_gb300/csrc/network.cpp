@@ -1,0 +1,205 @@
+// Tensor network of <x|U|0^n> (paper: Sec. "Existing Efforts on Simulation of
+// RQCs" -- a one-qubit gate is a rank-2 tensor, a two-qubit gate a rank-4
+// tensor), with closed output wires kept as fixed indices and small tensors
+// absorbed into neighbours.
+#include <algorithm>
+#include <cstring>
+#include <map>
+
+#include "tn_internal.h"
+
+namespace tn {
+
+// Host FP64 pairwise contraction of small tensors.  Result labels: U's
+// unshared labels, then T's unshared labels.
+static Leaf contract_small(const Leaf& U, const Leaf& T) {
+  Leaf R;
+  std::vector<int> shared;
+  for (int l : U.labels)
+    if (std::find(T.labels.begin(), T.labels.end(), l) != T.labels.end()) shared.push_back(l);
+  for (int l : U.labels)
+    if (std::find(shared.begin(), shared.end(), l) == shared.end()) R.labels.push_back(l);
+  for (int l : T.labels)
+    if (std::find(shared.begin(), shared.end(), l) == shared.end()) R.labels.push_back(l);
+  std::vector<int> uni = R.labels;
+  uni.insert(uni.end(), shared.begin(), shared.end());
+  const int nu = (int)uni.size(), nr = (int)R.labels.size();
+  auto pos_in = [&](const std::vector<int>& ls, int l) {
+    for (size_t i = 0; i < ls.size(); ++i)
+      if (ls[i] == l) return (int)i;
+    return -1;
+  };
+  // stride of each union label within U, T, R
+  std::vector<int64_t> su(nu, 0), st(nu, 0), sr(nu, 0);
+  for (int i = 0; i < nu; ++i) {
+    int p;
+    if ((p = pos_in(U.labels, uni[i])) >= 0) su[i] = int64_t(1) << (U.labels.size() - 1 - p);
+    if ((p = pos_in(T.labels, uni[i])) >= 0) st[i] = int64_t(1) << (T.labels.size() - 1 - p);
+    if ((p = pos_in(R.labels, uni[i])) >= 0) sr[i] = int64_t(1) << (R.labels.size() - 1 - p);
+  }
+  R.data.assign(size_t(1) << nr, cd(0, 0));
+  for (int64_t x = 0; x < (int64_t(1) << nu); ++x) {
+    int64_t ou = 0, ot = 0, orr = 0;
+    for (int i = 0; i < nu; ++i)
+      if ((x >> i) & 1) { ou += su[i]; ot += st[i]; orr += sr[i]; }
+    R.data[orr] += U.data[ou] * T.data[ot];
+  }
+  R.raw = U.raw;
+  R.raw.insert(R.raw.end(), T.raw.begin(), T.raw.end());
+  return R;
+}
+
+tn_status build_network(const Circuit& c, const int32_t* open, int num_open, Network& net) {
+  const int n = c.n;
+  net = Network();
+  net.n = n;
+  net.num_gates = (int)c.gates.size();
+  net.open_qubits.assign(open, open + num_open);
+  std::vector<int> seg(n, 0), cur(n, -1);
+  auto new_label = [&](int q, int t) {
+    net.wire.push_back({q, t});
+    net.kind.push_back(LK_INTERNAL);
+    net.closed_qubit.push_back(-1);
+    net.open_bit.push_back(-1);
+    return (int)net.wire.size() - 1;
+  };
+  std::vector<Leaf> leaves;
+  for (int q = 0; q < n; ++q) {
+    cur[q] = new_label(q, 0);
+    Leaf L;
+    L.labels = {cur[q]};
+    L.data = {cd(1, 0), cd(0, 0)};
+    L.raw = {net.num_gates + q};
+    leaves.push_back(L);
+  }
+  for (int i = 0; i < net.num_gates; ++i) {
+    const Gate& g = c.gates[i];
+    Leaf L;
+    L.raw = {i};
+    if (g.nq() == 1) {
+      int lin = cur[g.q0];
+      int lout = new_label(g.q0, ++seg[g.q0]);
+      cur[g.q0] = lout;
+      L.labels = {lout, lin};
+      L.data.assign(g.m, g.m + 4);
+    } else {
+      int ain = cur[g.q0], bin = cur[g.q1];
+      int aout = new_label(g.q0, ++seg[g.q0]);
+      int bout = new_label(g.q1, ++seg[g.q1]);
+      cur[g.q0] = aout;
+      cur[g.q1] = bout;
+      L.labels = {aout, bout, ain, bin};  // T[xa',xb',xa,xb] = m[(2xa'+xb')*4 + 2xa+xb]
+      L.data.assign(g.m, g.m + 16);
+    }
+    leaves.push_back(L);
+  }
+  for (int q = 0; q < n; ++q) {
+    int t = -1;
+    for (int k = 0; k < num_open; ++k)
+      if (open[k] == q) t = k;
+    if (t >= 0) {
+      net.kind[cur[q]] = LK_OPEN;
+      net.open_bit[cur[q]] = t;
+    } else {
+      net.kind[cur[q]] = LK_CLOSED;
+      net.closed_qubit[cur[q]] = q;
+    }
+  }
+  // Absorb tensors of topological rank <= 2 (closed outputs do not count)
+  // into the neighbour sharing the most labels (ties: lowest index).
+  std::vector<char> alive(leaves.size(), 1);
+  std::map<int, std::vector<int>> holders;
+  for (size_t i = 0; i < leaves.size(); ++i)
+    for (int l : leaves[i].labels) holders[l].push_back((int)i);
+  auto topo_rank = [&](const Leaf& L) {
+    int r = 0;
+    for (int l : L.labels) r += net.kind[l] != LK_CLOSED;
+    return r;
+  };
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    for (size_t i = 0; i < leaves.size(); ++i) {
+      if (!alive[i] || topo_rank(leaves[i]) > 2) continue;
+      int best = -1, best_shared = 0;
+      for (int l : leaves[i].labels) {
+        for (int j : holders[l]) {
+          if (j == (int)i || !alive[j]) continue;
+          int sh = 0;
+          for (int x : leaves[i].labels)
+            for (int y : leaves[j].labels) sh += (x == y);
+          if (sh > best_shared || (sh == best_shared && j < best)) { best = j; best_shared = sh; }
+        }
+      }
+      if (best < 0) continue;
+      Leaf R = contract_small(leaves[best], leaves[i]);
+      for (int l : leaves[i].labels) {
+        auto& h = holders[l];
+        h.erase(std::remove(h.begin(), h.end(), (int)i), h.end());
+      }
+      for (int l : leaves[best].labels) {
+        auto& h = holders[l];
+        h.erase(std::remove(h.begin(), h.end(), best), h.end());
+      }
+      alive[i] = 0;
+      leaves[best] = std::move(R);
+      for (int l : leaves[best].labels) holders[l].push_back(best);
+      changed = true;
+    }
+  }
+  for (size_t i = 0; i < leaves.size(); ++i)
+    if (alive[i]) net.leaves.push_back(std::move(leaves[i]));
+  return TN_OK;
+}
+
+}  // namespace tn
+
+using namespace tn;
+
+extern "C" tn_status tn_build_network(const tn_circuit* c, const int32_t* open, int32_t num_open,
+                                      tn_network** out) {
+  if (!c || !out) return fail(TN_EINVAL, "tn_build_network: NULL argument");
+  if (num_open < 0 || num_open > 30 || (num_open > 0 && !open))
+    return fail(TN_EINVAL, "tn_build_network: num_open %d not in [0, 30] or open_qubits NULL", num_open);
+  for (int i = 0; i < num_open; ++i) {
+    if (open[i] < 0 || open[i] >= c->c.n)
+      return fail(TN_EINVAL, "tn_build_network: open qubit %d out of range", open[i]);
+    for (int j = 0; j < i; ++j)
+      if (open[j] == open[i]) return fail(TN_EINVAL, "tn_build_network: open qubit %d repeated", open[i]);
+  }
+  auto* h = new (std::nothrow) tn_network_s;
+  if (!h) return fail(TN_ENOMEM, "tn_build_network: out of host memory");
+  tn_status st = build_network(c->c, open, num_open, h->net);
+  if (st != TN_OK) { delete h; return st; }
+  *out = h;
+  return TN_OK;
+}
+
+extern "C" tn_status tn_network_get_info(const tn_network* net, tn_network_info* info) {
+  if (!net || !info) return fail(TN_EINVAL, "tn_network_get_info: NULL argument");
+  const Network& N = net->net;
+  info->num_qubits = N.n;
+  info->num_open = (int)N.open_qubits.size();
+  info->num_leaves = (int)N.leaves.size();
+  info->num_labels = N.num_labels();
+  int mr = 0;
+  for (auto& L : N.leaves) mr = std::max(mr, (int)L.labels.size());
+  info->max_leaf_rank = mr;
+  int nc = 0;
+  for (int k : N.kind) nc += k == LK_CLOSED;
+  info->num_closed = nc;
+  return TN_OK;
+}
+
+extern "C" tn_status tn_network_label_wires(const tn_network* net, int32_t* pairs, int64_t cap) {
+  if (!net || !pairs) return fail(TN_EINVAL, "tn_network_label_wires: NULL argument");
+  const Network& N = net->net;
+  if (cap < N.num_labels()) return fail(TN_EINVAL, "tn_network_label_wires: capacity too small");
+  for (int l = 0; l < N.num_labels(); ++l) {
+    pairs[2 * l] = N.wire[l].first;
+    pairs[2 * l + 1] = N.wire[l].second;
+  }
+  return TN_OK;
+}
+
+extern "C" void tn_free_network(tn_network* net) { delete net; }

@@ -1,0 +1,129 @@
+// tn_contract_pair: one pairwise contraction on device tensors, through the
+// executor's kernels (fused) or as permute -> library GEMM -> permute
+// (unfused, the comparison baseline of the microbenchmark).
+#include <cublas_v2.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "kernels.h"
+#include "tn_internal.h"
+
+namespace tn {
+
+static tn_status check_labels(const int32_t* la, int ra, const int32_t* lb, int rb, const int32_t* lc, int rc) {
+  auto has = [](const int32_t* l, int r, int x) { return std::find(l, l + r, x) != l + r; };
+  auto distinct = [](const int32_t* l, int r) {
+    std::vector<int> v(l, l + r);
+    std::sort(v.begin(), v.end());
+    return std::adjacent_find(v.begin(), v.end()) == v.end();
+  };
+  if (!distinct(la, ra) || !distinct(lb, rb) || !distinct(lc, rc))
+    return fail(TN_EINVAL, "tn_contract_pair: repeated label within a tensor");
+  for (int i = 0; i < rc; ++i)
+    if (has(la, ra, lc[i]) == has(lb, rb, lc[i]))
+      return fail(TN_EINVAL, "tn_contract_pair: output label %d must appear in exactly one operand", lc[i]);
+  for (int i = 0; i < ra; ++i)
+    if (!has(lb, rb, la[i]) && !has(lc, rc, la[i]))
+      return fail(TN_EINVAL, "tn_contract_pair: label %d of A is neither contracted nor in C", la[i]);
+  for (int i = 0; i < rb; ++i)
+    if (!has(la, ra, lb[i]) && !has(lc, rc, lb[i]))
+      return fail(TN_EINVAL, "tn_contract_pair: label %d of B is neither contracted nor in C", lb[i]);
+  return TN_OK;
+}
+
+static cublasHandle_t cublas_handle(int dev) {
+  static std::mutex mu;
+  static std::vector<cublasHandle_t> hs;
+  std::lock_guard<std::mutex> g(mu);
+  if ((int)hs.size() <= dev) hs.resize(dev + 1, nullptr);
+  if (!hs[dev] && cublasCreate(&hs[dev]) != CUBLAS_STATUS_SUCCESS) hs[dev] = nullptr;
+  return hs[dev];
+}
+
+static tn_status unfused(const float2* A, const float2* B, float2* Cp, const GemmDesc& d, cudaStream_t st) {
+  const int64_t M = int64_t(1) << d.nm, N = int64_t(1) << d.nn, K = int64_t(1) << d.nk;
+  float2 *Ap = nullptr, *Bp = nullptr, *Cg = nullptr;
+  auto cleanup = [&]() {
+    if (Ap) cudaFreeAsync(Ap, st);
+    if (Bp) cudaFreeAsync(Bp, st);
+    if (Cg) cudaFreeAsync(Cg, st);
+  };
+  if (cudaMallocAsync(&Ap, M * K * sizeof(float2), st) != cudaSuccess ||
+      cudaMallocAsync(&Bp, K * N * sizeof(float2), st) != cudaSuccess ||
+      cudaMallocAsync(&Cg, M * N * sizeof(float2), st) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(TN_EHBM, "tn_contract_pair: unfused scratch allocation failed");
+  }
+  PermDesc pa{}, pb{}, pc{};
+  pa.rank = d.nm + d.nk;  // A' row-major [m][k]
+  for (int l = 0; l < d.nk; ++l) pa.st[l] = d.ak[l];
+  for (int i = 0; i < d.nm; ++i) pa.st[d.nk + i] = d.am[i];
+  pb.rank = d.nk + d.nn;  // B' row-major [k][n]
+  for (int j = 0; j < d.nn; ++j) pb.st[j] = d.bn[j];
+  for (int l = 0; l < d.nk; ++l) pb.st[d.nn + l] = d.bk[l];
+  // C (its own layout) gathers from C' row-major [m][n]: bit p of C's index
+  pc.rank = d.nm + d.nn;
+  for (int i = 0; i < d.nm; ++i) pc.st[__builtin_ctz(d.cm[i])] = (int32_t)(N << i);
+  for (int j = 0; j < d.nn; ++j) pc.st[__builtin_ctz(d.cn[j])] = int32_t(1) << j;
+  cudaError_t e = launch_permute(A, Ap, pa, 1, 0, 0, st);
+  if (e == cudaSuccess) e = launch_permute(B, Bp, pb, 1, 0, 0, st);
+  if (e != cudaSuccess) { cleanup(); return fail(TN_ECUDA, "unfused permute: %s", cudaGetErrorString(e)); }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cublasHandle_t h = cublas_handle(dev);
+  if (!h) { cleanup(); return fail(TN_ECUDA, "cublasCreate failed"); }
+  cublasSetStream(h, st);
+  const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
+  // row-major C'[M][N] = A'[M][K] B'[K][N]  <=>  column-major C'^T = B'^T A'^T
+  cublasStatus_t cs = cublasCgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, (int)M, (int)K, &one, (const cuComplex*)Bp,
+                                  (int)N, (const cuComplex*)Ap, (int)K, &zero, (cuComplex*)Cg, (int)N);
+  if (cs != CUBLAS_STATUS_SUCCESS) { cleanup(); return fail(TN_ECUDA, "cublasCgemm failed (%d)", (int)cs); }
+  e = launch_permute(Cg, Cp, pc, 1, 0, 0, st);
+  cleanup();
+  if (e != cudaSuccess) return fail(TN_ECUDA, "unfused permute: %s", cudaGetErrorString(e));
+  return TN_OK;
+}
+
+}  // namespace tn
+
+using namespace tn;
+
+extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, int32_t ra, const void* B,
+                                      const int32_t* b_labels, int32_t rb, void* Cv, const int32_t* c_labels,
+                                      int32_t rc, int32_t precision, int32_t algo, void* stream) {
+  if (!A || !B || !Cv) return fail(TN_EINVAL, "tn_contract_pair: NULL tensor");
+  if (ra < 0 || rb < 0 || rc < 0 || ra > 30 || rb > 30 || rc > 30)
+    return fail(TN_EINVAL, "tn_contract_pair: ranks must be in [0, 30]");
+  if ((ra && !a_labels) || (rb && !b_labels) || (rc && !c_labels))
+    return fail(TN_EINVAL, "tn_contract_pair: NULL labels");
+  tn_status st = check_labels(a_labels, ra, b_labels, rb, c_labels, rc);
+  if (st != TN_OK) return st;
+  if (precision != TN_PREC_C64 && precision != TN_PREC_SPLIT_BF16 && precision != TN_PREC_SPLIT_FP16)
+    return fail(TN_EINVAL, "tn_contract_pair: precision %d is not a complex64-storage mode", precision);
+  std::vector<int> la(a_labels, a_labels + ra), lb(b_labels, b_labels + rb), lc(c_labels, c_labels + rc);
+  GemmDesc d;
+  make_gemm_desc(la, lb, lc, d);
+  d.units = 1;
+  d.a_unit = d.b_unit = d.c_unit = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  const float2* a = (const float2*)A;
+  const float2* b = (const float2*)B;
+  float2* c = (float2*)Cv;
+  if (algo == TN_PAIR_AUTO) algo = (d.nn <= 4 && d.nk <= 4) ? TN_PAIR_VECTOR : TN_PAIR_FUSED_SIMT;
+  cudaError_t e;
+  switch (algo) {
+    case TN_PAIR_FUSED_SIMT: e = launch_gemm_simt(a, b, c, d, s); break;
+    case TN_PAIR_VECTOR:
+      if (d.nn > 4 || d.nk > 4) return fail(TN_EINVAL, "tn_contract_pair: vector kernel needs N, K <= 16");
+      e = launch_vector(a, b, c, d, s);
+      break;
+    case TN_PAIR_UNFUSED: return unfused(a, b, c, d, s);
+    default: return fail(TN_EINVAL, "tn_contract_pair: algo %d not available for precision %d", algo, precision);
+  }
+  if (e != cudaSuccess) return fail(TN_ECUDA, "tn_contract_pair launch: %s", cudaGetErrorString(e));
+  return TN_OK;
+}

@@ -1,0 +1,774 @@
+// Contraction-order search, slicing, step layout and memory planning.
+//
+// Paper: Sec. "Searching for Better Contraction Paths with a Reduced
+// Complexity" (the path decides the cost by orders of magnitude; the loss
+// weighs complexity together with compute density) and Sec. "A PEPS-based
+// Simulation Method with an Optimized Slicing Strategy" (slice S indices so
+// each of the 2^S sub-networks fits in memory; the sub-networks are
+// independent and their results are summed).
+//
+// Order search: many randomized trials of two generators -- a greedy pairwise
+// merge with a noisy size score, and recursive bisection of the network graph
+// refined with Fiduccia-Mattheyses moves -- each followed by greedy slicing.
+// The trial with the smallest modelled GB300 time wins (the compute-density
+// term: a step's time is the larger of its flops at the rate its kernel class
+// reaches and its bytes at HBM bandwidth).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <numeric>
+#include <random>
+
+#include "tn_internal.h"
+
+namespace tn {
+
+namespace {
+
+using LSet = std::vector<int>;  // sorted label ids
+
+LSet sym_diff(const LSet& a, const LSet& b) {
+  LSet r;
+  std::set_symmetric_difference(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(r));
+  return r;
+}
+int union_size(const LSet& a, const LSet& b) {
+  int i = 0, j = 0, n = 0;
+  while (i < (int)a.size() && j < (int)b.size()) {
+    if (a[i] == b[j]) { ++i; ++j; }
+    else if (a[i] < b[j]) ++i;
+    else ++j;
+    ++n;
+  }
+  return n + (int)(a.size() - i) + (int)(b.size() - j);
+}
+int shared_count(const LSet& a, const LSet& b) {
+  return (int)a.size() + (int)b.size() - union_size(a, b);
+}
+bool contains(const LSet& a, int l) { return std::binary_search(a.begin(), a.end(), l); }
+
+// Modelled GB300 time of one step with operand widths wa, wb and wu = |A u B|.
+double step_time(int wa, int wb, int wc, int wu) {
+  double flops = 8.0 * std::ldexp(1.0, wu);
+  double bytes = 8.0 * (std::ldexp(1.0, wa) + std::ldexp(1.0, wb) + std::ldexp(1.0, wc));
+  int nk = (wa + wb - wc) / 2;
+  int nm = wa - nk, nn = wb - nk;
+  if (nm < nn) std::swap(nm, nn);
+  bool dense = nm >= 7 && nn >= 3 && nk >= 3;
+  double rate = dense ? 6.0e14 : 6.0e13;
+  return std::max(flops / rate, bytes / 6.0e12) + 1.5e-7;
+}
+
+struct Builder {
+  std::vector<LSet> sets;           // per SSA id
+  std::vector<int> pairs;           // flattened SSA pairs
+  explicit Builder(const std::vector<LSet>& leaves) : sets(leaves) {}
+  int join(int a, int b) {
+    sets.push_back(sym_diff(sets[a], sets[b]));
+    pairs.push_back(a);
+    pairs.push_back(b);
+    return (int)sets.size() - 1;
+  }
+};
+
+// Randomized greedy merge of the given ids (any SSA ids) into one root.
+int greedy_join(Builder& B, std::vector<int> ids, double alpha, double tau, std::mt19937_64& rng) {
+  if (ids.empty()) return -1;
+  std::uniform_real_distribution<double> U(1e-12, 1.0);
+  struct Cand { double s; int i, j; bool operator<(const Cand& o) const { return s > o.s; } };
+  std::vector<char> alive;
+  auto ensure = [&](int id) { if ((int)alive.size() <= id) alive.resize(id + 1, 0); };
+  for (int id : ids) { ensure(id); alive[id] = 1; }
+  // label -> active holders
+  std::vector<std::vector<int>> holders;
+  auto add_holder = [&](int id) {
+    for (int l : B.sets[id]) {
+      if ((int)holders.size() <= l) holders.resize(l + 1);
+      holders[l].push_back(id);
+    }
+  };
+  for (int id : ids) add_holder(id);
+  auto score = [&](int i, int j) {
+    const LSet &a = B.sets[i], &b = B.sets[j];
+    int wc = (int)a.size() + (int)b.size() - 2 * shared_count(a, b);
+    double s = std::log2(std::ldexp(1.0, wc)) - alpha * std::log2(std::ldexp(1.0, (int)a.size()) + std::ldexp(1.0, (int)b.size()));
+    if (tau > 0) s -= tau * (-std::log(-std::log(U(rng))));
+    return s;
+  };
+  std::vector<Cand> heap;
+  auto push_pairs_of = [&](int id) {
+    for (int l : B.sets[id]) {
+      if (l >= (int)holders.size()) continue;
+      for (int o : holders[l])
+        if (o != id && alive[o]) {
+          heap.push_back({score(std::min(o, id), std::max(o, id)), std::min(o, id), std::max(o, id)});
+          std::push_heap(heap.begin(), heap.end());
+        }
+    }
+  };
+  for (int id : ids) push_pairs_of(id);
+  int remaining = (int)ids.size();
+  int last = ids[0];
+  while (remaining > 1) {
+    int i = -1, j = -1;
+    while (!heap.empty()) {
+      std::pop_heap(heap.begin(), heap.end());
+      Cand c = heap.back();
+      heap.pop_back();
+      if (alive[c.i] && alive[c.j]) { i = c.i; j = c.j; break; }
+    }
+    if (i < 0) {  // disconnected: join the two smallest
+      std::vector<int> act;
+      for (int id = 0; id < (int)alive.size(); ++id)
+        if (alive[id]) act.push_back(id);
+      std::sort(act.begin(), act.end(), [&](int x, int y) {
+        return B.sets[x].size() != B.sets[y].size() ? B.sets[x].size() < B.sets[y].size() : x < y;
+      });
+      i = act[0]; j = act[1];
+    }
+    alive[i] = alive[j] = 0;
+    for (int l : B.sets[i]) { auto& h = holders[l]; h.erase(std::remove(h.begin(), h.end(), i), h.end()); }
+    for (int l : B.sets[j]) { auto& h = holders[l]; h.erase(std::remove(h.begin(), h.end(), j), h.end()); }
+    int nid = B.join(i, j);
+    ensure(nid);
+    alive[nid] = 1;
+    add_holder(nid);
+    push_pairs_of(nid);
+    last = nid;
+    --remaining;
+  }
+  return last;
+}
+
+// Fiduccia-Mattheyses bisection of `ids` (leaf-level SSA ids) minimising the
+// number of shared labels cut, sizes within (1/2 +- eps).
+void bisect(const Builder& B, const std::vector<int>& ids, double eps, std::mt19937_64& rng,
+            std::vector<int>& part) {
+  const int n = (int)ids.size();
+  // adjacency via labels
+  std::vector<std::vector<std::pair<int, int>>> adj(n);
+  {
+    std::vector<std::pair<int, int>> lab;  // (label, local idx)
+    for (int v = 0; v < n; ++v)
+      for (int l : B.sets[ids[v]]) lab.push_back({l, v});
+    std::sort(lab.begin(), lab.end());
+    std::vector<std::vector<int>> w(0);
+    for (size_t s = 0; s < lab.size();) {
+      size_t e = s;
+      while (e < lab.size() && lab[e].first == lab[s].first) ++e;
+      for (size_t x = s; x < e; ++x)
+        for (size_t y = x + 1; y < e; ++y) {
+          adj[lab[x].second].push_back({lab[y].second, 1});
+          adj[lab[y].second].push_back({lab[x].second, 1});
+        }
+      s = e;
+    }
+    for (auto& a : adj) {  // merge parallel edges
+      std::sort(a.begin(), a.end());
+      std::vector<std::pair<int, int>> m;
+      for (auto& p : a) {
+        if (!m.empty() && m.back().first == p.first) m.back().second += p.second;
+        else m.push_back(p);
+      }
+      a.swap(m);
+    }
+  }
+  const int lo = std::max(1, (int)std::floor(n * (0.5 - eps)));
+  const int hi = std::min(n - 1, (int)std::ceil(n * (0.5 + eps)));
+  // initial: BFS growth from a random vertex up to a random target size
+  part.assign(n, 1);
+  std::uniform_int_distribution<int> pick(0, n - 1);
+  int target = std::uniform_int_distribution<int>(lo, hi)(rng);
+  {
+    std::vector<int> q;
+    std::vector<char> seen(n, 0);
+    int count = 0;
+    int start = pick(rng);
+    q.push_back(start);
+    seen[start] = 1;
+    size_t head = 0;
+    while (count < target) {
+      if (head == q.size()) {
+        int v;
+        do v = pick(rng); while (seen[v]);
+        seen[v] = 1;
+        q.push_back(v);
+      }
+      int v = q[head++];
+      part[v] = 0;
+      ++count;
+      for (auto& e : adj[v])
+        if (!seen[e.first]) { seen[e.first] = 1; q.push_back(e.first); }
+    }
+  }
+  auto gain_of = [&](int v) {
+    int g = 0;
+    for (auto& e : adj[v]) g += (part[e.first] != part[v]) ? e.second : -e.second;
+    return g;
+  };
+  int size0 = 0;
+  for (int v = 0; v < n; ++v) size0 += part[v] == 0;
+  for (int pass = 0; pass < 10; ++pass) {
+    std::vector<char> locked(n, 0);
+    std::vector<int> gain(n);
+    for (int v = 0; v < n; ++v) gain[v] = gain_of(v);
+    std::vector<int> moves;
+    int cur = 0, best = 0, best_len = 0, s0 = size0;
+    for (int step = 0; step < n; ++step) {
+      int bv = -1, bg = -1 << 30;
+      for (int v = 0; v < n; ++v) {
+        if (locked[v]) continue;
+        int ns0 = s0 + (part[v] == 0 ? -1 : 1);
+        if (ns0 < lo || ns0 > hi) continue;
+        if (gain[v] > bg) { bg = gain[v]; bv = v; }
+      }
+      if (bv < 0) break;
+      locked[bv] = 1;
+      s0 += part[bv] == 0 ? -1 : 1;
+      part[bv] ^= 1;
+      cur += bg;
+      moves.push_back(bv);
+      gain[bv] = -gain[bv];
+      for (auto& e : adj[bv]) {
+        int u = e.first;
+        gain[u] += (part[u] == part[bv]) ? -2 * e.second : 2 * e.second;
+      }
+      if (cur > best) { best = cur; best_len = (int)moves.size(); }
+    }
+    for (int k = (int)moves.size() - 1; k >= best_len; --k) part[moves[k]] ^= 1;
+    size0 = 0;
+    for (int v = 0; v < n; ++v) size0 += part[v] == 0;
+    if (best <= 0) break;
+  }
+}
+
+int bisect_tree(Builder& B, const std::vector<int>& ids, int cutoff, double eps, double alpha,
+                std::mt19937_64& rng) {
+  if ((int)ids.size() <= cutoff) return greedy_join(B, ids, alpha, 0.0, rng);
+  std::vector<int> part;
+  bisect(B, ids, eps, rng, part);
+  std::vector<int> s0, s1;
+  for (size_t v = 0; v < ids.size(); ++v) (part[v] ? s1 : s0).push_back(ids[v]);
+  if (s0.empty() || s1.empty()) return greedy_join(B, ids, alpha, 0.0, rng);
+  int a = bisect_tree(B, s0, cutoff, eps, alpha, rng);
+  int b = bisect_tree(B, s1, cutoff, eps, alpha, rng);
+  return B.join(a, b);
+}
+
+struct Eval {
+  double time = 0, cmac = 0;
+  int width = 0;
+  std::vector<int> sliced;
+};
+
+// Node label sets of a tree (leaf sets given), with the sliced labels removed.
+void node_sets(const std::vector<LSet>& leaves, const std::vector<int>& pairs,
+               const std::vector<int>& sliced, std::vector<LSet>& sets) {
+  sets.clear();
+  for (auto& s : leaves) {
+    LSet t;
+    for (int l : s)
+      if (std::find(sliced.begin(), sliced.end(), l) == sliced.end()) t.push_back(l);
+    sets.push_back(t);
+  }
+  for (size_t p = 0; p < pairs.size(); p += 2) sets.push_back(sym_diff(sets[pairs[p]], sets[pairs[p + 1]]));
+}
+
+void cost_of(const std::vector<LSet>& sets, const std::vector<int>& pairs, int L, double& time,
+             double& cmac, int& width) {
+  time = 0; cmac = 0; width = 0;
+  for (auto& s : sets) width = std::max(width, (int)s.size());
+  for (size_t p = 0; p < pairs.size(); p += 2) {
+    const LSet &a = sets[pairs[p]], &b = sets[pairs[p + 1]], &c = sets[L + p / 2];
+    int wu = union_size(a, b);
+    cmac += std::ldexp(1.0, wu);
+    time += step_time((int)a.size(), (int)b.size(), (int)c.size(), wu);
+  }
+}
+
+// Greedy slicing: repeatedly remove the label (present in a widest node) that
+// gives the smallest (width, modelled time).
+Eval slice_tree(const std::vector<LSet>& leaves, const std::vector<int>& pairs, const LSet& sliceable,
+                int num_sliced, int cap) {
+  const int L = (int)leaves.size();
+  Eval ev;
+  std::vector<LSet> sets;
+  node_sets(leaves, pairs, ev.sliced, sets);
+  cost_of(sets, pairs, L, ev.time, ev.cmac, ev.width);
+  auto need_more = [&]() {
+    if (num_sliced >= 0) return (int)ev.sliced.size() < num_sliced;
+    return cap > 0 && ev.width > cap;
+  };
+  while (need_more()) {
+    LSet cand;
+    for (auto& s : sets)
+      if ((int)s.size() == ev.width)
+        for (int l : s)
+          if (contains(sliceable, l)) cand.push_back(l);
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    if (cand.empty()) {  // widest nodes hold only open labels: slice elsewhere
+      for (auto& s : sets)
+        for (int l : s)
+          if (contains(sliceable, l)) cand.push_back(l);
+      std::sort(cand.begin(), cand.end());
+      cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    }
+    if (cand.empty()) break;
+    int best = -1, bw = 0;
+    double bt = 0;
+    for (int l : cand) {
+      std::vector<int> s2 = ev.sliced;
+      s2.push_back(l);
+      std::vector<LSet> st;
+      node_sets(leaves, pairs, s2, st);
+      double t, c;
+      int w;
+      cost_of(st, pairs, L, t, c, w);
+      if (best < 0 || w < bw || (w == bw && t < bt)) { best = l; bw = w; bt = t; }
+    }
+    ev.sliced.push_back(best);
+    node_sets(leaves, pairs, ev.sliced, sets);
+    cost_of(sets, pairs, L, ev.time, ev.cmac, ev.width);
+  }
+  return ev;
+}
+
+// Subtree reconfiguration: for each internal node, expand its subtree into a
+// frontier of up to `k` sub-tensors (largest first) and replace the part
+// above the frontier by the exact optimum over all contraction orders of the
+// frontier (dynamic programming over subsets), under the step-time model.
+// The frontier's joint label set is order independent, so every rewrite keeps
+// the tree valid.
+void reconfigure(const std::vector<LSet>& leaves, std::vector<int>& pairs, const std::vector<int>& sliced,
+                 int k, int passes) {
+  const int L = (int)leaves.size();
+  if (L < 3) return;
+  std::vector<int> lch(L, -1), rch(L, -1);
+  for (size_t p = 0; p < pairs.size(); p += 2) { lch.push_back(pairs[p]); rch.push_back(pairs[p + 1]); }
+  int root = (int)lch.size() - 1;
+  std::vector<LSet> sets;
+  node_sets(leaves, pairs, sliced, sets);
+  auto cost2 = [&](const LSet& a, const LSet& b) {
+    int u = union_size(a, b);
+    int sh = (int)a.size() + (int)b.size() - u;
+    return step_time((int)a.size(), (int)b.size(), u - sh, u);
+  };
+  for (int pass = 0; pass < passes; ++pass) {
+    // post-order list of internal nodes reachable from the root
+    std::vector<int> post, stack{root};
+    std::vector<int> tmp;
+    while (!stack.empty()) {
+      int v = stack.back(); stack.pop_back();
+      if (lch[v] < 0) continue;
+      tmp.push_back(v);
+      stack.push_back(lch[v]);
+      stack.push_back(rch[v]);
+    }
+    post.assign(tmp.rbegin(), tmp.rend());
+    bool improved = false;
+    for (int v : post) {
+      std::vector<int> front{lch[v], rch[v]};
+      std::vector<int> expanded{v};
+      while ((int)front.size() < k) {
+        int bi = -1;
+        for (int i = 0; i < (int)front.size(); ++i)
+          if (lch[front[i]] >= 0 && (bi < 0 || sets[front[i]].size() > sets[front[bi]].size())) bi = i;
+        if (bi < 0) break;
+        int u = front[bi];
+        expanded.push_back(u);
+        front[bi] = lch[u];
+        front.push_back(rch[u]);
+      }
+      const int f = (int)front.size();
+      if (f < 3) continue;
+      double cur = 0;
+      for (int u : expanded) cur += cost2(sets[lch[u]], sets[rch[u]]);
+      const int full = (1 << f) - 1;
+      std::vector<LSet> ss(1 << f);
+      std::vector<double> best(1 << f, 0.0);
+      std::vector<int> split(1 << f, 0);
+      for (int S = 1; S <= full; ++S) {
+        int low = S & -S;
+        if (S == low) { ss[S] = sets[front[__builtin_ctz(S)]]; continue; }
+        ss[S] = sym_diff(ss[S ^ low], ss[low]);
+        double b = 1e300;
+        int bs = 0;
+        // sub-splits containing the lowest bit
+        for (int S1 = (S - 1) & S; S1 > 0; S1 = (S1 - 1) & S) {
+          if (!(S1 & low)) continue;
+          int S2 = S ^ S1;
+          double c = best[S1] + best[S2] + cost2(ss[S1], ss[S2]);
+          if (c < b) { b = c; bs = S1; }
+        }
+        best[S] = b;
+        split[S] = bs;
+      }
+      if (best[full] < cur * (1 - 1e-9) - 1e-12) {
+        // rebuild: v keeps its id as the root of the rewritten part
+        std::function<int(int)> build = [&](int S) -> int {
+          if ((S & (S - 1)) == 0) return front[__builtin_ctz(S)];
+          int a = build(split[S]), b = build(S ^ split[S]);
+          lch.push_back(a); rch.push_back(b);
+          sets.push_back(sym_diff(sets[a], sets[b]));
+          return (int)lch.size() - 1;
+        };
+        int a = build(split[full]), b = build(full ^ split[full]);
+        lch[v] = a; rch[v] = b;
+        improved = true;
+      }
+    }
+    if (!improved) break;
+  }
+  // re-emit SSA pairs in post-order
+  std::vector<int> id(lch.size(), -1);
+  for (int i = 0; i < L; ++i) id[i] = i;
+  std::vector<int> out;
+  int nid = L;
+  std::vector<std::pair<int, int>> st{{root, 0}};
+  while (!st.empty()) {
+    auto& [v, state] = st.back();
+    if (lch[v] < 0) { st.pop_back(); continue; }
+    if (state == 0) { state = 1; st.push_back({lch[v], 0}); continue; }
+    if (state == 1) { state = 2; st.push_back({rch[v], 0}); continue; }
+    out.push_back(id[lch[v]]);
+    out.push_back(id[rch[v]]);
+    id[v] = nid++;
+    st.pop_back();
+  }
+  pairs.swap(out);
+}
+
+void put32(std::vector<uint8_t>& b, int32_t v) {
+  uint8_t t[4];
+  std::memcpy(t, &v, 4);
+  b.insert(b.end(), t, t + 4);
+}
+
+uint64_t fnv1a(const std::vector<uint8_t>& b) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  for (uint8_t x : b) { h ^= x; h *= 0x100000001b3ull; }
+  return h;
+}
+
+}  // namespace
+
+tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& P) {
+  P.net = net;
+  P.opts = opts;
+  const int L = (int)net.leaves.size();
+  if (L == 0) return fail(TN_EINVAL, "tn_plan: empty network");
+  std::vector<LSet> leaves(L);
+  LSet sliceable;
+  for (int i = 0; i < L; ++i) {
+    for (int l : net.leaves[i].labels)
+      if (net.kind[l] != LK_CLOSED) leaves[i].push_back(l);
+    std::sort(leaves[i].begin(), leaves[i].end());
+    for (int l : leaves[i])
+      if (net.kind[l] == LK_INTERNAL) sliceable.push_back(l);
+  }
+  std::sort(sliceable.begin(), sliceable.end());
+  sliceable.erase(std::unique(sliceable.begin(), sliceable.end()), sliceable.end());
+  if (opts.num_sliced > (int)sliceable.size())
+    return fail(TN_EINVAL, "tn_plan: num_sliced %d exceeds the %d internal indices", opts.num_sliced,
+                (int)sliceable.size());
+
+  const int trials = opts.search_trials > 0 ? opts.search_trials : 128;
+  std::mt19937_64 rng(opts.seed ^ 0x5DEECE66Dull);
+  std::vector<int> best_pairs;
+  Eval best;
+  bool have = false;
+  std::vector<int> all(L);
+  std::iota(all.begin(), all.end(), 0);
+  for (int t = 0; t < (L == 1 ? 1 : trials); ++t) {
+    Builder B(leaves);
+    std::mt19937_64 r2(rng());
+    if (L > 1) {
+      if (t % 2 == 0) {
+        double alpha = std::uniform_real_distribution<double>(0.0, 1.5)(r2);
+        const double taus[] = {0.0, 0.01, 0.05, 0.1, 0.3, 1.0};
+        double tau = taus[std::uniform_int_distribution<int>(0, 5)(r2)];
+        greedy_join(B, all, alpha, tau, r2);
+      } else {
+        int cutoff = std::uniform_int_distribution<int>(4, 24)(r2);
+        double eps = std::uniform_real_distribution<double>(0.02, 0.4)(r2);
+        double alpha = std::uniform_real_distribution<double>(0.0, 1.0)(r2);
+        bisect_tree(B, all, cutoff, eps, alpha, r2);
+      }
+    }
+    reconfigure(leaves, B.pairs, {}, 6, 3);
+    Eval ev = slice_tree(leaves, B.pairs, sliceable, opts.num_sliced, opts.max_log2_intermediate);
+    if (!ev.sliced.empty()) {
+      reconfigure(leaves, B.pairs, ev.sliced, 6, 3);
+      std::vector<LSet> st;
+      node_sets(leaves, B.pairs, ev.sliced, st);
+      cost_of(st, B.pairs, L, ev.time, ev.cmac, ev.width);
+    }
+    double score = ev.time * std::ldexp(1.0, (int)ev.sliced.size());
+    double bscore = have ? best.time * std::ldexp(1.0, (int)best.sliced.size()) : 0;
+    bool ok_cap = opts.max_log2_intermediate <= 0 || ev.width <= opts.max_log2_intermediate;
+    bool bok_cap = have && (opts.max_log2_intermediate <= 0 || best.width <= opts.max_log2_intermediate);
+    if (!have || (ok_cap && !bok_cap) || (ok_cap == bok_cap && score < bscore)) {
+      best = ev;
+      best_pairs = B.pairs;
+      have = true;
+    }
+  }
+  if (L > 2) {  // polish the winner with a wider window
+    reconfigure(leaves, best_pairs, best.sliced, 8, 6);
+    std::vector<LSet> st;
+    node_sets(leaves, best_pairs, best.sliced, st);
+    cost_of(st, best_pairs, L, best.time, best.cmac, best.width);
+  }
+  if (opts.max_log2_intermediate > 0 && best.width > opts.max_log2_intermediate)
+    return fail(TN_ETOOBIG, "tn_plan: could not reach width 2^%d (best 2^%d with %d sliced)",
+                opts.max_log2_intermediate, best.width, (int)best.sliced.size());
+  if (best.width > 30)
+    return fail(TN_ETOOBIG, "tn_plan: per-slice width 2^%d (cost 2^%.1f CMAC per slice) exceeds the 2^30 element limit; slice more",
+                best.width, std::log2(std::max(best.cmac, 1.0)));
+  double log2_total = std::log2(std::max(best.cmac, 1.0)) + (double)best.sliced.size();
+  if (opts.max_log2_cmac > 0 && log2_total > opts.max_log2_cmac)
+    return fail(TN_ETOOBIG, "tn_plan: cost 2^%.1f CMAC exceeds the cap 2^%.1f", log2_total, opts.max_log2_cmac);
+
+  P.sliced = best.sliced;
+  P.tree = best_pairs;
+  P.cmac_per_slice = best.cmac;
+  P.max_width = best.width;
+
+  // ---- leaves: fixed indices and sub-labels
+  std::vector<int> slice_bit(net.num_labels(), -1);
+  for (size_t j = 0; j < P.sliced.size(); ++j) slice_bit[P.sliced[j]] = (int)j;
+  P.leaf_use.assign(L, LeafUse());
+  int64_t store = 0;
+  for (int i = 0; i < L; ++i) {
+    LeafUse& U = P.leaf_use[i];
+    const Leaf& lf = net.leaves[i];
+    U.store_off = store;
+    store += int64_t(1) << lf.labels.size();
+    for (int l : lf.labels) {
+      if (net.kind[l] == LK_CLOSED) { U.fixed_src.push_back(-2 - net.closed_qubit[l]); U.variant = true; }
+      else if (slice_bit[l] >= 0) { U.fixed_src.push_back(slice_bit[l]); U.variant = true; }
+      else { U.fixed_src.push_back(-1); U.sub_labels.push_back(l); }
+    }
+  }
+  P.leaf_store_elems = store;
+
+  // ---- steps
+  std::vector<LSet> order(L);  // memory label order of each SSA id
+  std::vector<char> variant(L + best_pairs.size() / 2, 0);
+  for (int i = 0; i < L; ++i) { order[i] = P.leaf_use[i].sub_labels; variant[i] = P.leaf_use[i].variant; }
+  P.steps.clear();
+  for (size_t p = 0; p < best_pairs.size(); p += 2) {
+    int x = best_pairs[p], y = best_pairs[p + 1];
+    Step S;
+    const LSet &ox = order[x], &oy = order[y];
+    bool swap = oy.size() > ox.size();
+    S.a = swap ? y : x;
+    S.b = swap ? x : y;
+    S.la = order[S.a];
+    S.lb = order[S.b];
+    for (int l : S.la)
+      if (std::find(S.lb.begin(), S.lb.end(), l) == S.lb.end()) S.lc.push_back(l);
+    for (int l : S.lb)
+      if (std::find(S.la.begin(), S.la.end(), l) == S.la.end()) S.lc.push_back(l);
+    S.nk = (int)(S.la.size() + S.lb.size() - S.lc.size()) / 2;
+    S.nm = (int)S.la.size() - S.nk;
+    S.nn = (int)S.lb.size() - S.nk;
+    S.klass = (S.nn <= 4 && S.nk <= 4) ? SC_VECTOR : SC_SIMT;
+    S.variant = variant[S.a] || variant[S.b];
+    variant[L + p / 2] = S.variant;
+    order.push_back(S.lc);
+    P.steps.push_back(S);
+  }
+
+  // ---- memory: per-unit arena (variant leaves + variant outputs), invariant store
+  auto align = [](int64_t v) { return (v + 31) & ~int64_t(31); };
+  struct Blk { int64_t off, size; };
+  std::vector<Blk> freel;
+  int64_t top = 0;
+  auto alloc = [&](int64_t sz) {
+    sz = align(sz);
+    for (size_t i = 0; i < freel.size(); ++i)
+      if (freel[i].size >= sz) {
+        int64_t o = freel[i].off;
+        freel[i].off += sz;
+        freel[i].size -= sz;
+        if (freel[i].size == 0) freel.erase(freel.begin() + i);
+        return o;
+      }
+    int64_t o = top;
+    top += sz;
+    return o;
+  };
+  auto release = [&](int64_t off, int64_t sz) {
+    sz = align(sz);
+    freel.push_back({off, sz});
+    std::sort(freel.begin(), freel.end(), [](const Blk& a, const Blk& b) { return a.off < b.off; });
+    std::vector<Blk> m;
+    for (auto& b : freel) {
+      if (!m.empty() && m.back().off + m.back().size == b.off) m.back().size += b.size;
+      else m.push_back(b);
+    }
+    // give back a trailing block
+    if (!m.empty() && m.back().off + m.back().size == top) { top = m.back().off; m.pop_back(); }
+    freel.swap(m);
+  };
+  for (int i = 0; i < L; ++i)
+    if (P.leaf_use[i].variant) P.leaf_use[i].off = alloc(int64_t(1) << P.leaf_use[i].sub_labels.size());
+    else P.leaf_use[i].off = P.leaf_use[i].store_off;
+  int64_t peak = top;
+  int64_t inv = 0;
+  std::vector<int64_t> ssa_off(L + P.steps.size(), 0);
+  for (int i = 0; i < L; ++i) ssa_off[i] = P.leaf_use[i].off;
+  for (size_t s = 0; s < P.steps.size(); ++s) {
+    Step& S = P.steps[s];
+    int64_t sz = int64_t(1) << S.lc.size();
+    if (S.variant) {
+      S.off_c = alloc(sz);
+      peak = std::max(peak, top);
+      for (int opnd : {S.a, S.b}) {
+        bool var = opnd < L ? P.leaf_use[opnd].variant : P.steps[opnd - L].variant;
+        int64_t osz = int64_t(1) << order[opnd].size();
+        if (var) release(ssa_off[opnd], osz);
+      }
+    } else {
+      S.off_c = inv;
+      inv += align(sz);
+    }
+    ssa_off[L + s] = S.off_c;
+  }
+  P.unit_arena_elems = align(std::max<int64_t>(peak, 32));
+  P.invariant_elems = std::max<int64_t>(inv, 32);
+
+  // ---- root permutation: batch index j -> element offset of the root tensor
+  const LSet& root = L == 1 ? P.leaf_use[0].sub_labels : P.steps.back().lc;
+  int k = (int)net.open_qubits.size();
+  P.root_perm.assign(size_t(1) << k, 0);
+  for (int64_t j = 0; j < (int64_t(1) << k); ++j) {
+    int64_t off = 0;
+    for (size_t pos = 0; pos < root.size(); ++pos) {
+      int t = net.open_bit[root[pos]];
+      if (t < 0) return fail(TN_EINVAL, "tn_plan: internal error, root holds a non-open label");
+      if ((j >> t) & 1) off += int64_t(1) << (root.size() - 1 - pos);
+    }
+    P.root_perm[j] = off;
+  }
+
+  // ---- serialization + hash
+  auto& b = P.bytes;
+  b.clear();
+  const char magic[8] = {'T', 'N', 'P', 'L', 'A', 'N', '0', '1'};
+  b.insert(b.end(), magic, magic + 8);
+  put32(b, net.n);
+  put32(b, k);
+  for (int q : net.open_qubits) put32(b, q);
+  put32(b, (int)P.sliced.size());
+  for (int l : P.sliced) { put32(b, net.wire[l].first); put32(b, net.wire[l].second); }
+  put32(b, L);
+  for (int i = 0; i < L; ++i) {
+    put32(b, (int)net.leaves[i].labels.size());
+    for (int l : net.leaves[i].labels) { put32(b, net.wire[l].first); put32(b, net.wire[l].second); }
+  }
+  put32(b, (int)P.steps.size());
+  for (auto& S : P.steps) {
+    put32(b, S.a);
+    put32(b, S.b);
+    put32(b, S.klass);
+    put32(b, (int)S.lc.size());
+    for (int l : S.lc) { put32(b, net.wire[l].first); put32(b, net.wire[l].second); }
+  }
+  P.hash = fnv1a(b);
+  return TN_OK;
+}
+
+Plan::~Plan() {
+  if (exec) destroy_executor(exec);
+}
+
+}  // namespace tn
+
+using namespace tn;
+
+extern "C" tn_status tn_plan(const tn_network* net, const tn_plan_opts* opts, tn_plan_t** out) {
+  if (!net || !out) return fail(TN_EINVAL, "tn_plan: NULL argument");
+  tn_plan_opts o;
+  std::memset(&o, 0, sizeof o);
+  o.num_sliced = -1;
+  if (opts) o = *opts;
+  if (o.num_sliced < -1 || o.num_sliced > 62) return fail(TN_EINVAL, "tn_plan: num_sliced %d not in [-1, 62]", o.num_sliced);
+  if (o.max_log2_intermediate < 0 || o.max_log2_intermediate > 30)
+    return fail(TN_EINVAL, "tn_plan: max_log2_intermediate %d not in [0, 30]", o.max_log2_intermediate);
+  if (o.search_trials < 0 || o.search_trials > 100000) return fail(TN_EINVAL, "tn_plan: bad search_trials");
+  auto* h = new (std::nothrow) tn_plan_s;
+  if (!h) return fail(TN_ENOMEM, "tn_plan: out of host memory");
+  tn_status st = make_plan(net->net, o, h->plan);
+  if (st != TN_OK) { delete h; return st; }
+  *out = h;
+  return TN_OK;
+}
+
+extern "C" tn_status tn_plan_get_info(const tn_plan_t* p, tn_plan_info* info) {
+  if (!p || !info) return fail(TN_EINVAL, "tn_plan_get_info: NULL argument");
+  const Plan& P = p->plan;
+  std::memset(info, 0, sizeof *info);
+  info->num_qubits = P.net.n;
+  info->num_open = (int)P.net.open_qubits.size();
+  info->num_sliced = (int)P.sliced.size();
+  info->num_steps = (int)P.steps.size();
+  info->num_leaves = (int)P.net.leaves.size();
+  info->max_log2_intermediate = P.max_width;
+  info->num_slices = int64_t(1) << P.sliced.size();
+  info->cmac_per_slice = P.cmac_per_slice;
+  info->flops_per_slice = 8.0 * P.cmac_per_slice;
+  info->log2_cmac_total = std::log2(std::max(P.cmac_per_slice, 1.0)) + (double)P.sliced.size();
+  info->footprint_bytes_per_unit = P.unit_arena_elems * 8;
+  info->hash = P.hash;
+  for (auto& S : P.steps) {
+    if (S.klass == SC_VECTOR) info->num_vector_steps++;
+    else info->num_dense_steps++;
+  }
+  return TN_OK;
+}
+
+extern "C" tn_status tn_plan_sliced_wires(const tn_plan_t* p, int32_t* pairs, int64_t cap) {
+  if (!p || (!pairs && !p->plan.sliced.empty())) return fail(TN_EINVAL, "tn_plan_sliced_wires: NULL argument");
+  const Plan& P = p->plan;
+  if (cap < (int64_t)P.sliced.size()) return fail(TN_EINVAL, "tn_plan_sliced_wires: capacity too small");
+  for (size_t j = 0; j < P.sliced.size(); ++j) {
+    pairs[2 * j] = P.net.wire[P.sliced[j]].first;
+    pairs[2 * j + 1] = P.net.wire[P.sliced[j]].second;
+  }
+  return TN_OK;
+}
+
+extern "C" tn_status tn_plan_serialize(const tn_plan_t* p, uint8_t* buf, size_t cap, size_t* len) {
+  if (!p || !len) return fail(TN_EINVAL, "tn_plan_serialize: NULL argument");
+  const auto& b = p->plan.bytes;
+  *len = b.size();
+  if (!buf) return TN_OK;
+  if (cap < b.size()) return fail(TN_EINVAL, "tn_plan_serialize: capacity %zu < %zu", cap, b.size());
+  std::memcpy(buf, b.data(), b.size());
+  return TN_OK;
+}
+
+extern "C" tn_status tn_plan_tree(const tn_plan_t* p, int32_t* leaf_raw, int64_t cap_raw, int32_t* tree,
+                                  int64_t cap_tree) {
+  if (!p || !leaf_raw || !tree) return fail(TN_EINVAL, "tn_plan_tree: NULL argument");
+  const Plan& P = p->plan;
+  int64_t need = 0;
+  for (auto& lf : P.net.leaves) need += (int64_t)lf.raw.size() + 1;
+  if (cap_raw < need || cap_tree < (int64_t)P.tree.size())
+    return fail(TN_EINVAL, "tn_plan_tree: capacity too small (need %lld raw, %zu tree)", (long long)need, P.tree.size());
+  int64_t k = 0;
+  for (auto& lf : P.net.leaves) {
+    for (int r : lf.raw) leaf_raw[k++] = r;
+    leaf_raw[k++] = -1;
+  }
+  // steps store operands as (a, b) after the size swap; report the tree in step order
+  for (size_t s = 0; s < P.steps.size(); ++s) {
+    tree[2 * s] = P.steps[s].a;
+    tree[2 * s + 1] = P.steps[s].b;
+  }
+  return TN_OK;
+}

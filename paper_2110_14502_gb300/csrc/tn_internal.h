@@ -1,0 +1,113 @@
+// Internal data structures of the host library (circuits, networks, plans).
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "tn.h"
+
+namespace tn {
+
+using cd = std::complex<double>;
+
+// Records a printf-style message for tn_last_error() and returns `code`.
+tn_status fail(tn_status code, const char* fmt, ...);
+
+struct Gate {
+  int kind = 0;
+  int q0 = 0, q1 = -1;
+  double theta = 0, phi = 0;
+  cd m[16];  // row-major 2x2 (first 4) or 4x4
+  int nq() const { return q1 < 0 ? 1 : 2; }
+};
+
+struct Circuit {
+  int n = 0;
+  std::vector<Gate> gates;
+};
+
+// Fills g.m from g.kind/theta/phi for the named kinds.
+void gate_matrix(Gate& g);
+uint64_t splitmix64_next(uint64_t& state);
+
+enum LabelKind { LK_INTERNAL = 0, LK_OPEN = 1, LK_CLOSED = 2 };
+
+struct Leaf {
+  std::vector<int> labels;  // row-major order, first label slowest
+  std::vector<cd> data;     // 2^labels.size()
+  std::vector<int> raw;     // raw tensor ids merged into this leaf
+};
+
+struct Network {
+  int n = 0;
+  int num_gates = 0;
+  std::vector<int> open_qubits;
+  std::vector<Leaf> leaves;
+  std::vector<std::pair<int, int>> wire;  // label -> (q, t)
+  std::vector<int> kind;                  // label -> LabelKind
+  std::vector<int> closed_qubit;          // label -> qubit (LK_CLOSED) else -1
+  std::vector<int> open_bit;              // label -> bit of the batch index (LK_OPEN) else -1
+  int num_labels() const { return (int)wire.size(); }
+};
+
+// Kernel class of a pairwise step.
+enum StepClass { SC_SIMT = 0, SC_VECTOR = 1, SC_TC = 2 };
+
+struct Step {
+  int a = -1, b = -1;           // SSA operand ids: < L leaf, else L + step index
+  std::vector<int> la, lb, lc;  // operand / output labels in memory order (fixed labels removed)
+  int nm = 0, nn = 0, nk = 0;   // log2 M, N, K
+  int klass = SC_SIMT;
+  bool variant = true;          // depends on the unit's fixed-index values
+  int64_t off_c = 0;            // element offset of the output (unit arena or invariant store)
+};
+
+struct LeafUse {
+  bool variant = false;
+  std::vector<int> sub_labels;  // labels after removing fixed ones
+  // per full-label position: -1 kept, else source of the fixed value:
+  //   src >= 0      : sliced index number j (bit j of the slice id)
+  //   src <= -2     : closed output of qubit (-src - 2)
+  std::vector<int> fixed_src;
+  int64_t off = 0;              // variant: element offset in unit arena; invariant: offset in leaf store
+  int64_t store_off = 0;        // offset of the full leaf in the leaf store
+};
+
+struct Executor;  // device-side state (executor.cu)
+
+struct Plan {
+  Network net;
+  tn_plan_opts opts{};
+  std::vector<int> sliced;      // labels; bit j of the slice id -> sliced[j]
+  std::vector<int> tree;        // 2*(L-1) SSA ids
+  std::vector<Step> steps;
+  std::vector<LeafUse> leaf_use;
+  int64_t unit_arena_elems = 0;   // per-unit arena (complex elements)
+  int64_t invariant_elems = 0;    // invariant intermediates store
+  int64_t leaf_store_elems = 0;
+  std::vector<int64_t> root_perm; // batch index j -> element offset in the root tensor
+  double cmac_per_slice = 0;
+  int max_width = 0;
+  std::vector<uint8_t> bytes;     // serialized form
+  uint64_t hash = 0;
+  Executor* exec = nullptr;
+  ~Plan();
+};
+
+// network.cpp
+tn_status build_network(const Circuit& c, const int32_t* open, int num_open, Network& out);
+// planner.cpp
+tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& plan);
+// executor.cu
+void destroy_executor(Executor* e);
+tn_status contract_amplitudes(Plan& p, const uint64_t* bits, int64_t nb, double* out,
+                              const tn_exec_opts& o, tn_report* rep);
+
+}  // namespace tn
+
+struct tn_circuit_s { tn::Circuit c; };
+struct tn_network_s { tn::Network net; };
+struct tn_plan_s { tn::Plan plan; };

@@ -1,0 +1,130 @@
+"""End-to-end amplitude parity of the CUDA path against the CPU oracle.
+
+Bounds: relative L2 error of an amplitude batch <= 1e-5 for complex64
+(the tolerance of the plain complex64 path)."""
+import numpy as np
+import pytest
+
+import tn_inputs as I
+from oracle import circuit as OC
+from oracle import statevector as SV
+from oracle import tn as OTN
+
+from _lib import tnlib
+from _replay import replay
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def _setup(T, rows, cols, depth, cseed, open_q=(), **kw):
+    c = T.random_circuit(rows, cols, depth, cseed)
+    net = T.build_network(c, list(open_q))
+    return T.plan(net, **kw)
+
+
+def test_config_4x4_depth8_64_bitstrings_vs_statevector():
+    """4x4 grid, depth 1+8+1, seed 1, 64 bitstrings, complex64 unsliced."""
+    T = tnlib()
+    n = 16
+    p = _setup(T, 4, 4, 8, 1, search_trials=64, seed=1)
+    words = I.bitstrings(n, 64, 1)
+    got = p.contract_amplitudes(words)
+    gates = OC.random_circuit(4, 4, 8, 1)
+    ref = SV.amplitudes(SV.simulate(gates, n), n, [I.bits_of(w, n) for w in words])
+    assert got.shape == (64, 1)
+    assert rel(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("rows,cols,depth,seed,open_q,S", [
+    (3, 4, 10, 2, (10, 11, 3), 0),
+    (4, 4, 10, 5, (15, 14), 4),
+    (4, 5, 12, 6, (14, 15, 16, 17, 18, 19), 6),
+    (2, 3, 4, 8, (), 2),
+    (1, 1, 3, 9, (0,), 0),
+    (1, 2, 0, 9, (), 0),
+])
+def test_open_and_sliced_vs_statevector(rows, cols, depth, seed, open_q, S):
+    T = tnlib()
+    n = rows * cols
+    p = _setup(T, rows, cols, depth, seed, open_q, num_sliced=S, search_trials=32, seed=3)
+    assert p.info()["num_sliced"] == S
+    words = I.bitstrings(n, 5, seed)
+    got = p.contract_amplitudes(words)
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    ref = SV.amplitudes(SV.simulate(gates, n), n, [I.bits_of(w, n) for w in words], open_q)
+    assert rel(got, ref) <= 1e-5
+
+
+def test_slice_ids_map_to_the_oracle_assignment():
+    """Slice s fixes sliced wire j to bit j of s: per-slice values and a
+    ragged subset sum agree with the oracle's contraction of the same
+    assignment."""
+    T = tnlib()
+    rows, cols, depth, seed, open_q = 4, 4, 10, 11, (12, 13)
+    n = rows * cols
+    p = _setup(T, rows, cols, depth, seed, open_q, num_sliced=5, search_trials=32, seed=2)
+    wires = p.sliced_wires()
+    words = I.bitstrings(n, 2, seed)
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    for bi, w in enumerate(words):
+        bits = I.bits_of(w, n)
+        net = OTN.circuit_network(gates, n, bits, open_q)
+        for s in (0, 1, 6, 17, 31):
+            got = p.contract_amplitudes(words[bi:bi + 1], slice_begin=s, slice_count=1)[0]
+            ref = OTN.contract_slice(net, wires, s)
+            assert rel(got, ref) <= 1e-5, (bi, s)
+        got = p.contract_amplitudes(words[bi:bi + 1], slice_begin=3, slice_count=11)[0]
+        ref = OTN.contract_sliced(net, wires, range(3, 14))
+        assert rel(got, ref) <= 1e-5
+
+
+def test_group_size_does_not_change_the_sum():
+    """The FP64 cross-slice sum runs in unit order, so any grouping gives
+    bit-identical results."""
+    T = tnlib()
+    p = _setup(T, 4, 4, 10, 5, (15, 14), num_sliced=4, search_trials=16, seed=3)
+    words = I.bitstrings(16, 3, 5)
+    r0 = p.contract_amplitudes(words, units_per_group=1)
+    for g in (3, 7, 48, 0):
+        assert np.array_equal(p.contract_amplitudes(words, units_per_group=g), r0)
+
+
+def test_device_io_matches_host_io():
+    import torch
+    T = tnlib()
+    p = _setup(T, 4, 4, 8, 3, (0, 1), num_sliced=2, search_trials=16, seed=3)
+    words = I.bitstrings(16, 6, 3)
+    host = p.contract_amplitudes(words)
+    dw = torch.from_numpy(words.astype(np.int64)).cuda()
+    out = torch.empty(6 * 4 * 2, dtype=torch.float64, device="cuda")
+    s = torch.cuda.current_stream()
+    p.contract_amplitudes(dw, out=out, stream=s)
+    torch.cuda.synchronize()
+    dev = out.cpu().numpy().view(np.complex128).reshape(6, 4)
+    assert np.array_equal(dev, host)
+
+
+def test_full_size_6x6_sampled_slices_vs_oracle():
+    """6x6 grid (36 qubits), depth 1+16+1, seed 2, 10 sliced indices, six
+    open qubits (the last six): two sampled slices of one bitstring batch
+    against the oracle's FP64 contraction of the same slice assignment."""
+    T = tnlib()
+    rows, cols, depth, seed = 6, 6, 16, 2
+    n = 36
+    open_q = tuple(range(30, 36))
+    p = _setup(T, rows, cols, depth, seed, open_q, num_sliced=10, search_trials=64, seed=1)
+    info = p.info()
+    assert info["num_slices"] == 1024
+    wires = p.sliced_wires()
+    words = I.bitstrings(n, 4, seed)
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    bits = I.bits_of(words[0], n)
+    for s in (0, 777):
+        got = p.contract_amplitudes(words[:1], slice_begin=s, slice_count=1)[0]
+        fixed = {wires[j]: (s >> j) & 1 for j in range(len(wires))}
+        ref = replay(p, gates, n, bits, open_q, fixed)
+        assert rel(got, ref) <= 1e-5, s

@@ -1,0 +1,158 @@
+"""Host-side logic of the library (no GPU): circuit protocol against the
+oracle's independent generator, network and plan structure, plan determinism,
+replay of plan trees by the oracle contractor, and argument validation."""
+import ctypes as C
+import re
+
+import numpy as np
+import pytest
+
+import tn_inputs as I
+from oracle import circuit as OC
+from oracle import statevector as SV
+from oracle import tn as OTN
+
+from _lib import tnlib
+
+KIND = {0: "sqrtx", 1: "sqrty", 2: "sqrtw", 3: "fsim"}
+
+
+@pytest.mark.parametrize("rows,cols,depth,seed", [(4, 4, 8, 1), (6, 6, 16, 2), (3, 5, 7, 99), (8, 8, 20, 4)])
+def test_library_circuit_equals_oracle_circuit(rows, cols, depth, seed):
+    T = tnlib()
+    lib_gates = T.random_circuit(rows, cols, depth, seed).gates()
+    ora_gates = OC.random_circuit(rows, cols, depth, seed)
+    assert len(lib_gates) == len(ora_gates)
+    for (kind, q0, q1, th, ph, m), g in zip(lib_gates, ora_gates):
+        assert KIND[kind] == g.kind
+        assert (q0,) + ((q1,) if q1 >= 0 else ()) == tuple(g.qubits)
+        assert np.allclose(m, g.matrix, atol=1e-15, rtol=0)
+
+
+def test_network_counts():
+    T = tnlib()
+    c = T.random_circuit(3, 3, 4, 5)
+    net = T.build_network(c, [7, 8])
+    info = net.info()
+    assert info["num_qubits"] == 9 and info["num_open"] == 2 and info["num_closed"] == 7
+    # every wire segment is named (q, t) with t counting that qubit's gates
+    wires = net.label_wires()
+    per_q = {}
+    for q, t in wires:
+        per_q.setdefault(q, set()).add(t)
+    gates = c.gates()
+    for q in range(9):
+        n_on_q = sum(1 for g in gates if q in (g[1], g[2]))
+        assert per_q[q] == set(range(n_on_q + 1))
+
+
+def _plan(T, rows, cols, depth, cseed, open_q=(), **kw):
+    c = T.random_circuit(rows, cols, depth, cseed)
+    net = T.build_network(c, list(open_q))
+    return c, net, T.plan(net, **kw)
+
+
+def test_plan_is_deterministic():
+    T = tnlib()
+    _, _, p1 = _plan(T, 4, 4, 8, 1, search_trials=16, seed=7, num_sliced=3)
+    _, _, p2 = _plan(T, 4, 4, 8, 1, search_trials=16, seed=7, num_sliced=3)
+    assert p1.serialize() == p2.serialize()
+    assert p1.info()["hash"] == p2.info()["hash"]
+    assert p1.info()["num_sliced"] == 3 and p1.info()["num_slices"] == 8
+
+
+def test_plan_width_cap_and_errors():
+    T = tnlib()
+    _, _, p = _plan(T, 4, 5, 10, 3, open_q=(18, 19), max_log2_intermediate=8, search_trials=16)
+    assert p.info()["max_log2_intermediate"] <= 8
+    c = T.random_circuit(2, 2, 2, 1)
+    net = T.build_network(c, [])
+    with pytest.raises(T.TnError) as e:
+        T.plan(net, num_sliced=1000)
+    assert e.value.status == 1
+    with pytest.raises(T.TnError):
+        T.build_network(c, [0, 0])
+    with pytest.raises(T.TnError):
+        T.build_network(c, [5])
+
+
+def _oracle_replay(T, rows, cols, depth, cseed, open_q, bits, **kw):
+    """Contract the oracle's own network in the library plan's tree order."""
+    c, net, p = _plan(T, rows, cols, depth, cseed, open_q, **kw)
+    n = rows * cols
+    gates = OC.random_circuit(rows, cols, depth, cseed)
+    onet = OTN.circuit_network(gates, n, bits, open_q)
+    ng = len(gates)
+    leaves, pairs = p.tree(ng, n)
+    # oracle tensor order: n input vectors, then gates, then projectors of closed qubits
+    groups = []
+    last_raw = {q: ng + q for q in range(n)}
+    for gi, g in enumerate(gates):
+        for q in g.qubits:
+            last_raw[q] = gi
+    raw_to_oracle = lambda r: r + n if r < ng else r - ng
+    closed = [q for q in range(n) if q not in open_q]
+    proj_index = {q: n + ng + i for i, q in enumerate(closed)}
+    for raws in leaves:
+        grp = [raw_to_oracle(r) for r in raws]
+        for q in closed:
+            if last_raw[q] in raws:
+                grp.append(proj_index[q])
+        groups.append(grp)
+    assert sorted(x for g in groups for x in g) == list(range(len(onet.tensors)))
+    tens, labs = [], []
+    for grp in groups:
+        sub_t = [onet.tensors[i] for i in grp]
+        sub_l = [onet.labels[i] for i in grp]
+        t, l = OTN.contract_tree(sub_t, sub_l, OTN.greedy_order(sub_l)) if len(grp) > 1 else (sub_t[0], sub_l[0])
+        tens.append(t)
+        labs.append(l)
+    T_, l_ = OTN.contract_tree(tens, labs, pairs) if len(pairs) else (tens[0], labs[0])
+    return OTN.output_vector(T_, l_, onet.open_labels), gates, p
+
+
+@pytest.mark.parametrize("rows,cols,depth,seed,open_q", [(3, 3, 6, 1, ()), (3, 4, 8, 2, (10, 11)), (4, 4, 8, 3, (0, 15, 7))])
+def test_oracle_replay_of_plan_tree_matches_statevector(rows, cols, depth, seed, open_q):
+    T = tnlib()
+    n = rows * cols
+    bits = I.bits_of(I.bitstrings(n, 1, seed)[0], n)
+    v, gates, _ = _oracle_replay(T, rows, cols, depth, seed, open_q, bits, search_trials=16, seed=1)
+    ref = SV.amplitudes(SV.simulate(gates, n), n, [bits], open_q)[0]
+    assert np.linalg.norm(v - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_sliced_wires_name_internal_segments():
+    T = tnlib()
+    c, net, p = _plan(T, 4, 4, 8, 1, num_sliced=4, search_trials=16)
+    sw = p.sliced_wires()
+    assert len(sw) == 4 and len(set(sw)) == 4
+    gates = c.gates()
+    for q, t in sw:
+        n_on_q = sum(1 for g in gates if q in (g[1], g[2]))
+        assert 0 < t < n_on_q     # neither the input nor the output wire
+
+
+def test_contract_rejects_bad_arguments_before_device_work():
+    T = tnlib()
+    _, _, p = _plan(T, 2, 2, 2, 1, search_trials=4)
+    b = I.bitstrings(4, 2, 1)
+    with pytest.raises(T.TnError) as e:
+        p.contract_amplitudes(b, precision=99)
+    assert e.value.status == 1
+    with pytest.raises(T.TnError) as e:
+        p.contract_amplitudes(b, slice_begin=5)
+    assert e.value.status == 1
+
+
+def test_library_exports_every_declared_symbol():
+    T = tnlib()
+    from paper_2110_14502_gb300 import _abi
+    import os
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "tn.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    names = set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\*?\s+\*?(tn_[a-z0-9_]+)\s*\(", hdr, flags=re.M))
+    assert len(names) >= 19
+    h = C.CDLL(_abi.LIB_PATH)
+    for nm in sorted(names):
+        assert hasattr(h, nm), nm
+    assert names <= set(_abi.SIGNATURES), names - set(_abi.SIGNATURES)
