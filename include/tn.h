@@ -199,22 +199,27 @@ typedef struct {
   int32_t device_io;        /* 0: bitstrings/out are host memory; 1: device memory */
   int64_t slice_begin;      /* first slice id of the summed range */
   int64_t slice_count;      /* number of slices summed; -1 = all from slice_begin */
-  int32_t units_per_group;  /* (bitstring, slice) units contracted together; 0 = auto */
+  int32_t units_per_group;  /* slices contracted together per launch; 0 = auto */
   int32_t overflow_policy;  /* scaled modes: 0 = recompute a flagged slice in complex64, 1 = discard it (counted) */
   int32_t use_graph;        /* 1 = replay the per-group launch sequence as a CUDA graph */
-  int32_t reserved;
+  int32_t profile;          /* 1 = bracket every kernel launch with CUDA events and fill the per-class figures */
 } tn_exec_opts;
+
+/* Kernel classes of the per-class report figures. */
+enum { TN_KCLASS_GEMM_SIMT = 0, TN_KCLASS_VECTOR = 1, TN_KCLASS_GEMM_TC = 2, TN_KCLASS_OTHER = 3 };
 
 typedef struct {
   double device_ms;          /* device time of the call (CUDA events on the call's stream) */
-  double flops;              /* counted flops of the contracted units */
-  int64_t units;             /* (bitstring, slice) units contracted */
+  double flops;              /* counted flops of the work done (8 per complex MAC; shared work counted once) */
+  double flops_equivalent;   /* counted flops of the same result without sharing slice-only work across bitstrings */
+  int64_t units;             /* (bitstring, slice) units summed */
   int64_t kernel_launches;   /* kernels launched by the call */
   int64_t flagged_units;     /* scaled-mode units flagged for over/underflow */
   int64_t discarded_units;   /* flagged units dropped under overflow_policy = 1 */
-  double dominant_kernel_ms; /* summed device time of the dominant kernel class (when profiled) */
-  int32_t dominant_kernel;   /* 0 gemm-simt, 1 vector, 2 tcgen05 */
-  int32_t reserved;
+  double class_ms[4];        /* profile = 1: summed launch durations per kernel class (TN_KCLASS_*) */
+  int64_t class_launches[4];
+  double class_flops[4];     /* counted flops of those launches */
+  double class_bytes[4];     /* algorithmic bytes: each distinct operand read once, each output written once */
 } tn_report;
 
 /* Sums, over the slice range, the contraction of every bitstring's network:

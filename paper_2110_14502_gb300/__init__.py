@@ -160,7 +160,7 @@ class Plan:
 
     def contract_amplitudes(self, bitstrings, precision="c64", slice_begin=0, slice_count=-1,
                             units_per_group=0, stream=None, out=None, overflow_policy=0, use_graph=0,
-                            report=False):
+                            profile=False, report=False):
         """Amplitudes of each bitstring's open batch, summed over the slice range.
 
         bitstrings: uint64 words, shape (nb, ceil(n/64)) -- a NumPy array (host
@@ -177,6 +177,7 @@ class Plan:
         o.units_per_group = units_per_group
         o.overflow_policy = overflow_policy
         o.use_graph = use_graph
+        o.profile = 1 if profile else 0
         if stream is not None:
             o.stream = C.c_void_p(getattr(stream, "cuda_stream", stream))
         rep = Report()
@@ -196,7 +197,11 @@ class Plan:
             res = np.zeros((nb, 1 << k), dtype=np.complex128)
             check(lib().tn_contract_amplitudes(self._h, _ptr(b), nb, _ptr(res), C.byref(o), C.byref(rep)))
         if report:
-            return res, {f: getattr(rep, f) for f, _ in Report._fields_}
+            r = {}
+            for f, _ in Report._fields_:
+                v = getattr(rep, f)
+                r[f] = list(v) if hasattr(v, "__len__") else v
+            return res, r
         return res
 
 

@@ -53,13 +53,14 @@ class PlanInfo(C.Structure):
 class ExecOpts(C.Structure):
     _fields_ = [("stream", C.c_void_p), ("precision", C.c_int32), ("device_io", C.c_int32),
                 ("slice_begin", C.c_int64), ("slice_count", C.c_int64), ("units_per_group", C.c_int32),
-                ("overflow_policy", C.c_int32), ("use_graph", C.c_int32), ("reserved", C.c_int32)]
+                ("overflow_policy", C.c_int32), ("use_graph", C.c_int32), ("profile", C.c_int32)]
 
 
 class Report(C.Structure):
-    _fields_ = [("device_ms", C.c_double), ("flops", C.c_double), ("units", C.c_int64),
-                ("kernel_launches", C.c_int64), ("flagged_units", C.c_int64), ("discarded_units", C.c_int64),
-                ("dominant_kernel_ms", C.c_double), ("dominant_kernel", C.c_int32), ("reserved", C.c_int32)]
+    _fields_ = [("device_ms", C.c_double), ("flops", C.c_double), ("flops_equivalent", C.c_double),
+                ("units", C.c_int64), ("kernel_launches", C.c_int64), ("flagged_units", C.c_int64),
+                ("discarded_units", C.c_int64), ("class_ms", C.c_double * 4), ("class_launches", C.c_int64 * 4),
+                ("class_flops", C.c_double * 4), ("class_bytes", C.c_double * 4)]
 
 
 P = C.c_void_p

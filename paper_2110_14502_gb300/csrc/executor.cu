@@ -1,15 +1,23 @@
 // Executor: runs a plan's step chain over groups of (bitstring, slice) units
 // and sums the unit results in FP64 (paper: Sec. "A Customized Parallelization
-// Scheme" -- slices are independent sub-tasks; here they are the units of one
-// GPU's work instead of MPI processes -- and Sec. "Scaling", global reduction).
+// Scheme" -- slices are independent sub-tasks, here the units of one GPU's
+// work instead of MPI processes -- and Sec. "Scaling", global reduction).
+//
+// Steps run in three phases.  Phase 0 (no fixed index below the step) runs
+// once per plan.  Phase 1 (depends on sliced indices only) runs once per
+// slice and its results are shared by every bitstring of the call.  Phase 2
+// (depends on the bitstring's closed output bits) runs once per (bitstring,
+// slice) unit.  A launch covers a whole group of units (grid dimension), with
+// shared operands addressed through zero unit strides.
 //
 // Device memory of a plan (allocated on first use, kept until tn_free_plan):
-//   leaf store  -- every leaf tensor in complex64, full (fixed indices included)
-//   invariant   -- outputs of steps that depend on no fixed index (computed once)
-//   unit arena  -- G units x per-unit arena: variant leaf sub-tensors and
-//                  variant step outputs at the planner's liveness offsets
-//   accumulator -- nb x 2^k complex128
+//   leaf store   -- every leaf tensor in complex64, full (fixed indices included)
+//   invariant    -- outputs of phase-0 steps
+//   slice arena  -- Gs slices x per-slice arena (phase-1 leaves and outputs)
+//   pair arena   -- Gs x Gb units x per-unit arena (phase-2 leaves and outputs)
+//   accumulator  -- nb x 2^k complex128 (host I/O; device I/O sums into `out`)
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -23,17 +31,20 @@ struct Executor {
   float2* store = nullptr;
   float2* inv = nullptr;
   bool inv_ready = false;
-  float2* arena = nullptr;
-  int64_t arena_units = 0;
-  LeafGather* gather = nullptr;
-  int ngather = 0;
+  float2* sarena = nullptr;  // slice arena
+  float2* parena = nullptr;  // pair arena
+  int64_t sarena_cap = 0, parena_cap = 0;  // capacities in elements
+  LeafGather* gather = nullptr;  // phase-1 descriptors then phase-2 descriptors
+  int ngather1 = 0, ngather2 = 0;
   int64_t* perm = nullptr;
   uint64_t* bits = nullptr;
   int64_t bits_cap = 0;
   double2* acc = nullptr;
   int64_t acc_cap = 0;
+  int* err = nullptr;          // device error word of bounded waits
   std::vector<GemmDesc> desc;  // per step, unit strides filled at launch
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<cudaEvent_t> pev;  // profiling event pool
 };
 
 void destroy_executor(Executor* e) {
@@ -43,24 +54,29 @@ void destroy_executor(Executor* e) {
   if (e->device >= 0) cudaSetDevice(e->device);
   cudaFree(e->store);
   cudaFree(e->inv);
-  cudaFree(e->arena);
+  cudaFree(e->sarena);
+  cudaFree(e->parena);
   cudaFree(e->gather);
   cudaFree(e->perm);
   cudaFree(e->bits);
   cudaFree(e->acc);
+  cudaFree(e->err);
   if (e->ev0) cudaEventDestroy(e->ev0);
   if (e->ev1) cudaEventDestroy(e->ev1);
+  for (auto ev : e->pev) cudaEventDestroy(ev);
   if (cur >= 0) cudaSetDevice(cur);
   delete e;
 }
 
-#define CK(call)                                                                             \
-  do {                                                                                       \
-    cudaError_t _e = (call);                                                                 \
-    if (_e != cudaSuccess) return fail(TN_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(_e), __FILE__, __LINE__); \
+#define CK(call)                                                                                       \
+  do {                                                                                                 \
+    cudaError_t _e = (call);                                                                           \
+    if (_e != cudaSuccess)                                                                             \
+      return fail(TN_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(_e), __FILE__, __LINE__);    \
   } while (0)
 
-// Per-bit strides of the GEMM view of one step (see GemmDesc).
+// Per-bit strides of the GEMM view of one step (see GemmDesc): bits of each
+// group are numbered from the operand's fastest index upward.
 void make_gemm_desc(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc,
                     GemmDesc& d) {
   std::memset(&d, 0, sizeof d);
@@ -69,7 +85,6 @@ void make_gemm_desc(const std::vector<int>& la, const std::vector<int>& lb, cons
       if (ls[p] == l) return int32_t(1) << (ls.size() - 1 - p);
     return -1;
   };
-  // walk each operand from its fastest index upward
   for (int p = (int)la.size() - 1; p >= 0; --p) {
     int l = la[p];
     int32_t sb = stride_in(lb, l);
@@ -80,43 +95,46 @@ void make_gemm_desc(const std::vector<int>& la, const std::vector<int>& lb, cons
     int l = lb[p];
     if (stride_in(la, l) < 0) { d.bn[d.nn] = stride_in(lb, l); d.cn[d.nn] = stride_in(lc, l); ++d.nn; }
   }
+  d.units = d.units_lo = 1;
 }
 
 static tn_status setup(Plan& P, Executor& E) {
   CK(cudaGetDevice(&E.device));
   const Network& N = P.net;
   const int L = (int)N.leaves.size();
-  std::vector<float2> h_store(P.leaf_store_elems);
+  std::vector<float2> h_store(std::max<int64_t>(P.leaf_store_elems, 1));
   for (int i = 0; i < L; ++i) {
     const Leaf& lf = N.leaves[i];
     for (size_t e = 0; e < lf.data.size(); ++e)
       h_store[P.leaf_use[i].store_off + e] = make_float2((float)lf.data[e].real(), (float)lf.data[e].imag());
   }
-  CK(cudaMalloc(&E.store, std::max<int64_t>(P.leaf_store_elems, 1) * sizeof(float2)));
+  CK(cudaMalloc(&E.store, h_store.size() * sizeof(float2)));
   CK(cudaMemcpy(E.store, h_store.data(), h_store.size() * sizeof(float2), cudaMemcpyHostToDevice));
   CK(cudaMalloc(&E.inv, P.invariant_elems * sizeof(float2)));
-  std::vector<LeafGather> g;
+  std::vector<LeafGather> g1, g2;
   for (int i = 0; i < L; ++i) {
     const LeafUse& U = P.leaf_use[i];
-    if (!U.variant) continue;
+    if (U.phase == 0) continue;
     const Leaf& lf = N.leaves[i];
+    const int r = (int)lf.labels.size();
+    if (r > kMaxLeafRank) return fail(TN_EINVAL, "leaf rank %d > %d", r, kMaxLeafRank);
     LeafGather d;
     std::memset(&d, 0, sizeof d);
-    if ((int)lf.labels.size() > kMaxLeafRank) return fail(TN_EINVAL, "leaf rank %zu > %d", lf.labels.size(), kMaxLeafRank);
     d.store_off = U.store_off;
     d.dst_off = U.off;
-    const int r = (int)lf.labels.size();
     for (int p = 0; p < r; ++p) {
       int32_t st = int32_t(1) << (r - 1 - p);
       if (U.fixed_src[p] == -1) d.kept_stride[d.nkept++] = st;
       else { d.fixed_src[d.nfixed] = U.fixed_src[p]; d.fixed_stride[d.nfixed] = st; ++d.nfixed; }
     }
-    g.push_back(d);
+    (U.phase == 1 ? g1 : g2).push_back(d);
   }
-  E.ngather = (int)g.size();
-  if (!g.empty()) {
-    CK(cudaMalloc(&E.gather, g.size() * sizeof(LeafGather)));
-    CK(cudaMemcpy(E.gather, g.data(), g.size() * sizeof(LeafGather), cudaMemcpyHostToDevice));
+  E.ngather1 = (int)g1.size();
+  E.ngather2 = (int)g2.size();
+  g1.insert(g1.end(), g2.begin(), g2.end());
+  if (!g1.empty()) {
+    CK(cudaMalloc(&E.gather, g1.size() * sizeof(LeafGather)));
+    CK(cudaMemcpy(E.gather, g1.data(), g1.size() * sizeof(LeafGather), cudaMemcpyHostToDevice));
   }
   CK(cudaMalloc(&E.perm, P.root_perm.size() * sizeof(int64_t)));
   CK(cudaMemcpy(E.perm, P.root_perm.data(), P.root_perm.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
@@ -124,53 +142,127 @@ static tn_status setup(Plan& P, Executor& E) {
   for (size_t s = 0; s < P.steps.size(); ++s) make_gemm_desc(P.steps[s].la, P.steps[s].lb, P.steps[s].lc, E.desc[s]);
   CK(cudaEventCreate(&E.ev0));
   CK(cudaEventCreate(&E.ev1));
+  CK(cudaMalloc(&E.err, sizeof(int)));
+  CK(cudaMemset(E.err, 0, sizeof(int)));
   return TN_OK;
 }
 
-// Operand pointer and unit stride of SSA id x.
-static void operand(const Plan& P, const Executor& E, int x, const float2*& ptr, int64_t& unit_stride) {
-  const int L = (int)P.net.leaves.size();
-  if (x < L) {
-    const LeafUse& U = P.leaf_use[x];
-    if (U.variant) { ptr = E.arena + U.off; unit_stride = P.unit_arena_elems; }
-    else { ptr = E.store + U.store_off; unit_stride = 0; }
-  } else {
-    const Step& S = P.steps[x - L];
-    if (S.variant) { ptr = E.arena + S.off_c; unit_stride = P.unit_arena_elems; }
-    else { ptr = E.inv + S.off_c; unit_stride = 0; }
+namespace {
+
+// Geometry of the current launch group.
+struct Geo {
+  int gs = 1;       // slices in the group
+  int gb = 1;       // bitstrings in the group (phase 2)
+};
+
+struct Ctx {
+  const Plan& P;
+  Executor& E;
+  cudaStream_t st;
+  bool profile;
+  int64_t launches = 0;
+  struct Rec { int klass; double flops, bytes; size_t ev; };
+  std::vector<Rec> recs;
+  size_t nev = 0;
+  int precision = TN_PREC_C64;
+  Ctx(const Plan& p, Executor& e, cudaStream_t s, bool prof) : P(p), E(e), st(s), profile(prof) {}
+
+  tn_status event(size_t& idx) {
+    if (nev == E.pev.size()) {
+      cudaEvent_t ev;
+      CK(cudaEventCreate(&ev));
+      E.pev.push_back(ev);
+    }
+    idx = nev++;
+    CK(cudaEventRecord(E.pev[idx], st));
+    return TN_OK;
   }
+};
+
+// Base pointer and (lo, hi) unit strides of SSA operand x inside a launch of `phase`.
+void operand(const Plan& P, const Executor& E, int x, int phase, const Geo& g, const float2*& ptr, int64_t& lo,
+             int64_t& hi) {
+  const int L = (int)P.net.leaves.size();
+  int ph;
+  int64_t off;
+  if (x < L) { ph = P.leaf_use[x].phase; off = P.leaf_use[x].off; }
+  else { ph = P.steps[x - L].phase; off = P.steps[x - L].off_c; }
+  if (ph == 0) {
+    ptr = (x < L ? E.store : E.inv) + off;
+    lo = hi = 0;
+  } else if (ph == 1) {
+    ptr = E.sarena + off;
+    lo = P.slice_arena_elems;  // slice index is the low part of the unit in both phases
+    hi = 0;
+  } else {
+    ptr = E.parena + off;
+    lo = P.unit_arena_elems;
+    hi = (int64_t)g.gs * P.unit_arena_elems;
+  }
+  (void)phase;
 }
 
-static tn_status run_step(const Plan& P, Executor& E, size_t s, int units, cudaStream_t st, int64_t& launches) {
+tn_status run_step(Ctx& c, size_t s, const Geo& g) {
+  const Plan& P = c.P;
+  Executor& E = c.E;
   const Step& S = P.steps[s];
   GemmDesc d = E.desc[s];
-  const float2 *A, *B;
-  operand(P, E, S.a, A, d.a_unit);
-  operand(P, E, S.b, B, d.b_unit);
-  float2* C = (S.variant ? E.arena : E.inv) + S.off_c;
-  d.c_unit = S.variant ? P.unit_arena_elems : 0;
-  d.units = S.variant ? units : 1;
+  const float2 *A, *B, *Cc;
+  int64_t clo, chi;
+  operand(P, E, S.a, S.phase, g, A, d.a_lo, d.a_hi);
+  operand(P, E, S.b, S.phase, g, B, d.b_lo, d.b_hi);
+  operand(P, E, (int)P.net.leaves.size() + (int)s, S.phase, g, Cc, clo, chi);
+  d.c_lo = clo;
+  d.c_hi = chi;
+  float2* C = const_cast<float2*>(Cc);
+  d.units_lo = S.phase == 0 ? 1 : g.gs;
+  d.units = S.phase == 0 ? 1 : S.phase == 1 ? g.gs : g.gs * g.gb;
+  size_t e0 = 0, e1 = 0;
+  if (c.profile) { tn_status r = c.event(e0); if (r) return r; }
   cudaError_t e;
-  if (S.klass == SC_VECTOR) e = launch_vector(A, B, C, d, st);
-  else e = launch_gemm_simt(A, B, C, d, st);
-  ++launches;
+  int klass = S.klass == SC_VECTOR ? TN_KCLASS_VECTOR : TN_KCLASS_GEMM_SIMT;
+  const bool split = c.precision == TN_PREC_SPLIT_BF16;
+  if (S.klass != SC_VECTOR && split && tc_shape_ok(d)) klass = TN_KCLASS_GEMM_TC;
+  if (klass == TN_KCLASS_VECTOR) e = launch_vector(A, B, C, d, c.st);
+  else if (klass == TN_KCLASS_GEMM_TC) e = launch_gemm_tc(A, B, C, d, true, 1.f, 1.f, E.err, c.st);
+  else e = launch_gemm_simt(A, B, C, d, c.st);
+  ++c.launches;
   if (e != cudaSuccess) return fail(TN_ECUDA, "step %zu launch: %s", s, cudaGetErrorString(e));
+  if (c.profile) {
+    tn_status r = c.event(e1);
+    if (r) return r;
+    const double M = std::ldexp(1.0, d.nm), N = std::ldexp(1.0, d.nn), K = std::ldexp(1.0, d.nk);
+    const double U = d.units;
+    auto distinct = [&](int64_t lo, int64_t hi) {
+      return (lo ? (double)d.units_lo : 1.0) * (hi ? U / d.units_lo : 1.0);
+    };
+    double bytes = 8.0 * (M * K * distinct(d.a_lo, d.a_hi) + K * N * distinct(d.b_lo, d.b_hi) + M * N * U);
+    c.recs.push_back({klass, 8.0 * M * N * K * U, bytes, e0});
+  }
   return TN_OK;
 }
+
+tn_status run_misc(Ctx& c, cudaError_t e, const char* what) {
+  ++c.launches;
+  if (e != cudaSuccess) return fail(TN_ECUDA, "%s launch: %s", what, cudaGetErrorString(e));
+  return TN_OK;
+}
+
+}  // namespace
 
 tn_status contract_amplitudes(Plan& P, const uint64_t* bits, int64_t nb, double* out, const tn_exec_opts& o,
                               tn_report* rep) {
-  if (o.precision != TN_PREC_C64)
+  if (o.precision != TN_PREC_C64 && o.precision != TN_PREC_SPLIT_BF16)
     return fail(TN_EINVAL, "tn_contract_amplitudes: precision %d not available in this build", o.precision);
   const int n = P.net.n;
   const int k = (int)P.net.open_qubits.size();
   const int words = std::max(1, (n + 63) / 64);
   const int64_t S_all = int64_t(1) << P.sliced.size();
-  const int64_t s0 = o.slice_begin;
-  const int64_t ns = o.slice_count < 0 ? S_all - s0 : o.slice_count;
-  if (s0 < 0 || s0 > S_all || ns < 0 || s0 + ns > S_all)
-    return fail(TN_EINVAL, "tn_contract_amplitudes: slice range [%lld, %lld) outside [0, %lld)", (long long)s0,
-                (long long)(s0 + ns), (long long)S_all);
+  const int64_t s_begin = o.slice_begin;
+  const int64_t ns = o.slice_count < 0 ? S_all - s_begin : o.slice_count;
+  if (s_begin < 0 || s_begin > S_all || ns < 0 || s_begin + ns > S_all)
+    return fail(TN_EINVAL, "tn_contract_amplitudes: slice range [%lld, %lld) outside [0, %lld)", (long long)s_begin,
+                (long long)(s_begin + ns), (long long)S_all);
   cudaStream_t st = (cudaStream_t)o.stream;
   if (!P.exec) {
     P.exec = new Executor();
@@ -179,98 +271,153 @@ tn_status contract_amplitudes(Plan& P, const uint64_t* bits, int64_t nb, double*
   }
   Executor& E = *P.exec;
   const int64_t nout = nb << k;
-  const int64_t total_units = nb * ns;
-  int64_t launches = 0;
 
-  // group size
-  int64_t G = o.units_per_group;
-  if (G <= 0) {
+  // ---- group geometry: Gb bitstrings x Gs slices per launch
+  const int64_t Se = P.slice_arena_elems, Pe = P.unit_arena_elems;
+  int64_t Gb = std::max<int64_t>(1, std::min<int64_t>(nb, 256));
+  int64_t Gs = o.units_per_group;
+  if (Gs <= 0) {
     size_t freeb = 0, totb = 0;
     CK(cudaMemGetInfo(&freeb, &totb));
-    double budget = std::min<double>((double)freeb * 0.5 + (double)E.arena_units * P.unit_arena_elems * 8.0,
-                                     96.0 * (1ull << 30));
-    G = (int64_t)(budget / (P.unit_arena_elems * 8.0));
-    G = std::min<int64_t>(G, 1024);
+    double have = (double)(E.sarena_cap + E.parena_cap) * 8.0;
+    double budget = std::min<double>((double)freeb * 0.6 + have, 120.0 * (1ull << 30));
+    Gs = (int64_t)(budget / (8.0 * ((double)Se + (double)Gb * Pe)));
+    while (Gs < 1 && Gb > 1) {  // not even one slice fits with Gb bitstrings: shrink Gb
+      Gb = std::max<int64_t>(1, Gb / 2);
+      Gs = (int64_t)(budget / (8.0 * ((double)Se + (double)Gb * Pe)));
+    }
+    Gs = std::min<int64_t>(Gs, 1024);
   }
-  G = std::max<int64_t>(1, std::min<int64_t>({G, std::max<int64_t>(total_units, 1), 65535}));
-  if (E.arena_units < G) {
-    cudaFree(E.arena);
-    E.arena = nullptr;
-    E.arena_units = 0;
-    size_t bytes = (size_t)G * P.unit_arena_elems * sizeof(float2);
-    cudaError_t ae = cudaMalloc(&E.arena, bytes);
+  Gs = std::max<int64_t>(1, std::min<int64_t>(Gs, std::max<int64_t>(ns, 1)));
+  Gs = std::min<int64_t>(Gs, 65535 / Gb);
+  if (Gs < 1) return fail(TN_EINVAL, "tn_contract_amplitudes: launch geometry does not fit");
+  auto grow = [&](float2*& p, int64_t& cap, int64_t need) -> tn_status {
+    if (cap >= need) return TN_OK;
+    cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t ae = cudaMalloc(&p, (size_t)need * sizeof(float2));
     if (ae != cudaSuccess) {
       cudaGetLastError();
-      return fail(TN_EHBM, "tn_contract_amplitudes: arena of %zu bytes (%lld units) does not fit", bytes, (long long)G);
+      return fail(TN_EHBM, "tn_contract_amplitudes: %lld-byte arena does not fit in device memory",
+                  (long long)(need * 8));
     }
-    E.arena_units = G;
-  }
-  // bitstrings and accumulator
+    cap = need;
+    return TN_OK;
+  };
+  tn_status gs_ = grow(E.sarena, E.sarena_cap, Gs * Se);
+  if (gs_ != TN_OK) return gs_;
+  gs_ = grow(E.parena, E.parena_cap, Gs * Gb * Pe);
+  if (gs_ != TN_OK) return gs_;
+
   const uint64_t* d_bits = bits;
   double2* d_acc = (double2*)out;
   if (!o.device_io) {
     if (E.bits_cap < nb * words) {
       cudaFree(E.bits);
       E.bits = nullptr;
+      E.bits_cap = 0;
       CK(cudaMalloc(&E.bits, std::max<int64_t>(nb * words, 1) * sizeof(uint64_t)));
       E.bits_cap = nb * words;
     }
     if (E.acc_cap < nout) {
       cudaFree(E.acc);
       E.acc = nullptr;
+      E.acc_cap = 0;
       CK(cudaMalloc(&E.acc, std::max<int64_t>(nout, 1) * sizeof(double2)));
       E.acc_cap = nout;
     }
     d_bits = E.bits;
     d_acc = E.acc;
   }
+  Ctx c(P, E, st, o.profile != 0);
+  c.precision = o.precision;
   CK(cudaEventRecord(E.ev0, st));
-  if (!o.device_io && nb > 0) CK(cudaMemcpyAsync((void*)d_bits, bits, nb * words * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+  if (!o.device_io && nb > 0)
+    CK(cudaMemcpyAsync((void*)d_bits, bits, nb * words * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
   if (nout > 0) CK(cudaMemsetAsync(d_acc, 0, nout * sizeof(double2), st));
-  // invariant steps once
+  Geo g;
   if (!E.inv_ready) {
     for (size_t s = 0; s < P.steps.size(); ++s)
-      if (!P.steps[s].variant) {
-        tn_status e = run_step(P, E, s, 1, st, launches);
-        if (e != TN_OK) return e;
+      if (P.steps[s].phase == 0) {
+        tn_status r = run_step(c, s, g);
+        if (r != TN_OK) return r;
       }
     E.inv_ready = true;
   }
   const int L = (int)P.net.leaves.size();
-  const float2* root;
-  int64_t root_stride;
-  operand(P, E, L == 1 ? 0 : L + (int)P.steps.size() - 1, root, root_stride);
-  for (int64_t u0 = 0; u0 < total_units; u0 += G) {
+  const int root_id = L == 1 ? 0 : L + (int)P.steps.size() - 1;
+  for (int64_t s0 = s_begin; s0 < s_begin + ns && nb > 0; s0 += Gs) {
+    g.gs = (int)std::min<int64_t>(Gs, s_begin + ns - s0);
+    g.gb = 1;
     GroupInfo gi;
-    gi.unit0 = u0;
-    gi.slices = ns;
-    gi.slice_begin = s0;
+    gi.slice0 = s0;
+    gi.b0 = 0;
+    gi.nslice = g.gs;
+    gi.nb = 1;
     gi.words = words;
-    gi.units = (int)std::min<int64_t>(G, total_units - u0);
-    cudaError_t e = launch_gather(E.store, E.arena, P.unit_arena_elems, E.gather, E.ngather, d_bits, gi, st);
-    ++launches;
-    if (e != cudaSuccess) return fail(TN_ECUDA, "gather launch: %s", cudaGetErrorString(e));
+    gi.units = g.gs;
+    if (E.ngather1) {
+      tn_status r = run_misc(c, launch_gather(E.store, E.sarena, Se, E.gather, E.ngather1, d_bits, gi, st), "gather");
+      if (r) return r;
+    }
     for (size_t s = 0; s < P.steps.size(); ++s)
-      if (P.steps[s].variant) {
-        tn_status r = run_step(P, E, s, gi.units, st, launches);
+      if (P.steps[s].phase == 1) {
+        tn_status r = run_step(c, s, g);
         if (r != TN_OK) return r;
       }
-    e = launch_accumulate(root, root_stride, E.perm, (int)P.root_perm.size(), d_acc, gi, st);
-    ++launches;
-    if (e != cudaSuccess) return fail(TN_ECUDA, "accumulate launch: %s", cudaGetErrorString(e));
+    for (int64_t b0 = 0; b0 < nb; b0 += Gb) {
+      g.gb = (int)std::min<int64_t>(Gb, nb - b0);
+      gi.b0 = b0;
+      gi.nb = g.gb;
+      gi.units = g.gs * g.gb;
+      if (E.ngather2) {
+        tn_status r = run_misc(
+            c, launch_gather(E.store, E.parena, Pe, E.gather + E.ngather1, E.ngather2, d_bits, gi, st), "gather");
+        if (r) return r;
+      }
+      for (size_t s = 0; s < P.steps.size(); ++s)
+        if (P.steps[s].phase == 2) {
+          tn_status r = run_step(c, s, g);
+          if (r != TN_OK) return r;
+        }
+      const float2* root;
+      int64_t rlo, rhi;
+      operand(P, E, root_id, 2, g, root, rlo, rhi);
+      tn_status r = run_misc(
+          c, launch_accumulate(root, rlo, rhi, E.perm, (int)P.root_perm.size(), d_acc, gi, st), "accumulate");
+      if (r) return r;
+    }
   }
-  if (!o.device_io && nout > 0)
-    CK(cudaMemcpyAsync(out, d_acc, nout * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  if (!o.device_io && nout > 0) CK(cudaMemcpyAsync(out, d_acc, nout * sizeof(double2), cudaMemcpyDeviceToHost, st));
   CK(cudaEventRecord(E.ev1, st));
-  if (!o.device_io || rep) CK(cudaEventSynchronize(E.ev1));
+  if (!o.device_io || rep) {
+    CK(cudaEventSynchronize(E.ev1));
+    int herr = 0;
+    CK(cudaMemcpy(&herr, E.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) {
+      cudaMemset(E.err, 0, sizeof(int));
+      return fail(TN_ETIMEOUT, "tn_contract_amplitudes: a tensor-core pipeline wait expired (code %d)", herr);
+    }
+  }
   if (rep) {
     std::memset(rep, 0, sizeof *rep);
     float ms = 0;
     CK(cudaEventElapsedTime(&ms, E.ev0, E.ev1));
     rep->device_ms = ms;
-    rep->units = total_units;
-    rep->flops = 8.0 * P.cmac_per_slice * (double)total_units;
-    rep->kernel_launches = launches;
+    rep->units = nb * ns;
+    const double shared = P.cmac_slice_only, per = P.cmac_per_slice;
+    rep->flops = 8.0 * ((double)ns * shared + (double)nb * ns * (per - shared));
+    rep->flops_equivalent = 8.0 * per * (double)nb * ns;
+    rep->kernel_launches = c.launches;
+    for (auto& r : c.recs) {
+      float t = 0;
+      CK(cudaEventElapsedTime(&t, E.pev[r.ev], E.pev[r.ev + 1]));
+      rep->class_ms[r.klass] += t;
+      rep->class_launches[r.klass] += 1;
+      rep->class_flops[r.klass] += r.flops;
+      rep->class_bytes[r.klass] += r.bytes;
+    }
   }
   return TN_OK;
 }

@@ -20,9 +20,8 @@ __global__ void gather_kernel(const float2* __restrict__ store, float2* __restri
                               GroupInfo g) {
   const LeafGather& L = descs[blockIdx.x];
   const int u = blockIdx.y;
-  const int64_t gu = g.unit0 + u;
-  const int64_t b = gu / g.slices;
-  const int64_t s = g.slice_begin + gu % g.slices;
+  const int64_t s = g.slice0 + u % g.nslice;
+  const int64_t b = g.b0 + u / g.nslice;
   int64_t fixed_off = L.store_off;
   for (int f = 0; f < L.nfixed; ++f) {
     int src = L.fixed_src[f];
@@ -44,28 +43,21 @@ __global__ void gather_kernel(const float2* __restrict__ store, float2* __restri
   }
 }
 
-// acc[b, j] += sum over the group's units of bitstring b (in unit order) of root_u[perm[j]].
-__global__ void accumulate_kernel(const float2* __restrict__ root, int64_t root_unit_stride,
+__global__ void accumulate_kernel(const float2* __restrict__ root, int64_t r_lo, int64_t r_hi,
                                   const int64_t* __restrict__ perm, int nperm, double2* __restrict__ acc,
                                   GroupInfo g) {
-  const int64_t b_first = g.unit0 / g.slices;
-  const int64_t b_last = (g.unit0 + g.units - 1) / g.slices;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nbl = b_last - b_first + 1;
-  if (idx >= nbl * nperm) return;
-  const int64_t b = b_first + idx / nperm;
+  if (idx >= (int64_t)g.nb * nperm) return;
+  const int bl = (int)(idx / nperm);
   const int j = (int)(idx % nperm);
-  int64_t u_lo = b * g.slices - g.unit0, u_hi = (b + 1) * g.slices - g.unit0;
-  if (u_lo < 0) u_lo = 0;
-  if (u_hi > g.units) u_hi = g.units;
-  double2 a = acc[b * nperm + j];
-  const int64_t pj = perm[j];
-  for (int64_t u = u_lo; u < u_hi; ++u) {
-    float2 v = root[u * root_unit_stride + pj];
+  double2 a = acc[(g.b0 + bl) * nperm + j];
+  const float2* r = root + bl * r_hi + perm[j];
+  for (int sl = 0; sl < g.nslice; ++sl) {
+    float2 v = r[sl * r_lo];
     a.x += (double)v.x;
     a.y += (double)v.y;
   }
-  acc[b * nperm + j] = a;
+  acc[(g.b0 + bl) * nperm + j] = a;
 }
 
 __global__ void permute_kernel(const float2* __restrict__ src, float2* __restrict__ dst, const PermDesc pd,
@@ -90,13 +82,11 @@ cudaError_t launch_gather(const float2* store, float2* arena, int64_t arena_stri
   return cudaGetLastError();
 }
 
-cudaError_t launch_accumulate(const float2* root, int64_t root_unit_stride, const int64_t* perm, int nperm,
+cudaError_t launch_accumulate(const float2* root, int64_t r_lo, int64_t r_hi, const int64_t* perm, int nperm,
                               double2* acc, const GroupInfo& g, cudaStream_t s) {
-  const int64_t b_first = g.unit0 / g.slices;
-  const int64_t b_last = (g.unit0 + g.units - 1) / g.slices;
-  const int64_t total = (b_last - b_first + 1) * nperm;
+  const int64_t total = (int64_t)g.nb * nperm;
   const int nt = 256;
-  accumulate_kernel<<<(unsigned)((total + nt - 1) / nt), nt, 0, s>>>(root, root_unit_stride, perm, nperm, acc, g);
+  accumulate_kernel<<<(unsigned)((total + nt - 1) / nt), nt, 0, s>>>(root, r_lo, r_hi, perm, nperm, acc, g);
   return cudaGetLastError();
 }
 

@@ -28,10 +28,10 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(const float2* __restrict_
                                                         float2* __restrict__ C, const GemmDesc d) {
   const int64_t M = int64_t(1) << d.nm, N = int64_t(1) << d.nn, K = int64_t(1) << d.nk;
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
-  const int64_t u = blockIdx.z;
-  A += u * d.a_unit;
-  B += u * d.b_unit;
-  C += u * d.c_unit;
+  const int64_t ulo = blockIdx.z % d.units_lo, uhi = blockIdx.z / d.units_lo;
+  A += ulo * d.a_lo + uhi * d.a_hi;
+  B += ulo * d.b_lo + uhi * d.b_hi;
+  C += ulo * d.c_lo + uhi * d.c_hi;
   __shared__ int32_t rowA[BM], rowC[BM], colB[BN], colC[BN], kA[BK], kB[BK];
   __shared__ float2 As[BK][BM], Bs[BK][BN];
   const int tid = threadIdx.x;

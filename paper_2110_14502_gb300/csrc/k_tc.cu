@@ -1,0 +1,393 @@
+// Fused permute-GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// Paper: Sec. "Tensor Contraction Using Fused Permutation and Multiplication"
+// (dense case: fetch the permuted operand blocks and multiply them without a
+// separate permutation pass) and Sec. "A Mixed-Precision Computation Method
+// via Adaptive Precision Scaling" (half-precision products, single-precision
+// accumulation).
+//
+// Complex arithmetic uses the real block form: with A' = [Ar | Ai] interleaved
+// along K (A'[m][2k+c]) and B'[2k+c][2n+d] = {Br, Bi; -Bi, Br}[c][d],
+// D'[m][2n+d] = sum A' B' gives (Cr, Ci) interleaved -- 8 real MMA flops per
+// complex multiply-add, the counted rate.  For the split precision each
+// operand is x = hi + lo with hi = rn16(x), lo = rn16(x - hi) and the product
+// keeps hi*hi + hi*lo + lo*hi (three MMAs into the same FP32 accumulator).
+//
+// Per CTA: one 128 (complex rows) x 64 (complex columns) output tile held in
+// TMEM as 128 lanes x 128 FP32 columns.  Each K stage of 32 complex values is
+// gathered from global memory through per-row / per-column offsets (the
+// permutation), converted to 16-bit hi/lo, and stored K-major in 128-byte
+// swizzled shared memory; one thread issues the tcgen05.mma instructions and
+// commits them to the stage's mbarrier, which the loaders wait on before they
+// refill that stage.  Global loads of stage i+1 are issued before the MMAs of
+// stage i are queued, so they overlap.  Every mbarrier wait is bounded: on
+// expiry the CTA records an error word, skips the rest of its work and still
+// releases its TMEM.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "kernels.h"
+
+namespace tn {
+
+namespace {
+
+constexpr int TM = 128;          // complex rows per tile (= MMA M)
+constexpr int TN = 64;           // complex columns per tile (MMA N = 128 reals)
+constexpr int TK = 32;           // complex K per stage (64 reals = one 128-byte swizzle row)
+constexpr int NSTAGE = 3;
+constexpr int NTHREADS = 256;
+constexpr int TILE_BYTES = 128 * 128;               // 128 rows x 128 bytes
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;         // A hi, A lo, B' hi, B' lo
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024;  // + alignment slack
+constexpr uint32_t TMEM_COLS = 128;
+constexpr long long kWaitLimit = 1ll << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// Bounded wait for the given phase parity; returns false on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// K-major, 128-byte swizzled operand descriptor (tcgen05 shared memory descriptor):
+// start address >> 4 in bits 0-13, leading byte offset (unused for this
+// layout) in 16-29, stride byte offset 1024 (8 rows x 128 B) in 32-45,
+// descriptor version 1 in bits 46-47, swizzle mode 2 (128 B) in bits 61-63.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and
+// B format (bits 7-9, 10-12: 0 fp16, 1 bf16), both K-major, N >> 3 in bits
+// 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_f16(bool bf16, int M, int N) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ int32_t bit_offset(int64_t x, int nb, const int32_t* st) {
+  int32_t o = 0;
+  for (int i = 0; i < nb; ++i)
+    if ((x >> i) & 1) o += st[i];
+  return o;
+}
+
+// Byte offset of 16-byte chunk `c` of row `r` in a 128-byte swizzled tile.
+__device__ __forceinline__ uint32_t sw_off(int r, int c) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+}
+
+template <bool BF16>
+struct Half16;
+template <>
+struct Half16<true> {
+  static __device__ __forceinline__ void split(float x, uint16_t& hi, uint16_t& lo) {
+    __nv_bfloat16 h = __float2bfloat16_rn(x);
+    __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(l);
+  }
+};
+template <>
+struct Half16<false> {
+  static __device__ __forceinline__ void split(float x, uint16_t& hi, uint16_t& lo) {
+    __half h = __float2half_rn(x);
+    __half l = __float2half_rn(x - __half2float(h));
+    hi = __half_as_ushort(h);
+    lo = __half_as_ushort(l);
+  }
+};
+
+__device__ __forceinline__ uint32_t pack2(uint16_t a, uint16_t b) { return (uint32_t)a | ((uint32_t)b << 16); }
+
+// Register staging of one K stage: each thread owns 4 A-chunks and 2 B-chunks,
+// a chunk being 4 consecutive complex K values of one row (A) or column (B).
+struct Stage {
+  float2 a[4][4];
+  float2 b[2][4];
+};
+
+template <bool BF16>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    gemm_tc_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float2* __restrict__ C,
+                   const GemmDesc d, float a_scale, float b_scale, int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t bar_mma[NSTAGE];
+  __shared__ uint64_t bar_done;
+  __shared__ uint32_t tmem_base_slot;
+  __shared__ int32_t rowA[TM], rowC[TM], colB[TN], colC[TN];
+  __shared__ int32_t kA[2][TK], kB[2][TK];
+  __shared__ int abort_flag;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t M = int64_t(1) << d.nm, N = int64_t(1) << d.nn, K = int64_t(1) << d.nk;
+  const int64_t m0 = (int64_t)blockIdx.x * TM, n0 = (int64_t)blockIdx.y * TN;
+  {
+    const int64_t ulo = blockIdx.z % d.units_lo, uhi = blockIdx.z / d.units_lo;
+    A += ulo * d.a_lo + uhi * d.a_hi;
+    B += ulo * d.b_lo + uhi * d.b_hi;
+    C += ulo * d.c_lo + uhi * d.c_hi;
+  }
+  if (tid < TM) {
+    int64_t m = m0 + tid;
+    rowA[tid] = m < M ? bit_offset(m, d.nm, d.am) : -1;
+    rowC[tid] = m < M ? bit_offset(m, d.nm, d.cm) : -1;
+  } else if (tid < TM + TN) {
+    int64_t n = n0 + (tid - TM);
+    colB[tid - TM] = n < N ? bit_offset(n, d.nn, d.bn) : -1;
+    colC[tid - TM] = n < N ? bit_offset(n, d.nn, d.cn) : -1;
+  }
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; ++s) mbar_init(&bar_mma[s], 1);
+    mbar_init(&bar_done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  const int nkt = (int)((K + TK - 1) / TK);
+  auto k_offsets = [&](int kt, int buf) {
+    if (tid < TK) {
+      int64_t k = (int64_t)kt * TK + tid;
+      kA[buf][tid] = k < K ? bit_offset(k, d.nk, d.ak) : -1;
+    } else if (tid >= 32 && tid < 32 + TK) {
+      int64_t k = (int64_t)kt * TK + (tid - 32);
+      kB[buf][tid - 32] = k < K ? bit_offset(k, d.nk, d.bk) : -1;
+    }
+  };
+  k_offsets(0, 0);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_slot;
+
+  // Chunk ownership.  A: 128 rows x 8 chunks = 1024 chunks, 4 per thread.
+  // K-contiguous operands map consecutive threads to consecutive chunks of a
+  // row; otherwise to consecutive rows (coalesced along M / N).
+  const bool a_kfast = d.nk > 0 && d.ak[0] == 1;
+  const bool b_kfast = d.nk > 0 && d.bk[0] == 1;
+  auto a_task = [&](int i, int& r, int& c) {
+    int e = tid + i * NTHREADS;
+    if (a_kfast) { r = e >> 3; c = e & 7; } else { r = e & 127; c = e >> 7; }
+  };
+  auto b_task = [&](int i, int& r, int& c) {  // B: 64 columns x 8 chunks = 512, 2 per thread
+    int e = tid + i * NTHREADS;
+    if (b_kfast) { r = e >> 3; c = e & 7; } else { r = e & 63; c = e >> 6; }
+  };
+  auto load_stage = [&](Stage& st, int buf) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int r, c;
+      a_task(i, r, c);
+      const int32_t ro = rowA[r];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int32_t ko = kA[buf][c * 4 + j];
+        st.a[i][j] = (ro >= 0 && ko >= 0) ? __ldg(A + (int64_t)ro + ko) : make_float2(0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      int r, c;
+      b_task(i, r, c);
+      const int32_t co = colB[r];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int32_t ko = kB[buf][c * 4 + j];
+        st.b[i][j] = (co >= 0 && ko >= 0) ? __ldg(B + (int64_t)co + ko) : make_float2(0.f, 0.f);
+      }
+    }
+  };
+  auto store_stage = [&](const Stage& st, int s) {
+    uint8_t* base = smem + s * STAGE_BYTES;
+    uint8_t* ahi = base;
+    uint8_t* alo = base + TILE_BYTES;
+    uint8_t* bhi = base + 2 * TILE_BYTES;
+    uint8_t* blo = base + 3 * TILE_BYTES;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int r, c;
+      a_task(i, r, c);
+      uint16_t h[8], l[8];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        Half16<BF16>::split(st.a[i][j].x * a_scale, h[2 * j], l[2 * j]);
+        Half16<BF16>::split(st.a[i][j].y * a_scale, h[2 * j + 1], l[2 * j + 1]);
+      }
+      const uint32_t o = sw_off(r, c);
+      *(uint4*)(ahi + o) = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
+      *(uint4*)(alo + o) = make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]), pack2(l[6], l[7]));
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      int r, c;
+      b_task(i, r, c);
+      // row 2r:   [Br, -Bi] per k;  row 2r+1: [Bi, Br] per k
+      uint16_t rh[8], ih[8], nih[8], rl[8], il[8], nil[8];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        uint16_t h, l;
+        Half16<BF16>::split(st.b[i][j].x * b_scale, h, l);
+        rh[j] = h; rl[j] = l;
+        Half16<BF16>::split(st.b[i][j].y * b_scale, h, l);
+        ih[j] = h; il[j] = l;
+        nih[j] = h ^ 0x8000; nil[j] = l ^ 0x8000;
+      }
+      const uint32_t o0 = sw_off(2 * r, c), o1 = sw_off(2 * r + 1, c);
+      *(uint4*)(bhi + o0) = make_uint4(pack2(rh[0], nih[0]), pack2(rh[1], nih[1]), pack2(rh[2], nih[2]), pack2(rh[3], nih[3]));
+      *(uint4*)(bhi + o1) = make_uint4(pack2(ih[0], rh[0]), pack2(ih[1], rh[1]), pack2(ih[2], rh[2]), pack2(ih[3], rh[3]));
+      *(uint4*)(blo + o0) = make_uint4(pack2(rl[0], nil[0]), pack2(rl[1], nil[1]), pack2(rl[2], nil[2]), pack2(rl[3], nil[3]));
+      *(uint4*)(blo + o1) = make_uint4(pack2(il[0], rl[0]), pack2(il[1], rl[1]), pack2(il[2], rl[2]), pack2(il[3], rl[3]));
+    }
+  };
+
+  constexpr uint32_t IDESC = idesc_f16(BF16, 128, 128);
+  Stage st;
+  load_stage(st, 0);
+  for (int kt = 0; kt < nkt; ++kt) {
+    const int s = kt % NSTAGE;
+    if (kt >= NSTAGE) {
+      if (!mbar_wait(&bar_mma[s], ((kt / NSTAGE) - 1) & 1)) {
+        atomicExch(err, 1);
+        abort_flag = 1;
+      }
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    store_stage(st, s);
+    if (kt + 1 < nkt) k_offsets(kt + 1, (kt + 1) & 1);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t ahi = sw128_desc(base + kk * 32);
+        const uint64_t alo = sw128_desc(base + TILE_BYTES + kk * 32);
+        const uint64_t bhi = sw128_desc(base + 2 * TILE_BYTES + kk * 32);
+        const uint64_t blo = sw128_desc(base + 3 * TILE_BYTES + kk * 32);
+        const uint32_t first = (kt == 0 && kk == 0) ? 0u : 1u;
+        mma_f16(tmem, ahi, bhi, IDESC, first);
+        mma_f16(tmem, ahi, blo, IDESC, 1u);
+        mma_f16(tmem, alo, bhi, IDESC, 1u);
+      }
+      mma_commit(&bar_mma[s]);
+      if (kt == nkt - 1) mma_commit(&bar_done);
+    }
+    if (kt + 1 < nkt) load_stage(st, (kt + 1) & 1);  // in flight while the MMAs above run
+  }
+  __syncthreads();
+  // On an aborted loop the last commit was never issued: commit now so that the
+  // wait below also covers the MMAs already queued before TMEM is released.
+  const bool aborted = abort_flag != 0;
+  if (aborted && tid == 0 && nkt > 0) mma_commit(&bar_done);
+  bool drained = true;
+  if (nkt > 0 && !mbar_wait(&bar_done, 0)) {
+    atomicExch(err, 2);
+    drained = false;
+  }
+  __syncthreads();
+  if (!drained) abort_flag = 1;
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!abort_flag) {
+    // epilogue: warp w reads lanes 32*(w%4).. of TMEM; warps 0-3 take columns
+    // 0-63 (complex 0-31), warps 4-7 columns 64-127 (complex 32-63).
+    const int q = warp & 3, half = warp >> 2;
+    const int r = q * 32 + lane;
+    const float inv = 1.0f / (a_scale * b_scale);
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc) {
+      const int col = half * 64 + cc * 32;
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const int32_t ro = rowC[r];
+      if (ro >= 0) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int cn = col / 2 + j;
+          const int32_t co = colC[cn];
+          if (co >= 0) C[(int64_t)ro + co] = make_float2(__uint_as_float(v[2 * j]) * inv, __uint_as_float(v[2 * j + 1]) * inv);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+}  // namespace
+
+bool tc_shape_ok(const GemmDesc& d) { return d.nm >= 7 && d.nn >= 4 && d.nk >= 3; }
+
+cudaError_t launch_gemm_tc(const float2* A, const float2* B, float2* C, const GemmDesc& d, bool bf16, float a_scale,
+                           float b_scale, int* err, cudaStream_t s) {
+  if (!tc_shape_ok(d) || d.units > 65535) return cudaErrorInvalidValue;
+  static bool attr_set[2] = {false, false};
+  const int64_t M = int64_t(1) << d.nm, N = int64_t(1) << d.nn;
+  dim3 grid((unsigned)(M / TM), (unsigned)((N + TN - 1) / TN), (unsigned)d.units);
+  if (bf16) {
+    if (!attr_set[1]) {
+      cudaFuncSetAttribute(gemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+      attr_set[1] = true;
+    }
+    gemm_tc_kernel<true><<<grid, NTHREADS, SMEM_BYTES, s>>>(A, B, C, d, a_scale, b_scale, err);
+  } else {
+    if (!attr_set[0]) {
+      cudaFuncSetAttribute(gemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+      attr_set[0] = true;
+    }
+    gemm_tc_kernel<false><<<grid, NTHREADS, SMEM_BYTES, s>>>(A, B, C, d, a_scale, b_scale, err);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace tn

@@ -33,10 +33,10 @@ __global__ void __launch_bounds__(NT) vector_kernel(const float2* __restrict__ A
                                                     float2* __restrict__ C, const GemmDesc d) {
   constexpr int K = 1 << NK, N = 1 << NN;
   const int64_t M = int64_t(1) << d.nm;
-  const int64_t u = blockIdx.y;
-  A += u * d.a_unit;
-  B += u * d.b_unit;
-  C += u * d.c_unit;
+  const int64_t ulo = blockIdx.y % d.units_lo, uhi = blockIdx.y / d.units_lo;
+  A += ulo * d.a_lo + uhi * d.a_hi;
+  B += ulo * d.b_lo + uhi * d.b_hi;
+  C += ulo * d.c_lo + uhi * d.c_hi;
   __shared__ float2 Bs[K * N];
   __shared__ int32_t kA[K], nC[N];
   __shared__ int32_t tAlo[32], tAhi[32], tClo[32], tChi[32];

@@ -18,10 +18,15 @@ constexpr int kMaxBits = 32;
 // at sum_i bit_i(m) am[i] + sum_l bit_l(k) ak[l] (+ unit * a_unit), and
 // likewise for B (k, n) and C (m, n).  Bits are numbered so that bit 0 is the
 // operand's most contiguous index of that group.
+//
+// A launch covers `units` units; unit u splits into (u % units_lo, u / units_lo)
+// and each operand's base moves by (u % units_lo) * x_lo + (u / units_lo) * x_hi
+// elements, so an operand shared by some units (a slice-only tensor read by
+// every bitstring of the slice, or an invariant one) simply has a zero stride.
 struct GemmDesc {
   int nm, nn, nk;
-  int units;                 // grid extent over (bitstring, slice) units
-  int64_t a_unit, b_unit, c_unit;  // element stride between units (0 = shared operand)
+  int units, units_lo;
+  int64_t a_lo, a_hi, b_lo, b_hi, c_lo, c_hi;
   int32_t am[kMaxBits], cm[kMaxBits];
   int32_t bn[kMaxBits], cn[kMaxBits];
   int32_t ak[kMaxBits], bk[kMaxBits];
@@ -40,20 +45,32 @@ struct LeafGather {
   int32_t fixed_stride[kMaxLeafRank];
 };
 
+// A group of units: `nslice` consecutive slice ids from slice0 for the
+// bitstrings b0 .. b0+nb-1; unit u = (u % nslice) slice, (u / nslice) bitstring.
 struct GroupInfo {
-  int64_t unit0;             // first global unit of the group
-  int64_t slices;            // slices per bitstring in this call
-  int64_t slice_begin;
+  int64_t slice0;
+  int64_t b0;
+  int32_t nslice;
+  int32_t nb;                // 1 for slice-only launches
   int32_t words;             // uint64 words per bitstring
-  int32_t units;             // units in this group
+  int32_t units;             // nslice * nb
 };
 
 // launchers (return cudaGetLastError())
 cudaError_t launch_gemm_simt(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s);
+// tcgen05 fused permute-GEMM (complex64 in/out, 16-bit hi+lo split products,
+// FP32 accumulation).  Operands are multiplied by a_scale / b_scale before the
+// split and the result divided by their product (powers of two).  *err is set
+// non-zero when a bounded wait expired.
+bool tc_shape_ok(const GemmDesc& d);
+cudaError_t launch_gemm_tc(const float2* A, const float2* B, float2* C, const GemmDesc& d, bool bf16, float a_scale,
+                           float b_scale, int* err, cudaStream_t s);
 cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s);
 cudaError_t launch_gather(const float2* store, float2* arena, int64_t arena_stride, const LeafGather* descs,
                           int nleaves, const uint64_t* bits, const GroupInfo& g, cudaStream_t s);
-cudaError_t launch_accumulate(const float2* root, int64_t root_unit_stride, const int64_t* perm, int nperm,
+// acc[b, j] += sum over the group's slices (in slice order) of root(b, s)[perm[j]],
+// root(b, s) = root + s_local * r_lo + b_local * r_hi.
+cudaError_t launch_accumulate(const float2* root, int64_t r_lo, int64_t r_hi, const int64_t* perm, int nperm,
                               double2* acc, const GroupInfo& g, cudaStream_t s);
 // dst (dense, element e) = src[sum_p bit_p(e) * st[p]]: bit p of e is dst's
 // p-th fastest index, st[p] its element stride in src.

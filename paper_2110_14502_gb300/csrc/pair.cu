@@ -108,12 +108,17 @@ extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, in
   GemmDesc d;
   make_gemm_desc(la, lb, lc, d);
   d.units = 1;
-  d.a_unit = d.b_unit = d.c_unit = 0;
+  d.units_lo = 1;
+  d.a_lo = d.a_hi = d.b_lo = d.b_hi = d.c_lo = d.c_hi = 0;
   cudaStream_t s = (cudaStream_t)stream;
   const float2* a = (const float2*)A;
   const float2* b = (const float2*)B;
   float2* c = (float2*)Cv;
-  if (algo == TN_PAIR_AUTO) algo = (d.nn <= 4 && d.nk <= 4) ? TN_PAIR_VECTOR : TN_PAIR_FUSED_SIMT;
+  if (algo == TN_PAIR_AUTO) {
+    if (d.nn <= 4 && d.nk <= 4) algo = TN_PAIR_VECTOR;
+    else if (precision == TN_PREC_SPLIT_BF16 && tc_shape_ok(d)) algo = TN_PAIR_FUSED_TC;
+    else algo = TN_PAIR_FUSED_SIMT;
+  }
   cudaError_t e;
   switch (algo) {
     case TN_PAIR_FUSED_SIMT: e = launch_gemm_simt(a, b, c, d, s); break;
@@ -122,6 +127,27 @@ extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, in
       e = launch_vector(a, b, c, d, s);
       break;
     case TN_PAIR_UNFUSED: return unfused(a, b, c, d, s);
+    case TN_PAIR_FUSED_TC: {
+      if (precision != TN_PREC_SPLIT_BF16)
+        return fail(TN_EINVAL, "tn_contract_pair: the tensor-core kernel needs precision TN_PREC_SPLIT_BF16");
+      if (!tc_shape_ok(d)) return fail(TN_EINVAL, "tn_contract_pair: tensor-core kernel needs M >= 128, N >= 16, K >= 8");
+      static int* err = nullptr;
+      if (!err) {
+        if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return fail(TN_ECUDA, "tn_contract_pair: error word");
+        cudaMemset(err, 0, sizeof(int));
+      }
+      e = launch_gemm_tc(a, b, c, d, true, 1.f, 1.f, err, s);
+      if (e == cudaSuccess) {
+        int h = 0;
+        cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && h) {
+          cudaMemset(err, 0, sizeof(int));
+          return fail(TN_ETIMEOUT, "tn_contract_pair: a tensor-core pipeline wait expired (code %d)", h);
+        }
+      }
+      break;
+    }
     default: return fail(TN_EINVAL, "tn_contract_pair: algo %d not available for precision %d", algo, precision);
   }
   if (e != cudaSuccess) return fail(TN_ECUDA, "tn_contract_pair launch: %s", cudaGetErrorString(e));

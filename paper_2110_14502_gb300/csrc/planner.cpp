@@ -536,10 +536,11 @@ tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& P) {
   P.cmac_per_slice = best.cmac;
   P.max_width = best.width;
 
-  // ---- leaves: fixed indices and sub-labels
+  // ---- leaves: fixed indices and sub-labels; dependence (bit 0 closed, bit 1 sliced)
   std::vector<int> slice_bit(net.num_labels(), -1);
   for (size_t j = 0; j < P.sliced.size(); ++j) slice_bit[P.sliced[j]] = (int)j;
   P.leaf_use.assign(L, LeafUse());
+  std::vector<int> dep(L + best_pairs.size() / 2, 0);
   int64_t store = 0;
   for (int i = 0; i < L; ++i) {
     LeafUse& U = P.leaf_use[i];
@@ -547,18 +548,20 @@ tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& P) {
     U.store_off = store;
     store += int64_t(1) << lf.labels.size();
     for (int l : lf.labels) {
-      if (net.kind[l] == LK_CLOSED) { U.fixed_src.push_back(-2 - net.closed_qubit[l]); U.variant = true; }
-      else if (slice_bit[l] >= 0) { U.fixed_src.push_back(slice_bit[l]); U.variant = true; }
+      if (net.kind[l] == LK_CLOSED) { U.fixed_src.push_back(-2 - net.closed_qubit[l]); dep[i] |= 1; }
+      else if (slice_bit[l] >= 0) { U.fixed_src.push_back(slice_bit[l]); dep[i] |= 2; }
       else { U.fixed_src.push_back(-1); U.sub_labels.push_back(l); }
     }
+    U.variant = dep[i] != 0;
+    U.phase = dep[i] == 0 ? 0 : dep[i] == 2 ? 1 : 2;
   }
   P.leaf_store_elems = store;
 
-  // ---- steps
+  // ---- steps (tree order); phase 0 invariant, 1 slice-only, 2 per (bitstring, slice)
   std::vector<LSet> order(L);  // memory label order of each SSA id
-  std::vector<char> variant(L + best_pairs.size() / 2, 0);
-  for (int i = 0; i < L; ++i) { order[i] = P.leaf_use[i].sub_labels; variant[i] = P.leaf_use[i].variant; }
+  for (int i = 0; i < L; ++i) order[i] = P.leaf_use[i].sub_labels;
   P.steps.clear();
+  P.cmac_slice_only = 0;
   for (size_t p = 0; p < best_pairs.size(); p += 2) {
     int x = best_pairs[p], y = best_pairs[p + 1];
     Step S;
@@ -576,70 +579,74 @@ tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& P) {
     S.nm = (int)S.la.size() - S.nk;
     S.nn = (int)S.lb.size() - S.nk;
     S.klass = (S.nn <= 4 && S.nk <= 4) ? SC_VECTOR : SC_SIMT;
-    S.variant = variant[S.a] || variant[S.b];
-    variant[L + p / 2] = S.variant;
+    int d = dep[S.a] | dep[S.b];
+    dep[L + p / 2] = d;
+    S.variant = d != 0;
+    S.phase = d == 0 ? 0 : d == 2 ? 1 : 2;
+    if (S.phase == 1) P.cmac_slice_only += std::ldexp(1.0, S.nm + S.nn + S.nk);
     order.push_back(S.lc);
     P.steps.push_back(S);
   }
+  auto phase_of = [&](int id) { return id < L ? P.leaf_use[id].phase : P.steps[id - L].phase; };
 
-  // ---- memory: per-unit arena (variant leaves + variant outputs), invariant store
+  // ---- memory: invariant store (no reuse), slice arena and pair arena (first-fit with liveness)
   auto align = [](int64_t v) { return (v + 31) & ~int64_t(31); };
   struct Blk { int64_t off, size; };
-  std::vector<Blk> freel;
-  int64_t top = 0;
-  auto alloc = [&](int64_t sz) {
+  struct Arena {
+    std::vector<Blk> freel;
+    int64_t top = 0, peak = 0;
+  } ar[3];
+  auto alloc = [&](Arena& A, int64_t sz) {
     sz = align(sz);
-    for (size_t i = 0; i < freel.size(); ++i)
-      if (freel[i].size >= sz) {
-        int64_t o = freel[i].off;
-        freel[i].off += sz;
-        freel[i].size -= sz;
-        if (freel[i].size == 0) freel.erase(freel.begin() + i);
+    for (size_t i = 0; i < A.freel.size(); ++i)
+      if (A.freel[i].size >= sz) {
+        int64_t o = A.freel[i].off;
+        A.freel[i].off += sz;
+        A.freel[i].size -= sz;
+        if (A.freel[i].size == 0) A.freel.erase(A.freel.begin() + i);
         return o;
       }
-    int64_t o = top;
-    top += sz;
+    int64_t o = A.top;
+    A.top += sz;
+    A.peak = std::max(A.peak, A.top);
     return o;
   };
-  auto release = [&](int64_t off, int64_t sz) {
+  auto release = [&](Arena& A, int64_t off, int64_t sz) {
     sz = align(sz);
-    freel.push_back({off, sz});
-    std::sort(freel.begin(), freel.end(), [](const Blk& a, const Blk& b) { return a.off < b.off; });
+    A.freel.push_back({off, sz});
+    std::sort(A.freel.begin(), A.freel.end(), [](const Blk& a, const Blk& b) { return a.off < b.off; });
     std::vector<Blk> m;
-    for (auto& b : freel) {
+    for (auto& b : A.freel) {
       if (!m.empty() && m.back().off + m.back().size == b.off) m.back().size += b.size;
       else m.push_back(b);
     }
-    // give back a trailing block
-    if (!m.empty() && m.back().off + m.back().size == top) { top = m.back().off; m.pop_back(); }
-    freel.swap(m);
+    if (!m.empty() && m.back().off + m.back().size == A.top) { A.top = m.back().off; m.pop_back(); }
+    A.freel.swap(m);
   };
-  for (int i = 0; i < L; ++i)
-    if (P.leaf_use[i].variant) P.leaf_use[i].off = alloc(int64_t(1) << P.leaf_use[i].sub_labels.size());
-    else P.leaf_use[i].off = P.leaf_use[i].store_off;
-  int64_t peak = top;
-  int64_t inv = 0;
   std::vector<int64_t> ssa_off(L + P.steps.size(), 0);
-  for (int i = 0; i < L; ++i) ssa_off[i] = P.leaf_use[i].off;
-  for (size_t s = 0; s < P.steps.size(); ++s) {
-    Step& S = P.steps[s];
-    int64_t sz = int64_t(1) << S.lc.size();
-    if (S.variant) {
-      S.off_c = alloc(sz);
-      peak = std::max(peak, top);
-      for (int opnd : {S.a, S.b}) {
-        bool var = opnd < L ? P.leaf_use[opnd].variant : P.steps[opnd - L].variant;
-        int64_t osz = int64_t(1) << order[opnd].size();
-        if (var) release(ssa_off[opnd], osz);
-      }
-    } else {
-      S.off_c = inv;
-      inv += align(sz);
-    }
-    ssa_off[L + s] = S.off_c;
+  for (int i = 0; i < L; ++i) {
+    LeafUse& U = P.leaf_use[i];
+    U.off = U.phase == 0 ? U.store_off : alloc(ar[U.phase], int64_t(1) << U.sub_labels.size());
+    ssa_off[i] = U.off;
   }
-  P.unit_arena_elems = align(std::max<int64_t>(peak, 32));
-  P.invariant_elems = std::max<int64_t>(inv, 32);
+  // execution order: phase 0 steps, then phase 1, then phase 2 (each in tree order)
+  for (int ph = 0; ph < 3; ++ph) {
+    for (size_t s = 0; s < P.steps.size(); ++s) {
+      Step& S = P.steps[s];
+      if (S.phase != ph) continue;
+      int64_t sz = int64_t(1) << S.lc.size();
+      S.off_c = alloc(ar[ph], sz);
+      ssa_off[L + s] = S.off_c;
+      if (ph == 0) continue;  // invariant results stay
+      for (int opnd : {S.a, S.b}) {
+        // an operand lives in its own phase's memory; free it when consumed in that phase
+        if (phase_of(opnd) == ph) release(ar[ph], ssa_off[opnd], int64_t(1) << order[opnd].size());
+      }
+    }
+  }
+  P.invariant_elems = std::max<int64_t>(ar[0].peak, 32);
+  P.slice_arena_elems = align(std::max<int64_t>(ar[1].peak, 32));
+  P.unit_arena_elems = align(std::max<int64_t>(ar[2].peak, 32));
 
   // ---- root permutation: batch index j -> element offset of the root tensor
   const LSet& root = L == 1 ? P.leaf_use[0].sub_labels : P.steps.back().lc;
@@ -675,6 +682,7 @@ tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& P) {
     put32(b, S.a);
     put32(b, S.b);
     put32(b, S.klass);
+    put32(b, S.phase);
     put32(b, (int)S.lc.size());
     for (int l : S.lc) { put32(b, net.wire[l].first); put32(b, net.wire[l].second); }
   }
@@ -722,7 +730,7 @@ extern "C" tn_status tn_plan_get_info(const tn_plan_t* p, tn_plan_info* info) {
   info->cmac_per_slice = P.cmac_per_slice;
   info->flops_per_slice = 8.0 * P.cmac_per_slice;
   info->log2_cmac_total = std::log2(std::max(P.cmac_per_slice, 1.0)) + (double)P.sliced.size();
-  info->footprint_bytes_per_unit = P.unit_arena_elems * 8;
+  info->footprint_bytes_per_unit = (P.unit_arena_elems + P.slice_arena_elems) * 8;
   info->hash = P.hash;
   for (auto& S : P.steps) {
     if (S.klass == SC_VECTOR) info->num_vector_steps++;

@@ -62,11 +62,13 @@ struct Step {
   int nm = 0, nn = 0, nk = 0;   // log2 M, N, K
   int klass = SC_SIMT;
   bool variant = true;          // depends on the unit's fixed-index values
-  int64_t off_c = 0;            // element offset of the output (unit arena or invariant store)
+  int phase = 2;                // 0 invariant, 1 slice-only, 2 per (bitstring, slice)
+  int64_t off_c = 0;            // element offset of the output in its phase's memory
 };
 
 struct LeafUse {
   bool variant = false;
+  int phase = 0;                // 0 invariant (leaf store), 1 slice arena, 2 pair arena
   std::vector<int> sub_labels;  // labels after removing fixed ones
   // per full-label position: -1 kept, else source of the fixed value:
   //   src >= 0      : sliced index number j (bit j of the slice id)
@@ -85,11 +87,13 @@ struct Plan {
   std::vector<int> tree;        // 2*(L-1) SSA ids
   std::vector<Step> steps;
   std::vector<LeafUse> leaf_use;
-  int64_t unit_arena_elems = 0;   // per-unit arena (complex elements)
+  int64_t unit_arena_elems = 0;   // per-(bitstring, slice) arena (complex elements)
+  int64_t slice_arena_elems = 0;  // per-slice arena for slice-only tensors
   int64_t invariant_elems = 0;    // invariant intermediates store
   int64_t leaf_store_elems = 0;
   std::vector<int64_t> root_perm; // batch index j -> element offset in the root tensor
   double cmac_per_slice = 0;
+  double cmac_slice_only = 0;     // part of cmac_per_slice shared by every bitstring of a slice
   int max_width = 0;
   std::vector<uint8_t> bytes;     // serialized form
   uint64_t hash = 0;

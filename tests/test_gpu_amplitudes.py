@@ -128,3 +128,19 @@ def test_full_size_6x6_sampled_slices_vs_oracle():
         fixed = {wires[j]: (s >> j) & 1 for j in range(len(wires))}
         ref = replay(p, gates, n, bits, open_q, fixed)
         assert rel(got, ref) <= 1e-5, s
+
+
+def test_split_bf16_path_vs_statevector():
+    """A plan whose dense steps run on the tcgen05 kernel (bf16 hi+lo):
+    relative L2 <= 1e-4 against the state vector."""
+    T = tnlib()
+    rows, cols, depth, seed, open_q = 4, 5, 14, 12, (14, 15, 16, 17, 18, 19)
+    n = rows * cols
+    p = _setup(T, rows, cols, depth, seed, open_q, num_sliced=2, search_trials=32, seed=3)
+    words = I.bitstrings(n, 3, seed)
+    got, rep = p.contract_amplitudes(words, precision="split_bf16", report=True, profile=True)
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    ref = SV.amplitudes(SV.simulate(gates, n), n, [I.bits_of(w, n) for w in words], open_q)
+    assert rel(got, ref) <= 1e-4
+    c64 = p.contract_amplitudes(words, precision="c64")
+    assert rel(c64, ref) <= 1e-5
