@@ -1,0 +1,377 @@
+"""Benchmark of the amplitude hot path (one JSON line on rank 0).
+
+Workload (default): a 6x6 grid random circuit of depth 1+16+1 (circuit seed
+2), its network sliced on 10 bond indices (1024 slices), the last six qubits
+open, four bitstring batches of 64 amplitudes (256 amplitudes).  One "step"
+contracts every slice of every batch and sums them in FP64: the whole hot
+path (slice selection, the pairwise permute-GEMM chain, the cross-slice sum).
+
+`value` is counted complex-flop throughput (8 real flops per complex
+multiply-add of the work actually performed, work shared by the batches
+counted once) with inputs resident in HBM; `amplitudes_per_s` beside it.
+`e2e` repeats the step through the C ABI with host buffers (bitstrings in,
+amplitudes out, copies inside the timed region).  `roofline` describes the
+dominant kernel class from per-launch CUDA events during the timed steps;
+`cpu_baseline` times the FP64 CPU oracle on one slice of one batch.
+
+Modes:
+  python bench.py [--gpus N --steps K --warmup W] [--precision split_bf16|c64]
+  python bench.py --impl reference ...   # the CPU oracle as the reference arm
+  python bench.py --micro [--shape m,n,k]  # pairwise contraction microbenchmark
+Under torchrun each rank runs its own batches (weak scaling, no collective on
+the data path); rank 0 prints the max-over-ranks timing.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ROWS, COLS, DEPTH, CSEED = 6, 6, 16, 2
+NSLICED = 10
+NOPEN = 6
+NBATCH, BSEED = 4, 2
+PLAN_TRIALS, PLAN_SEED = 64, 1
+METRIC = "Contraction TFLOP/s & amplitudes/s at stated rel err vs FP64; p50/p99 latency"
+WORKLOAD = "6x6 grid, depth 1+16+1, fSim(pi/2,pi/6); 10 sliced indices (1024 slices); 6 open qubits; 4 batches x 64 amplitudes"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), \
+            d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 1900.0, 1700.0, 2070.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                f = [x.strip() for x in out.stdout.strip().split(",")]
+                if len(f) == 7:
+                    self.samples.append(f)
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if "Active" in s[3 + i]
+                          and "Not" not in s[3 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def make_workload(T, rank):
+    c = T.random_circuit(ROWS, COLS, DEPTH, CSEED)
+    n = ROWS * COLS
+    open_q = list(range(n - NOPEN, n))
+    net = T.build_network(c, open_q)
+    t0 = time.time()
+    p = T.plan(net, num_sliced=NSLICED, search_trials=PLAN_TRIALS, seed=PLAN_SEED)
+    plan_s = time.time() - t0
+    import tn_inputs as I
+    words = I.bitstrings(n, NBATCH, BSEED + 1000 * rank)
+    return c, net, p, words, open_q, plan_s
+
+
+def cpu_oracle_sample(p, words, open_q, slice_id=0):
+    """FP64 oracle on one slice of one bitstring batch; returns (value, seconds, cmac)."""
+    import tn_inputs as I
+    from oracle import circuit as OC
+    from oracle.replay import contract_in_order, work_cmac
+    n = ROWS * COLS
+    gates = OC.random_circuit(ROWS, COLS, DEPTH, CSEED)
+    bits = I.bits_of(words[0], n)
+    wires = p.sliced_wires()
+    fixed = {wires[j]: (slice_id >> j) & 1 for j in range(len(wires))}
+    leaves, pairs = p.tree(len(gates), n)
+    t0 = time.time()
+    v = contract_in_order(gates, n, bits, open_q, leaves, pairs, fixed)
+    dt = time.time() - t0
+    cmac = work_cmac(gates, n, bits, open_q, leaves, pairs, fixed)
+    return v, dt, cmac
+
+
+def traffic_record(kernel_file):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
+    the current source of the kernel (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    src = os.path.join(ROOT, "paper_2110_14502_gb300", "csrc", kernel_file)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    r = rec.get(kernel_file)
+    if not r or r.get("source_sha") != h:
+        return None
+    return r
+
+
+def run_ours(args):
+    import torch
+    import paper_2110_14502_gb300 as T
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    c, net, p, words, open_q, plan_s = make_workload(T, rank)
+    info = p.info()
+    k = info["num_open"]
+    nout = NBATCH << k
+    stream = torch.cuda.Stream()
+    dwords = torch.from_numpy(words.astype(np.int64)).cuda()
+    out = torch.empty(nout * 2, dtype=torch.float64, device="cuda")
+
+    def step(profile=False):
+        with torch.cuda.stream(stream):
+            _, rep = p.contract_amplitudes(dwords, out=out, stream=stream, precision=args.precision,
+                                           profile=profile, report=True)
+        return rep
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    reps, times = [], []
+    with Clocks(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            r = step(profile=True)
+            reps.append(r)
+            times.append(r["device_ms"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+    total_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    flops = sum(r["flops"] for r in reps) * world
+    flops_eq = sum(r["flops_equivalent"] for r in reps) * world
+    amps = nout * args.steps * world
+    value = flops / (total_ms * 1e-3) / 1e12
+    launches = int(sum(r["kernel_launches"] for r in reps) / len(reps))
+
+    # roofline of the dominant kernel class over the timed steps
+    hbm, bf16, bf16_sus, sm_max, src = peaks()
+    cls_ms = [sum(r["class_ms"][i] for r in reps) for i in range(4)]
+    cls_fl = [sum(r["class_flops"][i] for r in reps) for i in range(4)]
+    cls_by = [sum(r["class_bytes"][i] for r in reps) for i in range(4)]
+    cls_n = [sum(r["class_launches"][i] for r in reps) for i in range(4)]
+    dom = int(np.argmax(cls_ms))
+    kernel_file = {0: "k_simt.cu", 1: "k_vector.cu", 2: "k_tc.cu"}[dom]
+    tr = traffic_record(kernel_file)
+    if dom == 2:
+        achieved = cls_fl[dom] / (cls_ms[dom] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": round(achieved, 2), "peak": bf16_sus, "unit": "TFLOP/s",
+                "frac": round(achieved / bf16_sus, 4), "peak_kind": f"bf16 dense sustained ({src})",
+                "issued_mma_tflops": round(3 * achieved, 2),
+                "issued_frac": round(3 * achieved / bf16_sus, 4)}
+    elif dom == 1:
+        achieved = cls_by[dom] / (cls_ms[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "peak_kind": f"HBM copy ({src})"}
+    else:
+        achieved = cls_fl[dom] / (cls_ms[dom] * 1e-3) / 1e12
+        fp32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(fp32, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / fp32, 4), "peak_kind": "FP32 FFMA: 152 SMs x 128 lanes x 2 x max clock"}
+    roof["kernel"] = {0: "gemm_simt_kernel", 1: "vector_kernel", 2: "gemm_tc_kernel"}[dom]
+    roof["launches_per_step"] = cls_n[dom] / args.steps
+    roof["share_of_device_time"] = round(cls_ms[dom] / sum(cls_ms), 4) if sum(cls_ms) else None
+    roof["traffic"] = None if tr is None else tr["bytes_per_launch"]
+    roof["traffic_note"] = None if tr is None else tr["note"]
+
+    # e2e: host buffers through the C ABI, copies inside the timed region
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.time()
+        p.contract_amplitudes(words, precision=args.precision)
+        e2e_times.append(time.time() - t0)
+    e2e_s = sum(e2e_times)
+    e2e_flops = reps[0]["flops"] * len(e2e_times)
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3" if args.precision == "split_bf16" else "f32",
+        "data": "synthetic (seeded random circuit and bitstrings)",
+        "config": {"workload": WORKLOAD, "precision": args.precision, "global_batch": amps // args.steps,
+                   "slices": info["num_slices"], "plan_hash": hex(info["hash"]),
+                   "cmac_per_slice_log2": round(float(np.log2(info["cmac_per_slice"])), 3),
+                   "max_log2_intermediate": info["max_log2_intermediate"],
+                   "l2": "working set (>= 2^26-element intermediates per slice) larger than L2; no flush",
+                   "parallelism": f"slices x bitstrings per GPU; {world} independent replica(s)"},
+        "amplitudes_per_s": round(amps / (total_ms * 1e-3), 3),
+        "flops_equivalent_tflops": round(flops_eq / (total_ms * 1e-3) / 1e12, 3),
+        "p50_ms": round(float(np.percentile(times, 50)), 3), "p99_ms": round(float(np.percentile(times, 99)), 3),
+        "plan_s": round(plan_s, 3),
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clk.summary(),
+        "e2e": {"value": round(e2e_flops / e2e_s / 1e12, 3), "unit": "TFLOP/s",
+                "amplitudes_per_s": round(nout * len(e2e_times) / e2e_s, 3),
+                "h2d_bytes_per_step": int(words.nbytes), "d2h_bytes_per_step": int(nout * 16)},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, dt, cmac = cpu_oracle_sample(p, words, open_q, slice_id=0)
+        gpu1 = p.contract_amplitudes(words[:1], precision=args.precision, slice_begin=0, slice_count=1)[0]
+        line["cpu_baseline"] = {"value": round(8 * cmac / dt / 1e12, 6), "unit": "TFLOP/s",
+                                "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": "slice 0 of batch 0 (64 amplitudes, 1/1024 of the slices), FP64 NumPy "
+                                          f"contraction in the plan's order, {dt:.1f} s"}
+        line["rel_err_vs_fp64_sample"] = float(np.linalg.norm(gpu1 - v) / np.linalg.norm(v))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import paper_2110_14502_gb300 as T  # host planner only: supplies the schedule the oracle follows
+    c, net, p, words, open_q, plan_s = make_workload(T, 0)
+    info = p.info()
+    for _ in range(args.warmup):
+        cpu_oracle_sample(p, words, open_q, 0)
+    tot, fl, times = 0.0, 0.0, []
+    for s in range(args.steps):
+        _, dt, cmac = cpu_oracle_sample(p, words, open_q, slice_id=s)
+        tot += dt
+        fl += 8 * cmac
+        times.append(dt * 1e3)
+    value = fl / tot / 1e12
+    amps_s = 64.0 / info["num_slices"] * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "TFLOP/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot * 1e3 / args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded random circuit and bitstrings)",
+            "config": {"workload": WORKLOAD, "precision": "fp64 oracle", "sample_per_step": "one slice of one batch"},
+            "amplitudes_per_s": amps_s,
+            "p50_ms": round(float(np.percentile(times, 50)), 1), "p99_ms": round(float(np.percentile(times, 99)), 1),
+            "cpu_baseline": {"value": round(value, 6), "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "per step: one slice of one 64-amplitude batch, FP64 NumPy"},
+            "e2e": {"value": round(value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_micro(args):
+    """Pairwise contraction microbenchmark: fused kernels vs permute + cuBLAS."""
+    import torch
+    import paper_2110_14502_gb300 as T
+    import tn_inputs as I
+    shapes = [tuple(int(x) for x in args.shape.split(","))] if args.shape else \
+        [(14, 12, 10), (12, 12, 12), (13, 13, 13), (19, 11, 11), (17, 13, 9), (26, 2, 2)]
+    res = []
+    for nm, nn, nk in shapes:
+        rng = np.random.default_rng(3)
+        labels = list(range(nm + nn + nk))
+        M, N, K = labels[:nm], labels[nm:nm + nn], labels[nm + nn:]
+        # planner-style layouts: contracted indices innermost, in one shared order
+        perm_k = [int(x) for x in rng.permutation(K)]
+        la = [int(x) for x in rng.permutation(M)] + perm_k
+        lb = [int(x) for x in rng.permutation(N)] + perm_k
+        lc = [int(x) for x in rng.permutation(M + N)]
+        if args.random_layout:
+            la = [int(x) for x in rng.permutation(M + K)]
+            lb = [int(x) for x in rng.permutation(K + N)]
+        A = torch.from_numpy(I.random_tensor(len(la), 31, np.complex64)).cuda()
+        B = torch.from_numpy(I.random_tensor(len(lb), 32, np.complex64)).cuda()
+        Cc = torch.empty(1 << len(lc), dtype=torch.complex64, device="cuda")
+        flops = 8.0 * 2.0 ** (nm + nn + nk)
+        row = {"shape": [nm, nn, nk]}
+        algos = ["vector"] if (nn <= 4 and nk <= 4) else ["fused_tc", "fused_simt", "unfused"]
+        for algo in algos:
+            prec = "split_bf16" if algo == "fused_tc" else "c64"
+            for _ in range(args.warmup):
+                T.contract_pair(A, la, B, lb, Cc, lc, precision=prec, algo=algo)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                T.contract_pair(A, la, B, lb, Cc, lc, precision=prec, algo=algo)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            row[algo] = {"ms": round(ms, 4), "tflops": round(flops / ms / 1e9, 2),
+                         "gbs": round(8.0 * (2 ** len(la) + 2 ** len(lb) + 2 ** len(lc)) / ms / 1e6, 1)}
+        res.append(row)
+        print(json.dumps(row), flush=True)
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "c64"])
+    ap.add_argument("--micro", action="store_true")
+    ap.add_argument("--shape", default=None)
+    ap.add_argument("--random-layout", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    elif args.micro:
+        run_micro(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

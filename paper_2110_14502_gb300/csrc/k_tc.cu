@@ -33,15 +33,21 @@ namespace tn {
 namespace {
 
 constexpr int TM = 128;          // complex rows per tile (= MMA M)
-constexpr int TN = 64;           // complex columns per tile (MMA N = 128 reals)
 constexpr int TK = 32;           // complex K per stage (64 reals = one 128-byte swizzle row)
-constexpr int NSTAGE = 3;
 constexpr int NTHREADS = 256;
-constexpr int TILE_BYTES = 128 * 128;               // 128 rows x 128 bytes
-constexpr int STAGE_BYTES = 4 * TILE_BYTES;         // A hi, A lo, B' hi, B' lo
-constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024;  // + alignment slack
-constexpr uint32_t TMEM_COLS = 128;
+constexpr int A_TILE = 128 * 128;                   // 128 rows x 128 bytes
 constexpr long long kWaitLimit = 1ll << 24;
+
+// Tile configuration by complex column count TN (MMA N = 2 TN reals).
+template <int TN>
+struct Cfg {
+  static constexpr int B_TILE = 2 * TN * 128;                 // 2 TN rows x 128 bytes
+  static constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;       // A hi, A lo, B' hi, B' lo
+  static constexpr int NSTAGE = TN == 64 ? 3 : 2;
+  static constexpr int SMEM = NSTAGE * STAGE + 1024;          // + alignment slack
+  static constexpr uint32_t TMEM_COLS = 2 * TN;
+  static constexpr int BCH = TN * 8 / NTHREADS;               // B chunks per thread
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -133,17 +139,22 @@ struct Half16<false> {
 
 __device__ __forceinline__ uint32_t pack2(uint16_t a, uint16_t b) { return (uint32_t)a | ((uint32_t)b << 16); }
 
-// Register staging of one K stage: each thread owns 4 A-chunks and 2 B-chunks,
-// a chunk being 4 consecutive complex K values of one row (A) or column (B).
+// Register staging of one K stage: each thread owns 4 A-chunks and BCH
+// B-chunks, a chunk being 4 consecutive complex K values of one row (A) or
+// column (B).
+template <int BCH>
 struct Stage {
   float2 a[4][4];
-  float2 b[2][4];
+  float2 b[BCH][4];
 };
 
-template <bool BF16>
+template <bool BF16, int TN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_tc_kernel(const float2* __restrict__ A, const float2* __restrict__ B, float2* __restrict__ C,
                    const GemmDesc d, float a_scale, float b_scale, int* __restrict__ err) {
+  using CF = Cfg<TN>;
+  constexpr int NSTAGE = CF::NSTAGE, STAGE_BYTES = CF::STAGE, BCH = CF::BCH;
+  constexpr uint32_t TMEM_COLS = CF::TMEM_COLS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ uint64_t bar_mma[NSTAGE];
@@ -171,6 +182,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     colB[tid - TM] = n < N ? bit_offset(n, d.nn, d.bn) : -1;
     colC[tid - TM] = n < N ? bit_offset(n, d.nn, d.cn) : -1;
   }
+  static_assert(TM + TN <= NTHREADS, "offset threads");
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; ++s) mbar_init(&bar_mma[s], 1);
     mbar_init(&bar_done, 1);
@@ -179,7 +191,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_slot)),
-                 "r"(TMEM_COLS));
+                 "r"(TMEM_COLS));  // 128 or 256 columns: a power of two >= 32
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   const int nkt = (int)((K + TK - 1) / TK);
@@ -203,44 +215,55 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   // row; otherwise to consecutive rows (coalesced along M / N).
   const bool a_kfast = d.nk > 0 && d.ak[0] == 1;
   const bool b_kfast = d.nk > 0 && d.bk[0] == 1;
+  // 4 consecutive K values contiguous in memory: one chunk = two 16-byte loads
+  const bool a_vec = d.nk >= 2 && d.ak[0] == 1 && d.ak[1] == 2;
+  const bool b_vec = d.nk >= 2 && d.bk[0] == 1 && d.bk[1] == 2;
   auto a_task = [&](int i, int& r, int& c) {
     int e = tid + i * NTHREADS;
     if (a_kfast) { r = e >> 3; c = e & 7; } else { r = e & 127; c = e >> 7; }
   };
-  auto b_task = [&](int i, int& r, int& c) {  // B: 64 columns x 8 chunks = 512, 2 per thread
+  auto b_task = [&](int i, int& r, int& c) {  // B: TN columns x 8 chunks, BCH per thread
     int e = tid + i * NTHREADS;
-    if (b_kfast) { r = e >> 3; c = e & 7; } else { r = e & 63; c = e >> 6; }
+    if (b_kfast) { r = e >> 3; c = e & 7; } else { r = e % TN; c = e / TN; }
   };
-  auto load_stage = [&](Stage& st, int buf) {
+  auto load4 = [&](const float2* base, int32_t ro, const int32_t* ko, bool vec, float2* out) {
+    if (vec) {
+      // a chunk of 4 K values is either fully inside K or fully outside (K >= 4)
+      if (ro >= 0 && ko[0] >= 0) {
+        const float4* p = reinterpret_cast<const float4*>(base + (int64_t)ro + ko[0]);
+        float4 x = __ldg(p), y = __ldg(p + 1);
+        out[0] = make_float2(x.x, x.y); out[1] = make_float2(x.z, x.w);
+        out[2] = make_float2(y.x, y.y); out[3] = make_float2(y.z, y.w);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out[j] = make_float2(0.f, 0.f);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        out[j] = (ro >= 0 && ko[j] >= 0) ? __ldg(base + (int64_t)ro + ko[j]) : make_float2(0.f, 0.f);
+    }
+  };
+  auto load_stage = [&](Stage<BCH>& st, int buf) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       int r, c;
       a_task(i, r, c);
-      const int32_t ro = rowA[r];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int32_t ko = kA[buf][c * 4 + j];
-        st.a[i][j] = (ro >= 0 && ko >= 0) ? __ldg(A + (int64_t)ro + ko) : make_float2(0.f, 0.f);
-      }
+      load4(A, rowA[r], &kA[buf][c * 4], a_vec, st.a[i]);
     }
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < BCH; ++i) {
       int r, c;
       b_task(i, r, c);
-      const int32_t co = colB[r];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int32_t ko = kB[buf][c * 4 + j];
-        st.b[i][j] = (co >= 0 && ko >= 0) ? __ldg(B + (int64_t)co + ko) : make_float2(0.f, 0.f);
-      }
+      load4(B, colB[r], &kB[buf][c * 4], b_vec, st.b[i]);
     }
   };
-  auto store_stage = [&](const Stage& st, int s) {
+  auto store_stage = [&](const Stage<BCH>& st, int s) {
     uint8_t* base = smem + s * STAGE_BYTES;
     uint8_t* ahi = base;
-    uint8_t* alo = base + TILE_BYTES;
-    uint8_t* bhi = base + 2 * TILE_BYTES;
-    uint8_t* blo = base + 3 * TILE_BYTES;
+    uint8_t* alo = base + A_TILE;
+    uint8_t* bhi = base + 2 * A_TILE;
+    uint8_t* blo = base + 2 * A_TILE + CF::B_TILE;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       int r, c;
@@ -256,7 +279,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       *(uint4*)(alo + o) = make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]), pack2(l[6], l[7]));
     }
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < BCH; ++i) {
       int r, c;
       b_task(i, r, c);
       // row 2r:   [Br, -Bi] per k;  row 2r+1: [Bi, Br] per k
@@ -278,8 +301,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   };
 
-  constexpr uint32_t IDESC = idesc_f16(BF16, 128, 128);
-  Stage st;
+  constexpr uint32_t IDESC = idesc_f16(BF16, 128, 2 * TN);
+  Stage<BCH> st;
   load_stage(st, 0);
   for (int kt = 0; kt < nkt; ++kt) {
     const int s = kt % NSTAGE;
@@ -301,9 +324,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
         const uint64_t ahi = sw128_desc(base + kk * 32);
-        const uint64_t alo = sw128_desc(base + TILE_BYTES + kk * 32);
-        const uint64_t bhi = sw128_desc(base + 2 * TILE_BYTES + kk * 32);
-        const uint64_t blo = sw128_desc(base + 3 * TILE_BYTES + kk * 32);
+        const uint64_t alo = sw128_desc(base + A_TILE + kk * 32);
+        const uint64_t bhi = sw128_desc(base + 2 * A_TILE + kk * 32);
+        const uint64_t blo = sw128_desc(base + 2 * A_TILE + CF::B_TILE + kk * 32);
         const uint32_t first = (kt == 0 && kk == 0) ? 0u : 1u;
         mma_f16(tmem, ahi, bhi, IDESC, first);
         mma_f16(tmem, ahi, blo, IDESC, 1u);
@@ -329,14 +352,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!abort_flag) {
-    // epilogue: warp w reads lanes 32*(w%4).. of TMEM; warps 0-3 take columns
-    // 0-63 (complex 0-31), warps 4-7 columns 64-127 (complex 32-63).
+    // epilogue: warp w reads lanes 32*(w%4).. of TMEM; warps 0-3 take the
+    // first half of the 2*TN columns, warps 4-7 the second half.
     const int q = warp & 3, half = warp >> 2;
     const int r = q * 32 + lane;
     const float inv = 1.0f / (a_scale * b_scale);
 #pragma unroll
-    for (int cc = 0; cc < 2; ++cc) {
-      const int col = half * 64 + cc * 32;
+    for (int cc = 0; cc < TN / 32; ++cc) {
+      const int col = half * TN + cc * 32;
       uint32_t v[32];
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col;
       asm volatile(
@@ -368,26 +391,30 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 bool tc_shape_ok(const GemmDesc& d) { return d.nm >= 7 && d.nn >= 4 && d.nk >= 3; }
 
+template <bool BF16, int TN>
+static cudaError_t launch_cfg(const float2* A, const float2* B, float2* C, const GemmDesc& d, float as, float bs,
+                              int* err, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<BF16, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg<TN>::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int64_t M = int64_t(1) << d.nm, N = int64_t(1) << d.nn;
+  dim3 grid((unsigned)(M / TM), (unsigned)((N + TN - 1) / TN), (unsigned)d.units);
+  gemm_tc_kernel<BF16, TN><<<grid, NTHREADS, Cfg<TN>::SMEM, s>>>(A, B, C, d, as, bs, err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gemm_tc(const float2* A, const float2* B, float2* C, const GemmDesc& d, bool bf16, float a_scale,
                            float b_scale, int* err, cudaStream_t s) {
   if (!tc_shape_ok(d) || d.units > 65535) return cudaErrorInvalidValue;
-  static bool attr_set[2] = {false, false};
-  const int64_t M = int64_t(1) << d.nm, N = int64_t(1) << d.nn;
-  dim3 grid((unsigned)(M / TM), (unsigned)((N + TN - 1) / TN), (unsigned)d.units);
-  if (bf16) {
-    if (!attr_set[1]) {
-      cudaFuncSetAttribute(gemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-      attr_set[1] = true;
-    }
-    gemm_tc_kernel<true><<<grid, NTHREADS, SMEM_BYTES, s>>>(A, B, C, d, a_scale, b_scale, err);
-  } else {
-    if (!attr_set[0]) {
-      cudaFuncSetAttribute(gemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-      attr_set[0] = true;
-    }
-    gemm_tc_kernel<false><<<grid, NTHREADS, SMEM_BYTES, s>>>(A, B, C, d, a_scale, b_scale, err);
-  }
-  return cudaGetLastError();
+  const bool wide = d.nn >= 7;  // N >= 128 complex columns
+  if (bf16) return wide ? launch_cfg<true, 128>(A, B, C, d, a_scale, b_scale, err, s)
+                        : launch_cfg<true, 64>(A, B, C, d, a_scale, b_scale, err, s);
+  return wide ? launch_cfg<false, 128>(A, B, C, d, a_scale, b_scale, err, s)
+              : launch_cfg<false, 64>(A, B, C, d, a_scale, b_scale, err, s);
 }
 
 }  // namespace tn

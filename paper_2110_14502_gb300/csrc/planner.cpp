@@ -546,7 +546,7 @@ tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& P) {
     LeafUse& U = P.leaf_use[i];
     const Leaf& lf = net.leaves[i];
     U.store_off = store;
-    store += int64_t(1) << lf.labels.size();
+    store += ((int64_t(1) << lf.labels.size()) + 31) & ~int64_t(31);  // 256-byte aligned leaves
     for (int l : lf.labels) {
       if (net.kind[l] == LK_CLOSED) { U.fixed_src.push_back(-2 - net.closed_qubit[l]); dep[i] |= 1; }
       else if (slice_bit[l] >= 0) { U.fixed_src.push_back(slice_bit[l]); dep[i] |= 2; }
@@ -588,6 +588,36 @@ tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& P) {
     P.steps.push_back(S);
   }
   auto phase_of = [&](int id) { return id < L ? P.leaf_use[id].phase : P.steps[id - L].phase; };
+
+  // ---- output layouts, decided from the root down: every intermediate is
+  // written with the indices its consumer contracts innermost (in one order
+  // shared by both operands of the consumer), so the consumer's GEMM reads
+  // contiguous K runs from both operands -- the permutation of the next step
+  // is folded into this step's epilogue.
+  {
+    for (int t = (int)P.steps.size() - 1; t >= 0; --t) {
+      Step& S = P.steps[t];
+      LSet kt;  // contracted labels, ordered like the leaf operand if there is one
+      const int leaf_op = S.a < L ? S.a : (S.b < L ? S.b : -1);
+      const LSet& ref = leaf_op >= 0 ? order[leaf_op] : order[S.a];
+      const LSet& other = leaf_op >= 0 ? (leaf_op == S.a ? order[S.b] : order[S.a]) : order[S.b];
+      for (int l : ref)
+        if (std::find(other.begin(), other.end(), l) != other.end()) kt.push_back(l);
+      for (int x : {S.a, S.b}) {
+        if (x < L) continue;
+        LSet nl;
+        for (int l : order[x])
+          if (std::find(kt.begin(), kt.end(), l) == kt.end()) nl.push_back(l);
+        nl.insert(nl.end(), kt.begin(), kt.end());
+        order[x] = nl;
+        P.steps[x - L].lc = nl;
+      }
+    }
+    for (auto& S : P.steps) {
+      S.la = order[S.a];
+      S.lb = order[S.b];
+    }
+  }
 
   // ---- memory: invariant store (no reuse), slice arena and pair arena (first-fit with liveness)
   auto align = [](int64_t v) { return (v + 31) & ~int64_t(31); };

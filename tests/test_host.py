@@ -78,37 +78,10 @@ def test_plan_width_cap_and_errors():
 
 def _oracle_replay(T, rows, cols, depth, cseed, open_q, bits, **kw):
     """Contract the oracle's own network in the library plan's tree order."""
+    from _replay import replay
     c, net, p = _plan(T, rows, cols, depth, cseed, open_q, **kw)
-    n = rows * cols
     gates = OC.random_circuit(rows, cols, depth, cseed)
-    onet = OTN.circuit_network(gates, n, bits, open_q)
-    ng = len(gates)
-    leaves, pairs = p.tree(ng, n)
-    # oracle tensor order: n input vectors, then gates, then projectors of closed qubits
-    groups = []
-    last_raw = {q: ng + q for q in range(n)}
-    for gi, g in enumerate(gates):
-        for q in g.qubits:
-            last_raw[q] = gi
-    raw_to_oracle = lambda r: r + n if r < ng else r - ng
-    closed = [q for q in range(n) if q not in open_q]
-    proj_index = {q: n + ng + i for i, q in enumerate(closed)}
-    for raws in leaves:
-        grp = [raw_to_oracle(r) for r in raws]
-        for q in closed:
-            if last_raw[q] in raws:
-                grp.append(proj_index[q])
-        groups.append(grp)
-    assert sorted(x for g in groups for x in g) == list(range(len(onet.tensors)))
-    tens, labs = [], []
-    for grp in groups:
-        sub_t = [onet.tensors[i] for i in grp]
-        sub_l = [onet.labels[i] for i in grp]
-        t, l = OTN.contract_tree(sub_t, sub_l, OTN.greedy_order(sub_l)) if len(grp) > 1 else (sub_t[0], sub_l[0])
-        tens.append(t)
-        labs.append(l)
-    T_, l_ = OTN.contract_tree(tens, labs, pairs) if len(pairs) else (tens[0], labs[0])
-    return OTN.output_vector(T_, l_, onet.open_labels), gates, p
+    return replay(p, gates, rows * cols, bits, open_q), gates, p
 
 
 @pytest.mark.parametrize("rows,cols,depth,seed,open_q", [(3, 3, 6, 1, ()), (3, 4, 8, 2, (10, 11)), (4, 4, 8, 3, (0, 15, 7))])
