@@ -333,9 +333,9 @@ def run_micro(args):
         Cc = torch.empty(1 << len(lc), dtype=torch.complex64, device="cuda")
         flops = 8.0 * 2.0 ** (nm + nn + nk)
         row = {"shape": [nm, nn, nk]}
-        algos = ["vector"] if (nn <= 4 and nk <= 4) else ["fused_tc", "fused_simt", "unfused"]
+        algos = ["vector"] if (nn <= 4 and nk <= 4) else ["fused_tc", "gather_tc", "fused_simt", "unfused"]
         for algo in algos:
-            prec = "split_bf16" if algo == "fused_tc" else "c64"
+            prec = "split_bf16" if algo in ("fused_tc", "gather_tc") else "c64"
             for _ in range(args.warmup):
                 T.contract_pair(A, la, B, lb, Cc, lc, precision=prec, algo=algo)
             torch.cuda.synchronize()

@@ -240,8 +240,9 @@ enum {
   TN_PAIR_AUTO = 0,      /* the executor's kernel choice for this shape */
   TN_PAIR_FUSED_SIMT = 1,/* fused permute-GEMM, FP32 FFMA */
   TN_PAIR_VECTOR = 2,    /* bandwidth kernel (small N*K) */
-  TN_PAIR_FUSED_TC = 3,  /* fused permute-GEMM on tcgen05 (split or scaled precision) */
-  TN_PAIR_UNFUSED = 4    /* permute A and B to GEMM order, GEMM, permute C (library-allocated scratch) */
+  TN_PAIR_FUSED_TC = 3,  /* tcgen05 GEMM fed by TMA from split operand planes (library-allocated scratch) */
+  TN_PAIR_UNFUSED = 4,   /* permute A and B to GEMM order, GEMM, permute C (library-allocated scratch) */
+  TN_PAIR_GATHER_TC = 5  /* tcgen05 GEMM gathering and splitting operand tiles in the main loop (no scratch) */
 };
 
 /* C[c_labels] = sum over labels shared by A and B of A[a_labels] * B[b_labels].

@@ -42,6 +42,8 @@ struct Executor {
   double2* acc = nullptr;
   int64_t acc_cap = 0;
   int* err = nullptr;          // device error word of bounded waits
+  uint16_t* scratch = nullptr; // split operand planes of the tensor-core steps
+  int64_t scratch_cap = 0;     // in 16-bit elements
   std::vector<GemmDesc> desc;  // per step, unit strides filled at launch
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> pev;  // profiling event pool
@@ -61,6 +63,7 @@ void destroy_executor(Executor* e) {
   cudaFree(e->bits);
   cudaFree(e->acc);
   cudaFree(e->err);
+  cudaFree(e->scratch);
   if (e->ev0) cudaEventDestroy(e->ev0);
   if (e->ev1) cudaEventDestroy(e->ev1);
   for (auto ev : e->pev) cudaEventDestroy(ev);
@@ -224,7 +227,20 @@ tn_status run_step(Ctx& c, size_t s, const Geo& g) {
   const bool split = c.precision == TN_PREC_SPLIT_BF16;
   if (S.klass != SC_VECTOR && split && tc_shape_ok(d)) klass = TN_KCLASS_GEMM_TC;
   if (klass == TN_KCLASS_VECTOR) e = launch_vector(A, B, C, d, c.st);
-  else if (klass == TN_KCLASS_GEMM_TC) e = launch_gemm_tc(A, B, C, d, true, 1.f, 1.f, E.err, c.st);
+  else if (klass == TN_KCLASS_GEMM_TC) {
+    const int64_t need = tc2_scratch_elems(d);
+    if (need > E.scratch_cap) {
+      cudaFree(E.scratch);
+      E.scratch = nullptr;
+      E.scratch_cap = 0;
+      if (cudaMalloc(&E.scratch, (size_t)need * sizeof(uint16_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TN_EHBM, "step %zu: %lld bytes of operand planes do not fit", s, (long long)(need * 2));
+      }
+      E.scratch_cap = need;
+    }
+    e = run_gemm_tc2(A, B, C, d, true, E.scratch, E.err, c.st);
+  }
   else e = launch_gemm_simt(A, B, C, d, c.st);
   ++c.launches;
   if (e != cudaSuccess) return fail(TN_ECUDA, "step %zu launch: %s", s, cudaGetErrorString(e));

@@ -1,0 +1,359 @@
+// Warp-specialized tcgen05 GEMM fed by TMA, for complex operands prepared as
+// four K-major 16-bit planes {re_hi, re_lo, im_hi, im_lo} (see k_split.cu).
+//
+// Paper: Sec. "Tensor Contraction Using Fused Permutation and Multiplication"
+// (dense case: high compute density contraction at near-peak rate) and Sec.
+// "A Mixed-Precision Computation Method via Adaptive Precision Scaling"
+// (half-precision products, single-precision accumulation).
+//
+// Complex product on real tensor cores, planar form, split precision:
+//   Dr = Ar Br - Ai Bi,  Di = Ar Bi + Ai Br,
+// each real product X Y expanded as Xhi Yhi + Xhi Ylo + Xlo Yhi (FP32
+// accumulation in TMEM); the minus sign uses the MMA's negate-A bit.  Dr and
+// Di occupy TN columns of TMEM each.
+//
+// Roles (256 threads): warp 0 lane 0 issues TMA loads of one K stage (32
+// complex K values of a 128-row A tile and a TN-row B tile, all four planes,
+// 64-byte swizzled) into a ring of stages guarded by full/empty mbarriers;
+// warp 1 lane 0 issues the tcgen05.mma instructions and commits each stage
+// back to its empty barrier; warp 2 owns the TMEM allocation; warps 4-7 read
+// the accumulators (tcgen05.ld) and write complex64 C through per-row and
+// per-column offsets (the output permutation).  Every wait is bounded: on
+// expiry the CTA records an error code, stops issuing work, drains what it
+// issued and releases its TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "kernels.h"
+
+namespace tn {
+
+namespace {
+
+constexpr int TM = 128;
+constexpr int TKC = 32;                 // complex K per stage (64-byte rows of 16-bit values)
+constexpr int NTHREADS = 256;
+constexpr int A_STAGE = 4 * TM * 64;    // four planes of 128 rows x 64 bytes
+constexpr int SMEM_BUDGET = 196 * 1024;
+constexpr long long kWaitLimit = 1ll << 24;
+
+template <int TN>
+struct Cfg2 {
+  static constexpr int B_STAGE = 4 * TN * 64;
+  static constexpr int STAGE = A_STAGE + B_STAGE;
+  static constexpr int NSTAGE = (SMEM_BUDGET / STAGE) < 6 ? (SMEM_BUDGET / STAGE) : 6;
+  static constexpr int SMEM = NSTAGE * STAGE + 1024;
+  static constexpr uint32_t TMEM_COLS = 2 * TN < 32 ? 32 : 2 * TN;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// K-major, 64-byte swizzled operand: stride byte offset 512 (8 rows x 64 B),
+// descriptor version 1 (bits 46-47), swizzle mode 4 = 64 B (bits 61-63).
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
+// kind::f16 instruction descriptor: FP32 accumulate, A/B 16-bit format
+// (0 fp16, 1 bf16), optional negate-A (bit 13), K-major A and B, N >> 3 at
+// bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc2(bool bf16, int M, int N, bool neg_a) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((neg_a ? 1u : 0u) << 13) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ int32_t bit_offset(int64_t x, int nb, const int32_t* st) {
+  int32_t o = 0;
+  for (int i = 0; i < nb; ++i)
+    if ((x >> i) & 1) o += st[i];
+  return o;
+}
+
+template <int NREG>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t* v);
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
+template <int TN, bool BF16>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    gemm_tma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                    float2* __restrict__ C, const GemmDesc d, int kp, int a_zlo, int a_zhi, int b_zlo, int b_zhi,
+                    float inv_scale, int* __restrict__ err) {
+  using CF = Cfg2<TN>;
+  constexpr int NS = CF::NSTAGE;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t full[NS], empty[NS], done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int32_t rowC[TM], colC[TN];
+  __shared__ volatile int abort_flag;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ulo = blockIdx.z % d.units_lo, uhi = blockIdx.z / d.units_lo;
+  const int za = (a_zlo ? (int)ulo : 0) + (a_zhi ? (int)uhi * (a_zlo ? d.units_lo : 1) : 0);
+  const int zb = (b_zlo ? (int)ulo : 0) + (b_zhi ? (int)uhi * (b_zlo ? d.units_lo : 1) : 0);
+  C += ulo * d.c_lo + uhi * d.c_hi;
+  const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+  const int nkt = kp / TKC;
+
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    mbar_init(&done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(CF::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (warp >= 4) {  // output offsets, computed while the main loop runs
+    const int t = tid - 128;
+    const int64_t M = int64_t(1) << d.nm, N = int64_t(1) << d.nn;
+    rowC[t] = (m0 + t < M) ? bit_offset(m0 + t, d.nm, d.cm) : -1;
+    for (int j = t; j < TN; j += 128) colC[j] = (n0 + j < N) ? bit_offset(n0 + j, d.nn, d.cn) : -1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    // ---- TMA producer (one lane; the warp reconverges before the final barrier)
+    for (int kt = 0; lane == 0 && kt < nkt; ++kt) {
+      const int s = kt % NS;
+      if (kt >= NS && !mbar_wait(&empty[s], ((kt / NS) - 1) & 1)) {
+        atomicExch(err, 11);
+        abort_flag = 1;
+        break;
+      }
+      if (abort_flag) break;
+      uint8_t* st = smem + s * CF::STAGE;
+      mbar_expect_tx(&full[s], CF::STAGE);
+      tma_load_4d(st, &mapA, &full[s], kt * TKC, m0, 0, za);
+      tma_load_4d(st + A_STAGE, &mapB, &full[s], kt * TKC, n0, 0, zb);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---- MMA issuer (one lane)
+    constexpr uint32_t I = idesc2(BF16, TM, TN, false), IN = idesc2(BF16, TM, TN, true);
+    const uint32_t dr = tmem, di = tmem + TN;
+    int issued = 0;
+    for (int kt = 0; lane == 0 && kt < nkt; ++kt) {
+      const int s = kt % NS;
+      if (!mbar_wait(&full[s], (kt / NS) & 1)) {
+        atomicExch(err, 12);
+        abort_flag = 1;
+        break;
+      }
+      if (abort_flag) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a = smem_u32(smem + s * CF::STAGE);
+      const uint32_t b = a + A_STAGE;
+#pragma unroll
+      for (int kk = 0; kk < TKC / 16; ++kk) {
+        uint64_t A_[4], B_[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          A_[p] = sw64_desc(a + p * (TM * 64) + kk * 32);
+          B_[p] = sw64_desc(b + p * (TN * 64) + kk * 32);
+        }
+        const uint32_t acc = (kt | kk) ? 1u : 0u;
+        // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
+        mma(dr, A_[0], B_[0], I, acc);
+        mma(dr, A_[0], B_[1], I, 1u);
+        mma(dr, A_[1], B_[0], I, 1u);
+        mma(dr, A_[2], B_[2], IN, 1u);
+        mma(dr, A_[2], B_[3], IN, 1u);
+        mma(dr, A_[3], B_[2], IN, 1u);
+        mma(di, A_[0], B_[2], I, acc);
+        mma(di, A_[0], B_[3], I, 1u);
+        mma(di, A_[1], B_[2], I, 1u);
+        mma(di, A_[2], B_[0], I, 1u);
+        mma(di, A_[2], B_[1], I, 1u);
+        mma(di, A_[3], B_[0], I, 1u);
+      }
+      commit(&empty[s]);
+      ++issued;
+    }
+    if (lane == 0) {
+      if (issued > 0) commit(&done);  // tracks every MMA issued above
+      else if (nkt > 0) atomicExch(err, 13);
+    }
+    __syncwarp();
+  } else if (warp >= 4) {
+    // ---- epilogue (whole warps: tcgen05.ld is warp-collective)
+    const int q = warp & 3;
+    bool ok = nkt > 0 && mbar_wait(&done, 0);
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok && lane == 0 && nkt > 0) atomicExch(err, 14);
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const bool go = __all_sync(0xffffffffu, ok && !abort_flag);
+    if (go) {
+      const int r = q * 32 + lane;
+      const int32_t ro = rowC[r];
+#pragma unroll 1
+      for (int c0 = 0; c0 < TN; c0 += 16) {
+        uint32_t vr[16], vi[16];
+        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+        tmem_ld<16>(lane_base + (uint32_t)c0, vr);
+        tmem_ld<16>(lane_base + (uint32_t)(TN + c0), vi);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (ro >= 0) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int32_t co = colC[c0 + j];
+            if (co >= 0)
+              C[(int64_t)ro + co] =
+                  make_float2(__uint_as_float(vr[j]) * inv_scale, __uint_as_float(vi[j]) * inv_scale);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 2) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CF::TMEM_COLS));
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+// 4-D map over planes [z][plane][row][k] of 16-bit values; box = 32 k x box_rows x 4 planes x 1.
+bool encode_planes(CUtensorMap* map, const uint16_t* base, int64_t kp, int64_t rows, int64_t nz, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[4] = {(cuuint64_t)kp, (cuuint64_t)rows, 4, (cuuint64_t)nz};
+  cuuint64_t strides[3] = {(cuuint64_t)(kp * 2), (cuuint64_t)(rows * kp * 2), (cuuint64_t)(4 * rows * kp * 2)};
+  cuuint32_t box[4] = {(cuuint32_t)TKC, (cuuint32_t)box_rows, 4, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<uint16_t*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int TN, bool BF16>
+cudaError_t launch_cfg(const CUtensorMap& ma, const CUtensorMap& mb, float2* C, const GemmDesc& d, int kp,
+                       const int z[4], float inv_scale, int* err, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tma_kernel<TN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg2<TN>::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int64_t M = int64_t(1) << d.nm, N = int64_t(1) << d.nn;
+  dim3 grid((unsigned)(M / TM), (unsigned)(N / TN), (unsigned)d.units);
+  gemm_tma_kernel<TN, BF16><<<grid, NTHREADS, Cfg2<TN>::SMEM, s>>>(ma, mb, C, d, kp, z[0], z[1], z[2], z[3],
+                                                                   inv_scale, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int tma_tile_n(const GemmDesc& d) { return d.nn >= 7 ? 128 : (1 << d.nn); }
+
+int64_t split_plane_elems(int nrow_bits, int nk_bits) {
+  const int64_t kp = std::max<int64_t>(int64_t(1) << nk_bits, TKC);
+  return 4 * (int64_t(1) << nrow_bits) * kp;
+}
+
+cudaError_t launch_gemm_tma(const uint16_t* Ap, int nza, const uint16_t* Bp, int nzb, float2* C, const GemmDesc& d,
+                            const int zflags[4], bool bf16, float inv_scale, int* err, cudaStream_t s) {
+  if (!tc_shape_ok(d) || d.units > 65535) return cudaErrorInvalidValue;
+  const int TNv = tma_tile_n(d);
+  const int64_t kp = std::max<int64_t>(int64_t(1) << d.nk, TKC);
+  CUtensorMap ma, mb;
+  if (!encode_planes(&ma, Ap, kp, int64_t(1) << d.nm, nza, TM) ||
+      !encode_planes(&mb, Bp, kp, int64_t(1) << d.nn, nzb, TNv))
+    return cudaErrorInvalidValue;
+  const int kpi = (int)kp;
+  switch (TNv) {
+    case 128: return bf16 ? launch_cfg<128, true>(ma, mb, C, d, kpi, zflags, inv_scale, err, s)
+                          : launch_cfg<128, false>(ma, mb, C, d, kpi, zflags, inv_scale, err, s);
+    case 64: return bf16 ? launch_cfg<64, true>(ma, mb, C, d, kpi, zflags, inv_scale, err, s)
+                         : launch_cfg<64, false>(ma, mb, C, d, kpi, zflags, inv_scale, err, s);
+    case 32: return bf16 ? launch_cfg<32, true>(ma, mb, C, d, kpi, zflags, inv_scale, err, s)
+                         : launch_cfg<32, false>(ma, mb, C, d, kpi, zflags, inv_scale, err, s);
+    case 16: return bf16 ? launch_cfg<16, true>(ma, mb, C, d, kpi, zflags, inv_scale, err, s)
+                         : launch_cfg<16, false>(ma, mb, C, d, kpi, zflags, inv_scale, err, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace tn

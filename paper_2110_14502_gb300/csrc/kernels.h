@@ -65,6 +65,32 @@ cudaError_t launch_gemm_simt(const float2* A, const float2* B, float2* C, const 
 bool tc_shape_ok(const GemmDesc& d);
 cudaError_t launch_gemm_tc(const float2* A, const float2* B, float2* C, const GemmDesc& d, bool bf16, float a_scale,
                            float b_scale, int* err, cudaStream_t s);
+// Operand preparation for the TMA-fed GEMM: rows = M (A) or N (B), each row a
+// K run; element (r, k) at sum bit_i(r) row_st[i] + sum bit_l(k) k_st[l] of
+// the source tensor number z, whose base is src + (z % nlo) * lo + (z / nlo) * hi.
+// Output: per z four planes {re_hi, re_lo, im_hi, im_lo} of rows_pad x kp
+// 16-bit values (kp a multiple of 32, zero padded).
+struct SplitDesc {
+  int nrow, nk;
+  int rows_pad, kp;
+  int nlo;
+  int64_t lo, hi;
+  int32_t row_st[kMaxBits], k_st[kMaxBits];
+};
+cudaError_t launch_split(const float2* src, uint16_t* dst, const SplitDesc& d, int nz, bool bf16, float scale,
+                         cudaStream_t s);
+// TMA-fed warp-specialized tcgen05 GEMM on split planes.  zflags = {a varies
+// with the low unit index, a varies with the high one, same for b}; nza/nzb =
+// number of distinct operand tensors (planes sets) in Ap/Bp.
+int tma_tile_n(const GemmDesc& d);
+int64_t split_plane_elems(int nrow_bits, int nk_bits);
+cudaError_t launch_gemm_tma(const uint16_t* Ap, int nza, const uint16_t* Bp, int nzb, float2* C, const GemmDesc& d,
+                            const int zflags[4], bool bf16, float inv_scale, int* err, cudaStream_t s);
+// Split both operands of d into `scratch` (>= tc2_scratch_elems(d) 16-bit
+// values) and run the TMA GEMM.
+int64_t tc2_scratch_elems(const GemmDesc& d);
+cudaError_t run_gemm_tc2(const float2* A, const float2* B, float2* C, const GemmDesc& d, bool bf16, uint16_t* scratch,
+                         int* err, cudaStream_t s);
 cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s);
 cudaError_t launch_gather(const float2* store, float2* arena, int64_t arena_stride, const LeafGather* descs,
                           int nleaves, const uint64_t* bits, const GroupInfo& g, cudaStream_t s);

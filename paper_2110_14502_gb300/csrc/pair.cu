@@ -127,16 +127,27 @@ extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, in
       e = launch_vector(a, b, c, d, s);
       break;
     case TN_PAIR_UNFUSED: return unfused(a, b, c, d, s);
-    case TN_PAIR_FUSED_TC: {
+    case TN_PAIR_FUSED_TC:
+    case TN_PAIR_GATHER_TC: {
       if (precision != TN_PREC_SPLIT_BF16)
-        return fail(TN_EINVAL, "tn_contract_pair: the tensor-core kernel needs precision TN_PREC_SPLIT_BF16");
-      if (!tc_shape_ok(d)) return fail(TN_EINVAL, "tn_contract_pair: tensor-core kernel needs M >= 128, N >= 16, K >= 8");
+        return fail(TN_EINVAL, "tn_contract_pair: the tensor-core kernels need precision TN_PREC_SPLIT_BF16");
+      if (!tc_shape_ok(d)) return fail(TN_EINVAL, "tn_contract_pair: tensor-core kernels need M >= 128, N >= 16, K >= 8");
       static int* err = nullptr;
       if (!err) {
         if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return fail(TN_ECUDA, "tn_contract_pair: error word");
         cudaMemset(err, 0, sizeof(int));
       }
-      e = launch_gemm_tc(a, b, c, d, true, 1.f, 1.f, err, s);
+      uint16_t* scratch = nullptr;
+      if (algo == TN_PAIR_FUSED_TC) {
+        if (cudaMallocAsync(&scratch, (size_t)tc2_scratch_elems(d) * sizeof(uint16_t), s) != cudaSuccess) {
+          cudaGetLastError();
+          return fail(TN_EHBM, "tn_contract_pair: operand planes do not fit");
+        }
+        e = run_gemm_tc2(a, b, c, d, true, scratch, err, s);
+        cudaFreeAsync(scratch, s);
+      } else {
+        e = launch_gemm_tc(a, b, c, d, true, 1.f, 1.f, err, s);
+      }
       if (e == cudaSuccess) {
         int h = 0;
         cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);

@@ -70,11 +70,12 @@ def test_pair_rejects_bad_labels():
         T.contract_pair(a, [0, 0], a, [1, 2], a, [1, 2], algo="auto")   # repeated label
 
 
-TC_SHAPES = [(7, 4, 3), (7, 6, 5), (8, 7, 6), (10, 6, 9), (9, 9, 4), (12, 8, 10), (14, 7, 7)]
+TC_SHAPES = [(7, 4, 3), (7, 6, 5), (8, 7, 6), (10, 6, 9), (9, 9, 4), (12, 8, 10), (14, 7, 7), (7, 5, 4), (8, 8, 12)]
 
 
 @pytest.mark.parametrize("nm,nn,nk", TC_SHAPES)
-def test_tcgen05_split_bf16_matches_fp64(nm, nn, nk):
+@pytest.mark.parametrize("algo", ["fused_tc", "gather_tc"])
+def test_tcgen05_split_bf16_matches_fp64(nm, nn, nk, algo):
     """tcgen05 kernel, bf16 hi+lo split products with FP32 accumulation:
     relative L2 error <= 1e-4 (the split-precision bound)."""
     T = tnlib()
@@ -83,7 +84,7 @@ def test_tcgen05_split_bf16_matches_fp64(nm, nn, nk):
     dA = torch.from_numpy(A).cuda()
     dB = torch.from_numpy(B).cuda()
     dC = torch.empty(1 << len(lc), dtype=torch.complex64, device="cuda")
-    T.contract_pair(dA, la, dB, lb, dC, lc, precision="split_bf16", algo="fused_tc")
+    T.contract_pair(dA, la, dB, lb, dC, lc, precision="split_bf16", algo=algo)
     torch.cuda.synchronize()
     got = dC.cpu().numpy().astype(np.complex128)
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
