@@ -240,6 +240,7 @@ tn_status run_step(Ctx& c, size_t s, const Geo& g) {
       E.scratch_cap = need;
     }
     e = run_gemm_tc2(A, B, C, d, true, E.scratch, E.err, c.st);
+    c.launches += 2;  // the two operand-split kernels
   }
   else e = launch_gemm_simt(A, B, C, d, c.st);
   ++c.launches;
