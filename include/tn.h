@@ -256,6 +256,26 @@ tn_status tn_contract_pair(const void* A, const int32_t* a_labels, int32_t a_ran
                            void* C, const int32_t* c_labels, int32_t c_rank,
                            int32_t precision, int32_t algo, void* stream);
 
+/* Allocation-free variant of tn_contract_pair's tensor-core path (the paper
+ * has no counterpart: this serves callers that cannot let a library allocate
+ * device memory -- a framework whose caching allocator already holds the free
+ * HBM, a serving loop with a fixed memory budget or no allocator calls on its
+ * request path, code next to a CUDA graph capture).
+ * Same arguments and label rules as tn_contract_pair with algo =
+ * TN_PAIR_FUSED_TC and precision = TN_PREC_SPLIT_BF16 (M >= 128, N >= 16,
+ * K >= 8).  Scratch comes from one static device array of 64 MiB per GPU
+ * (kept until the process exits): the split operand planes,
+ * 8 * (M + N) * max(K, 32) bytes, must fit, else TN_EINVAL before any work.
+ * The first call on a device (that device current) looks up the array's
+ * address with cudaGetSymbolAddress; make it before any stream capture.  All
+ * calls on a device share the array: calls whose work overlaps on the GPU
+ * race and must be serialised by the caller.  No cudaMalloc, cudaFree or
+ * allocating library call is made.  Returns after the contraction has finished
+ * on `stream` (it reads back the kernel's error word). */
+tn_status tn_contract_pair_noalloc(const void* A, const int32_t* a_labels, int32_t a_rank,
+                                   const void* B, const int32_t* b_labels, int32_t b_rank,
+                                   void* C, const int32_t* c_labels, int32_t c_rank, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,7 +13,7 @@ from ._abi import (PAIR_ALGO, PREC, ExecOpts, Gate, NetworkInfo, PlanInfo, PlanO
                    i32array, lib)
 
 __all__ = ["Circuit", "Network", "Plan", "random_circuit", "circuit_from_gates", "build_network", "plan",
-           "contract_pair", "TnError", "PREC", "version"]
+           "contract_pair", "contract_pair_noalloc", "TnError", "PREC", "version"]
 
 
 def version():
@@ -228,4 +228,17 @@ def contract_pair(A, a_labels, B, b_labels, Cout, c_labels, precision="c64", alg
     al = PAIR_ALGO[algo] if isinstance(algo, str) else int(algo)
     check(lib().tn_contract_pair(_ptr(A), pa, len(la), _ptr(B), pb, len(lb), _ptr(Cout), pc, len(lc),
                                  prec, al, s))
+    return Cout
+
+
+def contract_pair_noalloc(A, a_labels, B, b_labels, Cout, c_labels, stream=None):
+    """tn_contract_pair_noalloc: the tensor-core contraction (bf16 hi+lo) with
+    scratch taken from the library's static device array instead of an
+    allocation; for callers that cannot let the library allocate.  Calls on
+    one GPU share the array, so overlapping calls race."""
+    la, pa = i32array(a_labels)
+    lb, pb = i32array(b_labels)
+    lc, pc = i32array(c_labels)
+    s = C.c_void_p(getattr(stream, "cuda_stream", stream) if stream is not None else None)
+    check(lib().tn_contract_pair_noalloc(_ptr(A), pa, len(la), _ptr(B), pb, len(lb), _ptr(Cout), pc, len(lc), s))
     return Cout

@@ -88,6 +88,8 @@ SIGNATURES = {
                                          C.POINTER(Report)]),
     "tn_contract_pair": (C.c_int, [C.c_void_p, I32P, C.c_int32, C.c_void_p, I32P, C.c_int32,
                                    C.c_void_p, I32P, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
+    "tn_contract_pair_noalloc": (C.c_int, [C.c_void_p, I32P, C.c_int32, C.c_void_p, I32P, C.c_int32,
+                                           C.c_void_p, I32P, C.c_int32, C.c_void_p]),
 }
 
 _lib = None
