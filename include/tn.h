@@ -206,7 +206,7 @@ typedef struct {
 } tn_exec_opts;
 
 /* Kernel classes of the per-class report figures. */
-enum { TN_KCLASS_GEMM_SIMT = 0, TN_KCLASS_VECTOR = 1, TN_KCLASS_GEMM_TC = 2, TN_KCLASS_OTHER = 3 };
+enum { TN_KCLASS_GEMM_SIMT = 0, TN_KCLASS_VECTOR = 1, TN_KCLASS_GEMM_TC = 2, TN_KCLASS_SPLIT = 3 };
 
 typedef struct {
   double device_ms;          /* device time of the call (CUDA events on the call's stream) */

@@ -168,6 +168,7 @@ struct Ctx {
   std::vector<Rec> recs;
   size_t nev = 0;
   int precision = TN_PREC_C64;
+  std::vector<char> planes_out;  // per step: output written as 16-bit planes for a tensor-core consumer
   Ctx(const Plan& p, Executor& e, cudaStream_t s, bool prof) : P(p), E(e), st(s), profile(prof) {}
 
   tn_status event(size_t& idx) {
@@ -228,7 +229,14 @@ tn_status run_step(Ctx& c, size_t s, const Geo& g) {
   if (S.klass != SC_VECTOR && split && tc_shape_ok(d)) klass = TN_KCLASS_GEMM_TC;
   if (klass == TN_KCLASS_VECTOR) e = launch_vector(A, B, C, d, c.st);
   else if (klass == TN_KCLASS_GEMM_TC) {
-    const int64_t need = tc2_scratch_elems(d);
+    const int L = (int)P.net.leaves.size();
+    PlaneOperand pa{}, pb{};
+    const bool a_in = S.a >= L && c.planes_out[S.a - L] && planes_in_place(A, d, false, pa);
+    const bool b_in = S.b >= L && c.planes_out[S.b - L] && planes_in_place(B, d, true, pb);
+    if ((S.a >= L && c.planes_out[S.a - L] && !a_in) || (S.b >= L && c.planes_out[S.b - L] && !b_in))
+      return fail(TN_EINVAL, "step %zu: internal error, operand planes do not match the step's view", s);
+    const int64_t need_a = a_in ? 0 : split_scratch_elems(d, false);
+    const int64_t need = need_a + (b_in ? 0 : split_scratch_elems(d, true));
     if (need > E.scratch_cap) {
       cudaFree(E.scratch);
       E.scratch = nullptr;
@@ -239,8 +247,23 @@ tn_status run_step(Ctx& c, size_t s, const Geo& g) {
       }
       E.scratch_cap = need;
     }
-    e = run_gemm_tc2(A, B, C, d, true, E.scratch, E.err, c.st);
-    c.launches += 2;  // the two operand-split kernels
+    e = cudaSuccess;
+    if (!a_in) { e = split_operand(A, d, false, true, E.scratch, pa, c.st); ++c.launches; }
+    if (e == cudaSuccess && !b_in) { e = split_operand(B, d, true, true, E.scratch + need_a, pb, c.st); ++c.launches; }
+    if (c.profile && e == cudaSuccess && need > 0) {
+      // the operand split and the GEMM are timed as separate classes
+      size_t em = 0;
+      tn_status r = c.event(em);
+      if (r) return r;
+      const double K = std::ldexp(1.0, d.nk), kp = std::max(K, 32.0);
+      const double nza = (d.a_lo ? d.units_lo : 1.0) * (d.a_hi ? (double)d.units / d.units_lo : 1.0);
+      const double nzb = (d.b_lo ? d.units_lo : 1.0) * (d.b_hi ? (double)d.units / d.units_lo : 1.0);
+      const double bytes = (a_in ? 0.0 : 8.0 * std::ldexp(1.0, d.nm) * (K + kp) * nza) +
+                           (b_in ? 0.0 : 8.0 * std::ldexp(1.0, d.nn) * (K + kp) * nzb);
+      c.recs.push_back({TN_KCLASS_SPLIT, 0.0, bytes, e0});
+      e0 = em;
+    }
+    if (e == cudaSuccess) e = launch_gemm_tma(pa, pb, C, c.planes_out[s] != 0, d, true, 1.f, E.err, c.st);
   }
   else e = launch_gemm_simt(A, B, C, d, c.st);
   ++c.launches;
@@ -349,6 +372,26 @@ tn_status contract_amplitudes(Plan& P, const uint64_t* bits, int64_t nb, double*
   }
   Ctx c(P, E, st, o.profile != 0);
   c.precision = o.precision;
+  c.planes_out.assign(P.steps.size(), 0);
+  if (o.precision == TN_PREC_SPLIT_BF16) {
+    // A step whose consumer also runs on the tensor cores hands its output over
+    // as split planes laid out for that consumer (no separate split pass).
+    const int L = (int)P.net.leaves.size();
+    std::vector<char> tc(P.steps.size(), 0);
+    for (size_t s = 0; s < P.steps.size(); ++s) tc[s] = P.steps[s].klass != SC_VECTOR && tc_shape_ok(E.desc[s]);
+    for (size_t t = 0; t < P.steps.size(); ++t) {
+      if (!tc[t]) continue;
+      const Step& S = P.steps[t];
+      for (int role = 0; role < 2; ++role) {
+        const int x = role ? S.b : S.a;
+        if (x < L) continue;
+        const int p = x - L;
+        PlaneOperand probe{};
+        if (tc[p] && P.steps[p].phase != 0 && planes_in_place(nullptr, E.desc[t], role == 1, probe))
+          c.planes_out[p] = 1;
+      }
+    }
+  }
   CK(cudaEventRecord(E.ev0, st));
   if (!o.device_io && nb > 0)
     CK(cudaMemcpyAsync((void*)d_bits, bits, nb * words * sizeof(uint64_t), cudaMemcpyHostToDevice, st));

@@ -49,17 +49,36 @@ __global__ void __launch_bounds__(NT) split_kernel(const float2* __restrict__ sr
     if (rok)
       for (int i = 0; i < d.nrow; ++i)
         if ((r >> i) & 1) ro += d.row_st[i];
+    float2 v[8];
+    if (d.kvec && rok && c * 8 < K) {
+      // 8 consecutive K values are contiguous: one 64-byte run
+      int32_t ko = 0;
+      const int64_t k0 = c * 8;
+      for (int i = 3; i < d.nk; ++i)
+        if ((k0 >> i) & 1) ko += d.k_st[i];
+      const float4* p = reinterpret_cast<const float4*>(src + (int64_t)ro + ko);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 x = __ldg(p + q);
+        v[2 * q] = make_float2(x.x, x.y);
+        v[2 * q + 1] = make_float2(x.z, x.w);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int64_t k = c * 8 + j;
+        v[j] = make_float2(0.f, 0.f);
+        if (rok && k < K) {
+          int32_t ko = 0;
+          for (int i = 0; i < d.nk; ++i)
+            if ((k >> i) & 1) ko += d.k_st[i];
+          v[j] = __ldg(src + (int64_t)ro + ko);
+        }
+      }
+    }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int64_t k = c * 8 + j;
-      float2 v = make_float2(0.f, 0.f);
-      if (rok && k < K) {
-        int32_t ko = 0;
-        for (int i = 0; i < d.nk; ++i)
-          if ((k >> i) & 1) ko += d.k_st[i];
-        v = __ldg(src + (int64_t)ro + ko);
-      }
-      const float re = v.x * scale, im = v.y * scale;
+      const float re = v[j].x * scale, im = v[j].y * scale;
       rh[j] = to16(re, bf16);
       rl[j] = to16(re - from16(rh[j], bf16), bf16);
       ih[j] = to16(im, bf16);
@@ -104,31 +123,71 @@ void split_desc(int nrow, const int32_t* row_st, int nk, const int32_t* k_st, in
   sd.hi = hi;
   for (int i = 0; i < nrow; ++i) sd.row_st[i] = row_st[i];
   for (int i = 0; i < nk; ++i) sd.k_st[i] = k_st[i];
+  // vector path: K >= 8 with its three lowest bits contiguous, 16-byte aligned rows
+  bool rows_aligned = true;
+  for (int i = 0; i < nrow; ++i) rows_aligned &= (row_st[i] % 2) == 0;
+  sd.kvec = nk >= 3 && k_st[0] == 1 && k_st[1] == 2 && k_st[2] == 4 && rows_aligned && (lo % 2) == 0 && (hi % 2) == 0;
 }
 int distinct(const GemmDesc& d, int64_t lo, int64_t hi) {
   return (lo ? d.units_lo : 1) * (hi ? d.units / d.units_lo : 1);
 }
 }  // namespace
 
-int64_t tc2_scratch_elems(const GemmDesc& d) {
-  return split_plane_elems(d.nm, d.nk) * distinct(d, d.a_lo, d.a_hi) +
-         split_plane_elems(d.nn, d.nk) * distinct(d, d.b_lo, d.b_hi);
+int64_t split_scratch_elems(const GemmDesc& d, bool which_b) {
+  return which_b ? split_plane_elems(d.nn, d.nk) * distinct(d, d.b_lo, d.b_hi)
+                 : split_plane_elems(d.nm, d.nk) * distinct(d, d.a_lo, d.a_hi);
+}
+
+int64_t tc2_scratch_elems(const GemmDesc& d) { return split_scratch_elems(d, false) + split_scratch_elems(d, true); }
+
+cudaError_t split_operand(const float2* src, const GemmDesc& d, bool which_b, bool bf16, uint16_t* scratch,
+                          PlaneOperand& out, cudaStream_t s) {
+  const int64_t lo = which_b ? d.b_lo : d.a_lo, hi = which_b ? d.b_hi : d.a_hi;
+  const int nrow = which_b ? d.nn : d.nm;
+  SplitDesc sd;
+  split_desc(nrow, which_b ? d.bn : d.am, d.nk, which_b ? d.bk : d.ak, lo ? d.units_lo : 1, lo, hi, sd);
+  const int nz = distinct(d, lo, hi);
+  cudaError_t e = launch_split(src, scratch, sd, nz, bf16, 1.f, s);
+  const int64_t set = 4 * (int64_t(1) << nrow) * sd.kp * 2;
+  out.base = scratch;
+  out.kp = sd.kp;
+  out.rows = int64_t(1) << nrow;
+  out.nlo = lo ? d.units_lo : 1;
+  out.nhi = hi ? d.units / d.units_lo : 1;
+  out.st_lo = set;
+  out.st_hi = set * out.nlo;
+  return e;
+}
+
+bool planes_in_place(const float2* base, const GemmDesc& d, bool which_b, PlaneOperand& out) {
+  const int nrow = which_b ? d.nn : d.nm;
+  const int32_t* rs = which_b ? d.bn : d.am;
+  const int32_t* ks = which_b ? d.bk : d.ak;
+  const int64_t K = int64_t(1) << d.nk;
+  if (K < 32) return false;
+  for (int l = 0; l < d.nk; ++l)
+    if (ks[l] != (int32_t(1) << l)) return false;
+  for (int i = 0; i < nrow; ++i)
+    if ((int64_t)rs[i] != (K << i)) return false;
+  const int64_t lo = which_b ? d.b_lo : d.a_lo, hi = which_b ? d.b_hi : d.a_hi;
+  out.base = reinterpret_cast<const uint16_t*>(base);
+  out.kp = K;
+  out.rows = int64_t(1) << nrow;
+  out.nlo = lo ? d.units_lo : 1;
+  out.nhi = hi ? d.units / d.units_lo : 1;
+  out.st_lo = lo * 8;
+  out.st_hi = hi * 8;
+  return true;
 }
 
 cudaError_t run_gemm_tc2(const float2* A, const float2* B, float2* C, const GemmDesc& d, bool bf16, uint16_t* scratch,
                          int* err, cudaStream_t s) {
-  SplitDesc sa, sb;
-  const int nza = distinct(d, d.a_lo, d.a_hi), nzb = distinct(d, d.b_lo, d.b_hi);
-  split_desc(d.nm, d.am, d.nk, d.ak, d.a_lo ? d.units_lo : 1, d.a_lo, d.a_hi, sa);
-  split_desc(d.nn, d.bn, d.nk, d.bk, d.b_lo ? d.units_lo : 1, d.b_lo, d.b_hi, sb);
-  uint16_t* Ap = scratch;
-  uint16_t* Bp = scratch + split_plane_elems(d.nm, d.nk) * nza;
-  cudaError_t e = launch_split(A, Ap, sa, nza, bf16, 1.f, s);
+  PlaneOperand pa, pb;
+  cudaError_t e = split_operand(A, d, false, bf16, scratch, pa, s);
   if (e != cudaSuccess) return e;
-  e = launch_split(B, Bp, sb, nzb, bf16, 1.f, s);
+  e = split_operand(B, d, true, bf16, scratch + split_scratch_elems(d, false), pb, s);
   if (e != cudaSuccess) return e;
-  const int zf[4] = {d.a_lo != 0, d.a_hi != 0, d.b_lo != 0, d.b_hi != 0};
-  return launch_gemm_tma(Ap, nza, Bp, nzb, C, d, zf, bf16, 1.f, err, s);
+  return launch_gemm_tma(pa, pb, C, false, d, bf16, 1.f, err, s);
 }
 
 }  // namespace tn

@@ -23,6 +23,8 @@
 // issued and releases its TMEM.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <mutex>
 
@@ -38,6 +40,7 @@ constexpr int NTHREADS = 256;
 constexpr int A_STAGE = 4 * TM * 64;    // four planes of 128 rows x 64 bytes
 constexpr int SMEM_BUDGET = 196 * 1024;
 constexpr long long kWaitLimit = 1ll << 24;
+constexpr int GROUP_M = 16;
 
 template <int TN>
 struct Cfg2 {
@@ -72,12 +75,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
-                                            int c3) {
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3, int c4) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-      "[%6];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
+      "[%7];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -120,6 +123,19 @@ __device__ __forceinline__ int32_t bit_offset(int64_t x, int nb, const int32_t* 
   return o;
 }
 
+template <bool BF16>
+__device__ __forceinline__ void split16(float x, uint16_t& hi, uint16_t& lo) {
+  if (BF16) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
+  } else {
+    const __half h = __float2half_rn(x);
+    hi = __half_as_ushort(h);
+    lo = __half_as_ushort(__float2half_rn(x - __half2float(h)));
+  }
+}
+
 template <int NREG>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t* v);
 template <>
@@ -135,7 +151,7 @@ template <int TN, bool BF16>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_tma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                     float2* __restrict__ C, const GemmDesc d, int kp, int a_zlo, int a_zhi, int b_zlo, int b_zhi,
-                    float inv_scale, int* __restrict__ err) {
+                    int c_planes, float inv_scale, int* __restrict__ err) {
   using CF = Cfg2<TN>;
   constexpr int NS = CF::NSTAGE;
   extern __shared__ uint8_t smem_raw[];
@@ -147,10 +163,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t ulo = blockIdx.z % d.units_lo, uhi = blockIdx.z / d.units_lo;
-  const int za = (a_zlo ? (int)ulo : 0) + (a_zhi ? (int)uhi * (a_zlo ? d.units_lo : 1) : 0);
-  const int zb = (b_zlo ? (int)ulo : 0) + (b_zhi ? (int)uhi * (b_zlo ? d.units_lo : 1) : 0);
+  const int za_lo = a_zlo ? (int)ulo : 0, za_hi = a_zhi ? (int)uhi : 0;
+  const int zb_lo = b_zlo ? (int)ulo : 0, zb_hi = b_zhi ? (int)uhi : 0;
   C += ulo * d.c_lo + uhi * d.c_hi;
-  const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+  // Grouped raster: tiles run GROUP_M M-tiles at a time with the N-tiles
+  // inside a group varying slowest, so concurrently resident CTAs share A row
+  // blocks and re-read B tiles from L2 rather than DRAM.
+  int m0, n0;
+  {
+    const int ntm = (int)((int64_t(1) << d.nm) / TM), ntn = (int)((int64_t(1) << d.nn) / TN);
+    const int t = blockIdx.x;
+    const int per_group = GROUP_M * ntn;
+    const int g = t / per_group, r = t % per_group;
+    const int gm = min(GROUP_M, ntm - g * GROUP_M);
+    m0 = (g * GROUP_M + r % gm) * TM;
+    n0 = (r / gm) * TN;
+  }
   const int nkt = kp / TKC;
 
   if (tid == 0) {
@@ -189,8 +217,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (abort_flag) break;
       uint8_t* st = smem + s * CF::STAGE;
       mbar_expect_tx(&full[s], CF::STAGE);
-      tma_load_4d(st, &mapA, &full[s], kt * TKC, m0, 0, za);
-      tma_load_4d(st + A_STAGE, &mapB, &full[s], kt * TKC, n0, 0, zb);
+      tma_load_5d(st, &mapA, &full[s], kt * TKC, m0, 0, za_lo, za_hi);
+      tma_load_5d(st + A_STAGE, &mapB, &full[s], kt * TKC, n0, 0, zb_lo, zb_hi);
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -260,12 +288,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tmem_ld<16>(lane_base + (uint32_t)(TN + c0), vi);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (ro >= 0) {
+          if (c_planes) {
+            // output consumed by another tensor-core step: write its four
+            // 16-bit planes {re_hi, re_lo, im_hi, im_lo} at the same offsets
+            uint16_t* P = reinterpret_cast<uint16_t*>(C);
+            const int64_t plane = int64_t(1) << (d.nm + d.nn);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int32_t co = colC[c0 + j];
-            if (co >= 0)
-              C[(int64_t)ro + co] =
-                  make_float2(__uint_as_float(vr[j]) * inv_scale, __uint_as_float(vi[j]) * inv_scale);
+            for (int j = 0; j < 16; ++j) {
+              const int32_t co = colC[c0 + j];
+              if (co < 0) continue;
+              const float re = __uint_as_float(vr[j]) * inv_scale, im = __uint_as_float(vi[j]) * inv_scale;
+              uint16_t rh, rl, ih, il;
+              split16<BF16>(re, rh, rl);
+              split16<BF16>(im, ih, il);
+              const int64_t o = (int64_t)ro + co;
+              P[o] = rh;
+              P[plane + o] = rl;
+              P[2 * plane + o] = ih;
+              P[3 * plane + o] = il;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int32_t co = colC[c0 + j];
+              if (co >= 0)
+                C[(int64_t)ro + co] =
+                    make_float2(__uint_as_float(vr[j]) * inv_scale, __uint_as_float(vi[j]) * inv_scale);
+            }
           }
         }
       }
@@ -293,15 +342,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 4-D map over planes [z][plane][row][k] of 16-bit values; box = 32 k x box_rows x 4 planes x 1.
-bool encode_planes(CUtensorMap* map, const uint16_t* base, int64_t kp, int64_t rows, int64_t nz, int box_rows) {
+// 5-D map over one operand's planes: [hi unit][lo unit][plane][row][k] of
+// 16-bit values; box = 32 k x box_rows x 4 planes x 1 x 1.
+bool encode_planes(CUtensorMap* map, const PlaneOperand& o, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t dims[4] = {(cuuint64_t)kp, (cuuint64_t)rows, 4, (cuuint64_t)nz};
-  cuuint64_t strides[3] = {(cuuint64_t)(kp * 2), (cuuint64_t)(rows * kp * 2), (cuuint64_t)(4 * rows * kp * 2)};
-  cuuint32_t box[4] = {(cuuint32_t)TKC, (cuuint32_t)box_rows, 4, 1};
-  cuuint32_t estr[4] = {1, 1, 1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<uint16_t*>(base), dims, strides, box, estr,
+  const int64_t set = 4 * o.rows * o.kp * 2;  // bytes of one plane set
+  cuuint64_t dims[5] = {(cuuint64_t)o.kp, (cuuint64_t)o.rows, 4, (cuuint64_t)o.nlo, (cuuint64_t)o.nhi};
+  cuuint64_t strides[4] = {(cuuint64_t)(o.kp * 2), (cuuint64_t)(o.rows * o.kp * 2),
+                           (cuuint64_t)(o.nlo > 1 ? o.st_lo : set), (cuuint64_t)(o.nhi > 1 ? o.st_hi : set)};
+  cuuint32_t box[5] = {(cuuint32_t)TKC, (cuuint32_t)box_rows, 4, 1, 1};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 5, const_cast<uint16_t*>(o.base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -309,7 +361,7 @@ bool encode_planes(CUtensorMap* map, const uint16_t* base, int64_t kp, int64_t r
 
 template <int TN, bool BF16>
 cudaError_t launch_cfg(const CUtensorMap& ma, const CUtensorMap& mb, float2* C, const GemmDesc& d, int kp,
-                       const int z[4], float inv_scale, int* err, cudaStream_t s) {
+                       const int z[4], int c_planes, float inv_scale, int* err, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(gemm_tma_kernel<TN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -318,8 +370,8 @@ cudaError_t launch_cfg(const CUtensorMap& ma, const CUtensorMap& mb, float2* C, 
     attr = true;
   }
   const int64_t M = int64_t(1) << d.nm, N = int64_t(1) << d.nn;
-  dim3 grid((unsigned)(M / TM), (unsigned)(N / TN), (unsigned)d.units);
-  gemm_tma_kernel<TN, BF16><<<grid, NTHREADS, Cfg2<TN>::SMEM, s>>>(ma, mb, C, d, kp, z[0], z[1], z[2], z[3],
+  dim3 grid((unsigned)((M / TM) * (N / TN)), 1, (unsigned)d.units);
+  gemm_tma_kernel<TN, BF16><<<grid, NTHREADS, Cfg2<TN>::SMEM, s>>>(ma, mb, C, d, kp, z[0], z[1], z[2], z[3], c_planes,
                                                                    inv_scale, err);
   return cudaGetLastError();
 }
@@ -333,25 +385,24 @@ int64_t split_plane_elems(int nrow_bits, int nk_bits) {
   return 4 * (int64_t(1) << nrow_bits) * kp;
 }
 
-cudaError_t launch_gemm_tma(const uint16_t* Ap, int nza, const uint16_t* Bp, int nzb, float2* C, const GemmDesc& d,
-                            const int zflags[4], bool bf16, float inv_scale, int* err, cudaStream_t s) {
-  if (!tc_shape_ok(d) || d.units > 65535) return cudaErrorInvalidValue;
+cudaError_t launch_gemm_tma(const PlaneOperand& a, const PlaneOperand& b, float2* C, bool c_planes, const GemmDesc& d,
+                            bool bf16, float inv_scale, int* err, cudaStream_t s) {
+  if (!tc_shape_ok(d) || d.units > 65535 || a.kp != b.kp || a.kp % TKC) return cudaErrorInvalidValue;
   const int TNv = tma_tile_n(d);
-  const int64_t kp = std::max<int64_t>(int64_t(1) << d.nk, TKC);
   CUtensorMap ma, mb;
-  if (!encode_planes(&ma, Ap, kp, int64_t(1) << d.nm, nza, TM) ||
-      !encode_planes(&mb, Bp, kp, int64_t(1) << d.nn, nzb, TNv))
-    return cudaErrorInvalidValue;
-  const int kpi = (int)kp;
+  if (!encode_planes(&ma, a, TM) || !encode_planes(&mb, b, TNv)) return cudaErrorInvalidValue;
+  const int kpi = (int)a.kp;
+  const int z[4] = {a.nlo > 1, a.nhi > 1, b.nlo > 1, b.nhi > 1};
+  const int cp = c_planes ? 1 : 0;
   switch (TNv) {
-    case 128: return bf16 ? launch_cfg<128, true>(ma, mb, C, d, kpi, zflags, inv_scale, err, s)
-                          : launch_cfg<128, false>(ma, mb, C, d, kpi, zflags, inv_scale, err, s);
-    case 64: return bf16 ? launch_cfg<64, true>(ma, mb, C, d, kpi, zflags, inv_scale, err, s)
-                         : launch_cfg<64, false>(ma, mb, C, d, kpi, zflags, inv_scale, err, s);
-    case 32: return bf16 ? launch_cfg<32, true>(ma, mb, C, d, kpi, zflags, inv_scale, err, s)
-                         : launch_cfg<32, false>(ma, mb, C, d, kpi, zflags, inv_scale, err, s);
-    case 16: return bf16 ? launch_cfg<16, true>(ma, mb, C, d, kpi, zflags, inv_scale, err, s)
-                         : launch_cfg<16, false>(ma, mb, C, d, kpi, zflags, inv_scale, err, s);
+    case 128: return bf16 ? launch_cfg<128, true>(ma, mb, C, d, kpi, z, cp, inv_scale, err, s)
+                          : launch_cfg<128, false>(ma, mb, C, d, kpi, z, cp, inv_scale, err, s);
+    case 64: return bf16 ? launch_cfg<64, true>(ma, mb, C, d, kpi, z, cp, inv_scale, err, s)
+                         : launch_cfg<64, false>(ma, mb, C, d, kpi, z, cp, inv_scale, err, s);
+    case 32: return bf16 ? launch_cfg<32, true>(ma, mb, C, d, kpi, z, cp, inv_scale, err, s)
+                         : launch_cfg<32, false>(ma, mb, C, d, kpi, z, cp, inv_scale, err, s);
+    case 16: return bf16 ? launch_cfg<16, true>(ma, mb, C, d, kpi, z, cp, inv_scale, err, s)
+                         : launch_cfg<16, false>(ma, mb, C, d, kpi, z, cp, inv_scale, err, s);
     default: return cudaErrorInvalidValue;
   }
 }

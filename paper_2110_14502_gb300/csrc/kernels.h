@@ -74,18 +74,35 @@ struct SplitDesc {
   int nrow, nk;
   int rows_pad, kp;
   int nlo;
+  int kvec;  // 8 consecutive K values contiguous and 16-byte aligned: vector loads
   int64_t lo, hi;
   int32_t row_st[kMaxBits], k_st[kMaxBits];
 };
 cudaError_t launch_split(const float2* src, uint16_t* dst, const SplitDesc& d, int nz, bool bf16, float scale,
                          cudaStream_t s);
-// TMA-fed warp-specialized tcgen05 GEMM on split planes.  zflags = {a varies
-// with the low unit index, a varies with the high one, same for b}; nza/nzb =
-// number of distinct operand tensors (planes sets) in Ap/Bp.
+// One GEMM operand stored as four K-major 16-bit planes {re_hi, re_lo, im_hi,
+// im_lo}, each rows x kp; consecutive units are st_lo / st_hi bytes apart
+// along the two unit dimensions (extent 1 = one tensor shared by all units).
+struct PlaneOperand {
+  const uint16_t* base;
+  int64_t kp, rows;
+  int64_t nlo, nhi;
+  int64_t st_lo, st_hi;
+};
+// TMA-fed warp-specialized tcgen05 GEMM on plane operands.  With c_planes
+// the epilogue writes C as planes (for a tensor-core consumer) instead of
+// complex64.
 int tma_tile_n(const GemmDesc& d);
 int64_t split_plane_elems(int nrow_bits, int nk_bits);
-cudaError_t launch_gemm_tma(const uint16_t* Ap, int nza, const uint16_t* Bp, int nzb, float2* C, const GemmDesc& d,
-                            const int zflags[4], bool bf16, float inv_scale, int* err, cudaStream_t s);
+cudaError_t launch_gemm_tma(const PlaneOperand& a, const PlaneOperand& b, float2* C, bool c_planes, const GemmDesc& d,
+                            bool bf16, float inv_scale, int* err, cudaStream_t s);
+// Split operand A (which_b = false) or B of d into `scratch` (returned planes).
+int64_t split_scratch_elems(const GemmDesc& d, bool which_b);
+cudaError_t split_operand(const float2* src, const GemmDesc& d, bool which_b, bool bf16, uint16_t* scratch,
+                          PlaneOperand& out, cudaStream_t s);
+// Plane operand of a tensor a producer epilogue already wrote as planes
+// (layout [rows][K], K >= 32); false when the step's view does not match.
+bool planes_in_place(const float2* base, const GemmDesc& d, bool which_b, PlaneOperand& out);
 // Split both operands of d into `scratch` (>= tc2_scratch_elems(d) 16-bit
 // values) and run the TMA GEMM.
 int64_t tc2_scratch_elems(const GemmDesc& d);
