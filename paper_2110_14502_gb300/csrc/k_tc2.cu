@@ -280,6 +280,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (go) {
       const int r = q * 32 + lane;
       const int32_t ro = rowC[r];
+      // the tile's first four column bits are C's four fastest indices: each
+      // thread's 16 columns form one contiguous run (16-element aligned)
+      const bool n16 = d.nn >= 4 && d.cn[0] == 1 && d.cn[1] == 2 && d.cn[2] == 4 && d.cn[3] == 8;
 #pragma unroll 1
       for (int c0 = 0; c0 < TN; c0 += 16) {
         uint32_t vr[16], vi[16];
@@ -293,20 +296,39 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             // 16-bit planes {re_hi, re_lo, im_hi, im_lo} at the same offsets
             uint16_t* P = reinterpret_cast<uint16_t*>(C);
             const int64_t plane = int64_t(1) << (d.nm + d.nn);
+            uint16_t h[4][16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-              const int32_t co = colC[c0 + j];
-              if (co < 0) continue;
-              const float re = __uint_as_float(vr[j]) * inv_scale, im = __uint_as_float(vi[j]) * inv_scale;
-              uint16_t rh, rl, ih, il;
-              split16<BF16>(re, rh, rl);
-              split16<BF16>(im, ih, il);
-              const int64_t o = (int64_t)ro + co;
-              P[o] = rh;
-              P[plane + o] = rl;
-              P[2 * plane + o] = ih;
-              P[3 * plane + o] = il;
+              split16<BF16>(__uint_as_float(vr[j]) * inv_scale, h[0][j], h[1][j]);
+              split16<BF16>(__uint_as_float(vi[j]) * inv_scale, h[2][j], h[3][j]);
             }
+            if (n16 && colC[c0] >= 0) {
+              // 16 consecutive columns are contiguous: two 16-byte stores per plane
+              const int64_t o = (int64_t)ro + colC[c0];
+#pragma unroll
+              for (int p = 0; p < 4; ++p) {
+                uint4* q = reinterpret_cast<uint4*>(P + p * plane + o);
+                q[0] = make_uint4(h[p][0] | (h[p][1] << 16), h[p][2] | (h[p][3] << 16), h[p][4] | (h[p][5] << 16),
+                                  h[p][6] | (h[p][7] << 16));
+                q[1] = make_uint4(h[p][8] | (h[p][9] << 16), h[p][10] | (h[p][11] << 16),
+                                  h[p][12] | (h[p][13] << 16), h[p][14] | (h[p][15] << 16));
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                const int32_t co = colC[c0 + j];
+                if (co < 0) continue;
+                const int64_t o = (int64_t)ro + co;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) P[p * plane + o] = h[p][j];
+              }
+            }
+          } else if (n16 && colC[c0] >= 0) {
+            float4* q = reinterpret_cast<float4*>(C + (int64_t)ro + colC[c0]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              q[j] = make_float4(__uint_as_float(vr[2 * j]) * inv_scale, __uint_as_float(vi[2 * j]) * inv_scale,
+                                 __uint_as_float(vr[2 * j + 1]) * inv_scale, __uint_as_float(vi[2 * j + 1]) * inv_scale);
           } else {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {

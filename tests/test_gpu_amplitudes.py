@@ -128,6 +128,10 @@ def test_full_size_6x6_sampled_slices_vs_oracle():
         fixed = {wires[j]: (s >> j) & 1 for j in range(len(wires))}
         ref = replay(p, gates, n, bits, open_q, fixed)
         assert rel(got, ref) <= 1e-5, s
+        # the tensor-core path (bf16 hi+lo split, operand planes handed from
+        # producer to consumer) on the same slice: the split-precision bound
+        got = p.contract_amplitudes(words[:1], slice_begin=s, slice_count=1, precision="split_bf16")[0]
+        assert rel(got, ref) <= 1e-4, s
 
 
 def test_split_bf16_path_vs_statevector():
