@@ -595,19 +595,42 @@ tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& P) {
   // contiguous K runs from both operands -- the permutation of the next step
   // is folded into this step's epilogue.
   {
+    // label sets of every SSA id (order-free) to tell a step's two sides apart
+    std::vector<LSet> sets(L + P.steps.size());
+    for (int i = 0; i < L; ++i) { sets[i] = order[i]; std::sort(sets[i].begin(), sets[i].end()); }
+    for (size_t s = 0; s < P.steps.size(); ++s) {
+      sets[L + s] = P.steps[s].lc;
+      std::sort(sets[L + s].begin(), sets[L + s].end());
+    }
     for (int t = (int)P.steps.size() - 1; t >= 0; --t) {
       Step& S = P.steps[t];
-      LSet kt;  // contracted labels, ordered like the leaf operand if there is one
+      const LSet& ct = order[L + t];  // final layout of this step's output
+      LSet kt;
       const int leaf_op = S.a < L ? S.a : (S.b < L ? S.b : -1);
-      const LSet& ref = leaf_op >= 0 ? order[leaf_op] : order[S.a];
-      const LSet& other = leaf_op >= 0 ? (leaf_op == S.a ? order[S.b] : order[S.a]) : order[S.b];
-      for (int l : ref)
-        if (std::find(other.begin(), other.end(), l) != other.end()) kt.push_back(l);
+      if (leaf_op >= 0) {
+        // a leaf keeps its layout: the contracted indices follow its order
+        const LSet& other = leaf_op == S.a ? order[S.b] : order[S.a];
+        for (int l : order[leaf_op])
+          if (std::find(other.begin(), other.end(), l) != other.end()) kt.push_back(l);
+      } else {
+        // contracted indices, innermost the ones that come from the larger side
+        // of the larger operand's producer (its epilogue then writes one run)
+        const int p = S.a - L;
+        const LSet& sa = sets[P.steps[p].a];
+        LSet from_a, from_b;
+        for (int l : order[S.a])
+          if (std::binary_search(sets[S.b].begin(), sets[S.b].end(), l))
+            (std::binary_search(sa.begin(), sa.end(), l) ? from_a : from_b).push_back(l);
+        if (from_a.size() >= from_b.size()) { kt = from_b; kt.insert(kt.end(), from_a.begin(), from_a.end()); }
+        else { kt = from_a; kt.insert(kt.end(), from_b.begin(), from_b.end()); }
+      }
       for (int x : {S.a, S.b}) {
         if (x < L) continue;
+        // free indices in the order they take in this step's output, so the
+        // GEMM's row / column bits follow the output's memory order
         LSet nl;
-        for (int l : order[x])
-          if (std::find(kt.begin(), kt.end(), l) == kt.end()) nl.push_back(l);
+        for (int l : ct)
+          if (std::binary_search(sets[x].begin(), sets[x].end(), l)) nl.push_back(l);
         nl.insert(nl.end(), kt.begin(), kt.end());
         order[x] = nl;
         P.steps[x - L].lc = nl;
