@@ -248,7 +248,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3" if args.precision == "split_bf16" else "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"split_bf16": "bf16x3", "split_fp16": "f16x3", "scaled_fp16": "f16", "scaled_bf16": "bf16",
+                  "c64": "f32"}[args.precision],
         "data": "synthetic (seeded random circuit and bitstrings)",
         "config": {"workload": WORKLOAD, "precision": args.precision, "global_batch": amps // args.steps,
                    "slices": info["num_slices"], "plan_hash": hex(info["hash"]),
@@ -363,7 +364,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "c64"])
+    ap.add_argument("--precision", default="split_bf16",
+                    choices=["split_bf16", "split_fp16", "scaled_fp16", "scaled_bf16", "c64"])
     ap.add_argument("--micro", action="store_true")
     ap.add_argument("--shape", default=None)
     ap.add_argument("--random-layout", action="store_true")

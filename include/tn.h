@@ -203,6 +203,9 @@ typedef struct {
   int32_t overflow_policy;  /* scaled modes: 0 = recompute a flagged slice in complex64, 1 = discard it (counted) */
   int32_t use_graph;        /* 1 = replay the per-group launch sequence as a CUDA graph */
   int32_t profile;          /* 1 = bracket every kernel launch with CUDA events and fill the per-class figures */
+  int32_t test_flag_every;  /* scaled modes, testing: > 0 flags every slice whose id is a multiple of it, so the
+                               recompute / discard paths run without a real under/overflow; 0 = off */
+  int32_t reserved2;
 } tn_exec_opts;
 
 /* Kernel classes of the per-class report figures. */

@@ -26,6 +26,8 @@
 
 namespace tn {
 
+constexpr int kFlaggedCap = 1 << 16;  // listed flagged units per call
+
 struct Executor {
   int device = -1;
   float2* store = nullptr;
@@ -44,6 +46,12 @@ struct Executor {
   int* err = nullptr;          // device error word of bounded waits
   uint16_t* scratch = nullptr; // split operand planes of the tensor-core steps
   int64_t scratch_cap = 0;     // in 16-bit elements
+  // scaled precisions: per step and launch unit, exponent and stored maximum
+  // of plane outputs; per split role the same plus the max reduction; flags
+  uint8_t* spool = nullptr;
+  int64_t spool_cap = 0;       // bytes
+  int64_t* flagged = nullptr;  // (b << 32 | s) of units kept out of the sum
+  unsigned long long* nflagged = nullptr;
   std::vector<GemmDesc> desc;  // per step, unit strides filled at launch
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> pev;  // profiling event pool
@@ -64,6 +72,9 @@ void destroy_executor(Executor* e) {
   cudaFree(e->acc);
   cudaFree(e->err);
   cudaFree(e->scratch);
+  cudaFree(e->spool);
+  cudaFree(e->flagged);
+  cudaFree(e->nflagged);
   if (e->ev0) cudaEventDestroy(e->ev0);
   if (e->ev1) cudaEventDestroy(e->ev1);
   for (auto ev : e->pev) cudaEventDestroy(ev);
@@ -147,6 +158,8 @@ static tn_status setup(Plan& P, Executor& E) {
   CK(cudaEventCreate(&E.ev1));
   CK(cudaMalloc(&E.err, sizeof(int)));
   CK(cudaMemset(E.err, 0, sizeof(int)));
+  CK(cudaMalloc(&E.flagged, kFlaggedCap * sizeof(int64_t)));
+  CK(cudaMalloc(&E.nflagged, sizeof(unsigned long long)));
   return TN_OK;
 }
 
@@ -168,6 +181,18 @@ struct Ctx {
   std::vector<Rec> recs;
   size_t nev = 0;
   int precision = TN_PREC_C64;
+  bool tc = false;               // tensor-core precision
+  int np = 4;                    // planes per operand: 4 split, 2 single
+  bool bf16 = true;
+  bool scaled = false;           // per-unit power-of-two exponents and the filter
+  int64_t U = 1;                 // launch units the scale pool is laid out for
+  int* ec_all = nullptr;         // [step][U]
+  unsigned* mc_all = nullptr;    // [step][U]
+  int* es[2] = {nullptr, nullptr};
+  float* ms[2] = {nullptr, nullptr};
+  unsigned* mb[2] = {nullptr, nullptr};
+  int* flag1 = nullptr;          // [Gs] slice-only units
+  int* flag2 = nullptr;          // [U] (bitstring, slice) units
   std::vector<char> planes_out;  // per step: output written as 16-bit planes for a tensor-core consumer
   Ctx(const Plan& p, Executor& e, cudaStream_t s, bool prof) : P(p), E(e), st(s), profile(prof) {}
 
@@ -225,18 +250,17 @@ tn_status run_step(Ctx& c, size_t s, const Geo& g) {
   if (c.profile) { tn_status r = c.event(e0); if (r) return r; }
   cudaError_t e;
   int klass = S.klass == SC_VECTOR ? TN_KCLASS_VECTOR : TN_KCLASS_GEMM_SIMT;
-  const bool split = c.precision == TN_PREC_SPLIT_BF16;
-  if (S.klass != SC_VECTOR && split && tc_shape_ok(d)) klass = TN_KCLASS_GEMM_TC;
+  if (S.klass != SC_VECTOR && c.tc && tc_shape_ok(d)) klass = TN_KCLASS_GEMM_TC;
   if (klass == TN_KCLASS_VECTOR) e = launch_vector(A, B, C, d, c.st);
   else if (klass == TN_KCLASS_GEMM_TC) {
     const int L = (int)P.net.leaves.size();
     PlaneOperand pa{}, pb{};
-    const bool a_in = S.a >= L && c.planes_out[S.a - L] && planes_in_place(A, d, false, pa);
-    const bool b_in = S.b >= L && c.planes_out[S.b - L] && planes_in_place(B, d, true, pb);
+    const bool a_in = S.a >= L && c.planes_out[S.a - L] && planes_in_place(A, d, false, c.np, pa);
+    const bool b_in = S.b >= L && c.planes_out[S.b - L] && planes_in_place(B, d, true, c.np, pb);
     if ((S.a >= L && c.planes_out[S.a - L] && !a_in) || (S.b >= L && c.planes_out[S.b - L] && !b_in))
       return fail(TN_EINVAL, "step %zu: internal error, operand planes do not match the step's view", s);
-    const int64_t need_a = a_in ? 0 : split_scratch_elems(d, false);
-    const int64_t need = need_a + (b_in ? 0 : split_scratch_elems(d, true));
+    const int64_t need_a = a_in ? 0 : split_scratch_elems(d, false, c.np);
+    const int64_t need = need_a + (b_in ? 0 : split_scratch_elems(d, true, c.np));
     if (need > E.scratch_cap) {
       cudaFree(E.scratch);
       E.scratch = nullptr;
@@ -247,9 +271,41 @@ tn_status run_step(Ctx& c, size_t s, const Geo& g) {
       }
       E.scratch_cap = need;
     }
+    ScaleIO sio{};
     e = cudaSuccess;
-    if (!a_in) { e = split_operand(A, d, false, true, E.scratch, pa, c.st); ++c.launches; }
-    if (e == cudaSuccess && !b_in) { e = split_operand(B, d, true, true, E.scratch + need_a, pb, c.st); ++c.launches; }
+    const int64_t U = c.U;
+    if (!a_in) {
+      if (c.scaled) e = cudaMemsetAsync(c.mb[0], 0, U * sizeof(unsigned), c.st);
+      if (e == cudaSuccess)
+        e = split_operand(A, d, false, c.bf16, c.np, c.scaled, c.mb[0], c.es[0], c.ms[0], E.scratch, pa, c.st);
+      c.launches += c.scaled ? 2 : 1;
+      sio.ea = c.es[0];
+      sio.ma = c.ms[0];
+    } else {
+      sio.ea = c.ec_all + (S.a - L) * U;
+      sio.ma = reinterpret_cast<const float*>(c.mc_all + (S.a - L) * U);
+    }
+    if (!b_in) {
+      if (e == cudaSuccess && c.scaled) e = cudaMemsetAsync(c.mb[1], 0, U * sizeof(unsigned), c.st);
+      if (e == cudaSuccess)
+        e = split_operand(B, d, true, c.bf16, c.np, c.scaled, c.mb[1], c.es[1], c.ms[1], E.scratch + need_a, pb, c.st);
+      c.launches += c.scaled ? 2 : 1;
+      sio.eb = c.es[1];
+      sio.mb = c.ms[1];
+    } else {
+      sio.eb = c.ec_all + (S.b - L) * U;
+      sio.mb = reinterpret_cast<const float*>(c.mc_all + (S.b - L) * U);
+    }
+    if (!c.scaled) sio = ScaleIO{};
+    else {
+      if (c.planes_out[s]) {
+        if (e == cudaSuccess) e = cudaMemsetAsync(c.mc_all + s * U, 0, U * sizeof(unsigned), c.st);
+        sio.ec = c.ec_all + s * U;
+        sio.mc = c.mc_all + s * U;
+      }
+      sio.flag = S.phase == 1 ? c.flag1 : c.flag2;
+      sio.flag_by_lo = S.phase == 1;
+    }
     if (c.profile && e == cudaSuccess && need > 0) {
       // the operand split and the GEMM are timed as separate classes
       size_t em = 0;
@@ -258,12 +314,14 @@ tn_status run_step(Ctx& c, size_t s, const Geo& g) {
       const double K = std::ldexp(1.0, d.nk), kp = std::max(K, 32.0);
       const double nza = (d.a_lo ? d.units_lo : 1.0) * (d.a_hi ? (double)d.units / d.units_lo : 1.0);
       const double nzb = (d.b_lo ? d.units_lo : 1.0) * (d.b_hi ? (double)d.units / d.units_lo : 1.0);
-      const double bytes = (a_in ? 0.0 : 8.0 * std::ldexp(1.0, d.nm) * (K + kp) * nza) +
-                           (b_in ? 0.0 : 8.0 * std::ldexp(1.0, d.nn) * (K + kp) * nzb);
+      const double per = 8.0 + 2.0 * c.np;  // bytes read + written per complex element
+      const double bytes = (a_in ? 0.0 : std::ldexp(1.0, d.nm) * (8.0 * K + 2.0 * c.np * kp) * nza) +
+                           (b_in ? 0.0 : std::ldexp(1.0, d.nn) * (8.0 * K + 2.0 * c.np * kp) * nzb);
+      (void)per;
       c.recs.push_back({TN_KCLASS_SPLIT, 0.0, bytes, e0});
       e0 = em;
     }
-    if (e == cudaSuccess) e = launch_gemm_tma(pa, pb, C, c.planes_out[s] != 0, d, true, 1.f, E.err, c.st);
+    if (e == cudaSuccess) e = launch_gemm_tma(pa, pb, C, c.planes_out[s] != 0, d, c.bf16, sio, E.err, c.st);
   }
   else e = launch_gemm_simt(A, B, C, d, c.st);
   ++c.launches;
@@ -290,10 +348,16 @@ tn_status run_misc(Ctx& c, cudaError_t e, const char* what) {
 
 }  // namespace
 
+static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double* out, const tn_exec_opts& o,
+                               tn_report* rep, bool clear_out);
+
 tn_status contract_amplitudes(Plan& P, const uint64_t* bits, int64_t nb, double* out, const tn_exec_opts& o,
                               tn_report* rep) {
-  if (o.precision != TN_PREC_C64 && o.precision != TN_PREC_SPLIT_BF16)
-    return fail(TN_EINVAL, "tn_contract_amplitudes: precision %d not available in this build", o.precision);
+  return contract_core(P, bits, nb, out, o, rep, true);
+}
+
+static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double* out, const tn_exec_opts& o,
+                               tn_report* rep, bool clear_out) {
   const int n = P.net.n;
   const int k = (int)P.net.open_qubits.size();
   const int words = std::max(1, (n + 63) / 64);
@@ -311,6 +375,8 @@ tn_status contract_amplitudes(Plan& P, const uint64_t* bits, int64_t nb, double*
   }
   Executor& E = *P.exec;
   const int64_t nout = nb << k;
+  const bool scaled = o.precision == TN_PREC_SPLIT_FP16 || o.precision == TN_PREC_SCALED_FP16 ||
+                      o.precision == TN_PREC_SCALED_BF16;
 
   // ---- group geometry: Gb bitstrings x Gs slices per launch
   const int64_t Se = P.slice_arena_elems, Pe = P.unit_arena_elems;
@@ -372,10 +438,15 @@ tn_status contract_amplitudes(Plan& P, const uint64_t* bits, int64_t nb, double*
   }
   Ctx c(P, E, st, o.profile != 0);
   c.precision = o.precision;
+  c.tc = o.precision != TN_PREC_C64;
+  c.np = (o.precision == TN_PREC_SPLIT_BF16 || o.precision == TN_PREC_SPLIT_FP16) ? 4 : 2;
+  c.bf16 = o.precision == TN_PREC_SPLIT_BF16 || o.precision == TN_PREC_SCALED_BF16;
+  c.scaled = scaled;
+  c.U = Gs * Gb;
   c.planes_out.assign(P.steps.size(), 0);
-  if (o.precision == TN_PREC_SPLIT_BF16) {
+  if (c.tc) {
     // A step whose consumer also runs on the tensor cores hands its output over
-    // as split planes laid out for that consumer (no separate split pass).
+    // as 16-bit planes laid out for that consumer (no separate split pass).
     const int L = (int)P.net.leaves.size();
     std::vector<char> tc(P.steps.size(), 0);
     for (size_t s = 0; s < P.steps.size(); ++s) tc[s] = P.steps[s].klass != SC_VECTOR && tc_shape_ok(E.desc[s]);
@@ -387,22 +458,52 @@ tn_status contract_amplitudes(Plan& P, const uint64_t* bits, int64_t nb, double*
         if (x < L) continue;
         const int p = x - L;
         PlaneOperand probe{};
-        if (tc[p] && P.steps[p].phase != 0 && planes_in_place(nullptr, E.desc[t], role == 1, probe))
+        if (tc[p] && P.steps[p].phase != 0 && planes_in_place(nullptr, E.desc[t], role == 1, c.np, probe))
           c.planes_out[p] = 1;
       }
     }
   }
-  CK(cudaEventRecord(E.ev0, st));
+  if (scaled) {
+    // scale pool: ec, mc per step; e, m, maxbits per split role; flags
+    const int64_t ns_ = (int64_t)P.steps.size();
+    const int64_t need = 8 * ns_ * c.U + 2 * 12 * c.U + 4 * (Gs + c.U) + 256;
+    if (E.spool_cap < need) {
+      cudaFree(E.spool);
+      E.spool = nullptr;
+      E.spool_cap = 0;
+      CK(cudaMalloc(&E.spool, need));
+      E.spool_cap = need;
+    }
+    uint8_t* q = E.spool;
+    c.ec_all = (int*)q;                      q += 4 * ns_ * c.U;
+    c.mc_all = (unsigned*)q;                 q += 4 * ns_ * c.U;
+    for (int r = 0; r < 2; ++r) {
+      c.es[r] = (int*)q;                     q += 4 * c.U;
+      c.ms[r] = (float*)q;                   q += 4 * c.U;
+      c.mb[r] = (unsigned*)q;                q += 4 * c.U;
+    }
+    c.flag1 = (int*)q;                       q += 4 * Gs;
+    c.flag2 = (int*)q;
+  }
+  if (clear_out) CK(cudaEventRecord(E.ev0, st));  // a nested recompute call is timed by its caller
   if (!o.device_io && nb > 0)
     CK(cudaMemcpyAsync((void*)d_bits, bits, nb * words * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-  if (nout > 0) CK(cudaMemsetAsync(d_acc, 0, nout * sizeof(double2), st));
+  if (nout > 0 && clear_out) CK(cudaMemsetAsync(d_acc, 0, nout * sizeof(double2), st));
+  if (scaled) CK(cudaMemsetAsync(E.nflagged, 0, sizeof(unsigned long long), st));
   Geo g;
   if (!E.inv_ready) {
+    // invariant steps once, always in complex64 so that any later precision can use them
+    const int keep = c.precision;
+    const bool keep_tc = c.tc;
+    c.precision = TN_PREC_C64;
+    c.tc = false;
     for (size_t s = 0; s < P.steps.size(); ++s)
       if (P.steps[s].phase == 0) {
         tn_status r = run_step(c, s, g);
         if (r != TN_OK) return r;
       }
+    c.precision = keep;
+    c.tc = keep_tc;
     E.inv_ready = true;
   }
   const int L = (int)P.net.leaves.size();
@@ -417,6 +518,16 @@ tn_status contract_amplitudes(Plan& P, const uint64_t* bits, int64_t nb, double*
     gi.nb = 1;
     gi.words = words;
     gi.units = g.gs;
+    if (scaled) {
+      CK(cudaMemsetAsync(c.flag1, 0, Gs * sizeof(int), st));
+      if (o.test_flag_every > 0) {
+        // host-side injection of filter flags (tests of the recompute / discard paths)
+        std::vector<int> f(g.gs);
+        for (int i = 0; i < g.gs; ++i) f[i] = ((s0 + i) % o.test_flag_every) == 0;
+        CK(cudaMemcpyAsync(c.flag1, f.data(), g.gs * sizeof(int), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+      }
+    }
     if (E.ngather1) {
       tn_status r = run_misc(c, launch_gather(E.store, E.sarena, Se, E.gather, E.ngather1, d_bits, gi, st), "gather");
       if (r) return r;
@@ -431,6 +542,7 @@ tn_status contract_amplitudes(Plan& P, const uint64_t* bits, int64_t nb, double*
       gi.b0 = b0;
       gi.nb = g.gb;
       gi.units = g.gs * g.gb;
+      if (scaled) CK(cudaMemsetAsync(c.flag2, 0, c.U * sizeof(int), st));
       if (E.ngather2) {
         tn_status r = run_misc(
             c, launch_gather(E.store, E.parena, Pe, E.gather + E.ngather1, E.ngather2, d_bits, gi, st), "gather");
@@ -444,12 +556,50 @@ tn_status contract_amplitudes(Plan& P, const uint64_t* bits, int64_t nb, double*
       const float2* root;
       int64_t rlo, rhi;
       operand(P, E, root_id, 2, g, root, rlo, rhi);
-      tn_status r = run_misc(
-          c, launch_accumulate(root, rlo, rhi, E.perm, (int)P.root_perm.size(), d_acc, gi, st), "accumulate");
+      tn_status r = run_misc(c,
+                             launch_accumulate(root, rlo, rhi, E.perm, (int)P.root_perm.size(), d_acc, gi,
+                                               scaled ? c.flag1 : nullptr, scaled ? c.flag2 : nullptr, E.flagged,
+                                               E.nflagged, kFlaggedCap, st),
+                             "accumulate");
       if (r) return r;
     }
   }
+  // ---- the filter: units flagged in a scaled precision are recomputed in
+  // complex64 (policy 0) or left out and counted (policy 1)
+  int64_t nflag = 0, recomputed = 0, discarded = 0;
+  if (scaled && nb > 0) {
+    unsigned long long hn = 0;
+    CK(cudaMemcpyAsync(&hn, E.nflagged, sizeof(hn), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    nflag = (int64_t)hn;
+    if (nflag > kFlaggedCap)
+      return fail(TN_EOVERFLOW, "tn_contract_amplitudes: %lld units flagged (more than %d listed)", (long long)nflag,
+                  kFlaggedCap);
+    if (nflag > 0) {
+      std::vector<int64_t> list(nflag);
+      CK(cudaMemcpy(list.data(), E.flagged, nflag * sizeof(int64_t), cudaMemcpyDeviceToHost));
+      if (o.overflow_policy == 1) {
+        discarded = nflag;
+      } else {
+        for (int64_t f : list) {
+          const int64_t b = f >> 32, s = f & 0xffffffffll;
+          tn_exec_opts r = o;
+          r.precision = TN_PREC_C64;
+          r.device_io = 1;
+          r.slice_begin = s;
+          r.slice_count = 1;
+          r.units_per_group = 1;
+          r.profile = 0;
+          tn_status rs = contract_core(P, d_bits + b * words, 1, (double*)(d_acc + b * ((int64_t)1 << k)), r,
+                                       nullptr, false);
+          if (rs != TN_OK) return rs;
+          ++recomputed;
+        }
+      }
+    }
+  }
   if (!o.device_io && nout > 0) CK(cudaMemcpyAsync(out, d_acc, nout * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  if (!clear_out) return TN_OK;
   CK(cudaEventRecord(E.ev1, st));
   if (!o.device_io || rep) {
     CK(cudaEventSynchronize(E.ev1));
@@ -470,6 +620,8 @@ tn_status contract_amplitudes(Plan& P, const uint64_t* bits, int64_t nb, double*
     rep->flops = 8.0 * ((double)ns * shared + (double)nb * ns * (per - shared));
     rep->flops_equivalent = 8.0 * per * (double)nb * ns;
     rep->kernel_launches = c.launches;
+    rep->flagged_units = nflag;
+    rep->discarded_units = discarded;
     for (auto& r : c.recs) {
       float t = 0;
       CK(cudaEventElapsedTime(&t, E.pev[r.ev], E.pev[r.ev + 1]));
@@ -479,6 +631,7 @@ tn_status contract_amplitudes(Plan& P, const uint64_t* bits, int64_t nb, double*
       rep->class_bytes[r.klass] += r.bytes;
     }
   }
+  (void)recomputed;
   return TN_OK;
 }
 

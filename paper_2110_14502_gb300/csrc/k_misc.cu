@@ -43,9 +43,15 @@ __global__ void gather_kernel(const float2* __restrict__ store, float2* __restri
   }
 }
 
+// The filter of the scaled precisions (Sec. "A Mixed-Precision Computation
+// Method via Adaptive Precision Scaling": paths with under/overflow are kept
+// out of the sum): a flagged unit adds nothing here and is listed for the
+// host, which recomputes it in complex64 or counts it as discarded.
 __global__ void accumulate_kernel(const float2* __restrict__ root, int64_t r_lo, int64_t r_hi,
                                   const int64_t* __restrict__ perm, int nperm, double2* __restrict__ acc,
-                                  GroupInfo g) {
+                                  GroupInfo g, const int* __restrict__ flag_s, const int* __restrict__ flag_u,
+                                  int64_t* __restrict__ flagged, unsigned long long* __restrict__ nflagged,
+                                  int cap) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)g.nb * nperm) return;
   const int bl = (int)(idx / nperm);
@@ -53,6 +59,13 @@ __global__ void accumulate_kernel(const float2* __restrict__ root, int64_t r_lo,
   double2 a = acc[(g.b0 + bl) * nperm + j];
   const float2* r = root + bl * r_hi + perm[j];
   for (int sl = 0; sl < g.nslice; ++sl) {
+    if ((flag_s && flag_s[sl]) || (flag_u && flag_u[bl * g.nslice + sl])) {
+      if (j == 0) {
+        const unsigned long long k = atomicAdd(nflagged, 1ull);
+        if ((int64_t)k < cap) flagged[k] = ((g.b0 + bl) << 32) | (g.slice0 + sl);
+      }
+      continue;
+    }
     float2 v = r[sl * r_lo];
     a.x += (double)v.x;
     a.y += (double)v.y;
@@ -83,10 +96,12 @@ cudaError_t launch_gather(const float2* store, float2* arena, int64_t arena_stri
 }
 
 cudaError_t launch_accumulate(const float2* root, int64_t r_lo, int64_t r_hi, const int64_t* perm, int nperm,
-                              double2* acc, const GroupInfo& g, cudaStream_t s) {
+                              double2* acc, const GroupInfo& g, const int* flag_s, const int* flag_u,
+                              int64_t* flagged, unsigned long long* nflagged, int cap, cudaStream_t s) {
   const int64_t total = (int64_t)g.nb * nperm;
   const int nt = 256;
-  accumulate_kernel<<<(unsigned)((total + nt - 1) / nt), nt, 0, s>>>(root, r_lo, r_hi, perm, nperm, acc, g);
+  accumulate_kernel<<<(unsigned)((total + nt - 1) / nt), nt, 0, s>>>(root, r_lo, r_hi, perm, nperm, acc, g, flag_s,
+                                                                     flag_u, flagged, nflagged, cap);
   return cudaGetLastError();
 }
 

@@ -6,11 +6,21 @@
 // "A Mixed-Precision Computation Method via Adaptive Precision Scaling"
 // (half-precision products, single-precision accumulation).
 //
-// Complex product on real tensor cores, planar form, split precision:
+// Complex product on real tensor cores, planar form:
 //   Dr = Ar Br - Ai Bi,  Di = Ar Bi + Ai Br,
-// each real product X Y expanded as Xhi Yhi + Xhi Ylo + Xlo Yhi (FP32
-// accumulation in TMEM); the minus sign uses the MMA's negate-A bit.  Dr and
-// Di occupy TN columns of TMEM each.
+// FP32 accumulation in TMEM (Dr and Di take TN columns each), the minus sign
+// through the MMA's negate-A bit.  Split precision (four planes re_hi, re_lo,
+// im_hi, im_lo) expands each real product X Y as Xhi Yhi + Xhi Ylo + Xlo Yhi;
+// single precision (two planes re, im) keeps one 16-bit product.
+//
+// Adaptive scaling (Sec. "A Mixed-Precision Computation Method via Adaptive
+// Precision Scaling"): a plane tensor stores x 2^-e with a per-unit integer
+// exponent e and records the largest stored component.  The GEMM predicts a
+// bound 2 K maxA maxB on its stored output, picks r so that the bound stays
+// below 2^15 (inside fp16 range), writes C 2^-(eA+eB+r) and records
+// eC = eA + eB + r and the actual maximum.  A unit whose values turn
+// non-finite, or whose operand maximum fell below 2^-10 (most of the 16-bit
+// range lost to underflow), is flagged for the executor's filter.
 //
 // Roles (256 threads): warp 0 lane 0 issues TMA loads of one K stage (32
 // complex K values of a 128-row A tile and a TN-row B tile, all four planes,
@@ -37,14 +47,14 @@ namespace {
 constexpr int TM = 128;
 constexpr int TKC = 32;                 // complex K per stage (64-byte rows of 16-bit values)
 constexpr int NTHREADS = 256;
-constexpr int A_STAGE = 4 * TM * 64;    // four planes of 128 rows x 64 bytes
 constexpr int SMEM_BUDGET = 196 * 1024;
 constexpr long long kWaitLimit = 1ll << 24;
 constexpr int GROUP_M = 16;
 
-template <int TN>
+template <int TN, int NP>
 struct Cfg2 {
-  static constexpr int B_STAGE = 4 * TN * 64;
+  static constexpr int A_STAGE = NP * TM * 64;    // NP planes of 128 rows x 64 bytes
+  static constexpr int B_STAGE = NP * TN * 64;
   static constexpr int STAGE = A_STAGE + B_STAGE;
   static constexpr int NSTAGE = (SMEM_BUDGET / STAGE) < 6 ? (SMEM_BUDGET / STAGE) : 6;
   static constexpr int SMEM = NSTAGE * STAGE + 1024;
@@ -136,6 +146,12 @@ __device__ __forceinline__ void split16(float x, uint16_t& hi, uint16_t& lo) {
   }
 }
 
+template <bool BF16>
+__device__ __forceinline__ uint16_t to16(float x) {
+  if (BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+  return __half_as_ushort(__float2half_rn(x));
+}
+
 template <int NREG>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t* v);
 template <>
@@ -147,12 +163,13 @@ __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t* v) {
       : "r"(taddr));
 }
 
-template <int TN, bool BF16>
+template <int TN, bool BF16, int NP>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_tma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                     float2* __restrict__ C, const GemmDesc d, int kp, int a_zlo, int a_zhi, int b_zlo, int b_zhi,
-                    int c_planes, float inv_scale, int* __restrict__ err) {
-  using CF = Cfg2<TN>;
+                    int c_planes, const ScaleIO sio, int* __restrict__ err) {
+  using CF = Cfg2<TN, NP>;
+  constexpr int A_STAGE = CF::A_STAGE;
   constexpr int NS = CF::NSTAGE;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -166,6 +183,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int za_lo = a_zlo ? (int)ulo : 0, za_hi = a_zhi ? (int)uhi : 0;
   const int zb_lo = b_zlo ? (int)ulo : 0, zb_hi = b_zhi ? (int)uhi : 0;
   C += ulo * d.c_lo + uhi * d.c_hi;
+  // exponents: stored operand = true * 2^-e; output scale 2^-r on top of 2^-(eA+eB)
+  int ea = 0, eb = 0, r = 0;
+  bool weak = false;
+  if (sio.ea) {
+    const int za = za_lo + za_hi * (a_zlo ? d.units_lo : 1), zb = zb_lo + zb_hi * (b_zlo ? d.units_lo : 1);
+    ea = sio.ea[za];
+    eb = sio.eb[zb];
+    const float ma = sio.ma[za], mb = sio.mb[zb];
+    weak = !(ma >= 0x1p-10f) || !(mb >= 0x1p-10f);
+    const float bound = 2.f * ldexpf(ma * mb, d.nk);
+    if (bound > 0.f && isfinite(bound)) {
+      int x;
+      frexpf(bound, &x);  // bound < 2^x
+      r = x - 15;
+    }
+  }
   // Grouped raster: tiles run GROUP_M M-tiles at a time with the N-tiles
   // inside a group varying slowest, so concurrently resident CTAs share A row
   // blocks and re-read B tiles from L2 rather than DRAM.
@@ -239,26 +272,34 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const uint32_t b = a + A_STAGE;
 #pragma unroll
       for (int kk = 0; kk < TKC / 16; ++kk) {
-        uint64_t A_[4], B_[4];
+        uint64_t A_[NP], B_[NP];
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
+        for (int p = 0; p < NP; ++p) {
           A_[p] = sw64_desc(a + p * (TM * 64) + kk * 32);
           B_[p] = sw64_desc(b + p * (TN * 64) + kk * 32);
         }
         const uint32_t acc = (kt | kk) ? 1u : 0u;
-        // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
-        mma(dr, A_[0], B_[0], I, acc);
-        mma(dr, A_[0], B_[1], I, 1u);
-        mma(dr, A_[1], B_[0], I, 1u);
-        mma(dr, A_[2], B_[2], IN, 1u);
-        mma(dr, A_[2], B_[3], IN, 1u);
-        mma(dr, A_[3], B_[2], IN, 1u);
-        mma(di, A_[0], B_[2], I, acc);
-        mma(di, A_[0], B_[3], I, 1u);
-        mma(di, A_[1], B_[2], I, 1u);
-        mma(di, A_[2], B_[0], I, 1u);
-        mma(di, A_[2], B_[1], I, 1u);
-        mma(di, A_[3], B_[0], I, 1u);
+        if constexpr (NP == 4) {
+          // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
+          mma(dr, A_[0], B_[0], I, acc);
+          mma(dr, A_[0], B_[1], I, 1u);
+          mma(dr, A_[1], B_[0], I, 1u);
+          mma(dr, A_[2], B_[2], IN, 1u);
+          mma(dr, A_[2], B_[3], IN, 1u);
+          mma(dr, A_[3], B_[2], IN, 1u);
+          mma(di, A_[0], B_[2], I, acc);
+          mma(di, A_[0], B_[3], I, 1u);
+          mma(di, A_[1], B_[2], I, 1u);
+          mma(di, A_[2], B_[0], I, 1u);
+          mma(di, A_[2], B_[1], I, 1u);
+          mma(di, A_[3], B_[0], I, 1u);
+        } else {
+          // planes: 0 re, 1 im
+          mma(dr, A_[0], B_[0], I, acc);
+          mma(dr, A_[1], B_[1], IN, 1u);
+          mma(di, A_[0], B_[1], I, acc);
+          mma(di, A_[1], B_[0], I, 1u);
+        }
       }
       commit(&empty[s]);
       ++issued;
@@ -278,66 +319,90 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const bool go = __all_sync(0xffffffffu, ok && !abort_flag);
     if (go) {
-      const int r = q * 32 + lane;
-      const int32_t ro = rowC[r];
+      const int r_ = q * 32 + lane;
+      const int32_t ro = rowC[r_];
       // the tile's first four column bits are C's four fastest indices: each
       // thread's 16 columns form one contiguous run (16-element aligned)
       const bool n16 = d.nn >= 4 && d.cn[0] == 1 && d.cn[1] == 2 && d.cn[2] == 4 && d.cn[3] == 8;
+      // plane output: stored = acc 2^-r; complex64 output: true value = acc 2^(eA+eB)
+      const int shift = c_planes ? -r : ea + eb;
+      float vmax = 0.f;
+      bool bad = false;
 #pragma unroll 1
       for (int c0 = 0; c0 < TN; c0 += 16) {
-        uint32_t vr[16], vi[16];
+        uint32_t ur[16], ui[16];
         const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-        tmem_ld<16>(lane_base + (uint32_t)c0, vr);
-        tmem_ld<16>(lane_base + (uint32_t)(TN + c0), vi);
+        tmem_ld<16>(lane_base + (uint32_t)c0, ur);
+        tmem_ld<16>(lane_base + (uint32_t)(TN + c0), ui);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (ro >= 0) {
-          if (c_planes) {
-            // output consumed by another tensor-core step: write its four
-            // 16-bit planes {re_hi, re_lo, im_hi, im_lo} at the same offsets
-            uint16_t* P = reinterpret_cast<uint16_t*>(C);
-            const int64_t plane = int64_t(1) << (d.nm + d.nn);
-            uint16_t h[4][16];
+        float vr[16], vi[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              split16<BF16>(__uint_as_float(vr[j]) * inv_scale, h[0][j], h[1][j]);
-              split16<BF16>(__uint_as_float(vi[j]) * inv_scale, h[2][j], h[3][j]);
+        for (int j = 0; j < 16; ++j) {
+          vr[j] = ldexpf(__uint_as_float(ur[j]), shift);
+          vi[j] = ldexpf(__uint_as_float(ui[j]), shift);
+        }
+        if (ro < 0) continue;
+        if (c_planes) {
+          // output consumed by another tensor-core step: write its NP 16-bit
+          // planes at the same offsets
+          uint16_t* P = reinterpret_cast<uint16_t*>(C);
+          const int64_t plane = int64_t(1) << (d.nm + d.nn);
+          uint16_t h[NP][16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            if (colC[c0 + j] >= 0) {
+              vmax = fmaxf(vmax, fmaxf(fabsf(vr[j]), fabsf(vi[j])));
+              bad |= !isfinite(vr[j]) || !isfinite(vi[j]);
             }
-            if (n16 && colC[c0] >= 0) {
-              // 16 consecutive columns are contiguous: two 16-byte stores per plane
-              const int64_t o = (int64_t)ro + colC[c0];
-#pragma unroll
-              for (int p = 0; p < 4; ++p) {
-                uint4* q = reinterpret_cast<uint4*>(P + p * plane + o);
-                q[0] = make_uint4(h[p][0] | (h[p][1] << 16), h[p][2] | (h[p][3] << 16), h[p][4] | (h[p][5] << 16),
-                                  h[p][6] | (h[p][7] << 16));
-                q[1] = make_uint4(h[p][8] | (h[p][9] << 16), h[p][10] | (h[p][11] << 16),
-                                  h[p][12] | (h[p][13] << 16), h[p][14] | (h[p][15] << 16));
-              }
+            if constexpr (NP == 4) {
+              split16<BF16>(vr[j], h[0][j], h[1][j]);
+              split16<BF16>(vi[j], h[2][j], h[3][j]);
             } else {
-#pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                const int32_t co = colC[c0 + j];
-                if (co < 0) continue;
-                const int64_t o = (int64_t)ro + co;
-#pragma unroll
-                for (int p = 0; p < 4; ++p) P[p * plane + o] = h[p][j];
-              }
+              h[0][j] = to16<BF16>(vr[j]);
+              h[1][j] = to16<BF16>(vi[j]);
             }
-          } else if (n16 && colC[c0] >= 0) {
-            float4* q = reinterpret_cast<float4*>(C + (int64_t)ro + colC[c0]);
+          }
+          if (n16 && colC[c0] >= 0) {
+            const int64_t o = (int64_t)ro + colC[c0];
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-              q[j] = make_float4(__uint_as_float(vr[2 * j]) * inv_scale, __uint_as_float(vi[2 * j]) * inv_scale,
-                                 __uint_as_float(vr[2 * j + 1]) * inv_scale, __uint_as_float(vi[2 * j + 1]) * inv_scale);
+            for (int p = 0; p < NP; ++p) {
+              uint4* qd = reinterpret_cast<uint4*>(P + p * plane + o);
+              qd[0] = make_uint4(h[p][0] | (h[p][1] << 16), h[p][2] | (h[p][3] << 16), h[p][4] | (h[p][5] << 16),
+                                 h[p][6] | (h[p][7] << 16));
+              qd[1] = make_uint4(h[p][8] | (h[p][9] << 16), h[p][10] | (h[p][11] << 16),
+                                 h[p][12] | (h[p][13] << 16), h[p][14] | (h[p][15] << 16));
+            }
           } else {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const int32_t co = colC[c0 + j];
-              if (co >= 0)
-                C[(int64_t)ro + co] =
-                    make_float2(__uint_as_float(vr[j]) * inv_scale, __uint_as_float(vi[j]) * inv_scale);
+              if (co < 0) continue;
+              const int64_t o = (int64_t)ro + co;
+#pragma unroll
+              for (int p = 0; p < NP; ++p) P[p * plane + o] = h[p][j];
             }
           }
+        } else if (n16 && colC[c0] >= 0) {
+          float4* qd = reinterpret_cast<float4*>(C + (int64_t)ro + colC[c0]);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) qd[j] = make_float4(vr[2 * j], vi[2 * j], vr[2 * j + 1], vi[2 * j + 1]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int32_t co = colC[c0 + j];
+            if (co >= 0) C[(int64_t)ro + co] = make_float2(vr[j], vi[j]);
+          }
+        }
+      }
+      if (sio.mc || sio.flag) {
+        // per-unit bookkeeping: largest stored component, exponent, filter flag
+        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        bad = __any_sync(0xffffffffu, bad);
+        const int zc = (int)blockIdx.z;
+        if (lane == 0) {
+          if (sio.mc && c_planes) atomicMax(sio.mc + zc, __float_as_uint(vmax));
+          if (sio.ec && c_planes && q == 0 && blockIdx.x == 0) sio.ec[zc] = ea + eb + r;
+          if (sio.flag && (bad || weak)) sio.flag[sio.flag_by_lo ? (int)ulo : zc] = 1;
         }
       }
     }
@@ -365,15 +430,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 5-D map over one operand's planes: [hi unit][lo unit][plane][row][k] of
-// 16-bit values; box = 32 k x box_rows x 4 planes x 1 x 1.
+// 16-bit values; box = 32 k x box_rows x np planes x 1 x 1.
 bool encode_planes(CUtensorMap* map, const PlaneOperand& o, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
-  const int64_t set = 4 * o.rows * o.kp * 2;  // bytes of one plane set
-  cuuint64_t dims[5] = {(cuuint64_t)o.kp, (cuuint64_t)o.rows, 4, (cuuint64_t)o.nlo, (cuuint64_t)o.nhi};
+  const int64_t set = (int64_t)o.np * o.rows * o.kp * 2;  // bytes of one plane set
+  cuuint64_t dims[5] = {(cuuint64_t)o.kp, (cuuint64_t)o.rows, (cuuint64_t)o.np, (cuuint64_t)o.nlo, (cuuint64_t)o.nhi};
   cuuint64_t strides[4] = {(cuuint64_t)(o.kp * 2), (cuuint64_t)(o.rows * o.kp * 2),
                            (cuuint64_t)(o.nlo > 1 ? o.st_lo : set), (cuuint64_t)(o.nhi > 1 ? o.st_hi : set)};
-  cuuint32_t box[5] = {(cuuint32_t)TKC, (cuuint32_t)box_rows, 4, 1, 1};
+  cuuint32_t box[5] = {(cuuint32_t)TKC, (cuuint32_t)box_rows, (cuuint32_t)o.np, 1, 1};
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 5, const_cast<uint16_t*>(o.base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -381,52 +446,60 @@ bool encode_planes(CUtensorMap* map, const PlaneOperand& o, int box_rows) {
   return r == CUDA_SUCCESS;
 }
 
-template <int TN, bool BF16>
+template <int TN, bool BF16, int NP>
 cudaError_t launch_cfg(const CUtensorMap& ma, const CUtensorMap& mb, float2* C, const GemmDesc& d, int kp,
-                       const int z[4], int c_planes, float inv_scale, int* err, cudaStream_t s) {
+                       const int z[4], int c_planes, const ScaleIO& sio, int* err, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tma_kernel<TN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg2<TN>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(gemm_tma_kernel<TN, BF16, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg2<TN, NP>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int64_t M = int64_t(1) << d.nm, N = int64_t(1) << d.nn;
   dim3 grid((unsigned)((M / TM) * (N / TN)), 1, (unsigned)d.units);
-  gemm_tma_kernel<TN, BF16><<<grid, NTHREADS, Cfg2<TN>::SMEM, s>>>(ma, mb, C, d, kp, z[0], z[1], z[2], z[3], c_planes,
-                                                                   inv_scale, err);
+  gemm_tma_kernel<TN, BF16, NP><<<grid, NTHREADS, Cfg2<TN, NP>::SMEM, s>>>(ma, mb, C, d, kp, z[0], z[1], z[2], z[3],
+                                                                           c_planes, sio, err);
   return cudaGetLastError();
+}
+
+template <bool BF16, int NP>
+cudaError_t launch_tn(int TNv, const CUtensorMap& ma, const CUtensorMap& mb, float2* C, const GemmDesc& d, int kp,
+                      const int z[4], int cp, const ScaleIO& sio, int* err, cudaStream_t s) {
+  switch (TNv) {
+    case 128: return launch_cfg<128, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+    case 64: return launch_cfg<64, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+    case 32: return launch_cfg<32, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+    case 16: return launch_cfg<16, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
 
 int tma_tile_n(const GemmDesc& d) { return d.nn >= 7 ? 128 : (1 << d.nn); }
 
-int64_t split_plane_elems(int nrow_bits, int nk_bits) {
+int64_t split_plane_elems(int nrow_bits, int nk_bits, int np) {
   const int64_t kp = std::max<int64_t>(int64_t(1) << nk_bits, TKC);
-  return 4 * (int64_t(1) << nrow_bits) * kp;
+  return np * (int64_t(1) << nrow_bits) * kp;
 }
 
 cudaError_t launch_gemm_tma(const PlaneOperand& a, const PlaneOperand& b, float2* C, bool c_planes, const GemmDesc& d,
-                            bool bf16, float inv_scale, int* err, cudaStream_t s) {
-  if (!tc_shape_ok(d) || d.units > 65535 || a.kp != b.kp || a.kp % TKC) return cudaErrorInvalidValue;
+                            bool bf16, const ScaleIO& sio, int* err, cudaStream_t s) {
+  if (!tc_shape_ok(d) || d.units > 65535 || a.kp != b.kp || a.kp % TKC || a.np != b.np ||
+      (a.np != 2 && a.np != 4))
+    return cudaErrorInvalidValue;
   const int TNv = tma_tile_n(d);
   CUtensorMap ma, mb;
   if (!encode_planes(&ma, a, TM) || !encode_planes(&mb, b, TNv)) return cudaErrorInvalidValue;
   const int kpi = (int)a.kp;
   const int z[4] = {a.nlo > 1, a.nhi > 1, b.nlo > 1, b.nhi > 1};
   const int cp = c_planes ? 1 : 0;
-  switch (TNv) {
-    case 128: return bf16 ? launch_cfg<128, true>(ma, mb, C, d, kpi, z, cp, inv_scale, err, s)
-                          : launch_cfg<128, false>(ma, mb, C, d, kpi, z, cp, inv_scale, err, s);
-    case 64: return bf16 ? launch_cfg<64, true>(ma, mb, C, d, kpi, z, cp, inv_scale, err, s)
-                         : launch_cfg<64, false>(ma, mb, C, d, kpi, z, cp, inv_scale, err, s);
-    case 32: return bf16 ? launch_cfg<32, true>(ma, mb, C, d, kpi, z, cp, inv_scale, err, s)
-                         : launch_cfg<32, false>(ma, mb, C, d, kpi, z, cp, inv_scale, err, s);
-    case 16: return bf16 ? launch_cfg<16, true>(ma, mb, C, d, kpi, z, cp, inv_scale, err, s)
-                         : launch_cfg<16, false>(ma, mb, C, d, kpi, z, cp, inv_scale, err, s);
-    default: return cudaErrorInvalidValue;
-  }
+  if (a.np == 4)
+    return bf16 ? launch_tn<true, 4>(TNv, ma, mb, C, d, kpi, z, cp, sio, err, s)
+                : launch_tn<false, 4>(TNv, ma, mb, C, d, kpi, z, cp, sio, err, s);
+  return bf16 ? launch_tn<true, 2>(TNv, ma, mb, C, d, kpi, z, cp, sio, err, s)
+              : launch_tn<false, 2>(TNv, ma, mb, C, d, kpi, z, cp, sio, err, s);
 }
 
 }  // namespace tn

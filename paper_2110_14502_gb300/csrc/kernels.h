@@ -78,13 +78,14 @@ struct SplitDesc {
   int64_t lo, hi;
   int32_t row_st[kMaxBits], k_st[kMaxBits];
 };
-cudaError_t launch_split(const float2* src, uint16_t* dst, const SplitDesc& d, int nz, bool bf16, float scale,
-                         cudaStream_t s);
+cudaError_t launch_split(const float2* src, uint16_t* dst, const SplitDesc& d, int nz, bool bf16, int np,
+                         unsigned* maxbits, int* e_out, float* m_out, cudaStream_t s);
 // One GEMM operand stored as four K-major 16-bit planes {re_hi, re_lo, im_hi,
 // im_lo}, each rows x kp; consecutive units are st_lo / st_hi bytes apart
 // along the two unit dimensions (extent 1 = one tensor shared by all units).
 struct PlaneOperand {
   const uint16_t* base;
+  int np;                // 4 planes (re_hi, re_lo, im_hi, im_lo) or 2 (re, im)
   int64_t kp, rows;
   int64_t nlo, nhi;
   int64_t st_lo, st_hi;
@@ -93,16 +94,37 @@ struct PlaneOperand {
 // the epilogue writes C as planes (for a tensor-core consumer) instead of
 // complex64.
 int tma_tile_n(const GemmDesc& d);
-int64_t split_plane_elems(int nrow_bits, int nk_bits);
+// I/O of the scaled precisions; every pointer may be null (exponent 0, no
+// tracking).  ea/ma, eb/mb: per distinct operand tensor, the exponent e of
+// its stored values (stored = true * 2^-e) and their largest |component|.
+// ec/mc: the same for a plane output (mc as float bits, atomicMax; cleared by
+// the caller).  flag: per launch unit (or per low unit index when flag_by_lo)
+// set when values turn non-finite or an operand maximum is below 2^-10.
+struct ScaleIO {
+  const int* ea;
+  const float* ma;
+  const int* eb;
+  const float* mb;
+  int* ec;
+  unsigned* mc;
+  int* flag;
+  int flag_by_lo;
+};
+int64_t split_plane_elems(int nrow_bits, int nk_bits, int np);
 cudaError_t launch_gemm_tma(const PlaneOperand& a, const PlaneOperand& b, float2* C, bool c_planes, const GemmDesc& d,
-                            bool bf16, float inv_scale, int* err, cudaStream_t s);
+                            bool bf16, const ScaleIO& sio, int* err, cudaStream_t s);
 // Split operand A (which_b = false) or B of d into `scratch` (returned planes).
-int64_t split_scratch_elems(const GemmDesc& d, bool which_b);
-cudaError_t split_operand(const float2* src, const GemmDesc& d, bool which_b, bool bf16, uint16_t* scratch,
-                          PlaneOperand& out, cudaStream_t s);
-// Plane operand of a tensor a producer epilogue already wrote as planes
+// With `scaled`, each distinct tensor z is first reduced to its largest
+// |component| (maxbits[z], cleared by the caller) and stored times 2^-e_z with
+// e_z chosen so that this maximum lands in [2^13, 2^14); e_out / m_out receive
+// e_z and the stored maximum.
+int64_t split_scratch_elems(const GemmDesc& d, bool which_b, int np);
+cudaError_t split_operand(const float2* src, const GemmDesc& d, bool which_b, bool bf16, int np, bool scaled,
+                          unsigned* maxbits, int* e_out, float* m_out, uint16_t* scratch, PlaneOperand& out,
+                          cudaStream_t s);
+// Plane operand of a tensor a producer epilogue already wrote as np planes
 // (layout [rows][K], K >= 32); false when the step's view does not match.
-bool planes_in_place(const float2* base, const GemmDesc& d, bool which_b, PlaneOperand& out);
+bool planes_in_place(const float2* base, const GemmDesc& d, bool which_b, int np, PlaneOperand& out);
 // Split both operands of d into `scratch` (>= tc2_scratch_elems(d) 16-bit
 // values) and run the TMA GEMM.
 int64_t tc2_scratch_elems(const GemmDesc& d);
@@ -113,8 +135,11 @@ cudaError_t launch_gather(const float2* store, float2* arena, int64_t arena_stri
                           int nleaves, const uint64_t* bits, const GroupInfo& g, cudaStream_t s);
 // acc[b, j] += sum over the group's slices (in slice order) of root(b, s)[perm[j]],
 // root(b, s) = root + s_local * r_lo + b_local * r_hi.
+// Flagged units (flag_s per slice of the group, flag_u per unit; both may be
+// null) are skipped and appended as (b << 32 | s) to `flagged` (capacity cap).
 cudaError_t launch_accumulate(const float2* root, int64_t r_lo, int64_t r_hi, const int64_t* perm, int nperm,
-                              double2* acc, const GroupInfo& g, cudaStream_t s);
+                              double2* acc, const GroupInfo& g, const int* flag_s, const int* flag_u,
+                              int64_t* flagged, unsigned long long* nflagged, int cap, cudaStream_t s);
 // dst (dense, element e) = src[sum_p bit_p(e) * st[p]]: bit p of e is dst's
 // p-th fastest index, st[p] its element stride in src.
 struct PermDesc {

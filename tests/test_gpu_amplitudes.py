@@ -132,6 +132,9 @@ def test_full_size_6x6_sampled_slices_vs_oracle():
         # producer to consumer) on the same slice: the split-precision bound
         got = p.contract_amplitudes(words[:1], slice_begin=s, slice_count=1, precision="split_bf16")[0]
         assert rel(got, ref) <= 1e-4, s
+        for mode in ("split_fp16", "scaled_fp16", "scaled_bf16"):
+            got = p.contract_amplitudes(words[:1], slice_begin=s, slice_count=1, precision=mode)[0]
+            assert rel(got, ref) <= MODE_BOUND[mode], (s, mode, rel(got, ref))
 
 
 def test_split_bf16_path_vs_statevector():
@@ -148,3 +151,48 @@ def test_split_bf16_path_vs_statevector():
     assert rel(got, ref) <= 1e-4
     c64 = p.contract_amplitudes(words, precision="c64")
     assert rel(c64, ref) <= 1e-5
+
+
+MODE_BOUND = {"c64": 1e-5, "split_bf16": 1e-4, "split_fp16": 1e-4, "scaled_fp16": 2e-2, "scaled_bf16": 2e-2}
+
+
+@pytest.mark.parametrize("mode", ["split_fp16", "scaled_fp16", "scaled_bf16"])
+def test_scaled_and_split_fp16_modes_vs_statevector(mode):
+    """Mixed-precision modes with per-unit power-of-two exponents on the
+    tensor cores, against the state vector within each mode's bound."""
+    T = tnlib()
+    rows, cols, depth, seed, open_q = 4, 5, 14, 12, (14, 15, 16, 17, 18, 19)
+    n = rows * cols
+    p = _setup(T, rows, cols, depth, seed, open_q, num_sliced=2, search_trials=32, seed=3)
+    words = I.bitstrings(n, 3, seed)
+    got, rep = p.contract_amplitudes(words, precision=mode, report=True)
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    ref = SV.amplitudes(SV.simulate(gates, n), n, [I.bits_of(w, n) for w in words], open_q)
+    assert rel(got, ref) <= MODE_BOUND[mode], (mode, rel(got, ref))
+    assert rep["discarded_units"] == 0
+
+
+def test_filter_recompute_and_discard():
+    """The filter of the scaled modes, driven by host-injected flags: a
+    flagged unit is recomputed in complex64 (policy 0) or left out of the sum
+    (policy 1, the paper's discard), which leaves the exact partial sum over
+    the kept slices."""
+    T = tnlib()
+    rows, cols, depth, seed, open_q = 4, 4, 10, 5, (15, 14)
+    n = rows * cols
+    p = _setup(T, rows, cols, depth, seed, open_q, num_sliced=4, search_trials=16, seed=3)
+    words = I.bitstrings(n, 2, seed)
+    base = p.contract_amplitudes(words, precision="scaled_fp16")
+    got, rep = p.contract_amplitudes(words, precision="scaled_fp16", test_flag_every=3, report=True)
+    flagged = [s for s in range(16) if s % 3 == 0]
+    assert rep["flagged_units"] == len(flagged) * 2 and rep["discarded_units"] == 0
+    assert rel(got, base) <= 2e-2
+    got, rep = p.contract_amplitudes(words, precision="scaled_fp16", test_flag_every=3, overflow_policy=1,
+                                     report=True)
+    assert rep["discarded_units"] == len(flagged) * 2
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    wires = p.sliced_wires()
+    for bi, w in enumerate(words):
+        net = OTN.circuit_network(gates, n, I.bits_of(w, n), open_q)
+        ref = OTN.contract_sliced(net, wires, [s for s in range(16) if s not in flagged])
+        assert rel(got[bi], ref) <= 2e-2
