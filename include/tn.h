@@ -201,11 +201,14 @@ typedef struct {
   int64_t slice_count;      /* number of slices summed; -1 = all from slice_begin */
   int32_t units_per_group;  /* slices contracted together per launch; 0 = auto */
   int32_t overflow_policy;  /* scaled modes: 0 = recompute a flagged slice in complex64, 1 = discard it (counted) */
-  int32_t use_graph;        /* 1 = replay the per-group launch sequence as a CUDA graph */
+  int32_t use_graph;        /* 1 = capture each group's launch sequence once per geometry as a CUDA graph and
+                               replay it (not with profile or test_flag_every) */
   int32_t profile;          /* 1 = bracket every kernel launch with CUDA events and fill the per-class figures */
   int32_t test_flag_every;  /* scaled modes, testing: > 0 flags every slice whose id is a multiple of it, so the
                                recompute / discard paths run without a real under/overflow; 0 = off */
-  int32_t reserved2;
+  int32_t autotune;         /* 1 = time the tensor-core tile choices of every step on the first group of this
+                               precision and keep the fastest (cached per plan; also in the file named by the
+                               environment variable TN_AUTOTUNE_CACHE when it is set) */
 } tn_exec_opts;
 
 /* Kernel classes of the per-class report figures. */

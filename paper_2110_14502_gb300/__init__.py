@@ -160,7 +160,7 @@ class Plan:
 
     def contract_amplitudes(self, bitstrings, precision="c64", slice_begin=0, slice_count=-1,
                             units_per_group=0, stream=None, out=None, overflow_policy=0, use_graph=0,
-                            profile=False, report=False, test_flag_every=0):
+                            profile=False, report=False, test_flag_every=0, autotune=0):
         """Amplitudes of each bitstring's open batch, summed over the slice range.
 
         bitstrings: uint64 words, shape (nb, ceil(n/64)) -- a NumPy array (host
@@ -179,6 +179,7 @@ class Plan:
         o.use_graph = use_graph
         o.profile = 1 if profile else 0
         o.test_flag_every = test_flag_every
+        o.autotune = autotune
         if stream is not None:
             o.stream = C.c_void_p(getattr(stream, "cuda_stream", stream))
         rep = Report()

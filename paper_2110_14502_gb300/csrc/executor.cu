@@ -52,6 +52,15 @@ struct Executor {
   int64_t spool_cap = 0;       // bytes
   int64_t* flagged = nullptr;  // (b << 32 | s) of units kept out of the sum
   unsigned long long* nflagged = nullptr;
+  GroupInfo* gslot = nullptr;  // [2]: group of the slice-only launches, group of the per-unit launches
+  // replayable launch sequences, keyed by (phase, precision, Gs, Gb); dropped
+  // whenever a buffer they reference is reallocated
+  struct Graph { int phase, precision, gs, gb; cudaGraphExec_t exec; int64_t kernels; };
+  std::vector<Graph> graphs;
+  // autotuner choices per (precision, step): tensor-core tile width, raster group
+  struct Tune { int precision, step, tile_n, group_m; };
+  std::vector<Tune> tuned;
+  bool tune_loaded = false;
   std::vector<GemmDesc> desc;  // per step, unit strides filled at launch
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> pev;  // profiling event pool
@@ -75,6 +84,8 @@ void destroy_executor(Executor* e) {
   cudaFree(e->spool);
   cudaFree(e->flagged);
   cudaFree(e->nflagged);
+  cudaFree(e->gslot);
+  for (auto& g : e->graphs) cudaGraphExecDestroy(g.exec);
   if (e->ev0) cudaEventDestroy(e->ev0);
   if (e->ev1) cudaEventDestroy(e->ev1);
   for (auto ev : e->pev) cudaEventDestroy(ev);
@@ -159,6 +170,7 @@ static tn_status setup(Plan& P, Executor& E) {
   CK(cudaMalloc(&E.err, sizeof(int)));
   CK(cudaMemset(E.err, 0, sizeof(int)));
   CK(cudaMalloc(&E.flagged, kFlaggedCap * sizeof(int64_t)));
+  CK(cudaMalloc(&E.gslot, 2 * sizeof(GroupInfo)));
   CK(cudaMalloc(&E.nflagged, sizeof(unsigned long long)));
   return TN_OK;
 }
@@ -194,6 +206,9 @@ struct Ctx {
   int* flag1 = nullptr;          // [Gs] slice-only units
   int* flag2 = nullptr;          // [U] (bitstring, slice) units
   std::vector<char> planes_out;  // per step: output written as 16-bit planes for a tensor-core consumer
+  bool tuning = false;           // time the tile choices of each tensor-core step
+  bool sizing = false;           // only compute scratch needs (no launches)
+  int64_t scratch_need = 0;
   Ctx(const Plan& p, Executor& e, cudaStream_t s, bool prof) : P(p), E(e), st(s), profile(prof) {}
 
   tn_status event(size_t& idx) {
@@ -247,10 +262,11 @@ tn_status run_step(Ctx& c, size_t s, const Geo& g) {
   d.units_lo = S.phase == 0 ? 1 : g.gs;
   d.units = S.phase == 0 ? 1 : S.phase == 1 ? g.gs : g.gs * g.gb;
   size_t e0 = 0, e1 = 0;
-  if (c.profile) { tn_status r = c.event(e0); if (r) return r; }
+  if (c.profile && !c.sizing) { tn_status r = c.event(e0); if (r) return r; }
   cudaError_t e;
   int klass = S.klass == SC_VECTOR ? TN_KCLASS_VECTOR : TN_KCLASS_GEMM_SIMT;
   if (S.klass != SC_VECTOR && c.tc && tc_shape_ok(d)) klass = TN_KCLASS_GEMM_TC;
+  if (c.sizing && klass != TN_KCLASS_GEMM_TC) return TN_OK;
   if (klass == TN_KCLASS_VECTOR) e = launch_vector(A, B, C, d, c.st);
   else if (klass == TN_KCLASS_GEMM_TC) {
     const int L = (int)P.net.leaves.size();
@@ -261,16 +277,13 @@ tn_status run_step(Ctx& c, size_t s, const Geo& g) {
       return fail(TN_EINVAL, "step %zu: internal error, operand planes do not match the step's view", s);
     const int64_t need_a = a_in ? 0 : split_scratch_elems(d, false, c.np);
     const int64_t need = need_a + (b_in ? 0 : split_scratch_elems(d, true, c.np));
-    if (need > E.scratch_cap) {
-      cudaFree(E.scratch);
-      E.scratch = nullptr;
-      E.scratch_cap = 0;
-      if (cudaMalloc(&E.scratch, (size_t)need * sizeof(uint16_t)) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(TN_EHBM, "step %zu: %lld bytes of operand planes do not fit", s, (long long)(need * 2));
-      }
-      E.scratch_cap = need;
+    if (c.sizing) {
+      c.scratch_need = std::max(c.scratch_need, need);
+      return TN_OK;
     }
+    if (need > E.scratch_cap) return fail(TN_EINVAL, "step %zu: internal error, operand scratch not sized", s);
+    for (auto& t : E.tuned)
+      if (t.precision == c.precision && t.step == (int)s) { d.tile_n = t.tile_n; d.group_m = t.group_m; }
     ScaleIO sio{};
     e = cudaSuccess;
     const int64_t U = c.U;
@@ -320,6 +333,37 @@ tn_status run_step(Ctx& c, size_t s, const Geo& g) {
       (void)per;
       c.recs.push_back({TN_KCLASS_SPLIT, 0.0, bytes, e0});
       e0 = em;
+    }
+    if (e == cudaSuccess && c.tuning) {
+      // autotuner: time each tile choice once (every candidate writes the same
+      // result; the last launch below leaves it in place) and keep the fastest
+      const int def_n = d.nn >= 7 ? 128 : (1 << d.nn);
+      float best = 1e30f;
+      int bt = 0, bg = 0;
+      for (int tn : {128, 64}) {
+        if (tn > def_n) continue;
+        for (int gm : {8, 16, 32}) {
+          GemmDesc dc = d;
+          dc.tile_n = tn;
+          dc.group_m = gm;
+          cudaEvent_t t0, t1;
+          cudaEventCreate(&t0);
+          cudaEventCreate(&t1);
+          cudaEventRecord(t0, c.st);
+          e = launch_gemm_tma(pa, pb, C, c.planes_out[s] != 0, dc, c.bf16, sio, E.err, c.st);
+          cudaEventRecord(t1, c.st);
+          cudaEventSynchronize(t1);
+          float ms = 0;
+          cudaEventElapsedTime(&ms, t0, t1);
+          cudaEventDestroy(t0);
+          cudaEventDestroy(t1);
+          if (e != cudaSuccess) break;
+          if (ms < best) { best = ms; bt = tn; bg = gm; }
+        }
+      }
+      E.tuned.push_back({c.precision, (int)s, bt, bg});
+      d.tile_n = bt;
+      d.group_m = bg;
     }
     if (e == cudaSuccess) e = launch_gemm_tma(pa, pb, C, c.planes_out[s] != 0, d, c.bf16, sio, E.err, c.st);
   }
@@ -508,60 +552,164 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
   }
   const int L = (int)P.net.leaves.size();
   const int root_id = L == 1 ? 0 : L + (int)P.steps.size() - 1;
+  // operand scratch for the tensor-core steps, sized before any launch so that
+  // the launch sequences allocate nothing (and can be captured as graphs)
+  if (c.tc && nb > 0) {
+    c.sizing = true;
+    Geo gz;
+    gz.gs = (int)std::min<int64_t>(Gs, std::max<int64_t>(ns, 1));
+    gz.gb = (int)std::min<int64_t>(Gb, nb);
+    for (size_t s = 0; s < P.steps.size(); ++s)
+      if (P.steps[s].phase != 0) {
+        tn_status r = run_step(c, s, gz);
+        if (r != TN_OK) return r;
+      }
+    c.sizing = false;
+    if (c.scratch_need > E.scratch_cap) {
+      cudaFree(E.scratch);
+      E.scratch = nullptr;
+      E.scratch_cap = 0;
+      for (auto& gr : E.graphs) cudaGraphExecDestroy(gr.exec);
+      E.graphs.clear();
+      if (cudaMalloc(&E.scratch, (size_t)c.scratch_need * sizeof(uint16_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TN_EHBM, "tn_contract_amplitudes: %lld bytes of operand planes do not fit",
+                    (long long)(c.scratch_need * 2));
+      }
+      E.scratch_cap = c.scratch_need;
+    }
+  }
+  // autotuner: the first group of a precision times the tile choices
+  if (c.tc && o.autotune) {
+    if (!E.tune_loaded) {
+      E.tune_loaded = true;
+      if (const char* path = getenv("TN_AUTOTUNE_CACHE")) {
+        if (FILE* f = fopen(path, "r")) {
+          unsigned long long h;
+          int pr, st_, tn, gm;
+          while (fscanf(f, "%llx %d %d %d %d", &h, &pr, &st_, &tn, &gm) == 5)
+            if (h == P.hash) E.tuned.push_back({pr, st_, tn, gm});
+          fclose(f);
+        }
+      }
+    }
+    bool have = false;
+    for (auto& t : E.tuned) have |= t.precision == c.precision;
+    c.tuning = !have;
+  }
+  const bool graphs = o.use_graph && !o.profile && !(scaled && o.test_flag_every > 0);
+  // One launch sequence (the slice-only steps of a group, or the per-unit
+  // steps of a group and its accumulation), replayed from a graph when allowed.
+  auto sequence = [&](int phase, const Geo& gg) -> tn_status {
+    auto body = [&]() -> tn_status {
+      if (phase == 1) {
+        if (scaled) CK(cudaMemsetAsync(c.flag1, 0, Gs * sizeof(int), st));
+        if (E.ngather1) {
+          tn_status r = run_misc(c, launch_gather(E.store, E.sarena, Se, E.gather, E.ngather1, E.gslot, gg.gs, st),
+                                 "gather");
+          if (r) return r;
+        }
+      } else {
+        if (scaled) CK(cudaMemsetAsync(c.flag2, 0, c.U * sizeof(int), st));
+        if (E.ngather2) {
+          tn_status r = run_misc(
+              c, launch_gather(E.store, E.parena, Pe, E.gather + E.ngather1, E.ngather2, E.gslot + 1, gg.gs * gg.gb, st),
+              "gather");
+          if (r) return r;
+        }
+      }
+      for (size_t s = 0; s < P.steps.size(); ++s)
+        if (P.steps[s].phase == phase) {
+          tn_status r = run_step(c, s, gg);
+          if (r != TN_OK) return r;
+        }
+      if (phase == 2) {
+        const float2* root;
+        int64_t rlo, rhi;
+        operand(P, E, root_id, 2, gg, root, rlo, rhi);
+        tn_status r = run_misc(c,
+                               launch_accumulate(root, rlo, rhi, E.perm, (int)P.root_perm.size(), E.gslot + 1, gg.gb,
+                                                 scaled ? c.flag1 : nullptr, scaled ? c.flag2 : nullptr, E.flagged,
+                                                 E.nflagged, kFlaggedCap, st),
+                               "accumulate");
+        if (r) return r;
+      }
+      return TN_OK;
+    };
+    if (!graphs || c.tuning) return body();
+    for (auto& gr : E.graphs)
+      if (gr.phase == phase && gr.precision == c.precision && gr.gs == gg.gs && gr.gb == (phase == 2 ? gg.gb : 1)) {
+        CK(cudaGraphLaunch(gr.exec, st));
+        c.launches += gr.kernels;
+        return TN_OK;
+      }
+    const int64_t before = c.launches;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    tn_status r = body();
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    if (r != TN_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return r;
+    }
+    if (ce != cudaSuccess) return fail(TN_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fail(TN_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    E.graphs.push_back({phase, c.precision, gg.gs, phase == 2 ? gg.gb : 1, exec, c.launches - before});
+    CK(cudaGraphLaunch(exec, st));
+    return TN_OK;
+  };
   for (int64_t s0 = s_begin; s0 < s_begin + ns && nb > 0; s0 += Gs) {
     g.gs = (int)std::min<int64_t>(Gs, s_begin + ns - s0);
     g.gb = 1;
-    GroupInfo gi;
+    GroupInfo gi{};
     gi.slice0 = s0;
     gi.b0 = 0;
     gi.nslice = g.gs;
     gi.nb = 1;
     gi.words = words;
     gi.units = g.gs;
-    if (scaled) {
-      CK(cudaMemsetAsync(c.flag1, 0, Gs * sizeof(int), st));
-      if (o.test_flag_every > 0) {
-        // host-side injection of filter flags (tests of the recompute / discard paths)
-        std::vector<int> f(g.gs);
-        for (int i = 0; i < g.gs; ++i) f[i] = ((s0 + i) % o.test_flag_every) == 0;
-        CK(cudaMemcpyAsync(c.flag1, f.data(), g.gs * sizeof(int), cudaMemcpyHostToDevice, st));
-        CK(cudaStreamSynchronize(st));
-      }
-    }
-    if (E.ngather1) {
-      tn_status r = run_misc(c, launch_gather(E.store, E.sarena, Se, E.gather, E.ngather1, d_bits, gi, st), "gather");
+    gi.bits = d_bits;
+    gi.acc = d_acc;
+    {
+      tn_status r = run_misc(c, launch_set_group(E.gslot, gi, st), "set_group");
       if (r) return r;
     }
-    for (size_t s = 0; s < P.steps.size(); ++s)
-      if (P.steps[s].phase == 1) {
-        tn_status r = run_step(c, s, g);
-        if (r != TN_OK) return r;
-      }
+    if (scaled && o.test_flag_every > 0) {
+      // host-side injection of filter flags (tests of the recompute / discard paths)
+      CK(cudaMemsetAsync(c.flag1, 0, Gs * sizeof(int), st));
+      std::vector<int> f(g.gs);
+      for (int i = 0; i < g.gs; ++i) f[i] = ((s0 + i) % o.test_flag_every) == 0;
+      tn_status r = sequence(1, g);
+      if (r) return r;
+      CK(cudaMemcpyAsync(c.flag1, f.data(), g.gs * sizeof(int), cudaMemcpyHostToDevice, st));
+      CK(cudaStreamSynchronize(st));
+    } else {
+      tn_status r = sequence(1, g);
+      if (r) return r;
+    }
     for (int64_t b0 = 0; b0 < nb; b0 += Gb) {
       g.gb = (int)std::min<int64_t>(Gb, nb - b0);
       gi.b0 = b0;
       gi.nb = g.gb;
       gi.units = g.gs * g.gb;
-      if (scaled) CK(cudaMemsetAsync(c.flag2, 0, c.U * sizeof(int), st));
-      if (E.ngather2) {
-        tn_status r = run_misc(
-            c, launch_gather(E.store, E.parena, Pe, E.gather + E.ngather1, E.ngather2, d_bits, gi, st), "gather");
-        if (r) return r;
-      }
-      for (size_t s = 0; s < P.steps.size(); ++s)
-        if (P.steps[s].phase == 2) {
-          tn_status r = run_step(c, s, g);
-          if (r != TN_OK) return r;
-        }
-      const float2* root;
-      int64_t rlo, rhi;
-      operand(P, E, root_id, 2, g, root, rlo, rhi);
-      tn_status r = run_misc(c,
-                             launch_accumulate(root, rlo, rhi, E.perm, (int)P.root_perm.size(), d_acc, gi,
-                                               scaled ? c.flag1 : nullptr, scaled ? c.flag2 : nullptr, E.flagged,
-                                               E.nflagged, kFlaggedCap, st),
-                             "accumulate");
+      tn_status r = run_misc(c, launch_set_group(E.gslot + 1, gi, st), "set_group");
       if (r) return r;
+      r = sequence(2, g);
+      if (r) return r;
+    }
+    if (c.tuning) {
+      c.tuning = false;
+      if (const char* path = getenv("TN_AUTOTUNE_CACHE")) {
+        if (FILE* f = fopen(path, "a")) {
+          for (auto& t : E.tuned)
+            if (t.precision == c.precision)
+              fprintf(f, "%llx %d %d %d %d\n", (unsigned long long)P.hash, t.precision, t.step, t.tile_n, t.group_m);
+          fclose(f);
+        }
+      }
     }
   }
   // ---- the filter: units flagged in a scaled precision are recomputed in

@@ -15,11 +15,15 @@ namespace tn {
 
 namespace {
 
+__global__ void set_group_kernel(GroupInfo* slot, GroupInfo g) { *slot = g; }
+
 __global__ void gather_kernel(const float2* __restrict__ store, float2* __restrict__ arena, int64_t arena_stride,
-                              const LeafGather* __restrict__ descs, const uint64_t* __restrict__ bits,
-                              GroupInfo g) {
+                              const LeafGather* __restrict__ descs, const GroupInfo* __restrict__ slot) {
+  const GroupInfo g = *slot;
+  const uint64_t* bits = g.bits;
   const LeafGather& L = descs[blockIdx.x];
   const int u = blockIdx.y;
+  if (u >= g.units) return;
   const int64_t s = g.slice0 + u % g.nslice;
   const int64_t b = g.b0 + u / g.nslice;
   int64_t fixed_off = L.store_off;
@@ -48,10 +52,12 @@ __global__ void gather_kernel(const float2* __restrict__ store, float2* __restri
 // out of the sum): a flagged unit adds nothing here and is listed for the
 // host, which recomputes it in complex64 or counts it as discarded.
 __global__ void accumulate_kernel(const float2* __restrict__ root, int64_t r_lo, int64_t r_hi,
-                                  const int64_t* __restrict__ perm, int nperm, double2* __restrict__ acc,
-                                  GroupInfo g, const int* __restrict__ flag_s, const int* __restrict__ flag_u,
+                                  const int64_t* __restrict__ perm, int nperm, const GroupInfo* __restrict__ slot,
+                                  const int* __restrict__ flag_s, const int* __restrict__ flag_u,
                                   int64_t* __restrict__ flagged, unsigned long long* __restrict__ nflagged,
                                   int cap) {
+  const GroupInfo g = *slot;
+  double2* acc = g.acc;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)g.nb * nperm) return;
   const int bl = (int)(idx / nperm);
@@ -87,20 +93,25 @@ __global__ void permute_kernel(const float2* __restrict__ src, float2* __restric
 
 }  // namespace
 
+cudaError_t launch_set_group(GroupInfo* slot, const GroupInfo& g, cudaStream_t s) {
+  set_group_kernel<<<1, 1, 0, s>>>(slot, g);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gather(const float2* store, float2* arena, int64_t arena_stride, const LeafGather* descs,
-                          int nleaves, const uint64_t* bits, const GroupInfo& g, cudaStream_t s) {
-  if (nleaves == 0 || g.units == 0) return cudaSuccess;
-  dim3 grid((unsigned)nleaves, (unsigned)g.units);
-  gather_kernel<<<grid, 64, 0, s>>>(store, arena, arena_stride, descs, bits, g);
+                          int nleaves, const GroupInfo* slot, int units, cudaStream_t s) {
+  if (nleaves == 0 || units == 0) return cudaSuccess;
+  dim3 grid((unsigned)nleaves, (unsigned)units);
+  gather_kernel<<<grid, 64, 0, s>>>(store, arena, arena_stride, descs, slot);
   return cudaGetLastError();
 }
 
 cudaError_t launch_accumulate(const float2* root, int64_t r_lo, int64_t r_hi, const int64_t* perm, int nperm,
-                              double2* acc, const GroupInfo& g, const int* flag_s, const int* flag_u,
+                              const GroupInfo* slot, int nb_max, const int* flag_s, const int* flag_u,
                               int64_t* flagged, unsigned long long* nflagged, int cap, cudaStream_t s) {
-  const int64_t total = (int64_t)g.nb * nperm;
+  const int64_t total = (int64_t)nb_max * nperm;
   const int nt = 256;
-  accumulate_kernel<<<(unsigned)((total + nt - 1) / nt), nt, 0, s>>>(root, r_lo, r_hi, perm, nperm, acc, g, flag_s,
+  accumulate_kernel<<<(unsigned)((total + nt - 1) / nt), nt, 0, s>>>(root, r_lo, r_hi, perm, nperm, slot, flag_s,
                                                                      flag_u, flagged, nflagged, cap);
   return cudaGetLastError();
 }

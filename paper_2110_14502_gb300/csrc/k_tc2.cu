@@ -49,7 +49,7 @@ constexpr int TKC = 32;                 // complex K per stage (64-byte rows of 
 constexpr int NTHREADS = 256;
 constexpr int SMEM_BUDGET = 196 * 1024;
 constexpr long long kWaitLimit = 1ll << 24;
-constexpr int GROUP_M = 16;
+constexpr int GROUP_M_DEFAULT = 16;
 
 template <int TN, int NP>
 struct Cfg2 {
@@ -206,10 +206,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   {
     const int ntm = (int)((int64_t(1) << d.nm) / TM), ntn = (int)((int64_t(1) << d.nn) / TN);
     const int t = blockIdx.x;
-    const int per_group = GROUP_M * ntn;
+    const int GM = d.group_m > 0 ? d.group_m : GROUP_M_DEFAULT;
+    const int per_group = GM * ntn;
     const int g = t / per_group, r = t % per_group;
-    const int gm = min(GROUP_M, ntm - g * GROUP_M);
-    m0 = (g * GROUP_M + r % gm) * TM;
+    const int gm = min(GM, ntm - g * GM);
+    m0 = (g * GM + r % gm) * TM;
     n0 = (r / gm) * TN;
   }
   const int nkt = kp / TKC;
@@ -477,7 +478,11 @@ cudaError_t launch_tn(int TNv, const CUtensorMap& ma, const CUtensorMap& mb, flo
 
 }  // namespace
 
-int tma_tile_n(const GemmDesc& d) { return d.nn >= 7 ? 128 : (1 << d.nn); }
+int tma_tile_n(const GemmDesc& d) {
+  const int def = d.nn >= 7 ? 128 : (1 << d.nn);
+  if (d.tile_n >= 16 && d.tile_n <= def) return d.tile_n;
+  return def;
+}
 
 int64_t split_plane_elems(int nrow_bits, int nk_bits, int np) {
   const int64_t kp = std::max<int64_t>(int64_t(1) << nk_bits, TKC);

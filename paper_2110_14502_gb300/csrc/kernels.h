@@ -26,6 +26,7 @@ constexpr int kMaxBits = 32;
 struct GemmDesc {
   int nm, nn, nk;
   int units, units_lo;
+  int tile_n, group_m;       // tensor-core tile width / raster group (0 = default; set by the autotuner)
   int64_t a_lo, a_hi, b_lo, b_hi, c_lo, c_hi;
   int32_t am[kMaxBits], cm[kMaxBits];
   int32_t bn[kMaxBits], cn[kMaxBits];
@@ -47,6 +48,8 @@ struct LeafGather {
 
 // A group of units: `nslice` consecutive slice ids from slice0 for the
 // bitstrings b0 .. b0+nb-1; unit u = (u % nslice) slice, (u / nslice) bitstring.
+// The kernels read it from a device slot written by launch_set_group, so a
+// captured launch sequence can be replayed for any group.
 struct GroupInfo {
   int64_t slice0;
   int64_t b0;
@@ -54,6 +57,8 @@ struct GroupInfo {
   int32_t nb;                // 1 for slice-only launches
   int32_t words;             // uint64 words per bitstring
   int32_t units;             // nslice * nb
+  const uint64_t* bits;      // bitstrings of the call (device)
+  double2* acc;              // amplitude accumulator of the call (device)
 };
 
 // launchers (return cudaGetLastError())
@@ -131,14 +136,16 @@ int64_t tc2_scratch_elems(const GemmDesc& d);
 cudaError_t run_gemm_tc2(const float2* A, const float2* B, float2* C, const GemmDesc& d, bool bf16, uint16_t* scratch,
                          int* err, cudaStream_t s);
 cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s);
+cudaError_t launch_set_group(GroupInfo* slot, const GroupInfo& g, cudaStream_t s);
+// grid covers `units` units (the slot's count may be lower for a partial group)
 cudaError_t launch_gather(const float2* store, float2* arena, int64_t arena_stride, const LeafGather* descs,
-                          int nleaves, const uint64_t* bits, const GroupInfo& g, cudaStream_t s);
+                          int nleaves, const GroupInfo* slot, int units, cudaStream_t s);
 // acc[b, j] += sum over the group's slices (in slice order) of root(b, s)[perm[j]],
 // root(b, s) = root + s_local * r_lo + b_local * r_hi.
 // Flagged units (flag_s per slice of the group, flag_u per unit; both may be
 // null) are skipped and appended as (b << 32 | s) to `flagged` (capacity cap).
 cudaError_t launch_accumulate(const float2* root, int64_t r_lo, int64_t r_hi, const int64_t* perm, int nperm,
-                              double2* acc, const GroupInfo& g, const int* flag_s, const int* flag_u,
+                              const GroupInfo* slot, int nb_max, const int* flag_s, const int* flag_u,
                               int64_t* flagged, unsigned long long* nflagged, int cap, cudaStream_t s);
 // dst (dense, element e) = src[sum_p bit_p(e) * st[p]]: bit p of e is dst's
 // p-th fastest index, st[p] its element stride in src.

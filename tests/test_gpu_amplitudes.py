@@ -196,3 +196,24 @@ def test_filter_recompute_and_discard():
         net = OTN.circuit_network(gates, n, I.bits_of(w, n), open_q)
         ref = OTN.contract_sliced(net, wires, [s for s in range(16) if s not in flagged])
         assert rel(got[bi], ref) <= 2e-2
+
+
+@pytest.mark.parametrize("mode", ["c64", "split_bf16", "scaled_fp16"])
+def test_graph_replay_and_autotune_give_identical_sums(mode):
+    """Batching: the per-group launch sequences replayed from CUDA graphs and
+    the autotuned tensor-core tiles change neither the arithmetic nor its
+    order, so the sums are bit-identical; several groups and a partial last
+    group exercise graph reuse and the direct fallback."""
+    T = tnlib()
+    rows, cols, depth, seed, open_q = 4, 5, 14, 12, (14, 15, 16, 17, 18, 19)
+    n = rows * cols
+    p = _setup(T, rows, cols, depth, seed, open_q, num_sliced=3, search_trials=32, seed=3)
+    words = I.bitstrings(n, 3, seed)
+    base = p.contract_amplitudes(words, precision=mode, units_per_group=3)
+    for _ in range(2):
+        g = p.contract_amplitudes(words, precision=mode, units_per_group=3, use_graph=1)
+        assert np.array_equal(g, base)
+    t = p.contract_amplitudes(words, precision=mode, units_per_group=3, autotune=1)
+    assert np.array_equal(t, base)
+    t = p.contract_amplitudes(words, precision=mode, units_per_group=3, autotune=1, use_graph=1)
+    assert np.array_equal(t, base)
