@@ -202,7 +202,7 @@ typedef struct {
   int32_t units_per_group;  /* slices contracted together per launch; 0 = auto */
   int32_t overflow_policy;  /* scaled modes: 0 = recompute a flagged slice in complex64, 1 = discard it (counted) */
   int32_t use_graph;        /* 1 = capture each group's launch sequence once per geometry as a CUDA graph and
-                               replay it (not with profile or test_flag_every) */
+                               replay it (needs a non-NULL stream; not with profile or test_flag_every) */
   int32_t profile;          /* 1 = bracket every kernel launch with CUDA events and fill the per-class figures */
   int32_t test_flag_every;  /* scaled modes, testing: > 0 flags every slice whose id is a multiple of it, so the
                                recompute / discard paths run without a real under/overflow; 0 = off */
@@ -236,6 +236,71 @@ typedef struct {
  * on opts->stream.  report may be NULL. */
 tn_status tn_contract_amplitudes(tn_plan_t* p, const uint64_t* bitstrings, int64_t nb, double* out,
                                  const tn_exec_opts* opts, tn_report* report);
+
+/* ------------------------------------------------------------------ */
+/* Serving: continuous batching of amplitude requests (the paper treats  */
+/* slices as independent sub-tasks, Sec. "A Customized Parallelization  */
+/* Scheme"; here one GPU interleaves the slices of many requests)        */
+/* ------------------------------------------------------------------ */
+
+typedef struct tn_server_s tn_server;
+
+typedef struct {
+  int32_t max_inflight;          /* requests contracted concurrently, one CUDA stream each; 0 = 4 (max 64) */
+  int32_t slices_per_quantum;    /* slices of one request queued per scheduling turn; 0 = 64 */
+  int32_t precision;             /* default TN_PREC_* of requests that ask for -1 */
+  int32_t plan_trials;           /* order-search restarts per new circuit; 0 = 16 */
+  int64_t hbm_budget_bytes;      /* device memory admitted requests may hold; 0 = 60% of the free memory */
+  double max_log2_cmac;          /* cost cap (log2 complex MACs of a request); 0 = 48 */
+  int32_t max_log2_intermediate; /* per-slice width cap when planning; 0 = 27 */
+  int32_t reserved;
+} tn_server_opts;
+
+/* One request: the amplitudes of nb bitstrings of the seeded random circuit
+ * (tn_random_circuit(rows, cols, depth, seed)) with its last num_open qubits
+ * open (2^num_open amplitudes per bitstring, batch index as in
+ * tn_contract_amplitudes). */
+typedef struct {
+  int32_t rows, cols, depth;
+  int32_t num_open;              /* 0 .. 12 */
+  uint64_t seed;
+  int64_t nb;                    /* >= 1 */
+  const uint64_t* bitstrings;    /* host, nb * ceil(n/64) words; copied by tn_submit */
+  int32_t precision;             /* TN_PREC_*; -1 = the server default */
+  int32_t reserved;
+} tn_request;
+
+typedef struct {
+  double submit_to_done_ms;      /* latency seen by the caller */
+  double queue_ms;               /* submit -> admitted (planning and waiting for a slot / budget) */
+  double device_ms;              /* admitted -> amplitudes back on the host */
+  double flops;                  /* counted flops of the request */
+  int64_t slices;
+  int32_t status;                /* the request's tn_status */
+  int32_t num_open;
+  int64_t nb;
+  uint64_t plan_hash;
+  int32_t planned_here;          /* 1 = this request ran the planner (plan cache miss) */
+  int32_t reserved;
+} tn_request_stats;
+
+/* Creates a server on the current CUDA device with a planner thread and a
+ * scheduler thread.  Requests are admitted in arrival order when an in-flight
+ * slot is free and their estimated device footprint fits the budget; admitted
+ * requests advance one quantum of slices per turn each, on their own streams.
+ * A request's amplitudes are bit-identical whatever runs beside it. */
+tn_status tn_server_create(const tn_server_opts* opts, tn_server** out);
+/* Queues a request (arguments validated here; TN_ETOOBIG for a cost above the
+ * cap and TN_EHBM for a request that can never fit are reported by tn_wait). */
+tn_status tn_submit(tn_server* s, const tn_request* req, int64_t* ticket);
+tn_status tn_poll(tn_server* s, int64_t ticket, int32_t* done);
+/* Waits (timeout_s <= 0: no limit) for a request, copies its nb * 2^num_open
+ * complex128 amplitudes to out (capacity in complex values), fills stats
+ * (may be NULL), releases the ticket and returns the request's status. */
+tn_status tn_wait(tn_server* s, int64_t ticket, double* out, int64_t capacity, tn_request_stats* stats,
+                  double timeout_s);
+/* Stops the threads, waits for the device and frees everything. */
+void tn_server_destroy(tn_server* s);
 
 /* ------------------------------------------------------------------ */
 /* One pairwise contraction (Sec. "Tensor Contraction Using Fused       */

@@ -9,11 +9,11 @@ import ctypes as C
 
 import numpy as np
 
-from ._abi import (PAIR_ALGO, PREC, ExecOpts, Gate, NetworkInfo, PlanInfo, PlanOpts, Report, TnError, check,
-                   i32array, lib)
+from ._abi import (PAIR_ALGO, PREC, ExecOpts, Gate, NetworkInfo, PlanInfo, PlanOpts, Report, Request,
+                   RequestStats, ServerOpts, TnError, check, i32array, lib)
 
 __all__ = ["Circuit", "Network", "Plan", "random_circuit", "circuit_from_gates", "build_network", "plan",
-           "contract_pair", "contract_pair_noalloc", "TnError", "PREC", "version"]
+           "contract_pair", "contract_pair_noalloc", "Server", "TnError", "PREC", "version"]
 
 
 def version():
@@ -244,3 +244,63 @@ def contract_pair_noalloc(A, a_labels, B, b_labels, Cout, c_labels, stream=None)
     s = C.c_void_p(getattr(stream, "cuda_stream", stream) if stream is not None else None)
     check(lib().tn_contract_pair_noalloc(_ptr(A), pa, len(la), _ptr(B), pb, len(lb), _ptr(Cout), pc, len(lc), s))
     return Cout
+
+
+class Server:
+    """Continuous-batching amplitude server (tn_server_*): requests for seeded
+    random circuits of any grid and depth are planned, admitted by device
+    memory and in-flight slots, and interleaved slice quantum by quantum."""
+
+    def __init__(self, max_inflight=4, slices_per_quantum=64, precision="c64", plan_trials=16,
+                 hbm_budget_bytes=0, max_log2_cmac=0.0, max_log2_intermediate=0):
+        o = ServerOpts()
+        o.max_inflight = max_inflight
+        o.slices_per_quantum = slices_per_quantum
+        o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+        o.plan_trials = plan_trials
+        o.hbm_budget_bytes = hbm_budget_bytes
+        o.max_log2_cmac = max_log2_cmac
+        o.max_log2_intermediate = max_log2_intermediate
+        h = C.c_void_p()
+        check(lib().tn_server_create(C.byref(o), C.byref(h)))
+        self._h = h
+        self._k = {}
+
+    def submit(self, rows, cols, depth, seed, num_open, bitstrings, precision=None):
+        b = np.ascontiguousarray(np.asarray(bitstrings, dtype=np.uint64))
+        if b.ndim == 1:
+            b = b.reshape(-1, 1)
+        r = Request()
+        r.rows, r.cols, r.depth, r.num_open, r.seed = rows, cols, depth, num_open, seed
+        r.nb = b.shape[0]
+        r.bitstrings = b.ctypes.data
+        r.precision = -1 if precision is None else (PREC[precision] if isinstance(precision, str) else int(precision))
+        t = C.c_int64()
+        check(lib().tn_submit(self._h, C.byref(r), C.byref(t)))
+        self._k[t.value] = (b.shape[0], num_open)
+        return t.value
+
+    def poll(self, ticket):
+        d = C.c_int32()
+        check(lib().tn_poll(self._h, ticket, C.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket, timeout=0.0):
+        """(complex128 amplitudes (nb, 2^num_open), stats dict); raises TnError
+        with the request's status when it failed."""
+        nb, k = self._k.pop(ticket)
+        out = np.zeros((nb, 1 << k), dtype=np.complex128)
+        st = RequestStats()
+        status = lib().tn_wait(self._h, ticket, out.ctypes.data, out.size, C.byref(st), timeout)
+        stats = {f: getattr(st, f) for f, _ in RequestStats._fields_}
+        if status != 0:
+            raise TnError(status, lib().tn_last_error().decode())
+        return out, stats
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tn_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

@@ -57,6 +57,24 @@ class ExecOpts(C.Structure):
                 ("test_flag_every", C.c_int32), ("autotune", C.c_int32)]
 
 
+class ServerOpts(C.Structure):
+    _fields_ = [("max_inflight", C.c_int32), ("slices_per_quantum", C.c_int32), ("precision", C.c_int32),
+                ("plan_trials", C.c_int32), ("hbm_budget_bytes", C.c_int64), ("max_log2_cmac", C.c_double),
+                ("max_log2_intermediate", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("rows", C.c_int32), ("cols", C.c_int32), ("depth", C.c_int32), ("num_open", C.c_int32),
+                ("seed", C.c_uint64), ("nb", C.c_int64), ("bitstrings", C.c_void_p), ("precision", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class RequestStats(C.Structure):
+    _fields_ = [("submit_to_done_ms", C.c_double), ("queue_ms", C.c_double), ("device_ms", C.c_double),
+                ("flops", C.c_double), ("slices", C.c_int64), ("status", C.c_int32), ("num_open", C.c_int32),
+                ("nb", C.c_int64), ("plan_hash", C.c_uint64), ("planned_here", C.c_int32), ("reserved", C.c_int32)]
+
+
 class Report(C.Structure):
     _fields_ = [("device_ms", C.c_double), ("flops", C.c_double), ("flops_equivalent", C.c_double),
                 ("units", C.c_int64), ("kernel_launches", C.c_int64), ("flagged_units", C.c_int64),
@@ -89,6 +107,11 @@ SIGNATURES = {
                                          C.POINTER(Report)]),
     "tn_contract_pair": (C.c_int, [C.c_void_p, I32P, C.c_int32, C.c_void_p, I32P, C.c_int32,
                                    C.c_void_p, I32P, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
+    "tn_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(P)]),
+    "tn_submit": (C.c_int, [P, C.POINTER(Request), C.POINTER(C.c_int64)]),
+    "tn_poll": (C.c_int, [P, C.c_int64, C.POINTER(C.c_int32)]),
+    "tn_wait": (C.c_int, [P, C.c_int64, C.c_void_p, C.c_int64, C.POINTER(RequestStats), C.c_double]),
+    "tn_server_destroy": (None, [P]),
     "tn_contract_pair_noalloc": (C.c_int, [C.c_void_p, I32P, C.c_int32, C.c_void_p, I32P, C.c_int32,
                                            C.c_void_p, I32P, C.c_int32, C.c_void_p]),
 }

@@ -393,15 +393,27 @@ tn_status run_misc(Ctx& c, cudaError_t e, const char* what) {
 }  // namespace
 
 static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double* out, const tn_exec_opts& o,
-                               tn_report* rep, bool clear_out);
+                               tn_report* rep, bool clear_out, int flags = 3);
 
 tn_status contract_amplitudes(Plan& P, const uint64_t* bits, int64_t nb, double* out, const tn_exec_opts& o,
                               tn_report* rep) {
   return contract_core(P, bits, nb, out, o, rep, true);
 }
 
+tn_status contract_amplitudes_ex(Plan& P, const uint64_t* bits, int64_t nb, double* out, const tn_exec_opts& o,
+                                 tn_report* rep, bool clear_out, int flags) {
+  return contract_core(P, bits, nb, out, o, rep, clear_out, flags);
+}
+
+int64_t executor_bytes(const Plan& P) {
+  const Executor* E = P.exec;
+  if (!E) return 0;
+  return 8 * (E->sarena_cap + E->parena_cap + P.invariant_elems + P.leaf_store_elems) + 2 * E->scratch_cap +
+         E->spool_cap;
+}
+
 static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double* out, const tn_exec_opts& o,
-                               tn_report* rep, bool clear_out) {
+                               tn_report* rep, bool clear_out, int flags) {
   const int n = P.net.n;
   const int k = (int)P.net.open_qubits.size();
   const int words = std::max(1, (n + 63) / 64);
@@ -533,7 +545,7 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
   if (!o.device_io && nb > 0)
     CK(cudaMemcpyAsync((void*)d_bits, bits, nb * words * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
   if (nout > 0 && clear_out) CK(cudaMemsetAsync(d_acc, 0, nout * sizeof(double2), st));
-  if (scaled) CK(cudaMemsetAsync(E.nflagged, 0, sizeof(unsigned long long), st));
+  if (scaled && (flags & 1)) CK(cudaMemsetAsync(E.nflagged, 0, sizeof(unsigned long long), st));
   Geo g;
   if (!E.inv_ready) {
     // invariant steps once, always in complex64 so that any later precision can use them
@@ -597,7 +609,8 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
     for (auto& t : E.tuned) have |= t.precision == c.precision;
     c.tuning = !have;
   }
-  const bool graphs = o.use_graph && !o.profile && !(scaled && o.test_flag_every > 0);
+  // (stream capture needs an explicit stream: the legacy default stream cannot be captured)
+  const bool graphs = o.use_graph && st != nullptr && !o.profile && !(scaled && o.test_flag_every > 0);
   // One launch sequence (the slice-only steps of a group, or the per-unit
   // steps of a group and its accumulation), replayed from a graph when allowed.
   auto sequence = [&](int phase, const Geo& gg) -> tn_status {
@@ -715,7 +728,7 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
   // ---- the filter: units flagged in a scaled precision are recomputed in
   // complex64 (policy 0) or left out and counted (policy 1)
   int64_t nflag = 0, recomputed = 0, discarded = 0;
-  if (scaled && nb > 0) {
+  if (scaled && nb > 0 && (flags & 2)) {
     unsigned long long hn = 0;
     CK(cudaMemcpyAsync(&hn, E.nflagged, sizeof(hn), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

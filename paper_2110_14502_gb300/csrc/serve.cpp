@@ -1,0 +1,484 @@
+// Serving: continuous batching of amplitude requests on one GPU.
+//
+// The paper's parallelisation (Sec. "A Customized Parallelization Scheme")
+// treats slices as independent sub-tasks; here the same independence lets one
+// GPU interleave the slices of many requests.  Requests for circuits of any
+// grid size and depth arrive at any time (tn_submit, any thread).  A planner
+// thread builds each request's network and plan (plans are cached per circuit
+// and open-qubit count; every admitted request gets its own copy with its own
+// device state, so a copy never shares buffers).  A scheduler thread admits
+// planned requests in arrival order while an in-flight slot is free and their
+// estimated device footprint fits the HBM budget, then interleaves them: each
+// turn queues one quantum (a group of consecutive slices) of every admitted
+// request on that request's own CUDA stream, so the requests' work overlaps on
+// the device.  A request whose slices are all queued gets its amplitudes copied
+// back; when that copy has completed it is done, its slot and budget are freed
+// and the next requests are admitted.  The FP64 sum of a request runs in slice
+// order whatever else is in flight, so a result is bit-identical alone and in
+// the mix.  Requests whose plan exceeds the cost cap fail with TN_ETOOBIG, and
+// ones that could never fit the budget with TN_EHBM; neither is dropped silently.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "tn_internal.h"
+
+namespace tn {
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+enum ReqState { RS_PENDING, RS_READY, RS_ACTIVE, RS_FINISHING, RS_DONE };
+
+struct Request {
+  int64_t ticket = 0;
+  tn_request params{};
+  std::vector<uint64_t> bits;
+  int32_t precision = 0;
+  ReqState state = RS_PENDING;
+  tn_status status = TN_OK;
+  std::string error;
+  std::unique_ptr<tn_plan_s> plan;  // own copy: own device state
+  int64_t ns = 0, cursor = 0, q = 1;
+  int64_t footprint = 0;
+  int words = 1, k = 0;
+  uint64_t* d_bits = nullptr;
+  double* d_acc = nullptr;
+  double* h_out = nullptr;  // pinned
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done_ev = nullptr;
+  std::vector<cudaEvent_t> quanta;  // events of queued quanta (bounded look-ahead)
+  Clock::time_point t_submit, t_admit, t_done;
+  bool planned_here = false;
+};
+
+struct PlanKey {
+  int rows, cols, depth, open;
+  uint64_t seed;
+  bool operator<(const PlanKey& o) const {
+    return std::tie(rows, cols, depth, open, seed) < std::tie(o.rows, o.cols, o.depth, o.open, o.seed);
+  }
+};
+
+}  // namespace
+
+struct Server {
+  tn_server_opts opts{};
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  int64_t next_ticket = 1;
+  std::map<int64_t, std::shared_ptr<Request>> reqs;
+  std::deque<std::shared_ptr<Request>> to_plan, ready;
+  std::vector<std::shared_ptr<Request>> active;
+  std::map<PlanKey, std::shared_ptr<tn_plan_s>> plan_cache;
+  int64_t budget = 0, in_use = 0;
+  std::vector<cudaStream_t> streams;  // one per slot
+  std::thread planner, scheduler;
+};
+
+namespace {
+
+tn_status plan_request(Server& S, Request& R) {
+  const tn_request& p = R.params;
+  PlanKey key{p.rows, p.cols, p.depth, p.num_open, p.seed};
+  std::shared_ptr<tn_plan_s> cached;
+  {
+    std::lock_guard<std::mutex> g(S.mu);
+    auto it = S.plan_cache.find(key);
+    if (it != S.plan_cache.end()) cached = it->second;
+  }
+  if (!cached) {
+    tn_circuit* c = nullptr;
+    tn_status st = tn_random_circuit(p.rows, p.cols, p.depth, p.seed, &c);
+    if (st != TN_OK) return st;
+    const int n = p.rows * p.cols;
+    std::vector<int32_t> open;
+    for (int q = n - p.num_open; q < n; ++q) open.push_back(q);
+    tn_network* net = nullptr;
+    st = tn_build_network(c, open.data(), (int32_t)open.size(), &net);
+    tn_free_circuit(c);
+    if (st != TN_OK) return st;
+    tn_plan_opts po{};
+    po.num_sliced = -1;
+    po.max_log2_intermediate = S.opts.max_log2_intermediate;
+    po.search_trials = S.opts.plan_trials;
+    po.seed = 1;
+    po.max_log2_cmac = S.opts.max_log2_cmac;
+    tn_plan_t* pl = nullptr;
+    st = tn_plan(net, &po, &pl);
+    tn_free_network(net);
+    if (st != TN_OK) return st;
+    cached.reset(pl);
+    R.planned_here = true;
+    std::lock_guard<std::mutex> g(S.mu);
+    S.plan_cache[key] = cached;
+  }
+  auto* copy = new (std::nothrow) tn_plan_s(cached->plan);
+  if (!copy) return fail(TN_ENOMEM, "serving: out of host memory");
+  R.plan.reset(copy);
+  const Plan& P = R.plan->plan;
+  R.ns = int64_t(1) << P.sliced.size();
+  R.q = std::min<int64_t>(R.ns, std::max(1, S.opts.slices_per_quantum));
+  R.k = (int)P.net.open_qubits.size();
+  R.words = std::max(1, (P.net.n + 63) / 64);
+  const int64_t gb = std::min<int64_t>(std::max<int64_t>(R.params.nb, 1), 256);
+  const int64_t arena = 8 * R.q * (P.slice_arena_elems + gb * P.unit_arena_elems);
+  // arenas + operand planes (bounded by the arenas) + leaves, invariants, I/O
+  R.footprint = arena + arena / 2 + 8 * (P.invariant_elems + P.leaf_store_elems) +
+                16 * (R.params.nb << R.k) + (int64_t(32) << 20);
+  return TN_OK;
+}
+
+void planner_loop(Server* S) {
+  cudaSetDevice(S->device);
+  for (;;) {
+    std::shared_ptr<Request> R;
+    {
+      std::unique_lock<std::mutex> g(S->mu);
+      S->cv.wait(g, [&] { return S->stop || !S->to_plan.empty(); });
+      if (S->stop) return;
+      R = S->to_plan.front();
+      S->to_plan.pop_front();
+    }
+    tn_status st = plan_request(*S, *R);
+    std::lock_guard<std::mutex> g(S->mu);
+    if (st != TN_OK) {
+      R->status = st;
+      R->error = tn_last_error();
+      R->state = RS_DONE;
+      R->t_done = Clock::now();
+    } else if (R->footprint > S->budget) {
+      R->status = fail(TN_EHBM, "serving: request %lld needs about %lld bytes, the budget is %lld",
+                       (long long)R->ticket, (long long)R->footprint, (long long)S->budget);
+      R->error = tn_last_error();
+      R->state = RS_DONE;
+      R->t_done = Clock::now();
+    } else {
+      R->state = RS_READY;
+      S->ready.push_back(R);
+    }
+    S->cv.notify_all();
+  }
+}
+
+void release(Server& S, Request& R) {
+  cudaFreeAsync(R.d_bits, R.stream);
+  cudaFreeAsync(R.d_acc, R.stream);
+  R.d_bits = nullptr;
+  R.d_acc = nullptr;
+  for (auto ev : R.quanta) cudaEventDestroy(ev);
+  R.quanta.clear();
+  if (R.done_ev) cudaEventDestroy(R.done_ev);
+  R.done_ev = nullptr;
+  S.in_use -= R.footprint;
+  // the request's plan copy keeps its arenas until the request is released by tn_wait
+}
+
+tn_status admit(Server& S, Request& R, cudaStream_t stream) {
+  R.stream = stream;
+  const int64_t nout = R.params.nb << R.k;
+  cudaError_t e = cudaMallocAsync(&R.d_bits, std::max<int64_t>(R.bits.size(), 1) * sizeof(uint64_t), stream);
+  if (e == cudaSuccess) e = cudaMallocAsync(&R.d_acc, std::max<int64_t>(nout, 1) * 16, stream);
+  if (e == cudaSuccess && !R.bits.empty())
+    e = cudaMemcpyAsync(R.d_bits, R.bits.data(), R.bits.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess && !R.h_out) e = cudaMallocHost(&R.h_out, std::max<int64_t>(nout, 1) * 16);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&R.done_ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(TN_ECUDA, "serving: admitting request %lld: %s", (long long)R.ticket, cudaGetErrorString(e));
+  }
+  R.t_admit = Clock::now();
+  return TN_OK;
+}
+
+// Queue the next quantum of R (slices cursor .. cursor+q-1); at the end queue
+// the copy of the amplitudes back.
+tn_status step_request(Request& R) {
+  tn_exec_opts o{};
+  o.stream = R.stream;
+  o.precision = R.precision;
+  o.device_io = 1;
+  o.slice_begin = R.cursor;
+  o.slice_count = std::min<int64_t>(R.q, R.ns - R.cursor);
+  o.units_per_group = (int32_t)R.q;
+  o.use_graph = 1;
+  // one FP64 sum over all quanta: the filter list is reset by the first
+  // quantum and processed (recompute / discard) after the last
+  const bool first = R.cursor == 0, last = R.cursor + o.slice_count >= R.ns;
+  tn_status st = contract_amplitudes_ex(R.plan->plan, R.d_bits, R.params.nb, R.d_acc, o, nullptr, first,
+                                        (first ? 1 : 0) | (last ? 2 : 0));
+  if (st != TN_OK) return st;
+  R.cursor += o.slice_count;
+  cudaEvent_t ev;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+    cudaEventRecord(ev, R.stream);
+    R.quanta.push_back(ev);
+  }
+  if (R.cursor >= R.ns) {
+    const int64_t nout = R.params.nb << R.k;
+    cudaError_t e = cudaMemcpyAsync(R.h_out, R.d_acc, std::max<int64_t>(nout, 1) * 16, cudaMemcpyDeviceToHost, R.stream);
+    if (e == cudaSuccess) e = cudaEventRecord(R.done_ev, R.stream);
+    if (e != cudaSuccess) return fail(TN_ECUDA, "serving: %s", cudaGetErrorString(e));
+    R.state = RS_FINISHING;
+  }
+  return TN_OK;
+}
+
+void scheduler_loop(Server* S) {
+  cudaSetDevice(S->device);
+  std::vector<char> slot_busy(S->streams.size(), 0);
+  std::map<Request*, int> slot_of;
+  for (;;) {
+    std::vector<std::shared_ptr<Request>> act;
+    {
+      std::unique_lock<std::mutex> g(S->mu);
+      if (S->stop) return;
+      // admission: arrival order, a free slot and room in the budget
+      while (!S->ready.empty()) {
+        auto& R = S->ready.front();
+        int slot = -1;
+        for (size_t i = 0; i < slot_busy.size(); ++i)
+          if (!slot_busy[i]) { slot = (int)i; break; }
+        if (slot < 0 || S->in_use + R->footprint > S->budget) break;
+        tn_status st = admit(*S, *R, S->streams[slot]);
+        if (st != TN_OK) {
+          R->status = st;
+          R->error = tn_last_error();
+          R->state = RS_DONE;
+          R->t_done = Clock::now();
+          S->ready.pop_front();
+          S->cv.notify_all();
+          continue;
+        }
+        slot_busy[slot] = 1;
+        slot_of[R.get()] = slot;
+        S->in_use += R->footprint;
+        R->state = RS_ACTIVE;
+        S->active.push_back(R);
+        S->ready.pop_front();
+      }
+      act = S->active;
+      if (act.empty()) {
+        S->cv.wait_for(g, std::chrono::milliseconds(2));
+        continue;
+      }
+    }
+    bool progressed = false;
+    for (auto& R : act) {
+      if (R->state == RS_ACTIVE) {
+        // bounded look-ahead: at most two quanta of a request in flight
+        while (!R->quanta.empty() && cudaEventQuery(R->quanta.front()) == cudaSuccess) {
+          cudaEventDestroy(R->quanta.front());
+          R->quanta.erase(R->quanta.begin());
+        }
+        if (R->quanta.size() < 2) {
+          tn_status st = step_request(*R);
+          progressed = true;
+          if (st != TN_OK) {
+            std::lock_guard<std::mutex> g(S->mu);
+            cudaStreamSynchronize(R->stream);
+            R->status = st;
+            R->error = tn_last_error();
+            R->state = RS_DONE;
+            R->t_done = Clock::now();
+            release(*S, *R);
+            slot_busy[slot_of[R.get()]] = 0;
+            slot_of.erase(R.get());
+            S->active.erase(std::find(S->active.begin(), S->active.end(), R));
+            S->cv.notify_all();
+          }
+        }
+      } else if (R->state == RS_FINISHING && cudaEventQuery(R->done_ev) == cudaSuccess) {
+        std::lock_guard<std::mutex> g(S->mu);
+        R->t_done = Clock::now();
+        R->state = RS_DONE;
+        release(*S, *R);
+        slot_busy[slot_of[R.get()]] = 0;
+        slot_of.erase(R.get());
+        S->active.erase(std::find(S->active.begin(), S->active.end(), R));
+        progressed = true;
+        S->cv.notify_all();
+      }
+    }
+    if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(200));
+  }
+}
+
+}  // namespace
+
+}  // namespace tn
+
+using namespace tn;
+
+struct tn_server_s {
+  Server s;
+};
+
+extern "C" tn_status tn_server_create(const tn_server_opts* opts, tn_server** out) {
+  if (!out) return fail(TN_EINVAL, "tn_server_create: out is NULL");
+  auto* h = new (std::nothrow) tn_server_s;
+  if (!h) return fail(TN_ENOMEM, "tn_server_create: out of host memory");
+  Server& S = h->s;
+  if (opts) S.opts = *opts;
+  if (S.opts.max_inflight <= 0) S.opts.max_inflight = 4;
+  if (S.opts.max_inflight > 64) S.opts.max_inflight = 64;
+  if (S.opts.slices_per_quantum <= 0) S.opts.slices_per_quantum = 64;
+  if (S.opts.plan_trials <= 0) S.opts.plan_trials = 16;
+  if (S.opts.max_log2_cmac <= 0) S.opts.max_log2_cmac = 48.0;
+  if (S.opts.max_log2_intermediate <= 0) S.opts.max_log2_intermediate = 27;
+  if (S.opts.precision < TN_PREC_C64 || S.opts.precision > TN_PREC_SCALED_BF16) {
+    delete h;
+    return fail(TN_EINVAL, "tn_server_create: unknown precision %d", S.opts.precision);
+  }
+  if (cudaGetDevice(&S.device) != cudaSuccess) {
+    delete h;
+    return fail(TN_ENODEVICE, "tn_server_create: no CUDA device");
+  }
+  size_t freeb = 0, totb = 0;
+  if (cudaMemGetInfo(&freeb, &totb) != cudaSuccess) {
+    delete h;
+    return fail(TN_ECUDA, "tn_server_create: cudaMemGetInfo failed");
+  }
+  S.budget = S.opts.hbm_budget_bytes > 0 ? S.opts.hbm_budget_bytes : (int64_t)(0.6 * (double)freeb);
+  for (int i = 0; i < S.opts.max_inflight; ++i) {
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      for (auto x : S.streams) cudaStreamDestroy(x);
+      delete h;
+      return fail(TN_ECUDA, "tn_server_create: stream creation failed");
+    }
+    S.streams.push_back(st);
+  }
+  S.planner = std::thread(planner_loop, &S);
+  S.scheduler = std::thread(scheduler_loop, &S);
+  *out = h;
+  return TN_OK;
+}
+
+extern "C" tn_status tn_submit(tn_server* h, const tn_request* req, int64_t* ticket) {
+  if (!h || !req || !ticket) return fail(TN_EINVAL, "tn_submit: NULL argument");
+  const int n = req->rows * req->cols;
+  if (req->rows < 1 || req->cols < 1 || n > 64 || req->depth < 0 || req->num_open < 0 || req->num_open > 12 ||
+      req->num_open > n || req->nb < 1 || !req->bitstrings)
+    return fail(TN_EINVAL, "tn_submit: bad request (grid %dx%d, depth %d, %d open, %lld bitstrings)", req->rows,
+                req->cols, req->depth, req->num_open, (long long)req->nb);
+  Server& S = h->s;
+  auto R = std::make_shared<Request>();
+  R->params = *req;
+  R->precision = req->precision < 0 ? S.opts.precision : req->precision;
+  if (R->precision < TN_PREC_C64 || R->precision > TN_PREC_SCALED_BF16)
+    return fail(TN_EINVAL, "tn_submit: unknown precision %d", R->precision);
+  const int words = std::max(1, (n + 63) / 64);
+  R->bits.assign(req->bitstrings, req->bitstrings + req->nb * words);
+  R->params.bitstrings = nullptr;
+  R->t_submit = Clock::now();
+  std::lock_guard<std::mutex> g(S.mu);
+  R->ticket = S.next_ticket++;
+  S.reqs[R->ticket] = R;
+  S.to_plan.push_back(R);
+  S.cv.notify_all();
+  *ticket = R->ticket;
+  return TN_OK;
+}
+
+extern "C" tn_status tn_poll(tn_server* h, int64_t ticket, int32_t* done) {
+  if (!h || !done) return fail(TN_EINVAL, "tn_poll: NULL argument");
+  std::lock_guard<std::mutex> g(h->s.mu);
+  auto it = h->s.reqs.find(ticket);
+  if (it == h->s.reqs.end()) return fail(TN_EINVAL, "tn_poll: unknown ticket %lld", (long long)ticket);
+  *done = it->second->state == RS_DONE;
+  return TN_OK;
+}
+
+extern "C" tn_status tn_wait(tn_server* h, int64_t ticket, double* out, int64_t capacity, tn_request_stats* stats,
+                             double timeout_s) {
+  if (!h) return fail(TN_EINVAL, "tn_wait: NULL server");
+  Server& S = h->s;
+  std::shared_ptr<Request> R;
+  {
+    std::unique_lock<std::mutex> g(S.mu);
+    auto it = S.reqs.find(ticket);
+    if (it == S.reqs.end()) return fail(TN_EINVAL, "tn_wait: unknown ticket %lld", (long long)ticket);
+    R = it->second;
+    auto pred = [&] { return R->state == RS_DONE; };
+    if (timeout_s > 0) {
+      if (!S.cv.wait_for(g, std::chrono::duration<double>(timeout_s), pred))
+        return fail(TN_ETIMEOUT, "tn_wait: request %lld not done after %.3f s", (long long)ticket, timeout_s);
+    } else {
+      S.cv.wait(g, pred);
+    }
+    S.reqs.erase(ticket);
+  }
+  const int64_t nout = R->params.nb << R->k;
+  if (stats) {
+    std::memset(stats, 0, sizeof *stats);
+    auto ms = [](Clock::time_point a, Clock::time_point b) {
+      return std::chrono::duration<double, std::milli>(b - a).count();
+    };
+    stats->submit_to_done_ms = ms(R->t_submit, R->t_done);
+    stats->queue_ms = R->status == TN_OK ? ms(R->t_submit, R->t_admit) : 0.0;
+    stats->device_ms = R->status == TN_OK ? ms(R->t_admit, R->t_done) : 0.0;
+    stats->slices = R->ns;
+    stats->status = R->status;
+    stats->num_open = R->k;
+    stats->nb = R->params.nb;
+    if (R->plan) {
+      const Plan& P = R->plan->plan;
+      stats->flops = 8.0 * ((double)R->ns * P.cmac_slice_only + (double)R->params.nb * R->ns *
+                                                                     (P.cmac_per_slice - P.cmac_slice_only));
+      stats->plan_hash = P.hash;
+    }
+    stats->planned_here = R->planned_here;
+  }
+  tn_status st = R->status;
+  if (st == TN_OK && out) {
+    if (capacity < nout) {
+      st = fail(TN_EINVAL, "tn_wait: capacity %lld < %lld complex results", (long long)capacity, (long long)nout);
+    } else {
+      std::memcpy(out, R->h_out, nout * 16);
+    }
+  } else if (st != TN_OK) {
+    fail(st, "%s", R->error.c_str());
+  }
+  if (R->h_out) cudaFreeHost(R->h_out);
+  R->h_out = nullptr;
+  R->plan.reset();  // frees the request's device state
+  return st;
+}
+
+extern "C" void tn_server_destroy(tn_server* h) {
+  if (!h) return;
+  Server& S = h->s;
+  {
+    std::lock_guard<std::mutex> g(S.mu);
+    S.stop = true;
+    S.cv.notify_all();
+  }
+  if (S.planner.joinable()) S.planner.join();
+  if (S.scheduler.joinable()) S.scheduler.join();
+  cudaDeviceSynchronize();
+  for (auto& kv : S.reqs) {
+    Request& R = *kv.second;
+    if (R.d_bits) cudaFree(R.d_bits);
+    if (R.d_acc) cudaFree(R.d_acc);
+    if (R.h_out) cudaFreeHost(R.h_out);
+    for (auto ev : R.quanta) cudaEventDestroy(ev);
+    if (R.done_ev) cudaEventDestroy(R.done_ev);
+    R.plan.reset();
+  }
+  for (auto x : S.streams) cudaStreamDestroy(x);
+  delete h;
+}

@@ -80,7 +80,7 @@ struct LeafUse {
 
 struct Executor;  // device-side state (executor.cu)
 
-struct Plan {
+struct PlanData {
   Network net;
   tn_plan_opts opts{};
   std::vector<int> sliced;      // labels; bit j of the slice id -> sliced[j]
@@ -97,7 +97,15 @@ struct Plan {
   int max_width = 0;
   std::vector<uint8_t> bytes;     // serialized form
   uint64_t hash = 0;
+};
+
+// A plan plus its device state.  Copies share nothing on the device: a copy
+// starts without an executor and allocates its own on first use.
+struct Plan : PlanData {
   Executor* exec = nullptr;
+  Plan() = default;
+  Plan(const Plan& o) : PlanData(o), exec(nullptr) {}
+  Plan& operator=(const Plan&) = delete;
   ~Plan();
 };
 
@@ -109,9 +117,21 @@ tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& plan);
 void destroy_executor(Executor* e);
 tn_status contract_amplitudes(Plan& p, const uint64_t* bits, int64_t nb, double* out,
                               const tn_exec_opts& o, tn_report* rep);
+// As above; clear_out = false adds into `out` (device I/O) instead of
+// overwriting it.  flags: bit 0 = reset the list of filter-flagged units at
+// the start, bit 1 = run the filter (recompute / discard) at the end; a caller
+// splitting one sum over several calls resets on the first and filters on the last.
+tn_status contract_amplitudes_ex(Plan& p, const uint64_t* bits, int64_t nb, double* out, const tn_exec_opts& o,
+                                 tn_report* rep, bool clear_out, int flags);
+// Device bytes held by the plan's executor (0 before its first use).
+int64_t executor_bytes(const Plan& p);
 
 }  // namespace tn
 
 struct tn_circuit_s { tn::Circuit c; };
 struct tn_network_s { tn::Network net; };
-struct tn_plan_s { tn::Plan plan; };
+struct tn_plan_s {
+  tn::Plan plan;
+  tn_plan_s() = default;
+  explicit tn_plan_s(const tn::Plan& p) : plan(p) {}
+};

@@ -209,11 +209,13 @@ def test_graph_replay_and_autotune_give_identical_sums(mode):
     n = rows * cols
     p = _setup(T, rows, cols, depth, seed, open_q, num_sliced=3, search_trials=32, seed=3)
     words = I.bitstrings(n, 3, seed)
-    base = p.contract_amplitudes(words, precision=mode, units_per_group=3)
+    import torch
+    s = torch.cuda.Stream()  # graphs need an explicit stream
+    base = p.contract_amplitudes(words, precision=mode, units_per_group=3, stream=s)
     for _ in range(2):
-        g = p.contract_amplitudes(words, precision=mode, units_per_group=3, use_graph=1)
+        g = p.contract_amplitudes(words, precision=mode, units_per_group=3, use_graph=1, stream=s)
         assert np.array_equal(g, base)
-    t = p.contract_amplitudes(words, precision=mode, units_per_group=3, autotune=1)
+    t = p.contract_amplitudes(words, precision=mode, units_per_group=3, autotune=1, stream=s)
     assert np.array_equal(t, base)
-    t = p.contract_amplitudes(words, precision=mode, units_per_group=3, autotune=1, use_graph=1)
+    t = p.contract_amplitudes(words, precision=mode, units_per_group=3, autotune=1, use_graph=1, stream=s)
     assert np.array_equal(t, base)
