@@ -18,6 +18,7 @@ Modes:
   python bench.py [--gpus N --steps K --warmup W] [--precision split_bf16|c64]
   python bench.py --impl reference ...   # the CPU oracle as the reference arm
   python bench.py --micro [--shape m,n,k]  # pairwise contraction microbenchmark
+  python bench.py --serve [--requests R]   # serving: batched mixed precision vs plain complex64
 Under torchrun each rank runs its own batches (weak scaling, no collective on
 the data path); rank 0 prints the max-over-ranks timing.
 """
@@ -360,6 +361,91 @@ def run_micro(args):
     return res
 
 
+def serve_workload(nreq, seed=5):
+    """Request stream of the serving benchmark: grids R x C with R, C in [4, 7]
+    and |R - C| <= 1, depth uniform in [10, 24], circuit seed 5 * 2^32 + id,
+    m amplitudes log-uniform in [1, 4096] served as one bitstring with
+    k = ceil(log2 m) open qubits; Poisson arrival gaps (unit rate)."""
+    import tn_inputs as I
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(nreq):
+        r = int(rng.integers(4, 8))
+        c = int(np.clip(r + rng.integers(-1, 2), 4, 7))
+        depth = int(rng.integers(10, 25))
+        m = int(np.exp(rng.uniform(0, np.log(4096))))
+        k = min(12, int(np.ceil(np.log2(max(m, 1)))))
+        s = 5 * 2 ** 32 + i
+        reqs.append(dict(rows=r, cols=c, depth=depth, seed=s, num_open=k,
+                         bitstrings=I.bitstrings(r * c, 1, s)))
+    gaps = rng.exponential(1.0, nreq)
+    return reqs, gaps
+
+
+def run_serve(args):
+    """Serving benchmark: the batched mixed-precision server against the plain
+    complex64 path that contracts one slice of one request at a time."""
+    import torch
+    import paper_2110_14502_gb300 as T
+    torch.cuda.set_device(0)
+    reqs, gaps = serve_workload(args.requests)
+    common = dict(plan_trials=8, max_log2_cmac=args.cost_cap, max_log2_intermediate=27, planner_threads=16)
+    # plans are cached per circuit: warm the cache once so both runs see planned circuits
+    warm = T.Server(max_inflight=8, slices_per_quantum=64, precision="c64", **common)
+
+    def closed_loop(srv, rate=None):
+        t0 = time.time()
+        tickets, lat, amps, rejected, flops = [], [], 0, 0, 0.0
+        start = time.time()
+        for i, r in enumerate(reqs):
+            if rate:
+                target = start + float(np.sum(gaps[:i + 1])) / rate
+                while time.time() < target:
+                    time.sleep(0.0002)
+            tickets.append(srv.submit(**r))
+        for t in tickets:
+            try:
+                out, st = srv.wait(t)
+                lat.append(st["submit_to_done_ms"])
+                amps += out.size
+                flops += st["flops"]
+            except T.TnError as e:
+                if e.status in (3, 6):
+                    rejected += 1
+                else:
+                    raise
+        dt = time.time() - t0
+        return dict(seconds=dt, amps=amps, amps_per_s=amps / dt, tflops=flops / dt / 1e12, rejected=rejected,
+                    p50_ms=float(np.percentile(lat, 50)) if lat else None,
+                    p99_ms=float(np.percentile(lat, 99)) if lat else None, served=len(lat))
+
+    pre = closed_loop(warm)
+    warm.close()
+    plain = T.Server(max_inflight=1, slices_per_quantum=1, precision="c64", **common)
+    batched = T.Server(max_inflight=8, slices_per_quantum=64, precision=args.precision, **common)
+    try:
+        # saturated throughput (every request submitted at once)
+        cap_plain = closed_loop(plain)
+        cap_batched = closed_loop(batched)
+        # latency under Poisson arrivals at 0.7 x the plain path's capacity (requests/s)
+        rate = 0.7 * cap_plain["served"] / cap_plain["seconds"]
+        lat_plain = closed_loop(plain, rate)
+        lat_batched = closed_loop(batched, rate)
+    finally:
+        plain.close()
+        batched.close()
+    line = {"metric": "serving amplitudes/s and p50/p99 latency", "value": round(cap_batched["amps_per_s"], 2),
+            "unit": "amplitudes/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"{args.requests} requests: grids 4x4..7x7 (|R-C|<=1), depth 10-24, 1-4096 "
+                                   f"amplitudes each, cost cap 2^{args.cost_cap} CMAC",
+                       "batched": f"8 in flight, 64-slice quanta, {args.precision}",
+                       "plain": "1 in flight, 1-slice quanta, c64"},
+            "batched_saturated": cap_batched, "plain_saturated": cap_plain,
+            "poisson_rate_req_per_s": rate, "batched_poisson": lat_batched, "plain_poisson": lat_plain,
+            "first_pass_with_planning": pre}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -372,11 +458,16 @@ def main():
     ap.add_argument("--shape", default=None)
     ap.add_argument("--random-layout", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serve", action="store_true")
+    ap.add_argument("--requests", type=int, default=100)
+    ap.add_argument("--cost-cap", type=float, default=40.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.micro:
         run_micro(args)
+    elif args.serve:
+        run_serve(args)
     else:
         run_ours(args)
 

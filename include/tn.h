@@ -253,7 +253,7 @@ typedef struct {
   int64_t hbm_budget_bytes;      /* device memory admitted requests may hold; 0 = 60% of the free memory */
   double max_log2_cmac;          /* cost cap (log2 complex MACs of a request); 0 = 48 */
   int32_t max_log2_intermediate; /* per-slice width cap when planning; 0 = 27 */
-  int32_t reserved;
+  int32_t planner_threads;       /* host threads planning new circuits concurrently; 0 = 4 (max 32) */
 } tn_server_opts;
 
 /* One request: the amplitudes of nb bitstrings of the seeded random circuit

@@ -498,6 +498,15 @@ tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& P) {
       }
     }
     reconfigure(leaves, B.pairs, {}, 6, 3);
+    if (opts.max_log2_cmac > 0) {
+      // slicing only adds work: a tree already above the cost cap is dropped unsliced
+      std::vector<LSet> st0;
+      node_sets(leaves, B.pairs, {}, st0);
+      double t0, c0;
+      int w0;
+      cost_of(st0, B.pairs, L, t0, c0, w0);
+      if (std::log2(std::max(c0, 1.0)) > opts.max_log2_cmac) continue;
+    }
     Eval ev = slice_tree(leaves, B.pairs, sliceable, opts.num_sliced, opts.max_log2_intermediate);
     if (!ev.sliced.empty()) {
       reconfigure(leaves, B.pairs, ev.sliced, 6, 3);
@@ -515,6 +524,8 @@ tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& P) {
       have = true;
     }
   }
+  if (!have)
+    return fail(TN_ETOOBIG, "tn_plan: every searched order costs more than the cap 2^%.1f CMAC", opts.max_log2_cmac);
   if (L > 2) {  // polish the winner with a wider window
     reconfigure(leaves, best_pairs, best.sliced, 8, 6);
     std::vector<LSet> st;

@@ -66,10 +66,19 @@ struct Request {
 struct PlanKey {
   int rows, cols, depth, open;
   uint64_t seed;
+  int trials, width;
+  double cap;
   bool operator<(const PlanKey& o) const {
-    return std::tie(rows, cols, depth, open, seed) < std::tie(o.rows, o.cols, o.depth, o.open, o.seed);
+    return std::tie(rows, cols, depth, open, seed, trials, width, cap) <
+           std::tie(o.rows, o.cols, o.depth, o.open, o.seed, o.trials, o.width, o.cap);
   }
 };
+
+// Plans are pure functions of the circuit and the planning options, so one
+// cache serves every server of the process (host memory only: copies of a
+// cached plan own their device state).
+std::mutex g_plan_mu;
+std::map<PlanKey, std::shared_ptr<tn_plan_s>> g_plan_cache;
 
 }  // namespace
 
@@ -83,22 +92,23 @@ struct Server {
   std::map<int64_t, std::shared_ptr<Request>> reqs;
   std::deque<std::shared_ptr<Request>> to_plan, ready;
   std::vector<std::shared_ptr<Request>> active;
-  std::map<PlanKey, std::shared_ptr<tn_plan_s>> plan_cache;
   int64_t budget = 0, in_use = 0;
   std::vector<cudaStream_t> streams;  // one per slot
-  std::thread planner, scheduler;
+  std::vector<std::thread> planners;
+  std::thread scheduler;
 };
 
 namespace {
 
 tn_status plan_request(Server& S, Request& R) {
   const tn_request& p = R.params;
-  PlanKey key{p.rows, p.cols, p.depth, p.num_open, p.seed};
+  PlanKey key{p.rows, p.cols, p.depth, p.num_open, p.seed, S.opts.plan_trials, S.opts.max_log2_intermediate,
+              S.opts.max_log2_cmac};
   std::shared_ptr<tn_plan_s> cached;
   {
-    std::lock_guard<std::mutex> g(S.mu);
-    auto it = S.plan_cache.find(key);
-    if (it != S.plan_cache.end()) cached = it->second;
+    std::lock_guard<std::mutex> g(g_plan_mu);
+    auto it = g_plan_cache.find(key);
+    if (it != g_plan_cache.end()) cached = it->second;
   }
   if (!cached) {
     tn_circuit* c = nullptr;
@@ -123,8 +133,8 @@ tn_status plan_request(Server& S, Request& R) {
     if (st != TN_OK) return st;
     cached.reset(pl);
     R.planned_here = true;
-    std::lock_guard<std::mutex> g(S.mu);
-    S.plan_cache[key] = cached;
+    std::lock_guard<std::mutex> g(g_plan_mu);
+    g_plan_cache[key] = cached;
   }
   auto* copy = new (std::nothrow) tn_plan_s(cached->plan);
   if (!copy) return fail(TN_ENOMEM, "serving: out of host memory");
@@ -362,7 +372,8 @@ extern "C" tn_status tn_server_create(const tn_server_opts* opts, tn_server** ou
     }
     S.streams.push_back(st);
   }
-  S.planner = std::thread(planner_loop, &S);
+  const int np_ = S.opts.planner_threads > 0 ? std::min(S.opts.planner_threads, 32) : 4;  // planner threads
+  for (int i = 0; i < np_; ++i) S.planners.push_back(std::thread(planner_loop, &S));
   S.scheduler = std::thread(scheduler_loop, &S);
   *out = h;
   return TN_OK;
@@ -467,7 +478,8 @@ extern "C" void tn_server_destroy(tn_server* h) {
     S.stop = true;
     S.cv.notify_all();
   }
-  if (S.planner.joinable()) S.planner.join();
+  for (auto& t : S.planners)
+    if (t.joinable()) t.join();
   if (S.scheduler.joinable()) S.scheduler.join();
   cudaDeviceSynchronize();
   for (auto& kv : S.reqs) {
