@@ -38,9 +38,11 @@ sys.path.insert(0, ROOT)
 
 ROWS, COLS, DEPTH, CSEED = 6, 6, 16, 2
 NSLICED = 10
+WIDTH_CAP = 0
 NOPEN = 6
 NBATCH, BSEED = 4, 2
 PLAN_TRIALS, PLAN_SEED = 64, 1
+SLICE_LIMIT = -1
 METRIC = "Contraction TFLOP/s & amplitudes/s at stated rel err vs FP64; p50/p99 latency"
 WORKLOAD = "6x6 grid, depth 1+16+1, fSim(pi/2,pi/6); 10 sliced indices (1024 slices); 6 open qubits; 4 batches x 64 amplitudes"
 
@@ -100,13 +102,24 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def use_8x8():
+    """The 8x8 configuration: 64 qubits, depth 1+20+1, seed 4, per-slice width
+    2^26, ten open qubits (1024 correlated amplitudes); the first 4096 of the
+    2^S slices are summed (a fidelity-4096/2^S partial sum)."""
+    global ROWS, COLS, DEPTH, CSEED, NSLICED, WIDTH_CAP, NOPEN, NBATCH, BSEED, PLAN_TRIALS, SLICE_LIMIT, WORKLOAD
+    ROWS, COLS, DEPTH, CSEED = 8, 8, 20, 4
+    NSLICED, WIDTH_CAP, NOPEN, NBATCH, BSEED, PLAN_TRIALS, SLICE_LIMIT = -1, 26, 10, 1, 4, 16, 4096
+    WORKLOAD = ("8x8 grid, depth 1+20+1, fSim(pi/2,pi/6); per-slice width 2^26; first 4096 slices; "
+                "10 open qubits; 1 batch x 1024 amplitudes")
+
+
 def make_workload(T, rank):
     c = T.random_circuit(ROWS, COLS, DEPTH, CSEED)
     n = ROWS * COLS
     open_q = list(range(n - NOPEN, n))
     net = T.build_network(c, open_q)
     t0 = time.time()
-    p = T.plan(net, num_sliced=NSLICED, search_trials=PLAN_TRIALS, seed=PLAN_SEED)
+    p = T.plan(net, num_sliced=NSLICED, max_log2_intermediate=WIDTH_CAP, search_trials=PLAN_TRIALS, seed=PLAN_SEED)
     plan_s = time.time() - t0
     import tn_inputs as I
     words = I.bitstrings(n, NBATCH, BSEED + 1000 * rank)
@@ -171,7 +184,7 @@ def run_ours(args):
     def step(profile=False):
         with torch.cuda.stream(stream):
             _, rep = p.contract_amplitudes(dwords, out=out, stream=stream, precision=args.precision,
-                                           profile=profile, report=True)
+                                           profile=profile, report=True, slice_count=SLICE_LIMIT)
         return rep
 
     for _ in range(args.warmup):
@@ -243,7 +256,7 @@ def run_ours(args):
     for _ in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.time()
-        p.contract_amplitudes(words, precision=args.precision)
+        p.contract_amplitudes(words, precision=args.precision, slice_count=SLICE_LIMIT)
         e2e_times.append(time.time() - t0)
     e2e_s = sum(e2e_times)
     e2e_flops = reps[0]["flops"] * len(e2e_times)
@@ -255,7 +268,7 @@ def run_ours(args):
                   "c64": "f32"}[args.precision],
         "data": "synthetic (seeded random circuit and bitstrings)",
         "config": {"workload": WORKLOAD, "precision": args.precision, "global_batch": amps // args.steps,
-                   "slices": info["num_slices"], "plan_hash": hex(info["hash"]),
+                   "slices": info["num_slices"] if SLICE_LIMIT < 0 else SLICE_LIMIT, "plan_hash": hex(info["hash"]),
                    "cmac_per_slice_log2": round(float(np.log2(info["cmac_per_slice"])), 3),
                    "max_log2_intermediate": info["max_log2_intermediate"],
                    "l2": "working set (>= 2^26-element intermediates per slice) larger than L2; no flush",
@@ -276,7 +289,7 @@ def run_ours(args):
         gpu1 = p.contract_amplitudes(words[:1], precision=args.precision, slice_begin=0, slice_count=1)[0]
         line["cpu_baseline"] = {"value": round(8 * cmac / dt / 1e12, 6), "unit": "TFLOP/s",
                                 "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": "slice 0 of batch 0 (64 amplitudes, 1/1024 of the slices), FP64 NumPy "
+                                "sample": f"slice 0 of batch 0 ({1 << NOPEN} amplitudes, one slice), FP64 NumPy "
                                           f"contraction in the plan's order, {dt:.1f} s"}
         line["rel_err_vs_fp64_sample"] = float(np.linalg.norm(gpu1 - v) / np.linalg.norm(v))
     if dist:
@@ -461,7 +474,10 @@ def main():
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--cost-cap", type=float, default=40.0)
+    ap.add_argument("--workload", default="6x6", choices=["6x6", "8x8"])
     args = ap.parse_args()
+    if args.workload == "8x8":
+        use_8x8()
     if args.impl == "reference":
         run_reference(args)
     elif args.micro:

@@ -288,49 +288,103 @@ void cost_of(const std::vector<LSet>& sets, const std::vector<int>& pairs, int L
 }
 
 // Greedy slicing: repeatedly remove the label (present in a widest node) that
-// gives the smallest (width, modelled time).
+// gives the smallest (width, modelled time).  Removing a label only changes
+// the steps and nodes that hold it, so each candidate is scored incrementally.
 Eval slice_tree(const std::vector<LSet>& leaves, const std::vector<int>& pairs, const LSet& sliceable,
                 int num_sliced, int cap) {
   const int L = (int)leaves.size();
+  const int nsteps = (int)pairs.size() / 2;
   Eval ev;
   std::vector<LSet> sets;
   node_sets(leaves, pairs, ev.sliced, sets);
-  cost_of(sets, pairs, L, ev.time, ev.cmac, ev.width);
+  // per step widths, per node sizes, and where every label occurs
+  std::vector<int> wa(nsteps), wb(nsteps), wc(nsteps), wu(nsteps);
+  std::vector<int> size(sets.size());
+  int maxlab = 0;
+  for (auto& st : sets)
+    for (int l : st) maxlab = std::max(maxlab, l + 1);
+  std::vector<std::vector<int>> in_node(maxlab), in_step(maxlab);
+  for (size_t v = 0; v < sets.size(); ++v) {
+    size[v] = (int)sets[v].size();
+    for (int l : sets[v]) in_node[l].push_back((int)v);
+  }
+  for (int t = 0; t < nsteps; ++t) {
+    const LSet &a = sets[pairs[2 * t]], &b = sets[pairs[2 * t + 1]];
+    wa[t] = (int)a.size();
+    wb[t] = (int)b.size();
+    wc[t] = (int)sets[L + t].size();
+    wu[t] = union_size(a, b);
+    LSet u;
+    std::set_union(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(u));
+    for (int l : u) in_step[l].push_back(t);
+  }
+  std::vector<char> removed(maxlab, 0);
+  auto totals = [&](double& time, double& cmac, int& width) {
+    time = 0; cmac = 0; width = 0;
+    for (int v : size) width = std::max(width, v);
+    for (int t = 0; t < nsteps; ++t) {
+      cmac += std::ldexp(1.0, wu[t]);
+      time += step_time(wa[t], wb[t], wc[t], wu[t]);
+    }
+  };
+  totals(ev.time, ev.cmac, ev.width);
   auto need_more = [&]() {
     if (num_sliced >= 0) return (int)ev.sliced.size() < num_sliced;
     return cap > 0 && ev.width > cap;
   };
   while (need_more()) {
+    // width histogram to update the maximum after a removal
+    std::vector<int> hist(ev.width + 2, 0);
+    for (int v : size) hist[v]++;
     LSet cand;
-    for (auto& s : sets)
-      if ((int)s.size() == ev.width)
-        for (int l : s)
-          if (contains(sliceable, l)) cand.push_back(l);
+    for (size_t v = 0; v < sets.size(); ++v)
+      if (size[v] == ev.width)
+        for (int l : sets[v])
+          if (!removed[l] && contains(sliceable, l)) cand.push_back(l);
     std::sort(cand.begin(), cand.end());
     cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
     if (cand.empty()) {  // widest nodes hold only open labels: slice elsewhere
-      for (auto& s : sets)
-        for (int l : s)
-          if (contains(sliceable, l)) cand.push_back(l);
-      std::sort(cand.begin(), cand.end());
-      cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+      for (int l = 0; l < maxlab; ++l)
+        if (!removed[l] && !in_node[l].empty() && contains(sliceable, l)) cand.push_back(l);
     }
     if (cand.empty()) break;
     int best = -1, bw = 0;
     double bt = 0;
     for (int l : cand) {
-      std::vector<int> s2 = ev.sliced;
-      s2.push_back(l);
-      std::vector<LSet> st;
-      node_sets(leaves, pairs, s2, st);
-      double t, c;
-      int w;
-      cost_of(st, pairs, L, t, c, w);
-      if (best < 0 || w < bw || (w == bw && t < bt)) { best = l; bw = w; bt = t; }
+      // new maximum width: nodes holding l shrink by one
+      int at_max = hist[ev.width], holding_max = 0;
+      for (int v : in_node[l]) holding_max += size[v] == ev.width;
+      const int w = (at_max > holding_max) ? ev.width : ev.width - 1;
+      double dt = 0;
+      for (int t : in_step[l]) {
+        const int a_has = std::binary_search(sets[pairs[2 * t]].begin(), sets[pairs[2 * t]].end(), l);
+        const int b_has = std::binary_search(sets[pairs[2 * t + 1]].begin(), sets[pairs[2 * t + 1]].end(), l);
+        const int c_has = a_has != b_has;
+        dt += step_time(wa[t] - a_has, wb[t] - b_has, wc[t] - c_has, wu[t] - 1) -
+              step_time(wa[t], wb[t], wc[t], wu[t]);
+      }
+      const double t_new = ev.time + dt;
+      if (best < 0 || w < bw || (w == bw && t_new < bt)) { best = l; bw = w; bt = t_new; }
     }
+    // apply the removal
+    for (int t : in_step[best]) {
+      const int a_has = std::binary_search(sets[pairs[2 * t]].begin(), sets[pairs[2 * t]].end(), best);
+      const int b_has = std::binary_search(sets[pairs[2 * t + 1]].begin(), sets[pairs[2 * t + 1]].end(), best);
+      wa[t] -= a_has;
+      wb[t] -= b_has;
+      wc[t] -= a_has != b_has;
+      wu[t] -= 1;
+    }
+    for (int v : in_node[best]) {
+      size[v] -= 1;
+      auto& st = sets[v];
+      st.erase(std::lower_bound(st.begin(), st.end(), best));
+    }
+    in_node[best].clear();
+    in_step[best].clear();
+    removed[best] = 1;
     ev.sliced.push_back(best);
-    node_sets(leaves, pairs, ev.sliced, sets);
-    cost_of(sets, pairs, L, ev.time, ev.cmac, ev.width);
+    totals(ev.time, ev.cmac, ev.width);
   }
   return ev;
 }

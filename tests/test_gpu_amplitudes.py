@@ -219,3 +219,29 @@ def test_graph_replay_and_autotune_give_identical_sums(mode):
     assert np.array_equal(t, base)
     t = p.contract_amplitudes(words, precision=mode, units_per_group=3, autotune=1, use_graph=1, stream=s)
     assert np.array_equal(t, base)
+
+
+def test_full_size_8x8_sampled_slices_vs_oracle():
+    """8x8 grid (64 qubits), depth 1+20+1, seed 4, per-slice width capped at
+    2^26, ten open qubits (1024 correlated amplitudes per bitstring): two
+    sampled slices against the oracle's FP64 contraction of the same slice
+    assignment, in complex64 and in split fp16."""
+    T = tnlib()
+    rows, cols, depth, seed = 8, 8, 20, 4
+    n = 64
+    open_q = tuple(range(54, 64))
+    p = _setup(T, rows, cols, depth, seed, open_q, max_log2_intermediate=26, search_trials=8, seed=1)
+    info = p.info()
+    assert info["max_log2_intermediate"] <= 26
+    wires = p.sliced_wires()
+    words = I.bitstrings(n, 1, seed)
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    bits = I.bits_of(words[0], n)
+    for s in (0, 4095):
+        fixed = {wires[j]: (s >> j) & 1 for j in range(len(wires))}
+        ref = replay(p, gates, n, bits, open_q, fixed)
+        got = p.contract_amplitudes(words, slice_begin=s, slice_count=1)[0]
+        assert got.shape == (1024,)
+        assert rel(got, ref) <= 1e-5, s
+        got = p.contract_amplitudes(words, slice_begin=s, slice_count=1, precision="split_fp16")[0]
+        assert rel(got, ref) <= 1e-4, s
