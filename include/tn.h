@@ -209,6 +209,10 @@ typedef struct {
   int32_t autotune;         /* 1 = time the tensor-core tile choices of every step on the first group of this
                                precision and keep the fastest (cached per plan; also in the file named by the
                                environment variable TN_AUTOTUNE_CACHE when it is set) */
+  int32_t handover;         /* tensor-core precisions: 0 = default, 1 = a step feeding a tensor-core step writes
+                               its output directly as 16-bit operand planes, 2 = it writes complex64 and the
+                               consumer splits it (exact per-tensor scale) */
+  int32_t reserved3;
 } tn_exec_opts;
 
 /* Kernel classes of the per-class report figures. */

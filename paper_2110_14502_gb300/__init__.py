@@ -160,7 +160,7 @@ class Plan:
 
     def contract_amplitudes(self, bitstrings, precision="c64", slice_begin=0, slice_count=-1,
                             units_per_group=0, stream=None, out=None, overflow_policy=0, use_graph=0,
-                            profile=False, report=False, test_flag_every=0, autotune=0):
+                            profile=False, report=False, test_flag_every=0, autotune=0, handover=0):
         """Amplitudes of each bitstring's open batch, summed over the slice range.
 
         bitstrings: uint64 words, shape (nb, ceil(n/64)) -- a NumPy array (host
@@ -180,6 +180,7 @@ class Plan:
         o.profile = 1 if profile else 0
         o.test_flag_every = test_flag_every
         o.autotune = autotune
+        o.handover = handover
         if stream is not None:
             o.stream = C.c_void_p(getattr(stream, "cuda_stream", stream))
         rep = Report()

@@ -54,7 +54,8 @@ class ExecOpts(C.Structure):
     _fields_ = [("stream", C.c_void_p), ("precision", C.c_int32), ("device_io", C.c_int32),
                 ("slice_begin", C.c_int64), ("slice_count", C.c_int64), ("units_per_group", C.c_int32),
                 ("overflow_policy", C.c_int32), ("use_graph", C.c_int32), ("profile", C.c_int32),
-                ("test_flag_every", C.c_int32), ("autotune", C.c_int32)]
+                ("test_flag_every", C.c_int32), ("autotune", C.c_int32), ("handover", C.c_int32),
+                ("reserved3", C.c_int32)]
 
 
 class ServerOpts(C.Structure):

@@ -27,6 +27,11 @@
 namespace tn {
 
 constexpr int kFlaggedCap = 1 << 16;  // listed flagged units per call
+// Default of the plane handover per precision (c64, split bf16, split fp16,
+// scaled fp16, scaled bf16).  A handed-over fp16 tensor is scaled by a bound
+// predicted before its values exist; split fp16, the accurate fp16 mode,
+// instead splits complex64 operands with their exact maxima.
+constexpr bool kHandoverDefault[5] = {false, true, false, true, true};
 
 struct Executor {
   int device = -1;
@@ -58,7 +63,7 @@ struct Executor {
   struct Graph { int phase, precision, gs, gb; cudaGraphExec_t exec; int64_t kernels; };
   std::vector<Graph> graphs;
   // autotuner choices per (precision, step): tensor-core tile width, raster group
-  struct Tune { int precision, step, tile_n, group_m; };
+  struct Tune { int precision, step, tile_n, group_m, persistent; };
   std::vector<Tune> tuned;
   bool tune_loaded = false;
   std::vector<GemmDesc> desc;  // per step, unit strides filled at launch
@@ -103,18 +108,35 @@ void destroy_executor(Executor* e) {
 // Per-bit strides of the GEMM view of one step (see GemmDesc): bits of each
 // group are numbered from the operand's fastest index upward.
 void make_gemm_desc(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc,
-                    GemmDesc& d) {
+                    GemmDesc& d, bool m_by_output) {
   std::memset(&d, 0, sizeof d);
   auto stride_in = [](const std::vector<int>& ls, int l) -> int32_t {
     for (size_t p = 0; p < ls.size(); ++p)
       if (ls[p] == l) return int32_t(1) << (ls.size() - 1 - p);
     return -1;
   };
-  for (int p = (int)la.size() - 1; p >= 0; --p) {
-    int l = la[p];
-    int32_t sb = stride_in(lb, l);
-    if (sb < 0) { d.am[d.nm] = stride_in(la, l); d.cm[d.nm] = stride_in(lc, l); ++d.nm; }
-    else { d.ak[d.nk] = stride_in(la, l); d.bk[d.nk] = sb; ++d.nk; }
+  if (m_by_output) {
+    // M bits from the output's fastest M index upward (stores coalesce across
+    // threads; the bandwidth kernel reads each row's K values as one run)
+    for (int p = (int)lc.size() - 1; p >= 0; --p) {
+      int l = lc[p];
+      if (stride_in(la, l) < 0) continue;
+      d.am[d.nm] = stride_in(la, l);
+      d.cm[d.nm] = stride_in(lc, l);
+      ++d.nm;
+    }
+    for (int p = (int)la.size() - 1; p >= 0; --p) {
+      int l = la[p];
+      int32_t sb = stride_in(lb, l);
+      if (sb >= 0) { d.ak[d.nk] = stride_in(la, l); d.bk[d.nk] = sb; ++d.nk; }
+    }
+  } else {
+    for (int p = (int)la.size() - 1; p >= 0; --p) {
+      int l = la[p];
+      int32_t sb = stride_in(lb, l);
+      if (sb < 0) { d.am[d.nm] = stride_in(la, l); d.cm[d.nm] = stride_in(lc, l); ++d.nm; }
+      else { d.ak[d.nk] = stride_in(la, l); d.bk[d.nk] = sb; ++d.nk; }
+    }
   }
   for (int p = (int)lb.size() - 1; p >= 0; --p) {
     int l = lb[p];
@@ -164,7 +186,8 @@ static tn_status setup(Plan& P, Executor& E) {
   CK(cudaMalloc(&E.perm, P.root_perm.size() * sizeof(int64_t)));
   CK(cudaMemcpy(E.perm, P.root_perm.data(), P.root_perm.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
   E.desc.resize(P.steps.size());
-  for (size_t s = 0; s < P.steps.size(); ++s) make_gemm_desc(P.steps[s].la, P.steps[s].lb, P.steps[s].lc, E.desc[s]);
+  for (size_t s = 0; s < P.steps.size(); ++s)
+    make_gemm_desc(P.steps[s].la, P.steps[s].lb, P.steps[s].lc, E.desc[s], P.steps[s].klass == SC_VECTOR);
   CK(cudaEventCreate(&E.ev0));
   CK(cudaEventCreate(&E.ev1));
   CK(cudaMalloc(&E.err, sizeof(int)));
@@ -283,7 +306,11 @@ tn_status run_step(Ctx& c, size_t s, const Geo& g) {
     }
     if (need > E.scratch_cap) return fail(TN_EINVAL, "step %zu: internal error, operand scratch not sized", s);
     for (auto& t : E.tuned)
-      if (t.precision == c.precision && t.step == (int)s) { d.tile_n = t.tile_n; d.group_m = t.group_m; }
+      if (t.precision == c.precision && t.step == (int)s) {
+        d.tile_n = t.tile_n;
+        d.group_m = t.group_m;
+        d.persistent = t.persistent;
+      }
     ScaleIO sio{};
     e = cudaSuccess;
     const int64_t U = c.U;
@@ -339,13 +366,16 @@ tn_status run_step(Ctx& c, size_t s, const Geo& g) {
       // result; the last launch below leaves it in place) and keep the fastest
       const int def_n = d.nn >= 7 ? 128 : (1 << d.nn);
       float best = 1e30f;
-      int bt = 0, bg = 0;
+      int bt = 0, bg = 0, bp = 0;
       for (int tn : {128, 64}) {
         if (tn > def_n) continue;
-        for (int gm : {8, 16, 32}) {
+        for (int cand = 0; cand < 6; ++cand) {
+          const int gm = (cand % 3 == 0) ? 8 : (cand % 3 == 1) ? 16 : 32;
+          const int pers = cand < 3 ? 1 : 2;
           GemmDesc dc = d;
           dc.tile_n = tn;
           dc.group_m = gm;
+          dc.persistent = pers;
           cudaEvent_t t0, t1;
           cudaEventCreate(&t0);
           cudaEventCreate(&t1);
@@ -358,12 +388,13 @@ tn_status run_step(Ctx& c, size_t s, const Geo& g) {
           cudaEventDestroy(t0);
           cudaEventDestroy(t1);
           if (e != cudaSuccess) break;
-          if (ms < best) { best = ms; bt = tn; bg = gm; }
+          if (ms < best) { best = ms; bt = tn; bg = gm; bp = pers; }
         }
       }
-      E.tuned.push_back({c.precision, (int)s, bt, bg});
+      E.tuned.push_back({c.precision, (int)s, bt, bg, bp});
       d.tile_n = bt;
       d.group_m = bg;
+      d.persistent = bp;
     }
     if (e == cudaSuccess) e = launch_gemm_tma(pa, pb, C, c.planes_out[s] != 0, d, c.bf16, sio, E.err, c.st);
   }
@@ -500,7 +531,8 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
   c.scaled = scaled;
   c.U = Gs * Gb;
   c.planes_out.assign(P.steps.size(), 0);
-  if (c.tc) {
+  const bool handover = o.handover == 1 || (o.handover == 0 && kHandoverDefault[o.precision]);
+  if (c.tc && handover) {
     // A step whose consumer also runs on the tensor cores hands its output over
     // as 16-bit planes laid out for that consumer (no separate split pass).
     const int L = (int)P.net.leaves.size();
@@ -599,8 +631,9 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
         if (FILE* f = fopen(path, "r")) {
           unsigned long long h;
           int pr, st_, tn, gm;
-          while (fscanf(f, "%llx %d %d %d %d", &h, &pr, &st_, &tn, &gm) == 5)
-            if (h == P.hash) E.tuned.push_back({pr, st_, tn, gm});
+          int pe;
+          while (fscanf(f, "%llx %d %d %d %d %d", &h, &pr, &st_, &tn, &gm, &pe) == 6)
+            if (h == P.hash) E.tuned.push_back({pr, st_, tn, gm, pe});
           fclose(f);
         }
       }
@@ -719,7 +752,8 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
         if (FILE* f = fopen(path, "a")) {
           for (auto& t : E.tuned)
             if (t.precision == c.precision)
-              fprintf(f, "%llx %d %d %d %d\n", (unsigned long long)P.hash, t.precision, t.step, t.tile_n, t.group_m);
+              fprintf(f, "%llx %d %d %d %d %d\n", (unsigned long long)P.hash, t.precision, t.step, t.tile_n,
+                      t.group_m, t.persistent);
           fclose(f);
         }
       }

@@ -27,6 +27,7 @@ struct GemmDesc {
   int nm, nn, nk;
   int units, units_lo;
   int tile_n, group_m;       // tensor-core tile width / raster group (0 = default; set by the autotuner)
+  int persistent;            // tensor-core GEMM: 0 auto, 1 persistent CTAs (double-buffered accumulators), 2 one tile per CTA
   int64_t a_lo, a_hi, b_lo, b_hi, c_lo, c_hi;
   int32_t am[kMaxBits], cm[kMaxBits];
   int32_t bn[kMaxBits], cn[kMaxBits];
@@ -158,7 +159,9 @@ cudaError_t launch_permute(const float2* src, float2* dst, const PermDesc& p, in
 
 struct Step;
 // GEMM view (per-bit strides) of one pairwise step.
+// m_by_output: number the M bits by the output's memory order (bandwidth
+// kernel) instead of A's (GEMM kernels, whose A rows follow A's layout).
 void make_gemm_desc(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc,
-                    GemmDesc& d);
+                    GemmDesc& d, bool m_by_output = false);
 
 }  // namespace tn

@@ -92,6 +92,15 @@ static tn_status unfused(const float2* A, const float2* B, float2* Cp, const Gem
 
 using namespace tn;
 
+// N <= 16 and K <= 16: the bandwidth kernel's shapes.
+static bool d_is_vector(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc) {
+  int nk = 0;
+  for (int l : la)
+    if (std::find(lb.begin(), lb.end(), l) != lb.end()) ++nk;
+  const int nn = (int)lb.size() - nk;
+  return nn <= 4 && nk <= 4;
+}
+
 extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, int32_t ra, const void* B,
                                       const int32_t* b_labels, int32_t rb, void* Cv, const int32_t* c_labels,
                                       int32_t rc, int32_t precision, int32_t algo, void* stream) {
@@ -106,7 +115,8 @@ extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, in
     return fail(TN_EINVAL, "tn_contract_pair: precision %d is not a complex64-storage mode", precision);
   std::vector<int> la(a_labels, a_labels + ra), lb(b_labels, b_labels + rb), lc(c_labels, c_labels + rc);
   GemmDesc d;
-  make_gemm_desc(la, lb, lc, d);
+  const bool vec_shape = d_is_vector(la, lb, lc);
+  make_gemm_desc(la, lb, lc, d, vec_shape && (algo == TN_PAIR_AUTO || algo == TN_PAIR_VECTOR));
   d.units = 1;
   d.units_lo = 1;
   d.a_lo = d.a_hi = d.b_lo = d.b_hi = d.c_lo = d.c_hi = 0;

@@ -70,7 +70,8 @@ def test_pair_rejects_bad_labels():
         T.contract_pair(a, [0, 0], a, [1, 2], a, [1, 2], algo="auto")   # repeated label
 
 
-TC_SHAPES = [(7, 4, 3), (7, 6, 5), (8, 7, 6), (10, 6, 9), (9, 9, 4), (12, 8, 10), (14, 7, 7), (7, 5, 4), (8, 8, 12)]
+TC_SHAPES = [(7, 4, 3), (7, 6, 5), (8, 7, 6), (10, 6, 9), (9, 9, 4), (12, 8, 10), (14, 7, 7), (7, 5, 4), (8, 8, 12),
+             (15, 8, 6), (16, 7, 5), (13, 9, 8)]  # the last three run the persistent kernel (>= 296 tiles)
 
 
 @pytest.mark.parametrize("nm,nn,nk", TC_SHAPES)
