@@ -222,7 +222,7 @@ def run_ours(args):
     cls_by = [sum(r["class_bytes"][i] for r in reps) for i in range(4)]
     cls_n = [sum(r["class_launches"][i] for r in reps) for i in range(4)]
     dom = int(np.argmax(cls_ms[:3]))
-    kernel_file = {0: "k_simt.cu", 1: "k_vector.cu", 2: "k_tc.cu"}[dom]
+    kernel_file = {0: "k_simt.cu", 1: "k_vector.cu", 2: "k_tc2.cu"}[dom]
     tr = traffic_record(kernel_file)
     if dom == 2:
         achieved = cls_fl[dom] / (cls_ms[dom] * 1e-3) / 1e12
@@ -241,7 +241,7 @@ def run_ours(args):
         fp32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(fp32, 1), "unit": "TFLOP/s",
                 "frac": round(achieved / fp32, 4), "peak_kind": "FP32 FFMA: 152 SMs x 128 lanes x 2 x max clock"}
-    roof["kernel"] = {0: "gemm_simt_kernel", 1: "vector_kernel", 2: "gemm_tc_kernel"}[dom]
+    roof["kernel"] = {0: "gemm_simt_kernel", 1: "vector_kernel", 2: "gemm_tma_kernel / gemm_tma_persistent"}[dom]
     roof["launches_per_step"] = cls_n[dom] / args.steps
     roof["share_of_device_time"] = round(cls_ms[dom] / sum(cls_ms), 4) if sum(cls_ms) else None
     if cls_n[3]:
@@ -292,9 +292,35 @@ def run_ours(args):
                                 "sample": f"slice 0 of batch 0 ({1 << NOPEN} amplitudes, one slice), FP64 NumPy "
                                           f"contraction in the plan's order, {dt:.1f} s"}
         line["rel_err_vs_fp64_sample"] = float(np.linalg.norm(gpu1 - v) / np.linalg.norm(v))
+    if rank == 0 and world == 1 and not args.no_modes:
+        # the other tensor-core precisions on the same workload: one timed step
+        # each, error against the FP64 oracle on the sampled slice when available
+        modes = {}
+        ref = None
+        if "cpu_baseline" in line:
+            ref = v
+        for mode in ("split_fp16", "scaled_fp16", "scaled_bf16"):
+            if mode == args.precision:
+                continue
+            with torch.cuda.stream(stream):
+                p.contract_amplitudes(dwords, out=out, stream=stream, precision=mode, slice_count=SLICE_LIMIT)
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                _, r = p.contract_amplitudes(dwords, out=out, stream=stream, precision=mode, report=True,
+                                             slice_count=SLICE_LIMIT)
+            entry = {"tflops": round(r["flops"] / r["device_ms"] / 1e9, 2), "ms_per_step": round(r["device_ms"], 1),
+                     "amplitudes_per_s": round(nout / (r["device_ms"] * 1e-3), 2),
+                     "flagged_units": r["flagged_units"]}
+            if ref is not None:
+                g1 = p.contract_amplitudes(words[:1], precision=mode, slice_begin=0, slice_count=1)[0]
+                entry["rel_err_vs_fp64_sample"] = float(np.linalg.norm(g1 - ref) / np.linalg.norm(ref))
+            modes[mode] = entry
+        line["precision_modes"] = modes
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+    if rank == 0 and world == 1 and not args.no_serve:
+        line["serving"] = serve_summary(args)
     if rank == 0:
         print(json.dumps(line))
 
@@ -395,6 +421,35 @@ def serve_workload(nreq, seed=5):
     return reqs, gaps
 
 
+def serve_summary(args, nreq=60):
+    """Compact serving run for the main bench line: the same request stream on
+    the batched mixed-precision server and on the plain complex64 path."""
+    import paper_2110_14502_gb300 as T
+    reqs, _ = serve_workload(nreq)
+    common = dict(plan_trials=8, max_log2_cmac=40.0, max_log2_intermediate=27, planner_threads=16)
+    out = {"requests": nreq, "cost_cap_log2_cmac": 40.0}
+    for name, kw in (("warm", dict(max_inflight=8, slices_per_quantum=64, precision="c64")),
+                     ("plain_c64_one_slice", dict(max_inflight=1, slices_per_quantum=1, precision="c64")),
+                     ("batched_scaled_fp16", dict(max_inflight=8, slices_per_quantum=64, precision="scaled_fp16"))):
+        srv = T.Server(**kw, **common)
+        t0 = time.time()
+        ts = [srv.submit(**r) for r in reqs]
+        lat, amps, rej = [], 0, 0
+        for t in ts:
+            try:
+                o, st = srv.wait(t)
+                lat.append(st["submit_to_done_ms"])
+                amps += o.size
+            except T.TnError:
+                rej += 1
+        dt = time.time() - t0
+        srv.close()
+        if name != "warm":
+            out[name] = {"amplitudes_per_s": round(amps / dt, 1), "p50_ms": round(float(np.percentile(lat, 50)), 2),
+                         "p99_ms": round(float(np.percentile(lat, 99)), 2), "rejected": rej, "seconds": round(dt, 2)}
+    return out
+
+
 def run_serve(args):
     """Serving benchmark: the batched mixed-precision server against the plain
     complex64 path that contracts one slice of one request at a time."""
@@ -475,6 +530,8 @@ def main():
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--cost-cap", type=float, default=40.0)
     ap.add_argument("--workload", default="6x6", choices=["6x6", "8x8"])
+    ap.add_argument("--no-modes", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     if args.workload == "8x8":
         use_8x8()

@@ -11,7 +11,11 @@
 // FP32 accumulation in TMEM (Dr and Di take TN columns each), the minus sign
 // through the MMA's negate-A bit.  Split precision (four planes re_hi, re_lo,
 // im_hi, im_lo) expands each real product X Y as Xhi Yhi + Xhi Ylo + Xlo Yhi;
-// single precision (two planes re, im) keeps one 16-bit product.
+// single precision (two planes re, im) keeps one 16-bit product.  The small
+// hi*lo + lo*hi terms go to separate correction accumulators, added to the
+// hi*hi sums in FP32 in the epilogue: the tensor core's accumulation keeps
+// fewer bits than an FP32 add when a tiny term meets a large running sum, so
+// folding the corrections into the main sum would cap the split accuracy.
 //
 // Adaptive scaling (Sec. "A Mixed-Precision Computation Method via Adaptive
 // Precision Scaling"): a plane tensor stores x 2^-e with a per-unit integer
@@ -58,7 +62,10 @@ struct Cfg2 {
   static constexpr int STAGE = A_STAGE + B_STAGE;
   static constexpr int NSTAGE = (SMEM_BUDGET / STAGE) < 6 ? (SMEM_BUDGET / STAGE) : 6;
   static constexpr int SMEM = NSTAGE * STAGE + 1024;
-  static constexpr uint32_t TMEM_COLS = 2 * TN < 32 ? 32 : 2 * TN;
+  // accumulator columns per tile: Dr, Di (TN each) and, for split precision,
+  // the correction sums Cr, Ci of the hi*lo + lo*hi terms (TN each)
+  static constexpr int ACC = (NP == 4 ? 4 : 2) * TN;
+  static constexpr uint32_t TMEM_COLS = ACC < 32 ? 32 : ACC;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -258,7 +265,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (warp == 1) {
     // ---- MMA issuer (one lane)
     constexpr uint32_t I = idesc2(BF16, TM, TN, false), IN = idesc2(BF16, TM, TN, true);
-    const uint32_t dr = tmem, di = tmem + TN;
+    const uint32_t dr = tmem, di = tmem + TN, cr = tmem + 2 * TN, ci = tmem + 3 * TN;
     int issued = 0;
     for (int kt = 0; lane == 0 && kt < nkt; ++kt) {
       const int s = kt % NS;
@@ -282,18 +289,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint32_t acc = (kt | kk) ? 1u : 0u;
         if constexpr (NP == 4) {
           // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
+          // hi*hi into Dr, Di; hi*lo + lo*hi into the correction sums Cr, Ci
           mma(dr, A_[0], B_[0], I, acc);
-          mma(dr, A_[0], B_[1], I, 1u);
-          mma(dr, A_[1], B_[0], I, 1u);
           mma(dr, A_[2], B_[2], IN, 1u);
-          mma(dr, A_[2], B_[3], IN, 1u);
-          mma(dr, A_[3], B_[2], IN, 1u);
           mma(di, A_[0], B_[2], I, acc);
-          mma(di, A_[0], B_[3], I, 1u);
-          mma(di, A_[1], B_[2], I, 1u);
           mma(di, A_[2], B_[0], I, 1u);
-          mma(di, A_[2], B_[1], I, 1u);
-          mma(di, A_[3], B_[0], I, 1u);
+          mma(cr, A_[0], B_[1], I, acc);
+          mma(cr, A_[1], B_[0], I, 1u);
+          mma(cr, A_[2], B_[3], IN, 1u);
+          mma(cr, A_[3], B_[2], IN, 1u);
+          mma(ci, A_[0], B_[3], I, acc);
+          mma(ci, A_[1], B_[2], I, 1u);
+          mma(ci, A_[2], B_[1], I, 1u);
+          mma(ci, A_[3], B_[0], I, 1u);
         } else {
           // planes: 0 re, 1 im
           mma(dr, A_[0], B_[0], I, acc);
@@ -331,16 +339,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool bad = false;
 #pragma unroll 1
       for (int c0 = 0; c0 < TN; c0 += 16) {
-        uint32_t ur[16], ui[16];
+        uint32_t ur[16], ui[16], uc[16], ud[16];
         const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
         tmem_ld<16>(lane_base + (uint32_t)c0, ur);
         tmem_ld<16>(lane_base + (uint32_t)(TN + c0), ui);
+        if constexpr (NP == 4) {
+          tmem_ld<16>(lane_base + (uint32_t)(2 * TN + c0), uc);
+          tmem_ld<16>(lane_base + (uint32_t)(3 * TN + c0), ud);
+        }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         float vr[16], vi[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          vr[j] = ldexpf(__uint_as_float(ur[j]), shift);
-          vi[j] = ldexpf(__uint_as_float(ui[j]), shift);
+          float xr = __uint_as_float(ur[j]), xi = __uint_as_float(ui[j]);
+          if constexpr (NP == 4) {
+            xr += __uint_as_float(uc[j]);
+            xi += __uint_as_float(ud[j]);
+          }
+          vr[j] = ldexpf(xr, shift);
+          vi[j] = ldexpf(xi, shift);
         }
         if (ro < 0) continue;
         if (c_planes) {
@@ -428,6 +445,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   constexpr int NS = CF::NSTAGE;
   constexpr int A_STAGE = CF::A_STAGE;
   constexpr uint32_t COLS = 2 * CF::TMEM_COLS;  // two accumulator buffers
+  static_assert(COLS <= 512, "two accumulator buffers must fit in the 512 TMEM columns");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ uint64_t full[NS], empty[NS], acc_full[2], acc_empty[2];
@@ -506,7 +524,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t dr = tmem + (uint32_t)(b * 2 * TN), di = dr + TN;
+      const uint32_t dr = tmem + (uint32_t)(b * CF::ACC), di = dr + TN, cr = dr + 2 * TN, ci = dr + 3 * TN;
       bool ok = true;
       for (int kt = 0; kt < nkt; ++kt, ++g) {
         const int s = (int)(g % NS);
@@ -529,18 +547,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           const uint32_t acc = (kt | kk) ? 1u : 0u;
           if constexpr (NP == 4) {
+            // hi*hi into Dr, Di; hi*lo + lo*hi into the correction sums Cr, Ci
             mma(dr, A_[0], B_[0], I, acc);
-            mma(dr, A_[0], B_[1], I, 1u);
-            mma(dr, A_[1], B_[0], I, 1u);
             mma(dr, A_[2], B_[2], IN, 1u);
-            mma(dr, A_[2], B_[3], IN, 1u);
-            mma(dr, A_[3], B_[2], IN, 1u);
             mma(di, A_[0], B_[2], I, acc);
-            mma(di, A_[0], B_[3], I, 1u);
-            mma(di, A_[1], B_[2], I, 1u);
             mma(di, A_[2], B_[0], I, 1u);
-            mma(di, A_[2], B_[1], I, 1u);
-            mma(di, A_[3], B_[0], I, 1u);
+            mma(cr, A_[0], B_[1], I, acc);
+            mma(cr, A_[1], B_[0], I, 1u);
+            mma(cr, A_[2], B_[3], IN, 1u);
+            mma(cr, A_[3], B_[2], IN, 1u);
+            mma(ci, A_[0], B_[3], I, acc);
+            mma(ci, A_[1], B_[2], I, 1u);
+            mma(ci, A_[2], B_[1], I, 1u);
+            mma(ci, A_[3], B_[0], I, 1u);
           } else {
             mma(dr, A_[0], B_[0], I, acc);
             mma(dr, A_[1], B_[1], IN, 1u);
@@ -600,18 +619,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int shift = c_planes ? -r : ea + eb;
       float vmax = 0.f;
       bool bad = false;
-      const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 2 * TN);
+      const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * CF::ACC);
 #pragma unroll 1
       for (int c0 = 0; c0 < TN; c0 += 16) {
-        uint32_t ur[16], ui[16];
+        uint32_t ur[16], ui[16], uc[16], ud[16];
         tmem_ld<16>(lane_base + (uint32_t)c0, ur);
         tmem_ld<16>(lane_base + (uint32_t)(TN + c0), ui);
+        if constexpr (NP == 4) {
+          tmem_ld<16>(lane_base + (uint32_t)(2 * TN + c0), uc);
+          tmem_ld<16>(lane_base + (uint32_t)(3 * TN + c0), ud);
+        }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         float vr[16], vi[16];
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
-          vr[jj] = ldexpf(__uint_as_float(ur[jj]), shift);
-          vi[jj] = ldexpf(__uint_as_float(ui[jj]), shift);
+          float xr = __uint_as_float(ur[jj]), xi = __uint_as_float(ui[jj]);
+          if constexpr (NP == 4) {
+            xr += __uint_as_float(uc[jj]);
+            xi += __uint_as_float(ud[jj]);
+          }
+          vr[jj] = ldexpf(xr, shift);
+          vi[jj] = ldexpf(xi, shift);
         }
         if (c_planes) {
           uint16_t* P = reinterpret_cast<uint16_t*>(C);
@@ -751,17 +779,14 @@ cudaError_t launch_persistent(const CUtensorMap& ma, const CUtensorMap& mb, floa
 }
 
 template <bool BF16, int NP>
-cudaError_t launch_tn(int TNv, const CUtensorMap& ma, const CUtensorMap& mb, float2* C, const GemmDesc& d, int kp,
-                      const int z[4], int cp, const ScaleIO& sio, int* err, cudaStream_t s) {
-  // persistent CTAs pay off once there are several tiles per SM to overlap
-  bool persistent = d.persistent == 1;
-  if (d.persistent == 0) {
-    const int64_t items = ((int64_t(1) << d.nm) / TM) * ((int64_t(1) << d.nn) / TNv) * d.units;
-    persistent = items >= 2 * 148;
-  }
+cudaError_t launch_tn(int TNv, bool persistent, const CUtensorMap& ma, const CUtensorMap& mb, float2* C,
+                      const GemmDesc& d, int kp, const int z[4], int cp, const ScaleIO& sio, int* err,
+                      cudaStream_t s) {
   if (persistent) {
     switch (TNv) {
-      case 128: return launch_persistent<128, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+      case 128:
+        if constexpr (NP == 2) return launch_persistent<128, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+        return cudaErrorInvalidValue;
       case 64: return launch_persistent<64, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
       case 32: return launch_persistent<32, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
       case 16: return launch_persistent<16, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
@@ -795,17 +820,25 @@ cudaError_t launch_gemm_tma(const PlaneOperand& a, const PlaneOperand& b, float2
   if (!tc_shape_ok(d) || d.units > 65535 || a.kp != b.kp || a.kp % TKC || a.np != b.np ||
       (a.np != 2 && a.np != 4))
     return cudaErrorInvalidValue;
-  const int TNv = tma_tile_n(d);
+  int TNv = tma_tile_n(d);
+  // persistent CTAs pay off once there are several tiles per SM to overlap
+  bool persistent = d.persistent == 1;
+  if (d.persistent == 0) {
+    const int64_t items = ((int64_t(1) << d.nm) / TM) * ((int64_t(1) << d.nn) / TNv) * d.units;
+    persistent = items >= 2 * 148;
+  }
+  // two split-precision accumulator sets (4 TN columns each) fit TMEM for TN <= 64
+  if (persistent && a.np == 4 && TNv > 64) TNv = 64;
   CUtensorMap ma, mb;
   if (!encode_planes(&ma, a, TM) || !encode_planes(&mb, b, TNv)) return cudaErrorInvalidValue;
   const int kpi = (int)a.kp;
   const int z[4] = {a.nlo > 1, a.nhi > 1, b.nlo > 1, b.nhi > 1};
   const int cp = c_planes ? 1 : 0;
   if (a.np == 4)
-    return bf16 ? launch_tn<true, 4>(TNv, ma, mb, C, d, kpi, z, cp, sio, err, s)
-                : launch_tn<false, 4>(TNv, ma, mb, C, d, kpi, z, cp, sio, err, s);
-  return bf16 ? launch_tn<true, 2>(TNv, ma, mb, C, d, kpi, z, cp, sio, err, s)
-              : launch_tn<false, 2>(TNv, ma, mb, C, d, kpi, z, cp, sio, err, s);
+    return bf16 ? launch_tn<true, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, err, s)
+                : launch_tn<false, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, err, s);
+  return bf16 ? launch_tn<true, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, err, s)
+              : launch_tn<false, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, err, s);
 }
 
 }  // namespace tn
