@@ -707,6 +707,301 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
+// Split precision, persistent, with chunked accumulation.  The tensor core
+// adds into its FP32 accumulator with truncation, so over a long K the error
+// grows linearly and is biased toward zero.  Here the MMA warp accumulates
+// each chunk of CHUNK K stages into a fresh TMEM partial P; the epilogue warps
+// fold P into a TMEM running sum R with round-to-nearest FP32 adds and, after
+// the last chunk of a tile, scale and store it.  The bias then scales with
+// the chunk length, not with K.  TMEM: P (2 TN columns) and R (2 TN).
+constexpr int CHUNK = 16;
+
+template <int TN, bool BF16>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    gemm_tma_chunked(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                     float2* __restrict__ C0, const GemmDesc d, int kp, int a_zlo, int a_zhi, int b_zlo, int b_zhi,
+                     int c_planes, const ScaleIO sio, int* __restrict__ err) {
+  constexpr int NP = 4;
+  using CF = Cfg2<TN, NP>;
+  constexpr int NS = CF::NSTAGE;
+  constexpr int A_STAGE = CF::A_STAGE;
+  constexpr uint32_t COLS = 4 * TN < 32 ? 32 : 4 * TN;
+  static_assert(4 * TN <= 512, "partial and running sums must fit in TMEM");
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t full[NS], empty[NS], p_full, p_empty;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int32_t colC[TN];
+  __shared__ volatile int abort_flag;
+  __shared__ volatile int epi_fail;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntm = (int)((int64_t(1) << d.nm) / TM), ntn = (int)((int64_t(1) << d.nn) / TN);
+  const int tiles = ntm * ntn;
+  const int64_t items = (int64_t)tiles * d.units;
+  const int nkt = kp / TKC;
+  const int nch = (nkt + CHUNK - 1) / CHUNK;
+  const int GM = d.group_m > 0 ? d.group_m : GROUP_M_DEFAULT;
+  auto decode = [&](int64_t item, int& unit, int& m0, int& n0) {
+    unit = (int)(item / tiles);
+    const int t = (int)(item % tiles);
+    const int per_group = GM * ntn;
+    const int g = t / per_group, r = t % per_group;
+    const int gm = min(GM, ntm - g * GM);
+    m0 = (g * GM + r % gm) * TM;
+    n0 = (r / gm) * TN;
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    mbar_init(&p_full, 1);
+    mbar_init(&p_empty, 128);
+    abort_flag = 0;
+    epi_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    // ---- TMA producer
+    int64_t g = 0;
+    for (int64_t it = blockIdx.x; lane == 0 && it < items && !abort_flag; it += gridDim.x) {
+      int unit, m0, n0;
+      decode(it, unit, m0, n0);
+      const int ulo = unit % d.units_lo, uhi = unit / d.units_lo;
+      const int za_lo = a_zlo ? ulo : 0, za_hi = a_zhi ? uhi : 0;
+      const int zb_lo = b_zlo ? ulo : 0, zb_hi = b_zhi ? uhi : 0;
+      for (int kt = 0; kt < nkt; ++kt, ++g) {
+        const int s = (int)(g % NS);
+        if (g >= NS && !mbar_wait(&empty[s], (uint32_t)(((g / NS) - 1) & 1))) {
+          atomicExch(err, 31);
+          abort_flag = 1;
+          break;
+        }
+        uint8_t* st = smem + s * CF::STAGE;
+        mbar_expect_tx(&full[s], CF::STAGE);
+        tma_load_5d(st, &mapA, &full[s], kt * TKC, m0, 0, za_lo, za_hi);
+        tma_load_5d(st + A_STAGE, &mapB, &full[s], kt * TKC, n0, 0, zb_lo, zb_hi);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---- MMA issuer: chunk jc of the CTA accumulates into P
+    constexpr uint32_t I = idesc2(BF16, TM, TN, false), IN = idesc2(BF16, TM, TN, true);
+    const uint32_t dr = tmem, di = tmem + TN;
+    int64_t g = 0, jc = 0;
+    bool ok = true;
+    for (int64_t it = blockIdx.x; lane == 0 && ok && it < items && !abort_flag; it += gridDim.x) {
+      for (int c = 0; c < nch && ok; ++c, ++jc) {
+        if (jc >= 1 && !mbar_wait(&p_empty, (uint32_t)((jc - 1) & 1))) {
+          atomicExch(err, 32);
+          abort_flag = 1;
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int k0 = c * CHUNK, k1 = min(nkt, k0 + CHUNK);
+        for (int kt = k0; kt < k1; ++kt, ++g) {
+          const int s = (int)(g % NS);
+          if (!mbar_wait(&full[s], (uint32_t)((g / NS) & 1))) {
+            atomicExch(err, 33);
+            abort_flag = 1;
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a = smem_u32(smem + s * CF::STAGE);
+          const uint32_t bb = a + A_STAGE;
+#pragma unroll
+          for (int kk = 0; kk < TKC / 16; ++kk) {
+            uint64_t A_[NP], B_[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+              A_[p] = sw64_desc(a + p * (TM * 64) + kk * 32);
+              B_[p] = sw64_desc(bb + p * (TN * 64) + kk * 32);
+            }
+            const uint32_t acc = (kt > k0 || kk) ? 1u : 0u;
+            // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo; the chunk is short,
+            // so the hi*lo + lo*hi terms share the hi*hi accumulator
+            mma(dr, A_[0], B_[0], I, acc);
+            mma(dr, A_[0], B_[1], I, 1u);
+            mma(dr, A_[1], B_[0], I, 1u);
+            mma(dr, A_[2], B_[2], IN, 1u);
+            mma(dr, A_[2], B_[3], IN, 1u);
+            mma(dr, A_[3], B_[2], IN, 1u);
+            mma(di, A_[0], B_[2], I, acc);
+            mma(di, A_[0], B_[3], I, 1u);
+            mma(di, A_[1], B_[2], I, 1u);
+            mma(di, A_[2], B_[0], I, 1u);
+            mma(di, A_[2], B_[1], I, 1u);
+            mma(di, A_[3], B_[0], I, 1u);
+          }
+          commit(&empty[s]);
+        }
+        commit(&p_full);  // also after an abort, so the epilogue's wait ends
+      }
+    }
+    __syncwarp();
+  } else if (warp >= 4) {
+    // ---- epilogue: fold every chunk into R; after the last one, store
+    const int q = warp & 3;
+    const int t = tid - 128;
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    const uint32_t P = tmem + lane_off, R = tmem + lane_off + 2 * TN;
+    int64_t jc = 0;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+      int unit, m0, n0;
+      decode(it, unit, m0, n0);
+      const int ulo = unit % d.units_lo, uhi = unit / d.units_lo;
+      for (int jj = t; jj < TN; jj += 128) colC[jj] = bit_offset(n0 + jj, d.nn, d.cn);
+      const int32_t ro = bit_offset(m0 + q * 32 + lane, d.nm, d.cm);
+      float2* C = C0 + (int64_t)ulo * d.c_lo + (int64_t)uhi * d.c_hi;
+      int ea = 0, eb = 0, r = 0;
+      bool weak = false;
+      if (sio.ea) {
+        const int za = (a_zlo ? ulo : 0) + (a_zhi ? uhi : 0) * (a_zlo ? d.units_lo : 1);
+        const int zb = (b_zlo ? ulo : 0) + (b_zhi ? uhi : 0) * (b_zlo ? d.units_lo : 1);
+        ea = sio.ea[za];
+        eb = sio.eb[zb];
+        const float ma = sio.ma[za], mb = sio.mb[zb];
+        weak = !(ma >= 0x1p-10f) || !(mb >= 0x1p-10f);
+        const float bound = 2.f * ldexpf(ma * mb, d.nk);
+        if (bound > 0.f && isfinite(bound)) {
+          int x;
+          frexpf(bound, &x);
+          r = x - 15;
+        }
+      }
+      const bool n16 = d.nn >= 4 && d.cn[0] == 1 && d.cn[1] == 2 && d.cn[2] == 4 && d.cn[3] == 8;
+      const int shift = c_planes ? -r : ea + eb;
+      float vmax = 0.f;
+      bool bad = false;
+      for (int c = 0; c < nch; ++c, ++jc) {
+        bool ok = mbar_wait(&p_full, (uint32_t)(jc & 1));
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok && lane == 0) {
+          atomicExch(err, 34);
+          abort_flag = 1;
+          epi_fail = 1;
+        }
+        // colC of this item and any failure visible to all 4 epilogue warps
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (epi_fail) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const bool last = c == nch - 1;
+#pragma unroll 1
+        for (int c0 = 0; c0 < TN; c0 += 16) {
+          uint32_t pr[16], pi[16], rr[16], ri[16];
+          tmem_ld<16>(P + (uint32_t)c0, pr);
+          tmem_ld<16>(P + (uint32_t)(TN + c0), pi);
+          if (c > 0) {
+            tmem_ld<16>(R + (uint32_t)c0, rr);
+            tmem_ld<16>(R + (uint32_t)(TN + c0), ri);
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (c > 0) {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              pr[jj] = __float_as_uint(__uint_as_float(pr[jj]) + __uint_as_float(rr[jj]));
+              pi[jj] = __float_as_uint(__uint_as_float(pi[jj]) + __uint_as_float(ri[jj]));
+            }
+          }
+          if (!last) {
+            tmem_st16(R + (uint32_t)c0, pr);
+            tmem_st16(R + (uint32_t)(TN + c0), pi);
+            continue;
+          }
+          float vr[16], vi[16];
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            vr[jj] = ldexpf(__uint_as_float(pr[jj]), shift);
+            vi[jj] = ldexpf(__uint_as_float(pi[jj]), shift);
+          }
+          if (c_planes) {
+            uint16_t* Pl = reinterpret_cast<uint16_t*>(C);
+            const int64_t plane = int64_t(1) << (d.nm + d.nn);
+            uint16_t h[NP][16];
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              vmax = fmaxf(vmax, fmaxf(fabsf(vr[jj]), fabsf(vi[jj])));
+              bad |= !isfinite(vr[jj]) || !isfinite(vi[jj]);
+              split16<BF16>(vr[jj], h[0][jj], h[1][jj]);
+              split16<BF16>(vi[jj], h[2][jj], h[3][jj]);
+            }
+            if (n16) {
+              const int64_t o = (int64_t)ro + colC[c0];
+#pragma unroll
+              for (int p = 0; p < NP; ++p) {
+                uint4* qd = reinterpret_cast<uint4*>(Pl + p * plane + o);
+                qd[0] = make_uint4(h[p][0] | (h[p][1] << 16), h[p][2] | (h[p][3] << 16),
+                                   h[p][4] | (h[p][5] << 16), h[p][6] | (h[p][7] << 16));
+                qd[1] = make_uint4(h[p][8] | (h[p][9] << 16), h[p][10] | (h[p][11] << 16),
+                                   h[p][12] | (h[p][13] << 16), h[p][14] | (h[p][15] << 16));
+              }
+            } else {
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) {
+                const int64_t o = (int64_t)ro + colC[c0 + jj];
+#pragma unroll
+                for (int p = 0; p < NP; ++p) Pl[p * plane + o] = h[p][jj];
+              }
+            }
+          } else if (n16) {
+            float4* qd = reinterpret_cast<float4*>(C + (int64_t)ro + colC[c0]);
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj)
+              qd[jj] = make_float4(vr[2 * jj], vi[2 * jj], vr[2 * jj + 1], vi[2 * jj + 1]);
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) C[(int64_t)ro + colC[c0 + jj]] = make_float2(vr[jj], vi[jj]);
+          }
+        }
+        if (!last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        // P may be refilled once every epilogue thread has read it (and R is written)
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&p_empty)) : "memory");
+      }
+      if (epi_fail) break;
+      if (sio.mc || sio.flag) {
+        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        bad = __any_sync(0xffffffffu, bad);
+        if (lane == 0) {
+          if (sio.mc && c_planes) atomicMax(sio.mc + unit, __float_as_uint(vmax));
+          if (sio.ec && c_planes && q == 0 && m0 == 0 && n0 == 0) sio.ec[unit] = ea + eb + r;
+          if (sio.flag && (bad || weak)) sio.flag[sio.flag_by_lo ? ulo : unit] = 1;
+        }
+      }
+      // every epilogue thread is done with colC before the next item rewrites it
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 2) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS));
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -778,27 +1073,60 @@ cudaError_t launch_persistent(const CUtensorMap& ma, const CUtensorMap& mb, floa
   return cudaGetLastError();
 }
 
+template <int TN, bool BF16>
+cudaError_t launch_chunked(const CUtensorMap& ma, const CUtensorMap& mb, float2* C, const GemmDesc& d, int kp,
+                           const int z[4], int c_planes, const ScaleIO& sio, int* err, cudaStream_t s) {
+  static bool attr = false;
+  static int sms = 0;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tma_chunked<TN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg2<TN, 4>::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+    attr = true;
+  }
+  const int64_t M = int64_t(1) << d.nm, N = int64_t(1) << d.nn;
+  const int64_t items = (M / TM) * (N / TN) * d.units;
+  const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
+  gemm_tma_chunked<TN, BF16><<<grid, NTHREADS, Cfg2<TN, 4>::SMEM, s>>>(ma, mb, C, d, kp, z[0], z[1], z[2], z[3],
+                                                                       c_planes, sio, err);
+  return cudaGetLastError();
+}
+
 template <bool BF16, int NP>
 cudaError_t launch_tn(int TNv, bool persistent, const CUtensorMap& ma, const CUtensorMap& mb, float2* C,
                       const GemmDesc& d, int kp, const int z[4], int cp, const ScaleIO& sio, int* err,
                       cudaStream_t s) {
-  if (persistent) {
+  if constexpr (NP == 4) {
+    // split precision always runs the chunked persistent kernel (accuracy)
+    (void)persistent;
     switch (TNv) {
-      case 128:
-        if constexpr (NP == 2) return launch_persistent<128, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
-        return cudaErrorInvalidValue;
-      case 64: return launch_persistent<64, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
-      case 32: return launch_persistent<32, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
-      case 16: return launch_persistent<16, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+      case 128: return launch_chunked<128, BF16>(ma, mb, C, d, kp, z, cp, sio, err, s);
+      case 64: return launch_chunked<64, BF16>(ma, mb, C, d, kp, z, cp, sio, err, s);
+      case 32: return launch_chunked<32, BF16>(ma, mb, C, d, kp, z, cp, sio, err, s);
+      case 16: return launch_chunked<16, BF16>(ma, mb, C, d, kp, z, cp, sio, err, s);
       default: return cudaErrorInvalidValue;
     }
-  }
-  switch (TNv) {
-    case 128: return launch_cfg<128, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
-    case 64: return launch_cfg<64, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
-    case 32: return launch_cfg<32, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
-    case 16: return launch_cfg<16, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
-    default: return cudaErrorInvalidValue;
+  } else {
+    if (persistent) {
+      switch (TNv) {
+        case 128: return launch_persistent<128, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+        case 64: return launch_persistent<64, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+        case 32: return launch_persistent<32, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+        case 16: return launch_persistent<16, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+        default: return cudaErrorInvalidValue;
+      }
+    }
+    switch (TNv) {
+      case 128: return launch_cfg<128, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+      case 64: return launch_cfg<64, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+      case 32: return launch_cfg<32, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+      case 16: return launch_cfg<16, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+      default: return cudaErrorInvalidValue;
+    }
   }
 }
 
@@ -827,8 +1155,7 @@ cudaError_t launch_gemm_tma(const PlaneOperand& a, const PlaneOperand& b, float2
     const int64_t items = ((int64_t(1) << d.nm) / TM) * ((int64_t(1) << d.nn) / TNv) * d.units;
     persistent = items >= 2 * 148;
   }
-  // two split-precision accumulator sets (4 TN columns each) fit TMEM for TN <= 64
-  if (persistent && a.np == 4 && TNv > 64) TNv = 64;
+
   CUtensorMap ma, mb;
   if (!encode_planes(&ma, a, TM) || !encode_planes(&mb, b, TNv)) return cudaErrorInvalidValue;
   const int kpi = (int)a.kp;
