@@ -71,7 +71,8 @@ def test_pair_rejects_bad_labels():
 
 
 TC_SHAPES = [(7, 4, 3), (7, 6, 5), (8, 7, 6), (10, 6, 9), (9, 9, 4), (12, 8, 10), (14, 7, 7), (7, 5, 4), (8, 8, 12),
-             (15, 8, 6), (16, 7, 5), (13, 9, 8)]  # the last three run the persistent kernel (>= 296 tiles)
+             (15, 8, 6), (16, 7, 5), (13, 9, 8),  # >= 296 tiles: persistent CTAs
+             (7, 4, 14), (7, 5, 16)]               # long K: chunked accumulation keeps the error flat
 
 
 @pytest.mark.parametrize("nm,nn,nk", TC_SHAPES)
@@ -90,3 +91,23 @@ def test_tcgen05_split_bf16_matches_fp64(nm, nn, nk, algo):
     got = dC.cpu().numpy().astype(np.complex128)
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert err <= 1e-4, err
+
+
+
+@pytest.mark.parametrize("nk", [10, 14, 16])
+def test_split_error_does_not_grow_with_k(nk):
+    """The tensor core's FP32 accumulation truncates, so a long K chain drifts
+    toward zero; the split-precision kernel accumulates chunks in TMEM and folds
+    them with round-to-nearest adds.  The error must stay at the split level
+    (a few 1e-6) and carry no systematic shrink of |C|."""
+    T = tnlib()
+    import torch
+    la, lb, lc, A, B, ref = _case(7, 5, nk, seed=77 + nk)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.empty(1 << len(lc), dtype=torch.complex64, device="cuda")
+    T.contract_pair(dA, la, dB, lb, dC, lc, precision="split_bf16", algo="fused_tc")
+    torch.cuda.synchronize()
+    got = dC.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 2e-5
+    bias = float(np.mean((np.abs(got) - np.abs(ref)) / np.abs(ref)))
+    assert abs(bias) <= 1e-5
