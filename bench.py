@@ -379,10 +379,14 @@ def run_micro(args):
         B = torch.from_numpy(I.random_tensor(len(lb), 32, np.complex64)).cuda()
         Cc = torch.empty(1 << len(lc), dtype=torch.complex64, device="cuda")
         flops = 8.0 * 2.0 ** (nm + nn + nk)
-        row = {"shape": [nm, nn, nk]}
+        row = {"shape": [nm, nn, nk], "tc_precision": args.precision if args.precision != "c64" else "split_bf16"}
         algos = ["vector"] if (nn <= 4 and nk <= 4) else ["fused_tc", "gather_tc", "fused_simt", "unfused"]
         for algo in algos:
-            prec = "split_bf16" if algo in ("fused_tc", "gather_tc") else "c64"
+            prec = "c64"
+            if algo == "fused_tc":
+                prec = args.precision if args.precision != "c64" else "split_bf16"
+            elif algo == "gather_tc":
+                prec = "split_bf16"
             for _ in range(args.warmup):
                 T.contract_pair(A, la, B, lb, Cc, lc, precision=prec, algo=algo)
             torch.cuda.synchronize()

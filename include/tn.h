@@ -254,7 +254,9 @@ typedef struct {
   int32_t slices_per_quantum;    /* slices of one request queued per scheduling turn; 0 = 64 */
   int32_t precision;             /* default TN_PREC_* of requests that ask for -1 */
   int32_t plan_trials;           /* order-search restarts per new circuit; 0 = 16 */
-  int64_t hbm_budget_bytes;      /* device memory admitted requests may hold; 0 = 60% of the free memory */
+  int64_t hbm_budget_bytes;      /* device memory of the server; 0 = 60% of the free memory.  One
+                                    eighth holds the stems of recent circuits, the rest bounds the
+                                    estimated footprint of the admitted requests */
   double max_log2_cmac;          /* cost cap (log2 complex MACs of a request); 0 = 48 */
   int32_t max_log2_intermediate; /* per-slice width cap when planning; 0 = 27 */
   int32_t planner_threads;       /* host threads planning new circuits concurrently; 0 = 4 (max 32) */
@@ -285,13 +287,18 @@ typedef struct {
   int64_t nb;
   uint64_t plan_hash;
   int32_t planned_here;          /* 1 = this request ran the planner (plan cache miss) */
-  int32_t reserved;
+  int32_t stem_reused;           /* 1 = the circuit's leaf tensors and invariant (phase-0)
+                                    intermediates were already resident from an earlier request */
 } tn_request_stats;
 
 /* Creates a server on the current CUDA device with a planner thread and a
  * scheduler thread.  Requests are admitted in arrival order when an in-flight
  * slot is free and their estimated device footprint fits the budget; admitted
  * requests advance one quantum of slices per turn each, on their own streams.
+ * Plans are cached per circuit, and each circuit's stem (its leaf tensors and
+ * the intermediates that depend on neither bitstring nor slice) stays
+ * resident on the device for later requests of the same circuit, within one
+ * eighth of the budget, least recently used first out.
  * A request's amplitudes are bit-identical whatever runs beside it. */
 tn_status tn_server_create(const tn_server_opts* opts, tn_server** out);
 /* Queues a request (arguments validated here; TN_ETOOBIG for a cost above the
@@ -324,8 +331,17 @@ enum {
  * A, B, C: device complex64 tensors (rank <= 30 each, row-major as above).
  * Every label of C appears in exactly one of A, B; a label shared by A and B
  * must not appear in C; labels are distinct within a tensor.
- * precision selects the arithmetic (TN_PREC_C64, _SPLIT_BF16, _SPLIT_FP16 on
- * complex64 storage).  Asynchronous on `stream`. */
+ * precision selects the arithmetic of the tensor-core algorithms:
+ * TN_PREC_SPLIT_BF16 (hi + lo split, no scaling), TN_PREC_SPLIT_FP16 (hi + lo
+ * split of operands scaled by their exact maxima), TN_PREC_SCALED_FP16 and
+ * TN_PREC_SCALED_BF16 (one 16-bit product per real product, operands scaled
+ * by their exact maxima, Sec. "A Mixed-Precision Computation Method via
+ * Adaptive Precision Scaling"); C is complex64 with the scales undone.  The
+ * gathering tensor-core kernel runs split bf16 only; the other algorithms
+ * compute in FP32 whatever the precision.  TN_PAIR_AUTO picks the TMA
+ * tensor-core kernel for any 16-bit precision when the shape allows it.
+ * Asynchronous on `stream`, except the tensor-core algorithms, which return
+ * once the kernel has finished (they check its error word). */
 tn_status tn_contract_pair(const void* A, const int32_t* a_labels, int32_t a_rank,
                            const void* B, const int32_t* b_labels, int32_t b_rank,
                            void* C, const int32_t* c_labels, int32_t c_rank,

@@ -73,7 +73,7 @@ class Request(C.Structure):
 class RequestStats(C.Structure):
     _fields_ = [("submit_to_done_ms", C.c_double), ("queue_ms", C.c_double), ("device_ms", C.c_double),
                 ("flops", C.c_double), ("slices", C.c_int64), ("status", C.c_int32), ("num_open", C.c_int32),
-                ("nb", C.c_int64), ("plan_hash", C.c_uint64), ("planned_here", C.c_int32), ("reserved", C.c_int32)]
+                ("nb", C.c_int64), ("plan_hash", C.c_uint64), ("planned_here", C.c_int32), ("stem_reused", C.c_int32)]
 
 
 class Report(C.Structure):

@@ -19,6 +19,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "kernels.h"
@@ -33,11 +35,57 @@ constexpr int kFlaggedCap = 1 << 16;  // listed flagged units per call
 // instead splits complex64 operands with their exact maxima.
 constexpr bool kHandoverDefault[5] = {false, true, false, true, true};
 
+// A plan's stem: the leaf store and the phase-0 outputs.  Neither depends on
+// the bitstring, the slice or the precision (phase 0 always runs in
+// complex64), so every plan of one circuit can read the same copy.  The
+// first plan that needs the phase-0 outputs computes them on its stream and
+// records `ready`; later plans make their streams wait for that event.
+struct Stem {
+  int device = -1;
+  uint64_t hash = 0;
+  float2* store = nullptr;
+  float2* inv = nullptr;
+  int64_t bytes = 0;
+  std::mutex mu;
+  bool inv_ready = false;
+  cudaEvent_t ready = nullptr;
+  ~Stem() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (device >= 0) cudaSetDevice(device);
+    cudaFree(store);
+    cudaFree(inv);
+    if (ready) cudaEventDestroy(ready);
+    if (cur >= 0) cudaSetDevice(cur);
+  }
+};
+
+struct StemCache {
+  std::mutex mu;
+  int64_t cap = 0, bytes = 0, hits = 0, misses = 0;
+  uint64_t tick = 0;
+  struct Entry { std::shared_ptr<Stem> stem; uint64_t last = 0; };
+  std::map<std::pair<int, uint64_t>, Entry> m;
+};
+
+std::shared_ptr<StemCache> make_stem_cache(int64_t cap_bytes) {
+  auto c = std::make_shared<StemCache>();
+  c->cap = std::max<int64_t>(0, cap_bytes);
+  return c;
+}
+
+StemCacheStats stem_cache_stats(StemCache& c) {
+  std::lock_guard<std::mutex> g(c.mu);
+  return {(int64_t)c.m.size(), c.bytes, c.hits, c.misses};
+}
+
 struct Executor {
   int device = -1;
   float2* store = nullptr;
   float2* inv = nullptr;
   bool inv_ready = false;
+  std::shared_ptr<Stem> stem;  // when set, store and inv belong to it
+  bool stem_reused = false;
   float2* sarena = nullptr;  // slice arena
   float2* parena = nullptr;  // pair arena
   int64_t sarena_cap = 0, parena_cap = 0;  // capacities in elements
@@ -76,8 +124,11 @@ void destroy_executor(Executor* e) {
   int cur = -1;
   cudaGetDevice(&cur);
   if (e->device >= 0) cudaSetDevice(e->device);
-  cudaFree(e->store);
-  cudaFree(e->inv);
+  if (!e->stem) {
+    cudaFree(e->store);
+    cudaFree(e->inv);
+  }
+  e->stem.reset();
   cudaFree(e->sarena);
   cudaFree(e->parena);
   cudaFree(e->gather);
@@ -145,19 +196,74 @@ void make_gemm_desc(const std::vector<int>& la, const std::vector<int>& lb, cons
   d.units = d.units_lo = 1;
 }
 
-static tn_status setup(Plan& P, Executor& E) {
-  CK(cudaGetDevice(&E.device));
+// Leaf store of a plan: every leaf in complex64 at its store offset.
+static tn_status upload_leaves(const Plan& P, float2** store) {
   const Network& N = P.net;
-  const int L = (int)N.leaves.size();
   std::vector<float2> h_store(std::max<int64_t>(P.leaf_store_elems, 1));
-  for (int i = 0; i < L; ++i) {
+  for (size_t i = 0; i < N.leaves.size(); ++i) {
     const Leaf& lf = N.leaves[i];
     for (size_t e = 0; e < lf.data.size(); ++e)
       h_store[P.leaf_use[i].store_off + e] = make_float2((float)lf.data[e].real(), (float)lf.data[e].imag());
   }
-  CK(cudaMalloc(&E.store, h_store.size() * sizeof(float2)));
-  CK(cudaMemcpy(E.store, h_store.data(), h_store.size() * sizeof(float2), cudaMemcpyHostToDevice));
-  CK(cudaMalloc(&E.inv, P.invariant_elems * sizeof(float2)));
+  CK(cudaMalloc(store, h_store.size() * sizeof(float2)));
+  CK(cudaMemcpy(*store, h_store.data(), h_store.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  return TN_OK;
+}
+
+// The plan's stem from its cache (created on a miss), evicting unused
+// entries beyond the cache's capacity.
+static tn_status acquire_stem(const Plan& P, int device, std::shared_ptr<Stem>& out) {
+  StemCache& C = *P.stems;
+  std::lock_guard<std::mutex> g(C.mu);
+  const auto key = std::make_pair(device, P.hash);
+  auto it = C.m.find(key);
+  if (it != C.m.end()) {
+    it->second.last = ++C.tick;
+    ++C.hits;
+    out = it->second.stem;
+    return TN_OK;
+  }
+  auto st = std::make_shared<Stem>();
+  st->device = device;
+  st->hash = P.hash;
+  tn_status r = upload_leaves(P, &st->store);
+  if (r != TN_OK) return r;
+  CK(cudaMalloc(&st->inv, std::max<int64_t>(P.invariant_elems, 1) * sizeof(float2)));
+  CK(cudaEventCreateWithFlags(&st->ready, cudaEventDisableTiming));
+  st->bytes = 8 * (std::max<int64_t>(P.leaf_store_elems, 1) + std::max<int64_t>(P.invariant_elems, 1));
+  ++C.misses;
+  C.bytes += st->bytes;
+  C.m[key] = StemCache::Entry{st, ++C.tick};
+  // least recently used entries that no plan holds go first
+  while (C.bytes > C.cap) {
+    auto victim = C.m.end();
+    for (auto j = C.m.begin(); j != C.m.end(); ++j)
+      if (j->second.stem.use_count() == 1 && (victim == C.m.end() || j->second.last < victim->second.last))
+        victim = j;
+    if (victim == C.m.end()) break;
+    C.bytes -= victim->second.stem->bytes;
+    C.m.erase(victim);
+  }
+  out = st;
+  return TN_OK;
+}
+
+bool stem_reused(const Plan& P) { return P.exec && P.exec->stem_reused; }
+
+static tn_status setup(Plan& P, Executor& E) {
+  CK(cudaGetDevice(&E.device));
+  const Network& N = P.net;
+  const int L = (int)N.leaves.size();
+  if (P.stems) {
+    tn_status r = acquire_stem(P, E.device, E.stem);
+    if (r != TN_OK) return r;
+    E.store = E.stem->store;
+    E.inv = E.stem->inv;
+  } else {
+    tn_status r = upload_leaves(P, &E.store);
+    if (r != TN_OK) return r;
+    CK(cudaMalloc(&E.inv, std::max<int64_t>(P.invariant_elems, 1) * sizeof(float2)));
+  }
   std::vector<LeafGather> g1, g2;
   for (int i = 0; i < L; ++i) {
     const LeafUse& U = P.leaf_use[i];
@@ -580,18 +686,30 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
   if (scaled && (flags & 1)) CK(cudaMemsetAsync(E.nflagged, 0, sizeof(unsigned long long), st));
   Geo g;
   if (!E.inv_ready) {
-    // invariant steps once, always in complex64 so that any later precision can use them
-    const int keep = c.precision;
-    const bool keep_tc = c.tc;
-    c.precision = TN_PREC_C64;
-    c.tc = false;
-    for (size_t s = 0; s < P.steps.size(); ++s)
-      if (P.steps[s].phase == 0) {
-        tn_status r = run_step(c, s, g);
-        if (r != TN_OK) return r;
+    // invariant steps once, always in complex64 so that any later precision
+    // can use them; with a shared stem, once for every plan of the circuit
+    std::unique_lock<std::mutex> lk;
+    if (E.stem) lk = std::unique_lock<std::mutex>(E.stem->mu);
+    if (E.stem && E.stem->inv_ready) {
+      CK(cudaStreamWaitEvent(st, E.stem->ready, 0));
+      E.stem_reused = true;
+    } else {
+      const int keep = c.precision;
+      const bool keep_tc = c.tc;
+      c.precision = TN_PREC_C64;
+      c.tc = false;
+      for (size_t s = 0; s < P.steps.size(); ++s)
+        if (P.steps[s].phase == 0) {
+          tn_status r = run_step(c, s, g);
+          if (r != TN_OK) return r;
+        }
+      c.precision = keep;
+      c.tc = keep_tc;
+      if (E.stem) {
+        CK(cudaEventRecord(E.stem->ready, st));
+        E.stem->inv_ready = true;
       }
-    c.precision = keep;
-    c.tc = keep_tc;
+    }
     E.inv_ready = true;
   }
   const int L = (int)P.net.leaves.size();

@@ -259,4 +259,24 @@ cudaError_t run_gemm_tc2(const float2* A, const float2* B, float2* C, const Gemm
   return launch_gemm_tma(pa, pb, C, false, d, bf16, none, err, s);
 }
 
+cudaError_t run_gemm_tc2_scaled(const float2* A, const float2* B, float2* C, const GemmDesc& d, bool bf16, int np,
+                                uint16_t* scratch, void* aux, int* err, cudaStream_t s) {
+  unsigned* mx = reinterpret_cast<unsigned*>(aux);
+  int* ex = reinterpret_cast<int*>(mx + 2);
+  float* ms = reinterpret_cast<float*>(ex + 2);
+  cudaError_t e = cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned), s);
+  PlaneOperand pa, pb;
+  if (e == cudaSuccess) e = split_operand(A, d, false, bf16, np, true, mx, ex, ms, scratch, pa, s);
+  if (e == cudaSuccess)
+    e = split_operand(B, d, true, bf16, np, true, mx + 1, ex + 1, ms + 1,
+                      scratch + split_scratch_elems(d, false, np), pb, s);
+  if (e != cudaSuccess) return e;
+  ScaleIO sio{};
+  sio.ea = ex;
+  sio.ma = ms;
+  sio.eb = ex + 1;
+  sio.mb = ms + 1;
+  return launch_gemm_tma(pa, pb, C, false, d, bf16, sio, err, s);
+}
+
 }  // namespace tn

@@ -12,9 +12,13 @@
 // complex multiply-add, the counted rate.  For the split precision each
 // operand is x = hi + lo with hi = rn16(x), lo = rn16(x - hi) and the product
 // keeps hi*hi + hi*lo + lo*hi (three MMAs into the same FP32 accumulator).
+// The tensor core adds into that accumulator with truncation, which over a
+// long K leaves an error growing with K and biased toward zero; so each chunk
+// of CHUNK K stages after the first accumulates into a fresh partial P, which
+// all warps then add into the running sum R with round-to-nearest FP32 adds.
 //
-// Per CTA: one 128 (complex rows) x 64 (complex columns) output tile held in
-// TMEM as 128 lanes x 128 FP32 columns.  Each K stage of 32 complex values is
+// Per CTA: one 128 (complex rows) x TN (complex columns) output tile held in
+// TMEM as 128 lanes x 2 TN FP32 columns (R), plus 2 TN columns for P.  Each K stage of 32 complex values is
 // gathered from global memory through per-row / per-column offsets (the
 // permutation), converted to 16-bit hi/lo, and stored K-major in 128-byte
 // swizzled shared memory; one thread issues the tcgen05.mma instructions and
@@ -37,6 +41,7 @@ constexpr int TK = 32;           // complex K per stage (64 reals = one 128-byte
 constexpr int NTHREADS = 256;
 constexpr int A_TILE = 128 * 128;                   // 128 rows x 128 bytes
 constexpr long long kWaitLimit = 1ll << 24;
+constexpr int CHUNK = 16;        // K stages per TMEM partial sum
 
 // Tile configuration by complex column count TN (MMA N = 2 TN reals).
 template <int TN>
@@ -45,7 +50,7 @@ struct Cfg {
   static constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;       // A hi, A lo, B' hi, B' lo
   static constexpr int NSTAGE = TN == 64 ? 3 : 2;
   static constexpr int SMEM = NSTAGE * STAGE + 1024;          // + alignment slack
-  static constexpr uint32_t TMEM_COLS = 2 * TN;
+  static constexpr uint32_t TMEM_COLS = 4 * TN;               // running sum R and chunk partial P
   static constexpr int BCH = TN * 8 / NTHREADS;               // B chunks per thread
 };
 
@@ -139,6 +144,23 @@ struct Half16<false> {
 
 __device__ __forceinline__ uint32_t pack2(uint16_t a, uint16_t b) { return (uint32_t)a | ((uint32_t)b << 16); }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
 // Register staging of one K stage: each thread owns 4 A-chunks and BCH
 // B-chunks, a chunk being 4 consecutive complex K values of one row (A) or
 // column (B).
@@ -158,7 +180,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ uint64_t bar_mma[NSTAGE];
-  __shared__ uint64_t bar_done;
+  __shared__ uint64_t bar_done, bar_chunk;
   __shared__ uint32_t tmem_base_slot;
   __shared__ int32_t rowA[TM], rowC[TM], colB[TN], colC[TN];
   __shared__ int32_t kA[2][TK], kB[2][TK];
@@ -186,6 +208,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; ++s) mbar_init(&bar_mma[s], 1);
     mbar_init(&bar_done, 1);
+    mbar_init(&bar_chunk, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -304,6 +327,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   constexpr uint32_t IDESC = idesc_f16(BF16, 128, 2 * TN);
   Stage<BCH> st;
   load_stage(st, 0);
+  uint32_t nfold = 0;
   for (int kt = 0; kt < nkt; ++kt) {
     const int s = kt % NSTAGE;
     if (kt >= NSTAGE) {
@@ -327,15 +351,45 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint64_t alo = sw128_desc(base + A_TILE + kk * 32);
         const uint64_t bhi = sw128_desc(base + 2 * A_TILE + kk * 32);
         const uint64_t blo = sw128_desc(base + 2 * A_TILE + CF::B_TILE + kk * 32);
-        const uint32_t first = (kt == 0 && kk == 0) ? 0u : 1u;
-        mma_f16(tmem, ahi, bhi, IDESC, first);
-        mma_f16(tmem, ahi, blo, IDESC, 1u);
-        mma_f16(tmem, alo, bhi, IDESC, 1u);
+        // chunk 0 accumulates into R, later chunks into a fresh P
+        const uint32_t dst = kt < CHUNK ? tmem : tmem + 2 * TN;
+        const uint32_t first = (kt % CHUNK == 0 && kk == 0) ? 0u : 1u;
+        mma_f16(dst, ahi, bhi, IDESC, first);
+        mma_f16(dst, ahi, blo, IDESC, 1u);
+        mma_f16(dst, alo, bhi, IDESC, 1u);
       }
       mma_commit(&bar_mma[s]);
+      if (kt >= CHUNK && (kt % CHUNK == CHUNK - 1 || kt == nkt - 1)) mma_commit(&bar_chunk);
       if (kt == nkt - 1) mma_commit(&bar_done);
     }
     if (kt + 1 < nkt) load_stage(st, (kt + 1) & 1);  // in flight while the MMAs above run
+    if (kt >= CHUNK && (kt % CHUNK == CHUNK - 1 || kt == nkt - 1)) {
+      // fold the chunk's partial P into R: warp w owns TMEM lanes 32 (w % 4)..
+      // and half w / 4 of the 2 TN columns
+      const bool ok = mbar_wait(&bar_chunk, nfold & 1);
+      ++nfold;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(err, 3);
+        abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int q = warp & 3, half = warp >> 2;
+      const uint32_t lb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * TN);
+#pragma unroll 1
+      for (int cc = 0; cc < TN; cc += 16) {
+        uint32_t pv[16], rv[16];
+        tmem_ld16(lb + 2 * TN + cc, pv);
+        tmem_ld16(lb + cc, rv);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) rv[j] = __float_as_uint(__uint_as_float(rv[j]) + __uint_as_float(pv[j]));
+        tmem_st16(lb + cc, rv);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+    }
   }
   __syncthreads();
   // On an aborted loop the last commit was never issued: commit now so that the

@@ -10,12 +10,11 @@
 //   Dr = Ar Br - Ai Bi,  Di = Ar Bi + Ai Br,
 // FP32 accumulation in TMEM (Dr and Di take TN columns each), the minus sign
 // through the MMA's negate-A bit.  Split precision (four planes re_hi, re_lo,
-// im_hi, im_lo) expands each real product X Y as Xhi Yhi + Xhi Ylo + Xlo Yhi;
-// single precision (two planes re, im) keeps one 16-bit product.  The small
-// hi*lo + lo*hi terms go to separate correction accumulators, added to the
-// hi*hi sums in FP32 in the epilogue: the tensor core's accumulation keeps
-// fewer bits than an FP32 add when a tiny term meets a large running sum, so
-// folding the corrections into the main sum would cap the split accuracy.
+// im_hi, im_lo) expands each real product X Y as Xhi Yhi + Xhi Ylo + Xlo Yhi
+// and runs in gemm_tma_chunked, which bounds the tensor core's truncating
+// accumulation to short chunks; single precision (two planes re, im) keeps
+// one 16-bit product and runs in gemm_tma_kernel (one tile per CTA) or
+// gemm_tma_persistent (one CTA per SM, double-buffered accumulators).
 //
 // Adaptive scaling (Sec. "A Mixed-Precision Computation Method via Adaptive
 // Precision Scaling"): a plane tensor stores x 2^-e with a per-unit integer
@@ -62,9 +61,8 @@ struct Cfg2 {
   static constexpr int STAGE = A_STAGE + B_STAGE;
   static constexpr int NSTAGE = (SMEM_BUDGET / STAGE) < 6 ? (SMEM_BUDGET / STAGE) : 6;
   static constexpr int SMEM = NSTAGE * STAGE + 1024;
-  // accumulator columns per tile: Dr, Di (TN each) and, for split precision,
-  // the correction sums Cr, Ci of the hi*lo + lo*hi terms (TN each)
-  static constexpr int ACC = (NP == 4 ? 4 : 2) * TN;
+  // accumulator columns per tile: Dr, Di (TN each)
+  static constexpr int ACC = 2 * TN;
   static constexpr uint32_t TMEM_COLS = ACC < 32 ? 32 : ACC;
 };
 
@@ -159,6 +157,22 @@ __device__ __forceinline__ uint16_t to16(float x) {
   return __half_as_ushort(__float2half_rn(x));
 }
 
+// Multiplication by 2^e for the exponent shifts of the scaled formats.  A
+// power of two in the normal range multiplies exactly, so one multiply gives
+// the correctly rounded x 2^e (the value ldexpf returns); shifts outside
+// [-126, 127] go through ldexpf.
+struct Pow2 {
+  int e;
+  float f;
+  bool direct;
+  __device__ explicit Pow2(int e_) {
+    e = e_;
+    direct = e_ >= -126 && e_ <= 127;
+    f = __int_as_float((min(max(e_, -126), 127) + 127) << 23);
+  }
+  __device__ float operator()(float x) const { return direct ? x * f : ldexpf(x, e); }
+};
+
 template <int NREG>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t* v);
 template <>
@@ -175,6 +189,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_tma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                     float2* __restrict__ C, const GemmDesc d, int kp, int a_zlo, int a_zhi, int b_zlo, int b_zhi,
                     int c_planes, const ScaleIO sio, int* __restrict__ err) {
+  static_assert(NP == 2, "split precision runs in gemm_tma_chunked");
   using CF = Cfg2<TN, NP>;
   constexpr int A_STAGE = CF::A_STAGE;
   constexpr int NS = CF::NSTAGE;
@@ -265,7 +280,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (warp == 1) {
     // ---- MMA issuer (one lane)
     constexpr uint32_t I = idesc2(BF16, TM, TN, false), IN = idesc2(BF16, TM, TN, true);
-    const uint32_t dr = tmem, di = tmem + TN, cr = tmem + 2 * TN, ci = tmem + 3 * TN;
+    const uint32_t dr = tmem, di = tmem + TN;
     int issued = 0;
     for (int kt = 0; lane == 0 && kt < nkt; ++kt) {
       const int s = kt % NS;
@@ -287,28 +302,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           B_[p] = sw64_desc(b + p * (TN * 64) + kk * 32);
         }
         const uint32_t acc = (kt | kk) ? 1u : 0u;
-        if constexpr (NP == 4) {
-          // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
-          // hi*hi into Dr, Di; hi*lo + lo*hi into the correction sums Cr, Ci
-          mma(dr, A_[0], B_[0], I, acc);
-          mma(dr, A_[2], B_[2], IN, 1u);
-          mma(di, A_[0], B_[2], I, acc);
-          mma(di, A_[2], B_[0], I, 1u);
-          mma(cr, A_[0], B_[1], I, acc);
-          mma(cr, A_[1], B_[0], I, 1u);
-          mma(cr, A_[2], B_[3], IN, 1u);
-          mma(cr, A_[3], B_[2], IN, 1u);
-          mma(ci, A_[0], B_[3], I, acc);
-          mma(ci, A_[1], B_[2], I, 1u);
-          mma(ci, A_[2], B_[1], I, 1u);
-          mma(ci, A_[3], B_[0], I, 1u);
-        } else {
-          // planes: 0 re, 1 im
-          mma(dr, A_[0], B_[0], I, acc);
-          mma(dr, A_[1], B_[1], IN, 1u);
-          mma(di, A_[0], B_[1], I, acc);
-          mma(di, A_[1], B_[0], I, 1u);
-        }
+        // planes: 0 re, 1 im
+        mma(dr, A_[0], B_[0], I, acc);
+        mma(dr, A_[1], B_[1], IN, 1u);
+        mma(di, A_[0], B_[1], I, acc);
+        mma(di, A_[1], B_[0], I, 1u);
       }
       commit(&empty[s]);
       ++issued;
@@ -334,30 +332,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // thread's 16 columns form one contiguous run (16-element aligned)
       const bool n16 = d.nn >= 4 && d.cn[0] == 1 && d.cn[1] == 2 && d.cn[2] == 4 && d.cn[3] == 8;
       // plane output: stored = acc 2^-r; complex64 output: true value = acc 2^(eA+eB)
-      const int shift = c_planes ? -r : ea + eb;
+      const Pow2 sc(c_planes ? -r : ea + eb);
       float vmax = 0.f;
       bool bad = false;
 #pragma unroll 1
       for (int c0 = 0; c0 < TN; c0 += 16) {
-        uint32_t ur[16], ui[16], uc[16], ud[16];
+        uint32_t ur[16], ui[16];
         const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
         tmem_ld<16>(lane_base + (uint32_t)c0, ur);
         tmem_ld<16>(lane_base + (uint32_t)(TN + c0), ui);
-        if constexpr (NP == 4) {
-          tmem_ld<16>(lane_base + (uint32_t)(2 * TN + c0), uc);
-          tmem_ld<16>(lane_base + (uint32_t)(3 * TN + c0), ud);
-        }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         float vr[16], vi[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           float xr = __uint_as_float(ur[j]), xi = __uint_as_float(ui[j]);
-          if constexpr (NP == 4) {
-            xr += __uint_as_float(uc[j]);
-            xi += __uint_as_float(ud[j]);
-          }
-          vr[j] = ldexpf(xr, shift);
-          vi[j] = ldexpf(xi, shift);
+          vr[j] = sc(xr);
+          vi[j] = sc(xi);
         }
         if (ro < 0) continue;
         if (c_planes) {
@@ -372,13 +362,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               vmax = fmaxf(vmax, fmaxf(fabsf(vr[j]), fabsf(vi[j])));
               bad |= !isfinite(vr[j]) || !isfinite(vi[j]);
             }
-            if constexpr (NP == 4) {
-              split16<BF16>(vr[j], h[0][j], h[1][j]);
-              split16<BF16>(vi[j], h[2][j], h[3][j]);
-            } else {
-              h[0][j] = to16<BF16>(vr[j]);
-              h[1][j] = to16<BF16>(vi[j]);
-            }
+            h[0][j] = to16<BF16>(vr[j]);
+            h[1][j] = to16<BF16>(vi[j]);
           }
           if (n16 && colC[c0] >= 0) {
             const int64_t o = (int64_t)ro + colC[c0];
@@ -441,6 +426,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_tma_persistent(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                         float2* __restrict__ C0, const GemmDesc d, int kp, int a_zlo, int a_zhi, int b_zlo,
                         int b_zhi, int c_planes, const ScaleIO sio, int* __restrict__ err) {
+  static_assert(NP == 2, "split precision runs in gemm_tma_chunked");
   using CF = Cfg2<TN, NP>;
   constexpr int NS = CF::NSTAGE;
   constexpr int A_STAGE = CF::A_STAGE;
@@ -524,7 +510,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t dr = tmem + (uint32_t)(b * CF::ACC), di = dr + TN, cr = dr + 2 * TN, ci = dr + 3 * TN;
+      const uint32_t dr = tmem + (uint32_t)(b * CF::ACC), di = dr + TN;
       bool ok = true;
       for (int kt = 0; kt < nkt; ++kt, ++g) {
         const int s = (int)(g % NS);
@@ -546,26 +532,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             B_[p] = sw64_desc(bb + p * (TN * 64) + kk * 32);
           }
           const uint32_t acc = (kt | kk) ? 1u : 0u;
-          if constexpr (NP == 4) {
-            // hi*hi into Dr, Di; hi*lo + lo*hi into the correction sums Cr, Ci
-            mma(dr, A_[0], B_[0], I, acc);
-            mma(dr, A_[2], B_[2], IN, 1u);
-            mma(di, A_[0], B_[2], I, acc);
-            mma(di, A_[2], B_[0], I, 1u);
-            mma(cr, A_[0], B_[1], I, acc);
-            mma(cr, A_[1], B_[0], I, 1u);
-            mma(cr, A_[2], B_[3], IN, 1u);
-            mma(cr, A_[3], B_[2], IN, 1u);
-            mma(ci, A_[0], B_[3], I, acc);
-            mma(ci, A_[1], B_[2], I, 1u);
-            mma(ci, A_[2], B_[1], I, 1u);
-            mma(ci, A_[3], B_[0], I, 1u);
-          } else {
-            mma(dr, A_[0], B_[0], I, acc);
-            mma(dr, A_[1], B_[1], IN, 1u);
-            mma(di, A_[0], B_[1], I, acc);
-            mma(di, A_[1], B_[0], I, 1u);
-          }
+          // planes: 0 re, 1 im
+          mma(dr, A_[0], B_[0], I, acc);
+          mma(dr, A_[1], B_[1], IN, 1u);
+          mma(di, A_[0], B_[1], I, acc);
+          mma(di, A_[1], B_[0], I, 1u);
         }
         commit(&empty[s]);
       }
@@ -616,30 +587,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
       const bool n16 = d.nn >= 4 && d.cn[0] == 1 && d.cn[1] == 2 && d.cn[2] == 4 && d.cn[3] == 8;
-      const int shift = c_planes ? -r : ea + eb;
+      const Pow2 sc(c_planes ? -r : ea + eb);
       float vmax = 0.f;
       bool bad = false;
       const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * CF::ACC);
 #pragma unroll 1
       for (int c0 = 0; c0 < TN; c0 += 16) {
-        uint32_t ur[16], ui[16], uc[16], ud[16];
+        uint32_t ur[16], ui[16];
         tmem_ld<16>(lane_base + (uint32_t)c0, ur);
         tmem_ld<16>(lane_base + (uint32_t)(TN + c0), ui);
-        if constexpr (NP == 4) {
-          tmem_ld<16>(lane_base + (uint32_t)(2 * TN + c0), uc);
-          tmem_ld<16>(lane_base + (uint32_t)(3 * TN + c0), ud);
-        }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         float vr[16], vi[16];
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
           float xr = __uint_as_float(ur[jj]), xi = __uint_as_float(ui[jj]);
-          if constexpr (NP == 4) {
-            xr += __uint_as_float(uc[jj]);
-            xi += __uint_as_float(ud[jj]);
-          }
-          vr[jj] = ldexpf(xr, shift);
-          vi[jj] = ldexpf(xi, shift);
+          vr[jj] = sc(xr);
+          vi[jj] = sc(xi);
         }
         if (c_planes) {
           uint16_t* P = reinterpret_cast<uint16_t*>(C);
@@ -649,13 +612,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           for (int jj = 0; jj < 16; ++jj) {
             vmax = fmaxf(vmax, fmaxf(fabsf(vr[jj]), fabsf(vi[jj])));
             bad |= !isfinite(vr[jj]) || !isfinite(vi[jj]);
-            if constexpr (NP == 4) {
-              split16<BF16>(vr[jj], h[0][jj], h[1][jj]);
-              split16<BF16>(vi[jj], h[2][jj], h[3][jj]);
-            } else {
-              h[0][jj] = to16<BF16>(vr[jj]);
-              h[1][jj] = to16<BF16>(vi[jj]);
-            }
+            h[0][jj] = to16<BF16>(vr[jj]);
+            h[1][jj] = to16<BF16>(vi[jj]);
           }
           if (n16) {
             const int64_t o = (int64_t)ro + colC[b][c0];
@@ -718,11 +676,18 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
 
 // Split precision, persistent, with chunked accumulation.  The tensor core
 // adds into its FP32 accumulator with truncation, so over a long K the error
-// grows linearly and is biased toward zero.  Here the MMA warp accumulates
-// each chunk of CHUNK K stages into a fresh TMEM partial P; the epilogue warps
-// fold P into a TMEM running sum R with round-to-nearest FP32 adds and, after
-// the last chunk of a tile, scale and store it.  The bias then scales with
-// the chunk length, not with K.  TMEM: P (2 TN columns) and R (2 TN).
+// grows linearly and is biased toward zero.  Here every chunk of CHUNK K
+// stages starts a fresh accumulator, and the epilogue warps add the chunks
+// with round-to-nearest FP32 adds, so the bias scales with the chunk length,
+// not with K.
+//
+// TMEM holds two buffers of 2 TN columns (Dr, Di).  The CTA's t-th tile keeps
+// its running sum R in buffer t & 1: its first chunk accumulates there
+// directly; every later chunk accumulates in the other buffer P, which the
+// epilogue folds into R (R += P, read P, read R, add, write R) and releases.
+// After the last chunk the epilogue scales and stores R while the MMA warp
+// already runs the next tile's first chunk in the other buffer (the next
+// tile's R), so the MMA warp waits only for the folds, never for a store.
 constexpr int CHUNK = 16;
 
 template <int TN, bool BF16>
@@ -734,11 +699,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   using CF = Cfg2<TN, NP>;
   constexpr int NS = CF::NSTAGE;
   constexpr int A_STAGE = CF::A_STAGE;
-  constexpr uint32_t COLS = 4 * TN < 32 ? 32 : 4 * TN;
-  static_assert(4 * TN <= 512, "partial and running sums must fit in TMEM");
+  constexpr uint32_t BUF = 2 * TN;  // columns of one buffer
+  constexpr uint32_t COLS = 2 * BUF < 32 ? 32 : 2 * BUF;
+  static_assert(2 * BUF <= 512, "two accumulator buffers must fit in TMEM");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t full[NS], empty[NS], p_full, p_empty;
+  __shared__ uint64_t full[NS], empty[NS], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int32_t colC[TN];
   __shared__ volatile int abort_flag;
@@ -763,8 +729,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    mbar_init(&p_full, 1);
-    mbar_init(&p_empty, 128);
+    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 128); }
     abort_flag = 0;
     epi_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -782,7 +747,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t tmem = tmem_slot;
 
   if (warp == 0) {
-    // ---- TMA producer
+    // ---- TMA producer: the stage ring runs on across items
     int64_t g = 0;
     for (int64_t it = blockIdx.x; lane == 0 && it < items && !abort_flag; it += gridDim.x) {
       int unit, m0, n0;
@@ -805,20 +770,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     __syncwarp();
   } else if (warp == 1) {
-    // ---- MMA issuer: chunk jc of the CTA accumulates into P
+    // ---- MMA issuer.  Chunk 0 of the t-th tile goes to buffer t & 1, later
+    // chunks to the other one; the n-th use of a buffer (n >= 1) waits for
+    // the epilogue's (n-1)-th release of it.
     constexpr uint32_t I = idesc2(BF16, TM, TN, false), IN = idesc2(BF16, TM, TN, true);
-    const uint32_t dr = tmem, di = tmem + TN;
-    int64_t g = 0, jc = 0;
+    int64_t g = 0, t = 0;
+    uint32_t used[2] = {0u, 0u};
     bool ok = true;
-    for (int64_t it = blockIdx.x; lane == 0 && ok && it < items && !abort_flag; it += gridDim.x) {
-      for (int c = 0; c < nch && ok; ++c, ++jc) {
-        if (jc >= 1 && !mbar_wait(&p_empty, (uint32_t)((jc - 1) & 1))) {
+    for (int64_t it = blockIdx.x; lane == 0 && ok && it < items && !abort_flag; it += gridDim.x, ++t) {
+      const int rb = (int)(t & 1);
+      for (int c = 0; c < nch && ok; ++c) {
+        const int b = c == 0 ? rb : 1 - rb;
+        if (used[b] >= 1 && !mbar_wait(&acc_empty[b], (used[b] - 1) & 1)) {
           atomicExch(err, 32);
           abort_flag = 1;
           ok = false;
           break;
         }
+        ++used[b];
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dr = tmem + (uint32_t)b * BUF, di = dr + TN;
         const int k0 = c * CHUNK, k1 = min(nkt, k0 + CHUNK);
         for (int kt = k0; kt < k1; ++kt, ++g) {
           const int s = (int)(g % NS);
@@ -857,22 +828,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           commit(&empty[s]);
         }
-        commit(&p_full);  // also after an abort, so the epilogue's wait ends
+        commit(&acc_full[b]);  // also after an abort, so the epilogue's wait ends
       }
     }
     __syncwarp();
   } else if (warp >= 4) {
-    // ---- epilogue: fold every chunk into R; after the last one, store
+    // ---- epilogue: fold chunks 1.. into R; after the last one, store R
     const int q = warp & 3;
-    const int t = tid - 128;
+    const int tq = tid - 128;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    const uint32_t P = tmem + lane_off, R = tmem + lane_off + 2 * TN;
-    int64_t jc = 0;
-    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    int64_t t = 0;
+    uint32_t seen[2] = {0u, 0u};
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x, ++t) {
       int unit, m0, n0;
       decode(it, unit, m0, n0);
       const int ulo = unit % d.units_lo, uhi = unit / d.units_lo;
-      for (int jj = t; jj < TN; jj += 128) colC[jj] = bit_offset(n0 + jj, d.nn, d.cn);
+      for (int jj = tq; jj < TN; jj += 128) colC[jj] = bit_offset(n0 + jj, d.nn, d.cn);
       const int32_t ro = bit_offset(m0 + q * 32 + lane, d.nm, d.cm);
       float2* C = C0 + (int64_t)ulo * d.c_lo + (int64_t)uhi * d.c_hi;
       int ea = 0, eb = 0, r = 0;
@@ -892,11 +863,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
       const bool n16 = d.nn >= 4 && d.cn[0] == 1 && d.cn[1] == 2 && d.cn[2] == 4 && d.cn[3] == 8;
-      const int shift = c_planes ? -r : ea + eb;
-      float vmax = 0.f;
-      bool bad = false;
-      for (int c = 0; c < nch; ++c, ++jc) {
-        bool ok = mbar_wait(&p_full, (uint32_t)(jc & 1));
+      const Pow2 sc(c_planes ? -r : ea + eb);
+      const int rb = (int)(t & 1);
+      const uint32_t R = tmem + lane_off + (uint32_t)rb * BUF, P = tmem + lane_off + (uint32_t)(1 - rb) * BUF;
+      for (int c = 0; c < nch; ++c) {
+        const int b = c == 0 ? rb : 1 - rb;
+        bool ok = mbar_wait(&acc_full[b], seen[b] & 1);
+        ++seen[b];
         ok = __all_sync(0xffffffffu, ok);
         if (!ok && lane == 0) {
           atomicExch(err, 34);
@@ -907,80 +880,85 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("bar.sync 1, 128;" ::: "memory");
         if (epi_fail) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const bool last = c == nch - 1;
+        if (c == 0) continue;  // the first chunk accumulated in R itself
 #pragma unroll 1
         for (int c0 = 0; c0 < TN; c0 += 16) {
           uint32_t pr[16], pi[16], rr[16], ri[16];
           tmem_ld<16>(P + (uint32_t)c0, pr);
           tmem_ld<16>(P + (uint32_t)(TN + c0), pi);
-          if (c > 0) {
-            tmem_ld<16>(R + (uint32_t)c0, rr);
-            tmem_ld<16>(R + (uint32_t)(TN + c0), ri);
-          }
+          tmem_ld<16>(R + (uint32_t)c0, rr);
+          tmem_ld<16>(R + (uint32_t)(TN + c0), ri);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (c > 0) {
-#pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              pr[jj] = __float_as_uint(__uint_as_float(pr[jj]) + __uint_as_float(rr[jj]));
-              pi[jj] = __float_as_uint(__uint_as_float(pi[jj]) + __uint_as_float(ri[jj]));
-            }
-          }
-          if (!last) {
-            tmem_st16(R + (uint32_t)c0, pr);
-            tmem_st16(R + (uint32_t)(TN + c0), pi);
-            continue;
-          }
-          float vr[16], vi[16];
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
-            vr[jj] = ldexpf(__uint_as_float(pr[jj]), shift);
-            vi[jj] = ldexpf(__uint_as_float(pi[jj]), shift);
+            rr[jj] = __float_as_uint(__uint_as_float(rr[jj]) + __uint_as_float(pr[jj]));
+            ri[jj] = __float_as_uint(__uint_as_float(ri[jj]) + __uint_as_float(pi[jj]));
           }
-          if (c_planes) {
-            uint16_t* Pl = reinterpret_cast<uint16_t*>(C);
-            const int64_t plane = int64_t(1) << (d.nm + d.nn);
-            uint16_t h[NP][16];
-#pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              vmax = fmaxf(vmax, fmaxf(fabsf(vr[jj]), fabsf(vi[jj])));
-              bad |= !isfinite(vr[jj]) || !isfinite(vi[jj]);
-              split16<BF16>(vr[jj], h[0][jj], h[1][jj]);
-              split16<BF16>(vi[jj], h[2][jj], h[3][jj]);
-            }
-            if (n16) {
-              const int64_t o = (int64_t)ro + colC[c0];
-#pragma unroll
-              for (int p = 0; p < NP; ++p) {
-                uint4* qd = reinterpret_cast<uint4*>(Pl + p * plane + o);
-                qd[0] = make_uint4(h[p][0] | (h[p][1] << 16), h[p][2] | (h[p][3] << 16),
-                                   h[p][4] | (h[p][5] << 16), h[p][6] | (h[p][7] << 16));
-                qd[1] = make_uint4(h[p][8] | (h[p][9] << 16), h[p][10] | (h[p][11] << 16),
-                                   h[p][12] | (h[p][13] << 16), h[p][14] | (h[p][15] << 16));
-              }
-            } else {
-#pragma unroll
-              for (int jj = 0; jj < 16; ++jj) {
-                const int64_t o = (int64_t)ro + colC[c0 + jj];
-#pragma unroll
-                for (int p = 0; p < NP; ++p) Pl[p * plane + o] = h[p][jj];
-              }
-            }
-          } else if (n16) {
-            float4* qd = reinterpret_cast<float4*>(C + (int64_t)ro + colC[c0]);
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj)
-              qd[jj] = make_float4(vr[2 * jj], vi[2 * jj], vr[2 * jj + 1], vi[2 * jj + 1]);
-          } else {
-#pragma unroll
-            for (int jj = 0; jj < 16; ++jj) C[(int64_t)ro + colC[c0 + jj]] = make_float2(vr[jj], vi[jj]);
-          }
+          tmem_st16(R + (uint32_t)c0, rr);
+          tmem_st16(R + (uint32_t)(TN + c0), ri);
         }
-        if (!last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        // P may be refilled once every epilogue thread has read it (and R is written)
+        // R complete before it is read again; P free for the next chunk
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&p_empty)) : "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[1 - rb])) : "memory");
       }
       if (epi_fail) break;
+      float vmax = 0.f;
+      bool bad = false;
+#pragma unroll 1
+      for (int c0 = 0; c0 < TN; c0 += 16) {
+        uint32_t ur[16], ui[16];
+        tmem_ld<16>(R + (uint32_t)c0, ur);
+        tmem_ld<16>(R + (uint32_t)(TN + c0), ui);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float vr[16], vi[16];
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          vr[jj] = sc(__uint_as_float(ur[jj]));
+          vi[jj] = sc(__uint_as_float(ui[jj]));
+        }
+        if (c_planes) {
+          uint16_t* Pl = reinterpret_cast<uint16_t*>(C);
+          const int64_t plane = int64_t(1) << (d.nm + d.nn);
+          uint16_t h[NP][16];
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            vmax = fmaxf(vmax, fmaxf(fabsf(vr[jj]), fabsf(vi[jj])));
+            bad |= !isfinite(vr[jj]) || !isfinite(vi[jj]);
+            split16<BF16>(vr[jj], h[0][jj], h[1][jj]);
+            split16<BF16>(vi[jj], h[2][jj], h[3][jj]);
+          }
+          if (n16) {
+            const int64_t o = (int64_t)ro + colC[c0];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+              uint4* qd = reinterpret_cast<uint4*>(Pl + p * plane + o);
+              qd[0] = make_uint4(h[p][0] | (h[p][1] << 16), h[p][2] | (h[p][3] << 16),
+                                 h[p][4] | (h[p][5] << 16), h[p][6] | (h[p][7] << 16));
+              qd[1] = make_uint4(h[p][8] | (h[p][9] << 16), h[p][10] | (h[p][11] << 16),
+                                 h[p][12] | (h[p][13] << 16), h[p][14] | (h[p][15] << 16));
+            }
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              const int64_t o = (int64_t)ro + colC[c0 + jj];
+#pragma unroll
+              for (int p = 0; p < NP; ++p) Pl[p * plane + o] = h[p][jj];
+            }
+          }
+        } else if (n16) {
+          float4* qd = reinterpret_cast<float4*>(C + (int64_t)ro + colC[c0]);
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj)
+            qd[jj] = make_float4(vr[2 * jj], vi[2 * jj], vr[2 * jj + 1], vi[2 * jj + 1]);
+        } else {
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) C[(int64_t)ro + colC[c0 + jj]] = make_float2(vr[jj], vi[jj]);
+        }
+      }
+      // R read out: the MMA warp may start a later tile's chunks in it
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[rb])) : "memory");
       if (sio.mc || sio.flag) {
         for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
         bad = __any_sync(0xffffffffu, bad);

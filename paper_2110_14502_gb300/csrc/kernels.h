@@ -136,6 +136,12 @@ bool planes_in_place(const float2* base, const GemmDesc& d, bool which_b, int np
 int64_t tc2_scratch_elems(const GemmDesc& d);
 cudaError_t run_gemm_tc2(const float2* A, const float2* B, float2* C, const GemmDesc& d, bool bf16, uint16_t* scratch,
                          int* err, cudaStream_t s);
+// Same with both operands scaled by their exact maxima (one power-of-two
+// exponent each) and split into np planes (4: split fp16/bf16, 2: scaled
+// single products); C is written in complex64 with the exponents applied.
+// aux: 24 bytes of device memory (maxima, exponents, stored maxima).
+cudaError_t run_gemm_tc2_scaled(const float2* A, const float2* B, float2* C, const GemmDesc& d, bool bf16, int np,
+                                uint16_t* scratch, void* aux, int* err, cudaStream_t s);
 cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s);
 cudaError_t launch_set_group(GroupInfo* slot, const GroupInfo& g, cudaStream_t s);
 // grid covers `units` units (the slot's count may be lower for a partial group)

@@ -111,8 +111,8 @@ extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, in
     return fail(TN_EINVAL, "tn_contract_pair: NULL labels");
   tn_status st = check_labels(a_labels, ra, b_labels, rb, c_labels, rc);
   if (st != TN_OK) return st;
-  if (precision != TN_PREC_C64 && precision != TN_PREC_SPLIT_BF16 && precision != TN_PREC_SPLIT_FP16)
-    return fail(TN_EINVAL, "tn_contract_pair: precision %d is not a complex64-storage mode", precision);
+  if (precision < TN_PREC_C64 || precision > TN_PREC_SCALED_BF16)
+    return fail(TN_EINVAL, "tn_contract_pair: unknown precision %d", precision);
   std::vector<int> la(a_labels, a_labels + ra), lb(b_labels, b_labels + rb), lc(c_labels, c_labels + rc);
   GemmDesc d;
   const bool vec_shape = d_is_vector(la, lb, lc);
@@ -126,7 +126,7 @@ extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, in
   float2* c = (float2*)Cv;
   if (algo == TN_PAIR_AUTO) {
     if (d.nn <= 4 && d.nk <= 4) algo = TN_PAIR_VECTOR;
-    else if (precision == TN_PREC_SPLIT_BF16 && tc_shape_ok(d)) algo = TN_PAIR_FUSED_TC;
+    else if (precision != TN_PREC_C64 && tc_shape_ok(d)) algo = TN_PAIR_FUSED_TC;
     else algo = TN_PAIR_FUSED_SIMT;
   }
   cudaError_t e;
@@ -139,8 +139,10 @@ extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, in
     case TN_PAIR_UNFUSED: return unfused(a, b, c, d, s);
     case TN_PAIR_FUSED_TC:
     case TN_PAIR_GATHER_TC: {
-      if (precision != TN_PREC_SPLIT_BF16)
-        return fail(TN_EINVAL, "tn_contract_pair: the tensor-core kernels need precision TN_PREC_SPLIT_BF16");
+      if (precision == TN_PREC_C64)
+        return fail(TN_EINVAL, "tn_contract_pair: the tensor-core kernels need a 16-bit precision");
+      if (algo == TN_PAIR_GATHER_TC && precision != TN_PREC_SPLIT_BF16)
+        return fail(TN_EINVAL, "tn_contract_pair: the gathering tensor-core kernel runs split bf16 only");
       if (!tc_shape_ok(d)) return fail(TN_EINVAL, "tn_contract_pair: tensor-core kernels need M >= 128, N >= 16, K >= 8");
       static int* err = nullptr;
       if (!err) {
@@ -149,11 +151,19 @@ extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, in
       }
       uint16_t* scratch = nullptr;
       if (algo == TN_PAIR_FUSED_TC) {
-        if (cudaMallocAsync(&scratch, (size_t)tc2_scratch_elems(d) * sizeof(uint16_t), s) != cudaSuccess) {
+        // operand planes, then 32 bytes for the scaled modes' maxima and exponents
+        const size_t planes = (size_t)tc2_scratch_elems(d) * sizeof(uint16_t);
+        if (cudaMallocAsync(&scratch, planes + 32, s) != cudaSuccess) {
           cudaGetLastError();
           return fail(TN_EHBM, "tn_contract_pair: operand planes do not fit");
         }
-        e = run_gemm_tc2(a, b, c, d, true, scratch, err, s);
+        void* aux = reinterpret_cast<char*>(scratch) + planes;
+        switch (precision) {
+          case TN_PREC_SPLIT_BF16: e = run_gemm_tc2(a, b, c, d, true, scratch, err, s); break;
+          case TN_PREC_SPLIT_FP16: e = run_gemm_tc2_scaled(a, b, c, d, false, 4, scratch, aux, err, s); break;
+          case TN_PREC_SCALED_FP16: e = run_gemm_tc2_scaled(a, b, c, d, false, 2, scratch, aux, err, s); break;
+          default: e = run_gemm_tc2_scaled(a, b, c, d, true, 2, scratch, aux, err, s); break;
+        }
         cudaFreeAsync(scratch, s);
       } else {
         e = launch_gemm_tc(a, b, c, d, true, 1.f, 1.f, err, s);

@@ -93,6 +93,9 @@ struct Server {
   std::deque<std::shared_ptr<Request>> to_plan, ready;
   std::vector<std::shared_ptr<Request>> active;
   int64_t budget = 0, in_use = 0;
+  // stems (leaf store + phase-0 outputs) of recent circuits, resident for
+  // later requests of the same circuit; its capacity is taken off the budget
+  std::shared_ptr<StemCache> stems;
   std::vector<cudaStream_t> streams;  // one per slot
   std::vector<std::thread> planners;
   std::thread scheduler;
@@ -138,6 +141,7 @@ tn_status plan_request(Server& S, Request& R) {
   }
   auto* copy = new (std::nothrow) tn_plan_s(cached->plan);
   if (!copy) return fail(TN_ENOMEM, "serving: out of host memory");
+  copy->plan.stems = S.stems;
   R.plan.reset(copy);
   const Plan& P = R.plan->plan;
   R.ns = int64_t(1) << P.sliced.size();
@@ -362,7 +366,9 @@ extern "C" tn_status tn_server_create(const tn_server_opts* opts, tn_server** ou
     delete h;
     return fail(TN_ECUDA, "tn_server_create: cudaMemGetInfo failed");
   }
-  S.budget = S.opts.hbm_budget_bytes > 0 ? S.opts.hbm_budget_bytes : (int64_t)(0.6 * (double)freeb);
+  const int64_t total = S.opts.hbm_budget_bytes > 0 ? S.opts.hbm_budget_bytes : (int64_t)(0.6 * (double)freeb);
+  S.stems = make_stem_cache(total / 8);
+  S.budget = total - total / 8;
   for (int i = 0; i < S.opts.max_inflight; ++i) {
     cudaStream_t st;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -453,6 +459,7 @@ extern "C" tn_status tn_wait(tn_server* h, int64_t ticket, double* out, int64_t 
       stats->plan_hash = P.hash;
     }
     stats->planned_here = R->planned_here;
+    stats->stem_reused = R->plan && stem_reused(R->plan->plan) ? 1 : 0;
   }
   tn_status st = R->status;
   if (st == TN_OK && out) {

@@ -78,7 +78,8 @@ struct LeafUse {
   int64_t store_off = 0;        // offset of the full leaf in the leaf store
 };
 
-struct Executor;  // device-side state (executor.cu)
+struct Executor;   // device-side state (executor.cu)
+struct StemCache;  // device-resident stems shared by plan copies (executor.cu)
 
 struct PlanData {
   Network net;
@@ -103,6 +104,10 @@ struct PlanData {
 // starts without an executor and allocates its own on first use.
 struct Plan : PlanData {
   Executor* exec = nullptr;
+  // When set, the plan's stem (leaf store and phase-0 outputs, which depend
+  // on neither the bitstring nor the slice) comes from this cache and is
+  // shared with every other plan of the same circuit that uses it.
+  std::shared_ptr<StemCache> stems;
   Plan() = default;
   Plan(const Plan& o) : PlanData(o), exec(nullptr) {}
   Plan& operator=(const Plan&) = delete;
@@ -125,6 +130,16 @@ tn_status contract_amplitudes_ex(Plan& p, const uint64_t* bits, int64_t nb, doub
                                  tn_report* rep, bool clear_out, int flags);
 // Device bytes held by the plan's executor (0 before its first use).
 int64_t executor_bytes(const Plan& p);
+// Stem cache of one server: entries keyed by (device, plan hash), each the
+// leaf store and phase-0 outputs of a plan.  Entries no plan uses any more
+// are evicted least recently used first once the cache holds more than
+// cap_bytes.
+std::shared_ptr<StemCache> make_stem_cache(int64_t cap_bytes);
+// Whether the plan's last call found its phase-0 outputs already computed by
+// another plan sharing its stem.
+bool stem_reused(const Plan& p);
+struct StemCacheStats { int64_t entries, bytes, hits, misses; };
+StemCacheStats stem_cache_stats(StemCache& c);
 
 }  // namespace tn
 

@@ -245,3 +245,73 @@ def test_full_size_8x8_sampled_slices_vs_oracle():
         assert rel(got, ref) <= 1e-5, s
         got = p.contract_amplitudes(words, slice_begin=s, slice_count=1, precision="split_fp16")[0]
         assert rel(got, ref) <= 1e-4, s
+
+
+@pytest.fixture(scope="module")
+def subcase_5x6():
+    """The 30-qubit sub-case of the 6x6 workload: 5x6 grid, depth 1+16+1,
+    circuit seed 2, the last 6 qubits open (64 amplitudes), 10 sliced indices
+    (1024 slices), one bitstring of the seed-2 bitstring stream.  The FP64
+    oracle sums every slice of the plan's tree."""
+    T = tnlib()
+    rows, cols, depth, seed = 5, 6, 16, 2
+    n = rows * cols
+    open_q = tuple(range(n - 6, n))
+    p = _setup(T, rows, cols, depth, seed, open_q, num_sliced=10, search_trials=32, seed=1,
+               max_log2_intermediate=22)
+    assert p.info()["num_slices"] == 1024
+    words = I.bitstrings(n, 1, seed)
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    wires = p.sliced_wires()
+    bits = I.bits_of(words[0], n)
+    ref = np.zeros(64, dtype=np.complex128)
+    for s in range(1024):
+        fixed = {wires[j]: (s >> j) & 1 for j in range(len(wires))}
+        ref += replay(p, gates, n, bits, open_q, fixed)
+    return p, words, ref
+
+
+@pytest.mark.parametrize("mode", list(MODE_BOUND))
+def test_30_qubit_subcase_every_mode_vs_fp64_oracle(subcase_5x6, mode):
+    """All 1024 slices summed on the GPU, in each precision mode, against the
+    oracle's exact FP64 sum, within the mode's bound."""
+    p, words, ref = subcase_5x6
+    got, rep = p.contract_amplitudes(words, precision=mode, report=True)
+    assert rel(got[0], ref) <= MODE_BOUND[mode], (mode, rel(got[0], ref))
+    assert rep["discarded_units"] == 0
+
+
+@pytest.mark.parametrize("mode", list(MODE_BOUND))
+def test_xeb_within_one_percent_of_the_oracle(mode):
+    """Linear XEB of bitstrings drawn from the exact output distribution
+    (state vector, inverse CDF of seeded uniforms), scored once with the
+    oracle's probabilities and once with the GPU's: the two must agree within
+    1% of the oracle's value.  The Porter-Thomas moments of the GPU's
+    probabilities over the uniformly drawn bitstrings agree with the oracle's
+    the same way."""
+    from oracle import stats as ST
+    T = tnlib()
+    rows, cols, depth, seed = 4, 5, 14, 21
+    n = rows * cols
+    open_q = (16, 17, 18, 19)
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    psi = SV.simulate(gates, n)
+    p_all = np.abs(psi) ** 2
+    u = np.random.default_rng(seed).random(400)
+    idx = ST.sample_inverse_cdf(p_all, u)
+    sample_bits = [[(int(i) >> q) & 1 for q in range(n)] for i in idx]
+    words = np.stack([I.pack_bits(b) for b in sample_bits])
+    plan = _setup(T, rows, cols, depth, seed, open_q, num_sliced=4, search_trials=32, seed=3)
+    amps = plan.contract_amplitudes(words, precision=mode)
+    col = [sum(b[q] << t for t, q in enumerate(open_q)) for b in sample_bits]
+    p_gpu = np.abs(amps[np.arange(len(idx)), col]) ** 2
+    f_ref = ST.linear_xeb(p_all[idx], n)
+    f_gpu = ST.linear_xeb(p_gpu, n)
+    assert f_ref > 0.5
+    assert abs(f_gpu - f_ref) <= 0.01 * abs(f_ref), (mode, f_gpu, f_ref)
+    uni = I.bitstrings(n, 64, seed)
+    ref_u = SV.amplitudes(psi, n, [I.bits_of(w, n) for w in uni], open_q)
+    got_u = plan.contract_amplitudes(uni, precision=mode)
+    m_ref = ST.porter_thomas_moments(np.abs(ref_u.ravel()) ** 2, n)
+    m_gpu = ST.porter_thomas_moments(np.abs(got_u.ravel()) ** 2, n)
+    assert np.allclose(m_gpu, m_ref, rtol=1e-2), (mode, m_gpu, m_ref)

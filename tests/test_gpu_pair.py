@@ -111,3 +111,27 @@ def test_split_error_does_not_grow_with_k(nk):
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 2e-5
     bias = float(np.mean((np.abs(got) - np.abs(ref)) / np.abs(ref)))
     assert abs(bias) <= 1e-5
+
+
+PAIR_BOUND = {"split_fp16": 2e-5, "scaled_fp16": 2e-3, "scaled_bf16": 1.5e-2}
+
+
+@pytest.mark.parametrize("mode", list(PAIR_BOUND))
+@pytest.mark.parametrize("nm,nn,nk", [(7, 4, 3), (8, 7, 6), (9, 5, 11), (13, 9, 8)])
+def test_tensor_core_precisions_vs_fp64(mode, nm, nn, nk):
+    """The TMA tensor-core kernel in the precisions that scale operands by
+    their exact maxima: split fp16 (four planes, chunked accumulation) and one
+    16-bit product per real product (two planes, double-buffered persistent
+    CTAs for the last shape), against FP64 einsum.  Operands are scaled by
+    2^-40 so that unscaled fp16 would underflow."""
+    T = tnlib()
+    import torch
+    la, lb, lc, A, B, ref = _case(nm, nn, nk, seed=5 * nm + nk)
+    s = np.float32(2.0 ** -40)
+    dA = torch.from_numpy(A * s).cuda()
+    dB = torch.from_numpy(B * s).cuda()
+    dC = torch.empty(1 << len(lc), dtype=torch.complex64, device="cuda")
+    T.contract_pair(dA, la, dB, lb, dC, lc, precision=mode, algo="fused_tc")
+    torch.cuda.synchronize()
+    got = dC.cpu().numpy().astype(np.complex128) / (float(s) ** 2)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= PAIR_BOUND[mode], mode

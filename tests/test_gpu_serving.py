@@ -63,3 +63,46 @@ def test_over_cap_and_over_budget_requests_fail_loudly():
         assert e.value.status == 3          # TN_EHBM
     finally:
         srv.close()
+
+
+def test_stems_stay_resident_for_later_requests_of_a_circuit():
+    """The second and later requests for a circuit reuse its resident stem
+    (leaf tensors and phase-0 intermediates) instead of rebuilding it, also
+    while several of them are in flight at once; their amplitudes are
+    bit-identical to those of a server that builds the stem afresh, and match
+    the state vector."""
+    T = tnlib()
+    rows, cols, depth, seed, k = 4, 5, 12, 23, 3
+    n = rows * cols
+    reqs = [dict(rows=rows, cols=cols, depth=depth, seed=seed, num_open=k,
+                 bitstrings=I.bitstrings(n, 2, 100 + i)) for i in range(5)]
+    kw = dict(max_inflight=4, slices_per_quantum=2, precision="c64", plan_trials=8, max_log2_intermediate=12)
+    srv = T.Server(**kw)
+    try:
+        first, st0 = srv.wait(srv.submit(**reqs[0]))
+        assert st0["stem_reused"] == 0
+        tickets = [srv.submit(**r) for r in reqs[1:]]
+        shared = []
+        for t in tickets:
+            o, st = srv.wait(t)
+            assert st["stem_reused"] == 1 and st["planned_here"] == 0
+            shared.append(o)
+    finally:
+        srv.close()
+    fresh = []
+    for r in reqs[1:]:
+        srv = T.Server(**kw)
+        try:
+            o, st = srv.wait(srv.submit(**r))
+            assert st["stem_reused"] == 0
+            fresh.append(o)
+        finally:
+            srv.close()
+    for a, b in zip(shared, fresh):
+        assert np.array_equal(a, b)
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    psi = SV.simulate(gates, n)
+    open_q = tuple(range(n - k, n))
+    for r, o in zip(reqs, [first] + shared):
+        ref = SV.amplitudes(psi, n, [I.bits_of(w, n) for w in r["bitstrings"]], open_q)
+        assert np.linalg.norm(o - ref) <= 1e-5 * np.linalg.norm(ref)
