@@ -39,6 +39,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <cstdlib>
 #include <mutex>
 
 #include "kernels.h"
@@ -676,7 +677,7 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
 
 // Split precision, persistent, with chunked accumulation.  The tensor core
 // adds into its FP32 accumulator with truncation, so over a long K the error
-// grows linearly and is biased toward zero.  Here every chunk of CHUNK K
+// grows linearly and is biased toward zero.  Here every chunk of `chunk` K
 // stages starts a fresh accumulator, and the epilogue warps add the chunks
 // with round-to-nearest FP32 adds, so the bias scales with the chunk length,
 // not with K.
@@ -688,13 +689,23 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
 // After the last chunk the epilogue scales and stores R while the MMA warp
 // already runs the next tile's first chunk in the other buffer (the next
 // tile's R), so the MMA warp waits only for the folds, never for a store.
-constexpr int CHUNK = 16;
+// K stages per chunk (32 complex K each): 16 unless TN_SPLIT_CHUNK says
+// otherwise; the bias grows with the chunk length, so longer chunks trade
+// accuracy for fewer folds.
+int split_chunk() {
+  static const int c = [] {
+    const char* e = getenv("TN_SPLIT_CHUNK");
+    const int v = e ? atoi(e) : 16;
+    return v >= 1 && v <= 4096 ? v : 16;
+  }();
+  return c;
+}
 
 template <int TN, bool BF16>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_tma_chunked(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                      float2* __restrict__ C0, const GemmDesc d, int kp, int a_zlo, int a_zhi, int b_zlo, int b_zhi,
-                     int c_planes, const ScaleIO sio, int* __restrict__ err) {
+                     int c_planes, const ScaleIO sio, int chunk, int fold, int* __restrict__ err) {
   constexpr int NP = 4;
   using CF = Cfg2<TN, NP>;
   constexpr int NS = CF::NSTAGE;
@@ -711,11 +722,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ volatile int epi_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ntm = (int)((int64_t(1) << d.nm) / TM), ntn = (int)((int64_t(1) << d.nn) / TN);
+  // fold > 1: `fold` consecutive hi units share A, and their N = 2^nn columns
+  // side by side form the TN columns of one tile (so TN = fold * 2^nn)
+  const int nsub = 1 << d.nn;
+  const int ntm = (int)((int64_t(1) << d.nm) / TM), ntn = fold > 1 ? 1 : (int)((int64_t(1) << d.nn) / TN);
   const int tiles = ntm * ntn;
-  const int64_t items = (int64_t)tiles * d.units;
+  const int64_t items = (int64_t)tiles * (d.units / fold);
   const int nkt = kp / TKC;
-  const int nch = (nkt + CHUNK - 1) / CHUNK;
+  const int nch = (nkt + chunk - 1) / chunk;
   const int GM = d.group_m > 0 ? d.group_m : GROUP_M_DEFAULT;
   auto decode = [&](int64_t item, int& unit, int& m0, int& n0) {
     unit = (int)(item / tiles);
@@ -752,7 +766,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int64_t it = blockIdx.x; lane == 0 && it < items && !abort_flag; it += gridDim.x) {
       int unit, m0, n0;
       decode(it, unit, m0, n0);
-      const int ulo = unit % d.units_lo, uhi = unit / d.units_lo;
+      const int ulo = unit % d.units_lo, uhi = (unit / d.units_lo) * fold;
       const int za_lo = a_zlo ? ulo : 0, za_hi = a_zhi ? uhi : 0;
       const int zb_lo = b_zlo ? ulo : 0, zb_hi = b_zhi ? uhi : 0;
       for (int kt = 0; kt < nkt; ++kt, ++g) {
@@ -765,7 +779,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         uint8_t* st = smem + s * CF::STAGE;
         mbar_expect_tx(&full[s], CF::STAGE);
         tma_load_5d(st, &mapA, &full[s], kt * TKC, m0, 0, za_lo, za_hi);
-        tma_load_5d(st + A_STAGE, &mapB, &full[s], kt * TKC, n0, 0, zb_lo, zb_hi);
+        if (fold == 1) {
+          tma_load_5d(st + A_STAGE, &mapB, &full[s], kt * TKC, n0, 0, zb_lo, zb_hi);
+        } else {
+          // the B map's box is one plane of 2^nn rows: plane p of hi unit
+          // uhi + f goes to rows f * 2^nn.. of plane p in the stage
+          for (int f = 0; f < fold; ++f)
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+              tma_load_5d(st + A_STAGE + (p * TN + f * nsub) * 64, &mapB, &full[s], kt * TKC, 0, p, zb_lo, uhi + f);
+        }
       }
     }
     __syncwarp();
@@ -790,7 +813,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         ++used[b];
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dr = tmem + (uint32_t)b * BUF, di = dr + TN;
-        const int k0 = c * CHUNK, k1 = min(nkt, k0 + CHUNK);
+        const int k0 = c * chunk, k1 = min(nkt, k0 + chunk);
         for (int kt = k0; kt < k1; ++kt, ++g) {
           const int s = (int)(g % NS);
           if (!mbar_wait(&full[s], (uint32_t)((g / NS) & 1))) {
@@ -842,10 +865,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x, ++t) {
       int unit, m0, n0;
       decode(it, unit, m0, n0);
-      const int ulo = unit % d.units_lo, uhi = unit / d.units_lo;
-      for (int jj = tq; jj < TN; jj += 128) colC[jj] = bit_offset(n0 + jj, d.nn, d.cn);
+      const int ulo = unit % d.units_lo, uhi = (unit / d.units_lo) * fold;
+      for (int jj = tq; jj < TN; jj += 128) colC[jj] = bit_offset(fold > 1 ? (jj & (nsub - 1)) : n0 + jj, d.nn, d.cn);
       const int32_t ro = bit_offset(m0 + q * 32 + lane, d.nm, d.cm);
-      float2* C = C0 + (int64_t)ulo * d.c_lo + (int64_t)uhi * d.c_hi;
+      float2* Cu = C0 + (int64_t)ulo * d.c_lo + (int64_t)uhi * d.c_hi;
       int ea = 0, eb = 0, r = 0;
       bool weak = false;
       if (sio.ea) {
@@ -907,6 +930,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool bad = false;
 #pragma unroll 1
       for (int c0 = 0; c0 < TN; c0 += 16) {
+        // columns of a folded tile belong to hi unit uhi + c0 / 2^nn
+        float2* C = Cu + (fold > 1 ? (int64_t)(c0 >> d.nn) * d.c_hi : 0);
         uint32_t ur[16], ui[16];
         tmem_ld<16>(R + (uint32_t)c0, ur);
         tmem_ld<16>(R + (uint32_t)(TN + c0), ui);
@@ -995,15 +1020,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 5-D map over one operand's planes: [hi unit][lo unit][plane][row][k] of
-// 16-bit values; box = 32 k x box_rows x np planes x 1 x 1.
-bool encode_planes(CUtensorMap* map, const PlaneOperand& o, int box_rows) {
+// 16-bit values; box = 32 k x box_rows x box_planes x 1 x 1 (box_planes 0:
+// all np planes).
+bool encode_planes(CUtensorMap* map, const PlaneOperand& o, int box_rows, int box_planes = 0) {
   auto fn = encode_fn();
   if (!fn) return false;
   const int64_t set = (int64_t)o.np * o.rows * o.kp * 2;  // bytes of one plane set
   cuuint64_t dims[5] = {(cuuint64_t)o.kp, (cuuint64_t)o.rows, (cuuint64_t)o.np, (cuuint64_t)o.nlo, (cuuint64_t)o.nhi};
   cuuint64_t strides[4] = {(cuuint64_t)(o.kp * 2), (cuuint64_t)(o.rows * o.kp * 2),
                            (cuuint64_t)(o.nlo > 1 ? o.st_lo : set), (cuuint64_t)(o.nhi > 1 ? o.st_hi : set)};
-  cuuint32_t box[5] = {(cuuint32_t)TKC, (cuuint32_t)box_rows, (cuuint32_t)o.np, 1, 1};
+  cuuint32_t box[5] = {(cuuint32_t)TKC, (cuuint32_t)box_rows, (cuuint32_t)(box_planes > 0 ? box_planes : o.np), 1, 1};
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 5, const_cast<uint16_t*>(o.base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -1053,7 +1079,7 @@ cudaError_t launch_persistent(const CUtensorMap& ma, const CUtensorMap& mb, floa
 
 template <int TN, bool BF16>
 cudaError_t launch_chunked(const CUtensorMap& ma, const CUtensorMap& mb, float2* C, const GemmDesc& d, int kp,
-                           const int z[4], int c_planes, const ScaleIO& sio, int* err, cudaStream_t s) {
+                           const int z[4], int c_planes, const ScaleIO& sio, int fold, int* err, cudaStream_t s) {
   static bool attr = false;
   static int sms = 0;
   if (!attr) {
@@ -1067,25 +1093,25 @@ cudaError_t launch_chunked(const CUtensorMap& ma, const CUtensorMap& mb, float2*
     attr = true;
   }
   const int64_t M = int64_t(1) << d.nm, N = int64_t(1) << d.nn;
-  const int64_t items = (M / TM) * (N / TN) * d.units;
+  const int64_t items = (M / TM) * (fold > 1 ? 1 : N / TN) * (d.units / fold);
   const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
   gemm_tma_chunked<TN, BF16><<<grid, NTHREADS, Cfg2<TN, 4>::SMEM, s>>>(ma, mb, C, d, kp, z[0], z[1], z[2], z[3],
-                                                                       c_planes, sio, err);
+                                                                       c_planes, sio, split_chunk(), fold, err);
   return cudaGetLastError();
 }
 
 template <bool BF16, int NP>
 cudaError_t launch_tn(int TNv, bool persistent, const CUtensorMap& ma, const CUtensorMap& mb, float2* C,
-                      const GemmDesc& d, int kp, const int z[4], int cp, const ScaleIO& sio, int* err,
+                      const GemmDesc& d, int kp, const int z[4], int cp, const ScaleIO& sio, int fold, int* err,
                       cudaStream_t s) {
   if constexpr (NP == 4) {
     // split precision always runs the chunked persistent kernel (accuracy)
     (void)persistent;
     switch (TNv) {
-      case 128: return launch_chunked<128, BF16>(ma, mb, C, d, kp, z, cp, sio, err, s);
-      case 64: return launch_chunked<64, BF16>(ma, mb, C, d, kp, z, cp, sio, err, s);
-      case 32: return launch_chunked<32, BF16>(ma, mb, C, d, kp, z, cp, sio, err, s);
-      case 16: return launch_chunked<16, BF16>(ma, mb, C, d, kp, z, cp, sio, err, s);
+      case 128: return launch_chunked<128, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s);
+      case 64: return launch_chunked<64, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s);
+      case 32: return launch_chunked<32, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s);
+      case 16: return launch_chunked<16, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s);
       default: return cudaErrorInvalidValue;
     }
   } else {
@@ -1133,17 +1159,28 @@ cudaError_t launch_gemm_tma(const PlaneOperand& a, const PlaneOperand& b, float2
     const int64_t items = ((int64_t(1) << d.nm) / TM) * ((int64_t(1) << d.nn) / TNv) * d.units;
     persistent = items >= 2 * 148;
   }
+  // Narrow N with A shared by the hi units (e.g. one slice-only tensor against
+  // the bitstrings of a group): fold consecutive hi units into the columns of
+  // one tile, so that the MMAs run 128 columns wide and A is read once for
+  // all of them (split precision without scaling: one exponent per tile).
+  int fold = 1;
+  if (a.np == 4 && !sio.ea && d.nn < 7 && a.nhi == 1 && b.nhi > 1 && d.units_lo > 0) {
+    const int uh = d.units / d.units_lo;
+    while (fold * 2 <= (128 >> d.nn) && uh % (fold * 2) == 0) fold *= 2;
+    if (fold > 1) TNv = (1 << d.nn) * fold;
+  }
 
   CUtensorMap ma, mb;
-  if (!encode_planes(&ma, a, TM) || !encode_planes(&mb, b, TNv)) return cudaErrorInvalidValue;
+  if (!encode_planes(&ma, a, TM) || !encode_planes(&mb, b, fold > 1 ? (1 << d.nn) : TNv, fold > 1 ? 1 : 0))
+    return cudaErrorInvalidValue;
   const int kpi = (int)a.kp;
   const int z[4] = {a.nlo > 1, a.nhi > 1, b.nlo > 1, b.nhi > 1};
   const int cp = c_planes ? 1 : 0;
   if (a.np == 4)
-    return bf16 ? launch_tn<true, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, err, s)
-                : launch_tn<false, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, err, s);
-  return bf16 ? launch_tn<true, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, err, s)
-              : launch_tn<false, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, err, s);
+    return bf16 ? launch_tn<true, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, fold, err, s)
+                : launch_tn<false, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, fold, err, s);
+  return bf16 ? launch_tn<true, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, 1, err, s)
+              : launch_tn<false, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, 1, err, s);
 }
 
 }  // namespace tn

@@ -43,6 +43,41 @@ static cublasHandle_t cublas_handle(int dev) {
   return hs[dev];
 }
 
+// Device state of the tensor-core algorithms, one per device: the kernels'
+// error word and a grow-only buffer for the operand planes.  A call holds the
+// mutex until its kernel has finished, so calls on one device are serialised
+// and the buffer is never in use by two calls at once.
+struct PairDevState {
+  int* err = nullptr;
+  void* scratch = nullptr;
+  size_t bytes = 0;
+};
+static std::mutex g_pair_mu;
+static std::vector<PairDevState> g_pair_state;
+
+static tn_status pair_state(size_t need, PairDevState*& out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(TN_ECUDA, "tn_contract_pair: cudaGetDevice failed");
+  if ((int)g_pair_state.size() <= dev) g_pair_state.resize(dev + 1);
+  PairDevState& st = g_pair_state[dev];
+  if (!st.err) {
+    if (cudaMalloc(&st.err, sizeof(int)) != cudaSuccess) return fail(TN_ECUDA, "tn_contract_pair: error word");
+    if (cudaMemset(st.err, 0, sizeof(int)) != cudaSuccess) return fail(TN_ECUDA, "tn_contract_pair: error word");
+  }
+  if (need > st.bytes) {
+    cudaFree(st.scratch);  // the previous call on this device has finished
+    st.scratch = nullptr;
+    st.bytes = 0;
+    if (cudaMalloc(&st.scratch, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(TN_EHBM, "tn_contract_pair: operand planes do not fit");
+    }
+    st.bytes = need;
+  }
+  out = &st;
+  return TN_OK;
+}
+
 static tn_status unfused(const float2* A, const float2* B, float2* Cp, const GemmDesc& d, cudaStream_t st) {
   const int64_t M = int64_t(1) << d.nm, N = int64_t(1) << d.nn, K = int64_t(1) << d.nk;
   float2 *Ap = nullptr, *Bp = nullptr, *Cg = nullptr;
@@ -144,27 +179,22 @@ extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, in
       if (algo == TN_PAIR_GATHER_TC && precision != TN_PREC_SPLIT_BF16)
         return fail(TN_EINVAL, "tn_contract_pair: the gathering tensor-core kernel runs split bf16 only");
       if (!tc_shape_ok(d)) return fail(TN_EINVAL, "tn_contract_pair: tensor-core kernels need M >= 128, N >= 16, K >= 8");
-      static int* err = nullptr;
-      if (!err) {
-        if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return fail(TN_ECUDA, "tn_contract_pair: error word");
-        cudaMemset(err, 0, sizeof(int));
-      }
-      uint16_t* scratch = nullptr;
+      std::lock_guard<std::mutex> lock(g_pair_mu);
+      // operand planes, then 32 bytes for the scaled modes' maxima and exponents
+      const size_t planes = algo == TN_PAIR_FUSED_TC ? (size_t)tc2_scratch_elems(d) * sizeof(uint16_t) : 0;
+      PairDevState* ps = nullptr;
+      tn_status pst = pair_state(planes + 32, ps);
+      if (pst != TN_OK) return pst;
+      int* err = ps->err;
       if (algo == TN_PAIR_FUSED_TC) {
-        // operand planes, then 32 bytes for the scaled modes' maxima and exponents
-        const size_t planes = (size_t)tc2_scratch_elems(d) * sizeof(uint16_t);
-        if (cudaMallocAsync(&scratch, planes + 32, s) != cudaSuccess) {
-          cudaGetLastError();
-          return fail(TN_EHBM, "tn_contract_pair: operand planes do not fit");
-        }
-        void* aux = reinterpret_cast<char*>(scratch) + planes;
+        uint16_t* scratch = static_cast<uint16_t*>(ps->scratch);
+        void* aux = static_cast<char*>(ps->scratch) + planes;
         switch (precision) {
           case TN_PREC_SPLIT_BF16: e = run_gemm_tc2(a, b, c, d, true, scratch, err, s); break;
           case TN_PREC_SPLIT_FP16: e = run_gemm_tc2_scaled(a, b, c, d, false, 4, scratch, aux, err, s); break;
           case TN_PREC_SCALED_FP16: e = run_gemm_tc2_scaled(a, b, c, d, false, 2, scratch, aux, err, s); break;
           default: e = run_gemm_tc2_scaled(a, b, c, d, true, 2, scratch, aux, err, s); break;
         }
-        cudaFreeAsync(scratch, s);
       } else {
         e = launch_gemm_tc(a, b, c, d, true, 1.f, 1.f, err, s);
       }

@@ -137,6 +137,31 @@ def test_full_size_6x6_sampled_slices_vs_oracle():
             assert rel(got, ref) <= MODE_BOUND[mode], (s, mode, rel(got, ref))
 
 
+def test_full_size_6x6_bitstring_batch_vs_oracle():
+    """The 6x6 benchmark plan on one slice for all four bitstrings of the batch
+    at once: the bitstring-dependent steps run with the batch in the launch
+    grid, and narrow tensor-core steps whose slice-only operand is shared by
+    the bitstrings fold the bitstrings into the columns of one tile.  Every
+    bitstring against the oracle, and the batch equal to the bitstrings one at
+    a time."""
+    T = tnlib()
+    rows, cols, depth, seed = 6, 6, 16, 2
+    n = 36
+    open_q = tuple(range(30, 36))
+    p = _setup(T, rows, cols, depth, seed, open_q, num_sliced=10, search_trials=64, seed=1)
+    wires = p.sliced_wires()
+    words = I.bitstrings(n, 4, seed)
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    s = 5
+    fixed = {wires[j]: (s >> j) & 1 for j in range(len(wires))}
+    got = p.contract_amplitudes(words, slice_begin=s, slice_count=1, precision="split_bf16")
+    for b in range(4):
+        ref = replay(p, gates, n, I.bits_of(words[b], n), open_q, fixed)
+        assert rel(got[b], ref) <= 1e-4, b
+        one = p.contract_amplitudes(words[b:b + 1], slice_begin=s, slice_count=1, precision="split_bf16")[0]
+        assert rel(got[b], one) <= 1e-6, b
+
+
 def test_split_bf16_path_vs_statevector():
     """A plan whose dense steps run on the tcgen05 kernel (bf16 hi+lo):
     relative L2 <= 1e-4 against the state vector."""
