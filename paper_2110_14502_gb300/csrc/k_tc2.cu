@@ -174,6 +174,72 @@ struct Pow2 {
   __device__ float operator()(float x) const { return direct ? x * f : ldexpf(x, e); }
 };
 
+// Number of leading tile column bits that are C's fastest indices in order
+// (strides 1, 2, 4, ..): runs of 2^vb tile columns are contiguous in C.
+__device__ __forceinline__ int vec_bits(const GemmDesc& d) {
+  int v = 0;
+  while (v < 4 && v < d.nn && d.cn[v] == (1 << v)) ++v;
+  return v;
+}
+
+// One thread's 16 consecutive tile columns of one row as NP 16-bit planes:
+// each contiguous run of 2^vb columns goes out as one store per plane (the
+// run starts at a multiple of 2^vb elements: every other index of C has a
+// larger stride).
+template <int NP>
+__device__ __forceinline__ void store_planes(uint16_t* P, int64_t plane, int64_t ro, const int32_t* col, int vb,
+                                             const uint16_t (&h)[NP][16]) {
+  auto pk = [&](int p, int j) { return (uint32_t)h[p][j] | ((uint32_t)h[p][j + 1] << 16); };
+  if (vb >= 3) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int64_t o = ro + col[8 * r];
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        *reinterpret_cast<uint4*>(P + p * plane + o) =
+            make_uint4(pk(p, 8 * r), pk(p, 8 * r + 2), pk(p, 8 * r + 4), pk(p, 8 * r + 6));
+    }
+  } else if (vb == 2) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int64_t o = ro + col[4 * r];
+#pragma unroll
+      for (int p = 0; p < NP; ++p) *reinterpret_cast<uint2*>(P + p * plane + o) = make_uint2(pk(p, 4 * r), pk(p, 4 * r + 2));
+    }
+  } else if (vb == 1) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int64_t o = ro + col[2 * r];
+#pragma unroll
+      for (int p = 0; p < NP; ++p) *reinterpret_cast<uint32_t*>(P + p * plane + o) = pk(p, 2 * r);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int64_t o = ro + col[j];
+#pragma unroll
+      for (int p = 0; p < NP; ++p) P[p * plane + o] = h[p][j];
+    }
+  }
+}
+
+// The same for complex64 output (two complex values per 16-byte store).
+__device__ __forceinline__ void store_c64(float2* C, int64_t ro, const int32_t* col, int vb, const float* vr,
+                                          const float* vi) {
+  if (vb >= 1) {
+    const int run = vb >= 4 ? 16 : (1 << vb);
+#pragma unroll
+    for (int j = 0; j < 16; j += 2) {
+      // pairs (j, j + 1) are contiguous; a new run starts every `run` columns
+      float4* q = reinterpret_cast<float4*>(C + ro + col[j & ~(run - 1)]) + ((j & (run - 1)) >> 1);
+      *q = make_float4(vr[j], vi[j], vr[j + 1], vi[j + 1]);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) C[ro + col[j]] = make_float2(vr[j], vi[j]);
+  }
+}
+
 template <int NREG>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t* v);
 template <>
@@ -331,7 +397,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int32_t ro = rowC[r_];
       // the tile's first four column bits are C's four fastest indices: each
       // thread's 16 columns form one contiguous run (16-element aligned)
-      const bool n16 = d.nn >= 4 && d.cn[0] == 1 && d.cn[1] == 2 && d.cn[2] == 4 && d.cn[3] == 8;
+      const int vb = vec_bits(d);
       // plane output: stored = acc 2^-r; complex64 output: true value = acc 2^(eA+eB)
       const Pow2 sc(c_planes ? -r : ea + eb);
       float vmax = 0.f;
@@ -350,7 +416,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           vr[j] = sc(xr);
           vi[j] = sc(xi);
         }
-        if (ro < 0) continue;
+        // M and N are multiples of the tile and of 16: a chunk is all in or all out
+        if (ro < 0 || colC[c0] < 0) continue;
         if (c_planes) {
           // output consumed by another tensor-core step: write its NP 16-bit
           // planes at the same offsets
@@ -359,43 +426,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           uint16_t h[NP][16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            if (colC[c0 + j] >= 0) {
-              vmax = fmaxf(vmax, fmaxf(fabsf(vr[j]), fabsf(vi[j])));
-              bad |= !isfinite(vr[j]) || !isfinite(vi[j]);
-            }
+            vmax = fmaxf(vmax, fmaxf(fabsf(vr[j]), fabsf(vi[j])));
+            bad |= !isfinite(vr[j]) || !isfinite(vi[j]);
             h[0][j] = to16<BF16>(vr[j]);
             h[1][j] = to16<BF16>(vi[j]);
           }
-          if (n16 && colC[c0] >= 0) {
-            const int64_t o = (int64_t)ro + colC[c0];
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-              uint4* qd = reinterpret_cast<uint4*>(P + p * plane + o);
-              qd[0] = make_uint4(h[p][0] | (h[p][1] << 16), h[p][2] | (h[p][3] << 16), h[p][4] | (h[p][5] << 16),
-                                 h[p][6] | (h[p][7] << 16));
-              qd[1] = make_uint4(h[p][8] | (h[p][9] << 16), h[p][10] | (h[p][11] << 16),
-                                 h[p][12] | (h[p][13] << 16), h[p][14] | (h[p][15] << 16));
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int32_t co = colC[c0 + j];
-              if (co < 0) continue;
-              const int64_t o = (int64_t)ro + co;
-#pragma unroll
-              for (int p = 0; p < NP; ++p) P[p * plane + o] = h[p][j];
-            }
-          }
-        } else if (n16 && colC[c0] >= 0) {
-          float4* qd = reinterpret_cast<float4*>(C + (int64_t)ro + colC[c0]);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) qd[j] = make_float4(vr[2 * j], vi[2 * j], vr[2 * j + 1], vi[2 * j + 1]);
+          store_planes<NP>(P, plane, ro, &colC[c0], vb, h);
         } else {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int32_t co = colC[c0 + j];
-            if (co >= 0) C[(int64_t)ro + co] = make_float2(vr[j], vi[j]);
-          }
+          store_c64(C, ro, &colC[c0], vb, vr, vi);
         }
       }
       if (sio.mc || sio.flag) {
@@ -587,7 +625,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           r = x - 15;
         }
       }
-      const bool n16 = d.nn >= 4 && d.cn[0] == 1 && d.cn[1] == 2 && d.cn[2] == 4 && d.cn[3] == 8;
+      const int vb = vec_bits(d);
       const Pow2 sc(c_planes ? -r : ea + eb);
       float vmax = 0.f;
       bool bad = false;
@@ -616,32 +654,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             h[0][jj] = to16<BF16>(vr[jj]);
             h[1][jj] = to16<BF16>(vi[jj]);
           }
-          if (n16) {
-            const int64_t o = (int64_t)ro + colC[b][c0];
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-              uint4* qd = reinterpret_cast<uint4*>(P + p * plane + o);
-              qd[0] = make_uint4(h[p][0] | (h[p][1] << 16), h[p][2] | (h[p][3] << 16), h[p][4] | (h[p][5] << 16),
-                                 h[p][6] | (h[p][7] << 16));
-              qd[1] = make_uint4(h[p][8] | (h[p][9] << 16), h[p][10] | (h[p][11] << 16),
-                                 h[p][12] | (h[p][13] << 16), h[p][14] | (h[p][15] << 16));
-            }
-          } else {
-#pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              const int64_t o = (int64_t)ro + colC[b][c0 + jj];
-#pragma unroll
-              for (int p = 0; p < NP; ++p) P[p * plane + o] = h[p][jj];
-            }
-          }
-        } else if (n16) {
-          float4* qd = reinterpret_cast<float4*>(C + (int64_t)ro + colC[b][c0]);
-#pragma unroll
-          for (int jj = 0; jj < 8; ++jj)
-            qd[jj] = make_float4(vr[2 * jj], vi[2 * jj], vr[2 * jj + 1], vi[2 * jj + 1]);
+          store_planes<NP>(P, plane, ro, &colC[b][c0], vb, h);
         } else {
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) C[(int64_t)ro + colC[b][c0 + jj]] = make_float2(vr[jj], vi[jj]);
+          store_c64(C, ro, &colC[b][c0], vb, vr, vi);
         }
       }
       // buffer b may be refilled once every epilogue thread has read it
@@ -885,7 +900,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           r = x - 15;
         }
       }
-      const bool n16 = d.nn >= 4 && d.cn[0] == 1 && d.cn[1] == 2 && d.cn[2] == 4 && d.cn[3] == 8;
+      const int vb = vec_bits(d);
       const Pow2 sc(c_planes ? -r : ea + eb);
       const int rb = (int)(t & 1);
       const uint32_t R = tmem + lane_off + (uint32_t)rb * BUF, P = tmem + lane_off + (uint32_t)(1 - rb) * BUF;
@@ -953,32 +968,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             split16<BF16>(vr[jj], h[0][jj], h[1][jj]);
             split16<BF16>(vi[jj], h[2][jj], h[3][jj]);
           }
-          if (n16) {
-            const int64_t o = (int64_t)ro + colC[c0];
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-              uint4* qd = reinterpret_cast<uint4*>(Pl + p * plane + o);
-              qd[0] = make_uint4(h[p][0] | (h[p][1] << 16), h[p][2] | (h[p][3] << 16),
-                                 h[p][4] | (h[p][5] << 16), h[p][6] | (h[p][7] << 16));
-              qd[1] = make_uint4(h[p][8] | (h[p][9] << 16), h[p][10] | (h[p][11] << 16),
-                                 h[p][12] | (h[p][13] << 16), h[p][14] | (h[p][15] << 16));
-            }
-          } else {
-#pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              const int64_t o = (int64_t)ro + colC[c0 + jj];
-#pragma unroll
-              for (int p = 0; p < NP; ++p) Pl[p * plane + o] = h[p][jj];
-            }
-          }
-        } else if (n16) {
-          float4* qd = reinterpret_cast<float4*>(C + (int64_t)ro + colC[c0]);
-#pragma unroll
-          for (int jj = 0; jj < 8; ++jj)
-            qd[jj] = make_float4(vr[2 * jj], vi[2 * jj], vr[2 * jj + 1], vi[2 * jj + 1]);
+          store_planes<NP>(Pl, plane, ro, &colC[c0], vb, h);
         } else {
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) C[(int64_t)ro + colC[c0 + jj]] = make_float2(vr[jj], vi[jj]);
+          store_c64(C, ro, &colC[c0], vb, vr, vi);
         }
       }
       // R read out: the MMA warp may start a later tile's chunks in it
