@@ -100,6 +100,28 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// Same, written to the same shared-memory offset of every CTA in `mask` of
+// the cluster, each of which gets the complete_tx on its own barrier.
+__device__ __forceinline__ void tma_load_5d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                               int c2, int c3, int c4, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
+      "%3, %4, %5, %6}], [%7], %8;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// Every thread of every CTA of the cluster (release / acquire).
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // K-major, 64-byte swizzled operand: stride byte offset 512 (8 rows x 64 B),
 // descriptor version 1 (bits 46-47), swizzle mode 4 = 64 B (bits 61-63).
 __device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
@@ -129,6 +151,15 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
 
 __device__ __forceinline__ void commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// Arrive on the barrier at this offset in every CTA of `mask` once the MMAs
+// issued so far have completed.
+__device__ __forceinline__ void commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                   smem_u32(bar)),
+               "h"(mask)
                : "memory");
 }
 
@@ -716,7 +747,7 @@ int split_chunk() {
   return c;
 }
 
-template <int TN, bool BF16>
+template <int TN, bool BF16, int CL>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_tma_chunked(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                      float2* __restrict__ C0, const GemmDesc d, int kp, int a_zlo, int a_zhi, int b_zlo, int b_zhi,
@@ -737,10 +768,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ volatile int epi_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // CL = 2: a cluster of two CTAs takes the tiles (2 p, n) and (2 p + 1, n)
+  // of an item; they share the B tile, and each loads half of it into both
+  // (TMA multicast), so every stage needs both CTAs' MMAs done before reuse
+  const int rank = CL > 1 ? (int)cluster_ctarank() : 0;
+  const int64_t first = blockIdx.x / CL, stride = gridDim.x / CL;
   // fold > 1: `fold` consecutive hi units share A, and their N = 2^nn columns
   // side by side form the TN columns of one tile (so TN = fold * 2^nn)
   const int nsub = 1 << d.nn;
-  const int ntm = (int)((int64_t(1) << d.nm) / TM), ntn = fold > 1 ? 1 : (int)((int64_t(1) << d.nn) / TN);
+  const int ntm = (int)((int64_t(1) << d.nm) / (TM * CL)), ntn = fold > 1 ? 1 : (int)((int64_t(1) << d.nn) / TN);
   const int tiles = ntm * ntn;
   const int64_t items = (int64_t)tiles * (d.units / fold);
   const int nkt = kp / TKC;
@@ -752,12 +788,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int per_group = GM * ntn;
     const int g = t / per_group, r = t % per_group;
     const int gm = min(GM, ntm - g * GM);
-    m0 = (g * GM + r % gm) * TM;
+    m0 = ((g * GM + r % gm) * CL + rank) * TM;
     n0 = (r / gm) * TN;
   };
 
   if (tid == 0) {
-    for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], CL); }
     for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 128); }
     abort_flag = 0;
     epi_fail = 0;
@@ -772,13 +808,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (CL > 1) cluster_sync();  // the peer's barriers exist before any multicast reaches them
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
   if (warp == 0) {
     // ---- TMA producer: the stage ring runs on across items
     int64_t g = 0;
-    for (int64_t it = blockIdx.x; lane == 0 && it < items && !abort_flag; it += gridDim.x) {
+    for (int64_t it = first; lane == 0 && it < items && !abort_flag; it += stride) {
       int unit, m0, n0;
       decode(it, unit, m0, n0);
       const int ulo = unit % d.units_lo, uhi = (unit / d.units_lo) * fold;
@@ -794,7 +831,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         uint8_t* st = smem + s * CF::STAGE;
         mbar_expect_tx(&full[s], CF::STAGE);
         tma_load_5d(st, &mapA, &full[s], kt * TKC, m0, 0, za_lo, za_hi);
-        if (fold == 1) {
+        if (CL > 1) {
+          // this CTA's half of the B rows, one plane per box, into both CTAs
+          if (fold == 1) {
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+              tma_load_5d_mc(st + A_STAGE + (p * TN + rank * (TN / 2)) * 64, &mapB, &full[s], kt * TKC,
+                             n0 + rank * (TN / 2), p, zb_lo, zb_hi, (uint16_t)3);
+          } else {
+            for (int f = rank * (fold / 2); f < (rank + 1) * (fold / 2); ++f)
+#pragma unroll
+              for (int p = 0; p < NP; ++p)
+                tma_load_5d_mc(st + A_STAGE + (p * TN + f * nsub) * 64, &mapB, &full[s], kt * TKC, 0, p, zb_lo,
+                               uhi + f, (uint16_t)3);
+          }
+        } else if (fold == 1) {
           tma_load_5d(st + A_STAGE, &mapB, &full[s], kt * TKC, n0, 0, zb_lo, zb_hi);
         } else {
           // the B map's box is one plane of 2^nn rows: plane p of hi unit
@@ -803,6 +854,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
             for (int p = 0; p < NP; ++p)
               tma_load_5d(st + A_STAGE + (p * TN + f * nsub) * 64, &mapB, &full[s], kt * TKC, 0, p, zb_lo, uhi + f);
+        }
+      }
+    }
+    // CL > 1: before this CTA may leave, both CTAs' MMA commits for the last
+    // stages it filled have arrived on its empty barriers
+    if (CL > 1 && lane == 0 && !abort_flag) {
+      for (int64_t q = g > NS ? g - NS : 0; q < g; ++q) {
+        if (!mbar_wait(&empty[q % NS], (uint32_t)((q / NS) & 1))) {
+          atomicExch(err, 35);
+          break;
         }
       }
     }
@@ -815,7 +876,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int64_t g = 0, t = 0;
     uint32_t used[2] = {0u, 0u};
     bool ok = true;
-    for (int64_t it = blockIdx.x; lane == 0 && ok && it < items && !abort_flag; it += gridDim.x, ++t) {
+    for (int64_t it = first; lane == 0 && ok && it < items && !abort_flag; it += stride, ++t) {
       const int rb = (int)(t & 1);
       for (int c = 0; c < nch && ok; ++c) {
         const int b = c == 0 ? rb : 1 - rb;
@@ -864,7 +925,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mma(di, A_[2], B_[1], I, 1u);
             mma(di, A_[3], B_[0], I, 1u);
           }
-          commit(&empty[s]);
+          if (CL > 1) commit_mc(&empty[s], (uint16_t)3);  // both CTAs wrote into this stage
+          else commit(&empty[s]);
         }
         commit(&acc_full[b]);  // also after an abort, so the epilogue's wait ends
       }
@@ -877,7 +939,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     int64_t t = 0;
     uint32_t seen[2] = {0u, 0u};
-    for (int64_t it = blockIdx.x; it < items; it += gridDim.x, ++t) {
+    for (int64_t it = first; it < items; it += stride, ++t) {
       int unit, m0, n0;
       decode(it, unit, m0, n0);
       const int ulo = unit % d.units_lo, uhi = (unit / d.units_lo) * fold;
@@ -995,6 +1057,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS));
   }
+  // no CTA leaves while its peer may still write into its shared memory or
+  // arrive on its barriers
+  if (CL > 1) cluster_sync();
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -1071,12 +1136,16 @@ cudaError_t launch_persistent(const CUtensorMap& ma, const CUtensorMap& mb, floa
 
 template <int TN, bool BF16>
 cudaError_t launch_chunked(const CUtensorMap& ma, const CUtensorMap& mb, float2* C, const GemmDesc& d, int kp,
-                           const int z[4], int c_planes, const ScaleIO& sio, int fold, int* err, cudaStream_t s) {
+                           const int z[4], int c_planes, const ScaleIO& sio, int fold, int cl, int* err,
+                           cudaStream_t s) {
   static bool attr = false;
   static int sms = 0;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tma_chunked<TN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(gemm_tma_chunked<TN, BF16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Cfg2<TN, 4>::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gemm_tma_chunked<TN, BF16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               Cfg2<TN, 4>::SMEM);
     if (e != cudaSuccess) return e;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1085,25 +1154,53 @@ cudaError_t launch_chunked(const CUtensorMap& ma, const CUtensorMap& mb, float2*
     attr = true;
   }
   const int64_t M = int64_t(1) << d.nm, N = int64_t(1) << d.nn;
-  const int64_t items = (M / TM) * (fold > 1 ? 1 : N / TN) * (d.units / fold);
-  const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
-  gemm_tma_chunked<TN, BF16><<<grid, NTHREADS, Cfg2<TN, 4>::SMEM, s>>>(ma, mb, C, d, kp, z[0], z[1], z[2], z[3],
-                                                                       c_planes, sio, split_chunk(), fold, err);
-  return cudaGetLastError();
+  const int64_t items = (M / (TM * cl)) * (fold > 1 ? 1 : N / TN) * (d.units / fold);
+  const int chunk = split_chunk();
+  if (cl == 1) {
+    const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
+    gemm_tma_chunked<TN, BF16, 1><<<grid, NTHREADS, Cfg2<TN, 4>::SMEM, s>>>(
+        ma, mb, C, d, kp, z[0], z[1], z[2], z[3], c_planes, sio, chunk, fold, err);
+    return cudaGetLastError();
+  }
+  // clusters of two CTAs, one cluster per item at most, all SMs covered
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(items, sms / 2)), 1, 1);
+  cfg.blockDim = dim3(NTHREADS, 1, 1);
+  cfg.dynamicSmemBytes = Cfg2<TN, 4>::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, gemm_tma_chunked<TN, BF16, 2>, ma, mb, C, d, kp, z[0], z[1], z[2], z[3], c_planes,
+                            sio, chunk, fold, err);
+}
+
+// Two-CTA clusters for the split kernel (B tile shared through TMA multicast):
+// on unless TN_TMA_CLUSTER=0.
+bool use_clusters() {
+  static const bool on = [] {
+    const char* e = getenv("TN_TMA_CLUSTER");
+    return !(e && e[0] == '0');
+  }();
+  return on;
 }
 
 template <bool BF16, int NP>
 cudaError_t launch_tn(int TNv, bool persistent, const CUtensorMap& ma, const CUtensorMap& mb, float2* C,
-                      const GemmDesc& d, int kp, const int z[4], int cp, const ScaleIO& sio, int fold, int* err,
-                      cudaStream_t s) {
+                      const GemmDesc& d, int kp, const int z[4], int cp, const ScaleIO& sio, int fold, int cl,
+                      int* err, cudaStream_t s) {
   if constexpr (NP == 4) {
     // split precision always runs the chunked persistent kernel (accuracy)
     (void)persistent;
     switch (TNv) {
-      case 128: return launch_chunked<128, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s);
-      case 64: return launch_chunked<64, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s);
-      case 32: return launch_chunked<32, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s);
-      case 16: return launch_chunked<16, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s);
+      case 128: return launch_chunked<128, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, cl, err, s);
+      case 64: return launch_chunked<64, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, cl, err, s);
+      case 32: return launch_chunked<32, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, cl, err, s);
+      case 16: return launch_chunked<16, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, cl, err, s);
       default: return cudaErrorInvalidValue;
     }
   } else {
@@ -1162,17 +1259,21 @@ cudaError_t launch_gemm_tma(const PlaneOperand& a, const PlaneOperand& b, float2
     if (fold > 1) TNv = (1 << d.nn) * fold;
   }
 
+  // split precision: pairs of CTAs on vertically adjacent tiles share the B
+  // tile (each loads half of it, one plane per box, into both)
+  const int cl = a.np == 4 && use_clusters() && d.nm >= 8 && TNv >= 32 ? 2 : 1;
+  const int b_rows = fold > 1 ? (1 << d.nn) : (cl == 2 ? TNv / 2 : TNv);
   CUtensorMap ma, mb;
-  if (!encode_planes(&ma, a, TM) || !encode_planes(&mb, b, fold > 1 ? (1 << d.nn) : TNv, fold > 1 ? 1 : 0))
+  if (!encode_planes(&ma, a, TM) || !encode_planes(&mb, b, b_rows, fold > 1 || cl == 2 ? 1 : 0))
     return cudaErrorInvalidValue;
   const int kpi = (int)a.kp;
   const int z[4] = {a.nlo > 1, a.nhi > 1, b.nlo > 1, b.nhi > 1};
   const int cp = c_planes ? 1 : 0;
   if (a.np == 4)
-    return bf16 ? launch_tn<true, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, fold, err, s)
-                : launch_tn<false, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, fold, err, s);
-  return bf16 ? launch_tn<true, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, 1, err, s)
-              : launch_tn<false, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, 1, err, s);
+    return bf16 ? launch_tn<true, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, fold, cl, err, s)
+                : launch_tn<false, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, fold, cl, err, s);
+  return bf16 ? launch_tn<true, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, 1, 1, err, s)
+              : launch_tn<false, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, 1, 1, err, s);
 }
 
 }  // namespace tn
