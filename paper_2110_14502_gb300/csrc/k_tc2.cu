@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // Persistent variant: one CTA per SM walks the (unit, tile) work items; the
 // K-stage ring runs on across items, and two TMEM accumulator buffers let the
 // epilogue warps drain item j while the MMA warp already accumulates item j+1.
-template <int TN, bool BF16, int NP>
+template <int TN, bool BF16, int NP, int CL>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_tma_persistent(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                         float2* __restrict__ C0, const GemmDesc d, int kp, int a_zlo, int a_zhi, int b_zlo,
@@ -511,7 +511,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ volatile int epi_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ntm = (int)((int64_t(1) << d.nm) / TM), ntn = (int)((int64_t(1) << d.nn) / TN);
+  // CL = 2: two CTAs take the vertically adjacent tiles of an item and share
+  // its B tile (each loads half of it into both, TMA multicast)
+  const int rank = CL > 1 ? (int)cluster_ctarank() : 0;
+  const int64_t first = blockIdx.x / CL, stride = gridDim.x / CL;
+  const int ntm = (int)((int64_t(1) << d.nm) / (TM * CL)), ntn = (int)((int64_t(1) << d.nn) / TN);
   const int tiles = ntm * ntn;
   const int64_t items = (int64_t)tiles * d.units;
   const int nkt = kp / TKC;
@@ -522,12 +526,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int per_group = GM * ntn;
     const int g = t / per_group, r = t % per_group;
     const int gm = min(GM, ntm - g * GM);
-    m0 = (g * GM + r % gm) * TM;
+    m0 = ((g * GM + r % gm) * CL + rank) * TM;
     n0 = (r / gm) * TN;
   };
 
   if (tid == 0) {
-    for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], CL); }
     for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 128); }
     abort_flag = 0;
     epi_fail = 0;
@@ -542,13 +546,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (CL > 1) cluster_sync();  // the peer's barriers exist before any multicast reaches them
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
   if (warp == 0) {
     // ---- TMA producer: the stage ring continues across items
     int64_t g = 0;
-    for (int64_t it = blockIdx.x; lane == 0 && it < items && !abort_flag; it += gridDim.x) {
+    for (int64_t it = first; lane == 0 && it < items && !abort_flag; it += stride) {
       int unit, m0, n0;
       decode(it, unit, m0, n0);
       const int ulo = unit % d.units_lo, uhi = unit / d.units_lo;
@@ -564,7 +569,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         uint8_t* st = smem + s * CF::STAGE;
         mbar_expect_tx(&full[s], CF::STAGE);
         tma_load_5d(st, &mapA, &full[s], kt * TKC, m0, 0, za_lo, za_hi);
-        tma_load_5d(st + A_STAGE, &mapB, &full[s], kt * TKC, n0, 0, zb_lo, zb_hi);
+        if (CL > 1) {
+#pragma unroll
+          for (int p = 0; p < NP; ++p)
+            tma_load_5d_mc(st + A_STAGE + (p * TN + rank * (TN / 2)) * 64, &mapB, &full[s], kt * TKC,
+                           n0 + rank * (TN / 2), p, zb_lo, zb_hi, (uint16_t)3);
+        } else {
+          tma_load_5d(st + A_STAGE, &mapB, &full[s], kt * TKC, n0, 0, zb_lo, zb_hi);
+        }
+      }
+    }
+    // CL > 1: before this CTA may leave, both CTAs' MMA commits for the last
+    // stages it filled have arrived on its empty barriers
+    if (CL > 1 && lane == 0 && !abort_flag) {
+      for (int64_t q = g > NS ? g - NS : 0; q < g; ++q) {
+        if (!mbar_wait(&empty[q % NS], (uint32_t)((q / NS) & 1))) {
+          atomicExch(err, 25);
+          break;
+        }
       }
     }
     __syncwarp();
@@ -572,7 +594,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ---- MMA issuer: item j accumulates into TMEM buffer j & 1
     constexpr uint32_t I = idesc2(BF16, TM, TN, false), IN = idesc2(BF16, TM, TN, true);
     int64_t g = 0, j = 0;
-    for (int64_t it = blockIdx.x; lane == 0 && it < items && !abort_flag; it += gridDim.x, ++j) {
+    for (int64_t it = first; lane == 0 && it < items && !abort_flag; it += stride, ++j) {
       const int b = (int)(j & 1);
       if (j >= 2 && !mbar_wait(&acc_empty[b], (uint32_t)(((j / 2) - 1) & 1))) {
         atomicExch(err, 22);
@@ -608,7 +630,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           mma(di, A_[0], B_[1], I, acc);
           mma(di, A_[1], B_[0], I, 1u);
         }
-        commit(&empty[s]);
+        if (CL > 1) commit_mc(&empty[s], (uint16_t)3);  // both CTAs wrote into this stage
+        else commit(&empty[s]);
       }
       commit(&acc_full[b]);  // also on an aborted item, so the epilogue's wait ends
       if (!ok) break;
@@ -619,7 +642,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int q = warp & 3;
     const int t = tid - 128;
     int64_t j = 0;
-    for (int64_t it = blockIdx.x; it < items; it += gridDim.x, ++j) {
+    for (int64_t it = first; it < items; it += stride, ++j) {
       const int b = (int)(j & 1);
       int unit, m0, n0;
       decode(it, unit, m0, n0);
@@ -710,6 +733,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS));
   }
+  // no CTA leaves while its peer may still write into its shared memory or
+  // arrive on its barriers
+  if (CL > 1) cluster_sync();
 }
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
@@ -1113,12 +1139,15 @@ cudaError_t launch_cfg(const CUtensorMap& ma, const CUtensorMap& mb, float2* C, 
 
 template <int TN, bool BF16, int NP>
 cudaError_t launch_persistent(const CUtensorMap& ma, const CUtensorMap& mb, float2* C, const GemmDesc& d, int kp,
-                              const int z[4], int c_planes, const ScaleIO& sio, int* err, cudaStream_t s) {
+                              const int z[4], int c_planes, const ScaleIO& sio, int cl, int* err, cudaStream_t s) {
   static bool attr = false;
   static int sms = 0;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tma_persistent<TN, BF16, NP>,
+    cudaError_t e = cudaFuncSetAttribute(gemm_tma_persistent<TN, BF16, NP, 1>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg2<TN, NP>::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gemm_tma_persistent<TN, BF16, NP, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               Cfg2<TN, NP>::SMEM);
     if (e != cudaSuccess) return e;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1127,11 +1156,27 @@ cudaError_t launch_persistent(const CUtensorMap& ma, const CUtensorMap& mb, floa
     attr = true;
   }
   const int64_t M = int64_t(1) << d.nm, N = int64_t(1) << d.nn;
-  const int64_t items = (M / TM) * (N / TN) * d.units;
-  const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
-  gemm_tma_persistent<TN, BF16, NP><<<grid, NTHREADS, Cfg2<TN, NP>::SMEM, s>>>(ma, mb, C, d, kp, z[0], z[1], z[2],
-                                                                               z[3], c_planes, sio, err);
-  return cudaGetLastError();
+  const int64_t items = (M / (TM * cl)) * (N / TN) * d.units;
+  if (cl == 1) {
+    const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
+    gemm_tma_persistent<TN, BF16, NP, 1><<<grid, NTHREADS, Cfg2<TN, NP>::SMEM, s>>>(
+        ma, mb, C, d, kp, z[0], z[1], z[2], z[3], c_planes, sio, err);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(items, sms / 2)), 1, 1);
+  cfg.blockDim = dim3(NTHREADS, 1, 1);
+  cfg.dynamicSmemBytes = Cfg2<TN, NP>::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, gemm_tma_persistent<TN, BF16, NP, 2>, ma, mb, C, d, kp, z[0], z[1], z[2], z[3],
+                            c_planes, sio, err);
 }
 
 template <int TN, bool BF16>
@@ -1206,10 +1251,10 @@ cudaError_t launch_tn(int TNv, bool persistent, const CUtensorMap& ma, const CUt
   } else {
     if (persistent) {
       switch (TNv) {
-        case 128: return launch_persistent<128, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
-        case 64: return launch_persistent<64, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
-        case 32: return launch_persistent<32, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
-        case 16: return launch_persistent<16, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+        case 128: return launch_persistent<128, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, cl, err, s);
+        case 64: return launch_persistent<64, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, cl, err, s);
+        case 32: return launch_persistent<32, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, cl, err, s);
+        case 16: return launch_persistent<16, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, cl, err, s);
         default: return cudaErrorInvalidValue;
       }
     }
@@ -1259,9 +1304,9 @@ cudaError_t launch_gemm_tma(const PlaneOperand& a, const PlaneOperand& b, float2
     if (fold > 1) TNv = (1 << d.nn) * fold;
   }
 
-  // split precision: pairs of CTAs on vertically adjacent tiles share the B
-  // tile (each loads half of it, one plane per box, into both)
-  const int cl = a.np == 4 && use_clusters() && d.nm >= 8 && TNv >= 32 ? 2 : 1;
+  // persistent kernels: pairs of CTAs on vertically adjacent tiles share the
+  // B tile (each loads half of it, one plane per box, into both)
+  const int cl = (a.np == 4 || persistent) && use_clusters() && d.nm >= 8 && TNv >= 32 ? 2 : 1;
   const int b_rows = fold > 1 ? (1 << d.nn) : (cl == 2 ? TNv / 2 : TNv);
   CUtensorMap ma, mb;
   if (!encode_planes(&ma, a, TM) || !encode_planes(&mb, b, b_rows, fold > 1 || cl == 2 ? 1 : 0))
@@ -1272,8 +1317,8 @@ cudaError_t launch_gemm_tma(const PlaneOperand& a, const PlaneOperand& b, float2
   if (a.np == 4)
     return bf16 ? launch_tn<true, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, fold, cl, err, s)
                 : launch_tn<false, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, fold, cl, err, s);
-  return bf16 ? launch_tn<true, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, 1, 1, err, s)
-              : launch_tn<false, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, 1, 1, err, s);
+  return bf16 ? launch_tn<true, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, 1, cl, err, s)
+              : launch_tn<false, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, 1, cl, err, s);
 }
 
 }  // namespace tn
