@@ -144,9 +144,10 @@ def cpu_oracle_sample(p, words, open_q, slice_id=0):
     return v, dt, cmac
 
 
-def traffic_record(kernel_file):
-    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
-    the current source of the kernel (else None)."""
+def traffic_record(kernel_file, precision):
+    """Per-launch DRAM bytes of the dominant kernel class in `precision` from
+    the committed ncu capture of the bench, if it was taken on the current
+    source of the kernel file (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
@@ -158,7 +159,7 @@ def traffic_record(kernel_file):
     r = rec.get(kernel_file)
     if not r or r.get("source_sha") != h:
         return None
-    return r
+    return r.get(precision)
 
 
 def run_ours(args):
@@ -223,7 +224,7 @@ def run_ours(args):
     cls_n = [sum(r["class_launches"][i] for r in reps) for i in range(4)]
     dom = int(np.argmax(cls_ms[:3]))
     kernel_file = {0: "k_simt.cu", 1: "k_vector.cu", 2: "k_tc2.cu"}[dom]
-    tr = traffic_record(kernel_file)
+    tr = traffic_record(kernel_file, args.precision)
     if dom == 2:
         achieved = cls_fl[dom] / (cls_ms[dom] * 1e-3) / 1e12
         # split precisions issue three 16-bit products per real product
@@ -241,13 +242,16 @@ def run_ours(args):
         fp32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(fp32, 1), "unit": "TFLOP/s",
                 "frac": round(achieved / fp32, 4), "peak_kind": "FP32 FFMA: 152 SMs x 128 lanes x 2 x max clock"}
-    roof["kernel"] = {0: "gemm_simt_kernel", 1: "vector_kernel", 2: "gemm_tma_kernel / gemm_tma_persistent"}[dom]
+    roof["kernel"] = {0: "gemm_simt_kernel", 1: "vector_kernel",
+                      2: "gemm_tma_chunked" if args.precision.startswith("split")
+                      else "gemm_tma_persistent / gemm_tma_kernel"}[dom]
     roof["launches_per_step"] = cls_n[dom] / args.steps
     roof["share_of_device_time"] = round(cls_ms[dom] / sum(cls_ms), 4) if sum(cls_ms) else None
     if cls_n[3]:
         roof["split_pass"] = {"ms_per_step": round(cls_ms[3] / args.steps, 2),
                               "gbs": round(cls_by[3] / (cls_ms[3] * 1e-3) / 1e9, 1),
                               "share_of_device_time": round(cls_ms[3] / sum(cls_ms), 4)}
+    roof["algorithmic_bytes_per_launch"] = round(cls_by[dom] / cls_n[dom]) if cls_n[dom] else None
     roof["traffic"] = None if tr is None else tr["bytes_per_launch"]
     roof["traffic_note"] = None if tr is None else tr["note"]
 

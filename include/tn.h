@@ -274,6 +274,10 @@ typedef struct {
   const uint64_t* bitstrings;    /* host, nb * ceil(n/64) words; copied by tn_submit */
   int32_t precision;             /* TN_PREC_*; -1 = the server default */
   int32_t reserved;
+  double fidelity;               /* (0, 1): serve only the first ceil(fidelity * 2^S) slices
+                                    of the plan's 2^S (Sec. "A Mixed-Precision Computation Method
+                                    via Adaptive Precision Scaling": a fraction f of the slices
+                                    gives amplitudes of fidelity about f); 0 or 1 = all slices */
 } tn_request;
 
 typedef struct {
@@ -289,6 +293,7 @@ typedef struct {
   int32_t planned_here;          /* 1 = this request ran the planner (plan cache miss) */
   int32_t stem_reused;           /* 1 = the circuit's leaf tensors and invariant (phase-0)
                                     intermediates were already resident from an earlier request */
+  double slice_fraction;         /* slices served / 2^S: the expected fidelity of the amplitudes */
 } tn_request_stats;
 
 /* Creates a server on the current CUDA device with a planner thread and a
@@ -324,7 +329,8 @@ enum {
   TN_PAIR_VECTOR = 2,    /* bandwidth kernel (small N*K) */
   TN_PAIR_FUSED_TC = 3,  /* tcgen05 GEMM fed by TMA from split operand planes (library-allocated scratch) */
   TN_PAIR_UNFUSED = 4,   /* permute A and B to GEMM order, GEMM, permute C (library-allocated scratch) */
-  TN_PAIR_GATHER_TC = 5  /* tcgen05 GEMM gathering and splitting operand tiles in the main loop (no scratch) */
+  TN_PAIR_GATHER_TC = 5, /* tcgen05 GEMM gathering and splitting operand tiles in the main loop (no scratch) */
+  TN_PAIR_REDUCE = 6     /* bandwidth kernel for M N <= 64 outputs and K >= 256 (warp-shuffle reduction over K) */
 };
 
 /* C[c_labels] = sum over labels shared by A and B of A[a_labels] * B[b_labels].

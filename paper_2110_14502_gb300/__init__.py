@@ -268,7 +268,7 @@ class Server:
         self._h = h
         self._k = {}
 
-    def submit(self, rows, cols, depth, seed, num_open, bitstrings, precision=None):
+    def submit(self, rows, cols, depth, seed, num_open, bitstrings, precision=None, fidelity=0.0):
         b = np.ascontiguousarray(np.asarray(bitstrings, dtype=np.uint64))
         if b.ndim == 1:
             b = b.reshape(-1, 1)
@@ -277,6 +277,7 @@ class Server:
         r.nb = b.shape[0]
         r.bitstrings = b.ctypes.data
         r.precision = -1 if precision is None else (PREC[precision] if isinstance(precision, str) else int(precision))
+        r.fidelity = float(fidelity)
         t = C.c_int64()
         check(lib().tn_submit(self._h, C.byref(r), C.byref(t)))
         self._k[t.value] = (b.shape[0], num_open)

@@ -18,7 +18,7 @@ STATUS = {0: "TN_OK", 1: "TN_EINVAL", 2: "TN_ENOMEM", 3: "TN_EHBM", 4: "TN_ECUDA
           6: "TN_ETOOBIG", 7: "TN_EOVERFLOW", 8: "TN_ENOTREADY", 9: "TN_ENODEVICE"}
 GATE_KINDS = {"sqrtx": 0, "sqrty": 1, "sqrtw": 2, "fsim": 3, "mat1": 4, "mat2": 5}
 PREC = {"c64": 0, "split_bf16": 1, "split_fp16": 2, "scaled_fp16": 3, "scaled_bf16": 4}
-PAIR_ALGO = {"auto": 0, "fused_simt": 1, "vector": 2, "fused_tc": 3, "unfused": 4, "gather_tc": 5}
+PAIR_ALGO = {"auto": 0, "fused_simt": 1, "vector": 2, "fused_tc": 3, "unfused": 4, "gather_tc": 5, "reduce": 6}
 
 
 class TnError(RuntimeError):
@@ -67,13 +67,14 @@ class ServerOpts(C.Structure):
 class Request(C.Structure):
     _fields_ = [("rows", C.c_int32), ("cols", C.c_int32), ("depth", C.c_int32), ("num_open", C.c_int32),
                 ("seed", C.c_uint64), ("nb", C.c_int64), ("bitstrings", C.c_void_p), ("precision", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("fidelity", C.c_double)]
 
 
 class RequestStats(C.Structure):
     _fields_ = [("submit_to_done_ms", C.c_double), ("queue_ms", C.c_double), ("device_ms", C.c_double),
                 ("flops", C.c_double), ("slices", C.c_int64), ("status", C.c_int32), ("num_open", C.c_int32),
-                ("nb", C.c_int64), ("plan_hash", C.c_uint64), ("planned_here", C.c_int32), ("stem_reused", C.c_int32)]
+                ("nb", C.c_int64), ("plan_hash", C.c_uint64), ("planned_here", C.c_int32), ("stem_reused", C.c_int32),
+                ("slice_fraction", C.c_double)]
 
 
 class Report(C.Structure):

@@ -397,8 +397,12 @@ tn_status run_step(Ctx& c, size_t s, const Geo& g) {
   cudaError_t e;
   int klass = S.klass == SC_VECTOR ? TN_KCLASS_VECTOR : TN_KCLASS_GEMM_SIMT;
   if (S.klass != SC_VECTOR && c.tc && tc_shape_ok(d)) klass = TN_KCLASS_GEMM_TC;
+  // few outputs with a long contracted index: the bandwidth-bound reduction
+  const bool reduce = klass == TN_KCLASS_GEMM_SIMT && reduce_shape_ok(d);
+  if (reduce) klass = TN_KCLASS_VECTOR;
   if (c.sizing && klass != TN_KCLASS_GEMM_TC) return TN_OK;
-  if (klass == TN_KCLASS_VECTOR) e = launch_vector(A, B, C, d, c.st);
+  if (reduce) e = launch_reduce(A, B, C, d, c.st);
+  else if (klass == TN_KCLASS_VECTOR) e = launch_vector(A, B, C, d, c.st);
   else if (klass == TN_KCLASS_GEMM_TC) {
     const int L = (int)P.net.leaves.size();
     PlaneOperand pa{}, pb{};

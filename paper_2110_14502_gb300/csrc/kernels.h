@@ -143,6 +143,10 @@ cudaError_t run_gemm_tc2(const float2* A, const float2* B, float2* C, const Gemm
 cudaError_t run_gemm_tc2_scaled(const float2* A, const float2* B, float2* C, const GemmDesc& d, bool bf16, int np,
                                 uint16_t* scratch, void* aux, int* err, cudaStream_t s);
 cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s);
+// Few outputs (M N <= 64), long contracted index (K >= 256): one CTA per
+// unit, K spread over the threads, warp-shuffle reduction (k_reduce.cu).
+bool reduce_shape_ok(const GemmDesc& d);
+cudaError_t launch_reduce(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s);
 cudaError_t launch_set_group(GroupInfo* slot, const GroupInfo& g, cudaStream_t s);
 // grid covers `units` units (the slot's count may be lower for a partial group)
 cudaError_t launch_gather(const float2* store, float2* arena, int64_t arena_stride, const LeafGather* descs,

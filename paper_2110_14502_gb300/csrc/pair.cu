@@ -161,6 +161,7 @@ extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, in
   float2* c = (float2*)Cv;
   if (algo == TN_PAIR_AUTO) {
     if (d.nn <= 4 && d.nk <= 4) algo = TN_PAIR_VECTOR;
+    else if (reduce_shape_ok(d) && !(precision != TN_PREC_C64 && tc_shape_ok(d))) algo = TN_PAIR_REDUCE;
     else if (precision != TN_PREC_C64 && tc_shape_ok(d)) algo = TN_PAIR_FUSED_TC;
     else algo = TN_PAIR_FUSED_SIMT;
   }
@@ -172,6 +173,11 @@ extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, in
       e = launch_vector(a, b, c, d, s);
       break;
     case TN_PAIR_UNFUSED: return unfused(a, b, c, d, s);
+    case TN_PAIR_REDUCE:
+      if (!reduce_shape_ok(d))
+        return fail(TN_EINVAL, "tn_contract_pair: the reduction kernel needs M N <= 64 and K >= 256");
+      e = launch_reduce(a, b, c, d, s);
+      break;
     case TN_PAIR_FUSED_TC:
     case TN_PAIR_GATHER_TC: {
       if (precision == TN_PREC_C64)

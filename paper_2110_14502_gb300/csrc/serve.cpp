@@ -18,6 +18,7 @@
 // the mix.  Requests whose plan exceeds the cost cap fail with TN_ETOOBIG, and
 // ones that could never fit the budget with TN_EHBM; neither is dropped silently.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -144,7 +145,10 @@ tn_status plan_request(Server& S, Request& R) {
   copy->plan.stems = S.stems;
   R.plan.reset(copy);
   const Plan& P = R.plan->plan;
-  R.ns = int64_t(1) << P.sliced.size();
+  // fidelity by fraction: the first ceil(f 2^S) slices (all for f = 0 or 1)
+  const int64_t all = int64_t(1) << P.sliced.size();
+  const double f = R.params.fidelity;
+  R.ns = f > 0.0 && f < 1.0 ? std::max<int64_t>(1, std::min<int64_t>(all, (int64_t)std::ceil(f * (double)all))) : all;
   R.q = std::min<int64_t>(R.ns, std::max(1, S.opts.slices_per_quantum));
   R.k = (int)P.net.open_qubits.size();
   R.words = std::max(1, (P.net.n + 63) / 64);
@@ -389,7 +393,7 @@ extern "C" tn_status tn_submit(tn_server* h, const tn_request* req, int64_t* tic
   if (!h || !req || !ticket) return fail(TN_EINVAL, "tn_submit: NULL argument");
   const int n = req->rows * req->cols;
   if (req->rows < 1 || req->cols < 1 || n > 64 || req->depth < 0 || req->num_open < 0 || req->num_open > 12 ||
-      req->num_open > n || req->nb < 1 || !req->bitstrings)
+      req->num_open > n || req->nb < 1 || !req->bitstrings || !(req->fidelity >= 0.0 && req->fidelity <= 1.0))
     return fail(TN_EINVAL, "tn_submit: bad request (grid %dx%d, depth %d, %d open, %lld bitstrings)", req->rows,
                 req->cols, req->depth, req->num_open, (long long)req->nb);
   Server& S = h->s;
@@ -449,6 +453,7 @@ extern "C" tn_status tn_wait(tn_server* h, int64_t ticket, double* out, int64_t 
     stats->queue_ms = R->status == TN_OK ? ms(R->t_submit, R->t_admit) : 0.0;
     stats->device_ms = R->status == TN_OK ? ms(R->t_admit, R->t_done) : 0.0;
     stats->slices = R->ns;
+    if (R->plan) stats->slice_fraction = (double)R->ns / std::ldexp(1.0, (int)R->plan->plan.sliced.size());
     stats->status = R->status;
     stats->num_open = R->k;
     stats->nb = R->params.nb;

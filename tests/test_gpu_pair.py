@@ -60,6 +60,18 @@ def test_vector_kernel_matches_fp64(nm, nn, nk):
     assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("nm,nn,nk", [(0, 0, 8), (4, 2, 12), (2, 4, 9), (6, 0, 10), (0, 6, 8), (3, 3, 14),
+                                      (1, 2, 16)])
+def test_reduction_kernel_matches_fp64(nm, nn, nk):
+    """Few outputs (M N <= 64) and a long contracted index: K spread over the
+    threads of a CTA and combined with warp shuffles; random index orders."""
+    T = tnlib()
+    la, lb, lc, A, B, ref = _case(nm, nn, nk, seed=200 + 10 * nm + nk)
+    for algo in ("reduce", "auto"):
+        got = _run(T, la, lb, lc, A, B, algo)
+        assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref), algo
+
+
 def test_pair_rejects_bad_labels():
     T = tnlib()
     import torch

@@ -106,3 +106,48 @@ def test_stems_stay_resident_for_later_requests_of_a_circuit():
     for r, o in zip(reqs, [first] + shared):
         ref = SV.amplitudes(psi, n, [I.bits_of(w, n) for w in r["bitstrings"]], open_q)
         assert np.linalg.norm(o - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_partial_fidelity_requests_serve_a_fraction_of_the_slices():
+    """Fidelity by fraction: a request with fidelity f is served from the first
+    ceil(f 2^S) slices.  Its amplitudes are the exact partial sum over those
+    slices (the plain path on the same slice range), and over the whole
+    output space their fidelity with the state vector, and the XEB of exact
+    samples scored with them, are close to the served fraction."""
+    T = tnlib()
+    rows, cols, depth, seed = 4, 5, 14, 21
+    n = rows * cols
+    k = 12
+    # 256 bitstrings whose closed qubits 0..7 take every value: all 2^20 amplitudes
+    words = np.array([[x] for x in range(256)], dtype=np.uint64)
+    kw = dict(max_inflight=2, slices_per_quantum=4, precision="c64", plan_trials=8, max_log2_intermediate=15)
+    srv = T.Server(**kw)
+    try:
+        full, st1 = srv.wait(srv.submit(rows=rows, cols=cols, depth=depth, seed=seed, num_open=k, bitstrings=words))
+        part, st = srv.wait(srv.submit(rows=rows, cols=cols, depth=depth, seed=seed, num_open=k, bitstrings=words,
+                                       fidelity=0.25))
+    finally:
+        srv.close()
+    S_all = st1["slices"]
+    assert S_all >= 16 and st1["slice_fraction"] == 1.0
+    m = int(np.ceil(0.25 * S_all))
+    assert st["slices"] == m and abs(st["slice_fraction"] - m / S_all) < 1e-12
+    # the same plan through the plain path, first m slices
+    c = T.random_circuit(rows, cols, depth, seed)
+    p = T.plan(T.build_network(c, list(range(n - k, n))), max_log2_intermediate=15, search_trials=8, seed=1,
+               max_log2_cmac=48.0)
+    assert p.info()["hash"] == st["plan_hash"]
+    ref = p.contract_amplitudes(words, slice_count=m)
+    assert np.linalg.norm(part - ref) <= 1e-6 * np.linalg.norm(ref)
+    # amplitude of basis index x: bitstring x & 255, open index x >> 8
+    a_f = part.T.reshape(-1)
+    a = full.T.reshape(-1)
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    psi = SV.simulate(gates, n)
+    assert np.linalg.norm(a - psi) <= 1e-5 * np.linalg.norm(psi)
+    fid = abs(np.vdot(a_f, psi)) ** 2 / (np.vdot(a_f, a_f).real * np.vdot(psi, psi).real)
+    p_true = np.abs(psi) ** 2
+    p_f = np.abs(a_f) ** 2 / np.sum(np.abs(a_f) ** 2)
+    xeb = (2.0 ** n) * np.sum(p_true * p_f) - 1.0
+    frac = m / S_all
+    assert abs(fid - frac) <= 0.05 and abs(xeb - frac) <= 0.05, (fid, xeb, frac)
