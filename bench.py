@@ -144,10 +144,10 @@ def cpu_oracle_sample(p, words, open_q, slice_id=0):
     return v, dt, cmac
 
 
-def traffic_record(kernel_file, precision):
-    """Per-launch DRAM bytes of the dominant kernel class in `precision` from
-    the committed ncu capture of the bench, if it was taken on the current
-    source of the kernel file (else None)."""
+def traffic_record(kernel_file, key):
+    """Per-launch DRAM bytes of the dominant kernel class for `key`
+    ("<workload>/<precision>") from the committed ncu capture of the bench, if
+    it was taken on the current source of the kernel file (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
@@ -159,7 +159,7 @@ def traffic_record(kernel_file, precision):
     r = rec.get(kernel_file)
     if not r or r.get("source_sha") != h:
         return None
-    return r.get(precision)
+    return r.get(key)
 
 
 def run_ours(args):
@@ -224,7 +224,7 @@ def run_ours(args):
     cls_n = [sum(r["class_launches"][i] for r in reps) for i in range(4)]
     dom = int(np.argmax(cls_ms[:3]))
     kernel_file = {0: "k_simt.cu", 1: "k_vector.cu", 2: "k_tc2.cu"}[dom]
-    tr = traffic_record(kernel_file, args.precision)
+    tr = traffic_record(kernel_file, f"{args.workload}/{args.precision}")
     if dom == 2:
         achieved = cls_fl[dom] / (cls_ms[dom] * 1e-3) / 1e12
         # split precisions issue three 16-bit products per real product
