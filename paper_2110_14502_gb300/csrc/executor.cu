@@ -320,7 +320,7 @@ struct Ctx {
   cudaStream_t st;
   bool profile;
   int64_t launches = 0;
-  struct Rec { int klass; double flops, bytes; size_t ev; int step, nm, nn, nk; int64_t units; int cfast, planes, n16, ulo, uhi; };
+  struct Rec { int klass; double flops, bytes; size_t ev; int step, nm, nn, nk; int64_t units; long long cfast; int planes, n16, ulo, uhi; };
   std::vector<Rec> recs;
   size_t nev = 0;
   int precision = TN_PREC_C64;
@@ -524,9 +524,14 @@ tn_status run_step(Ctx& c, size_t s, const Geo& g) {
     double bytes = 8.0 * (M * K * distinct(d.a_lo, d.a_hi) + K * N * distinct(d.b_lo, d.b_hi) + M * N * U);
     // diagnostics: C's unit-stride index (row bit i -> i, column bit j -> 100 + j), plane output,
     // 16-column vector stores, which operands vary with the lo / hi unit index
-    int cfast = -1;
-    for (int i = 0; i < d.nm; ++i) if (d.cm[i] == 1) cfast = i;
-    for (int j = 0; j < d.nn; ++j) if (d.cn[j] == 1) cfast = 100 + j;
+    // C's four fastest indices: row bit i -> i, column bit j -> 100 + j (base-1000 digits)
+    long long cfast = 0;
+    for (int q = 3; q >= 0; --q) {
+      int who = 999;
+      for (int i = 0; i < d.nm; ++i) if (d.cm[i] == (1 << q)) who = i;
+      for (int j = 0; j < d.nn; ++j) if (d.cn[j] == (1 << q)) who = 100 + j;
+      cfast = cfast * 1000 + who;
+    }
     const int n16 = d.nn >= 4 && d.cn[0] == 1 && d.cn[1] == 2 && d.cn[2] == 4 && d.cn[3] == 8;
     const int ulo = (d.a_lo ? 1 : 0) | (d.b_lo ? 2 : 0), uhi = (d.a_hi ? 1 : 0) | (d.b_hi ? 2 : 0);
     c.recs.push_back({klass, 8.0 * M * N * K * U, bytes, e0, (int)s, d.nm, d.nn, d.nk, d.units, cfast,
@@ -950,7 +955,7 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
     rep->flagged_units = nflag;
     rep->discarded_units = discarded;
     // TN_PROFILE_STEPS=1: per-step breakdown of the timed launches on stderr
-    struct StepAgg { int klass = 0, nm = 0, nn = 0, nk = 0, launches = 0, cfast = 0, planes = 0, n16 = 0, ulo = 0, uhi = 0; int64_t units = 0; double ms = 0, flops = 0; };
+    struct StepAgg { int klass = 0, nm = 0, nn = 0, nk = 0, launches = 0, planes = 0, n16 = 0, ulo = 0, uhi = 0; long long cfast = 0; int64_t units = 0; double ms = 0, flops = 0; };
     std::map<int, StepAgg> per_step;
     const bool by_step = getenv("TN_PROFILE_STEPS") != nullptr;
     for (auto& r : c.recs) {
@@ -983,7 +988,7 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
       for (auto& [st_i, a] : v)
         fprintf(stderr,
                 "step %d phase %d class %d M 2^%d N 2^%d K 2^%d units %lld launches %d ms %.3f tflops %.1f "
-                "cfast %d planes %d n16 %d ulo %d uhi %d\n",
+                "cfast %012lld planes %d n16 %d ulo %d uhi %d\n",
                 st_i, P.steps[st_i].phase, a.klass, a.nm, a.nn, a.nk, (long long)a.units, a.launches, a.ms,
                 a.ms > 0 ? a.flops / (a.ms * 1e9) : 0.0, a.cfast, a.planes, a.n16, a.ulo, a.uhi);
     }
