@@ -540,9 +540,16 @@ def main():
     ap.add_argument("--workload", default="6x6", choices=["6x6", "8x8"])
     ap.add_argument("--no-modes", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--plan-trials", type=int, default=0, help="order-search restarts (0: the workload's default)")
+    ap.add_argument("--plan-seed", type=int, default=0, help="planner seed (0: the workload's default)")
     args = ap.parse_args()
     if args.workload == "8x8":
         use_8x8()
+    global PLAN_TRIALS, PLAN_SEED
+    if args.plan_trials > 0:
+        PLAN_TRIALS = args.plan_trials
+    if args.plan_seed > 0:
+        PLAN_SEED = args.plan_seed
     if args.impl == "reference":
         run_reference(args)
     elif args.micro:
