@@ -145,7 +145,9 @@ typedef struct {
   int32_t num_sliced;            /* exact number of sliced indices S; -1 = as few as the width cap needs */
   int32_t max_log2_intermediate; /* per-slice width cap (log2 elements); 0 = no cap */
   int32_t search_trials;         /* order-search restarts; 0 = default (128) */
-  int32_t reserved;
+  int32_t bitstrings_hint;       /* bitstrings expected per call: the search weighs the steps that
+                                    depend on the bitstring (run once per bitstring and slice) by it
+                                    against the slice-only ones (run once per slice); 0 = 1 */
   uint64_t seed;                 /* search seed; equal inputs + seed give byte-identical plans */
   double max_log2_cmac;          /* cost cap on total complex MACs (log2); 0 = none -> TN_ETOOBIG when exceeded */
 } tn_plan_opts;

@@ -39,7 +39,7 @@ class NetworkInfo(C.Structure):
 
 class PlanOpts(C.Structure):
     _fields_ = [("num_sliced", C.c_int32), ("max_log2_intermediate", C.c_int32), ("search_trials", C.c_int32),
-                ("reserved", C.c_int32), ("seed", C.c_uint64), ("max_log2_cmac", C.c_double)]
+                ("bitstrings_hint", C.c_int32), ("seed", C.c_uint64), ("max_log2_cmac", C.c_double)]
 
 
 class PlanInfo(C.Structure):

@@ -275,15 +275,29 @@ void node_sets(const std::vector<LSet>& leaves, const std::vector<int>& pairs,
   for (size_t p = 0; p < pairs.size(); p += 2) sets.push_back(sym_diff(sets[pairs[p]], sets[pairs[p + 1]]));
 }
 
-void cost_of(const std::vector<LSet>& sets, const std::vector<int>& pairs, int L, double& time,
-             double& cmac, int& width) {
+// Weight of every step of a tree in the modelled time: `hint` for a step whose
+// subtree holds a bitstring-dependent leaf (it runs once per bitstring and
+// slice), 1 for the others (once per slice, shared by the bitstrings).
+std::vector<double> step_weights(const std::vector<char>& var_leaf, const std::vector<int>& pairs, double hint) {
+  std::vector<char> var(var_leaf);
+  std::vector<double> w(pairs.size() / 2);
+  for (size_t p = 0; p < pairs.size(); p += 2) {
+    const char v = var[pairs[p]] | var[pairs[p + 1]];
+    var.push_back(v);
+    w[p / 2] = v ? hint : 1.0;
+  }
+  return w;
+}
+
+void cost_of(const std::vector<LSet>& sets, const std::vector<int>& pairs, int L, const std::vector<double>& w,
+             double& time, double& cmac, int& width) {
   time = 0; cmac = 0; width = 0;
   for (auto& s : sets) width = std::max(width, (int)s.size());
   for (size_t p = 0; p < pairs.size(); p += 2) {
     const LSet &a = sets[pairs[p]], &b = sets[pairs[p + 1]], &c = sets[L + p / 2];
     int wu = union_size(a, b);
     cmac += std::ldexp(1.0, wu);
-    time += step_time((int)a.size(), (int)b.size(), (int)c.size(), wu);
+    time += w[p / 2] * step_time((int)a.size(), (int)b.size(), (int)c.size(), wu);
   }
 }
 
@@ -291,7 +305,7 @@ void cost_of(const std::vector<LSet>& sets, const std::vector<int>& pairs, int L
 // gives the smallest (width, modelled time).  Removing a label only changes
 // the steps and nodes that hold it, so each candidate is scored incrementally.
 Eval slice_tree(const std::vector<LSet>& leaves, const std::vector<int>& pairs, const LSet& sliceable,
-                int num_sliced, int cap) {
+                int num_sliced, int cap, const std::vector<double>& wt) {
   const int L = (int)leaves.size();
   const int nsteps = (int)pairs.size() / 2;
   Eval ev;
@@ -324,7 +338,7 @@ Eval slice_tree(const std::vector<LSet>& leaves, const std::vector<int>& pairs, 
     for (int v : size) width = std::max(width, v);
     for (int t = 0; t < nsteps; ++t) {
       cmac += std::ldexp(1.0, wu[t]);
-      time += step_time(wa[t], wb[t], wc[t], wu[t]);
+      time += wt[t] * step_time(wa[t], wb[t], wc[t], wu[t]);
     }
   };
   totals(ev.time, ev.cmac, ev.width);
@@ -360,8 +374,8 @@ Eval slice_tree(const std::vector<LSet>& leaves, const std::vector<int>& pairs, 
         const int a_has = std::binary_search(sets[pairs[2 * t]].begin(), sets[pairs[2 * t]].end(), l);
         const int b_has = std::binary_search(sets[pairs[2 * t + 1]].begin(), sets[pairs[2 * t + 1]].end(), l);
         const int c_has = a_has != b_has;
-        dt += step_time(wa[t] - a_has, wb[t] - b_has, wc[t] - c_has, wu[t] - 1) -
-              step_time(wa[t], wb[t], wc[t], wu[t]);
+        dt += wt[t] * (step_time(wa[t] - a_has, wb[t] - b_has, wc[t] - c_has, wu[t] - 1) -
+                       step_time(wa[t], wb[t], wc[t], wu[t]));
       }
       const double t_new = ev.time + dt;
       if (best < 0 || w < bw || (w == bw && t_new < bt)) { best = l; bw = w; bt = t_new; }
@@ -396,7 +410,7 @@ Eval slice_tree(const std::vector<LSet>& leaves, const std::vector<int>& pairs, 
 // The frontier's joint label set is order independent, so every rewrite keeps
 // the tree valid.
 void reconfigure(const std::vector<LSet>& leaves, std::vector<int>& pairs, const std::vector<int>& sliced,
-                 int k, int passes) {
+                 int k, int passes, const std::vector<char>& var_leaf, double hint) {
   const int L = (int)leaves.size();
   if (L < 3) return;
   std::vector<int> lch(L, -1), rch(L, -1);
@@ -404,10 +418,13 @@ void reconfigure(const std::vector<LSet>& leaves, std::vector<int>& pairs, const
   int root = (int)lch.size() - 1;
   std::vector<LSet> sets;
   node_sets(leaves, pairs, sliced, sets);
-  auto cost2 = [&](const LSet& a, const LSet& b) {
+  // bitstring dependence of every node (weight `hint` on the steps that have it)
+  std::vector<char> var(var_leaf);
+  for (size_t p = 0; p < pairs.size(); p += 2) var.push_back(var[pairs[p]] | var[pairs[p + 1]]);
+  auto cost2 = [&](const LSet& a, const LSet& b, bool v) {
     int u = union_size(a, b);
     int sh = (int)a.size() + (int)b.size() - u;
-    return step_time((int)a.size(), (int)b.size(), u - sh, u);
+    return (v ? hint : 1.0) * step_time((int)a.size(), (int)b.size(), u - sh, u);
   };
   for (int pass = 0; pass < passes; ++pass) {
     // post-order list of internal nodes reachable from the root
@@ -438,22 +455,24 @@ void reconfigure(const std::vector<LSet>& leaves, std::vector<int>& pairs, const
       const int f = (int)front.size();
       if (f < 3) continue;
       double cur = 0;
-      for (int u : expanded) cur += cost2(sets[lch[u]], sets[rch[u]]);
+      for (int u : expanded) cur += cost2(sets[lch[u]], sets[rch[u]], var[u]);
       const int full = (1 << f) - 1;
       std::vector<LSet> ss(1 << f);
+      std::vector<char> vs(1 << f, 0);
       std::vector<double> best(1 << f, 0.0);
       std::vector<int> split(1 << f, 0);
       for (int S = 1; S <= full; ++S) {
         int low = S & -S;
-        if (S == low) { ss[S] = sets[front[__builtin_ctz(S)]]; continue; }
+        if (S == low) { ss[S] = sets[front[__builtin_ctz(S)]]; vs[S] = var[front[__builtin_ctz(S)]]; continue; }
         ss[S] = sym_diff(ss[S ^ low], ss[low]);
+        vs[S] = vs[S ^ low] | vs[low];
         double b = 1e300;
         int bs = 0;
         // sub-splits containing the lowest bit
         for (int S1 = (S - 1) & S; S1 > 0; S1 = (S1 - 1) & S) {
           if (!(S1 & low)) continue;
           int S2 = S ^ S1;
-          double c = best[S1] + best[S2] + cost2(ss[S1], ss[S2]);
+          double c = best[S1] + best[S2] + cost2(ss[S1], ss[S2], vs[S]);
           if (c < b) { b = c; bs = S1; }
         }
         best[S] = b;
@@ -466,6 +485,7 @@ void reconfigure(const std::vector<LSet>& leaves, std::vector<int>& pairs, const
           int a = build(split[S]), b = build(S ^ split[S]);
           lch.push_back(a); rch.push_back(b);
           sets.push_back(sym_diff(sets[a], sets[b]));
+          var.push_back(var[a] | var[b]);
           return (int)lch.size() - 1;
         };
         int a = build(split[full]), b = build(full ^ split[full]);
@@ -515,9 +535,13 @@ tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& P) {
   if (L == 0) return fail(TN_EINVAL, "tn_plan: empty network");
   std::vector<LSet> leaves(L);
   LSet sliceable;
+  // leaves holding a closed output index depend on the bitstring
+  std::vector<char> var_leaf(L, 0);
+  const double hint = std::max(1, opts.bitstrings_hint);
   for (int i = 0; i < L; ++i) {
     for (int l : net.leaves[i].labels)
       if (net.kind[l] != LK_CLOSED) leaves[i].push_back(l);
+      else var_leaf[i] = 1;
     std::sort(leaves[i].begin(), leaves[i].end());
     for (int l : leaves[i])
       if (net.kind[l] == LK_INTERNAL) sliceable.push_back(l);
@@ -551,22 +575,23 @@ tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& P) {
         bisect_tree(B, all, cutoff, eps, alpha, r2);
       }
     }
-    reconfigure(leaves, B.pairs, {}, 6, 3);
+    reconfigure(leaves, B.pairs, {}, 6, 3, var_leaf, hint);
     if (opts.max_log2_cmac > 0) {
       // slicing only adds work: a tree already above the cost cap is dropped unsliced
       std::vector<LSet> st0;
       node_sets(leaves, B.pairs, {}, st0);
       double t0, c0;
       int w0;
-      cost_of(st0, B.pairs, L, t0, c0, w0);
+      cost_of(st0, B.pairs, L, step_weights(var_leaf, B.pairs, hint), t0, c0, w0);
       if (std::log2(std::max(c0, 1.0)) > opts.max_log2_cmac) continue;
     }
-    Eval ev = slice_tree(leaves, B.pairs, sliceable, opts.num_sliced, opts.max_log2_intermediate);
+    Eval ev = slice_tree(leaves, B.pairs, sliceable, opts.num_sliced, opts.max_log2_intermediate,
+                         step_weights(var_leaf, B.pairs, hint));
     if (!ev.sliced.empty()) {
-      reconfigure(leaves, B.pairs, ev.sliced, 6, 3);
+      reconfigure(leaves, B.pairs, ev.sliced, 6, 3, var_leaf, hint);
       std::vector<LSet> st;
       node_sets(leaves, B.pairs, ev.sliced, st);
-      cost_of(st, B.pairs, L, ev.time, ev.cmac, ev.width);
+      cost_of(st, B.pairs, L, step_weights(var_leaf, B.pairs, hint), ev.time, ev.cmac, ev.width);
     }
     double score = ev.time * std::ldexp(1.0, (int)ev.sliced.size());
     double bscore = have ? best.time * std::ldexp(1.0, (int)best.sliced.size()) : 0;
@@ -581,10 +606,10 @@ tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& P) {
   if (!have)
     return fail(TN_ETOOBIG, "tn_plan: every searched order costs more than the cap 2^%.1f CMAC", opts.max_log2_cmac);
   if (L > 2) {  // polish the winner with a wider window
-    reconfigure(leaves, best_pairs, best.sliced, 8, 6);
+    reconfigure(leaves, best_pairs, best.sliced, 8, 6, var_leaf, hint);
     std::vector<LSet> st;
     node_sets(leaves, best_pairs, best.sliced, st);
-    cost_of(st, best_pairs, L, best.time, best.cmac, best.width);
+    cost_of(st, best_pairs, L, step_weights(var_leaf, best_pairs, hint), best.time, best.cmac, best.width);
   }
   if (opts.max_log2_intermediate > 0 && best.width > opts.max_log2_intermediate)
     return fail(TN_ETOOBIG, "tn_plan: could not reach width 2^%d (best 2^%d with %d sliced)",
