@@ -340,3 +340,49 @@ def test_xeb_within_one_percent_of_the_oracle(mode):
     m_ref = ST.porter_thomas_moments(np.abs(ref_u.ravel()) ** 2, n)
     m_gpu = ST.porter_thomas_moments(np.abs(got_u.ravel()) ** 2, n)
     assert np.allclose(m_gpu, m_ref, rtol=1e-2), (mode, m_gpu, m_ref)
+
+
+def test_empty_batches_and_split_slice_ranges():
+    """Edge cases of the call: no bitstrings, an empty slice range, and a sum
+    split into two slice ranges (equal to the whole range up to the FP64
+    rounding of one extra addition)."""
+    T = tnlib()
+    rows, cols, depth, seed, open_q = 4, 4, 10, 5, (15, 14)
+    n = rows * cols
+    p = _setup(T, rows, cols, depth, seed, open_q, num_sliced=4, search_trials=16, seed=3)
+    words = I.bitstrings(n, 3, seed)
+    none = p.contract_amplitudes(words[:0])
+    assert none.shape == (0, 4)
+    zero = p.contract_amplitudes(words, slice_count=0)
+    assert zero.shape == (3, 4) and not np.any(zero)
+    for mode in ("c64", "split_bf16"):
+        full = p.contract_amplitudes(words, precision=mode)
+        a = p.contract_amplitudes(words, precision=mode, slice_begin=0, slice_count=7)
+        b = p.contract_amplitudes(words, precision=mode, slice_begin=7)
+        assert np.allclose(a + b, full, rtol=1e-12, atol=1e-15 * np.abs(full).max())
+    with pytest.raises(T.TnError):
+        p.contract_amplitudes(words, slice_begin=10, slice_count=7)
+
+
+def test_autotune_choices_persist_in_the_cache_file(tmp_path, monkeypatch):
+    """TN_AUTOTUNE_CACHE: the first plan that tunes writes its tile choices;
+    a fresh plan of the same circuit reads them instead of tuning again, and
+    every choice gives the same sums."""
+    T = tnlib()
+    import torch
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("TN_AUTOTUNE_CACHE", str(cache))
+    rows, cols, depth, seed, open_q = 4, 5, 14, 12, (14, 15, 16, 17, 18, 19)
+    n = rows * cols
+    words = I.bitstrings(n, 3, seed)
+    s = torch.cuda.Stream()
+    p1 = _setup(T, rows, cols, depth, seed, open_q, num_sliced=3, search_trials=32, seed=3)
+    base = p1.contract_amplitudes(words, precision="split_bf16", stream=s)
+    t1 = p1.contract_amplitudes(words, precision="split_bf16", autotune=1, stream=s)
+    assert np.array_equal(t1, base)
+    lines = cache.read_text().split()
+    assert len(lines) >= 6 and lines[0] == format(p1.info()["hash"], "x")
+    p2 = _setup(T, rows, cols, depth, seed, open_q, num_sliced=3, search_trials=32, seed=3)
+    t2 = p2.contract_amplitudes(words, precision="split_bf16", autotune=1, stream=s)
+    assert np.array_equal(t2, base)
+    assert cache.read_text().split() == lines  # read, not tuned again

@@ -147,3 +147,50 @@ def test_tensor_core_precisions_vs_fp64(mode, nm, nn, nk):
     torch.cuda.synchronize()
     got = dC.cpu().numpy().astype(np.complex128) / (float(s) ** 2)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= PAIR_BOUND[mode], mode
+
+
+def test_rank_30_operand_sampled_outputs():
+    """Largest operand rank (30: 2^30 complex64 = 8 GiB) through the
+    tensor-core and FP32 kernels: M = 2^20, N = 2^6, K = 2^10 with random
+    index orders; 64 sampled outputs against FP64 dot products of the same
+    input values on the host."""
+    T = tnlib()
+    import torch
+    nm, nn, nk = 20, 6, 10
+    rng = np.random.default_rng(30)
+    labels = list(range(nm + nn + nk))
+    M, N, K = labels[:nm], labels[nm:nm + nn], labels[nm + nn:]
+    la = [int(x) for x in rng.permutation(M + K)]
+    lb = [int(x) for x in rng.permutation(K + N)]
+    lc = [int(x) for x in rng.permutation(M + N)]
+    g = torch.Generator(device="cuda").manual_seed(30)
+    dA = torch.randn(1 << len(la), dtype=torch.complex64, device="cuda", generator=g)
+    dB = torch.randn(1 << len(lb), dtype=torch.complex64, device="cuda", generator=g)
+    dC = torch.empty(1 << len(lc), dtype=torch.complex64, device="cuda")
+
+    def stride(ls, l):
+        return 1 << (len(ls) - 1 - ls.index(l))
+
+    ms = rng.integers(0, 1 << nm, 64)
+    ns = rng.integers(0, 1 << nn, 64)
+    ks = np.arange(1 << nk)
+
+    def offsets(ls, idx, bits):
+        o = np.zeros(len(idx), dtype=np.int64)
+        for i, l in enumerate(bits):
+            o += ((idx >> i) & 1) * stride(ls, l)
+        return o
+
+    a_rows = offsets(la, ms, M)[:, None] + offsets(la, ks, K)[None, :]
+    b_cols = offsets(lb, ks, K)[None, :] + offsets(lb, ns, N)[:, None]
+    A_s = dA[torch.from_numpy(a_rows).cuda()].cpu().numpy().astype(np.complex128)
+    B_s = dB[torch.from_numpy(b_cols).cuda()].cpu().numpy().astype(np.complex128)
+    ref = np.sum(A_s * B_s, axis=1)
+    c_off = torch.from_numpy(offsets(lc, ms, M) + offsets(lc, ns, N)).cuda()
+    for precision, algo, tol in (("split_bf16", "fused_tc", 1e-4), ("c64", "fused_simt", 1e-5)):
+        T.contract_pair(dA, la, dB, lb, dC, lc, precision=precision, algo=algo)
+        torch.cuda.synchronize()
+        got = dC[c_off].cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref), (algo, np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    del dA, dB, dC
+    torch.cuda.empty_cache()
