@@ -358,8 +358,9 @@ extern "C" tn_status tn_server_create(const tn_server_opts* opts, tn_server** ou
   if (S.opts.max_log2_cmac <= 0) S.opts.max_log2_cmac = 48.0;
   if (S.opts.max_log2_intermediate <= 0) S.opts.max_log2_intermediate = 27;
   if (S.opts.precision < TN_PREC_C64 || S.opts.precision > TN_PREC_SCALED_BF16) {
+    const int prec = S.opts.precision;  // S lives in h
     delete h;
-    return fail(TN_EINVAL, "tn_server_create: unknown precision %d", S.opts.precision);
+    return fail(TN_EINVAL, "tn_server_create: unknown precision %d", prec);
   }
   if (cudaGetDevice(&S.device) != cudaSuccess) {
     delete h;
