@@ -216,7 +216,7 @@ void bisect(const Builder& B, const std::vector<int>& ids, double eps, std::mt19
     std::vector<int> moves;
     int cur = 0, best = 0, best_len = 0, s0 = size0;
     for (int step = 0; step < n; ++step) {
-      int bv = -1, bg = -1 << 30;
+      int bv = -1, bg = -(1 << 30);
       for (int v = 0; v < n; ++v) {
         if (locked[v]) continue;
         int ns0 = s0 + (part[v] == 0 ? -1 : 1);

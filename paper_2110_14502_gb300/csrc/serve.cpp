@@ -205,7 +205,7 @@ void release(Server& S, Request& R) {
   // the request's plan copy keeps its arenas until the request is released by tn_wait
 }
 
-tn_status admit(Server& S, Request& R, cudaStream_t stream) {
+tn_status admit(Server&, Request& R, cudaStream_t stream) {
   R.stream = stream;
   const int64_t nout = R.params.nb << R.k;
   cudaError_t e = cudaMallocAsync(&R.d_bits, std::max<int64_t>(R.bits.size(), 1) * sizeof(uint64_t), stream);
