@@ -186,7 +186,8 @@ def run_ours(args):
     def step(profile=False):
         with torch.cuda.stream(stream):
             _, rep = p.contract_amplitudes(dwords, out=out, stream=stream, precision=args.precision,
-                                           profile=profile, report=True, slice_count=SLICE_LIMIT)
+                                           profile=profile, report=True, slice_count=SLICE_LIMIT,
+                                           autotune=1 if args.autotune else 0)
         return rep
 
     for _ in range(args.warmup):
@@ -545,6 +546,8 @@ def main():
     ap.add_argument("--workload", default="6x6", choices=["6x6", "8x8"])
     ap.add_argument("--no-modes", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="tune the tensor-core tiles per step in the first (warm-up) call")
     ap.add_argument("--plan-trials", type=int, default=0, help="order-search restarts (0: the workload's default)")
     ap.add_argument("--plan-seed", type=int, default=0, help="planner seed (0: the workload's default)")
     ap.add_argument("--bitstrings-hint", type=int, default=-1,

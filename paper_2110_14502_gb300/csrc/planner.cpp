@@ -12,7 +12,7 @@
 // refined with Fiduccia-Mattheyses moves -- each followed by greedy slicing.
 // The trial with the smallest modelled GB300 time wins (the compute-density
 // term: a step's time is the larger of its flops at the rate its kernel class
-// reaches and its bytes at HBM bandwidth).
+// reaches and its memory time; see step_time).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -48,16 +48,20 @@ int shared_count(const LSet& a, const LSet& b) {
 }
 bool contains(const LSet& a, int l) { return std::binary_search(a.begin(), a.end(), l); }
 
-// Modelled GB300 time of one step with operand widths wa, wb and wu = |A u B|.
+// Modelled GB300 time of one step with operand widths wa, wb and wu = |A u B|:
+// the larger of its flops at the rate of its kernel class and its memory
+// time.  A tensor-core step reads its operands at HBM speed but writes its
+// output through the epilogue's scattered per-thread stores, measured at
+// about 3 TB/s; other steps move all their bytes at HBM speed.
 double step_time(int wa, int wb, int wc, int wu) {
-  double flops = 8.0 * std::ldexp(1.0, wu);
-  double bytes = 8.0 * (std::ldexp(1.0, wa) + std::ldexp(1.0, wb) + std::ldexp(1.0, wc));
+  const double flops = 8.0 * std::ldexp(1.0, wu);
+  const double in = 8.0 * (std::ldexp(1.0, wa) + std::ldexp(1.0, wb)), out = 8.0 * std::ldexp(1.0, wc);
   int nk = (wa + wb - wc) / 2;
   int nm = wa - nk, nn = wb - nk;
   if (nm < nn) std::swap(nm, nn);
-  bool dense = nm >= 7 && nn >= 3 && nk >= 3;
-  double rate = dense ? 6.0e14 : 6.0e13;
-  return std::max(flops / rate, bytes / 6.0e12) + 1.5e-7;
+  const bool dense = nm >= 7 && nn >= 3 && nk >= 3;
+  if (dense) return std::max(flops / 6.0e14, in / 6.0e12 + out / 3.0e12) + 1.5e-7;
+  return std::max(flops / 6.0e13, (in + out) / 6.0e12) + 1.5e-7;
 }
 
 struct Builder {
