@@ -12,7 +12,7 @@ import numpy as np
 from ._abi import (PAIR_ALGO, PREC, ExecOpts, Gate, NetworkInfo, PlanInfo, PlanOpts, Report, Request,
                    RequestStats, ServerOpts, TnError, check, i32array, lib)
 
-__all__ = ["Circuit", "Network", "Plan", "random_circuit", "circuit_from_gates", "build_network", "plan",
+__all__ = ["Circuit", "Network", "Plan", "random_circuit", "circuit_from_gates", "build_network", "plan", "select_plan",
            "contract_pair", "contract_pair_noalloc", "Server", "TnError", "PREC", "version"]
 
 
@@ -220,6 +220,30 @@ def plan(network, num_sliced=-1, max_log2_intermediate=0, search_trials=0, seed=
     h = C.c_void_p()
     check(lib().tn_plan(network._h, C.byref(o), C.byref(h)))
     return Plan(h, network)
+
+
+def select_plan(network, bitstrings, seeds=(1, 2, 3, 4), probe_slices=32, precision="split_bf16", **plan_kw):
+    """The fastest of several plans, measured: plan the network once per seed
+    (keyword arguments as for plan()), contract the first probe_slices slices
+    of `bitstrings` with each plan (one untimed call to set the plan up, one
+    timed by the report's device time) and keep the plan with the shortest
+    time per slice.  Returns (plan, [(seed, ms per slice, plan hash), ...]).
+    The planner's model ranks plans only roughly on GB300 (its kernel rates
+    depend on shapes and layouts), so a few probes of real slices choose
+    better than the model alone."""
+    best, best_t, table = None, None, []
+    for seed in seeds:
+        p = plan(network, seed=seed, **plan_kw)
+        ns = min(probe_slices, p.info()["num_slices"])
+        p.contract_amplitudes(bitstrings, precision=precision, slice_count=ns)
+        _, rep = p.contract_amplitudes(bitstrings, precision=precision, slice_count=ns, report=True)
+        t = rep["device_ms"] / ns
+        table.append((seed, t, p.info()["hash"]))
+        if best_t is None or t < best_t:
+            best, best_t = p, t
+        else:
+            del p  # frees its device state
+    return best, table
 
 
 def contract_pair(A, a_labels, B, b_labels, Cout, c_labels, precision="c64", algo="auto", stream=None):

@@ -1,4 +1,5 @@
-// Bandwidth-bound contraction for vector-like steps (N <= 16 and K <= 16).
+// Bandwidth-bound contraction for vector-like steps (N <= 16 and K <= 16, or
+// N <= 8 and K <= 128).
 //
 // Paper: Sec. "Tensor Contraction Using Fused Permutation and
 // Multiplication", imbalanced case (a high-rank tensor against a rank-4 one):
@@ -96,6 +97,86 @@ __global__ void __launch_bounds__(NT) vector_kernel(const float2* __restrict__ A
   }
 }
 
+// Longer contracted index (K = 32..128) with a narrow B (N <= 8, N K <= 1024):
+// the same streaming layout, but each row's K values are consumed one at a
+// time into N running sums instead of being held in registers.
+template <int NK, int NN>
+__global__ void __launch_bounds__(NT) vector_long_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
+                                                         float2* __restrict__ C, const GemmDesc d) {
+  constexpr int K = 1 << NK, N = 1 << NN;
+  static_assert(K * N <= 1024, "B must fit in shared memory");
+  const int64_t M = int64_t(1) << d.nm;
+  const int64_t ulo = blockIdx.y % d.units_lo, uhi = blockIdx.y / d.units_lo;
+  A += ulo * d.a_lo + uhi * d.a_hi;
+  B += ulo * d.b_lo + uhi * d.b_hi;
+  C += ulo * d.c_lo + uhi * d.c_hi;
+  __shared__ float2 Bs[K * N];
+  __shared__ int32_t kA[K], nC[N];
+  __shared__ int32_t tAlo[32], tAhi[32], tClo[32], tChi[32];
+  __shared__ int32_t baseA, baseC;
+  const int tid = threadIdx.x;
+  const int64_t base = (int64_t)blockIdx.x * CH;
+  for (int e = tid; e < K * N; e += NT) {
+    const int k = e / N, n = e % N;
+    Bs[e] = B[bit_offset(k, NK, d.bk) + bit_offset(n, NN, d.bn)];
+  }
+  for (int k = tid; k < K; k += NT) kA[k] = bit_offset(k, NK, d.ak);
+  if (tid >= 192 && tid < 192 + N) nC[tid - 192] = bit_offset(tid - 192, NN, d.cn);
+  const int lb = d.nm < CH_BITS ? d.nm : CH_BITS;
+  if (tid >= 128 && tid < 160) {
+    const int x = tid - 128, b0 = lb < 5 ? lb : 5;
+    tAlo[x] = x < (1 << b0) ? bit_offset(x, b0, d.am) : 0;
+    tClo[x] = x < (1 << b0) ? bit_offset(x, b0, d.cm) : 0;
+  }
+  if (tid >= 160 && tid < 192) {
+    const int x = tid - 160, b1 = lb > 5 ? lb - 5 : 0;
+    tAhi[x] = x < (1 << b1) ? bit_offset(x, b1, d.am + 5) : 0;
+    tChi[x] = x < (1 << b1) ? bit_offset(x, b1, d.cm + 5) : 0;
+  }
+  if (tid == 0) {
+    int32_t oa = 0, oc = 0;
+    for (int i = CH_BITS; i < d.nm; ++i)
+      if ((base >> i) & 1) { oa += d.am[i]; oc += d.cm[i]; }
+    baseA = oa;
+    baseC = oc;
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int r = 0; r < PER; ++r) {
+    const int loc = tid + r * NT;
+    if (base + loc >= M) break;
+    const int32_t oa = baseA + tAlo[loc & 31] + tAhi[loc >> 5];
+    const int32_t oc = baseC + tClo[loc & 31] + tChi[loc >> 5];
+    float2 acc[N];
+#pragma unroll
+    for (int n = 0; n < N; ++n) acc[n] = make_float2(0.f, 0.f);
+#pragma unroll 8
+    for (int k = 0; k < K; ++k) {
+      const float2 a = __ldg(A + (int64_t)oa + kA[k]);
+#pragma unroll
+      for (int n = 0; n < N; ++n) {
+        const float2 b = Bs[k * N + n];
+        acc[n].x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc[n].x));
+        acc[n].y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc[n].y));
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < N; ++n) C[(int64_t)oc + nC[n]] = acc[n];
+  }
+}
+
+template <int NK>
+cudaError_t launch_long(const float2* A, const float2* B, float2* C, const GemmDesc& d, dim3 g, cudaStream_t s) {
+  switch (d.nn) {
+    case 0: vector_long_kernel<NK, 0><<<g, NT, 0, s>>>(A, B, C, d); break;
+    case 1: vector_long_kernel<NK, 1><<<g, NT, 0, s>>>(A, B, C, d); break;
+    case 2: vector_long_kernel<NK, 2><<<g, NT, 0, s>>>(A, B, C, d); break;
+    case 3: vector_long_kernel<NK, 3><<<g, NT, 0, s>>>(A, B, C, d); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 template <int NK>
 cudaError_t launch_nn(const float2* A, const float2* B, float2* C, const GemmDesc& d, dim3 g, cudaStream_t s) {
   switch (d.nn) {
@@ -111,10 +192,19 @@ cudaError_t launch_nn(const float2* A, const float2* B, float2* C, const GemmDes
 
 }  // namespace
 
+bool vector_shape_ok(const GemmDesc& d) { return (d.nn <= 4 && d.nk <= 4) || (d.nn <= 3 && d.nk <= 7); }
+
 cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s) {
-  if (d.nk > 4 || d.nn > 4 || d.units > 65535) return cudaErrorInvalidValue;
+  if (!vector_shape_ok(d) || d.units > 65535) return cudaErrorInvalidValue;
   int64_t M = int64_t(1) << d.nm;
   dim3 g((unsigned)((M + CH - 1) / CH), (unsigned)d.units);
+  if (d.nk > 4) {
+    switch (d.nk) {
+      case 5: return launch_long<5>(A, B, C, d, g, s);
+      case 6: return launch_long<6>(A, B, C, d, g, s);
+      default: return launch_long<7>(A, B, C, d, g, s);
+    }
+  }
   switch (d.nk) {
     case 0: return launch_nn<0>(A, B, C, d, g, s);
     case 1: return launch_nn<1>(A, B, C, d, g, s);

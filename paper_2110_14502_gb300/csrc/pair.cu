@@ -133,7 +133,7 @@ static bool d_is_vector(const std::vector<int>& la, const std::vector<int>& lb, 
   for (int l : la)
     if (std::find(lb.begin(), lb.end(), l) != lb.end()) ++nk;
   const int nn = (int)lb.size() - nk;
-  return nn <= 4 && nk <= 4;
+  return (nn <= 4 && nk <= 4) || (nn <= 3 && nk <= 7);
 }
 
 extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, int32_t ra, const void* B,
@@ -160,7 +160,7 @@ extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, in
   const float2* b = (const float2*)B;
   float2* c = (float2*)Cv;
   if (algo == TN_PAIR_AUTO) {
-    if (d.nn <= 4 && d.nk <= 4) algo = TN_PAIR_VECTOR;
+    if (vector_shape_ok(d)) algo = TN_PAIR_VECTOR;
     else if (reduce_shape_ok(d) && !(precision != TN_PREC_C64 && tc_shape_ok(d))) algo = TN_PAIR_REDUCE;
     else if (precision != TN_PREC_C64 && tc_shape_ok(d)) algo = TN_PAIR_FUSED_TC;
     else algo = TN_PAIR_FUSED_SIMT;
@@ -169,7 +169,8 @@ extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, in
   switch (algo) {
     case TN_PAIR_FUSED_SIMT: e = launch_gemm_simt(a, b, c, d, s); break;
     case TN_PAIR_VECTOR:
-      if (d.nn > 4 || d.nk > 4) return fail(TN_EINVAL, "tn_contract_pair: vector kernel needs N, K <= 16");
+      if (!vector_shape_ok(d))
+        return fail(TN_EINVAL, "tn_contract_pair: the vector kernel needs N, K <= 16 or N <= 8, K <= 128");
       e = launch_vector(a, b, c, d, s);
       break;
     case TN_PAIR_UNFUSED: return unfused(a, b, c, d, s);

@@ -672,7 +672,8 @@ tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& P) {
     S.nk = (int)(S.la.size() + S.lb.size() - S.lc.size()) / 2;
     S.nm = (int)S.la.size() - S.nk;
     S.nn = (int)S.lb.size() - S.nk;
-    S.klass = (S.nn <= 4 && S.nk <= 4) ? SC_VECTOR : SC_SIMT;
+    // bandwidth-bound streaming kernel: N <= 16 with K <= 16, or N <= 8 with K <= 128
+    S.klass = ((S.nn <= 4 && S.nk <= 4) || (S.nn <= 3 && S.nk <= 7)) ? SC_VECTOR : SC_SIMT;
     int d = dep[S.a] | dep[S.b];
     dep[L + p / 2] = d;
     S.variant = d != 0;

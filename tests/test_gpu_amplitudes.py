@@ -386,3 +386,23 @@ def test_autotune_choices_persist_in_the_cache_file(tmp_path, monkeypatch):
     t2 = p2.contract_amplitudes(words, precision="split_bf16", autotune=1, stream=s)
     assert np.array_equal(t2, base)
     assert cache.read_text().split() == lines  # read, not tuned again
+
+
+def test_select_plan_keeps_the_fastest_probe_and_its_amplitudes():
+    """Measured plan choice: every candidate is timed on the same probe, the
+    one with the shortest time per slice is returned, and its amplitudes over
+    all slices match the state vector."""
+    T = tnlib()
+    rows, cols, depth, seed, open_q = 4, 5, 14, 12, (16, 17, 18, 19)
+    n = rows * cols
+    net = T.build_network(T.random_circuit(rows, cols, depth, seed), list(open_q))
+    words = I.bitstrings(n, 2, seed)
+    best, table = T.select_plan(net, words, seeds=(1, 2, 3), probe_slices=8, precision="c64", num_sliced=5,
+                                search_trials=16)
+    assert len(table) == 3
+    fastest = min(table, key=lambda r: r[1])
+    assert best.info()["hash"] == fastest[2]
+    got = best.contract_amplitudes(words)
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    ref = SV.amplitudes(SV.simulate(gates, n), n, [I.bits_of(w, n) for w in words], open_q)
+    assert rel(got, ref) <= 1e-5

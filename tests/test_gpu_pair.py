@@ -52,12 +52,17 @@ def test_pair_c64_matches_fp64(nm, nn, nk, algo):
     assert err <= 1e-5, err
 
 
-@pytest.mark.parametrize("nm,nn,nk", [(0, 0, 0), (5, 1, 3), (12, 4, 4), (18, 2, 2), (20, 4, 2)])
+@pytest.mark.parametrize("nm,nn,nk", [(0, 0, 0), (5, 1, 3), (12, 4, 4), (18, 2, 2), (20, 4, 2),
+                                      (3, 3, 5), (11, 3, 5), (13, 2, 6), (9, 0, 7), (16, 3, 7), (10, 1, 6)])
 def test_vector_kernel_matches_fp64(nm, nn, nk):
+    """Streaming kernel: N, K <= 16 with the row's K values in registers, and
+    N <= 8 with K up to 128 consumed into running sums; ragged M below one
+    CTA's 1024 rows included."""
     T = tnlib()
-    la, lb, lc, A, B, ref = _case(nm, nn, nk, seed=7 + nm)
-    got = _run(T, la, lb, lc, A, B, "vector")
-    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+    la, lb, lc, A, B, ref = _case(nm, nn, nk, seed=7 + nm + nk)
+    for algo in ("vector", "auto"):
+        got = _run(T, la, lb, lc, A, B, algo)
+        assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref), algo
 
 
 @pytest.mark.parametrize("nm,nn,nk", [(0, 0, 8), (4, 2, 12), (2, 4, 9), (6, 0, 10), (0, 6, 8), (3, 3, 14),
