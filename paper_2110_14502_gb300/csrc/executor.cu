@@ -23,6 +23,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "kernels.h"
@@ -108,9 +109,9 @@ struct Executor {
   int64_t* flagged = nullptr;  // (b << 32 | s) of units kept out of the sum
   unsigned long long* nflagged = nullptr;
   GroupInfo* gslot = nullptr;  // [2]: group of the slice-only launches, group of the per-unit launches
-  // replayable launch sequences, keyed by (phase, precision, Gs, Gb); dropped
-  // whenever a buffer they reference is reallocated
-  struct Graph { int phase, precision, gs, gb; cudaGraphExec_t exec; int64_t kernels; };
+  // replayable launch sequences, keyed by (phase, precision, plane handover,
+  // Gs, Gb); dropped whenever a buffer they reference is reallocated
+  struct Graph { int phase, precision, handover, gs, gb; cudaGraphExec_t exec; int64_t kernels; };
   std::vector<Graph> graphs;
   // autotuner choices per (precision, step): tensor-core tile width, raster group
   struct Tune { int precision, step, tile_n, group_m, persistent; };
@@ -149,6 +150,40 @@ void destroy_executor(Executor* e) {
   for (auto ev : e->pev) cudaEventDestroy(ev);
   if (cur >= 0) cudaSetDevice(cur);
   delete e;
+}
+
+// Host-side fault injection for the tests: with TN_FAULT_ALLOC=k set, the
+// k-th device allocation of the executor made since the variable took its
+// current value fails as if the device were out of memory.  Every call that
+// allocates checks the variable, so a test can set and clear it between calls.
+cudaError_t dev_alloc(void** p, size_t bytes) {
+  static std::mutex mu;
+  static std::string last;
+  static long count = 0;
+  const char* v = getenv("TN_FAULT_ALLOC");
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (!v) {
+      last.clear();
+    } else {
+      if (last != v) {
+        last = v;
+        count = 0;
+      }
+      if (++count == atol(v)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t bytes) {
+  void* q = nullptr;
+  const cudaError_t e = dev_alloc(&q, bytes);
+  *p = static_cast<T*>(q);
+  return e;
 }
 
 #define CK(call)                                                                                       \
@@ -207,7 +242,7 @@ static tn_status upload_leaves(const Plan& P, float2** store) {
     for (size_t e = 0; e < lf.data.size(); ++e)
       h_store[P.leaf_use[i].store_off + e] = make_float2((float)lf.data[e].real(), (float)lf.data[e].imag());
   }
-  CK(cudaMalloc(store, h_store.size() * sizeof(float2)));
+  CK(dev_alloc(store, h_store.size() * sizeof(float2)));
   CK(cudaMemcpy(*store, h_store.data(), h_store.size() * sizeof(float2), cudaMemcpyHostToDevice));
   return TN_OK;
 }
@@ -230,7 +265,7 @@ static tn_status acquire_stem(const Plan& P, int device, std::shared_ptr<Stem>& 
   st->hash = P.hash;
   tn_status r = upload_leaves(P, &st->store);
   if (r != TN_OK) return r;
-  CK(cudaMalloc(&st->inv, std::max<int64_t>(P.invariant_elems, 1) * sizeof(float2)));
+  CK(dev_alloc(&st->inv, std::max<int64_t>(P.invariant_elems, 1) * sizeof(float2)));
   CK(cudaEventCreateWithFlags(&st->ready, cudaEventDisableTiming));
   st->bytes = 8 * (std::max<int64_t>(P.leaf_store_elems, 1) + std::max<int64_t>(P.invariant_elems, 1));
   ++C.misses;
@@ -264,7 +299,7 @@ static tn_status setup(Plan& P, Executor& E) {
   } else {
     tn_status r = upload_leaves(P, &E.store);
     if (r != TN_OK) return r;
-    CK(cudaMalloc(&E.inv, std::max<int64_t>(P.invariant_elems, 1) * sizeof(float2)));
+    CK(dev_alloc(&E.inv, std::max<int64_t>(P.invariant_elems, 1) * sizeof(float2)));
   }
   std::vector<LeafGather> g1, g2;
   for (int i = 0; i < L; ++i) {
@@ -288,21 +323,21 @@ static tn_status setup(Plan& P, Executor& E) {
   E.ngather2 = (int)g2.size();
   g1.insert(g1.end(), g2.begin(), g2.end());
   if (!g1.empty()) {
-    CK(cudaMalloc(&E.gather, g1.size() * sizeof(LeafGather)));
+    CK(dev_alloc(&E.gather, g1.size() * sizeof(LeafGather)));
     CK(cudaMemcpy(E.gather, g1.data(), g1.size() * sizeof(LeafGather), cudaMemcpyHostToDevice));
   }
-  CK(cudaMalloc(&E.perm, P.root_perm.size() * sizeof(int64_t)));
+  CK(dev_alloc(&E.perm, P.root_perm.size() * sizeof(int64_t)));
   CK(cudaMemcpy(E.perm, P.root_perm.data(), P.root_perm.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
   E.desc.resize(P.steps.size());
   for (size_t s = 0; s < P.steps.size(); ++s)
     make_gemm_desc(P.steps[s].la, P.steps[s].lb, P.steps[s].lc, E.desc[s], P.steps[s].klass == SC_VECTOR);
   CK(cudaEventCreate(&E.ev0));
   CK(cudaEventCreate(&E.ev1));
-  CK(cudaMalloc(&E.err, sizeof(int)));
+  CK(dev_alloc(&E.err, sizeof(int)));
   CK(cudaMemset(E.err, 0, sizeof(int)));
-  CK(cudaMalloc(&E.flagged, kFlaggedCap * sizeof(int64_t)));
-  CK(cudaMalloc(&E.gslot, 2 * sizeof(GroupInfo)));
-  CK(cudaMalloc(&E.nflagged, sizeof(unsigned long long)));
+  CK(dev_alloc(&E.flagged, kFlaggedCap * sizeof(int64_t)));
+  CK(dev_alloc(&E.gslot, 2 * sizeof(GroupInfo)));
+  CK(dev_alloc(&E.nflagged, sizeof(unsigned long long)));
   return TN_OK;
 }
 
@@ -609,12 +644,19 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
   Gs = std::max<int64_t>(1, std::min<int64_t>(Gs, std::max<int64_t>(ns, 1)));
   Gs = std::min<int64_t>(Gs, 65535 / Gb);
   if (Gs < 1) return fail(TN_EINVAL, "tn_contract_amplitudes: launch geometry does not fit");
+  // captured launch sequences hold the addresses of the arenas, the scale
+  // pool and the operand scratch: replacing any of them invalidates them all
+  auto drop_graphs = [&]() {
+    for (auto& gr : E.graphs) cudaGraphExecDestroy(gr.exec);
+    E.graphs.clear();
+  };
   auto grow = [&](float2*& p, int64_t& cap, int64_t need) -> tn_status {
     if (cap >= need) return TN_OK;
+    drop_graphs();
     cudaFree(p);
     p = nullptr;
     cap = 0;
-    cudaError_t ae = cudaMalloc(&p, (size_t)need * sizeof(float2));
+    cudaError_t ae = dev_alloc(&p, (size_t)need * sizeof(float2));
     if (ae != cudaSuccess) {
       cudaGetLastError();
       return fail(TN_EHBM, "tn_contract_amplitudes: %lld-byte arena does not fit in device memory",
@@ -635,14 +677,14 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
       cudaFree(E.bits);
       E.bits = nullptr;
       E.bits_cap = 0;
-      CK(cudaMalloc(&E.bits, std::max<int64_t>(nb * words, 1) * sizeof(uint64_t)));
+      CK(dev_alloc(&E.bits, std::max<int64_t>(nb * words, 1) * sizeof(uint64_t)));
       E.bits_cap = nb * words;
     }
     if (E.acc_cap < nout) {
       cudaFree(E.acc);
       E.acc = nullptr;
       E.acc_cap = 0;
-      CK(cudaMalloc(&E.acc, std::max<int64_t>(nout, 1) * sizeof(double2)));
+      CK(dev_alloc(&E.acc, std::max<int64_t>(nout, 1) * sizeof(double2)));
       E.acc_cap = nout;
     }
     d_bits = E.bits;
@@ -681,10 +723,11 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
     const int64_t ns_ = (int64_t)P.steps.size();
     const int64_t need = 8 * ns_ * c.U + 2 * 12 * c.U + 4 * (Gs + c.U) + 256;
     if (E.spool_cap < need) {
+      drop_graphs();
       cudaFree(E.spool);
       E.spool = nullptr;
       E.spool_cap = 0;
-      CK(cudaMalloc(&E.spool, need));
+      CK(dev_alloc(&E.spool, need));
       E.spool_cap = need;
     }
     uint8_t* q = E.spool;
@@ -747,12 +790,11 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
       }
     c.sizing = false;
     if (c.scratch_need > E.scratch_cap) {
+      drop_graphs();
       cudaFree(E.scratch);
       E.scratch = nullptr;
       E.scratch_cap = 0;
-      for (auto& gr : E.graphs) cudaGraphExecDestroy(gr.exec);
-      E.graphs.clear();
-      if (cudaMalloc(&E.scratch, (size_t)c.scratch_need * sizeof(uint16_t)) != cudaSuccess) {
+      if (dev_alloc(&E.scratch, (size_t)c.scratch_need * sizeof(uint16_t)) != cudaSuccess) {
         cudaGetLastError();
         return fail(TN_EHBM, "tn_contract_amplitudes: %lld bytes of operand planes do not fit",
                     (long long)(c.scratch_need * 2));
@@ -821,7 +863,8 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
     };
     if (!graphs || c.tuning) return body();
     for (auto& gr : E.graphs)
-      if (gr.phase == phase && gr.precision == c.precision && gr.gs == gg.gs && gr.gb == (phase == 2 ? gg.gb : 1)) {
+      if (gr.phase == phase && gr.precision == c.precision && gr.handover == (int)handover && gr.gs == gg.gs &&
+          gr.gb == (phase == 2 ? gg.gb : 1)) {
         CK(cudaGraphLaunch(gr.exec, st));
         c.launches += gr.kernels;
         return TN_OK;
@@ -840,7 +883,7 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
     ce = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) return fail(TN_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
-    E.graphs.push_back({phase, c.precision, gg.gs, phase == 2 ? gg.gb : 1, exec, c.launches - before});
+    E.graphs.push_back({phase, c.precision, (int)handover, gg.gs, phase == 2 ? gg.gb : 1, exec, c.launches - before});
     CK(cudaGraphLaunch(exec, st));
     return TN_OK;
   };
@@ -954,7 +997,10 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
     rep->kernel_launches = c.launches;
     rep->flagged_units = nflag;
     rep->discarded_units = discarded;
-    // TN_PROFILE_STEPS=1: per-step breakdown of the timed launches on stderr
+    // TN_PROFILE_STEPS=1: per-step breakdown of the timed launches on stderr,
+    // one JSON object per step, slowest first.  c_fastest lists C's four
+    // fastest indices (stride 8, 4, 2, 1) as three-digit codes: row bit i ->
+    // i, column bit j -> 100 + j, none -> 999.
     struct StepAgg { int klass = 0, nm = 0, nn = 0, nk = 0, launches = 0, planes = 0, n16 = 0, ulo = 0, uhi = 0; long long cfast = 0; int64_t units = 0; double ms = 0, flops = 0; };
     std::map<int, StepAgg> per_step;
     const bool by_step = getenv("TN_PROFILE_STEPS") != nullptr;
@@ -985,12 +1031,15 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
     if (by_step) {
       std::vector<std::pair<int, StepAgg>> v(per_step.begin(), per_step.end());
       std::sort(v.begin(), v.end(), [](const auto& x, const auto& y) { return x.second.ms > y.second.ms; });
+      static const char* kname[4] = {"simt", "vector", "tensor", "split"};
       for (auto& [st_i, a] : v)
         fprintf(stderr,
-                "step %d phase %d class %d M 2^%d N 2^%d K 2^%d units %lld launches %d ms %.3f tflops %.1f "
-                "cfast %012lld planes %d n16 %d ulo %d uhi %d\n",
-                st_i, P.steps[st_i].phase, a.klass, a.nm, a.nn, a.nk, (long long)a.units, a.launches, a.ms,
-                a.ms > 0 ? a.flops / (a.ms * 1e9) : 0.0, a.cfast, a.planes, a.n16, a.ulo, a.uhi);
+                "{\"step\": %d, \"phase\": %d, \"class\": \"%s\", \"log2_m\": %d, \"log2_n\": %d, "
+                "\"log2_k\": %d, \"units\": %lld, \"launches\": %d, \"ms\": %.3f, \"tflops\": %.1f, "
+                "\"c_fastest\": \"%012lld\", \"planes_out\": %d, \"vec16\": %d, \"a_b_vary_lo\": %d, "
+                "\"a_b_vary_hi\": %d}\n",
+                st_i, P.steps[st_i].phase, kname[a.klass & 3], a.nm, a.nn, a.nk, (long long)a.units, a.launches,
+                a.ms, a.ms > 0 ? a.flops / (a.ms * 1e9) : 0.0, a.cfast, a.planes, a.n16, a.ulo, a.uhi);
     }
   }
   (void)recomputed;

@@ -406,3 +406,52 @@ def test_select_plan_keeps_the_fastest_probe_and_its_amplitudes():
     gates = OC.random_circuit(rows, cols, depth, seed)
     ref = SV.amplitudes(SV.simulate(gates, n), n, [I.bits_of(w, n) for w in words], open_q)
     assert rel(got, ref) <= 1e-5
+
+
+def test_graphs_follow_buffer_and_handover_changes():
+    """Replayed launch sequences hold buffer addresses: a call that needs
+    larger arenas (more bitstrings) replaces the buffers and the recorded
+    sequences with them, and the plane handover is part of a sequence's key.
+    Every graph-replayed result equals the direct launches."""
+    T = tnlib()
+    import torch
+    rows, cols, depth, seed, open_q = 4, 5, 14, 12, (14, 15, 16, 17, 18, 19)
+    n = rows * cols
+    p = _setup(T, rows, cols, depth, seed, open_q, num_sliced=3, search_trials=32, seed=3)
+    s = torch.cuda.Stream()
+    for nb in (1, 3, 1, 2, 3, 1):
+        words = I.bitstrings(n, nb, seed + nb)
+        base = p.contract_amplitudes(words, precision="split_bf16", units_per_group=3, stream=s)
+        g = p.contract_amplitudes(words, precision="split_bf16", units_per_group=3, use_graph=1, stream=s)
+        assert np.array_equal(g, base), nb
+    words = I.bitstrings(n, 2, seed)
+    for ho in (1, 2, 1, 2):
+        base = p.contract_amplitudes(words, precision="scaled_fp16", handover=ho, stream=s)
+        g = p.contract_amplitudes(words, precision="scaled_fp16", handover=ho, use_graph=1, stream=s)
+        assert np.array_equal(g, base), ho
+
+
+def test_failed_device_allocations_report_errors_and_recover(monkeypatch):
+    """Host-side fault injection (TN_FAULT_ALLOC=k fails the executor's k-th
+    device allocation): every failure point returns an error status instead
+    of crashing, and the same plan then contracts correctly once allocations
+    succeed again."""
+    T = tnlib()
+    rows, cols, depth, seed, open_q = 4, 4, 10, 5, (15, 14)
+    n = rows * cols
+    words = I.bitstrings(n, 2, seed)
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    ref = SV.amplitudes(SV.simulate(gates, n), n, [I.bits_of(w, n) for w in words], open_q)
+    failures = 0
+    for k in range(1, 25):
+        p = _setup(T, rows, cols, depth, seed, open_q, num_sliced=4, search_trials=16, seed=3)
+        monkeypatch.setenv("TN_FAULT_ALLOC", f"{k}")
+        try:
+            p.contract_amplitudes(words, precision="split_bf16")
+        except T.TnError as e:
+            assert e.status in (3, 4), e   # TN_EHBM or TN_ECUDA
+            failures += 1
+        monkeypatch.delenv("TN_FAULT_ALLOC")
+        got = p.contract_amplitudes(words, precision="split_bf16")
+        assert rel(got, ref) <= 1e-4, k
+    assert failures >= 8

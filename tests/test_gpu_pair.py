@@ -77,6 +77,38 @@ def test_reduction_kernel_matches_fp64(nm, nn, nk):
         assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref), algo
 
 
+@pytest.mark.parametrize("order", ["identity", "reversed", "interleaved"])
+@pytest.mark.parametrize("algo,precision,tol", [("fused_simt", "c64", 1e-5), ("fused_tc", "split_bf16", 1e-4),
+                                                ("vector", "c64", 1e-5)])
+def test_permutation_corner_cases(order, algo, precision, tol):
+    """Operand and output orders: identity (contracted indices innermost, free
+    indices in order), fully reversed, and contracted indices interleaved with
+    free ones."""
+    T = tnlib()
+    import torch
+    nm, nn, nk = (9, 4, 3) if algo == "vector" else (9, 6, 5)
+    M, N, K = list(range(nm)), list(range(nm, nm + nn)), list(range(nm + nn, nm + nn + nk))
+    if order == "identity":
+        la, lb, lc = M + K, N + K, M + N
+    elif order == "reversed":
+        la, lb, lc = (K + M)[::-1], (K + N)[::-1], (N + M)[::-1]
+    else:
+        la = [x for pair in zip(M, K) for x in pair] + M[len(K):]
+        lb = [x for pair in zip(K, N) for x in pair] + N[len(K):] + K[len(N):]
+        lc = [x for pair in zip(N, M) for x in pair] + M[len(N):]
+    A = I.random_tensor(len(la), 41).astype(np.complex64)
+    B = I.random_tensor(len(lb), 42).astype(np.complex64)
+    sub = lambda ls: "".join(LETTERS[x] for x in ls)
+    ref = np.einsum(f"{sub(la)},{sub(lb)}->{sub(lc)}", A.astype(np.complex128).reshape((2,) * len(la)),
+                    B.astype(np.complex128).reshape((2,) * len(lb))).reshape(-1)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.empty(1 << len(lc), dtype=torch.complex64, device="cuda")
+    T.contract_pair(dA, la, dB, lb, dC, lc, precision=precision, algo=algo)
+    torch.cuda.synchronize()
+    got = dC.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref), order
+
+
 def test_pair_rejects_bad_labels():
     T = tnlib()
     import torch
