@@ -150,6 +150,11 @@ typedef struct {
                                     against the slice-only ones (run once per slice); 0 = 1 */
   uint64_t seed;                 /* search seed; equal inputs + seed give byte-identical plans */
   double max_log2_cmac;          /* cost cap on total complex MACs (log2); 0 = none -> TN_ETOOBIG when exceeded */
+  int32_t order_generator;       /* 0: randomized greedy + graph bisection (default); 1: PEPS-style
+                                    lattice sweep (each grid column merged in time order, then the
+                                    columns absorbed from one side; trials cycle through the four
+                                    sweep directions), Sec. "A PEPS-based Simulation Method ..." */
+  int32_t reserved2;
 } tn_plan_opts;
 
 typedef struct {

@@ -87,6 +87,7 @@ extern "C" tn_status tn_random_circuit(int32_t rows, int32_t cols, int32_t depth
   if (!h) return fail(TN_ENOMEM, "tn_random_circuit: out of host memory");
   Circuit& C = h->c;
   C.n = rows * cols;
+  C.cols = cols;
   uint64_t s = seed;
   std::vector<int> prev(C.n, -1);
   auto one_qubit_layer = [&]() {

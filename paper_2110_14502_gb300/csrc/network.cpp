@@ -53,6 +53,7 @@ tn_status build_network(const Circuit& c, const int32_t* open, int num_open, Net
   const int n = c.n;
   net = Network();
   net.n = n;
+  net.cols = c.cols;
   net.num_gates = (int)c.gates.size();
   net.open_qubits.assign(open, open + num_open);
   std::vector<int> seg(n, 0), cur(n, -1);

@@ -19,6 +19,7 @@
 #include <functional>
 #include <numeric>
 #include <random>
+#include <tuple>
 
 #include "tn_internal.h"
 
@@ -258,6 +259,42 @@ int bisect_tree(Builder& B, const std::vector<int>& ids, int cutoff, double eps,
   int a = bisect_tree(B, s0, cutoff, eps, alpha, rng);
   int b = bisect_tree(B, s1, cutoff, eps, alpha, rng);
   return B.join(a, b);
+}
+
+// PEPS-style lattice order (Sec. "A PEPS-based Simulation Method with an
+// Optimized Slicing Strategy"): a leaf sits at the grid site of the lowest
+// qubit among its wires and at the earliest time step; the leaves of every
+// grid column (or row) are merged one after another in (row, time) order into
+// one boundary tensor of that line, and the lines are then absorbed one by one
+// from one side of the grid to the other.  variant: bit 0 sweeps rows instead
+// of columns, bit 1 starts from the far side.
+int lattice_join(Builder& B, const Network& net, int variant) {
+  const int L = (int)net.leaves.size();
+  const int cols = net.cols > 0 ? net.cols : std::max(net.n, 1);
+  std::vector<std::tuple<int, int, int, int>> key;  // (line, position along it, time, leaf)
+  for (int i = 0; i < L; ++i) {
+    int q = net.n, t = 1 << 30;
+    for (int l : net.leaves[i].labels) {
+      q = std::min(q, net.wire[l].first);
+      t = std::min(t, net.wire[l].second);
+    }
+    if (q >= net.n) q = 0;
+    const int r = q / cols, c = q % cols;
+    int line = (variant & 1) ? r : c, pos = (variant & 1) ? c : r;
+    if (variant & 2) line = -line;
+    key.emplace_back(line, pos, t, i);
+  }
+  std::sort(key.begin(), key.end());
+  int acc = -1;
+  for (size_t i = 0; i < key.size();) {
+    int col = -1;
+    size_t j = i;
+    for (; j < key.size() && std::get<0>(key[j]) == std::get<0>(key[i]); ++j)
+      col = col < 0 ? std::get<3>(key[j]) : B.join(col, std::get<3>(key[j]));
+    acc = acc < 0 ? col : B.join(acc, col);
+    i = j;
+  }
+  return acc;
 }
 
 struct Eval {
@@ -566,7 +603,9 @@ tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& P) {
   for (int t = 0; t < (L == 1 ? 1 : trials); ++t) {
     Builder B(leaves);
     std::mt19937_64 r2(rng());
-    if (L > 1) {
+    if (L > 1 && opts.order_generator == 1) {
+      lattice_join(B, net, t % 4);
+    } else if (L > 1) {
       if (t % 2 == 0) {
         double alpha = std::uniform_real_distribution<double>(0.0, 1.5)(r2);
         const double taus[] = {0.0, 0.01, 0.05, 0.1, 0.3, 1.0};

@@ -26,6 +26,7 @@ struct Gate {
 
 struct Circuit {
   int n = 0;
+  int cols = 0;  // grid width of a generated circuit (qubit q at row q / cols, column q % cols); 0 = unknown
   std::vector<Gate> gates;
 };
 
@@ -43,6 +44,7 @@ struct Leaf {
 
 struct Network {
   int n = 0;
+  int cols = 0;  // grid width of the circuit, 0 = unknown
   int num_gates = 0;
   std::vector<int> open_qubits;
   std::vector<Leaf> leaves;

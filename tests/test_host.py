@@ -129,3 +129,21 @@ def test_library_exports_every_declared_symbol():
     for nm in sorted(names):
         assert hasattr(h, nm), nm
     assert names <= set(_abi.SIGNATURES), names - set(_abi.SIGNATURES)
+
+
+@pytest.mark.parametrize("rows,cols,depth,seed,open_q", [(3, 4, 8, 2, (10, 11)), (4, 4, 8, 1, ())])
+def test_lattice_order_generator(rows, cols, depth, seed, open_q):
+    """The PEPS-style lattice sweep (order_generator=1) gives a valid tree --
+    its oracle replay equals the state vector -- and on these random fSim
+    circuits costs at least as many complex MACs as the default search."""
+    T = tnlib()
+    n = rows * cols
+    bits = I.bits_of(I.bitstrings(n, 1, seed)[0], n)
+    v, gates, p = _oracle_replay(T, rows, cols, depth, seed, open_q, bits, search_trials=4, seed=1,
+                                 order_generator=1)
+    ref = SV.amplitudes(SV.simulate(gates, n), n, [bits], open_q)[0]
+    assert np.linalg.norm(v - ref) <= 1e-12 * np.linalg.norm(ref)
+    _, _, p0 = _plan(T, rows, cols, depth, seed, open_q, search_trials=64, seed=1)
+    assert p.info()["log2_cmac_total"] >= p0.info()["log2_cmac_total"] - 1e-9
+    _, _, p2 = _plan(T, rows, cols, depth, seed, open_q, search_trials=4, seed=1, order_generator=1)
+    assert p2.info()["hash"] == p.info()["hash"]
