@@ -222,7 +222,8 @@ typedef struct {
   int32_t reserved3;
 } tn_exec_opts;
 
-/* Kernel classes of the per-class report figures. */
+/* Kernel classes of the per-class report figures: FP32 GEMM, bandwidth-bound
+ * streaming and reduction kernels, tensor-core GEMMs, operand split passes. */
 enum { TN_KCLASS_GEMM_SIMT = 0, TN_KCLASS_VECTOR = 1, TN_KCLASS_GEMM_TC = 2, TN_KCLASS_SPLIT = 3 };
 
 typedef struct {
@@ -244,7 +245,9 @@ typedef struct {
  * bitstrings: nb * ceil(n/64) uint64 words; out: nb * 2^k complex128.  Both
  * live on the host (device_io = 0) or the device (device_io = 1).  The call
  * is synchronous for host I/O; for device I/O it returns once work is queued
- * on opts->stream.  report may be NULL. */
+ * on opts->stream, except that the scaled precisions (their filter reads the
+ * count of flagged units) and a non-NULL report wait for the device.  report
+ * may be NULL. */
 tn_status tn_contract_amplitudes(tn_plan_t* p, const uint64_t* bitstrings, int64_t nb, double* out,
                                  const tn_exec_opts* opts, tn_report* report);
 
