@@ -13,9 +13,15 @@
 // Device memory of a plan (allocated on first use, kept until tn_free_plan):
 //   leaf store   -- every leaf tensor in complex64, full (fixed indices included)
 //   invariant    -- outputs of phase-0 steps
+//                   (these two come from the server's stem cache when the plan
+//                   is a serving copy: shared by the plans of one circuit)
 //   slice arena  -- Gs slices x per-slice arena (phase-1 leaves and outputs)
 //   pair arena   -- Gs x Gb units x per-unit arena (phase-2 leaves and outputs)
 //   accumulator  -- nb x 2^k complex128 (host I/O; device I/O sums into `out`)
+//   scratch      -- 16-bit operand planes of the tensor-core steps
+//   scale pool   -- exponents, maxima and flags of the scaled precisions
+// The arenas, scratch and pool only grow; growing one drops the recorded
+// CUDA graphs, which hold their addresses.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
