@@ -147,3 +147,18 @@ def test_lattice_order_generator(rows, cols, depth, seed, open_q):
     assert p.info()["log2_cmac_total"] >= p0.info()["log2_cmac_total"] - 1e-9
     _, _, p2 = _plan(T, rows, cols, depth, seed, open_q, search_trials=4, seed=1, order_generator=1)
     assert p2.info()["hash"] == p.info()["hash"]
+
+
+def test_planner_options_default_to_the_plain_search():
+    """bitstrings_hint 0 and 1 and order_generator 0 are the plain search:
+    the same plan bytes as the defaults; a hint above 1 may change the plan
+    but keeps it valid."""
+    T = tnlib()
+    c = T.random_circuit(5, 5, 12, 3)
+    net = T.build_network(c, [20, 21, 22])
+    base = T.plan(net, num_sliced=4, search_trials=16, seed=2)
+    for kw in (dict(bitstrings_hint=0), dict(bitstrings_hint=1), dict(order_generator=0)):
+        p = T.plan(net, num_sliced=4, search_trials=16, seed=2, **kw)
+        assert p.serialize() == base.serialize(), kw
+    p4 = T.plan(net, num_sliced=4, search_trials=16, seed=2, bitstrings_hint=4)
+    assert p4.info()["num_sliced"] == 4 and p4.info()["num_qubits"] == 25
