@@ -32,8 +32,8 @@
 // back to its empty barrier; warp 2 owns the TMEM allocation; warps 4-7 read
 // the accumulators (tcgen05.ld) and write complex64 C through per-row and
 // per-column offsets (the output permutation).  Every wait is bounded: on
-// expiry the CTA records an error code, stops issuing work, drains what it
-// issued and releases its TMEM.
+// expiry the CTA records an error code, stops issuing work, lets its issued
+// MMAs complete (bounded) and releases its TMEM.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
