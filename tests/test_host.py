@@ -162,3 +162,17 @@ def test_planner_options_default_to_the_plain_search():
         assert p.serialize() == base.serialize(), kw
     p4 = T.plan(net, num_sliced=4, search_trials=16, seed=2, bitstrings_hint=4)
     assert p4.info()["num_sliced"] == 4 and p4.info()["num_qubits"] == 25
+
+
+def test_bench_workload_plan_is_reproducible():
+    """The planner is deterministic host code: the bench's 6x6 workload plans
+    to the same tree, hash and work on any host (the hash and the work below
+    are the ones the bench reports on the GPU machine's Arm host)."""
+    import bench
+    T = tnlib()
+    _, _, p, words, open_q, _ = bench.make_workload(T, 0)
+    info = p.info()
+    assert hex(info["hash"]) == "0x3e0860a7cb099543"
+    assert round(float(np.log2(info["cmac_per_slice"])), 3) == 36.525
+    assert info["num_slices"] == 1024 and info["max_log2_intermediate"] == 26
+    assert words.shape[0] == bench.NBATCH and open_q == list(range(30, 36))
