@@ -53,7 +53,8 @@ typedef enum {
   TN_ETOOBIG = 6,     /* the plan's cost exceeds the caller's cap */
   TN_EOVERFLOW = 7,   /* a scaled low-precision slice over/underflowed and the policy forbids recompute */
   TN_ENOTREADY = 8,   /* a serving request has not completed yet */
-  TN_ENODEVICE = 9    /* no usable sm_103 device */
+  TN_ENODEVICE = 9,   /* no usable sm_103 device */
+  TN_EINTERNAL = 10   /* unexpected host-side failure inside the library; the message names it */
 } tn_status;
 
 /* Human-readable description of the last error on this thread. */
@@ -242,7 +243,8 @@ typedef struct {
 
 /* Sums, over the slice range, the contraction of every bitstring's network:
  *   out[b*2^k + j] = sum_{s in range} C_{b,s}[j]   (complex128, (re, im))
- * bitstrings: nb * ceil(n/64) uint64 words; out: nb * 2^k complex128.  Both
+ * bitstrings: nb * ceil(n/64) uint64 words; out: nb * 2^k complex128, with
+ * nb * 2^k <= 2^40 (TN_EINVAL above).  Both
  * live on the host (device_io = 0) or the device (device_io = 1).  The call
  * is synchronous for host I/O; for device I/O it returns once work is queued
  * on opts->stream, except that the scaled precisions (their filter reads the
@@ -280,7 +282,7 @@ typedef struct {
   int32_t rows, cols, depth;
   int32_t num_open;              /* 0 .. 12 */
   uint64_t seed;
-  int64_t nb;                    /* >= 1 */
+  int64_t nb;                    /* 1 .. 2^24 */
   const uint64_t* bitstrings;    /* host, nb * ceil(n/64) words; copied by tn_submit */
   int32_t precision;             /* TN_PREC_*; -1 = the server default */
   int32_t reserved;
@@ -306,7 +308,7 @@ typedef struct {
   double slice_fraction;         /* slices served / 2^S: the expected fidelity of the amplitudes */
 } tn_request_stats;
 
-/* Creates a server on the current CUDA device with a planner thread and a
+/* Creates a server on the current CUDA device with planner threads and a
  * scheduler thread.  Requests are admitted in arrival order when an in-flight
  * slot is free and their estimated device footprint fits the budget; admitted
  * requests advance one quantum of slices per turn each, on their own streams.

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libtn.so")
 
 TN_OK = 0
 STATUS = {0: "TN_OK", 1: "TN_EINVAL", 2: "TN_ENOMEM", 3: "TN_EHBM", 4: "TN_ECUDA", 5: "TN_ETIMEOUT",
-          6: "TN_ETOOBIG", 7: "TN_EOVERFLOW", 8: "TN_ENOTREADY", 9: "TN_ENODEVICE"}
+          6: "TN_ETOOBIG", 7: "TN_EOVERFLOW", 8: "TN_ENOTREADY", 9: "TN_ENODEVICE", 10: "TN_EINTERNAL"}
 GATE_KINDS = {"sqrtx": 0, "sqrty": 1, "sqrtw": 2, "fsim": 3, "mat1": 4, "mat2": 5}
 PREC = {"c64": 0, "split_bf16": 1, "split_fp16": 2, "scaled_fp16": 3, "scaled_bf16": 4}
 PAIR_ALGO = {"auto": 0, "fused_simt": 1, "vector": 2, "fused_tc": 3, "unfused": 4, "gather_tc": 5, "reduce": 6}

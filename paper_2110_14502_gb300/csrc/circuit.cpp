@@ -81,10 +81,10 @@ extern "C" const char* tn_version(void) { return "gb300-rqc-tn 0.1"; }
 extern "C" tn_status tn_random_circuit(int32_t rows, int32_t cols, int32_t depth, uint64_t seed,
                                        tn_circuit** out) {
   if (!out) return fail(TN_EINVAL, "tn_random_circuit: out is NULL");
-  if (rows < 1 || cols < 1 || rows * cols > 64 || depth < 0 || depth > 4096)
+  if (rows < 1 || cols < 1 || rows > 64 || cols > 64 || rows * cols > 64 || depth < 0 || depth > 4096)
     return fail(TN_EINVAL, "tn_random_circuit: bad grid %dx%d depth %d", rows, cols, depth);
-  auto* h = new (std::nothrow) tn_circuit_s;
-  if (!h) return fail(TN_ENOMEM, "tn_random_circuit: out of host memory");
+  return guarded("tn_random_circuit", [&]() -> tn_status {
+  std::unique_ptr<tn_circuit_s> h(new tn_circuit_s);
   Circuit& C = h->c;
   C.n = rows * cols;
   C.cols = cols;
@@ -121,8 +121,9 @@ extern "C" tn_status tn_random_circuit(int32_t rows, int32_t cols, int32_t depth
     }
     one_qubit_layer();
   }
-  *out = h;
+  *out = h.release();
   return TN_OK;
+  });
 }
 
 extern "C" tn_status tn_circuit_from_gates(int32_t n, int64_t num_gates, const tn_gate* gates,
@@ -131,8 +132,8 @@ extern "C" tn_status tn_circuit_from_gates(int32_t n, int64_t num_gates, const t
   if (n < 1 || n > 64) return fail(TN_EINVAL, "tn_circuit_from_gates: num_qubits %d not in [1, 64]", n);
   if (num_gates < 0 || (num_gates > 0 && !gates))
     return fail(TN_EINVAL, "tn_circuit_from_gates: bad gate array");
-  auto* h = new (std::nothrow) tn_circuit_s;
-  if (!h) return fail(TN_ENOMEM, "tn_circuit_from_gates: out of host memory");
+  return guarded("tn_circuit_from_gates", [&]() -> tn_status {
+  std::unique_ptr<tn_circuit_s> h(new tn_circuit_s);
   h->c.n = n;
   for (int64_t i = 0; i < num_gates; ++i) {
     const tn_gate& t = gates[i];
@@ -140,10 +141,8 @@ extern "C" tn_status tn_circuit_from_gates(int32_t n, int64_t num_gates, const t
     g.kind = t.kind; g.q0 = t.q0; g.q1 = t.q1; g.theta = t.theta; g.phi = t.phi;
     bool two = (t.kind == TN_GATE_FSIM || t.kind == TN_GATE_MAT2);
     bool known = t.kind >= TN_GATE_SQRTX && t.kind <= TN_GATE_MAT2;
-    if (!known || t.q0 < 0 || t.q0 >= n || (two && (t.q1 < 0 || t.q1 >= n || t.q1 == t.q0))) {
-      delete h;
+    if (!known || t.q0 < 0 || t.q0 >= n || (two && (t.q1 < 0 || t.q1 >= n || t.q1 == t.q0)))
       return fail(TN_EINVAL, "tn_circuit_from_gates: gate %lld has bad kind/qubits", (long long)i);
-    }
     if (!two) g.q1 = -1;
     if (t.kind == TN_GATE_MAT1 || t.kind == TN_GATE_MAT2) {
       int d = two ? 4 : 2;
@@ -153,8 +152,9 @@ extern "C" tn_status tn_circuit_from_gates(int32_t n, int64_t num_gates, const t
     }
     h->c.gates.push_back(g);
   }
-  *out = h;
+  *out = h.release();
   return TN_OK;
+  });
 }
 
 extern "C" tn_status tn_circuit_info(const tn_circuit* c, int32_t* n, int64_t* ng) {

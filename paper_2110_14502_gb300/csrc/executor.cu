@@ -1060,6 +1060,9 @@ extern "C" tn_status tn_contract_amplitudes(tn_plan_t* p, const uint64_t* bits, 
                                             const tn_exec_opts* opts, tn_report* rep) {
   if (!p) return fail(TN_EINVAL, "tn_contract_amplitudes: plan is NULL");
   if (nb < 0 || (nb > 0 && (!bits || !out))) return fail(TN_EINVAL, "tn_contract_amplitudes: bad bitstrings/out");
+  const int k = (int)p->plan.net.open_qubits.size();
+  if (nb > (int64_t(1) << (40 - k)))
+    return fail(TN_EINVAL, "tn_contract_amplitudes: %lld bitstrings x 2^%d amplitudes exceed 2^40", (long long)nb, k);
   tn_exec_opts o;
   std::memset(&o, 0, sizeof o);
   o.slice_count = -1;
@@ -1067,7 +1070,7 @@ extern "C" tn_status tn_contract_amplitudes(tn_plan_t* p, const uint64_t* bits, 
   if (o.units_per_group < 0) return fail(TN_EINVAL, "tn_contract_amplitudes: units_per_group < 0");
   if (o.precision < TN_PREC_C64 || o.precision > TN_PREC_SCALED_BF16)
     return fail(TN_EINVAL, "tn_contract_amplitudes: unknown precision %d", o.precision);
-  return contract_amplitudes(p->plan, bits, nb, out, o, rep);
+  return guarded("tn_contract_amplitudes", [&] { return contract_amplitudes(p->plan, bits, nb, out, o, rep); });
 }
 
 extern "C" void tn_free_plan(tn_plan_t* p) { delete p; }

@@ -168,12 +168,13 @@ extern "C" tn_status tn_build_network(const tn_circuit* c, const int32_t* open, 
     for (int j = 0; j < i; ++j)
       if (open[j] == open[i]) return fail(TN_EINVAL, "tn_build_network: open qubit %d repeated", open[i]);
   }
-  auto* h = new (std::nothrow) tn_network_s;
-  if (!h) return fail(TN_ENOMEM, "tn_build_network: out of host memory");
-  tn_status st = build_network(c->c, open, num_open, h->net);
-  if (st != TN_OK) { delete h; return st; }
-  *out = h;
-  return TN_OK;
+  return guarded("tn_build_network", [&]() -> tn_status {
+    std::unique_ptr<tn_network_s> h(new tn_network_s);
+    tn_status st = build_network(c->c, open, num_open, h->net);
+    if (st != TN_OK) return st;
+    *out = h.release();
+    return TN_OK;
+  });
 }
 
 extern "C" tn_status tn_network_get_info(const tn_network* net, tn_network_info* info) {

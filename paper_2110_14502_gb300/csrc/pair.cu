@@ -148,6 +148,7 @@ extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, in
   if (st != TN_OK) return st;
   if (precision < TN_PREC_C64 || precision > TN_PREC_SCALED_BF16)
     return fail(TN_EINVAL, "tn_contract_pair: unknown precision %d", precision);
+  return guarded("tn_contract_pair", [&]() -> tn_status {
   std::vector<int> la(a_labels, a_labels + ra), lb(b_labels, b_labels + rb), lc(c_labels, c_labels + rc);
   GemmDesc d;
   const bool vec_shape = d_is_vector(la, lb, lc);
@@ -220,4 +221,5 @@ extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, in
   }
   if (e != cudaSuccess) return fail(TN_ECUDA, "tn_contract_pair launch: %s", cudaGetErrorString(e));
   return TN_OK;
+  });
 }

@@ -125,6 +125,7 @@ extern "C" tn_status tn_contract_pair_noalloc(const void* A, const int32_t* a_la
     return fail(TN_EINVAL, "tn_contract_pair_noalloc: NULL labels");
   tn_status st = check_labels(a_labels, ra, b_labels, rb, c_labels, rc);
   if (st != TN_OK) return st;
+  return guarded("tn_contract_pair_noalloc", [&]() -> tn_status {
   std::vector<int> la(a_labels, a_labels + ra), lb(b_labels, b_labels + rb), lc(c_labels, c_labels + rc);
   GemmDesc d;
   make_gemm_desc(la, lb, lc, d);
@@ -152,4 +153,5 @@ extern "C" tn_status tn_contract_pair_noalloc(const void* A, const int32_t* a_la
     return fail(TN_ETIMEOUT, "tn_contract_pair_noalloc: a tensor-core pipeline wait expired (code %d)", h);
   }
   return TN_OK;
+  });
 }

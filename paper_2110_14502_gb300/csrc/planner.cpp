@@ -895,12 +895,13 @@ extern "C" tn_status tn_plan(const tn_network* net, const tn_plan_opts* opts, tn
   if (o.max_log2_intermediate < 0 || o.max_log2_intermediate > 30)
     return fail(TN_EINVAL, "tn_plan: max_log2_intermediate %d not in [0, 30]", o.max_log2_intermediate);
   if (o.search_trials < 0 || o.search_trials > 100000) return fail(TN_EINVAL, "tn_plan: bad search_trials");
-  auto* h = new (std::nothrow) tn_plan_s;
-  if (!h) return fail(TN_ENOMEM, "tn_plan: out of host memory");
-  tn_status st = make_plan(net->net, o, h->plan);
-  if (st != TN_OK) { delete h; return st; }
-  *out = h;
-  return TN_OK;
+  return guarded("tn_plan", [&]() -> tn_status {
+    std::unique_ptr<tn_plan_s> h(new tn_plan_s);
+    tn_status st = make_plan(net->net, o, h->plan);
+    if (st != TN_OK) return st;
+    *out = h.release();
+    return TN_OK;
+  });
 }
 
 extern "C" tn_status tn_plan_get_info(const tn_plan_t* p, tn_plan_info* info) {
@@ -953,8 +954,10 @@ extern "C" tn_status tn_plan_tree(const tn_plan_t* p, int32_t* leaf_raw, int64_t
   const Plan& P = p->plan;
   int64_t need = 0;
   for (auto& lf : P.net.leaves) need += (int64_t)lf.raw.size() + 1;
-  if (cap_raw < need || cap_tree < (int64_t)P.tree.size())
-    return fail(TN_EINVAL, "tn_plan_tree: capacity too small (need %lld raw, %zu tree)", (long long)need, P.tree.size());
+  const int64_t need_tree = 2 * (int64_t)P.steps.size();
+  if (cap_raw < need || cap_tree < need_tree)
+    return fail(TN_EINVAL, "tn_plan_tree: capacity too small (need %lld raw, %lld tree)", (long long)need,
+                (long long)need_tree);
   int64_t k = 0;
   for (auto& lf : P.net.leaves) {
     for (int r : lf.raw) leaf_raw[k++] = r;

@@ -171,7 +171,7 @@ void planner_loop(Server* S) {
       R = S->to_plan.front();
       S->to_plan.pop_front();
     }
-    tn_status st = plan_request(*S, *R);
+    tn_status st = guarded("serving: planning", [&] { return plan_request(*S, *R); });
     std::lock_guard<std::mutex> g(S->mu);
     if (st != TN_OK) {
       R->status = st;
@@ -271,7 +271,7 @@ void scheduler_loop(Server* S) {
         for (size_t i = 0; i < slot_busy.size(); ++i)
           if (!slot_busy[i]) { slot = (int)i; break; }
         if (slot < 0 || S->in_use + R->footprint > S->budget) break;
-        tn_status st = admit(*S, *R, S->streams[slot]);
+        tn_status st = guarded("serving: admission", [&] { return admit(*S, *R, S->streams[slot]); });
         if (st != TN_OK) {
           R->status = st;
           R->error = tn_last_error();
@@ -303,7 +303,7 @@ void scheduler_loop(Server* S) {
           R->quanta.erase(R->quanta.begin());
         }
         if (R->quanta.size() < 2) {
-          tn_status st = step_request(*R);
+          tn_status st = guarded("serving: contraction", [&] { return step_request(*R); });
           progressed = true;
           if (st != TN_OK) {
             std::lock_guard<std::mutex> g(S->mu);
@@ -372,7 +372,6 @@ extern "C" tn_status tn_server_create(const tn_server_opts* opts, tn_server** ou
     return fail(TN_ECUDA, "tn_server_create: cudaMemGetInfo failed");
   }
   const int64_t total = S.opts.hbm_budget_bytes > 0 ? S.opts.hbm_budget_bytes : (int64_t)(0.6 * (double)freeb);
-  S.stems = make_stem_cache(total / 8);
   S.budget = total - total / 8;
   for (int i = 0; i < S.opts.max_inflight; ++i) {
     cudaStream_t st;
@@ -384,25 +383,36 @@ extern "C" tn_status tn_server_create(const tn_server_opts* opts, tn_server** ou
     S.streams.push_back(st);
   }
   const int np_ = S.opts.planner_threads > 0 ? std::min(S.opts.planner_threads, 32) : 4;  // planner threads
-  for (int i = 0; i < np_; ++i) S.planners.push_back(std::thread(planner_loop, &S));
-  S.scheduler = std::thread(scheduler_loop, &S);
+  const tn_status st = guarded("tn_server_create", [&]() -> tn_status {
+    S.stems = make_stem_cache(total / 8);
+    for (int i = 0; i < np_; ++i) S.planners.push_back(std::thread(planner_loop, &S));
+    S.scheduler = std::thread(scheduler_loop, &S);
+    return TN_OK;
+  });
+  if (st != TN_OK) {
+    const std::string msg = tn_last_error();
+    tn_server_destroy(h);  // stops and joins the threads that did start
+    return fail(st, "%s", msg.c_str());
+  }
   *out = h;
   return TN_OK;
 }
 
 extern "C" tn_status tn_submit(tn_server* h, const tn_request* req, int64_t* ticket) {
   if (!h || !req || !ticket) return fail(TN_EINVAL, "tn_submit: NULL argument");
-  const int n = req->rows * req->cols;
-  if (req->rows < 1 || req->cols < 1 || n > 64 || req->depth < 0 || req->num_open < 0 || req->num_open > 12 ||
-      req->num_open > n || req->nb < 1 || !req->bitstrings || !(req->fidelity >= 0.0 && req->fidelity <= 1.0))
+  const int n = req->rows >= 1 && req->rows <= 64 && req->cols >= 1 && req->cols <= 64 ? req->rows * req->cols : 0;
+  if (n < 1 || n > 64 || req->depth < 0 || req->num_open < 0 || req->num_open > 12 ||
+      req->num_open > n || req->nb < 1 || req->nb > (int64_t(1) << 24) || !req->bitstrings ||
+      !(req->fidelity >= 0.0 && req->fidelity <= 1.0))
     return fail(TN_EINVAL, "tn_submit: bad request (grid %dx%d, depth %d, %d open, %lld bitstrings)", req->rows,
                 req->cols, req->depth, req->num_open, (long long)req->nb);
   Server& S = h->s;
+  const int32_t prec = req->precision < 0 ? S.opts.precision : req->precision;
+  if (prec < TN_PREC_C64 || prec > TN_PREC_SCALED_BF16) return fail(TN_EINVAL, "tn_submit: unknown precision %d", prec);
+  return guarded("tn_submit", [&]() -> tn_status {
   auto R = std::make_shared<Request>();
   R->params = *req;
-  R->precision = req->precision < 0 ? S.opts.precision : req->precision;
-  if (R->precision < TN_PREC_C64 || R->precision > TN_PREC_SCALED_BF16)
-    return fail(TN_EINVAL, "tn_submit: unknown precision %d", R->precision);
+  R->precision = prec;
   const int words = std::max(1, (n + 63) / 64);
   R->bits.assign(req->bitstrings, req->bitstrings + req->nb * words);
   R->params.bitstrings = nullptr;
@@ -414,6 +424,7 @@ extern "C" tn_status tn_submit(tn_server* h, const tn_request* req, int64_t* tic
   S.cv.notify_all();
   *ticket = R->ticket;
   return TN_OK;
+  });
 }
 
 extern "C" tn_status tn_poll(tn_server* h, int64_t ticket, int32_t* done) {

@@ -3,7 +3,9 @@
 
 #include <complex>
 #include <cstdint>
+#include <exception>
 #include <memory>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -15,6 +17,22 @@ using cd = std::complex<double>;
 
 // Records a printf-style message for tn_last_error() and returns `code`.
 tn_status fail(tn_status code, const char* fmt, ...);
+
+// Runs an entry point's body (a callable returning tn_status) so that no C++
+// exception crosses the C ABI: a failed host allocation becomes TN_ENOMEM,
+// any other exception TN_EINTERNAL with its message.
+template <class F>
+tn_status guarded(const char* fn, F&& body) noexcept {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return fail(TN_ENOMEM, "%s: out of host memory", fn);
+  } catch (const std::exception& e) {
+    return fail(TN_EINTERNAL, "%s: %s", fn, e.what());
+  } catch (...) {
+    return fail(TN_EINTERNAL, "%s: unexpected exception", fn);
+  }
+}
 
 struct Gate {
   int kind = 0;

@@ -176,3 +176,28 @@ def test_bench_workload_plan_is_reproducible():
     assert round(float(np.log2(info["cmac_per_slice"])), 3) == 36.525
     assert info["num_slices"] == 1024 and info["max_log2_intermediate"] == 26
     assert words.shape[0] == bench.NBATCH and open_q == list(range(30, 36))
+
+
+def test_size_limits_fail_before_any_work():
+    """Sizes whose products would overflow 64-bit offsets are rejected with
+    TN_EINVAL on the host: a grid side far above 64, more than 2^40 amplitudes
+    in one call, a tree buffer shorter than the plan's steps."""
+    T = tnlib()
+    from paper_2110_14502_gb300 import _abi
+    L = _abi.lib()
+    h = C.c_void_p()
+    assert L.tn_random_circuit(1 << 20, 1 << 20, 4, 1, C.byref(h)) == 1
+    assert "bad grid" in L.tn_last_error().decode()
+    _, _, p = _plan(T, 2, 3, 4, 1, open_q=(4, 5), search_trials=4)
+    words = np.zeros(1, dtype=np.uint64)
+    out = np.zeros(2, dtype=np.float64)
+    st = L.tn_contract_amplitudes(p._h, words.ctypes.data_as(C.c_void_p), 1 << 39, out.ctypes.data_as(C.c_void_p),
+                                  None, None)
+    assert st == 1 and "2^40" in L.tn_last_error().decode()
+    nl = p.info()["num_leaves"]
+    raw = np.zeros(4096, dtype=np.int32)
+    tree = np.zeros(2 * (nl - 1) - 1, dtype=np.int32)
+    st = L.tn_plan_tree(p._h, raw.ctypes.data_as(C.POINTER(C.c_int32)), raw.size,
+                        tree.ctypes.data_as(C.POINTER(C.c_int32)), tree.size)
+    assert st == 1 and "capacity too small" in L.tn_last_error().decode()
+    assert _abi.STATUS[10] == "TN_EINTERNAL"
