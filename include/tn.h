@@ -312,7 +312,8 @@ typedef struct {
  * scheduler thread.  Requests are admitted in arrival order when an in-flight
  * slot is free and their estimated device footprint fits the budget; admitted
  * requests advance one quantum of slices per turn each, on their own streams.
- * Plans are cached per circuit, and each circuit's stem (its leaf tensors and
+ * Plans are cached per circuit (the 256 most recently used, shared by the
+ * servers of a process), and each circuit's stem (its leaf tensors and
  * the intermediates that depend on neither bitstring nor slice) stays
  * resident on the device for later requests of the same circuit, within one
  * eighth of the budget, least recently used first out.

@@ -77,9 +77,16 @@ struct PlanKey {
 
 // Plans are pure functions of the circuit and the planning options, so one
 // cache serves every server of the process (host memory only: copies of a
-// cached plan own their device state).
+// cached plan own their device state).  It holds the kPlanCacheSize most
+// recently used plans.
+constexpr size_t kPlanCacheSize = 256;
+struct CachedPlan {
+  std::shared_ptr<tn_plan_s> plan;
+  uint64_t last = 0;
+};
 std::mutex g_plan_mu;
-std::map<PlanKey, std::shared_ptr<tn_plan_s>> g_plan_cache;
+std::map<PlanKey, CachedPlan> g_plan_cache;
+uint64_t g_plan_clock = 0;
 
 }  // namespace
 
@@ -112,7 +119,10 @@ tn_status plan_request(Server& S, Request& R) {
   {
     std::lock_guard<std::mutex> g(g_plan_mu);
     auto it = g_plan_cache.find(key);
-    if (it != g_plan_cache.end()) cached = it->second;
+    if (it != g_plan_cache.end()) {
+      cached = it->second.plan;
+      it->second.last = ++g_plan_clock;
+    }
   }
   if (!cached) {
     tn_circuit* c = nullptr;
@@ -138,7 +148,13 @@ tn_status plan_request(Server& S, Request& R) {
     cached.reset(pl);
     R.planned_here = true;
     std::lock_guard<std::mutex> g(g_plan_mu);
-    g_plan_cache[key] = cached;
+    if (g_plan_cache.size() >= kPlanCacheSize && !g_plan_cache.count(key)) {
+      auto oldest = g_plan_cache.begin();
+      for (auto i = g_plan_cache.begin(); i != g_plan_cache.end(); ++i)
+        if (i->second.last < oldest->second.last) oldest = i;
+      g_plan_cache.erase(oldest);  // requests still holding it keep their own copy
+    }
+    g_plan_cache[key] = CachedPlan{cached, ++g_plan_clock};
   }
   auto* copy = new (std::nothrow) tn_plan_s(cached->plan);
   if (!copy) return fail(TN_ENOMEM, "serving: out of host memory");
