@@ -201,3 +201,29 @@ def test_size_limits_fail_before_any_work():
                         tree.ctypes.data_as(C.POINTER(C.c_int32)), tree.size)
     assert st == 1 and "capacity too small" in L.tn_last_error().decode()
     assert _abi.STATUS[10] == "TN_EINTERNAL"
+
+
+def test_header_is_plain_c_and_the_library_links_from_c(tmp_path):
+    """include/tn.h compiles as strict C99, and a C program linked against the
+    library plans the same bytes (hash) as the Python binding."""
+    import os
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    T = tnlib()
+    from paper_2110_14502_gb300 import _abi
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.dirname(_abi.LIB_PATH)
+    exe = str(tmp_path / "c_abi_host")
+    cmd = [gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(root, "include"),
+           os.path.join(root, "tests", "c_abi_host.c"), "-o", exe, "-L", libdir, "-ltn", f"-Wl,-rpath,{libdir}"]
+    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    fields = dict(kv.split("=") for kv in r.stdout.split())
+    c = T.random_circuit(4, 4, 8, 1)
+    p = T.plan(T.build_network(c, [14, 15]), num_sliced=2, search_trials=8, seed=3)
+    assert int(fields["hash"], 16) == p.info()["hash"]
+    assert int(fields["slices"]) == 4 and int(fields["bytes"]) == len(p.serialize())
