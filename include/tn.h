@@ -269,7 +269,8 @@ typedef struct {
   int64_t hbm_budget_bytes;      /* device memory of the server; 0 = 60% of the free memory.  One
                                     eighth holds the stems of recent circuits, the rest bounds the
                                     estimated footprint of the admitted requests */
-  double max_log2_cmac;          /* cost cap (log2 complex MACs of a request); 0 = 48 */
+  double max_log2_cmac;          /* cost cap (log2 complex MACs a request is served, per
+                                    bitstring); 0 = 48 */
   int32_t max_log2_intermediate; /* per-slice width cap when planning; 0 = 27 */
   int32_t planner_threads;       /* host threads planning new circuits concurrently; 0 = 4 (max 32) */
 } tn_server_opts;
@@ -289,7 +290,8 @@ typedef struct {
   double fidelity;               /* (0, 1): serve only the first ceil(fidelity * 2^S) slices
                                     of the plan's 2^S (Sec. "A Mixed-Precision Computation Method
                                     via Adaptive Precision Scaling": a fraction f of the slices
-                                    gives amplitudes of fidelity about f); 0 or 1 = all slices */
+                                    gives amplitudes of fidelity about f); 0 or 1 = all slices.
+                                    The server's cost cap applies to the slices served */
 } tn_request;
 
 typedef struct {

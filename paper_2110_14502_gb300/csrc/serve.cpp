@@ -113,8 +113,12 @@ namespace {
 
 tn_status plan_request(Server& S, Request& R) {
   const tn_request& p = R.params;
-  PlanKey key{p.rows, p.cols, p.depth, p.num_open, p.seed, S.opts.plan_trials, S.opts.max_log2_intermediate,
-              S.opts.max_log2_cmac};
+  // the cost cap bounds the work served: a request of fidelity f runs a
+  // fraction f of the slices, so its plan may cost up to 2^cap / f in full
+  const double f = p.fidelity;
+  const bool partial = f > 0.0 && f < 1.0;
+  const double cap = S.opts.max_log2_cmac + (partial ? -std::log2(f) : 0.0);
+  PlanKey key{p.rows, p.cols, p.depth, p.num_open, p.seed, S.opts.plan_trials, S.opts.max_log2_intermediate, cap};
   std::shared_ptr<tn_plan_s> cached;
   {
     std::lock_guard<std::mutex> g(g_plan_mu);
@@ -140,7 +144,7 @@ tn_status plan_request(Server& S, Request& R) {
     po.max_log2_intermediate = S.opts.max_log2_intermediate;
     po.search_trials = S.opts.plan_trials;
     po.seed = 1;
-    po.max_log2_cmac = S.opts.max_log2_cmac;
+    po.max_log2_cmac = cap;
     tn_plan_t* pl = nullptr;
     st = tn_plan(net, &po, &pl);
     tn_free_network(net);
@@ -163,8 +167,12 @@ tn_status plan_request(Server& S, Request& R) {
   const Plan& P = R.plan->plan;
   // fidelity by fraction: the first ceil(f 2^S) slices (all for f = 0 or 1)
   const int64_t all = int64_t(1) << P.sliced.size();
-  const double f = R.params.fidelity;
-  R.ns = f > 0.0 && f < 1.0 ? std::max<int64_t>(1, std::min<int64_t>(all, (int64_t)std::ceil(f * (double)all))) : all;
+  R.ns = partial ? std::max<int64_t>(1, std::min<int64_t>(all, (int64_t)std::ceil(f * (double)all))) : all;
+  // rounding up to whole slices can serve more than f of the work
+  const double served = std::log2(std::max(1.0, (double)R.ns * P.cmac_per_slice));
+  if (partial && served > S.opts.max_log2_cmac)
+    return fail(TN_ETOOBIG, "serving: %lld of %lld slices cost 2^%.1f CMAC, above the cap 2^%.1f", (long long)R.ns,
+                (long long)all, served, S.opts.max_log2_cmac);
   R.q = std::min<int64_t>(R.ns, std::max(1, S.opts.slices_per_quantum));
   R.k = (int)P.net.open_qubits.size();
   R.words = std::max(1, (P.net.n + 63) / 64);
