@@ -151,3 +151,32 @@ def test_partial_fidelity_requests_serve_a_fraction_of_the_slices():
     xeb = (2.0 ** n) * np.sum(p_true * p_f) - 1.0
     frac = m / S_all
     assert abs(fid - frac) <= 0.05 and abs(xeb - frac) <= 0.05, (fid, xeb, frac)
+
+
+def test_partial_fidelity_requests_are_charged_for_the_slices_served():
+    """The server's cost cap bounds the work a request is served.  The 4x5
+    depth-12 circuit below plans to 2^26.38 CMAC in 2^8 slices: at full
+    fidelity and at f = 0.75 it is over a 2^25.3 cap, at f = 0.25 its 64
+    slices cost 2^24.38 and it is served, with the plain path's partial sum
+    over the same slices."""
+    import math
+    T = tnlib()
+    req = _req(4, 5, 12, 21, 3, 2)
+    cap = 25.3
+    srv = T.Server(max_inflight=2, precision="c64", plan_trials=8, max_log2_intermediate=12, max_log2_cmac=cap)
+    try:
+        for f in (0.0, 0.75):
+            with pytest.raises(T.TnError) as e:
+                srv.wait(srv.submit(**req, fidelity=f))
+            assert e.value.status == 6          # TN_ETOOBIG
+        part, st = srv.wait(srv.submit(**req, fidelity=0.25))
+    finally:
+        srv.close()
+    assert st["status"] == 0 and st["slices"] == 64 and st["slice_fraction"] == 0.25
+    c = T.random_circuit(4, 5, 12, 21)
+    p = T.plan(T.build_network(c, [17, 18, 19]), max_log2_intermediate=12, search_trials=8, seed=1,
+               max_log2_cmac=cap + 2.0)
+    assert p.info()["hash"] == st["plan_hash"]
+    assert math.log2(64 * p.info()["cmac_per_slice"]) <= cap
+    ref = p.contract_amplitudes(req["bitstrings"], slice_count=64)
+    assert np.linalg.norm(part - ref) <= 1e-6 * np.linalg.norm(ref)

@@ -227,3 +227,22 @@ def test_header_is_plain_c_and_the_library_links_from_c(tmp_path):
     p = T.plan(T.build_network(c, [14, 15]), num_sliced=2, search_trials=8, seed=3)
     assert int(fields["hash"], 16) == p.info()["hash"]
     assert int(fields["slices"]) == 4 and int(fields["bytes"]) == len(p.serialize())
+
+
+def test_cost_cap_premise_of_the_partial_fidelity_serving_test():
+    """Host facts the partial-fidelity serving test relies on: the 4x5
+    depth-12 circuit (seed 21, 3 open, width 2^12, 8 trials, seed 1) plans to
+    2^26.38 CMAC in 2^8 slices; a 2^25.3 cap refuses it, and so does the cap a
+    fidelity-0.75 request gets (25.3 + log2(4/3)); the fidelity-0.25 cap
+    (27.3) plans it."""
+    import math
+    T = tnlib()
+    net = T.build_network(T.random_circuit(4, 5, 12, 21), [17, 18, 19])
+    kw = dict(max_log2_intermediate=12, search_trials=8, seed=1)
+    for cap in (25.3, 25.3 + math.log2(4 / 3)):
+        with pytest.raises(T.TnError) as e:
+            T.plan(net, max_log2_cmac=cap, **kw)
+        assert e.value.status == 6
+    info = T.plan(net, max_log2_cmac=27.3, **kw).info()
+    assert info["num_sliced"] == 8 and abs(info["log2_cmac_total"] - 26.382) < 1e-3
+    assert math.log2(64 * info["cmac_per_slice"]) <= 25.3
