@@ -246,3 +246,24 @@ def test_cost_cap_premise_of_the_partial_fidelity_serving_test():
     info = T.plan(net, max_log2_cmac=27.3, **kw).info()
     assert info["num_sliced"] == 8 and abs(info["log2_cmac_total"] - 26.382) < 1e-3
     assert math.log2(64 * info["cmac_per_slice"]) <= 25.3
+
+
+@pytest.mark.parametrize("rows,cols,depth,seed,open_q,ns", [(3, 4, 8, 2, (10, 11), 3), (4, 4, 8, 3, (), 4)])
+def test_sliced_plan_replayed_slice_by_slice_sums_to_the_statevector(rows, cols, depth, seed, open_q, ns):
+    """Slicing is exact: fixing the plan's sliced wires to the bits of each
+    slice id (bit j of s for sliced index j) and contracting every slice in
+    the plan's order with the oracle, the FP64 sum over the 2^S slices is the
+    state-vector amplitude; no single slice is."""
+    T = tnlib()
+    from _replay import replay
+    n = rows * cols
+    c, net, p = _plan(T, rows, cols, depth, seed, open_q, num_sliced=ns, search_trials=16, seed=1)
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    bits = I.bits_of(I.bitstrings(n, 1, seed)[0], n)
+    wires = p.sliced_wires()
+    assert len(wires) == ns
+    parts = [replay(p, gates, n, bits, open_q, {wires[j]: (s >> j) & 1 for j in range(ns)}) for s in range(1 << ns)]
+    ref = SV.amplitudes(SV.simulate(gates, n), n, [bits], open_q)[0]
+    total = np.sum(parts, axis=0)
+    assert np.linalg.norm(total - ref) <= 1e-12 * np.linalg.norm(ref)
+    assert all(np.linalg.norm(x - ref) > 1e-6 * np.linalg.norm(ref) for x in parts)
