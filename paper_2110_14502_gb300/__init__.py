@@ -10,7 +10,7 @@ import ctypes as C
 import numpy as np
 
 from ._abi import (PAIR_ALGO, PREC, ExecOpts, Gate, NetworkInfo, PlanInfo, PlanOpts, Report, Request,
-                   RequestStats, ServerOpts, TnError, check, i32array, lib)
+                   RequestStats, ServerOpts, TnError, check, i32array, lib, require_buffer)
 
 __all__ = ["Circuit", "Network", "Plan", "random_circuit", "circuit_from_gates", "build_network", "plan", "select_plan",
            "contract_pair", "contract_pair_noalloc", "Server", "TnError", "PREC", "version"]
@@ -185,10 +185,15 @@ class Plan:
             o.stream = C.c_void_p(getattr(stream, "cuda_stream", stream))
         rep = Report()
         device = hasattr(bitstrings, "is_cuda") and bitstrings.is_cuda
+        words = (info["num_qubits"] + 63) // 64
         if device:
             nb = bitstrings.shape[0]
             if out is None:
                 raise ValueError("device I/O needs an `out` tensor")
+            if bitstrings.dim() not in (1, 2) or bitstrings.numel() != nb * words:
+                raise TnError(1, f"bitstrings must have shape ({nb}, {words}) or ({nb},)")
+            require_buffer(bitstrings, "bitstrings", 8 * nb * words, True, ("int64", "uint64"))
+            require_buffer(out, "out", 16 * (nb << k), True, ("float64", "complex128"))
             o.device_io = 1
             check(lib().tn_contract_amplitudes(self._h, _ptr(bitstrings), nb, _ptr(out), C.byref(o), C.byref(rep)))
             res = out
@@ -196,6 +201,8 @@ class Plan:
             b = np.ascontiguousarray(np.asarray(bitstrings, dtype=np.uint64))
             if b.ndim == 1:
                 b = b.reshape(-1, 1)
+            if b.ndim != 2 or b.shape[1] != words:
+                raise TnError(1, f"bitstrings must have shape (nb, {words}), got {b.shape}")
             nb = b.shape[0]
             res = np.zeros((nb, 1 << k), dtype=np.complex128)
             check(lib().tn_contract_amplitudes(self._h, _ptr(b), nb, _ptr(res), C.byref(o), C.byref(rep)))
@@ -247,12 +254,21 @@ def select_plan(network, bitstrings, seeds=(1, 2, 3, 4), probe_slices=32, precis
     return best, table
 
 
+def _require_pair_operands(A, la, B, lb, Cout, lc):
+    """Each operand is a contiguous CUDA complex64 tensor of 2^rank elements
+    (ranks above 30 are left to the library to reject)."""
+    for x, ls, what in ((A, la, "A"), (B, lb, "B"), (Cout, lc, "C")):
+        if len(ls) <= 30:
+            require_buffer(x, what, 8 << len(ls), True, ("complex64",))
+
+
 def contract_pair(A, a_labels, B, b_labels, Cout, c_labels, precision="c64", algo="auto", stream=None):
     """C[c_labels] = sum over shared labels of A[a_labels] * B[b_labels] on the
     GPU; A, B, C are CUDA complex64 torch tensors (contiguous)."""
     la, pa = i32array(a_labels)
     lb, pb = i32array(b_labels)
     lc, pc = i32array(c_labels)
+    _require_pair_operands(A, la, B, lb, Cout, lc)
     s = C.c_void_p(getattr(stream, "cuda_stream", stream) if stream is not None else None)
     prec = PREC[precision] if isinstance(precision, str) else int(precision)
     al = PAIR_ALGO[algo] if isinstance(algo, str) else int(algo)
@@ -269,6 +285,7 @@ def contract_pair_noalloc(A, a_labels, B, b_labels, Cout, c_labels, stream=None)
     la, pa = i32array(a_labels)
     lb, pb = i32array(b_labels)
     lc, pc = i32array(c_labels)
+    _require_pair_operands(A, la, B, lb, Cout, lc)
     s = C.c_void_p(getattr(stream, "cuda_stream", stream) if stream is not None else None)
     check(lib().tn_contract_pair_noalloc(_ptr(A), pa, len(la), _ptr(B), pb, len(lb), _ptr(Cout), pc, len(lc), s))
     return Cout

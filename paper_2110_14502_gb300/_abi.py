@@ -141,6 +141,23 @@ def check(status):
         raise TnError(status, lib().tn_last_error().decode())
 
 
+def require_buffer(x, what, nbytes, device, dtypes):
+    """Checks a buffer before its raw pointer crosses the C ABI, which cannot
+    see sizes: `x` must be a contiguous CUDA torch tensor (device=True) or a
+    C-contiguous NumPy array (device=False) of one of the dtype names in
+    `dtypes`, holding at least `nbytes` bytes.  Raises TnError(TN_EINVAL)."""
+    if hasattr(x, "data_ptr"):
+        on_dev, ok = bool(x.is_cuda), x.is_contiguous()
+        dt, size = str(x.dtype).replace("torch.", ""), x.numel() * x.element_size()
+    else:
+        on_dev, ok = False, bool(x.flags.c_contiguous)
+        dt, size = str(x.dtype), x.nbytes
+    side = "a CUDA tensor" if device else "a host array"
+    if on_dev != device or not ok or dt not in dtypes or size < nbytes:
+        raise TnError(1, f"{what} must be {side}, contiguous, of dtype {'/'.join(dtypes)} and at least {nbytes} "
+                         f"bytes (got {'device' if on_dev else 'host'}, contiguous={ok}, {dt}, {size} bytes)")
+
+
 def i32array(xs):
     a = np.ascontiguousarray(np.asarray(list(xs), dtype=np.int32))
     return a, (a.ctypes.data_as(I32P) if a.size else None)

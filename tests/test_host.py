@@ -267,3 +267,25 @@ def test_sliced_plan_replayed_slice_by_slice_sums_to_the_statevector(rows, cols,
     total = np.sum(parts, axis=0)
     assert np.linalg.norm(total - ref) <= 1e-12 * np.linalg.norm(ref)
     assert all(np.linalg.norm(x - ref) > 1e-6 * np.linalg.norm(ref) for x in parts)
+
+
+def test_binding_checks_buffers_before_passing_pointers():
+    """The C ABI cannot see buffer sizes, so the binding checks side, dtype,
+    contiguity and size of every buffer it passes as a raw pointer."""
+    import torch
+    T = tnlib()
+    from paper_2110_14502_gb300._abi import require_buffer
+    _, _, p = _plan(T, 2, 3, 4, 1, open_q=(4, 5), search_trials=4)
+    with pytest.raises(T.TnError) as e:
+        p.contract_amplitudes(np.zeros((2, 2), dtype=np.uint64))      # two words per bitstring for 6 qubits
+    assert e.value.status == 1
+    a = torch.zeros(4, dtype=torch.complex64)                          # host tensors: the pair path is device-only
+    with pytest.raises(T.TnError) as e:
+        T.contract_pair(a, [0, 1], a, [1, 2], a, [0, 2])
+    assert e.value.status == 1 and "CUDA tensor" in str(e.value)
+    require_buffer(np.zeros(4, np.complex64), "x", 32, False, ("complex64",))
+    for bad in (np.zeros(3, np.complex64), np.zeros(4, np.complex128), np.zeros((4, 2), np.complex64)[:, 0]):
+        with pytest.raises(T.TnError):
+            require_buffer(bad, "x", 32, False, ("complex64",))
+    with pytest.raises(T.TnError):
+        require_buffer(np.zeros(4, np.complex64), "x", 32, True, ("complex64",))
