@@ -316,6 +316,9 @@ class Server:
         b = np.ascontiguousarray(np.asarray(bitstrings, dtype=np.uint64))
         if b.ndim == 1:
             b = b.reshape(-1, 1)
+        words = max(1, (rows * cols + 63) // 64)
+        if b.ndim != 2 or b.shape[1] != words:
+            raise TnError(1, f"bitstrings must have shape (nb, {words}), got {b.shape}")
         r = Request()
         r.rows, r.cols, r.depth, r.num_open, r.seed = rows, cols, depth, num_open, seed
         r.nb = b.shape[0]
@@ -335,10 +338,12 @@ class Server:
     def wait(self, ticket, timeout=0.0):
         """(complex128 amplitudes (nb, 2^num_open), stats dict); raises TnError
         with the request's status when it failed."""
-        nb, k = self._k.pop(ticket)
+        nb, k = self._k[ticket]
         out = np.zeros((nb, 1 << k), dtype=np.complex128)
         st = RequestStats()
         status = lib().tn_wait(self._h, ticket, out.ctypes.data, out.size, C.byref(st), timeout)
+        if status != 5:  # TN_ETIMEOUT keeps the ticket open for a later wait
+            del self._k[ticket]
         stats = {f: getattr(st, f) for f, _ in RequestStats._fields_}
         if status != 0:
             raise TnError(status, lib().tn_last_error().decode())
