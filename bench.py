@@ -281,7 +281,8 @@ def run_ours(args):
                    "slices": info["num_slices"] if SLICE_LIMIT < 0 else SLICE_LIMIT, "plan_hash": hex(info["hash"]),
                    "cmac_per_slice_log2": round(float(np.log2(info["cmac_per_slice"])), 3),
                    "max_log2_intermediate": info["max_log2_intermediate"],
-                   "l2": "working set (>= 2^26-element intermediates per slice) larger than L2; no flush",
+                   "l2": f"working set (2^{info['max_log2_intermediate']}-element complex64 intermediates per "
+                         "slice, many slices per launch) larger than L2; no flush",
                    "parallelism": f"slices x bitstrings per GPU; {world} independent replica(s)"},
         "amplitudes_per_s": round(amps / (total_ms * 1e-3), 3),
         "flops_equivalent_tflops": round(flops_eq / (total_ms * 1e-3) / 1e12, 3),
