@@ -164,9 +164,10 @@ class Plan:
         """Amplitudes of each bitstring's open batch, summed over the slice range.
 
         bitstrings: uint64 words, shape (nb, ceil(n/64)) -- a NumPy array (host
-        I/O: result returned as complex128 NumPy (nb, 2^k)) or a CUDA torch
-        tensor (device I/O: `out` must be a CUDA float64 tensor of nb*2^k*2
-        entries; work is queued on `stream`, a torch.cuda.Stream or raw handle).
+        I/O: result returned as complex128 NumPy (nb, 2^k), written into `out`
+        when given, e.g. an array over pinned memory) or a CUDA torch tensor
+        (device I/O: `out` must be a CUDA float64 tensor of nb*2^k*2 entries;
+        work is queued on `stream`, a torch.cuda.Stream or raw handle).
         """
         info = self.info()
         k = info["num_open"]
@@ -204,7 +205,11 @@ class Plan:
             if b.ndim != 2 or b.shape[1] != words:
                 raise TnError(1, f"bitstrings must have shape (nb, {words}), got {b.shape}")
             nb = b.shape[0]
-            res = np.zeros((nb, 1 << k), dtype=np.complex128)
+            if out is None:
+                res = np.zeros((nb, 1 << k), dtype=np.complex128)
+            else:
+                require_buffer(out, "out", 16 * (nb << k), False, ("complex128",))
+                res = out
             check(lib().tn_contract_amplitudes(self._h, _ptr(b), nb, _ptr(res), C.byref(o), C.byref(rep)))
         if report:
             r = {}

@@ -279,6 +279,11 @@ def test_binding_checks_buffers_before_passing_pointers():
     with pytest.raises(T.TnError) as e:
         p.contract_amplitudes(np.zeros((2, 2), dtype=np.uint64))      # two words per bitstring for 6 qubits
     assert e.value.status == 1
+    words = np.zeros((3, 1), dtype=np.uint64)
+    for out in (np.zeros((3, 4), np.complex64), np.zeros((2, 4), np.complex128), np.zeros((4, 3), np.complex128).T):
+        with pytest.raises(T.TnError) as e:                          # host `out`: complex128, 3 x 2^2, contiguous
+            p.contract_amplitudes(words, out=out)
+        assert e.value.status == 1 and "out must be" in str(e.value)
     a = torch.zeros(4, dtype=torch.complex64)                          # host tensors: the pair path is device-only
     with pytest.raises(T.TnError) as e:
         T.contract_pair(a, [0, 1], a, [1, 2], a, [0, 2])
