@@ -444,13 +444,15 @@ def serve_workload(nreq, seed=5):
 
 def serve_summary(args, nreq=60):
     """Compact serving run for the main bench line: the same request stream on
-    the batched mixed-precision server and on the plain complex64 path."""
+    the plain complex64 path and on the batched server, in complex64 (the
+    plain path's accuracy) and in scaled fp16."""
     import paper_2110_14502_gb300 as T
     reqs, _ = serve_workload(nreq)
     common = dict(plan_trials=8, max_log2_cmac=40.0, max_log2_intermediate=27, planner_threads=16)
     out = {"requests": nreq, "cost_cap_log2_cmac": 40.0}
     for name, kw in (("warm", dict(max_inflight=8, slices_per_quantum=64, precision="c64")),
                      ("plain_c64_one_slice", dict(max_inflight=1, slices_per_quantum=1, precision="c64")),
+                     ("batched_c64", dict(max_inflight=8, slices_per_quantum=64, precision="c64")),
                      ("batched_scaled_fp16", dict(max_inflight=8, slices_per_quantum=64, precision="scaled_fp16"))):
         srv = T.Server(**kw, **common)
         t0 = time.time()
@@ -512,10 +514,12 @@ def run_serve(args):
     warm.close()
     plain = T.Server(max_inflight=1, slices_per_quantum=1, precision="c64", **common)
     batched = T.Server(max_inflight=8, slices_per_quantum=64, precision=args.precision, **common)
+    batched_c64 = T.Server(max_inflight=8, slices_per_quantum=64, precision="c64", **common)
     try:
         # saturated throughput (every request submitted at once)
         cap_plain = closed_loop(plain)
         cap_batched = closed_loop(batched)
+        cap_batched_c64 = closed_loop(batched_c64)  # batching alone, at the plain path's accuracy
         # latency under Poisson arrivals at 0.7 x the plain path's capacity (requests/s)
         rate = 0.7 * cap_plain["served"] / cap_plain["seconds"]
         lat_plain = closed_loop(plain, rate)
@@ -523,13 +527,14 @@ def run_serve(args):
     finally:
         plain.close()
         batched.close()
+        batched_c64.close()
     line = {"metric": "serving amplitudes/s and p50/p99 latency", "value": round(cap_batched["amps_per_s"], 2),
             "unit": "amplitudes/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
             "config": {"workload": f"{args.requests} requests: grids 4x4..7x7 (|R-C|<=1), depth 10-24, 1-4096 "
                                    f"amplitudes each, cost cap 2^{args.cost_cap} CMAC",
                        "batched": f"8 in flight, 64-slice quanta, {args.precision}",
                        "plain": "1 in flight, 1-slice quanta, c64"},
-            "batched_saturated": cap_batched, "plain_saturated": cap_plain,
+            "batched_saturated": cap_batched, "batched_c64_saturated": cap_batched_c64, "plain_saturated": cap_plain,
             "poisson_rate_req_per_s": rate, "batched_poisson": lat_batched, "plain_poisson": lat_plain,
             "first_pass_with_planning": pre}
     print(json.dumps(line))
