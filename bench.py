@@ -512,14 +512,18 @@ def run_serve(args):
 
     pre = closed_loop(warm)
     warm.close()
+    # batching alone, at the plain path's accuracy (saturated)
+    batched_c64 = T.Server(max_inflight=8, slices_per_quantum=64, precision="c64", **common)
+    try:
+        cap_batched_c64 = closed_loop(batched_c64)
+    finally:
+        batched_c64.close()
     plain = T.Server(max_inflight=1, slices_per_quantum=1, precision="c64", **common)
     batched = T.Server(max_inflight=8, slices_per_quantum=64, precision=args.precision, **common)
-    batched_c64 = T.Server(max_inflight=8, slices_per_quantum=64, precision="c64", **common)
     try:
         # saturated throughput (every request submitted at once)
         cap_plain = closed_loop(plain)
         cap_batched = closed_loop(batched)
-        cap_batched_c64 = closed_loop(batched_c64)  # batching alone, at the plain path's accuracy
         # latency under Poisson arrivals at 0.7 x the plain path's capacity (requests/s)
         rate = 0.7 * cap_plain["served"] / cap_plain["seconds"]
         lat_plain = closed_loop(plain, rate)
@@ -527,7 +531,6 @@ def run_serve(args):
     finally:
         plain.close()
         batched.close()
-        batched_c64.close()
     line = {"metric": "serving amplitudes/s and p50/p99 latency", "value": round(cap_batched["amps_per_s"], 2),
             "unit": "amplitudes/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
             "config": {"workload": f"{args.requests} requests: grids 4x4..7x7 (|R-C|<=1), depth 10-24, 1-4096 "
