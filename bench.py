@@ -41,7 +41,7 @@ NSLICED = 10
 WIDTH_CAP = 0
 NOPEN = 6
 NBATCH, BSEED = 4, 2
-PLAN_TRIALS, PLAN_SEED, PLAN_HINT = 64, 1, 0
+PLAN_TRIALS, PLAN_SEED, PLAN_HINT, PLAN_CAP_AWARE = 64, 1, 0, 0
 SLICE_LIMIT = -1
 METRIC = "Contraction TFLOP/s & amplitudes/s at stated rel err vs FP64; p50/p99 latency"
 WORKLOAD = "6x6 grid, depth 1+16+1, fSim(pi/2,pi/6); 10 sliced indices (1024 slices); 6 open qubits; 4 batches x 64 amplitudes"
@@ -120,7 +120,7 @@ def make_workload(T, rank):
     net = T.build_network(c, open_q)
     t0 = time.time()
     p = T.plan(net, num_sliced=NSLICED, max_log2_intermediate=WIDTH_CAP, search_trials=PLAN_TRIALS, seed=PLAN_SEED,
-               bitstrings_hint=PLAN_HINT)
+               bitstrings_hint=PLAN_HINT, cap_aware_rewrites=PLAN_CAP_AWARE)
     plan_s = time.time() - t0
     import tn_inputs as I
     words = I.bitstrings(n, NBATCH, BSEED + 1000 * rank)
@@ -567,6 +567,8 @@ def main():
     ap.add_argument("--plan-seed", type=int, default=0, help="planner seed (0: the workload's default)")
     ap.add_argument("--bitstrings-hint", type=int, default=-1,
                     help="planner weight of bitstring-dependent steps (-1: the workload's default)")
+    ap.add_argument("--cap-aware-rewrites", action="store_true",
+                    help="plan with width-cap-aware subtree rewrites (fewer sliced indices under a width cap)")
     args = ap.parse_args()
     if args.workload == "8x8":
         use_8x8()
@@ -575,9 +577,11 @@ def main():
         PLAN_TRIALS = args.plan_trials
     if args.plan_seed > 0:
         PLAN_SEED = args.plan_seed
-    global PLAN_HINT
+    global PLAN_HINT, PLAN_CAP_AWARE
     if args.bitstrings_hint >= 0:
         PLAN_HINT = args.bitstrings_hint
+    if args.cap_aware_rewrites:
+        PLAN_CAP_AWARE = 1
     if args.impl == "reference":
         run_reference(args)
     elif args.micro:

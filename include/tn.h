@@ -155,7 +155,11 @@ typedef struct {
                                     lattice sweep (each grid column merged in time order, then the
                                     columns absorbed from one side; trials cycle through the four
                                     sweep directions), Sec. "A PEPS-based Simulation Method ..." */
-  int32_t reserved2;
+  int32_t cap_aware_rewrites;    /* subtree rewrites after slicing (exact reordering of small
+                                    subtrees) under a width cap: 0 = unconstrained, and the search
+                                    is repeated with constrained rewrites only when no plan met the
+                                    cap; 1 = always constrained (no rewrite builds an intermediate
+                                    wider than the cap: often far cheaper plans under tight caps) */
 } tn_plan_opts;
 
 typedef struct {

@@ -221,7 +221,9 @@ class Plan:
 
 
 def plan(network, num_sliced=-1, max_log2_intermediate=0, search_trials=0, seed=0, max_log2_cmac=0.0,
-         bitstrings_hint=0, order_generator=0):
+         bitstrings_hint=0, order_generator=0, cap_aware_rewrites=0):
+    """tn_plan: contraction order, slicing and layout of `network` (options as
+    the fields of tn_plan_opts in include/tn.h)."""
     o = PlanOpts()
     o.num_sliced = num_sliced
     o.max_log2_intermediate = max_log2_intermediate
@@ -230,6 +232,7 @@ def plan(network, num_sliced=-1, max_log2_intermediate=0, search_trials=0, seed=
     o.max_log2_cmac = max_log2_cmac
     o.bitstrings_hint = bitstrings_hint
     o.order_generator = order_generator
+    o.cap_aware_rewrites = cap_aware_rewrites
     h = C.c_void_p()
     check(lib().tn_plan(network._h, C.byref(o), C.byref(h)))
     return Plan(h, network)

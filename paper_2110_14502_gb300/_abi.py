@@ -40,7 +40,7 @@ class NetworkInfo(C.Structure):
 class PlanOpts(C.Structure):
     _fields_ = [("num_sliced", C.c_int32), ("max_log2_intermediate", C.c_int32), ("search_trials", C.c_int32),
                 ("bitstrings_hint", C.c_int32), ("seed", C.c_uint64), ("max_log2_cmac", C.c_double),
-                ("order_generator", C.c_int32), ("reserved2", C.c_int32)]
+                ("order_generator", C.c_int32), ("cap_aware_rewrites", C.c_int32)]
 
 
 class PlanInfo(C.Structure):

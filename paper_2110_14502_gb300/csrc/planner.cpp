@@ -449,9 +449,10 @@ Eval slice_tree(const std::vector<LSet>& leaves, const std::vector<int>& pairs, 
 // above the frontier by the exact optimum over all contraction orders of the
 // frontier (dynamic programming over subsets), under the step-time model.
 // The frontier's joint label set is order independent, so every rewrite keeps
-// the tree valid.
+// the tree valid.  With wcap > 0 no new intermediate may hold more than wcap
+// unsliced labels, so a rewrite never breaks the per-slice width cap.
 void reconfigure(const std::vector<LSet>& leaves, std::vector<int>& pairs, const std::vector<int>& sliced,
-                 int k, int passes, const std::vector<char>& var_leaf, double hint) {
+                 int k, int passes, const std::vector<char>& var_leaf, double hint, int wcap) {
   const int L = (int)leaves.size();
   if (L < 3) return;
   std::vector<int> lch(L, -1), rch(L, -1);
@@ -507,6 +508,10 @@ void reconfigure(const std::vector<LSet>& leaves, std::vector<int>& pairs, const
         if (S == low) { ss[S] = sets[front[__builtin_ctz(S)]]; vs[S] = var[front[__builtin_ctz(S)]]; continue; }
         ss[S] = sym_diff(ss[S ^ low], ss[low]);
         vs[S] = vs[S ^ low] | vs[low];
+        if (wcap > 0 && S != full && (int)ss[S].size() > wcap) {  // over the width cap: never built
+          best[S] = 1e300;
+          continue;
+        }
         double b = 1e300;
         int bs = 0;
         // sub-splits containing the lowest bit
@@ -594,66 +599,85 @@ tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& P) {
                 (int)sliceable.size());
 
   const int trials = opts.search_trials > 0 ? opts.search_trials : 128;
-  std::mt19937_64 rng(opts.seed ^ 0x5DEECE66Dull);
-  std::vector<int> best_pairs;
-  Eval best;
-  bool have = false;
   std::vector<int> all(L);
   std::iota(all.begin(), all.end(), 0);
-  for (int t = 0; t < (L == 1 ? 1 : trials); ++t) {
-    Builder B(leaves);
-    std::mt19937_64 r2(rng());
-    if (L > 1 && opts.order_generator == 1) {
-      lattice_join(B, net, t % 4);
-    } else if (L > 1) {
-      if (t % 2 == 0) {
-        double alpha = std::uniform_real_distribution<double>(0.0, 1.5)(r2);
-        const double taus[] = {0.0, 0.01, 0.05, 0.1, 0.3, 1.0};
-        double tau = taus[std::uniform_int_distribution<int>(0, 5)(r2)];
-        greedy_join(B, all, alpha, tau, r2);
-      } else {
-        int cutoff = std::uniform_int_distribution<int>(4, 24)(r2);
-        double eps = std::uniform_real_distribution<double>(0.02, 0.4)(r2);
-        double alpha = std::uniform_real_distribution<double>(0.0, 1.0)(r2);
-        bisect_tree(B, all, cutoff, eps, alpha, r2);
+  // One search: `trials` randomized trees, each sliced and rewritten, the best
+  // kept and polished.  With cap_aware the rewrites after slicing build no
+  // intermediate wider than the width cap; otherwise they may, and a trial
+  // whose rewrite broke the cap only wins when no trial kept it.
+  auto search = [&](bool cap_aware, Eval& best, std::vector<int>& best_pairs) -> bool {
+    const int wcap = cap_aware ? opts.max_log2_intermediate : 0;
+    std::mt19937_64 rng(opts.seed ^ 0x5DEECE66Dull);
+    bool have = false;
+    for (int t = 0; t < (L == 1 ? 1 : trials); ++t) {
+      Builder B(leaves);
+      std::mt19937_64 r2(rng());
+      if (L > 1 && opts.order_generator == 1) {
+        lattice_join(B, net, t % 4);
+      } else if (L > 1) {
+        if (t % 2 == 0) {
+          double alpha = std::uniform_real_distribution<double>(0.0, 1.5)(r2);
+          const double taus[] = {0.0, 0.01, 0.05, 0.1, 0.3, 1.0};
+          double tau = taus[std::uniform_int_distribution<int>(0, 5)(r2)];
+          greedy_join(B, all, alpha, tau, r2);
+        } else {
+          int cutoff = std::uniform_int_distribution<int>(4, 24)(r2);
+          double eps = std::uniform_real_distribution<double>(0.02, 0.4)(r2);
+          double alpha = std::uniform_real_distribution<double>(0.0, 1.0)(r2);
+          bisect_tree(B, all, cutoff, eps, alpha, r2);
+        }
+      }
+      reconfigure(leaves, B.pairs, {}, 6, 3, var_leaf, hint, 0);
+      if (opts.max_log2_cmac > 0) {
+        // slicing only adds work: a tree already above the cost cap is dropped unsliced
+        std::vector<LSet> st0;
+        node_sets(leaves, B.pairs, {}, st0);
+        double t0, c0;
+        int w0;
+        cost_of(st0, B.pairs, L, step_weights(var_leaf, B.pairs, hint), t0, c0, w0);
+        if (std::log2(std::max(c0, 1.0)) > opts.max_log2_cmac) continue;
+      }
+      Eval ev = slice_tree(leaves, B.pairs, sliceable, opts.num_sliced, opts.max_log2_intermediate,
+                           step_weights(var_leaf, B.pairs, hint));
+      if (!ev.sliced.empty()) {
+        reconfigure(leaves, B.pairs, ev.sliced, 6, 3, var_leaf, hint, wcap);
+        std::vector<LSet> st;
+        node_sets(leaves, B.pairs, ev.sliced, st);
+        cost_of(st, B.pairs, L, step_weights(var_leaf, B.pairs, hint), ev.time, ev.cmac, ev.width);
+      }
+      double score = ev.time * std::ldexp(1.0, (int)ev.sliced.size());
+      double bscore = have ? best.time * std::ldexp(1.0, (int)best.sliced.size()) : 0;
+      bool ok_cap = opts.max_log2_intermediate <= 0 || ev.width <= opts.max_log2_intermediate;
+      bool bok_cap = have && (opts.max_log2_intermediate <= 0 || best.width <= opts.max_log2_intermediate);
+      if (!have || (ok_cap && !bok_cap) || (ok_cap == bok_cap && score < bscore)) {
+        best = ev;
+        best_pairs = B.pairs;
+        have = true;
       }
     }
-    reconfigure(leaves, B.pairs, {}, 6, 3, var_leaf, hint);
-    if (opts.max_log2_cmac > 0) {
-      // slicing only adds work: a tree already above the cost cap is dropped unsliced
-      std::vector<LSet> st0;
-      node_sets(leaves, B.pairs, {}, st0);
-      double t0, c0;
-      int w0;
-      cost_of(st0, B.pairs, L, step_weights(var_leaf, B.pairs, hint), t0, c0, w0);
-      if (std::log2(std::max(c0, 1.0)) > opts.max_log2_cmac) continue;
-    }
-    Eval ev = slice_tree(leaves, B.pairs, sliceable, opts.num_sliced, opts.max_log2_intermediate,
-                         step_weights(var_leaf, B.pairs, hint));
-    if (!ev.sliced.empty()) {
-      reconfigure(leaves, B.pairs, ev.sliced, 6, 3, var_leaf, hint);
+    if (have && L > 2) {  // polish the winner with a wider window
+      reconfigure(leaves, best_pairs, best.sliced, 8, 6, var_leaf, hint, wcap);
       std::vector<LSet> st;
-      node_sets(leaves, B.pairs, ev.sliced, st);
-      cost_of(st, B.pairs, L, step_weights(var_leaf, B.pairs, hint), ev.time, ev.cmac, ev.width);
+      node_sets(leaves, best_pairs, best.sliced, st);
+      cost_of(st, best_pairs, L, step_weights(var_leaf, best_pairs, hint), best.time, best.cmac, best.width);
     }
-    double score = ev.time * std::ldexp(1.0, (int)ev.sliced.size());
-    double bscore = have ? best.time * std::ldexp(1.0, (int)best.sliced.size()) : 0;
-    bool ok_cap = opts.max_log2_intermediate <= 0 || ev.width <= opts.max_log2_intermediate;
-    bool bok_cap = have && (opts.max_log2_intermediate <= 0 || best.width <= opts.max_log2_intermediate);
-    if (!have || (ok_cap && !bok_cap) || (ok_cap == bok_cap && score < bscore)) {
-      best = ev;
-      best_pairs = B.pairs;
-      have = true;
+    return have;
+  };
+  Eval best;
+  std::vector<int> best_pairs;
+  const bool cap_aware = opts.cap_aware_rewrites == 1;
+  bool have = search(cap_aware, best, best_pairs);
+  if (have && !cap_aware && opts.max_log2_intermediate > 0 && best.width > opts.max_log2_intermediate) {
+    // every trial's rewrites broke the width cap: search again keeping it
+    Eval b2;
+    std::vector<int> p2;
+    if (search(true, b2, p2)) {
+      best = b2;
+      best_pairs.swap(p2);
     }
   }
   if (!have)
     return fail(TN_ETOOBIG, "tn_plan: every searched order costs more than the cap 2^%.1f CMAC", opts.max_log2_cmac);
-  if (L > 2) {  // polish the winner with a wider window
-    reconfigure(leaves, best_pairs, best.sliced, 8, 6, var_leaf, hint);
-    std::vector<LSet> st;
-    node_sets(leaves, best_pairs, best.sliced, st);
-    cost_of(st, best_pairs, L, step_weights(var_leaf, best_pairs, hint), best.time, best.cmac, best.width);
-  }
   if (opts.max_log2_intermediate > 0 && best.width > opts.max_log2_intermediate)
     return fail(TN_ETOOBIG, "tn_plan: could not reach width 2^%d (best 2^%d with %d sliced)",
                 opts.max_log2_intermediate, best.width, (int)best.sliced.size());
@@ -895,6 +919,8 @@ extern "C" tn_status tn_plan(const tn_network* net, const tn_plan_opts* opts, tn
   if (o.max_log2_intermediate < 0 || o.max_log2_intermediate > 30)
     return fail(TN_EINVAL, "tn_plan: max_log2_intermediate %d not in [0, 30]", o.max_log2_intermediate);
   if (o.search_trials < 0 || o.search_trials > 100000) return fail(TN_EINVAL, "tn_plan: bad search_trials");
+  if (o.cap_aware_rewrites < 0 || o.cap_aware_rewrites > 1)
+    return fail(TN_EINVAL, "tn_plan: cap_aware_rewrites %d not 0 or 1", o.cap_aware_rewrites);
   return guarded("tn_plan", [&]() -> tn_status {
     std::unique_ptr<tn_plan_s> h(new tn_plan_s);
     tn_status st = make_plan(net->net, o, h->plan);

@@ -294,3 +294,55 @@ def test_binding_checks_buffers_before_passing_pointers():
             require_buffer(bad, "x", 32, False, ("complex64",))
     with pytest.raises(T.TnError):
         require_buffer(np.zeros(4, np.complex64), "x", 32, True, ("complex64",))
+
+
+@pytest.mark.parametrize("rows,cols,depth,seed,open_q,kw", [
+    (3, 3, 5, 11, (8,), dict(num_sliced=2)),
+    (4, 4, 8, 12, (), dict(max_log2_intermediate=9)),
+    (3, 5, 9, 13, (12, 13, 14), dict(num_sliced=3, order_generator=1)),
+    (5, 4, 10, 14, (18, 19), dict(max_log2_intermediate=11, bitstrings_hint=8)),
+])
+def test_plan_tree_is_a_binary_tree_over_the_leaves(rows, cols, depth, seed, open_q, kw):
+    """Structure of any plan: L - 1 steps whose operands are SSA ids, each
+    leaf and each intermediate consumed exactly once, every operand defined
+    before its use, the last step the root; the leaves' raw gate lists
+    partition the circuit's gates and input vectors; the width cap holds."""
+    T = tnlib()
+    n = rows * cols
+    c, net, p = _plan(T, rows, cols, depth, seed, open_q, search_trials=8, seed=5, **kw)
+    info = p.info()
+    L = info["num_leaves"]
+    ng = len(c.gates())
+    leaves, pairs = p.tree(ng, n)
+    assert len(leaves) == L and len(pairs) == L - 1 == info["num_steps"]
+    used = []
+    for i, (a, b) in enumerate(pairs):
+        assert a != b and max(a, b) < L + i          # defined before use
+        used += [a, b]
+    assert sorted(used) == list(range(L + len(pairs) - 1))   # everything but the root, once
+    raws = sorted(r for lf in leaves for r in lf)
+    assert raws == list(range(ng + n))
+    if kw.get("max_log2_intermediate"):
+        assert info["max_log2_intermediate"] <= kw["max_log2_intermediate"]
+
+
+def test_cap_aware_rewrites_keep_the_width_cap_and_cut_the_8x8_cost():
+    """Subtree rewrites after slicing may widen an intermediate beyond the
+    per-slice width cap; a trial whose rewrite did so loses to any trial that
+    kept the cap.  Constraining the rewrites (cap_aware_rewrites=1) keeps
+    every trial valid: on the 8x8 depth-(1+20+1) network under a 2^26 cap the
+    plan needs 12 fewer sliced indices and 2^10 less total work.  The default
+    search keeps its plans (the bench's 8x8 plan hash below) and falls back to
+    constrained rewrites only when no trial met the cap."""
+    T = tnlib()
+    net = T.build_network(T.random_circuit(8, 8, 20, 4), list(range(54, 64)))
+    kw = dict(max_log2_intermediate=26, search_trials=16, seed=1)
+    plain = T.plan(net, **kw).info()
+    aware = T.plan(net, cap_aware_rewrites=1, **kw).info()
+    assert hex(plain["hash"]) == "0x5973de292b52ff33"
+    assert plain["max_log2_intermediate"] <= 26 and aware["max_log2_intermediate"] <= 26
+    assert aware["num_sliced"] <= plain["num_sliced"] - 12
+    assert aware["log2_cmac_total"] <= plain["log2_cmac_total"] - 10
+    with pytest.raises(T.TnError) as e:
+        T.plan(net, cap_aware_rewrites=2, **kw)
+    assert e.value.status == 1
