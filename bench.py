@@ -216,7 +216,7 @@ def run_ours(args):
     flops_eq = sum(r["flops_equivalent"] for r in reps) * world
     amps = nout * args.steps * world
     value = flops / (total_ms * 1e-3) / 1e12
-    launches = int(sum(r["kernel_launches"] for r in reps) / len(reps))
+    launches = int(sum(r["kernel_launches"] for r in reps))  # every launch of the timed steps
 
     # roofline of the dominant kernel class over the timed steps
     hbm, bf16, bf16_sus, sm_max, src = peaks()
@@ -290,7 +290,7 @@ def run_ours(args):
         "flops_equivalent_tflops": round(flops_eq / (total_ms * 1e-3) / 1e12, 3),
         "p50_ms": round(float(np.percentile(times, 50)), 3), "p99_ms": round(float(np.percentile(times, 99)), 3),
         "plan_s": round(plan_s, 3),
-        "gpu_launches": launches,
+        "gpu_launches": launches, "gpu_launches_per_step": launches // args.steps,
         "roofline": roof,
         "clocks": clk.summary(),
         "e2e": {"value": round(e2e_flops / e2e_s / 1e12, 3), "unit": "TFLOP/s",
