@@ -191,6 +191,27 @@ tn_status tn_plan_serialize(const tn_plan_t* p, uint8_t* buf, size_t capacity, s
  * input vector of qubit q); tree receives 2*(num_leaves-1) SSA ids (leaves
  * 0..L-1, step i result L+i).  Sizes via tn_plan_get_info. */
 tn_status tn_plan_tree(const tn_plan_t* p, int32_t* leaf_raw, int64_t leaf_raw_capacity, int32_t* tree, int64_t tree_capacity);
+
+/* Where each tensor of a slice's contraction lives in device memory (the
+ * planner's layout: a leaf store, an invariant store, and per-slice and
+ * per-(bitstring, slice) arenas reused by liveness). */
+typedef struct {
+  int32_t phase;        /* 0: leaf store (a leaf) or invariant store (a step output);
+                           1: slice arena (slice-only tensors); 2: pair arena (per bitstring and slice) */
+  int32_t producer;     /* step writing the tensor; -1 for a leaf */
+  int32_t consumer;     /* step reading it; -1 for the root */
+  int32_t log2_elems;   /* complex64 elements as contracted (fixed indices removed), log2 */
+  int64_t offset;       /* element offset in the memory named by phase (per slice / per unit for 1, 2) */
+  int64_t store_offset; /* a leaf: element offset of the whole leaf in the leaf store; -1 for a step output */
+  int32_t store_log2;   /* a leaf: log2 elements of the whole leaf (fixed indices included); -1 otherwise */
+  int32_t reserved;
+} tn_tensor_layout;
+
+/* Fills out[x] for every SSA tensor x (leaves 0..L-1, step i's output L+i;
+ * capacity >= num_leaves + num_steps) and arena_elems[0..3] with the sizes in
+ * complex64 elements of the leaf store, the invariant store, the slice arena
+ * (per slice) and the pair arena (per bitstring and slice). */
+tn_status tn_plan_layout(const tn_plan_t* p, tn_tensor_layout* out, int64_t capacity, int64_t* arena_elems);
 void tn_free_plan(tn_plan_t* p);
 
 /* ------------------------------------------------------------------ */

@@ -10,7 +10,7 @@ import ctypes as C
 import numpy as np
 
 from ._abi import (PAIR_ALGO, PREC, ExecOpts, Gate, NetworkInfo, PlanInfo, PlanOpts, Report, Request,
-                   RequestStats, ServerOpts, TnError, check, i32array, lib, require_buffer)
+                   RequestStats, ServerOpts, TensorLayout, TnError, check, i32array, lib, require_buffer)
 
 __all__ = ["Circuit", "Network", "Plan", "random_circuit", "circuit_from_gates", "build_network", "plan", "select_plan",
            "contract_pair", "contract_pair_noalloc", "Server", "TnError", "PREC", "version"]
@@ -139,6 +139,19 @@ class Plan:
         buf = (C.c_uint8 * n.value)()
         check(lib().tn_plan_serialize(self._h, buf, n.value, C.byref(n)))
         return bytes(buf)
+
+    def layout(self):
+        """tn_plan_layout: ([per SSA tensor dict of phase, producer, consumer,
+        log2_elems, offset, store_offset, store_log2], {"leaf_store",
+        "invariant", "slice_arena", "pair_arena"} sizes in complex64 elements)."""
+        info = self.info()
+        nt = info["num_leaves"] + info["num_steps"]
+        arr = (TensorLayout * max(nt, 1))()
+        sizes = (C.c_int64 * 4)()
+        check(lib().tn_plan_layout(self._h, arr, nt, sizes))
+        names = [f for f, _ in TensorLayout._fields_ if f != "reserved"]
+        tensors = [{f: getattr(arr[i], f) for f in names} for i in range(nt)]
+        return tensors, dict(zip(("leaf_store", "invariant", "slice_arena", "pair_arena"), list(sizes)))
 
     def tree(self, num_gates, num_qubits):
         """(leaf raw-tensor lists, SSA pairs) of the contraction tree."""

@@ -51,6 +51,12 @@ class PlanInfo(C.Structure):
                 ("num_dense_steps", C.c_int32), ("num_vector_steps", C.c_int32)]
 
 
+class TensorLayout(C.Structure):
+    _fields_ = [("phase", C.c_int32), ("producer", C.c_int32), ("consumer", C.c_int32), ("log2_elems", C.c_int32),
+                ("offset", C.c_int64), ("store_offset", C.c_int64), ("store_log2", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 class ExecOpts(C.Structure):
     _fields_ = [("stream", C.c_void_p), ("precision", C.c_int32), ("device_io", C.c_int32),
                 ("slice_begin", C.c_int64), ("slice_count", C.c_int64), ("units_per_group", C.c_int32),
@@ -105,6 +111,7 @@ SIGNATURES = {
     "tn_plan_sliced_wires": (C.c_int, [P, I32P, C.c_int64]),
     "tn_plan_serialize": (C.c_int, [P, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "tn_plan_tree": (C.c_int, [P, I32P, C.c_int64, I32P, C.c_int64]),
+    "tn_plan_layout": (C.c_int, [P, C.POINTER(TensorLayout), C.c_int64, C.POINTER(C.c_int64)]),
     "tn_free_plan": (None, [P]),
     "tn_contract_amplitudes": (C.c_int, [P, C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(ExecOpts),
                                          C.POINTER(Report)]),

@@ -996,3 +996,48 @@ extern "C" tn_status tn_plan_tree(const tn_plan_t* p, int32_t* leaf_raw, int64_t
   }
   return TN_OK;
 }
+
+extern "C" tn_status tn_plan_layout(const tn_plan_t* p, tn_tensor_layout* out, int64_t capacity,
+                                    int64_t* arena_elems) {
+  if (!p || !out || !arena_elems) return fail(TN_EINVAL, "tn_plan_layout: NULL argument");
+  const Plan& P = p->plan;
+  const int L = (int)P.net.leaves.size();
+  const int64_t nt = L + (int64_t)P.steps.size();
+  if (capacity < nt) return fail(TN_EINVAL, "tn_plan_layout: capacity %lld < %lld tensors", (long long)capacity,
+                                 (long long)nt);
+  return guarded("tn_plan_layout", [&]() -> tn_status {
+    std::vector<int32_t> consumer(nt, -1);
+    for (size_t s = 0; s < P.steps.size(); ++s) {
+      consumer[P.steps[s].a] = (int32_t)s;
+      consumer[P.steps[s].b] = (int32_t)s;
+    }
+    for (int i = 0; i < L; ++i) {
+      const LeafUse& U = P.leaf_use[i];
+      tn_tensor_layout t{};
+      t.phase = U.phase;
+      t.producer = -1;
+      t.consumer = consumer[i];
+      t.log2_elems = (int32_t)U.sub_labels.size();
+      t.offset = U.off;
+      t.store_offset = U.store_off;
+      t.store_log2 = (int32_t)P.net.leaves[i].labels.size();
+      out[i] = t;
+    }
+    for (size_t s = 0; s < P.steps.size(); ++s) {
+      tn_tensor_layout t{};
+      t.phase = P.steps[s].phase;
+      t.producer = (int32_t)s;
+      t.consumer = consumer[L + s];
+      t.log2_elems = (int32_t)P.steps[s].lc.size();
+      t.offset = P.steps[s].off_c;
+      t.store_offset = -1;
+      t.store_log2 = -1;
+      out[L + s] = t;
+    }
+    arena_elems[0] = P.leaf_store_elems;
+    arena_elems[1] = P.invariant_elems;
+    arena_elems[2] = P.slice_arena_elems;
+    arena_elems[3] = P.unit_arena_elems;
+    return TN_OK;
+  });
+}

@@ -346,3 +346,89 @@ def test_cap_aware_rewrites_keep_the_width_cap_and_cut_the_8x8_cost():
     with pytest.raises(T.TnError) as e:
         T.plan(net, cap_aware_rewrites=2, **kw)
     assert e.value.status == 1
+
+
+def _check_layout(tensors, size, info):
+    """Memory layout invariants of a plan (see test below); returns the
+    number of tensors checked per memory."""
+    L = info["num_leaves"]
+    assert len(tensors) == L + info["num_steps"]
+    # the tree: every tensor but the root consumed once, by a later step
+    assert sum(t["consumer"] < 0 for t in tensors) == 1
+    for x, t in enumerate(tensors):
+        assert (t["producer"] < 0) == (x < L)
+        assert t["consumer"] < 0 or t["consumer"] > max(t["producer"], -1)
+    # execution order: phase 0 steps, then phase 1, then phase 2, each in step order
+    order = sorted(range(info["num_steps"]), key=lambda s: (tensors[L + s]["phase"], s))
+    when = {s: i for i, s in enumerate(order)}
+    END = len(order)
+    spaces = {"leaf_store": [], "invariant": [], "slice_arena": [], "pair_arena": []}
+    for x, t in enumerate(tensors):
+        n = 1 << t["log2_elems"]
+        assert t["offset"] % 32 == 0
+        if x < L:
+            spaces["leaf_store"].append((t["store_offset"], 1 << t["store_log2"], -1, END))
+            assert t["store_offset"] % 32 == 0 and t["store_log2"] >= t["log2_elems"]
+            if t["phase"] == 0:
+                assert t["offset"] == t["store_offset"]
+                continue
+        born = -1 if x < L else when[t["producer"]]
+        c = t["consumer"]
+        # a tensor is freed when a step of its own phase consumes it; one read by
+        # a later phase (or the root) stays until the end
+        dies = when[c] if c >= 0 and tensors[L + c]["phase"] == t["phase"] else END
+        space = ("invariant", "slice_arena", "pair_arena")[t["phase"]]
+        spaces[space].append((t["offset"], n, born, dies))
+    for name, blocks in spaces.items():
+        for off, n, _, _ in blocks:
+            assert 0 <= off and off + n <= size[name], name
+        for i in range(len(blocks)):
+            for j in range(i + 1, len(blocks)):
+                (o1, n1, b1, d1), (o2, n2, b2, d2) = blocks[i], blocks[j]
+                live_together = not (d1 < b2 or d2 < b1)
+                apart = o1 + n1 <= o2 or o2 + n2 <= o1
+                assert apart or not live_together, (name, blocks[i], blocks[j])
+    return {k: len(v) for k, v in spaces.items()}
+
+
+@pytest.mark.parametrize("rows,cols,depth,seed,open_q,kw", [
+    (3, 4, 8, 2, (10, 11), dict(num_sliced=3)),
+    (4, 4, 10, 5, (15, 14), dict(num_sliced=4)),
+    (4, 5, 12, 21, (17, 18, 19), dict(max_log2_intermediate=12)),
+    (5, 5, 12, 3, (22, 23, 24), dict(max_log2_intermediate=14, bitstrings_hint=4)),
+    (6, 6, 16, 2, tuple(range(30, 36)), dict(num_sliced=10, search_trials=64, seed=1)),
+])
+def test_plan_memory_layout_is_disjoint_while_live(rows, cols, depth, seed, open_q, kw):
+    """The planner's HBM layout: leaves packed in the leaf store, phase-0
+    results in the invariant store without reuse, slice-only and per-unit
+    tensors in their arenas by first-fit over liveness.  Every tensor is
+    32-element aligned and inside its memory, and no two tensors of one
+    memory overlap while both are live (a step's output is live together with
+    its inputs)."""
+    T = tnlib()
+    kw = dict(dict(search_trials=16, seed=3), **kw)
+    _, _, p = _plan(T, rows, cols, depth, seed, open_q, **kw)
+    counts = _check_layout(*p.layout(), p.info())
+    assert counts["leaf_store"] == p.info()["num_leaves"]
+
+
+def test_layout_check_catches_an_overlap():
+    """The layout check is not vacuous: moving a step's output onto one of its
+    own inputs, or past the end of its arena, fails it."""
+    T = tnlib()
+    _, _, p = _plan(T, 4, 4, 10, 5, (15, 14), num_sliced=4, search_trials=16, seed=3)
+    tensors, size = p.layout()
+    info = p.info()
+    L = info["num_leaves"]
+    _check_layout(tensors, size, info)
+    s = next(s for s in range(info["num_steps"])
+             if tensors[L + s]["phase"] == 2 and any(t["consumer"] == s and t["phase"] == 2 for t in tensors))
+    src = next(t for t in tensors if t["consumer"] == s and t["phase"] == 2)
+    bad = [dict(t) for t in tensors]
+    bad[L + s]["offset"] = src["offset"]
+    with pytest.raises(AssertionError):
+        _check_layout(bad, size, info)
+    bad = [dict(t) for t in tensors]
+    bad[L + s]["offset"] = size["pair_arena"]
+    with pytest.raises(AssertionError):
+        _check_layout(bad, size, info)
