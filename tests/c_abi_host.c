@@ -1,5 +1,6 @@
 /* Host-only use of the library from plain C99 through include/tn.h: circuit,
- * network and plan handles, plan determinism, error reporting and NULL frees.
+ * network and plan handles, plan determinism, the memory layout, error
+ * reporting and NULL frees.
  * Prints one line "hash=<hex> slices=<n> steps=<n> bytes=<n>" on success and
  * exits non-zero on the first failed check. */
 #include <stdio.h>
@@ -20,6 +21,8 @@
 static int plan_bytes(const tn_network* net, uint8_t** bytes, size_t* len, tn_plan_info* info) {
   tn_plan_opts o;
   tn_plan_t* p = NULL;
+  tn_tensor_layout* lay = NULL;
+  int64_t arena[4], nt, x;
   memset(&o, 0, sizeof o);
   o.num_sliced = 2;
   o.search_trials = 8;
@@ -30,6 +33,18 @@ static int plan_bytes(const tn_network* net, uint8_t** bytes, size_t* len, tn_pl
   *bytes = (uint8_t*)malloc(*len);
   CHECK(*bytes != NULL);
   CHECK(tn_plan_serialize(p, *bytes, *len, len) == TN_OK);
+  /* the layout: one entry per tensor, the root the only tensor nobody reads */
+  nt = (int64_t)info->num_leaves + info->num_steps;
+  lay = (tn_tensor_layout*)malloc((size_t)nt * sizeof *lay);
+  CHECK(lay != NULL);
+  CHECK(tn_plan_layout(p, lay, nt - 1, arena) == TN_EINVAL);
+  CHECK(tn_plan_layout(p, lay, nt, arena) == TN_OK);
+  for (x = 0; x < nt; ++x) {
+    CHECK((lay[x].consumer < 0) == (x == nt - 1));
+    CHECK(lay[x].offset >= 0 && lay[x].offset % 32 == 0);
+  }
+  CHECK(arena[0] > 0 && arena[2] > 0 && arena[3] > 0);
+  free(lay);
   tn_free_plan(p);
   return 0;
 }
