@@ -432,3 +432,48 @@ def test_layout_check_catches_an_overlap():
     bad[L + s]["offset"] = size["pair_arena"]
     with pytest.raises(AssertionError):
         _check_layout(bad, size, info)
+
+
+def _random_configs(count, seed=2024):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        rows, cols = int(rng.integers(1, 4)), int(rng.integers(2, 5))
+        n = rows * cols
+        depth = int(rng.integers(0, 9))
+        k = int(rng.integers(0, min(n, 4) + 1))
+        open_q = tuple(sorted(int(q) for q in rng.choice(n, size=k, replace=False)))
+        kw = dict(search_trials=int(rng.integers(1, 9)), seed=int(rng.integers(1, 1000)),
+                  order_generator=int(rng.integers(0, 2)), bitstrings_hint=int(rng.integers(0, 5)))
+        out.append((rows, cols, depth, int(rng.integers(1, 10 ** 6)), open_q, int(rng.integers(0, 4)), kw))
+    return out
+
+
+@pytest.mark.parametrize("rows,cols,depth,cseed,open_q,ns,kw", _random_configs(16))
+def test_random_small_plans_are_exact(rows, cols, depth, cseed, open_q, ns, kw):
+    """Sixteen seeded random small circuits (1..3 x 2..4 grids, depth 0..8,
+    0..4 open qubits at random positions, up to 3 sliced indices (as many as
+    the network has), random planner options): the plan's tree replayed by
+    the oracle and summed over all 2^S slice assignments equals the state
+    vector, and the memory layout holds."""
+    T = tnlib()
+    from _replay import replay
+    n = rows * cols
+    c = T.random_circuit(rows, cols, depth, cseed)
+    net = T.build_network(c, list(open_q))
+    while True:                                         # the most sliced indices <= ns the network has
+        try:
+            p = T.plan(net, num_sliced=ns, **kw)
+            break
+        except T.TnError as e:
+            assert e.status == 1 and "exceeds" in str(e) and ns > 0, str(e)
+            ns -= 1
+    gates = OC.random_circuit(rows, cols, depth, cseed)
+    bits = I.bits_of(I.bitstrings(n, 1, cseed)[0], n)
+    wires = p.sliced_wires()
+    S = len(wires)
+    total = sum(replay(p, gates, n, bits, open_q, {wires[j]: (s >> j) & 1 for j in range(S)} if S else None)
+                for s in range(1 << S))
+    ref = SV.amplitudes(SV.simulate(gates, n), n, [bits], open_q)[0]
+    assert np.linalg.norm(total - ref) <= 1e-12 * max(np.linalg.norm(ref), 1e-300)
+    _check_layout(*p.layout(), p.info())
