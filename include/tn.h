@@ -204,6 +204,11 @@ typedef struct {
   int64_t offset;       /* element offset in the memory named by phase (per slice / per unit for 1, 2) */
   int64_t store_offset; /* a leaf: element offset of the whole leaf in the leaf store; -1 for a step output */
   int32_t store_log2;   /* a leaf: log2 elements of the whole leaf (fixed indices included); -1 otherwise */
+  int32_t step_class;   /* a step output: the planned class of its step: 0 dense (a GEMM: on the tensor
+                           cores in a tensor-core precision when M >= 128, N >= 16 and K >= 8, else FP32),
+                           1 vector-like (streaming kernels); -1 for a leaf */
+  int32_t log2_m, log2_n, log2_k; /* a step output: its step's GEMM shape (M rows of A, N columns of B,
+                                     K contracted); -1 for a leaf */
   int32_t reserved;
 } tn_tensor_layout;
 

@@ -54,6 +54,7 @@ class PlanInfo(C.Structure):
 class TensorLayout(C.Structure):
     _fields_ = [("phase", C.c_int32), ("producer", C.c_int32), ("consumer", C.c_int32), ("log2_elems", C.c_int32),
                 ("offset", C.c_int64), ("store_offset", C.c_int64), ("store_log2", C.c_int32),
+                ("step_class", C.c_int32), ("log2_m", C.c_int32), ("log2_n", C.c_int32), ("log2_k", C.c_int32),
                 ("reserved", C.c_int32)]
 
 

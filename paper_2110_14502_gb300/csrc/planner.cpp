@@ -1021,6 +1021,7 @@ extern "C" tn_status tn_plan_layout(const tn_plan_t* p, tn_tensor_layout* out, i
       t.offset = U.off;
       t.store_offset = U.store_off;
       t.store_log2 = (int32_t)P.net.leaves[i].labels.size();
+      t.step_class = t.log2_m = t.log2_n = t.log2_k = -1;
       out[i] = t;
     }
     for (size_t s = 0; s < P.steps.size(); ++s) {
@@ -1032,6 +1033,10 @@ extern "C" tn_status tn_plan_layout(const tn_plan_t* p, tn_tensor_layout* out, i
       t.offset = P.steps[s].off_c;
       t.store_offset = -1;
       t.store_log2 = -1;
+      t.step_class = P.steps[s].klass;
+      t.log2_m = P.steps[s].nm;
+      t.log2_n = P.steps[s].nn;
+      t.log2_k = P.steps[s].nk;
       out[L + s] = t;
     }
     arena_elems[0] = P.leaf_store_elems;

@@ -477,3 +477,29 @@ def test_random_small_plans_are_exact(rows, cols, depth, cseed, open_q, ns, kw):
     ref = SV.amplitudes(SV.simulate(gates, n), n, [bits], open_q)[0]
     assert np.linalg.norm(total - ref) <= 1e-12 * max(np.linalg.norm(ref), 1e-300)
     _check_layout(*p.layout(), p.info())
+
+
+def test_step_shapes_account_for_the_counted_work():
+    """The GEMM shape of every step in the layout: its output holds M N
+    elements, its operands M K and K N (in either order), and the counted
+    work of a slice, 2^(m+n+k) complex MACs summed over the steps, is the
+    plan's cmac_per_slice exactly (the flops the bench reports are these).
+    Vector-like steps are the narrow ones."""
+    T = tnlib()
+    import bench
+    _, _, p, _, _, _ = bench.make_workload(T, 0)
+    tensors, _ = p.layout()
+    info = p.info()
+    L = info["num_leaves"]
+    total = 0.0
+    for s, t in enumerate(tensors[L:]):
+        m, n, k = t["log2_m"], t["log2_n"], t["log2_k"]
+        assert t["log2_elems"] == m + n
+        ops = sorted(tensors[x]["log2_elems"] for x in range(len(tensors)) if tensors[x]["consumer"] == s)
+        assert ops == sorted([m + k, k + n]), s
+        assert t["step_class"] in (0, 1)
+        if t["step_class"] == 1:
+            assert (n <= 4 and k <= 4) or (n <= 3 and k <= 7)
+        total += 2.0 ** (m + n + k)
+    assert total == info["cmac_per_slice"]
+    assert info["num_vector_steps"] == sum(t["step_class"] == 1 for t in tensors[L:])
