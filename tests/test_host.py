@@ -503,3 +503,17 @@ def test_step_shapes_account_for_the_counted_work():
         total += 2.0 ** (m + n + k)
     assert total == info["cmac_per_slice"]
     assert info["num_vector_steps"] == sum(t["step_class"] == 1 for t in tensors[L:])
+
+
+def test_plan_hash_is_fnv1a_of_the_serialized_bytes():
+    """The plan hash is FNV-1a 64 (offset basis 0xcbf29ce484222325, prime
+    0x100000001b3, Fowler-Noll-Vo) over the serialized plan, computed here
+    independently; the bytes start with the format tag."""
+    T = tnlib()
+    _, _, p = _plan(T, 4, 4, 8, 1, open_q=(14, 15), num_sliced=2, search_trials=8, seed=3)
+    b = p.serialize()
+    h = 0xcbf29ce484222325
+    for x in b:
+        h = ((h ^ x) * 0x100000001b3) & 0xFFFFFFFFFFFFFFFF
+    assert h == p.info()["hash"]
+    assert b[:8] == b"TNPLAN01"
