@@ -173,8 +173,10 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
+        # replicas share nothing on the data path: the process group (gloo,
+        # on the host) only carries the barriers and the max-over-ranks time
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.init_process_group("gloo")
     c, net, p, words, open_q, plan_s = make_workload(T, rank)
     info = p.info()
     k = info["num_open"]
@@ -209,7 +211,7 @@ def run_ours(args):
         torch.cuda.synchronize()
     total_ms = e0.elapsed_time(e1)
     if dist:
-        t = torch.tensor([total_ms], device="cuda")
+        t = torch.tensor([total_ms], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     flops = sum(r["flops"] for r in reps) * world

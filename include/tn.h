@@ -398,6 +398,21 @@ tn_status tn_contract_pair(const void* A, const int32_t* a_labels, int32_t a_ran
                            void* C, const int32_t* c_labels, int32_t c_rank,
                            int32_t precision, int32_t algo, void* stream);
 
+/* Failure detection of the tensor-core pipelines (Sec. "A Customized
+ * Parallelization Scheme" runs every sub-task to completion; the bound below
+ * is this library's own guard against a pipeline that stops making progress,
+ * the paper has none).  Every wait of a TMA-fed tensor-core kernel (the
+ * kernels of TN_PAIR_FUSED_TC and of tn_contract_amplitudes' 16-bit
+ * precisions) polls its barrier at most `polls` times; a wait that runs out
+ * records an error code, the CTA stops issuing work, waits (with the default
+ * bound) for the copies and MMAs it already issued, releases its shared
+ * memory and TMEM and exits, and the host call returns TN_ETIMEOUT.
+ * polls < 0 restores the default (2^24); 0 makes every pipeline wait give up
+ * at once (used by the tests of the TN_ETIMEOUT path).  Applies to the
+ * current device, for every later launch until changed; synchronous.
+ * Returns TN_ECUDA if the device symbol cannot be written. */
+tn_status tn_set_wait_limit(int64_t polls);
+
 /* Allocation-free variant of tn_contract_pair's tensor-core path (the paper
  * has no counterpart: this serves callers that cannot let a library allocate
  * device memory -- a framework whose caching allocator already holds the free

@@ -195,18 +195,3 @@ def amplitudes(gates, n, bit_rows, open_qubits=(), sliced=None, slice_ids=None):
         else:
             out.append(contract(net))
     return np.array(out)
-
-
-def order_cost(label_lists, pairs):
-    """(log2 of the summed 2^|A u B| work, log2 of the largest tensor) of a tree."""
-    store = {i: frozenset(l) for i, l in enumerate(label_lists)}
-    nid = len(label_lists)
-    work, width = 0.0, max((len(s) for s in store.values()), default=0)
-    for i, j in pairs:
-        a, b = store.pop(i), store.pop(j)
-        work += 2.0 ** len(a | b)
-        c = a ^ b
-        width = max(width, len(c))
-        store[nid] = c
-        nid += 1
-    return float(np.log2(work)) if work > 0 else 0.0, width

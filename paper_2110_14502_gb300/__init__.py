@@ -13,7 +13,7 @@ from ._abi import (PAIR_ALGO, PREC, ExecOpts, Gate, NetworkInfo, PlanInfo, PlanO
                    RequestStats, ServerOpts, TensorLayout, TnError, check, i32array, lib, require_buffer)
 
 __all__ = ["Circuit", "Network", "Plan", "random_circuit", "circuit_from_gates", "build_network", "plan", "select_plan",
-           "contract_pair", "contract_pair_noalloc", "Server", "TnError", "PREC", "version"]
+           "contract_pair", "contract_pair_noalloc", "set_wait_limit", "Server", "TnError", "PREC", "version"]
 
 
 def version():
@@ -310,6 +310,13 @@ def contract_pair_noalloc(A, a_labels, B, b_labels, Cout, c_labels, stream=None)
     s = C.c_void_p(getattr(stream, "cuda_stream", stream) if stream is not None else None)
     check(lib().tn_contract_pair_noalloc(_ptr(A), pa, len(la), _ptr(B), pb, len(lb), _ptr(Cout), pc, len(lc), s))
     return Cout
+
+
+def set_wait_limit(polls=-1):
+    """tn_set_wait_limit: bound on the polls of every pipeline wait of the TMA
+    tensor-core kernels on the current GPU (-1: the default 2^24; 0: every
+    such wait gives up at once and the call returns TN_ETIMEOUT)."""
+    check(lib().tn_set_wait_limit(int(polls)))
 
 
 class Server:

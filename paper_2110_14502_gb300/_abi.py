@@ -125,6 +125,7 @@ SIGNATURES = {
     "tn_server_destroy": (None, [P]),
     "tn_contract_pair_noalloc": (C.c_int, [C.c_void_p, I32P, C.c_int32, C.c_void_p, I32P, C.c_int32,
                                            C.c_void_p, I32P, C.c_int32, C.c_void_p]),
+    "tn_set_wait_limit": (C.c_int, [C.c_int64]),
 }
 
 _lib = None

@@ -39,10 +39,12 @@ namespace tn {
 
 constexpr int kFlaggedCap = 1 << 16;  // listed flagged units per call
 // Default of the plane handover per precision (c64, split bf16, split fp16,
-// scaled fp16, scaled bf16).  A handed-over fp16 tensor is scaled by a bound
-// predicted before its values exist; split fp16, the accurate fp16 mode,
-// instead splits complex64 operands with their exact maxima.
-constexpr bool kHandoverDefault[5] = {false, true, false, true, true};
+// scaled fp16, scaled bf16).  A handed-over 16-bit tensor is scaled by the
+// bound 2 K maxA maxB predicted before its values exist, so its stored
+// maximum may sit a few binades below the target range; in split fp16 the lo
+// plane still carries the bits the hi plane drops, and only components far
+// below the maximum lose precision to fp16's subnormal range.
+constexpr bool kHandoverDefault[5] = {false, true, true, true, true};
 
 // A plan's stem: the leaf store and the phase-0 outputs.  Neither depends on
 // the bitstring, the slice or the precision (phase 0 always runs in
@@ -987,7 +989,7 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
     int herr = 0;
     CK(cudaMemcpy(&herr, E.err, sizeof(int), cudaMemcpyDeviceToHost));
     if (herr) {
-      cudaMemset(E.err, 0, sizeof(int));
+      CK(cudaMemset(E.err, 0, sizeof(int)));
       return fail(TN_ETIMEOUT, "tn_contract_amplitudes: a tensor-core pipeline wait expired (code %d)", herr);
     }
   }

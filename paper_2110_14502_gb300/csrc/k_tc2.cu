@@ -32,8 +32,11 @@
 // back to its empty barrier; warp 2 owns the TMEM allocation; warps 4-7 read
 // the accumulators (tcgen05.ld) and write complex64 C through per-row and
 // per-column offsets (the output permutation).  Every wait is bounded: on
-// expiry the CTA records an error code, stops issuing work, lets its issued
-// MMAs complete (bounded) and releases its TMEM.
+// expiry the CTA records an error code and stops issuing work; before it
+// leaves, the producer waits (bounded) for every TMA load it issued and the
+// MMA warp for every MMA it issued, so no asynchronous copy or MMA still
+// targets the CTA's shared memory or TMEM when it releases them.  Each CTA
+// loads its own operand tiles from this GPU's memory (no clusters).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -52,7 +55,8 @@ constexpr int TM = 128;
 constexpr int TKC = 32;                 // complex K per stage (64-byte rows of 16-bit values)
 constexpr int NTHREADS = 256;
 constexpr int SMEM_BUDGET = 196 * 1024;
-constexpr long long kWaitLimit = 1ll << 24;
+constexpr long long kWaitLimit = 1ll << 24;  // default polls of a pipeline wait
+constexpr long long kDrainLimit = 1ll << 24;  // polls of a wait for this CTA's own copies / MMAs on the way out
 constexpr int GROUP_M_DEFAULT = 16;
 
 template <int TN, int NP>
@@ -73,9 +77,13 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Polls of every pipeline wait of the kernels below on this device (set by
+// set_tc_wait_limit; 0 makes every pipeline wait give up at once).
+__device__ long long g_wait_limit = kWaitLimit;
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
   const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < kWaitLimit; ++it) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -98,28 +106,6 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, u
       "[%7];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
       : "memory");
-}
-
-// Same, written to the same shared-memory offset of every CTA in `mask` of
-// the cluster, each of which gets the complete_tx on its own barrier.
-__device__ __forceinline__ void tma_load_5d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
-                                               int c2, int c3, int c4, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
-      "%3, %4, %5, %6}], [%7], %8;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-// Every thread of every CTA of the cluster (release / acquire).
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // K-major, 64-byte swizzled operand: stride byte offset 512 (8 rows x 64 B),
@@ -151,15 +137,6 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
 
 __device__ __forceinline__ void commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-// Arrive on the barrier at this offset in every CTA of `mask` once the MMAs
-// issued so far have completed.
-__device__ __forceinline__ void commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                   smem_u32(bar)),
-               "h"(mask)
                : "memory");
 }
 
@@ -282,6 +259,18 @@ __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t* v) {
       : "r"(taddr));
 }
 
+// Producer's way out: wait (bounded) until the TMA loads of the last
+// min(issued, ns) stages it filled have landed.  Earlier stages were waited
+// for by the MMA warp before their slots were refilled; on the normal path
+// these phases have completed already and every wait returns at once.
+__device__ __forceinline__ void drain_loads(uint64_t* full, int ns, int64_t issued, int* err) {
+  for (int64_t q = issued > ns ? issued - ns : 0; q < issued; ++q)
+    if (!mbar_wait(&full[q % ns], (uint32_t)((q / ns) & 1), kDrainLimit)) {
+      atomicExch(err, 9);
+      return;
+    }
+}
+
 template <int TN, bool BF16, int NP>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_tma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
@@ -299,6 +288,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ volatile int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long wl = g_wait_limit;
   const int64_t ulo = blockIdx.z % d.units_lo, uhi = blockIdx.z / d.units_lo;
   const int za_lo = a_zlo ? (int)ulo : 0, za_hi = a_zhi ? (int)uhi : 0;
   const int zb_lo = b_zlo ? (int)ulo : 0, zb_hi = b_zhi ? (int)uhi : 0;
@@ -361,9 +351,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0) {
     // ---- TMA producer (one lane; the warp reconverges before the final barrier)
+    int nis = 0;  // stages issued
     for (int kt = 0; lane == 0 && kt < nkt; ++kt) {
       const int s = kt % NS;
-      if (kt >= NS && !mbar_wait(&empty[s], ((kt / NS) - 1) & 1)) {
+      if (kt >= NS && !mbar_wait(&empty[s], ((kt / NS) - 1) & 1, wl)) {
         atomicExch(err, 11);
         abort_flag = 1;
         break;
@@ -373,7 +364,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_expect_tx(&full[s], CF::STAGE);
       tma_load_5d(st, &mapA, &full[s], kt * TKC, m0, 0, za_lo, za_hi);
       tma_load_5d(st + A_STAGE, &mapB, &full[s], kt * TKC, n0, 0, zb_lo, zb_hi);
+      ++nis;
     }
+    if (lane == 0) drain_loads(full, NS, nis, err);
     __syncwarp();
   } else if (warp == 1) {
     // ---- MMA issuer (one lane)
@@ -382,7 +375,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int issued = 0;
     for (int kt = 0; lane == 0 && kt < nkt; ++kt) {
       const int s = kt % NS;
-      if (!mbar_wait(&full[s], (kt / NS) & 1)) {
+      if (!mbar_wait(&full[s], (kt / NS) & 1, wl)) {
         atomicExch(err, 12);
         abort_flag = 1;
         break;
@@ -410,14 +403,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       ++issued;
     }
     if (lane == 0) {
-      if (issued > 0) commit(&done);  // tracks every MMA issued above
-      else if (nkt > 0) atomicExch(err, 13);
+      if (issued > 0) {
+        commit(&done);  // tracks every MMA issued above
+        // the MMAs have finished with the stages and the accumulator before
+        // this warp reaches the final barrier, whatever the epilogue saw
+        if (!mbar_wait(&done, 0, kDrainLimit)) atomicExch(err, 15);
+      } else if (nkt > 0) {
+        atomicExch(err, 13);
+      }
     }
     __syncwarp();
   } else if (warp >= 4) {
     // ---- epilogue (whole warps: tcgen05.ld is warp-collective)
     const int q = warp & 3;
-    bool ok = nkt > 0 && mbar_wait(&done, 0);
+    bool ok = nkt > 0 && mbar_wait(&done, 0, wl);
     ok = __all_sync(0xffffffffu, ok);
     if (!ok && lane == 0 && nkt > 0) atomicExch(err, 14);
     __syncwarp();
@@ -491,7 +490,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // Persistent variant: one CTA per SM walks the (unit, tile) work items; the
 // K-stage ring runs on across items, and two TMEM accumulator buffers let the
 // epilogue warps drain item j while the MMA warp already accumulates item j+1.
-template <int TN, bool BF16, int NP, int CL>
+template <int TN, bool BF16, int NP>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_tma_persistent(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                         float2* __restrict__ C0, const GemmDesc d, int kp, int a_zlo, int a_zhi, int b_zlo,
@@ -504,18 +503,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   static_assert(COLS <= 512, "two accumulator buffers must fit in the 512 TMEM columns");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t full[NS], empty[NS], acc_full[2], acc_empty[2];
+  __shared__ uint64_t full[NS], empty[NS], acc_full[2], acc_empty[2], mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int32_t colC[2][TN];
   __shared__ volatile int abort_flag;
   __shared__ volatile int epi_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // CL = 2: two CTAs take the vertically adjacent tiles of an item and share
-  // its B tile (each loads half of it into both, TMA multicast)
-  const int rank = CL > 1 ? (int)cluster_ctarank() : 0;
-  const int64_t first = blockIdx.x / CL, stride = gridDim.x / CL;
-  const int ntm = (int)((int64_t(1) << d.nm) / (TM * CL)), ntn = (int)((int64_t(1) << d.nn) / TN);
+  const long long wl = g_wait_limit;
+  const int64_t first = blockIdx.x, stride = gridDim.x;
+  const int ntm = (int)((int64_t(1) << d.nm) / TM), ntn = (int)((int64_t(1) << d.nn) / TN);
   const int tiles = ntm * ntn;
   const int64_t items = (int64_t)tiles * d.units;
   const int nkt = kp / TKC;
@@ -526,13 +523,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int per_group = GM * ntn;
     const int g = t / per_group, r = t % per_group;
     const int gm = min(GM, ntm - g * GM);
-    m0 = ((g * GM + r % gm) * CL + rank) * TM;
+    m0 = (g * GM + r % gm) * TM;
     n0 = (r / gm) * TN;
   };
 
   if (tid == 0) {
-    for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], CL); }
+    for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 128); }
+    mbar_init(&mma_done, 1);
     abort_flag = 0;
     epi_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -546,7 +544,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (CL > 1) cluster_sync();  // the peer's barriers exist before any multicast reaches them
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
@@ -561,7 +558,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int zb_lo = b_zlo ? ulo : 0, zb_hi = b_zhi ? uhi : 0;
       for (int kt = 0; kt < nkt; ++kt, ++g) {
         const int s = (int)(g % NS);
-        if (g >= NS && !mbar_wait(&empty[s], (uint32_t)(((g / NS) - 1) & 1))) {
+        if (g >= NS && !mbar_wait(&empty[s], (uint32_t)(((g / NS) - 1) & 1), wl)) {
           atomicExch(err, 21);
           abort_flag = 1;
           break;
@@ -569,26 +566,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         uint8_t* st = smem + s * CF::STAGE;
         mbar_expect_tx(&full[s], CF::STAGE);
         tma_load_5d(st, &mapA, &full[s], kt * TKC, m0, 0, za_lo, za_hi);
-        if (CL > 1) {
-#pragma unroll
-          for (int p = 0; p < NP; ++p)
-            tma_load_5d_mc(st + A_STAGE + (p * TN + rank * (TN / 2)) * 64, &mapB, &full[s], kt * TKC,
-                           n0 + rank * (TN / 2), p, zb_lo, zb_hi, (uint16_t)3);
-        } else {
-          tma_load_5d(st + A_STAGE, &mapB, &full[s], kt * TKC, n0, 0, zb_lo, zb_hi);
-        }
+        tma_load_5d(st + A_STAGE, &mapB, &full[s], kt * TKC, n0, 0, zb_lo, zb_hi);
       }
     }
-    // CL > 1: before this CTA may leave, both CTAs' MMA commits for the last
-    // stages it filled have arrived on its empty barriers
-    if (CL > 1 && lane == 0 && !abort_flag) {
-      for (int64_t q = g > NS ? g - NS : 0; q < g; ++q) {
-        if (!mbar_wait(&empty[q % NS], (uint32_t)((q / NS) & 1))) {
-          atomicExch(err, 25);
-          break;
-        }
-      }
-    }
+    if (lane == 0) drain_loads(full, NS, g, err);  // g = stages issued
     __syncwarp();
   } else if (warp == 1) {
     // ---- MMA issuer: item j accumulates into TMEM buffer j & 1
@@ -596,7 +577,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int64_t g = 0, j = 0;
     for (int64_t it = first; lane == 0 && it < items && !abort_flag; it += stride, ++j) {
       const int b = (int)(j & 1);
-      if (j >= 2 && !mbar_wait(&acc_empty[b], (uint32_t)(((j / 2) - 1) & 1))) {
+      if (j >= 2 && !mbar_wait(&acc_empty[b], (uint32_t)(((j / 2) - 1) & 1), wl)) {
         atomicExch(err, 22);
         abort_flag = 1;
         break;
@@ -606,7 +587,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       for (int kt = 0; kt < nkt; ++kt, ++g) {
         const int s = (int)(g % NS);
-        if (!mbar_wait(&full[s], (uint32_t)((g / NS) & 1))) {
+        if (!mbar_wait(&full[s], (uint32_t)((g / NS) & 1), wl)) {
           atomicExch(err, 23);
           abort_flag = 1;
           ok = false;
@@ -630,11 +611,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           mma(di, A_[0], B_[1], I, acc);
           mma(di, A_[1], B_[0], I, 1u);
         }
-        if (CL > 1) commit_mc(&empty[s], (uint16_t)3);  // both CTAs wrote into this stage
-        else commit(&empty[s]);
+        commit(&empty[s]);
       }
       commit(&acc_full[b]);  // also on an aborted item, so the epilogue's wait ends
       if (!ok) break;
+    }
+    // every MMA issued has finished reading shared memory and writing TMEM
+    // before this warp reaches the final barrier
+    if (lane == 0 && g > 0) {
+      commit(&mma_done);
+      if (!mbar_wait(&mma_done, 0, kDrainLimit)) atomicExch(err, 26);
     }
     __syncwarp();
   } else if (warp >= 4) {
@@ -649,7 +635,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int ulo = unit % d.units_lo, uhi = unit / d.units_lo;
       for (int jj = t; jj < TN; jj += 128) colC[b][jj] = bit_offset(n0 + jj, d.nn, d.cn);
       const int32_t ro = bit_offset(m0 + q * 32 + lane, d.nm, d.cm);
-      bool ok = mbar_wait(&acc_full[b], (uint32_t)((j / 2) & 1));
+      bool ok = mbar_wait(&acc_full[b], (uint32_t)((j / 2) & 1), wl);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok && lane == 0) {
         atomicExch(err, 24);
@@ -733,9 +719,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS));
   }
-  // no CTA leaves while its peer may still write into its shared memory or
-  // arrive on its barriers
-  if (CL > 1) cluster_sync();
 }
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
@@ -773,7 +756,7 @@ int split_chunk() {
   return c;
 }
 
-template <int TN, bool BF16, int CL>
+template <int TN, bool BF16>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_tma_chunked(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                      float2* __restrict__ C0, const GemmDesc d, int kp, int a_zlo, int a_zhi, int b_zlo, int b_zhi,
@@ -787,22 +770,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   static_assert(2 * BUF <= 512, "two accumulator buffers must fit in TMEM");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t full[NS], empty[NS], acc_full[2], acc_empty[2];
+  __shared__ uint64_t full[NS], empty[NS], acc_full[2], acc_empty[2], mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int32_t colC[TN];
   __shared__ volatile int abort_flag;
   __shared__ volatile int epi_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // CL = 2: a cluster of two CTAs takes the tiles (2 p, n) and (2 p + 1, n)
-  // of an item; they share the B tile, and each loads half of it into both
-  // (TMA multicast), so every stage needs both CTAs' MMAs done before reuse
-  const int rank = CL > 1 ? (int)cluster_ctarank() : 0;
-  const int64_t first = blockIdx.x / CL, stride = gridDim.x / CL;
+  const long long wl = g_wait_limit;
+  const int64_t first = blockIdx.x, stride = gridDim.x;
   // fold > 1: `fold` consecutive hi units share A, and their N = 2^nn columns
   // side by side form the TN columns of one tile (so TN = fold * 2^nn)
   const int nsub = 1 << d.nn;
-  const int ntm = (int)((int64_t(1) << d.nm) / (TM * CL)), ntn = fold > 1 ? 1 : (int)((int64_t(1) << d.nn) / TN);
+  const int ntm = (int)((int64_t(1) << d.nm) / TM), ntn = fold > 1 ? 1 : (int)((int64_t(1) << d.nn) / TN);
   const int tiles = ntm * ntn;
   const int64_t items = (int64_t)tiles * (d.units / fold);
   const int nkt = kp / TKC;
@@ -814,13 +794,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int per_group = GM * ntn;
     const int g = t / per_group, r = t % per_group;
     const int gm = min(GM, ntm - g * GM);
-    m0 = ((g * GM + r % gm) * CL + rank) * TM;
+    m0 = (g * GM + r % gm) * TM;
     n0 = (r / gm) * TN;
   };
 
   if (tid == 0) {
-    for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], CL); }
+    for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 128); }
+    mbar_init(&mma_done, 1);
     abort_flag = 0;
     epi_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -834,7 +815,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (CL > 1) cluster_sync();  // the peer's barriers exist before any multicast reaches them
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
@@ -849,7 +829,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int zb_lo = b_zlo ? ulo : 0, zb_hi = b_zhi ? uhi : 0;
       for (int kt = 0; kt < nkt; ++kt, ++g) {
         const int s = (int)(g % NS);
-        if (g >= NS && !mbar_wait(&empty[s], (uint32_t)(((g / NS) - 1) & 1))) {
+        if (g >= NS && !mbar_wait(&empty[s], (uint32_t)(((g / NS) - 1) & 1), wl)) {
           atomicExch(err, 31);
           abort_flag = 1;
           break;
@@ -857,21 +837,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         uint8_t* st = smem + s * CF::STAGE;
         mbar_expect_tx(&full[s], CF::STAGE);
         tma_load_5d(st, &mapA, &full[s], kt * TKC, m0, 0, za_lo, za_hi);
-        if (CL > 1) {
-          // this CTA's half of the B rows, one plane per box, into both CTAs
-          if (fold == 1) {
-#pragma unroll
-            for (int p = 0; p < NP; ++p)
-              tma_load_5d_mc(st + A_STAGE + (p * TN + rank * (TN / 2)) * 64, &mapB, &full[s], kt * TKC,
-                             n0 + rank * (TN / 2), p, zb_lo, zb_hi, (uint16_t)3);
-          } else {
-            for (int f = rank * (fold / 2); f < (rank + 1) * (fold / 2); ++f)
-#pragma unroll
-              for (int p = 0; p < NP; ++p)
-                tma_load_5d_mc(st + A_STAGE + (p * TN + f * nsub) * 64, &mapB, &full[s], kt * TKC, 0, p, zb_lo,
-                               uhi + f, (uint16_t)3);
-          }
-        } else if (fold == 1) {
+        if (fold == 1) {
           tma_load_5d(st + A_STAGE, &mapB, &full[s], kt * TKC, n0, 0, zb_lo, zb_hi);
         } else {
           // the B map's box is one plane of 2^nn rows: plane p of hi unit
@@ -883,16 +849,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
     }
-    // CL > 1: before this CTA may leave, both CTAs' MMA commits for the last
-    // stages it filled have arrived on its empty barriers
-    if (CL > 1 && lane == 0 && !abort_flag) {
-      for (int64_t q = g > NS ? g - NS : 0; q < g; ++q) {
-        if (!mbar_wait(&empty[q % NS], (uint32_t)((q / NS) & 1))) {
-          atomicExch(err, 35);
-          break;
-        }
-      }
-    }
+    if (lane == 0) drain_loads(full, NS, g, err);  // g = stages issued
     __syncwarp();
   } else if (warp == 1) {
     // ---- MMA issuer.  Chunk 0 of the t-th tile goes to buffer t & 1, later
@@ -906,7 +863,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int rb = (int)(t & 1);
       for (int c = 0; c < nch && ok; ++c) {
         const int b = c == 0 ? rb : 1 - rb;
-        if (used[b] >= 1 && !mbar_wait(&acc_empty[b], (used[b] - 1) & 1)) {
+        if (used[b] >= 1 && !mbar_wait(&acc_empty[b], (used[b] - 1) & 1, wl)) {
           atomicExch(err, 32);
           abort_flag = 1;
           ok = false;
@@ -918,7 +875,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int k0 = c * chunk, k1 = min(nkt, k0 + chunk);
         for (int kt = k0; kt < k1; ++kt, ++g) {
           const int s = (int)(g % NS);
-          if (!mbar_wait(&full[s], (uint32_t)((g / NS) & 1))) {
+          if (!mbar_wait(&full[s], (uint32_t)((g / NS) & 1), wl)) {
             atomicExch(err, 33);
             abort_flag = 1;
             ok = false;
@@ -951,11 +908,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mma(di, A_[2], B_[1], I, 1u);
             mma(di, A_[3], B_[0], I, 1u);
           }
-          if (CL > 1) commit_mc(&empty[s], (uint16_t)3);  // both CTAs wrote into this stage
-          else commit(&empty[s]);
+          commit(&empty[s]);
         }
         commit(&acc_full[b]);  // also after an abort, so the epilogue's wait ends
       }
+    }
+    // every MMA issued has finished reading shared memory and writing TMEM
+    // before this warp reaches the final barrier
+    if (lane == 0 && g > 0) {
+      commit(&mma_done);
+      if (!mbar_wait(&mma_done, 0, kDrainLimit)) atomicExch(err, 36);
     }
     __syncwarp();
   } else if (warp >= 4) {
@@ -972,11 +934,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int jj = tq; jj < TN; jj += 128) colC[jj] = bit_offset(fold > 1 ? (jj & (nsub - 1)) : n0 + jj, d.nn, d.cn);
       const int32_t ro = bit_offset(m0 + q * 32 + lane, d.nm, d.cm);
       float2* Cu = C0 + (int64_t)ulo * d.c_lo + (int64_t)uhi * d.c_hi;
-      int ea = 0, eb = 0, r = 0;
-      bool weak = false;
-      if (sio.ea) {
+      // Scaled formats: exponents of the operands of the tile's f-th unit (a
+      // folded tile holds `fold` hi units side by side, f = column / 2^nn,
+      // with A shared and B, C of their own) and the output shift r that keeps
+      // the predicted bound 2 K maxA maxB below 2^15.
+      auto unit_scale = [&](int f, int& ea, int& eb, int& r, bool& weak) {
+        ea = eb = r = 0;
+        weak = false;
+        if (!sio.ea) return;
         const int za = (a_zlo ? ulo : 0) + (a_zhi ? uhi : 0) * (a_zlo ? d.units_lo : 1);
-        const int zb = (b_zlo ? ulo : 0) + (b_zhi ? uhi : 0) * (b_zlo ? d.units_lo : 1);
+        const int zb = (b_zlo ? ulo : 0) + (b_zhi ? uhi + f : 0) * (b_zlo ? d.units_lo : 1);
         ea = sio.ea[za];
         eb = sio.eb[zb];
         const float ma = sio.ma[za], mb = sio.mb[zb];
@@ -987,14 +954,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           frexpf(bound, &x);
           r = x - 15;
         }
-      }
+      };
       const int vb = vec_bits(d);
-      const Pow2 sc(c_planes ? -r : ea + eb);
+      const int gw = fold > 1 ? nsub : TN;  // tile columns of one unit
       const int rb = (int)(t & 1);
       const uint32_t R = tmem + lane_off + (uint32_t)rb * BUF, P = tmem + lane_off + (uint32_t)(1 - rb) * BUF;
       for (int c = 0; c < nch; ++c) {
         const int b = c == 0 ? rb : 1 - rb;
-        bool ok = mbar_wait(&acc_full[b], seen[b] & 1);
+        bool ok = mbar_wait(&acc_full[b], seen[b] & 1, wl);
         ++seen[b];
         ok = __all_sync(0xffffffffu, ok);
         if (!ok && lane == 0) {
@@ -1030,11 +997,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       if (epi_fail) break;
       float vmax = 0.f;
-      bool bad = false;
+      bool bad = false, weak = false;
+      int ea = 0, eb = 0, r = 0;
+      Pow2 sc(0);
 #pragma unroll 1
       for (int c0 = 0; c0 < TN; c0 += 16) {
-        // columns of a folded tile belong to hi unit uhi + c0 / 2^nn
-        float2* C = Cu + (fold > 1 ? (int64_t)(c0 >> d.nn) * d.c_hi : 0);
+        // columns of a folded tile belong to hi unit uhi + c0 / 2^nn (N >= 16:
+        // a 16-column chunk never straddles two units)
+        const int f = fold > 1 ? (c0 >> d.nn) : 0;
+        if (c0 % gw == 0) {
+          unit_scale(f, ea, eb, r, weak);
+          sc = Pow2(c_planes ? -r : ea + eb);
+          vmax = 0.f;
+          bad = false;
+        }
+        float2* C = Cu + (int64_t)f * d.c_hi;
         uint32_t ur[16], ui[16];
         tmem_ld<16>(R + (uint32_t)c0, ur);
         tmem_ld<16>(R + (uint32_t)(TN + c0), ui);
@@ -1060,19 +1037,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         } else {
           store_c64(C, ro, &colC[c0], vb, vr, vi);
         }
+        if ((c0 + 16) % gw == 0 && (sio.mc || sio.flag)) {
+          // the unit's columns are done: its largest stored component,
+          // exponent and filter flag (launch unit ulo + (uhi + f) units_lo)
+          const int un = fold > 1 ? ulo + (uhi + f) * d.units_lo : unit;
+          for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+          const bool any_bad = __any_sync(0xffffffffu, bad);
+          if (lane == 0) {
+            if (sio.mc && c_planes) atomicMax(sio.mc + un, __float_as_uint(vmax));
+            if (sio.ec && c_planes && q == 0 && m0 == 0 && n0 == 0) sio.ec[un] = ea + eb + r;
+            if (sio.flag && (any_bad || weak)) sio.flag[sio.flag_by_lo ? ulo : un] = 1;
+          }
+        }
       }
       // R read out: the MMA warp may start a later tile's chunks in it
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[rb])) : "memory");
-      if (sio.mc || sio.flag) {
-        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-        bad = __any_sync(0xffffffffu, bad);
-        if (lane == 0) {
-          if (sio.mc && c_planes) atomicMax(sio.mc + unit, __float_as_uint(vmax));
-          if (sio.ec && c_planes && q == 0 && m0 == 0 && n0 == 0) sio.ec[unit] = ea + eb + r;
-          if (sio.flag && (bad || weak)) sio.flag[sio.flag_by_lo ? ulo : unit] = 1;
-        }
-      }
       // every epilogue thread is done with colC before the next item rewrites it
       asm volatile("bar.sync 1, 128;" ::: "memory");
     }
@@ -1083,9 +1063,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS));
   }
-  // no CTA leaves while its peer may still write into its shared memory or
-  // arrive on its barriers
-  if (CL > 1) cluster_sync();
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -1137,124 +1114,76 @@ cudaError_t launch_cfg(const CUtensorMap& ma, const CUtensorMap& mb, float2* C, 
   return cudaGetLastError();
 }
 
+// SM count of the current device (one CTA per SM for the persistent kernels).
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 148;
+}
+
 template <int TN, bool BF16, int NP>
 cudaError_t launch_persistent(const CUtensorMap& ma, const CUtensorMap& mb, float2* C, const GemmDesc& d, int kp,
-                              const int z[4], int c_planes, const ScaleIO& sio, int cl, int* err, cudaStream_t s) {
+                              const int z[4], int c_planes, const ScaleIO& sio, int* err, cudaStream_t s) {
   static bool attr = false;
   static int sms = 0;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tma_persistent<TN, BF16, NP, 1>,
+    cudaError_t e = cudaFuncSetAttribute(gemm_tma_persistent<TN, BF16, NP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg2<TN, NP>::SMEM);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gemm_tma_persistent<TN, BF16, NP, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               Cfg2<TN, NP>::SMEM);
     if (e != cudaSuccess) return e;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 148;
+    sms = sm_count();
     attr = true;
   }
   const int64_t M = int64_t(1) << d.nm, N = int64_t(1) << d.nn;
-  const int64_t items = (M / (TM * cl)) * (N / TN) * d.units;
-  if (cl == 1) {
-    const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
-    gemm_tma_persistent<TN, BF16, NP, 1><<<grid, NTHREADS, Cfg2<TN, NP>::SMEM, s>>>(
-        ma, mb, C, d, kp, z[0], z[1], z[2], z[3], c_planes, sio, err);
-    return cudaGetLastError();
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(items, sms / 2)), 1, 1);
-  cfg.blockDim = dim3(NTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = Cfg2<TN, NP>::SMEM;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, gemm_tma_persistent<TN, BF16, NP, 2>, ma, mb, C, d, kp, z[0], z[1], z[2], z[3],
-                            c_planes, sio, err);
+  const int64_t items = (M / TM) * (N / TN) * d.units;
+  const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
+  gemm_tma_persistent<TN, BF16, NP><<<grid, NTHREADS, Cfg2<TN, NP>::SMEM, s>>>(ma, mb, C, d, kp, z[0], z[1], z[2],
+                                                                              z[3], c_planes, sio, err);
+  return cudaGetLastError();
 }
 
 template <int TN, bool BF16>
 cudaError_t launch_chunked(const CUtensorMap& ma, const CUtensorMap& mb, float2* C, const GemmDesc& d, int kp,
-                           const int z[4], int c_planes, const ScaleIO& sio, int fold, int cl, int* err,
-                           cudaStream_t s) {
+                           const int z[4], int c_planes, const ScaleIO& sio, int fold, int* err, cudaStream_t s) {
   static bool attr = false;
   static int sms = 0;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tma_chunked<TN, BF16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(gemm_tma_chunked<TN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Cfg2<TN, 4>::SMEM);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gemm_tma_chunked<TN, BF16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               Cfg2<TN, 4>::SMEM);
     if (e != cudaSuccess) return e;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 148;
+    sms = sm_count();
     attr = true;
   }
   const int64_t M = int64_t(1) << d.nm, N = int64_t(1) << d.nn;
-  const int64_t items = (M / (TM * cl)) * (fold > 1 ? 1 : N / TN) * (d.units / fold);
+  const int64_t items = (M / TM) * (fold > 1 ? 1 : N / TN) * (d.units / fold);
   const int chunk = split_chunk();
-  if (cl == 1) {
-    const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
-    gemm_tma_chunked<TN, BF16, 1><<<grid, NTHREADS, Cfg2<TN, 4>::SMEM, s>>>(
-        ma, mb, C, d, kp, z[0], z[1], z[2], z[3], c_planes, sio, chunk, fold, err);
-    return cudaGetLastError();
-  }
-  // clusters of two CTAs, one cluster per item at most, all SMs covered
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(items, sms / 2)), 1, 1);
-  cfg.blockDim = dim3(NTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = Cfg2<TN, 4>::SMEM;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, gemm_tma_chunked<TN, BF16, 2>, ma, mb, C, d, kp, z[0], z[1], z[2], z[3], c_planes,
-                            sio, chunk, fold, err);
-}
-
-// Two-CTA clusters for the split kernel (B tile shared through TMA multicast):
-// on unless TN_TMA_CLUSTER=0.
-bool use_clusters() {
-  static const bool on = [] {
-    const char* e = getenv("TN_TMA_CLUSTER");
-    return !(e && e[0] == '0');
-  }();
-  return on;
+  const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
+  gemm_tma_chunked<TN, BF16><<<grid, NTHREADS, Cfg2<TN, 4>::SMEM, s>>>(ma, mb, C, d, kp, z[0], z[1], z[2], z[3],
+                                                                     c_planes, sio, chunk, fold, err);
+  return cudaGetLastError();
 }
 
 template <bool BF16, int NP>
 cudaError_t launch_tn(int TNv, bool persistent, const CUtensorMap& ma, const CUtensorMap& mb, float2* C,
-                      const GemmDesc& d, int kp, const int z[4], int cp, const ScaleIO& sio, int fold, int cl,
-                      int* err, cudaStream_t s) {
+                      const GemmDesc& d, int kp, const int z[4], int cp, const ScaleIO& sio, int fold, int* err,
+                      cudaStream_t s) {
   if constexpr (NP == 4) {
     // split precision always runs the chunked persistent kernel (accuracy)
     (void)persistent;
     switch (TNv) {
-      case 128: return launch_chunked<128, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, cl, err, s);
-      case 64: return launch_chunked<64, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, cl, err, s);
-      case 32: return launch_chunked<32, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, cl, err, s);
-      case 16: return launch_chunked<16, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, cl, err, s);
+      case 128: return launch_chunked<128, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s);
+      case 64: return launch_chunked<64, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s);
+      case 32: return launch_chunked<32, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s);
+      case 16: return launch_chunked<16, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s);
       default: return cudaErrorInvalidValue;
     }
   } else {
     if (persistent) {
       switch (TNv) {
-        case 128: return launch_persistent<128, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, cl, err, s);
-        case 64: return launch_persistent<64, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, cl, err, s);
-        case 32: return launch_persistent<32, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, cl, err, s);
-        case 16: return launch_persistent<16, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, cl, err, s);
+        case 128: return launch_persistent<128, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+        case 64: return launch_persistent<64, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+        case 32: return launch_persistent<32, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
+        case 16: return launch_persistent<16, BF16, NP>(ma, mb, C, d, kp, z, cp, sio, err, s);
         default: return cudaErrorInvalidValue;
       }
     }
@@ -1269,6 +1198,11 @@ cudaError_t launch_tn(int TNv, bool persistent, const CUtensorMap& ma, const CUt
 }
 
 }  // namespace
+
+cudaError_t set_tc_wait_limit(long long polls) {
+  const long long v = polls < 0 ? kWaitLimit : polls;
+  return cudaMemcpyToSymbol(g_wait_limit, &v, sizeof v);
+}
 
 int tma_tile_n(const GemmDesc& d) {
   const int def = d.nn >= 7 ? 128 : (1 << d.nn);
@@ -1296,29 +1230,26 @@ cudaError_t launch_gemm_tma(const PlaneOperand& a, const PlaneOperand& b, float2
   // Narrow N with A shared by the hi units (e.g. one slice-only tensor against
   // the bitstrings of a group): fold consecutive hi units into the columns of
   // one tile, so that the MMAs run 128 columns wide and A is read once for
-  // all of them (split precision without scaling: one exponent per tile).
+  // all of them (split precision; with scaling, the epilogue takes each
+  // unit's exponents for its own columns).
   int fold = 1;
-  if (a.np == 4 && !sio.ea && d.nn < 7 && a.nhi == 1 && b.nhi > 1 && d.units_lo > 0) {
+  if (a.np == 4 && d.nn < 7 && a.nhi == 1 && b.nhi > 1 && d.units_lo > 0) {
     const int uh = d.units / d.units_lo;
     while (fold * 2 <= (128 >> d.nn) && uh % (fold * 2) == 0) fold *= 2;
     if (fold > 1) TNv = (1 << d.nn) * fold;
   }
 
-  // persistent kernels: pairs of CTAs on vertically adjacent tiles share the
-  // B tile (each loads half of it, one plane per box, into both)
-  const int cl = (a.np == 4 || persistent) && use_clusters() && d.nm >= 8 && TNv >= 32 ? 2 : 1;
-  const int b_rows = fold > 1 ? (1 << d.nn) : (cl == 2 ? TNv / 2 : TNv);
+  const int b_rows = fold > 1 ? (1 << d.nn) : TNv;
   CUtensorMap ma, mb;
-  if (!encode_planes(&ma, a, TM) || !encode_planes(&mb, b, b_rows, fold > 1 || cl == 2 ? 1 : 0))
-    return cudaErrorInvalidValue;
+  if (!encode_planes(&ma, a, TM) || !encode_planes(&mb, b, b_rows, fold > 1 ? 1 : 0)) return cudaErrorInvalidValue;
   const int kpi = (int)a.kp;
   const int z[4] = {a.nlo > 1, a.nhi > 1, b.nlo > 1, b.nhi > 1};
   const int cp = c_planes ? 1 : 0;
   if (a.np == 4)
-    return bf16 ? launch_tn<true, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, fold, cl, err, s)
-                : launch_tn<false, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, fold, cl, err, s);
-  return bf16 ? launch_tn<true, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, 1, cl, err, s)
-              : launch_tn<false, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, 1, cl, err, s);
+    return bf16 ? launch_tn<true, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, fold, err, s)
+                : launch_tn<false, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, fold, err, s);
+  return bf16 ? launch_tn<true, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, 1, err, s)
+              : launch_tn<false, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, 1, err, s);
 }
 
 }  // namespace tn

@@ -117,6 +117,10 @@ struct ScaleIO {
   int flag_by_lo;
 };
 int64_t split_plane_elems(int nrow_bits, int nk_bits, int np);
+// Polls of every pipeline wait of the TMA tensor-core kernels on the current
+// device (negative: the default, 2^24).  A wait that runs out records an
+// error code in the kernel's error word and the CTA winds down.
+cudaError_t set_tc_wait_limit(long long polls);
 cudaError_t launch_gemm_tma(const PlaneOperand& a, const PlaneOperand& b, float2* C, bool c_planes, const GemmDesc& d,
                             bool bf16, const ScaleIO& sio, int* err, cudaStream_t s);
 // Split operand A (which_b = false) or B of d into `scratch` (returned planes).

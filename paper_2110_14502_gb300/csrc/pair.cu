@@ -136,6 +136,12 @@ static bool d_is_vector(const std::vector<int>& la, const std::vector<int>& lb, 
   return (nn <= 4 && nk <= 4) || (nn <= 3 && nk <= 7);
 }
 
+extern "C" tn_status tn_set_wait_limit(int64_t polls) {
+  const cudaError_t e = set_tc_wait_limit((long long)polls);
+  if (e != cudaSuccess) return fail(TN_ECUDA, "tn_set_wait_limit: %s", cudaGetErrorString(e));
+  return TN_OK;
+}
+
 extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, int32_t ra, const void* B,
                                       const int32_t* b_labels, int32_t rb, void* Cv, const int32_t* c_labels,
                                       int32_t rc, int32_t precision, int32_t algo, void* stream) {
@@ -211,7 +217,9 @@ extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, in
         cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
         e = cudaStreamSynchronize(s);
         if (e == cudaSuccess && h) {
-          cudaMemset(err, 0, sizeof(int));
+          const cudaError_t ce = cudaMemset(err, 0, sizeof(int));
+          if (ce != cudaSuccess)
+            return fail(TN_ECUDA, "tn_contract_pair: clearing the error word: %s", cudaGetErrorString(ce));
           return fail(TN_ETIMEOUT, "tn_contract_pair: a tensor-core pipeline wait expired (code %d)", h);
         }
       }

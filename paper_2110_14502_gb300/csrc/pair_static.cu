@@ -1,9 +1,10 @@
 // tn_contract_pair_noalloc: the tensor-core pairwise contraction without any
 // device allocation.
 //
-// Why it exists: the regular tensor-core path of tn_contract_pair asks the
-// CUDA stream-ordered allocator for scratch memory (the split 16-bit operand
-// planes) on every call.  Some callers cannot let a library allocate:
+// Why it exists: the regular tensor-core path of tn_contract_pair takes its
+// scratch memory (the split 16-bit operand planes) from cudaMalloc, growing a
+// per-device buffer whenever a call needs more.  Some callers cannot let a
+// library allocate:
 //   - a host framework whose caching allocator already holds nearly all free
 //     device memory (PyTorch reserves HBM in large blocks), so a cudaMalloc
 //     from the library fails although the framework could have served it;
@@ -31,9 +32,10 @@
 //     or different host threads) race on the array and give wrong results:
 //     serialise them.
 //   - The call allocates nothing: no cudaMalloc, cudaFree, cudaMallocAsync or
-//     allocating library routine.  Like the regular tensor-core path it checks
-//     the kernel's error word after the launch, so it returns once the
-//     contraction has finished on `stream`.
+//     allocating library routine.  It clears the shared error word on
+//     `stream` before its launch and reads it back afterwards, so it returns
+//     once the contraction has finished on `stream`, and a wait that expired
+//     in an earlier call is never reported again.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -142,16 +144,17 @@ extern "C" tn_status tn_contract_pair_noalloc(const void* A, const int32_t* a_la
   st = static_slots(slots);
   if (st != TN_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = run_gemm_tc2((const float2*)A, (const float2*)B, (float2*)Cv, d, true, slots.scratch, slots.err, s);
+  // this call's error word starts at zero, in stream order before its kernels
+  cudaError_t e = cudaMemsetAsync(slots.err, 0, sizeof(int), s);
+  if (e != cudaSuccess)
+    return fail(TN_ECUDA, "tn_contract_pair_noalloc: clearing the error word: %s", cudaGetErrorString(e));
+  e = run_gemm_tc2((const float2*)A, (const float2*)B, (float2*)Cv, d, true, slots.scratch, slots.err, s);
   if (e != cudaSuccess) return fail(TN_ECUDA, "tn_contract_pair_noalloc launch: %s", cudaGetErrorString(e));
   int h = 0;
   e = cudaMemcpyAsync(&h, slots.err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(TN_ECUDA, "tn_contract_pair_noalloc: %s", cudaGetErrorString(e));
-  if (h) {
-    cudaMemsetAsync(slots.err, 0, sizeof(int), s);
-    return fail(TN_ETIMEOUT, "tn_contract_pair_noalloc: a tensor-core pipeline wait expired (code %d)", h);
-  }
+  if (h) return fail(TN_ETIMEOUT, "tn_contract_pair_noalloc: a tensor-core pipeline wait expired (code %d)", h);
   return TN_OK;
   });
 }

@@ -4,9 +4,11 @@ Slices are independent sub-tasks (Sec. "A Customized Parallelization
 Scheme"); the only exchange is the final reduction of the amplitude vector
 (Sec. "Scaling").  Rank r of a world of w contracts a contiguous range of slice
 ids on its own GPU; the partial sums, nb * 2^k complex128 values per rank, are
-all-gathered and added in rank order on every rank, so the result depends
-only on the world size, not on the order in which the collective combines
-them.  With one rank it is the plain single-GPU sum.
+all-gathered through the host (a gloo process group: at most a few hundred
+KiB, so no GPU collective, peer access or NCCL is involved) and added in rank
+order on every rank, so the result depends only on the world size, not on
+the order in which the collective combines them.  With one rank it is the
+plain single-GPU sum.
 """
 import numpy as np
 
@@ -22,14 +24,15 @@ def slice_range(rank, world, num_slices):
 
 
 def reduce_in_rank_order(partial, group=None):
-    """Sum over the ranks of `group` of each rank's complex128 partial
-    amplitudes, added in rank order (identical on every rank)."""
+    """Sum over the ranks of `group` (a gloo process group) of each rank's
+    complex128 partial amplitudes, added in rank order (identical on every
+    rank)."""
     import torch
     import torch.distributed as dist
+    if dist.get_backend(group) != "gloo":
+        raise ValueError("the amplitude reduction runs on the host: pass a gloo process group")
     part = np.ascontiguousarray(partial, dtype=np.complex128)
     t = torch.from_numpy(part.view(np.float64).copy())
-    if dist.get_backend(group) == "nccl":
-        t = t.cuda()
     bufs = [torch.empty_like(t) for _ in range(dist.get_world_size(group))]
     dist.all_gather(bufs, t, group=group)
     acc = np.zeros_like(part)

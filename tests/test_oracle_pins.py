@@ -226,3 +226,97 @@ def test_tn_sliced_sum_equals_unsliced():
     s = 19
     fixed = TN.fix_indices(net, {lab: (s >> j) & 1 for j, lab in enumerate(sliced)})
     assert np.allclose(TN.contract_slice(net, sliced, s), TN.contract(fixed))
+
+
+# ---- work count of a contraction tree (oracle.replay.work_cmac): the complex
+# multiply-adds of the pairwise steps between leaf groups, 2^|A u B| each
+# (Sec. "How Performance Was Measured": count the arithmetic performed).
+
+def _gate(kind, qubits):
+    mats = {"sqrtx": G.SQRT_X, "sqrty": G.SQRT_Y, "sqrtw": G.SQRT_W}
+    if kind == "fsim":
+        return C.Gate("fsim", qubits, G.FSIM_THETA, G.FSIM_PHI, G.fsim(G.FSIM_THETA, G.FSIM_PHI))
+    return C.Gate(kind, qubits, matrix=mats[kind])
+
+
+def test_work_cmac_hand_counts():
+    from oracle.replay import work_cmac
+    # one qubit, X then Y then W, raw ids 0..2 the gates and 3 the |0> input:
+    # <x| W Y X |0> is two 2x2 matrix-vector products (4 MACs each) and one
+    # length-2 dot product with the projector folded into W's group (2 MACs)
+    g1 = [_gate("sqrtx", (0,)), _gate("sqrty", (0,)), _gate("sqrtw", (0,))]
+    groups = [[3], [0], [1], [2]]
+    pairs = [(0, 1), (4, 2), (5, 3)]
+    assert work_cmac(g1, 1, [1], [], groups, pairs) == 10.0
+    # the same with the qubit open: no projector, the last step is a 2x2
+    # matrix-vector product (4 MACs)
+    assert work_cmac(g1, 1, [0], [0], groups, pairs) == 12.0
+    # two qubits, X on 0 then fSim(0, 1): each input meets its neighbour (4 +
+    # 4 MACs), the two rank-1 results meet in a dot product (2 MACs); fSim's
+    # group absorbs both projectors
+    g2 = [_gate("sqrtx", (0,)), _gate("fsim", (0, 1))]
+    assert work_cmac(g2, 2, [0, 1], [], [[2], [3], [0], [1]], [(0, 2), (1, 3), (4, 5)]) == 10.0
+    # merging the |0> of qubit 0 into the X group moves that product inside a
+    # leaf group, where it is not counted: 4 + 2 MACs remain
+    assert work_cmac(g2, 2, [0, 1], [], [[2, 0], [3], [1]], [(1, 2), (0, 3)]) == 6.0
+
+
+def test_work_cmac_equals_the_products_of_the_actual_contraction():
+    """On random small circuits and random trees over single-tensor groups,
+    the count equals the sum over the tensordot calls of the oracle's own
+    contraction of (elements of A) x (elements of B) / (contracted extent)."""
+    from oracle.replay import work_cmac
+    for seed in range(4):
+        rows, cols, depth = 2, 2 + seed % 2, 3 + seed
+        gates = C.random_circuit(rows, cols, depth, seed)
+        n = rows * cols
+        bits = [int(b) for b in _rows(n, 1, seed)[0]]
+        open_q = [n - 1] if seed % 2 else []
+        net = TN.circuit_network(gates, n, bits, open_q)
+        ng = len(gates)
+        closed = [q for q in range(n) if q not in open_q]
+        last = {q: ng + q for q in range(n)}
+        for gi, g in enumerate(gates):
+            for q in g.qubits:
+                last[q] = gi
+        # raw id r (gate or input) -> network tensors of its group (+ projectors)
+        raws = list(range(ng)) + [ng + q for q in range(n)]
+        groups = [[r] for r in raws]
+        members = []
+        for r in raws:
+            m = [r + n if r < ng else r - ng]
+            m += [n + ng + i for i, q in enumerate(closed) if last[q] == r]
+            members.append(m)
+        tens, labs = [], []
+        for m in members:
+            t, l = net.tensors[m[0]], list(net.labels[m[0]])
+            for i in m[1:]:
+                t, l = _contract_counted(t, l, net.tensors[i], list(net.labels[i]), [0])
+            tens.append(t)
+            labs.append(l)
+        rng = np.random.default_rng(seed)
+        live, pairs, nid, work = list(range(len(tens))), [], len(tens), [0]
+        store = dict(enumerate(zip(tens, labs)))
+        while len(live) > 1:
+            # a random live tensor and a random partner sharing an index with
+            # it (any partner once the network has become disconnected)
+            i = int(rng.choice(live))
+            nbr = [x for x in live if x != i and set(store[x][1]) & set(store[i][1])]
+            j = int(rng.choice(nbr if nbr else [x for x in live if x != i]))
+            live.remove(i)
+            live.remove(j)
+            (ta, la), (tb, lb) = store.pop(i), store.pop(j)
+            store[nid] = _contract_counted(ta, la, tb, lb, work)
+            pairs.append((i, j))
+            live.append(nid)
+            nid += 1
+        assert work_cmac(gates, n, bits, open_q, groups, pairs) == float(work[0]), seed
+
+
+def _contract_counted(ta, la, tb, lb, work):
+    shared = [x for x in la if x in lb]
+    ia = [la.index(x) for x in shared]
+    ib = [lb.index(x) for x in shared]
+    work[0] += ta.size * tb.size // (2 ** len(shared))
+    t = np.tensordot(ta, tb, axes=(ia, ib))
+    return t, [x for x in la if x not in shared] + [x for x in lb if x not in shared]

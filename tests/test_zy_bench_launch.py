@@ -1,5 +1,5 @@
 """Parity in the benchmark's own launch configuration at full size (kept in a
-file of its own that runs after the other GPU tests)."""
+file of its own that runs after the other amplitude tests)."""
 import numpy as np
 import pytest
 
