@@ -1,10 +1,14 @@
 """Benchmark of the amplitude hot path (one JSON line on rank 0).
 
-Workload (default): a 6x6 grid random circuit of depth 1+16+1 (circuit seed
-2), its network sliced on 10 bond indices (1024 slices), the last six qubits
-open, four bitstring batches of 64 amplitudes (256 amplitudes).  One "step"
-contracts every slice of every batch and sums them in FP64: the whole hot
-path (slice selection, the pairwise permute-GEMM chain, the cross-slice sum).
+Workload (default): the 8x8 grid random circuit of depth 1+20+1 (circuit
+seed 4), its network sliced so that no per-slice intermediate exceeds 2^26
+complex elements, the first 4096 slices summed (a partial sum of fidelity
+4096 / 2^S), the last ten qubits open: 1024 correlated amplitudes in FP16
+hi+lo split precision with the FP64 cross-slice sum.  One "step" contracts
+every slice for the batch and sums them: the whole hot path (slice
+selection, the pairwise permute-GEMM chain, the cross-slice sum).
+`--workload 6x6` runs the 6x6 grid of depth 1+16+1 (seed 2), 10 sliced
+indices (1024 slices), six open qubits, four batches of 64 amplitudes.
 
 `value` is counted complex-flop throughput (8 real flops per complex
 multiply-add of the work actually performed, work shared by the batches
@@ -12,10 +16,15 @@ counted once) with inputs resident in HBM; `amplitudes_per_s` beside it.
 `e2e` repeats the step through the C ABI with host buffers (bitstrings in,
 amplitudes out, copies inside the timed region).  `roofline` describes the
 dominant kernel class from per-launch CUDA events during the timed steps;
-`cpu_baseline` times the FP64 CPU oracle on one slice of one batch.
+`cpu_baseline` times the FP64 CPU oracle on one slice of one batch (median
+of three runs).  `precision_modes` times the other precisions on the same
+workload (plain complex64 on a leading range of slices), each with its error
+against the FP64 oracle on a sampled slice; `workload_6x6` does the same for
+the 6x6 configuration; `serving` runs a Poisson request stream through the
+plain one-slice-at-a-time complex64 path and the batched server.
 
 Modes:
-  python bench.py [--gpus N --steps K --warmup W] [--precision split_bf16|c64]
+  python bench.py [--gpus N --steps K --warmup W] [--workload 8x8|6x6] [--precision split_fp16|...]
   python bench.py --impl reference ...   # the CPU oracle as the reference arm
   python bench.py --micro [--shape m,n,k]  # pairwise contraction microbenchmark
   python bench.py --serve [--requests R]   # serving: batched mixed precision vs plain complex64
@@ -36,15 +45,35 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-ROWS, COLS, DEPTH, CSEED = 6, 6, 16, 2
-NSLICED = 10
-WIDTH_CAP = 0
-NOPEN = 6
-NBATCH, BSEED = 4, 2
-PLAN_TRIALS, PLAN_SEED, PLAN_HINT, PLAN_CAP_AWARE = 64, 1, 0, 0
-SLICE_LIMIT = -1
 METRIC = "Contraction TFLOP/s & amplitudes/s at stated rel err vs FP64; p50/p99 latency"
-WORKLOAD = "6x6 grid, depth 1+16+1, fSim(pi/2,pi/6); 10 sliced indices (1024 slices); 6 open qubits; 4 batches x 64 amplitudes"
+# the two single-GPU amplitude workloads (grid, depth, circuit seed, sliced
+# indices (-1: as many as the width cap needs), per-slice width cap (0: none),
+# open qubits, bitstring batches, bitstring seed, planner trials, slices summed
+# (-1: all))
+WORKLOADS = {
+    "8x8": dict(rows=8, cols=8, depth=20, cseed=4, nsliced=-1, width_cap=26, nopen=10, nbatch=1, bseed=4,
+                trials=16, slices=4096,
+                text="8x8 grid, depth 1+20+1, fSim(pi/2,pi/6); per-slice width <= 2^26; first 4096 slices; "
+                     "10 open qubits; 1 batch x 1024 correlated amplitudes"),
+    "6x6": dict(rows=6, cols=6, depth=16, cseed=2, nsliced=10, width_cap=0, nopen=6, nbatch=4, bseed=2,
+                trials=64, slices=-1,
+                text="6x6 grid, depth 1+16+1, fSim(pi/2,pi/6); 10 sliced indices (1024 slices); 6 open qubits; "
+                     "4 batches x 64 amplitudes"),
+}
+ROWS = COLS = DEPTH = CSEED = NSLICED = WIDTH_CAP = NOPEN = NBATCH = BSEED = PLAN_TRIALS = SLICE_LIMIT = None
+WORKLOAD = None
+PLAN_SEED, PLAN_HINT, PLAN_CAP_AWARE = 1, 0, 0
+
+
+def use_workload(name):
+    global ROWS, COLS, DEPTH, CSEED, NSLICED, WIDTH_CAP, NOPEN, NBATCH, BSEED, PLAN_TRIALS, SLICE_LIMIT, WORKLOAD
+    w = WORKLOADS[name]
+    ROWS, COLS, DEPTH, CSEED = w["rows"], w["cols"], w["depth"], w["cseed"]
+    NSLICED, WIDTH_CAP, NOPEN, NBATCH, BSEED = w["nsliced"], w["width_cap"], w["nopen"], w["nbatch"], w["bseed"]
+    PLAN_TRIALS, SLICE_LIMIT, WORKLOAD = w["trials"], w["slices"], w["text"]
+
+
+use_workload("8x8")
 
 
 def peaks():
@@ -102,17 +131,6 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def use_8x8():
-    """The 8x8 configuration: 64 qubits, depth 1+20+1, seed 4, per-slice width
-    2^26, ten open qubits (1024 correlated amplitudes); the first 4096 of the
-    2^S slices are summed (a fidelity-4096/2^S partial sum)."""
-    global ROWS, COLS, DEPTH, CSEED, NSLICED, WIDTH_CAP, NOPEN, NBATCH, BSEED, PLAN_TRIALS, SLICE_LIMIT, WORKLOAD
-    ROWS, COLS, DEPTH, CSEED = 8, 8, 20, 4
-    NSLICED, WIDTH_CAP, NOPEN, NBATCH, BSEED, PLAN_TRIALS, SLICE_LIMIT = -1, 26, 10, 1, 4, 16, 4096
-    WORKLOAD = ("8x8 grid, depth 1+20+1, fSim(pi/2,pi/6); per-slice width 2^26; first 4096 slices; "
-                "10 open qubits; 1 batch x 1024 amplitudes")
-
-
 def make_workload(T, rank):
     c = T.random_circuit(ROWS, COLS, DEPTH, CSEED)
     n = ROWS * COLS
@@ -163,6 +181,54 @@ def traffic_record(kernel_file, key):
     return r.get(key)
 
 
+MODES = ("split_fp16", "split_bf16", "scaled_fp16", "scaled_bf16", "c64")
+DTYPE = {"split_bf16": "bf16x3", "split_fp16": "f16x3", "scaled_fp16": "f16", "scaled_bf16": "bf16", "c64": "f32"}
+# plain complex64 runs on the FP32 CUDA cores: time it on a leading range of
+# the slices (every slice of a plan does the same work)
+C64_SLICE_FRACTION = {"8x8": 16, "6x6": 8}
+
+
+def oracle_reference(p, words, open_q, runs=1):
+    """FP64 oracle on slice 0 of batch 0: (values, [seconds per run], cmac)."""
+    times = []
+    for _ in range(runs):
+        v, dt, cmac = cpu_oracle_sample(p, words, open_q, slice_id=0)
+        times.append(dt)
+    return v, times, cmac
+
+
+def rel_err(a, b):
+    return float(np.linalg.norm(np.asarray(a) - b) / np.linalg.norm(b))
+
+
+def time_mode(p, dwords, out, stream, mode, slices, frac, nout):
+    """One warm-up and one timed call of `mode` on the first slices / frac
+    slices (frac 1: the whole step); counted TFLOP/s and amplitudes/s of the
+    whole step projected from the timed slice range."""
+    import torch
+    part = max(1, slices // frac)
+    for rep_ in (False, True):
+        with torch.cuda.stream(stream):
+            _, r = p.contract_amplitudes(dwords, out=out, stream=stream, precision=mode, report=True,
+                                         slice_count=part)
+        torch.cuda.synchronize()
+    ms_step = r["device_ms"] * slices / part
+    e = {"tflops": round(r["flops"] / r["device_ms"] / 1e9, 2), "ms_per_step": round(ms_step, 1),
+         "amplitudes_per_s": round(nout / (ms_step * 1e-3), 3), "flagged_units": r["flagged_units"]}
+    if part < slices:
+        e["slices_timed"] = part
+        e["note"] = f"timed on slices 0..{part - 1} of {slices}; step time projected (equal work per slice)"
+    return e
+
+
+def mode_errors(p, words, ref, modes):
+    out = {}
+    for mode in modes:
+        g1 = p.contract_amplitudes(words[:1], precision=mode, slice_begin=0, slice_count=1)[0]
+        out[mode] = rel_err(g1, ref)
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_2110_14502_gb300 as T
@@ -181,15 +247,18 @@ def run_ours(args):
     info = p.info()
     k = info["num_open"]
     nout = NBATCH << k
+    slices = info["num_slices"] if SLICE_LIMIT < 0 else min(SLICE_LIMIT, info["num_slices"])
+    if args.slices > 0:
+        slices = min(slices, args.slices)
     stream = torch.cuda.Stream()
     dwords = torch.from_numpy(words.astype(np.int64)).cuda()
     out = torch.empty(nout * 2, dtype=torch.float64, device="cuda")
+    tune = 1 if args.autotune else 0
 
     def step(profile=False):
         with torch.cuda.stream(stream):
             _, rep = p.contract_amplitudes(dwords, out=out, stream=stream, precision=args.precision,
-                                           profile=profile, report=True, slice_count=SLICE_LIMIT,
-                                           autotune=1 if args.autotune else 0)
+                                           profile=profile, report=True, slice_count=slices, autotune=tune)
         return rep
 
     for _ in range(args.warmup):
@@ -237,8 +306,8 @@ def run_ours(args):
         peak = bf16_sus / mult
         roof = {"bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4),
-                "peak_kind": f"bf16 dense sustained ({src})" + (" / 3 (three bf16 MMAs per counted product)"
-                                                                if mult == 3 else ""),
+                "peak_kind": f"bf16 dense sustained ({src}; fp16 runs at the same rate)" +
+                             (" / 3 (three 16-bit MMAs per counted product)" if mult == 3 else ""),
                 "issued_mma_tflops": round(mult * achieved, 2),
                 "frac_of_bf16_peak_counted": round(achieved / bf16_sus, 4)}
     elif dom == 1:
@@ -263,26 +332,15 @@ def run_ours(args):
     roof["traffic"] = None if tr is None else tr["bytes_per_launch"]
     roof["traffic_note"] = None if tr is None else tr["note"]
 
-    # e2e: pinned host buffers through the C ABI, copies inside the timed region
-    words_h = torch.from_numpy(words.view(np.int64)).pin_memory().numpy().view(np.uint64)
-    amps_h = torch.empty(nout, dtype=torch.complex128).pin_memory().numpy().reshape(NBATCH, 1 << k)
-    e2e_times = []
-    for _ in range(max(1, min(args.steps, 3))):
-        torch.cuda.synchronize()
-        t0 = time.time()
-        p.contract_amplitudes(words_h, precision=args.precision, slice_count=SLICE_LIMIT, out=amps_h)
-        e2e_times.append(time.time() - t0)
-    e2e_s = sum(e2e_times)
-    e2e_flops = reps[0]["flops"] * len(e2e_times)
-
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"split_bf16": "bf16x3", "split_fp16": "f16x3", "scaled_fp16": "f16", "scaled_bf16": "bf16",
-                  "c64": "f32"}[args.precision],
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
         "data": "synthetic (seeded random circuit and bitstrings)",
         "config": {"workload": WORKLOAD, "precision": args.precision, "global_batch": amps // args.steps,
-                   "slices": info["num_slices"] if SLICE_LIMIT < 0 else SLICE_LIMIT, "plan_hash": hex(info["hash"]),
+                   "slices": slices, "num_sliced": info["num_sliced"],
+                   "fidelity_fraction_log2": round(float(np.log2(slices)) - info["num_sliced"], 3),
+                   "plan_hash": hex(info["hash"]),
                    "cmac_per_slice_log2": round(float(np.log2(info["cmac_per_slice"])), 3),
                    "max_log2_intermediate": info["max_log2_intermediate"],
                    "l2": f"working set (2^{info['max_log2_intermediate']}-element complex64 intermediates per "
@@ -295,43 +353,50 @@ def run_ours(args):
         "gpu_launches": launches, "gpu_launches_per_step": launches // args.steps,
         "roofline": roof,
         "clocks": clk.summary(),
-        "e2e": {"value": round(e2e_flops / e2e_s / 1e12, 3), "unit": "TFLOP/s",
-                "amplitudes_per_s": round(nout * len(e2e_times) / e2e_s, 3),
-                "h2d_bytes_per_step": int(words_h.nbytes), "d2h_bytes_per_step": int(amps_h.nbytes),
-                "host_buffers": "pinned"},
     }
+    if not args.no_e2e:
+        # e2e: pinned host buffers through the C ABI, copies inside the timed region
+        words_h = torch.from_numpy(words.view(np.int64)).pin_memory().numpy().view(np.uint64)
+        amps_h = torch.empty(nout, dtype=torch.complex128).pin_memory().numpy().reshape(NBATCH, 1 << k)
+        e2e_times = []
+        for _ in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.time()
+            p.contract_amplitudes(words_h, precision=args.precision, slice_count=slices, out=amps_h,
+                                  autotune=tune)
+            e2e_times.append(time.time() - t0)
+        e2e_s = sum(e2e_times)
+        e2e_flops = reps[0]["flops"] * len(e2e_times)
+        line["e2e"] = {"value": round(e2e_flops / e2e_s / 1e12, 3), "unit": "TFLOP/s",
+                       "amplitudes_per_s": round(nout * len(e2e_times) / e2e_s, 3),
+                       "h2d_bytes_per_step": int(words_h.nbytes), "d2h_bytes_per_step": int(amps_h.nbytes),
+                       "host_buffers": "pinned"}
+    ref = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, dt, cmac = cpu_oracle_sample(p, words, open_q, slice_id=0)
-        gpu1 = p.contract_amplitudes(words[:1], precision=args.precision, slice_begin=0, slice_count=1)[0]
-        line["cpu_baseline"] = {"value": round(8 * cmac / dt / 1e12, 6), "unit": "TFLOP/s",
+        ref, dts, cmac = oracle_reference(p, words, open_q, runs=3)
+        med, best = statistics.median(dts), min(dts)
+        line["cpu_baseline"] = {"value": round(8 * cmac / med / 1e12, 6), "unit": "TFLOP/s",
+                                "best_of_3": round(8 * cmac / best / 1e12, 6),
                                 "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-                                "sample": f"slice 0 of batch 0 ({1 << NOPEN} amplitudes, one slice), FP64 NumPy "
-                                          f"contraction in the plan's order, {dt:.1f} s"}
-        line["rel_err_vs_fp64_sample"] = float(np.linalg.norm(gpu1 - v) / np.linalg.norm(v))
+                                "sample": f"slice 0 of batch 0 ({1 << NOPEN} amplitudes, one slice of {slices}), "
+                                          f"FP64 NumPy contraction in the plan's order; median of 3 runs "
+                                          f"({', '.join(f'{x:.1f}' for x in dts)} s)"}
+        line["rel_err_vs_fp64_sample"] = mode_errors(p, words, ref, [args.precision])[args.precision]
     if rank == 0 and world == 1 and not args.no_modes:
-        # the other tensor-core precisions on the same workload: one timed step
-        # each, error against the FP64 oracle on the sampled slice when available
+        # the other precisions on the same workload, each with its error
+        # against the FP64 oracle on the sampled slice
         modes = {}
-        ref = None
-        if "cpu_baseline" in line:
-            ref = v
-        for mode in ("split_fp16", "scaled_fp16", "scaled_bf16"):
+        errs = mode_errors(p, words, ref, [m for m in MODES if m != args.precision]) if ref is not None else {}
+        for mode in MODES:
             if mode == args.precision:
                 continue
-            with torch.cuda.stream(stream):
-                p.contract_amplitudes(dwords, out=out, stream=stream, precision=mode, slice_count=SLICE_LIMIT)
-            torch.cuda.synchronize()
-            with torch.cuda.stream(stream):
-                _, r = p.contract_amplitudes(dwords, out=out, stream=stream, precision=mode, report=True,
-                                             slice_count=SLICE_LIMIT)
-            entry = {"tflops": round(r["flops"] / r["device_ms"] / 1e9, 2), "ms_per_step": round(r["device_ms"], 1),
-                     "amplitudes_per_s": round(nout / (r["device_ms"] * 1e-3), 2),
-                     "flagged_units": r["flagged_units"]}
-            if ref is not None:
-                g1 = p.contract_amplitudes(words[:1], precision=mode, slice_begin=0, slice_count=1)[0]
-                entry["rel_err_vs_fp64_sample"] = float(np.linalg.norm(g1 - ref) / np.linalg.norm(ref))
-            modes[mode] = entry
+            frac = C64_SLICE_FRACTION[args.workload] if mode == "c64" else 1
+            modes[mode] = time_mode(p, dwords, out, stream, mode, slices, frac, nout)
+            if mode in errs:
+                modes[mode]["rel_err_vs_fp64_sample"] = errs[mode]
         line["precision_modes"] = modes
+        if args.workload == "8x8" and not args.no_6x6:
+            line["workload_6x6"] = six_by_six_summary(T)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -339,6 +404,37 @@ def run_ours(args):
         line["serving"] = serve_summary(args)
     if rank == 0:
         print(json.dumps(line))
+
+
+def six_by_six_summary(T):
+    """Every precision on the 6x6 configuration (1024 slices x 4 batches of 64
+    amplitudes): one timed call each, error against the FP64 oracle on slice
+    0 of batch 0."""
+    import torch
+    keep = {name: globals()[name] for name in ("ROWS", "COLS", "DEPTH", "CSEED", "NSLICED", "WIDTH_CAP", "NOPEN",
+                                                "NBATCH", "BSEED", "PLAN_TRIALS", "SLICE_LIMIT", "WORKLOAD")}
+    use_workload("6x6")
+    try:
+        c, net, p, words, open_q, plan_s = make_workload(T, 0)
+        info = p.info()
+        nout = NBATCH << info["num_open"]
+        slices = info["num_slices"]
+        stream = torch.cuda.Stream()
+        dwords = torch.from_numpy(words.astype(np.int64)).cuda()
+        out = torch.empty(nout * 2, dtype=torch.float64, device="cuda")
+        ref, _, _ = oracle_reference(p, words, open_q)
+        errs = mode_errors(p, words, ref, MODES)
+        res = {"workload": WORKLOAD, "plan_hash": hex(info["hash"]),
+               "cmac_per_slice_log2": round(float(np.log2(info["cmac_per_slice"])), 3), "modes": {}}
+        for mode in MODES:
+            frac = C64_SLICE_FRACTION["6x6"] if mode == "c64" else 1
+            e = time_mode(p, dwords, out, stream, mode, slices, frac, nout)
+            e["rel_err_vs_fp64_sample"] = errs[mode]
+            res["modes"][mode] = e
+        del p
+        return res
+    finally:
+        globals().update(keep)
 
 
 def run_reference(args):
@@ -358,7 +454,7 @@ def run_reference(args):
         times.append(dt * 1e3)
     value = fl / tot / 1e12
     # one slice of a 2^k-amplitude batch is 1/slices of the work of those amplitudes
-    slices = info["num_slices"] if SLICE_LIMIT < 0 else SLICE_LIMIT
+    slices = info["num_slices"] if SLICE_LIMIT < 0 else min(SLICE_LIMIT, info["num_slices"])
     amps_s = float(1 << info["num_open"]) / slices * args.steps / tot
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot * 1e3 / args.steps, 1),
@@ -444,104 +540,101 @@ def serve_workload(nreq, seed=5):
     return reqs, gaps
 
 
-def serve_summary(args, nreq=60):
-    """Compact serving run for the main bench line: the same request stream on
-    the plain complex64 path and on the batched server, in complex64 (the
-    plain path's accuracy) and in scaled fp16."""
+def run_stream(T, srv, reqs, gaps=None, rate=None, keep=()):
+    """Submits the requests (all at once, or at the Poisson arrival times
+    gaps / rate) and waits for all of them: throughput, p50/p99 latency,
+    refused count, and the amplitudes of the requests whose index is in
+    `keep`."""
+    t0 = time.time()
+    tickets = []
+    for i, r in enumerate(reqs):
+        if rate:
+            target = t0 + float(np.sum(gaps[:i + 1])) / rate
+            while time.time() < target:
+                time.sleep(0.0002)
+        tickets.append(srv.submit(**r))
+    lat, amps, refused, flops, kept = [], 0, 0, 0.0, {}
+    for i, t in enumerate(tickets):
+        try:
+            o, st = srv.wait(t)
+            lat.append(st["submit_to_done_ms"])
+            amps += o.size
+            flops += st["flops"]
+            if i in keep:
+                kept[i] = o
+        except T.TnError as e:
+            if e.status in (3, 6):  # TN_EHBM, TN_ETOOBIG: counted, never dropped silently
+                refused += 1
+            else:
+                raise
+    dt = time.time() - t0
+    return {"seconds": round(dt, 3), "served": len(lat), "refused": refused,
+            "amplitudes_per_s": round(amps / dt, 1), "tflops": round(flops / dt / 1e12, 3),
+            "p50_ms": round(float(np.percentile(lat, 50)), 2) if lat else None,
+            "p99_ms": round(float(np.percentile(lat, 99)), 2) if lat else None}, kept
+
+
+def serve_summary(args):
+    """The serving stream (Poisson arrivals over random circuits, 4x4..7x7
+    grids, depths 10-24, 1-4096 amplitudes each) on the plain path (one
+    request at a time, one slice per launch group, complex64) and on the
+    batched server (8 requests in flight, 64-slice quanta interleaved) in
+    complex64, split bf16 and scaled fp16.  Each runs saturated (every request
+    submitted at once: capacity) and with Poisson arrivals at 0.7 x the plain
+    path's capacity (latency).  Served amplitudes of the 16-qubit requests are
+    checked against the FP64 state vector."""
     import paper_2110_14502_gb300 as T
-    reqs, _ = serve_workload(nreq)
-    common = dict(plan_trials=8, max_log2_cmac=40.0, max_log2_intermediate=27, planner_threads=16)
-    out = {"requests": nreq, "cost_cap_log2_cmac": 40.0}
-    for name, kw in (("warm", dict(max_inflight=8, slices_per_quantum=64, precision="c64")),
-                     ("plain_c64_one_slice", dict(max_inflight=1, slices_per_quantum=1, precision="c64")),
-                     ("batched_c64", dict(max_inflight=8, slices_per_quantum=64, precision="c64")),
-                     ("batched_scaled_fp16", dict(max_inflight=8, slices_per_quantum=64, precision="scaled_fp16"))):
+    import tn_inputs as I
+    from oracle import circuit as OC
+    from oracle import statevector as SV
+    reqs, gaps = serve_workload(args.requests)
+    common = dict(plan_trials=8, max_log2_cmac=args.cost_cap, max_log2_intermediate=27, planner_threads=16)
+    small = [i for i, r in enumerate(reqs) if r["rows"] * r["cols"] <= 16][:8]
+    refs = {}
+    for i in small:
+        r = reqs[i]
+        n = r["rows"] * r["cols"]
+        psi = SV.simulate(OC.random_circuit(r["rows"], r["cols"], r["depth"], r["seed"]), n)
+        refs[i] = SV.amplitudes(psi, n, [I.bits_of(w, n) for w in r["bitstrings"]],
+                                list(range(n - r["num_open"], n)))
+    out = {"requests": args.requests, "cost_cap_log2_cmac": args.cost_cap,
+           "stream": "seed 5; grids R x C, R, C in [4, 7], |R - C| <= 1; depth U[10, 24]; circuit seed 5 * 2^32 + id; "
+                     "1-4096 amplitudes (log-uniform) as open-qubit batches",
+           "error_check": f"{len(small)} served 16-qubit requests against the FP64 state vector"}
+    # the plan cache is process-wide: the first pass plans every circuit
+    warm = T.Server(max_inflight=8, slices_per_quantum=64, precision="c64", **common)
+    out["first_pass_with_planning"], _ = run_stream(T, warm, reqs)
+    warm.close()
+    runs = (("plain_c64", dict(max_inflight=1, slices_per_quantum=1, precision="c64")),
+            ("batched_c64", dict(max_inflight=8, slices_per_quantum=64, precision="c64")),
+            ("batched_split_bf16", dict(max_inflight=8, slices_per_quantum=64, precision="split_bf16")),
+            ("batched_scaled_fp16", dict(max_inflight=8, slices_per_quantum=64, precision="scaled_fp16")))
+    rate = None
+    for name, kw in runs:
         srv = T.Server(**kw, **common)
-        t0 = time.time()
-        ts = [srv.submit(**r) for r in reqs]
-        lat, amps, rej = [], 0, 0
-        for t in ts:
-            try:
-                o, st = srv.wait(t)
-                lat.append(st["submit_to_done_ms"])
-                amps += o.size
-            except T.TnError:
-                rej += 1
-        dt = time.time() - t0
-        srv.close()
-        if name != "warm":
-            out[name] = {"amplitudes_per_s": round(amps / dt, 1), "p50_ms": round(float(np.percentile(lat, 50)), 2),
-                         "p99_ms": round(float(np.percentile(lat, 99)), 2), "rejected": rej, "seconds": round(dt, 2)}
+        try:
+            sat, kept = run_stream(T, srv, reqs, keep=set(small))
+            if rate is None:  # the plain path's capacity sets the arrival rate
+                rate = 0.7 * (sat["served"] + sat["refused"]) / sat["seconds"]
+                out["poisson_rate_req_per_s"] = round(rate, 2)
+            poi, _ = run_stream(T, srv, reqs, gaps, rate)
+        finally:
+            srv.close()
+        errs = [rel_err(kept[i].reshape(-1), refs[i].reshape(-1)) for i in small if i in kept]
+        out[name] = {"saturated": sat, "poisson": poi,
+                     "max_rel_err_vs_fp64": max(errs) if errs else None}
     return out
 
 
 def run_serve(args):
-    """Serving benchmark: the batched mixed-precision server against the plain
-    complex64 path that contracts one slice of one request at a time."""
+    """Serving benchmark alone: the serving summary of the main line, with
+    --requests requests."""
     import torch
-    import paper_2110_14502_gb300 as T
     torch.cuda.set_device(0)
-    reqs, gaps = serve_workload(args.requests)
-    common = dict(plan_trials=8, max_log2_cmac=args.cost_cap, max_log2_intermediate=27, planner_threads=16)
-    # plans are cached per circuit: warm the cache once so both runs see planned circuits
-    warm = T.Server(max_inflight=8, slices_per_quantum=64, precision="c64", **common)
-
-    def closed_loop(srv, rate=None):
-        t0 = time.time()
-        tickets, lat, amps, rejected, flops = [], [], 0, 0, 0.0
-        start = time.time()
-        for i, r in enumerate(reqs):
-            if rate:
-                target = start + float(np.sum(gaps[:i + 1])) / rate
-                while time.time() < target:
-                    time.sleep(0.0002)
-            tickets.append(srv.submit(**r))
-        for t in tickets:
-            try:
-                out, st = srv.wait(t)
-                lat.append(st["submit_to_done_ms"])
-                amps += out.size
-                flops += st["flops"]
-            except T.TnError as e:
-                if e.status in (3, 6):
-                    rejected += 1
-                else:
-                    raise
-        dt = time.time() - t0
-        return dict(seconds=dt, amps=amps, amps_per_s=amps / dt, tflops=flops / dt / 1e12, rejected=rejected,
-                    p50_ms=float(np.percentile(lat, 50)) if lat else None,
-                    p99_ms=float(np.percentile(lat, 99)) if lat else None, served=len(lat))
-
-    pre = closed_loop(warm)
-    warm.close()
-    # batching alone, at the plain path's accuracy (saturated)
-    batched_c64 = T.Server(max_inflight=8, slices_per_quantum=64, precision="c64", **common)
-    try:
-        cap_batched_c64 = closed_loop(batched_c64)
-    finally:
-        batched_c64.close()
-    plain = T.Server(max_inflight=1, slices_per_quantum=1, precision="c64", **common)
-    batched = T.Server(max_inflight=8, slices_per_quantum=64, precision=args.precision, **common)
-    try:
-        # saturated throughput (every request submitted at once)
-        cap_plain = closed_loop(plain)
-        cap_batched = closed_loop(batched)
-        # latency under Poisson arrivals at 0.7 x the plain path's capacity (requests/s)
-        rate = 0.7 * cap_plain["served"] / cap_plain["seconds"]
-        lat_plain = closed_loop(plain, rate)
-        lat_batched = closed_loop(batched, rate)
-    finally:
-        plain.close()
-        batched.close()
-    line = {"metric": "serving amplitudes/s and p50/p99 latency", "value": round(cap_batched["amps_per_s"], 2),
-            "unit": "amplitudes/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
-            "config": {"workload": f"{args.requests} requests: grids 4x4..7x7 (|R-C|<=1), depth 10-24, 1-4096 "
-                                   f"amplitudes each, cost cap 2^{args.cost_cap} CMAC",
-                       "batched": f"8 in flight, 64-slice quanta, {args.precision}",
-                       "plain": "1 in flight, 1-slice quanta, c64"},
-            "batched_saturated": cap_batched, "batched_c64_saturated": cap_batched_c64, "plain_saturated": cap_plain,
-            "poisson_rate_req_per_s": rate, "batched_poisson": lat_batched, "plain_poisson": lat_plain,
-            "first_pass_with_planning": pre}
+    s = serve_summary(args)
+    line = {"metric": "serving amplitudes/s and p50/p99 latency",
+            "value": s["batched_scaled_fp16"]["saturated"]["amplitudes_per_s"], "unit": "amplitudes/s", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic", "serving": s}
     print(json.dumps(line))
 
 
@@ -551,18 +644,21 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="split_bf16",
-                    choices=["split_bf16", "split_fp16", "scaled_fp16", "scaled_bf16", "c64"])
+    ap.add_argument("--precision", default="split_fp16", choices=list(MODES))
     ap.add_argument("--micro", action="store_true")
     ap.add_argument("--shape", default=None)
     ap.add_argument("--random-layout", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serve", action="store_true")
-    ap.add_argument("--requests", type=int, default=100)
+    ap.add_argument("--requests", type=int, default=300)
     ap.add_argument("--cost-cap", type=float, default=40.0)
-    ap.add_argument("--workload", default="6x6", choices=["6x6", "8x8"])
+    ap.add_argument("--workload", default="8x8", choices=list(WORKLOADS))
+    ap.add_argument("--slices", type=int, default=0,
+                    help="sum only the first N slices of the workload (profiling captures; 0: the workload's count)")
     ap.add_argument("--no-modes", action="store_true")
+    ap.add_argument("--no-6x6", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--autotune", action="store_true",
                     help="tune the tensor-core tiles per step in the first (warm-up) call")
     ap.add_argument("--plan-trials", type=int, default=0, help="order-search restarts (0: the workload's default)")
@@ -572,8 +668,7 @@ def main():
     ap.add_argument("--cap-aware-rewrites", action="store_true",
                     help="plan with width-cap-aware subtree rewrites (fewer sliced indices under a width cap)")
     args = ap.parse_args()
-    if args.workload == "8x8":
-        use_8x8()
+    use_workload(args.workload)
     global PLAN_TRIALS, PLAN_SEED
     if args.plan_trials > 0:
         PLAN_TRIALS = args.plan_trials

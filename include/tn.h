@@ -338,6 +338,10 @@ typedef struct {
   int32_t stem_reused;           /* 1 = the circuit's leaf tensors and invariant (phase-0)
                                     intermediates were already resident from an earlier request */
   double slice_fraction;         /* slices served / 2^S: the expected fidelity of the amplitudes */
+  double gpu_begin_ms;           /* device time (CUDA events, ms after the server's creation) at which the
+                                    request's first slice quantum was reached on its stream */
+  double gpu_end_ms;             /* device time at which its last quantum had finished */
+  int64_t quanta;                /* slice quanta it was served in (one per scheduler turn) */
 } tn_request_stats;
 
 /* Creates a server on the current CUDA device with planner threads and a

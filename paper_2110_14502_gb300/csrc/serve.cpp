@@ -60,6 +60,11 @@ struct Request {
   cudaStream_t stream = nullptr;
   cudaEvent_t done_ev = nullptr;
   std::vector<cudaEvent_t> quanta;  // events of queued quanta (bounded look-ahead)
+  // device timeline: timing events before the first quantum and after the
+  // last one, read against the server's epoch once the request is done
+  cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
+  int64_t nquanta = 0;
+  double gpu_begin_ms = 0, gpu_end_ms = 0;
   Clock::time_point t_submit, t_admit, t_done;
   bool planned_here = false;
 };
@@ -105,6 +110,7 @@ struct Server {
   // later requests of the same circuit; its capacity is taken off the budget
   std::shared_ptr<StemCache> stems;
   std::vector<cudaStream_t> streams;  // one per slot
+  cudaEvent_t epoch = nullptr;        // device time zero of the request timelines
   std::vector<std::thread> planners;
   std::thread scheduler;
 };
@@ -225,6 +231,9 @@ void release(Server& S, Request& R) {
   R.quanta.clear();
   if (R.done_ev) cudaEventDestroy(R.done_ev);
   R.done_ev = nullptr;
+  if (R.ev_begin) cudaEventDestroy(R.ev_begin);
+  if (R.ev_end) cudaEventDestroy(R.ev_end);
+  R.ev_begin = R.ev_end = nullptr;
   S.in_use -= R.footprint;
   // the request's plan copy keeps its arenas until the request is released by tn_wait
 }
@@ -238,6 +247,8 @@ tn_status admit(Server&, Request& R, cudaStream_t stream) {
     e = cudaMemcpyAsync(R.d_bits, R.bits.data(), R.bits.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess && !R.h_out) e = cudaMallocHost(&R.h_out, std::max<int64_t>(nout, 1) * 16);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&R.done_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&R.ev_begin);
+  if (e == cudaSuccess) e = cudaEventCreate(&R.ev_end);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(TN_ECUDA, "serving: admitting request %lld: %s", (long long)R.ticket, cudaGetErrorString(e));
@@ -260,10 +271,13 @@ tn_status step_request(Request& R) {
   // one FP64 sum over all quanta: the filter list is reset by the first
   // quantum and processed (recompute / discard) after the last
   const bool first = R.cursor == 0, last = R.cursor + o.slice_count >= R.ns;
+  if (first && cudaEventRecord(R.ev_begin, R.stream) != cudaSuccess)
+    return fail(TN_ECUDA, "serving: recording the request's first-quantum event");
   tn_status st = contract_amplitudes_ex(R.plan->plan, R.d_bits, R.params.nb, R.d_acc, o, nullptr, first,
                                         (first ? 1 : 0) | (last ? 2 : 0));
   if (st != TN_OK) return st;
   R.cursor += o.slice_count;
+  ++R.nquanta;
   cudaEvent_t ev;
   if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
     cudaEventRecord(ev, R.stream);
@@ -271,7 +285,9 @@ tn_status step_request(Request& R) {
   }
   if (R.cursor >= R.ns) {
     const int64_t nout = R.params.nb << R.k;
-    cudaError_t e = cudaMemcpyAsync(R.h_out, R.d_acc, std::max<int64_t>(nout, 1) * 16, cudaMemcpyDeviceToHost, R.stream);
+    cudaError_t e = cudaEventRecord(R.ev_end, R.stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(R.h_out, R.d_acc, std::max<int64_t>(nout, 1) * 16, cudaMemcpyDeviceToHost, R.stream);
     if (e == cudaSuccess) e = cudaEventRecord(R.done_ev, R.stream);
     if (e != cudaSuccess) return fail(TN_ECUDA, "serving: %s", cudaGetErrorString(e));
     R.state = RS_FINISHING;
@@ -345,6 +361,12 @@ void scheduler_loop(Server* S) {
         }
       } else if (R->state == RS_FINISHING && cudaEventQuery(R->done_ev) == cudaSuccess) {
         std::lock_guard<std::mutex> g(S->mu);
+        float b = 0.f, e = 0.f;
+        if (cudaEventElapsedTime(&b, S->epoch, R->ev_begin) == cudaSuccess &&
+            cudaEventElapsedTime(&e, S->epoch, R->ev_end) == cudaSuccess) {
+          R->gpu_begin_ms = b;
+          R->gpu_end_ms = e;
+        }
         R->t_done = Clock::now();
         R->state = RS_DONE;
         release(*S, *R);
@@ -405,6 +427,13 @@ extern "C" tn_status tn_server_create(const tn_server_opts* opts, tn_server** ou
       return fail(TN_ECUDA, "tn_server_create: stream creation failed");
     }
     S.streams.push_back(st);
+  }
+  if (cudaEventCreate(&S.epoch) != cudaSuccess || cudaEventRecord(S.epoch, S.streams[0]) != cudaSuccess ||
+      cudaEventSynchronize(S.epoch) != cudaSuccess) {
+    if (S.epoch) cudaEventDestroy(S.epoch);
+    for (auto x : S.streams) cudaStreamDestroy(x);
+    delete h;
+    return fail(TN_ECUDA, "tn_server_create: epoch event");
   }
   const int np_ = S.opts.planner_threads > 0 ? std::min(S.opts.planner_threads, 32) : 4;  // planner threads
   const tn_status st = guarded("tn_server_create", [&]() -> tn_status {
@@ -501,6 +530,9 @@ extern "C" tn_status tn_wait(tn_server* h, int64_t ticket, double* out, int64_t 
     }
     stats->planned_here = R->planned_here;
     stats->stem_reused = R->plan && stem_reused(R->plan->plan) ? 1 : 0;
+    stats->gpu_begin_ms = R->gpu_begin_ms;
+    stats->gpu_end_ms = R->gpu_end_ms;
+    stats->quanta = R->nquanta;
   }
   tn_status st = R->status;
   if (st == TN_OK && out) {
@@ -537,8 +569,11 @@ extern "C" void tn_server_destroy(tn_server* h) {
     if (R.h_out) cudaFreeHost(R.h_out);
     for (auto ev : R.quanta) cudaEventDestroy(ev);
     if (R.done_ev) cudaEventDestroy(R.done_ev);
+    if (R.ev_begin) cudaEventDestroy(R.ev_begin);
+    if (R.ev_end) cudaEventDestroy(R.ev_end);
     R.plan.reset();
   }
+  if (S.epoch) cudaEventDestroy(S.epoch);
   for (auto x : S.streams) cudaStreamDestroy(x);
   delete h;
 }

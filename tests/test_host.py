@@ -164,18 +164,25 @@ def test_planner_options_default_to_the_plain_search():
     assert p4.info()["num_sliced"] == 4 and p4.info()["num_qubits"] == 25
 
 
-def test_bench_workload_plan_is_reproducible():
-    """The planner is deterministic host code: the bench's 6x6 workload plans
-    to the same tree, hash and work on any host (the hash and the work below
+@pytest.mark.parametrize("workload,hash_,log2_cmac,sliced,width,nb,first_open", [
+    ("8x8", "0x5973de292b52ff33", 35.846, 80, 24, 1, 54),
+    ("6x6", "0x3e0860a7cb099543", 36.525, 10, 26, 4, 30)])
+def test_bench_workload_plan_is_reproducible(workload, hash_, log2_cmac, sliced, width, nb, first_open):
+    """The planner is deterministic host code: the bench's workloads plan to
+    the same tree, hash and work on any host (the hashes and the work below
     are the ones the bench reports on the GPU machine's Arm host)."""
     import bench
     T = tnlib()
-    _, _, p, words, open_q, _ = bench.make_workload(T, 0)
+    bench.use_workload(workload)
+    try:
+        _, _, p, words, open_q, _ = bench.make_workload(T, 0)
+    finally:
+        bench.use_workload("8x8")
     info = p.info()
-    assert hex(info["hash"]) == "0x3e0860a7cb099543"
-    assert round(float(np.log2(info["cmac_per_slice"])), 3) == 36.525
-    assert info["num_slices"] == 1024 and info["max_log2_intermediate"] == 26
-    assert words.shape[0] == bench.NBATCH and open_q == list(range(30, 36))
+    assert hex(info["hash"]) == hash_
+    assert round(float(np.log2(info["cmac_per_slice"])), 3) == log2_cmac
+    assert info["num_sliced"] == sliced and info["max_log2_intermediate"] == width
+    assert words.shape[0] == nb and open_q == list(range(first_open, first_open + len(open_q)))
 
 
 def test_size_limits_fail_before_any_work():
