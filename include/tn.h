@@ -251,7 +251,45 @@ typedef struct {
                                its output directly as 16-bit operand planes, 2 = it writes complex64 and the
                                consumer splits it (exact per-tensor scale) */
   int32_t reserved3;
+  const int8_t* step_precision; /* NULL, or host array of one entry per plan step (num_steps of
+                               tn_plan_get_info): TN_PREC_* for that step, -1 = `precision`.  Steps
+                               that depend on neither slice nor bitstring always run in complex64.
+                               Per-step precision (Sec. "A Mixed-Precision Computation Method via
+                               Adaptive Precision Scaling": the precision-sensitive parts keep the
+                               accurate format); tn_precision_analysis fills one.  Disables use_graph */
 } tn_exec_opts;
+
+/* Per-step precision from a pre-analysis (Sec. "A Mixed-Precision Computation
+ * Method via Adaptive Precision Scaling": a pre-analysis on a few paths finds
+ * the precision-sensitive parts, which keep the accurate format).  On a probe
+ * -- the nb host bitstrings summed over slices [0, probe_slices) -- it
+ * contracts the complex64 reference, then each candidate step (every step
+ * after the plan-invariant phase whose GEMM fits the tensor cores) in
+ * fast_precision with the other candidates in accurate_precision, orders the
+ * candidates by the error each brings in, and keeps accurate the fewest most
+ * sensitive steps whose mixed assignment meets target_rel_err (relative L2
+ * against the reference) on the probe.  step_precision (num_steps entries,
+ * caller-owned) receives the assignment for tn_exec_opts.step_precision:
+ * fast_precision or accurate_precision on candidates, -1 elsewhere; when even
+ * the all-accurate assignment misses the target every candidate is accurate
+ * and rep->err_mixed says by how much.  Precisions must be 16-bit tensor-core
+ * ones (TN_PREC_SPLIT_BF16 .. TN_PREC_SCALED_BF16); 1 <= nb <= 4096;
+ * TN_EINVAL otherwise, before any work.  Synchronous; runs about
+ * candidates + 2 log2(candidates) probe contractions on the current device. */
+typedef struct {
+  double err_fast;               /* probe error with every candidate fast */
+  double err_accurate;           /* ... every candidate accurate */
+  double err_mixed;              /* ... with the returned assignment */
+  int32_t candidate_steps;
+  int32_t accurate_steps;        /* candidates kept in accurate_precision */
+  double accurate_flops_fraction;/* share of the candidates' counted work (per probe) that runs accurate */
+  int32_t accurate_slice_only_steps; /* of the accurate steps, those that depend on the slice but not on the
+                                        bitstring (the steps nearest the sliced indices) */
+  int32_t probe_runs;            /* contractions the analysis ran */
+} tn_precision_report;
+tn_status tn_precision_analysis(tn_plan_t* p, const uint64_t* bitstrings, int64_t nb, int64_t probe_slices,
+                                int32_t fast_precision, int32_t accurate_precision, double target_rel_err,
+                                int8_t* step_precision, tn_precision_report* rep);
 
 /* Kernel classes of the per-class report figures: FP32 GEMM, bandwidth-bound
  * streaming and reduction kernels, tensor-core GEMMs, operand split passes. */

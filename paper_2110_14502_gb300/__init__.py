@@ -9,7 +9,7 @@ import ctypes as C
 
 import numpy as np
 
-from ._abi import (PAIR_ALGO, PREC, ExecOpts, Gate, NetworkInfo, PlanInfo, PlanOpts, Report, Request,
+from ._abi import (PAIR_ALGO, PREC, ExecOpts, Gate, NetworkInfo, PlanInfo, PlanOpts, PrecisionReport, Report, Request,
                    RequestStats, ServerOpts, TensorLayout, TnError, check, i32array, lib, require_buffer)
 
 __all__ = ["Circuit", "Network", "Plan", "random_circuit", "circuit_from_gates", "build_network", "plan", "select_plan",
@@ -171,9 +171,26 @@ class Plan:
                 cur.append(int(v))
         return leaves, [tuple(int(x) for x in p) for p in tree[: 2 * (L - 1)].reshape(-1, 2)]
 
+    def precision_analysis(self, bitstrings, probe_slices=4, fast="scaled_bf16", accurate="split_fp16",
+                           target=1e-3):
+        """tn_precision_analysis: (int8 per-step precisions for
+        contract_amplitudes(step_precision=...), report dict)."""
+        b = np.ascontiguousarray(np.asarray(bitstrings, dtype=np.uint64))
+        words = (self.info()["num_qubits"] + 63) // 64
+        if b.ndim == 1:
+            b = b.reshape(-1, 1)
+        if b.ndim != 2 or b.shape[1] != words:
+            raise TnError(1, f"bitstrings must have shape (nb, {words}), got {b.shape}")
+        sp = np.zeros(max(self.info()["num_steps"], 1), dtype=np.int8)
+        rep = PrecisionReport()
+        check(lib().tn_precision_analysis(self._h, b.ctypes.data, b.shape[0], probe_slices, PREC[fast],
+                                          PREC[accurate], float(target), sp.ctypes.data, C.byref(rep)))
+        return sp[: self.info()["num_steps"]], {f: getattr(rep, f) for f, _ in PrecisionReport._fields_}
+
     def contract_amplitudes(self, bitstrings, precision="c64", slice_begin=0, slice_count=-1,
                             units_per_group=0, stream=None, out=None, overflow_policy=0, use_graph=0,
-                            profile=False, report=False, test_flag_every=0, autotune=0, handover=0):
+                            profile=False, report=False, test_flag_every=0, autotune=0, handover=0,
+                            step_precision=None):
         """Amplitudes of each bitstring's open batch, summed over the slice range.
 
         bitstrings: uint64 words, shape (nb, ceil(n/64)) -- a NumPy array (host
@@ -195,6 +212,11 @@ class Plan:
         o.test_flag_every = test_flag_every
         o.autotune = autotune
         o.handover = handover
+        if step_precision is not None:
+            sp = np.ascontiguousarray(np.asarray(step_precision, dtype=np.int8))
+            if sp.shape != (info["num_steps"],):
+                raise TnError(1, f"step_precision needs one entry per step ({info['num_steps']}), got {sp.shape}")
+            o.step_precision = sp.ctypes.data
         if stream is not None:
             o.stream = C.c_void_p(getattr(stream, "cuda_stream", stream))
         rep = Report()

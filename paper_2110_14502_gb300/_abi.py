@@ -63,7 +63,7 @@ class ExecOpts(C.Structure):
                 ("slice_begin", C.c_int64), ("slice_count", C.c_int64), ("units_per_group", C.c_int32),
                 ("overflow_policy", C.c_int32), ("use_graph", C.c_int32), ("profile", C.c_int32),
                 ("test_flag_every", C.c_int32), ("autotune", C.c_int32), ("handover", C.c_int32),
-                ("reserved3", C.c_int32)]
+                ("reserved3", C.c_int32), ("step_precision", C.c_void_p)]
 
 
 class ServerOpts(C.Structure):
@@ -84,6 +84,13 @@ class RequestStats(C.Structure):
                 ("nb", C.c_int64), ("plan_hash", C.c_uint64), ("planned_here", C.c_int32), ("stem_reused", C.c_int32),
                 ("slice_fraction", C.c_double), ("gpu_begin_ms", C.c_double), ("gpu_end_ms", C.c_double),
                 ("quanta", C.c_int64)]
+
+
+class PrecisionReport(C.Structure):
+    _fields_ = [("err_fast", C.c_double), ("err_accurate", C.c_double), ("err_mixed", C.c_double),
+                ("candidate_steps", C.c_int32), ("accurate_steps", C.c_int32),
+                ("accurate_flops_fraction", C.c_double), ("accurate_slice_only_steps", C.c_int32),
+                ("probe_runs", C.c_int32)]
 
 
 class Report(C.Structure):
@@ -127,6 +134,8 @@ SIGNATURES = {
     "tn_contract_pair_noalloc": (C.c_int, [C.c_void_p, I32P, C.c_int32, C.c_void_p, I32P, C.c_int32,
                                            C.c_void_p, I32P, C.c_int32, C.c_void_p]),
     "tn_set_wait_limit": (C.c_int, [C.c_int64]),
+    "tn_precision_analysis": (C.c_int, [P, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_double,
+                                        C.c_void_p, C.POINTER(PrecisionReport)]),
 }
 
 _lib = None

@@ -380,6 +380,8 @@ struct Ctx {
   int* flag1 = nullptr;          // [Gs] slice-only units
   int* flag2 = nullptr;          // [U] (bitstring, slice) units
   std::vector<char> planes_out;  // per step: output written as 16-bit planes for a tensor-core consumer
+  const int8_t* step_prec = nullptr;  // per-step precision override (TN_PREC_*, -1 = the call's)
+  int call_precision = TN_PREC_C64;
   bool tuning = false;           // time the tile choices of each tensor-core step
   bool sizing = false;           // only compute scratch needs (no launches)
   int64_t scratch_need = 0;
@@ -420,7 +422,34 @@ void operand(const Plan& P, const Executor& E, int x, int phase, const Geo& g, c
   (void)phase;
 }
 
+void set_precision(Ctx& c, int prec) {
+  c.precision = prec;
+  c.tc = prec != TN_PREC_C64;
+  c.np = (prec == TN_PREC_SPLIT_BF16 || prec == TN_PREC_SPLIT_FP16) ? 4 : 2;
+  c.bf16 = prec == TN_PREC_SPLIT_BF16 || prec == TN_PREC_SCALED_BF16;
+  c.scaled = prec == TN_PREC_SPLIT_FP16 || prec == TN_PREC_SCALED_FP16 || prec == TN_PREC_SCALED_BF16;
+}
+
+tn_status run_step_in(Ctx& c, size_t s, const Geo& g);
+
+// One step in its own precision: the call's, or the per-step override for
+// the steps after phase 0 (phase 0 always runs in complex64).
 tn_status run_step(Ctx& c, size_t s, const Geo& g) {
+  if (!c.step_prec || c.P.steps[s].phase == 0) return run_step_in(c, s, g);
+  const int keep = c.precision;
+  const bool keep_tc = c.tc, keep_bf16 = c.bf16, keep_scaled = c.scaled;
+  const int keep_np = c.np;
+  set_precision(c, c.step_prec[s] >= 0 ? (int)c.step_prec[s] : c.call_precision);
+  const tn_status r = run_step_in(c, s, g);
+  c.precision = keep;
+  c.tc = keep_tc;
+  c.np = keep_np;
+  c.bf16 = keep_bf16;
+  c.scaled = keep_scaled;
+  return r;
+}
+
+tn_status run_step_in(Ctx& c, size_t s, const Geo& g) {
   const Plan& P = c.P;
   Executor& E = c.E;
   const Step& S = P.steps[s];
@@ -630,8 +659,22 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
   }
   Executor& E = *P.exec;
   const int64_t nout = nb << k;
-  const bool scaled = o.precision == TN_PREC_SPLIT_FP16 || o.precision == TN_PREC_SCALED_FP16 ||
-                      o.precision == TN_PREC_SCALED_BF16;
+  // the precision of each step after phase 0 (the call's unless overridden)
+  auto prec_of = [&](size_t s) {
+    return o.step_precision && o.step_precision[s] >= 0 ? (int)o.step_precision[s] : (int)o.precision;
+  };
+  auto is_scaled = [](int pr) {
+    return pr == TN_PREC_SPLIT_FP16 || pr == TN_PREC_SCALED_FP16 || pr == TN_PREC_SCALED_BF16;
+  };
+  bool scaled = is_scaled(o.precision), any_tc = o.precision != TN_PREC_C64;
+  if (o.step_precision) {
+    scaled = any_tc = false;
+    for (size_t s = 0; s < P.steps.size(); ++s)
+      if (P.steps[s].phase != 0) {
+        scaled |= is_scaled(prec_of(s));
+        any_tc |= prec_of(s) != TN_PREC_C64;
+      }
+  }
 
   // ---- group geometry: Gb bitstrings x Gs slices per launch
   const int64_t Se = P.slice_arena_elems, Pe = P.unit_arena_elems;
@@ -699,29 +742,34 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
     d_acc = E.acc;
   }
   Ctx c(P, E, st, o.profile != 0);
-  c.precision = o.precision;
-  c.tc = o.precision != TN_PREC_C64;
-  c.np = (o.precision == TN_PREC_SPLIT_BF16 || o.precision == TN_PREC_SPLIT_FP16) ? 4 : 2;
-  c.bf16 = o.precision == TN_PREC_SPLIT_BF16 || o.precision == TN_PREC_SCALED_BF16;
+  set_precision(c, o.precision);
+  c.tc = any_tc;
   c.scaled = scaled;
+  c.step_prec = o.step_precision;
+  c.call_precision = o.precision;
   c.U = Gs * Gb;
   c.planes_out.assign(P.steps.size(), 0);
   const bool handover = o.handover == 1 || (o.handover == 0 && kHandoverDefault[o.precision]);
-  if (c.tc && handover) {
-    // A step whose consumer also runs on the tensor cores hands its output over
-    // as 16-bit planes laid out for that consumer (no separate split pass).
+  auto handover_of = [&](int pr) { return o.handover == 1 || (o.handover == 0 && kHandoverDefault[pr]); };
+  if (c.tc) {
+    // A step whose consumer also runs on the tensor cores, in the same
+    // precision, hands its output over as 16-bit planes laid out for that
+    // consumer (no separate split pass).
     const int L = (int)P.net.leaves.size();
     std::vector<char> tc(P.steps.size(), 0);
-    for (size_t s = 0; s < P.steps.size(); ++s) tc[s] = P.steps[s].klass != SC_VECTOR && tc_shape_ok(E.desc[s]);
+    for (size_t s = 0; s < P.steps.size(); ++s)
+      tc[s] = P.steps[s].klass != SC_VECTOR && tc_shape_ok(E.desc[s]) && prec_of(s) != TN_PREC_C64;
     for (size_t t = 0; t < P.steps.size(); ++t) {
-      if (!tc[t]) continue;
+      if (!tc[t] || !handover_of(prec_of(t))) continue;
       const Step& S = P.steps[t];
+      const int np_t = (prec_of(t) == TN_PREC_SPLIT_BF16 || prec_of(t) == TN_PREC_SPLIT_FP16) ? 4 : 2;
       for (int role = 0; role < 2; ++role) {
         const int x = role ? S.b : S.a;
         if (x < L) continue;
         const int p = x - L;
         PlaneOperand probe{};
-        if (tc[p] && P.steps[p].phase != 0 && planes_in_place(nullptr, E.desc[t], role == 1, c.np, probe))
+        if (tc[p] && P.steps[p].phase != 0 && prec_of(p) == prec_of(t) &&
+            planes_in_place(nullptr, E.desc[t], role == 1, np_t, probe))
           c.planes_out[p] = 1;
       }
     }
@@ -830,7 +878,8 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
     c.tuning = !have;
   }
   // (stream capture needs an explicit stream: the legacy default stream cannot be captured)
-  const bool graphs = o.use_graph && st != nullptr && !o.profile && !(scaled && o.test_flag_every > 0);
+  const bool graphs = o.use_graph && st != nullptr && !o.profile && !(scaled && o.test_flag_every > 0) &&
+                      !o.step_precision;
   // One launch sequence (the slice-only steps of a group, or the per-unit
   // steps of a group and its accumulation), replayed from a graph when allowed.
   auto sequence = [&](int phase, const Geo& gg) -> tn_status {
@@ -968,6 +1017,7 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
           const int64_t b = f >> 32, s = f & 0xffffffffll;
           tn_exec_opts r = o;
           r.precision = TN_PREC_C64;
+          r.step_precision = nullptr;
           r.device_io = 1;
           r.slice_begin = s;
           r.slice_count = 1;
@@ -1072,6 +1122,10 @@ extern "C" tn_status tn_contract_amplitudes(tn_plan_t* p, const uint64_t* bits, 
   if (o.units_per_group < 0) return fail(TN_EINVAL, "tn_contract_amplitudes: units_per_group < 0");
   if (o.precision < TN_PREC_C64 || o.precision > TN_PREC_SCALED_BF16)
     return fail(TN_EINVAL, "tn_contract_amplitudes: unknown precision %d", o.precision);
+  if (o.step_precision)
+    for (size_t s = 0; s < p->plan.steps.size(); ++s)
+      if (o.step_precision[s] < -1 || o.step_precision[s] > TN_PREC_SCALED_BF16)
+        return fail(TN_EINVAL, "tn_contract_amplitudes: step %zu: unknown precision %d", s, (int)o.step_precision[s]);
   return guarded("tn_contract_amplitudes", [&] { return contract_amplitudes(p->plan, bits, nb, out, o, rep); });
 }
 

@@ -244,6 +244,28 @@ def test_graph_replay_and_autotune_give_identical_sums(mode):
     assert np.array_equal(t, base)
     t = p.contract_amplitudes(words, precision=mode, units_per_group=3, autotune=1, use_graph=1, stream=s)
     assert np.array_equal(t, base)
+    # and every one of them is the right answer: the state vector
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    ref = SV.amplitudes(SV.simulate(gates, n), n, [I.bits_of(w, n) for w in words], open_q)
+    assert rel(base, ref) <= {"c64": 1e-5, "split_bf16": 1e-4, "scaled_fp16": 2e-2}[mode]
+
+
+@pytest.mark.parametrize("mode,tol", [("c64", 1e-5), ("split_fp16", 1e-4), ("scaled_bf16", 2e-2)])
+def test_lattice_ordered_plan_vs_statevector(mode, tol):
+    """A plan from the PEPS-style lattice sweep (order_generator=1; Sec. "A
+    PEPS-based Simulation Method with an Optimized Slicing Strategy")
+    contracted on the GPU, sliced and with open qubits, against the state
+    vector."""
+    T = tnlib()
+    rows, cols, depth, seed, open_q = 4, 5, 12, 13, (15, 16, 17, 18, 19)
+    n = rows * cols
+    p = _setup(T, rows, cols, depth, seed, open_q, num_sliced=4, search_trials=4, seed=1, order_generator=1)
+    assert p.info()["num_sliced"] == 4
+    words = I.bitstrings(n, 3, seed)
+    got = p.contract_amplitudes(words, precision=mode)
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    ref = SV.amplitudes(SV.simulate(gates, n), n, [I.bits_of(w, n) for w in words], open_q)
+    assert rel(got, ref) <= tol
 
 
 def test_full_size_8x8_sampled_slices_vs_oracle():
@@ -455,3 +477,30 @@ def test_failed_device_allocations_report_errors_and_recover(monkeypatch):
         got = p.contract_amplitudes(words, precision="split_bf16")
         assert rel(got, ref) <= 1e-4, k
     assert failures >= 8
+
+
+def test_precision_analysis_keeps_the_sensitive_steps_accurate():
+    """Per-step precision from a pre-analysis (Sec. "A Mixed-Precision
+    Computation Method via Adaptive Precision Scaling"): on a probe of four
+    slices the analysis keeps the most error-sensitive steps in split fp16 and
+    the rest in scaled bf16.  The mixed assignment meets the target on the
+    probe, keeps only part of the steps accurate, and over all slices lands
+    between the all-accurate and the all-fast errors against the state vector."""
+    T = tnlib()
+    rows, cols, depth, seed, open_q = 4, 5, 16, 2, (14, 15, 16, 17, 18, 19)
+    n = rows * cols
+    p = _setup(T, rows, cols, depth, seed, open_q, num_sliced=6, search_trials=16, seed=1)
+    words = I.bitstrings(n, 2, seed)
+    sp, rep = p.precision_analysis(words[:1], probe_slices=4, fast="scaled_bf16", accurate="split_fp16",
+                                   target=2e-3)
+    assert rep["candidate_steps"] > 0 and rep["err_fast"] > 2e-3, rep
+    assert rep["err_mixed"] <= 2e-3 and rep["accurate_steps"] < rep["candidate_steps"], rep
+    assert set(np.unique(sp)) <= {-1, 2, 4}
+    assert int((sp == 2).sum()) == rep["accurate_steps"]
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    ref = SV.amplitudes(SV.simulate(gates, n), n, [I.bits_of(w, n) for w in words], open_q)
+    mixed = rel(p.contract_amplitudes(words, precision="c64", step_precision=sp), ref)
+    fast = rel(p.contract_amplitudes(words, precision="scaled_bf16"), ref)
+    accurate = rel(p.contract_amplitudes(words, precision="split_fp16"), ref)
+    assert accurate <= 1e-4 and mixed < fast, (accurate, mixed, fast)
+    assert mixed <= 5e-3, (accurate, mixed, fast)

@@ -524,3 +524,31 @@ def test_plan_hash_is_fnv1a_of_the_serialized_bytes():
         h = ((h ^ x) * 0x100000001b3) & 0xFFFFFFFFFFFFFFFF
     assert h == p.info()["hash"]
     assert b[:8] == b"TNPLAN01"
+
+
+def test_step_precision_and_precision_analysis_arguments_are_checked():
+    """A per-step precision outside TN_PREC_* and the pre-analysis' bad
+    arguments fail with TN_EINVAL on the host, before any device work."""
+    T = tnlib()
+    from paper_2110_14502_gb300 import _abi
+    L = _abi.lib()
+    _, _, p = _plan(T, 3, 3, 6, 1, open_q=(7, 8), num_sliced=2, search_trials=4)
+    ns = p.info()["num_steps"]
+    words = np.zeros(1, dtype=np.uint64)
+    out = np.zeros(8, dtype=np.complex128)
+    bad = np.full(ns, 7, dtype=np.int8)
+    o = _abi.ExecOpts()
+    o.slice_count = -1
+    o.step_precision = bad.ctypes.data
+    st = L.tn_contract_amplitudes(p._h, words.ctypes.data_as(C.c_void_p), 1, out.ctypes.data_as(C.c_void_p),
+                                  C.byref(o), None)
+    assert st == 1 and "unknown precision 7" in L.tn_last_error().decode()
+    sp = np.zeros(ns, dtype=np.int8)
+    rep = _abi.PrecisionReport()
+    for args, msg in (((words.ctypes.data, 1, 4, 0, 2, 1e-3), "16-bit"),       # c64 is not a 16-bit precision
+                      ((words.ctypes.data, 1, 4, 4, 2, 0.0), "target"),
+                      ((words.ctypes.data, 0, 4, 4, 2, 1e-3), "probe bitstrings"),
+                      ((words.ctypes.data, 1, 5, 4, 2, 1e-3), "outside"),      # 2 sliced indices: 4 slices
+                      ((None, 1, 4, 4, 2, 1e-3), "NULL")):
+        st = L.tn_precision_analysis(p._h, *args, sp.ctypes.data, C.byref(rep))
+        assert st == 1 and msg in L.tn_last_error().decode(), (args, L.tn_last_error())
