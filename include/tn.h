@@ -129,9 +129,28 @@ typedef struct {
  * absorbed into a neighbour (FP64 on the host).  open_qubits may be NULL when
  * num_open == 0; entries must be distinct and in [0, n). */
 tn_status tn_build_network(const tn_circuit* c, const int32_t* open_qubits, int32_t num_open, tn_network** out);
+/* Options of tn_build_network_ex. */
+enum {
+  /* Diagonal decomposition (Sec. "A PEPS-based Simulation Method with an
+   * Optimized Slicing Strategy": diagonal gates turn their wire indices into
+   * hyperedges).  Every two-qubit gate that is a wire swap times a diagonal
+   * (fSim(pi/2, phi) = SWAP diag(1, -i, -i, e^{-i phi}); checked on the
+   * matrix to 1e-12) gets no tensor: the swap renames the wires, and the
+   * diagonal's two operator-Schmidt factors (bond index of dimension 2, named
+   * (q, t) = (-1 - g, 0) for gate g) are merged into the tensors that produced
+   * the two input wires, so every index still has two holders.  Raw tensor
+   * ids of the factors (tn_plan_tree): num_gates + n + 2 g (the copy of wire
+   * x_a into the bond) and num_gates + n + 2 g + 1 (D(bond, x_b)). */
+  TN_NET_SPLIT_DIAGONAL = 1
+};
+/* tn_build_network with options (a bitwise OR of TN_NET_*; TN_EINVAL for
+ * unknown bits). */
+tn_status tn_build_network_ex(const tn_circuit* c, const int32_t* open_qubits, int32_t num_open, int32_t flags,
+                              tn_network** out);
 tn_status tn_network_get_info(const tn_network* net, tn_network_info* info);
 /* Wire-segment name of a label: qubit q after its t-th gate (t = 0 is the
- * input wire).  pairs_out receives 2*num_labels int32 (q, t). */
+ * input wire); (-1 - g, 0) for the bond of gate g's split diagonal.
+ * pairs_out receives 2*num_labels int32 (q, t). */
 tn_status tn_network_label_wires(const tn_network* net, int32_t* pairs_out, int64_t capacity_pairs);
 void tn_free_network(tn_network* net);
 

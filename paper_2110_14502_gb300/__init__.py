@@ -105,10 +105,13 @@ class Network:
         return [tuple(x) for x in a.reshape(-1, 2)]
 
 
-def build_network(circuit, open_qubits=()):
+def build_network(circuit, open_qubits=(), split_diagonal=False):
+    """tn_build_network_ex: the network of <x|U|0^n> with open_qubits open;
+    split_diagonal (TN_NET_SPLIT_DIAGONAL) turns every swap-times-diagonal
+    two-qubit gate into a wire swap plus a rank-2 bond."""
     arr, p = i32array(open_qubits)
     h = C.c_void_p()
-    check(lib().tn_build_network(circuit._h, p, len(arr), C.byref(h)))
+    check(lib().tn_build_network_ex(circuit._h, p, len(arr), 1 if split_diagonal else 0, C.byref(h)))
     return Network(h, circuit)
 
 
@@ -156,7 +159,7 @@ class Plan:
     def tree(self, num_gates, num_qubits):
         """(leaf raw-tensor lists, SSA pairs) of the contraction tree."""
         L = self.info()["num_leaves"]
-        raw = np.zeros(num_gates + num_qubits + L + 1, dtype=np.int32)
+        raw = np.zeros(2 * num_gates + num_qubits + L + 1, dtype=np.int32)  # split diagonals: two factors per gate
         tree = np.zeros(2 * max(L - 1, 1), dtype=np.int32)
         check(lib().tn_plan_tree(self._h, raw.ctypes.data_as(C.POINTER(C.c_int32)), raw.size,
                                  tree.ctypes.data_as(C.POINTER(C.c_int32)), tree.size))

@@ -112,6 +112,7 @@ SIGNATURES = {
     "tn_circuit_gates": (C.c_int, [P, C.POINTER(Gate), C.c_int64]),
     "tn_free_circuit": (None, [P]),
     "tn_build_network": (C.c_int, [P, I32P, C.c_int32, C.POINTER(P)]),
+    "tn_build_network_ex": (C.c_int, [P, I32P, C.c_int32, C.c_int32, C.POINTER(P)]),
     "tn_network_get_info": (C.c_int, [P, C.POINTER(NetworkInfo)]),
     "tn_network_label_wires": (C.c_int, [P, I32P, C.c_int64]),
     "tn_free_network": (None, [P]),

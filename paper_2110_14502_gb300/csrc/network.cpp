@@ -2,6 +2,18 @@
 // RQCs" -- a one-qubit gate is a rank-2 tensor, a two-qubit gate a rank-4
 // tensor), with closed output wires kept as fixed indices and small tensors
 // absorbed into neighbours.
+//
+// Diagonal decomposition (option TN_NET_SPLIT_DIAGONAL; paper: Sec. "A
+// PEPS-based Simulation Method with an Optimized Slicing Strategy", where
+// diagonal gates make their wire indices hyperedges).  A two-qubit gate that
+// is a wire swap times a diagonal -- fSim(pi/2, phi) = SWAP diag(1, -i, -i,
+// e^{-i phi}) -- needs no tensor of its own: the swap renames the wires (the
+// input index of qubit a continues as the wire of qubit b and vice versa)
+// and the diagonal D(x_a, x_b) would make both wire indices hyperedges.  D has
+// operator-Schmidt rank 2, D(x, y) = sum_c delta(x, c) D(c, y), so its two
+// factors go into the tensors that produced the two wires: the producer of
+// x_a gains the bond index c as a copy of x_a, the producer of x_b the factor
+// D(c, x_b).  Every index keeps exactly two holders.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -49,7 +61,19 @@ static Leaf contract_small(const Leaf& U, const Leaf& T) {
   return R;
 }
 
-tn_status build_network(const Circuit& c, const int32_t* open, int num_open, Network& net) {
+// True when the 4x4 matrix m (basis 2 x_a + x_b) is a swap times a diagonal:
+// its only non-zeros are m[00,00], m[01,10], m[10,01], m[11,11].
+static bool swap_times_diagonal(const cd* m) {
+  double off = 0;
+  for (int r = 0; r < 4; ++r)
+    for (int col = 0; col < 4; ++col) {
+      const int swapped = ((col & 1) << 1) | (col >> 1);
+      if (r != swapped) off += std::abs(m[r * 4 + col]);
+    }
+  return off < 1e-12;
+}
+
+tn_status build_network(const Circuit& c, const int32_t* open, int num_open, Network& net, int flags) {
   const int n = c.n;
   net = Network();
   net.n = n;
@@ -65,8 +89,14 @@ tn_status build_network(const Circuit& c, const int32_t* open, int num_open, Net
     return (int)net.wire.size() - 1;
   };
   std::vector<Leaf> leaves;
+  std::vector<int> producer;  // label -> leaf that holds it as an output index
+  auto set_producer = [&](int l, int leaf) {
+    if ((int)producer.size() <= l) producer.resize(l + 1, -1);
+    producer[l] = leaf;
+  };
   for (int q = 0; q < n; ++q) {
     cur[q] = new_label(q, 0);
+    set_producer(cur[q], (int)leaves.size());
     Leaf L;
     L.labels = {cur[q]};
     L.data = {cd(1, 0), cd(0, 0)};
@@ -83,6 +113,43 @@ tn_status build_network(const Circuit& c, const int32_t* open, int num_open, Net
       cur[g.q0] = lout;
       L.labels = {lout, lin};
       L.data.assign(g.m, g.m + 4);
+      set_producer(lout, (int)leaves.size());
+    } else if ((flags & TN_NET_SPLIT_DIAGONAL) && swap_times_diagonal(g.m)) {
+      const int ain = cur[g.q0], bin = cur[g.q1];
+      // D(x_a, x_b): the gate maps |x_a x_b> to D(x_a, x_b) |x_b x_a>
+      auto D = [&](int x, int y) { return g.m[(2 * y + x) * 4 + 2 * x + y]; };
+      const int pa = producer[ain], pb = producer[bin];
+      auto pos = [](const Leaf& F, int l) {
+        int p = 0;
+        while (F.labels[p] != l) ++p;
+        return p;
+      };
+      // raw ids of the two factors (after the gates and the inputs)
+      const int raw_a = net.num_gates + n + 2 * i, raw_b = raw_a + 1;
+      if (pa == pb) {  // one tensor produced both wires: D goes in whole
+        Leaf& F = leaves[pa];
+        const int r = (int)F.labels.size(), ia = pos(F, ain), ib = pos(F, bin);
+        for (size_t e = 0; e < F.data.size(); ++e) F.data[e] *= D((e >> (r - 1 - ia)) & 1, (e >> (r - 1 - ib)) & 1);
+        F.raw.push_back(raw_a);
+        F.raw.push_back(raw_b);
+      } else {
+        const int bond = new_label(-1 - i, 0);
+        for (int side = 0; side < 2; ++side) {
+          Leaf& F = leaves[side ? pb : pa];
+          const int r = (int)F.labels.size(), ip = pos(F, side ? bin : ain);
+          std::vector<cd> nd(F.data.size() * 2);
+          for (size_t e = 0; e < F.data.size(); ++e) {
+            const int w = (int)((e >> (r - 1 - ip)) & 1);
+            for (int cc = 0; cc < 2; ++cc) nd[2 * e + cc] = F.data[e] * (side ? D(cc, w) : cd(w == cc ? 1.0 : 0.0, 0.0));
+          }
+          F.data.swap(nd);
+          F.labels.push_back(bond);
+          F.raw.push_back(side ? raw_b : raw_a);
+        }
+      }
+      cur[g.q0] = bin;
+      cur[g.q1] = ain;
+      continue;
     } else {
       int ain = cur[g.q0], bin = cur[g.q1];
       int aout = new_label(g.q0, ++seg[g.q0]);
@@ -91,6 +158,8 @@ tn_status build_network(const Circuit& c, const int32_t* open, int num_open, Net
       cur[g.q1] = bout;
       L.labels = {aout, bout, ain, bin};  // T[xa',xb',xa,xb] = m[(2xa'+xb')*4 + 2xa+xb]
       L.data.assign(g.m, g.m + 16);
+      set_producer(aout, (int)leaves.size());
+      set_producer(bout, (int)leaves.size());
     }
     leaves.push_back(L);
   }
@@ -157,9 +226,10 @@ tn_status build_network(const Circuit& c, const int32_t* open, int num_open, Net
 
 using namespace tn;
 
-extern "C" tn_status tn_build_network(const tn_circuit* c, const int32_t* open, int32_t num_open,
-                                      tn_network** out) {
+extern "C" tn_status tn_build_network_ex(const tn_circuit* c, const int32_t* open, int32_t num_open, int32_t flags,
+                                         tn_network** out) {
   if (!c || !out) return fail(TN_EINVAL, "tn_build_network: NULL argument");
+  if (flags & ~TN_NET_SPLIT_DIAGONAL) return fail(TN_EINVAL, "tn_build_network: unknown flags 0x%x", flags);
   if (num_open < 0 || num_open > 30 || (num_open > 0 && !open))
     return fail(TN_EINVAL, "tn_build_network: num_open %d not in [0, 30] or open_qubits NULL", num_open);
   for (int i = 0; i < num_open; ++i) {
@@ -170,11 +240,16 @@ extern "C" tn_status tn_build_network(const tn_circuit* c, const int32_t* open, 
   }
   return guarded("tn_build_network", [&]() -> tn_status {
     std::unique_ptr<tn_network_s> h(new tn_network_s);
-    tn_status st = build_network(c->c, open, num_open, h->net);
+    tn_status st = build_network(c->c, open, num_open, h->net, flags);
     if (st != TN_OK) return st;
     *out = h.release();
     return TN_OK;
   });
+}
+
+extern "C" tn_status tn_build_network(const tn_circuit* c, const int32_t* open, int32_t num_open,
+                                      tn_network** out) {
+  return tn_build_network_ex(c, open, num_open, 0, out);
 }
 
 extern "C" tn_status tn_network_get_info(const tn_network* net, tn_network_info* info) {

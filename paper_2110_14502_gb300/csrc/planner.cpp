@@ -275,6 +275,7 @@ int lattice_join(Builder& B, const Network& net, int variant) {
   for (int i = 0; i < L; ++i) {
     int q = net.n, t = 1 << 30;
     for (int l : net.leaves[i].labels) {
+      if (net.wire[l].first < 0) continue;  // bond of a split diagonal: no grid site
       q = std::min(q, net.wire[l].first);
       t = std::min(t, net.wire[l].second);
     }

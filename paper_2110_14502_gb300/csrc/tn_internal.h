@@ -135,7 +135,7 @@ struct Plan : PlanData {
 };
 
 // network.cpp
-tn_status build_network(const Circuit& c, const int32_t* open, int num_open, Network& out);
+tn_status build_network(const Circuit& c, const int32_t* open, int num_open, Network& out, int flags = 0);
 // planner.cpp
 tn_status make_plan(const Network& net, const tn_plan_opts& opts, Plan& plan);
 // executor.cu

@@ -552,3 +552,44 @@ def test_step_precision_and_precision_analysis_arguments_are_checked():
                       ((None, 1, 4, 4, 2, 1e-3), "NULL")):
         st = L.tn_precision_analysis(p._h, *args, sp.ctypes.data, C.byref(rep))
         assert st == 1 and msg in L.tn_last_error().decode(), (args, L.tn_last_error())
+
+
+@pytest.mark.parametrize("rows,cols,depth,seed,open_q,S", [(3, 3, 6, 1, (), 0), (3, 4, 8, 2, (10, 11), 3),
+                                                           (4, 4, 8, 3, (0, 15, 7), 4)])
+def test_split_diagonal_plan_replays_to_the_statevector(rows, cols, depth, seed, open_q, S):
+    """TN_NET_SPLIT_DIAGONAL: the library's network with every fSim(pi/2, pi/6)
+    turned into a wire swap plus a bond, planned and sliced; the oracle's own
+    hyperedge network (oracle.hyper) contracted in the plan's tree order and
+    summed over every assignment of the sliced indices (named by wire, bonds
+    by gate) equals the state vector."""
+    from _replay import replay
+    T = tnlib()
+    n = rows * cols
+    c = T.random_circuit(rows, cols, depth, seed)
+    net = T.build_network(c, list(open_q), split_diagonal=True)
+    p = T.plan(net, num_sliced=S, search_trials=16, seed=1)
+    assert p.info()["num_sliced"] == S
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    bits = I.bits_of(I.bitstrings(n, 1, seed)[0], n)
+    wires = p.sliced_wires()
+    total = 0
+    for s in range(1 << S):
+        fixed = {w: (s >> j) & 1 for j, w in enumerate(wires)}
+        total = total + replay(p, gates, n, bits, open_q, fixed, split=True)
+    ref = SV.amplitudes(SV.simulate(gates, n), n, [bits], open_q)[0]
+    assert np.linalg.norm(total - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_split_diagonal_costs_against_the_plain_network():
+    """The measured effect of the diagonal decomposition on the planner's cost
+    (log2 complex MACs per slice, same search): about even on the 4x4, worse on
+    the 6x6 with 10 sliced indices, because each swap carries a qubit's wire to
+    its neighbour's site and the lattice's cuts grow."""
+    T = tnlib()
+    res = {}
+    for split in (False, True):
+        c = T.random_circuit(6, 6, 16, 2)
+        p = T.plan(T.build_network(c, list(range(30, 36)), split_diagonal=split), num_sliced=10, search_trials=64,
+                   seed=1)
+        res[split] = round(float(np.log2(p.info()["cmac_per_slice"])), 2)
+    assert res == {False: 36.53, True: 39.54}, res

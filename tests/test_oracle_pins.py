@@ -320,3 +320,77 @@ def _contract_counted(ta, la, tb, lb, work):
     work[0] += ta.size * tb.size // (2 ** len(shared))
     t = np.tensordot(ta, tb, axes=(ia, ib))
     return t, [x for x in la if x not in shared] + [x for x in lb if x not in shared]
+
+
+# ---- hyperedge networks and the diagonal decomposition (oracle.hyper)
+
+@pytest.mark.parametrize("phi", [np.pi / 6, 0.3, np.pi])
+def test_fsim_half_pi_is_a_swap_times_its_diagonal(phi):
+    """fSim(pi/2, phi) = SWAP diag(1, -i, -i, e^{-i phi}): the factors U
+    (copy) and V (D) joined by the bond rebuild the gate exactly."""
+    from oracle import hyper as H
+    F = G.fsim(np.pi / 2, phi)
+    D = H.swap_diagonal(F)
+    assert np.allclose(D, [[1, -1j], [-1j, np.exp(-1j * phi)]], atol=1e-15)
+    U, V = np.eye(2), D.T                                   # U[x_a, c], V[x_b, c]
+    T = np.zeros((2, 2, 2, 2), dtype=np.complex128)         # [a', b', a, b]
+    for a in range(2):
+        for b in range(2):
+            T[b, a, a, b] = sum(U[a, c] * V[b, c] for c in range(2))
+    assert np.allclose(T.reshape(4, 4), F, atol=1e-15)
+
+
+def test_swap_diagonal_rejects_other_gates():
+    from oracle import hyper as H
+    assert H.swap_diagonal(G.fsim(np.pi / 3, np.pi / 6)) is None
+    assert H.swap_diagonal(np.kron(G.SQRT_X, np.eye(2))) is None
+    assert H.swap_diagonal(np.diag([1, 1j, 1j, -1])) is None          # diagonal without the swap
+
+
+def test_hyperedge_contraction_by_hand():
+    """Three tensors on one index (a hyperedge): the first pair keeps the
+    index for the third, which sums it: sum_x a_x M_xy c_x, by brute force."""
+    from oracle import hyper as H
+    rng = np.random.default_rng(5)
+    a = rng.normal(size=2) + 1j * rng.normal(size=2)
+    M = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
+    c = rng.normal(size=2) + 1j * rng.normal(size=2)
+    want = np.array([sum(a[x] * M[x, y] * c[x] for x in range(2)) for y in range(2)])
+    for pairs in ([(0, 1), (3, 2)], [(1, 2), (3, 0)], [(0, 2), (3, 1)]):
+        t, l = H.contract_tree([a, M, c], [("x",), ("x", "y"), ("x",)], ["y"], pairs)
+        assert l == ("y",) and np.allclose(t, want, atol=1e-14), pairs
+
+
+@pytest.mark.parametrize("rows,cols,depth,seed,opened", [(3, 3, 6, 1, ()), (2, 4, 8, 2, (6, 7)), (3, 4, 6, 3, (0, 11))])
+def test_split_network_matches_statevector(rows, cols, depth, seed, opened):
+    from oracle import hyper as H
+    gates = C.random_circuit(rows, cols, depth, seed)
+    n = rows * cols
+    rows_ = _rows(n, 2, seed)
+    psi = SV.simulate(gates, n)
+    ref = SV.amplitudes(psi, n, rows_, opened)
+    got = H.amplitudes(gates, n, rows_, opened)
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+    # every fSim of the benchmark gate set was decomposed: no rank-4 tensor left
+    net = H.circuit_network_split(gates, n, rows_[0], opened)
+    assert max(len(l) for l in net.labels) == 2
+
+
+def test_split_network_sliced_sum_equals_unsliced():
+    """Slicing a hyperedge wire index fixes it in all three holders; slicing
+    a bond fixes it in both factors; the sum over assignments is unchanged."""
+    from oracle import hyper as H
+    gates = C.random_circuit(3, 3, 8, 4)
+    n = 9
+    bits = _rows(n, 1, 4)
+    net = H.circuit_network_split(gates, n, bits[0], (8,))
+    count = {}
+    for ls in net.labels:
+        for x in ls:
+            count[x] = count.get(x, 0) + 1
+    hyper_wires = [x for x, k in count.items() if k == 3][:2]
+    bonds = [x for x in count if x[0] < 0][:2]
+    assert len(hyper_wires) == 2 and len(bonds) == 2
+    full = H.amplitudes(gates, n, bits, (8,))
+    sliced = H.amplitudes(gates, n, bits, (8,), sliced=hyper_wires + bonds)
+    assert np.linalg.norm(sliced - full) <= 1e-12 * np.linalg.norm(full)
