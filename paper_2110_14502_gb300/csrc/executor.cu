@@ -30,6 +30,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "kernels.h"
@@ -48,12 +49,15 @@ constexpr bool kHandoverDefault[5] = {false, true, true, true, true};
 
 // A plan's stem: the leaf store and the phase-0 outputs.  Neither depends on
 // the bitstring, the slice or the precision (phase 0 always runs in
-// complex64), so every plan of one circuit can read the same copy.  The
+// complex64), so every plan of one circuit can read the same copy.  A stem
+// is identified by the plan's hash and by a hash of its leaf tensors' values:
+// circuits of the same grid and depth drawn with different seeds have the
+// same structure, hence the same plan, but different gate matrices.  The
 // first plan that needs the phase-0 outputs computes them on its stream and
 // records `ready`; later plans make their streams wait for that event.
 struct Stem {
   int device = -1;
-  uint64_t hash = 0;
+  uint64_t hash = 0, data_hash = 0;
   float2* store = nullptr;
   float2* inv = nullptr;
   int64_t bytes = 0;
@@ -76,7 +80,7 @@ struct StemCache {
   int64_t cap = 0, bytes = 0, hits = 0, misses = 0;
   uint64_t tick = 0;
   struct Entry { std::shared_ptr<Stem> stem; uint64_t last = 0; };
-  std::map<std::pair<int, uint64_t>, Entry> m;
+  std::map<std::tuple<int, uint64_t, uint64_t>, Entry> m;  // (device, plan hash, leaf data hash)
 };
 
 std::shared_ptr<StemCache> make_stem_cache(int64_t cap_bytes) {
@@ -260,7 +264,16 @@ static tn_status upload_leaves(const Plan& P, float2** store) {
 static tn_status acquire_stem(const Plan& P, int device, std::shared_ptr<Stem>& out) {
   StemCache& C = *P.stems;
   std::lock_guard<std::mutex> g(C.mu);
-  const auto key = std::make_pair(device, P.hash);
+  // FNV-1a 64 over the bytes of every leaf tensor's values, in leaf order
+  uint64_t dh = 0xcbf29ce484222325ull;
+  for (const Leaf& lf : P.net.leaves) {
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(lf.data.data());
+    for (size_t i = 0; i < lf.data.size() * sizeof(cd); ++i) {
+      dh ^= b[i];
+      dh *= 0x100000001b3ull;
+    }
+  }
+  const auto key = std::make_tuple(device, P.hash, dh);
   auto it = C.m.find(key);
   if (it != C.m.end()) {
     it->second.last = ++C.tick;
@@ -271,6 +284,7 @@ static tn_status acquire_stem(const Plan& P, int device, std::shared_ptr<Stem>& 
   auto st = std::make_shared<Stem>();
   st->device = device;
   st->hash = P.hash;
+  st->data_hash = dh;
   tn_status r = upload_leaves(P, &st->store);
   if (r != TN_OK) return r;
   CK(dev_alloc(&st->inv, std::max<int64_t>(P.invariant_elems, 1) * sizeof(float2)));

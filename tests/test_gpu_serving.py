@@ -210,3 +210,26 @@ def test_admitted_requests_overlap_on_the_device():
         ref = SV.amplitudes(SV.simulate(gates, n), n, [I.bits_of(w, n) for w in r["bitstrings"]],
                             tuple(range(n - 4, n)))
         assert np.linalg.norm(m - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_same_plan_different_circuits_keep_their_own_stems():
+    """Two circuits of the same grid and depth drawn with different seeds plan
+    to the same tree (the same plan hash) but have different gate matrices:
+    the resident stem of one must never serve the other."""
+    T = tnlib()
+    reqs = [_req(4, 5, 14, 60 + i, 4, 2) for i in range(2)]
+    srv = T.Server(max_inflight=2, slices_per_quantum=16, precision="c64", plan_trials=8, max_log2_intermediate=15)
+    try:
+        res = [srv.wait(srv.submit(**r)) for r in reqs]
+        again = srv.wait(srv.submit(**reqs[0]))
+    finally:
+        srv.close()
+    assert res[0][1]["plan_hash"] == res[1][1]["plan_hash"]
+    assert res[1][1]["stem_reused"] == 0 and again[1]["stem_reused"] == 1
+    assert np.array_equal(again[0], res[0][0])
+    n = 20
+    for r, (out, _) in zip(reqs, res):
+        gates = OC.random_circuit(r["rows"], r["cols"], r["depth"], r["seed"])
+        ref = SV.amplitudes(SV.simulate(gates, n), n, [I.bits_of(w, n) for w in r["bitstrings"]],
+                            tuple(range(n - 4, n)))
+        assert np.linalg.norm(out - ref) <= 1e-5 * np.linalg.norm(ref)
