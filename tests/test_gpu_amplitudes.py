@@ -549,3 +549,39 @@ def test_split_diagonal_6x6_sampled_slice_vs_oracle():
     ref = replay(p, gates, n, I.bits_of(words[0], n), open_q, {w: (s >> j) & 1 for j, w in enumerate(wires)},
                  split=True)
     assert rel(got, ref) <= 1e-5
+
+
+def test_c_program_contracts_and_serves_through_the_abi(tmp_path):
+    """A plain C99 program (tests/c_abi_contract.c) linked against the library
+    calls tn_contract_amplitudes with host buffers in complex64 and split fp16
+    and serves one request; its printed amplitudes match the state vector."""
+    import os
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if not gcc:
+        pytest.skip("no C compiler")
+    T = tnlib()
+    from paper_2110_14502_gb300 import _abi
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.dirname(_abi.LIB_PATH)
+    exe = str(tmp_path / "c_abi_contract")
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(root, "include"),
+                    os.path.join(root, "tests", "c_abi_contract.c"), "-o", exe, "-L", libdir, "-ltn",
+                    f"-Wl,-rpath,{libdir}"], check=True, capture_output=True, text=True)
+    rows, cols, depth, seed, k = 4, 5, 12, 15, 3
+    n = rows * cols
+    words = I.bitstrings(n, 3, seed)
+    r = subprocess.run([exe] + [f"{int(w):x}" for w in words.reshape(-1)], capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr
+    got = {}
+    for line in r.stdout.split("\n"):
+        if line:
+            tag, b, j, re_, im_ = line.split()
+            got.setdefault(tag, np.zeros((len(words), 1 << k), dtype=np.complex128))[int(b), int(j)] = \
+                float(re_) + 1j * float(im_)
+    gates = OC.random_circuit(rows, cols, depth, seed)
+    ref = SV.amplitudes(SV.simulate(gates, n), n, [I.bits_of(w, n) for w in words], tuple(range(n - k, n)))
+    assert rel(got["c64"], ref) <= 1e-5 and rel(got["served"], ref) <= 1e-5
+    assert rel(got["split_fp16"], ref) <= 1e-4
