@@ -188,7 +188,8 @@ typedef struct {
   int32_t num_steps;
   int32_t num_leaves;
   int32_t max_log2_intermediate; /* largest per-slice tensor (log2 elements) */
-  int64_t num_slices;            /* 2^num_sliced */
+  int64_t num_slices;            /* slice ids a call can address: 2^num_sliced, at most 2^62 (higher
+                                    sliced indices then stay at 0) */
   double cmac_per_slice;         /* counted complex multiply-adds of one slice */
   double flops_per_slice;        /* 8 real flops per complex MAC (counted, not issued) */
   double log2_cmac_total;        /* log2(cmac_per_slice * num_slices) */

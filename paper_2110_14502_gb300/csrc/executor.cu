@@ -556,7 +556,8 @@ tn_status run_step_in(Ctx& c, size_t s, const Geo& g) {
       const double bytes = (a_in ? 0.0 : std::ldexp(1.0, d.nm) * (8.0 * K + 2.0 * c.np * kp) * nza) +
                            (b_in ? 0.0 : std::ldexp(1.0, d.nn) * (8.0 * K + 2.0 * c.np * kp) * nzb);
       (void)per;
-      c.recs.push_back({TN_KCLASS_SPLIT, 0.0, bytes, e0});
+      c.recs.push_back({TN_KCLASS_SPLIT, 0.0, bytes, e0, (int)s, d.nm, d.nn, d.nk, d.units, 0,
+                        (a_in ? 0 : 1) | (b_in ? 0 : 2), 0, 0, 0});
       e0 = em;
     }
     if (e == cudaSuccess && c.tuning) {
@@ -659,7 +660,7 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
   const int n = P.net.n;
   const int k = (int)P.net.open_qubits.size();
   const int words = std::max(1, (n + 63) / 64);
-  const int64_t S_all = int64_t(1) << P.sliced.size();
+  const int64_t S_all = num_slice_ids(P);
   const int64_t s_begin = o.slice_begin;
   const int64_t ns = o.slice_count < 0 ? S_all - s_begin : o.slice_count;
   if (s_begin < 0 || s_begin > S_all || ns < 0 || s_begin + ns > S_all)
@@ -1073,7 +1074,7 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
     // one JSON object per step, slowest first.  c_fastest lists C's four
     // fastest indices (stride 8, 4, 2, 1) as three-digit codes: row bit i ->
     // i, column bit j -> 100 + j, none -> 999.
-    struct StepAgg { int klass = 0, nm = 0, nn = 0, nk = 0, launches = 0, planes = 0, n16 = 0, ulo = 0, uhi = 0; long long cfast = 0; int64_t units = 0; double ms = 0, flops = 0; };
+    struct StepAgg { int step = 0, klass = 0, nm = 0, nn = 0, nk = 0, launches = 0, planes = 0, n16 = 0, ulo = 0, uhi = 0; long long cfast = 0; int64_t units = 0; double ms = 0, flops = 0; };
     std::map<int, StepAgg> per_step;
     const bool by_step = getenv("TN_PROFILE_STEPS") != nullptr;
     for (auto& r : c.recs) {
@@ -1084,7 +1085,9 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
       rep->class_flops[r.klass] += r.flops;
       rep->class_bytes[r.klass] += r.bytes;
       if (by_step) {
-        StepAgg& a = per_step[r.step];
+        // a step's operand split pass is listed apart from its GEMM
+        StepAgg& a = per_step[r.klass == TN_KCLASS_SPLIT ? -1 - r.step : r.step];
+        a.step = r.step;
         a.klass = r.klass;
         a.nm = r.nm;
         a.nn = r.nn;
@@ -1110,7 +1113,7 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
                 "\"log2_k\": %d, \"units\": %lld, \"launches\": %d, \"ms\": %.3f, \"tflops\": %.1f, "
                 "\"c_fastest\": \"%012lld\", \"planes_out\": %d, \"vec16\": %d, \"a_b_vary_lo\": %d, "
                 "\"a_b_vary_hi\": %d}\n",
-                st_i, P.steps[st_i].phase, kname[a.klass & 3], a.nm, a.nn, a.nk, (long long)a.units, a.launches,
+                a.step, P.steps[a.step].phase, kname[a.klass & 3], a.nm, a.nn, a.nk, (long long)a.units, a.launches,
                 a.ms, a.ms > 0 ? a.flops / (a.ms * 1e9) : 0.0, a.cfast, a.planes, a.n16, a.ulo, a.uhi);
     }
   }

@@ -941,7 +941,7 @@ extern "C" tn_status tn_plan_get_info(const tn_plan_t* p, tn_plan_info* info) {
   info->num_steps = (int)P.steps.size();
   info->num_leaves = (int)P.net.leaves.size();
   info->max_log2_intermediate = P.max_width;
-  info->num_slices = int64_t(1) << P.sliced.size();
+  info->num_slices = num_slice_ids(P);
   info->cmac_per_slice = P.cmac_per_slice;
   info->flops_per_slice = 8.0 * P.cmac_per_slice;
   info->log2_cmac_total = std::log2(std::max(P.cmac_per_slice, 1.0)) + (double)P.sliced.size();

@@ -56,7 +56,7 @@ extern "C" tn_status tn_precision_analysis(tn_plan_t* p, const uint64_t* bitstri
     return fail(TN_EINVAL, "tn_precision_analysis: fast and accurate precisions must be 16-bit tensor-core ones");
   if (!(target_rel_err > 0)) return fail(TN_EINVAL, "tn_precision_analysis: target error must be > 0");
   const Plan& P = p->plan;
-  const int64_t S_all = P.sliced.size() >= 62 ? INT64_MAX : int64_t(1) << P.sliced.size();
+  const int64_t S_all = num_slice_ids(P);
   if (probe_slices < 1 || probe_slices > S_all)
     return fail(TN_EINVAL, "tn_precision_analysis: probe of %lld slices outside [1, 2^%zu]", (long long)probe_slices,
                 P.sliced.size());

@@ -172,7 +172,7 @@ tn_status plan_request(Server& S, Request& R) {
   R.plan.reset(copy);
   const Plan& P = R.plan->plan;
   // fidelity by fraction: the first ceil(f 2^S) slices (all for f = 0 or 1)
-  const int64_t all = int64_t(1) << P.sliced.size();
+  const int64_t all = num_slice_ids(P);
   R.ns = partial ? std::max<int64_t>(1, std::min<int64_t>(all, (int64_t)std::ceil(f * (double)all))) : all;
   // rounding up to whole slices can serve more than f of the work
   const double served = std::log2(std::max(1.0, (double)R.ns * P.cmac_per_slice));

@@ -120,6 +120,13 @@ struct PlanData {
   uint64_t hash = 0;
 };
 
+// Slice ids a call can address: 2^S, or 2^62 when S >= 62 (ids are int64_t;
+// bit j of the id fixes sliced index j, so higher sliced indices of a plan
+// with S >= 62 stay at 0 -- a leading range of the 2^S slices).
+inline int64_t num_slice_ids(const PlanData& P) {
+  return P.sliced.size() >= 62 ? int64_t(1) << 62 : int64_t(1) << P.sliced.size();
+}
+
 // A plan plus its device state.  Copies share nothing on the device: a copy
 // starts without an executor and allocates its own on first use.
 struct Plan : PlanData {

@@ -268,16 +268,19 @@ def test_lattice_ordered_plan_vs_statevector(mode, tol):
     assert rel(got, ref) <= tol
 
 
-def test_full_size_8x8_sampled_slices_vs_oracle():
+@pytest.mark.parametrize("cap_aware", [0, 1])
+def test_full_size_8x8_sampled_slices_vs_oracle(cap_aware):
     """8x8 grid (64 qubits), depth 1+20+1, seed 4, per-slice width capped at
     2^26, ten open qubits (1024 correlated amplitudes per bitstring): two
     sampled slices against the oracle's FP64 contraction of the same slice
-    assignment, in complex64 and in split fp16."""
+    assignment, in complex64 and in split fp16; with the plain search and
+    with width-cap-aware subtree rewrites (68 instead of 80 sliced indices)."""
     T = tnlib()
     rows, cols, depth, seed = 8, 8, 20, 4
     n = 64
     open_q = tuple(range(54, 64))
-    p = _setup(T, rows, cols, depth, seed, open_q, max_log2_intermediate=26, search_trials=8, seed=1)
+    p = _setup(T, rows, cols, depth, seed, open_q, max_log2_intermediate=26, search_trials=8 if not cap_aware else 16,
+               seed=1, cap_aware_rewrites=cap_aware)
     info = p.info()
     assert info["max_log2_intermediate"] <= 26
     wires = p.sliced_wires()

@@ -593,3 +593,26 @@ def test_split_diagonal_costs_against_the_plain_network():
                    seed=1)
         res[split] = round(float(np.log2(p.info()["cmac_per_slice"])), 2)
     assert res == {False: 36.53, True: 39.54}, res
+
+
+def test_plans_with_more_than_62_sliced_indices_address_a_leading_slice_range():
+    """With S >= 62 sliced indices the slice ids (int64) address the first
+    2^62 slices (bit j of the id fixes sliced index j; higher indices stay 0):
+    num_slices says so, a range inside it passes the host checks and one
+    beyond it fails with TN_EINVAL before any device work."""
+    T = tnlib()
+    from paper_2110_14502_gb300 import _abi
+    L = _abi.lib()
+    p = T.plan(T.build_network(T.random_circuit(8, 8, 20, 4), list(range(54, 64))), max_log2_intermediate=26,
+               search_trials=16, seed=1, cap_aware_rewrites=1)
+    info = p.info()
+    assert info["num_sliced"] == 68 and info["num_slices"] == 1 << 62
+    assert abs(info["log2_cmac_total"] - (68 + np.log2(info["cmac_per_slice"]))) < 1e-9
+    words = np.zeros((1, 1), dtype=np.uint64)
+    out = np.zeros(2 << 10, dtype=np.float64)
+    o = _abi.ExecOpts()
+    o.slice_begin = (1 << 62) - 1
+    o.slice_count = 2
+    st = L.tn_contract_amplitudes(p._h, words.ctypes.data_as(C.c_void_p), 1, out.ctypes.data_as(C.c_void_p),
+                                  C.byref(o), None)
+    assert st == 1 and "outside [0, 4611686018427387904)" in L.tn_last_error().decode()
