@@ -553,13 +553,15 @@ def run_stream(T, srv, reqs, gaps=None, rate=None, keep=()):
             while time.time() < target:
                 time.sleep(0.0002)
         tickets.append(srv.submit(**r))
-    lat, amps, refused, flops, kept = [], 0, 0, 0.0, {}
+    lat, amps, refused, flops, kept, fractions = [], 0, 0, 0.0, {}, []
     for i, t in enumerate(tickets):
         try:
             o, st = srv.wait(t)
             lat.append(st["submit_to_done_ms"])
             amps += o.size
             flops += st["flops"]
+            if st["slice_fraction"] < 1.0:
+                fractions.append(st["slice_fraction"])
             if i in keep:
                 kept[i] = o
         except T.TnError as e:
@@ -568,10 +570,15 @@ def run_stream(T, srv, reqs, gaps=None, rate=None, keep=()):
             else:
                 raise
     dt = time.time() - t0
-    return {"seconds": round(dt, 3), "served": len(lat), "refused": refused,
-            "amplitudes_per_s": round(amps / dt, 1), "tflops": round(flops / dt / 1e12, 3),
-            "p50_ms": round(float(np.percentile(lat, 50)), 2) if lat else None,
-            "p99_ms": round(float(np.percentile(lat, 99)), 2) if lat else None}, kept
+    res = {"seconds": round(dt, 3), "served": len(lat), "refused": refused,
+           "amplitudes_per_s": round(amps / dt, 1), "tflops": round(flops / dt / 1e12, 3),
+           "p50_ms": round(float(np.percentile(lat, 50)), 2) if lat else None,
+           "p99_ms": round(float(np.percentile(lat, 99)), 2) if lat else None}
+    if fractions:
+        lf = np.log2(fractions)
+        res["partial_fidelity"] = {"requests": len(fractions), "log2_fraction_min": round(float(lf.min()), 2),
+                                   "log2_fraction_median": round(float(np.median(lf)), 2)}
+    return res, kept
 
 
 def serve_summary(args):
@@ -623,6 +630,13 @@ def serve_summary(args):
         errs = [rel_err(kept[i].reshape(-1), refs[i].reshape(-1)) for i in small if i in kept]
         out[name] = {"saturated": sat, "poisson": poi,
                      "max_rel_err_vs_fp64": max(errs) if errs else None}
+    # the same stream with over-cap requests served at partial fidelity (the
+    # largest leading slice range that fits the cap) instead of refused
+    srv = T.Server(max_inflight=8, slices_per_quantum=64, precision="split_bf16", over_cap_policy=1, **common)
+    try:
+        out["batched_split_bf16_over_cap_partial"], _ = run_stream(T, srv, reqs)
+    finally:
+        srv.close()
     return out
 
 

@@ -361,6 +361,13 @@ typedef struct {
                                     bitstring); 0 = 48 */
   int32_t max_log2_intermediate; /* per-slice width cap when planning; 0 = 27 */
   int32_t planner_threads;       /* host threads planning new circuits concurrently; 0 = 4 (max 32) */
+  int32_t over_cap_policy;       /* a request whose full plan costs more than the cap: 0 = fail it with
+                                    TN_ETOOBIG; 1 = serve it at partial fidelity, from the largest
+                                    leading range of slices that fits the cap (Sec. "A Mixed-Precision
+                                    Computation Method via Adaptive Precision Scaling": a fraction f of
+                                    the slices gives fidelity about f; tn_request_stats.slice_fraction
+                                    reports f), TN_ETOOBIG only when one slice exceeds the cap */
+  int32_t reserved;
 } tn_server_opts;
 
 /* One request: the amplitudes of nb bitstrings of the seeded random circuit

@@ -350,7 +350,8 @@ class Server:
     memory and in-flight slots, and interleaved slice quantum by quantum."""
 
     def __init__(self, max_inflight=4, slices_per_quantum=64, precision="c64", plan_trials=16,
-                 hbm_budget_bytes=0, max_log2_cmac=0.0, max_log2_intermediate=0, planner_threads=0):
+                 hbm_budget_bytes=0, max_log2_cmac=0.0, max_log2_intermediate=0, planner_threads=0,
+                 over_cap_policy=0):
         o = ServerOpts()
         o.max_inflight = max_inflight
         o.slices_per_quantum = slices_per_quantum
@@ -360,6 +361,7 @@ class Server:
         o.max_log2_cmac = max_log2_cmac
         o.max_log2_intermediate = max_log2_intermediate
         o.planner_threads = planner_threads
+        o.over_cap_policy = over_cap_policy
         h = C.c_void_p()
         check(lib().tn_server_create(C.byref(o), C.byref(h)))
         self._h = h

@@ -69,7 +69,8 @@ class ExecOpts(C.Structure):
 class ServerOpts(C.Structure):
     _fields_ = [("max_inflight", C.c_int32), ("slices_per_quantum", C.c_int32), ("precision", C.c_int32),
                 ("plan_trials", C.c_int32), ("hbm_budget_bytes", C.c_int64), ("max_log2_cmac", C.c_double),
-                ("max_log2_intermediate", C.c_int32), ("planner_threads", C.c_int32)]
+                ("max_log2_intermediate", C.c_int32), ("planner_threads", C.c_int32),
+                ("over_cap_policy", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Request(C.Structure):

@@ -123,7 +123,9 @@ tn_status plan_request(Server& S, Request& R) {
   // fraction f of the slices, so its plan may cost up to 2^cap / f in full
   const double f = p.fidelity;
   const bool partial = f > 0.0 && f < 1.0;
-  const double cap = S.opts.max_log2_cmac + (partial ? -std::log2(f) : 0.0);
+  // over_cap_policy 1: plan without a cost cap and serve the slices that fit
+  const bool fit = S.opts.over_cap_policy == 1 && !partial;
+  const double cap = fit ? 1000.0 : S.opts.max_log2_cmac + (partial ? -std::log2(f) : 0.0);
   PlanKey key{p.rows, p.cols, p.depth, p.num_open, p.seed, S.opts.plan_trials, S.opts.max_log2_intermediate, cap};
   std::shared_ptr<tn_plan_s> cached;
   {
@@ -174,6 +176,17 @@ tn_status plan_request(Server& S, Request& R) {
   // fidelity by fraction: the first ceil(f 2^S) slices (all for f = 0 or 1)
   const int64_t all = num_slice_ids(P);
   R.ns = partial ? std::max<int64_t>(1, std::min<int64_t>(all, (int64_t)std::ceil(f * (double)all))) : all;
+  if (fit) {
+    // the largest leading range of slices whose work fits the cap
+    const double full = std::log2(std::max(1.0, P.cmac_per_slice)) + (double)P.sliced.size();
+    if (full > S.opts.max_log2_cmac) {
+      const double fits = std::floor(std::exp2(S.opts.max_log2_cmac) / std::max(1.0, P.cmac_per_slice));
+      if (fits < 1.0)
+        return fail(TN_ETOOBIG, "serving: one slice costs 2^%.1f CMAC, above the cap 2^%.1f",
+                    std::log2(P.cmac_per_slice), S.opts.max_log2_cmac);
+      R.ns = std::min<int64_t>(all, (int64_t)std::min(fits, 4.0e18));
+    }
+  }
   // rounding up to whole slices can serve more than f of the work
   const double served = std::log2(std::max(1.0, (double)R.ns * P.cmac_per_slice));
   if (partial && served > S.opts.max_log2_cmac)

@@ -233,3 +233,31 @@ def test_same_plan_different_circuits_keep_their_own_stems():
         ref = SV.amplitudes(SV.simulate(gates, n), n, [I.bits_of(w, n) for w in r["bitstrings"]],
                             tuple(range(n - 4, n)))
         assert np.linalg.norm(out - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_over_cap_requests_are_served_at_partial_fidelity_when_asked():
+    """over_cap_policy 1: a request whose full plan costs more than the cap is
+    served from the largest leading range of slices that fits it (fidelity
+    about the served fraction) instead of failing; its amplitudes are the
+    plain path's partial sum over the same slices."""
+    import math
+    T = tnlib()
+    req = _req(4, 5, 12, 21, 3, 2)
+    cap = 25.3
+    srv = T.Server(max_inflight=2, precision="c64", plan_trials=8, max_log2_intermediate=12, max_log2_cmac=cap,
+                   over_cap_policy=1)
+    try:
+        part, st = srv.wait(srv.submit(**req))
+    finally:
+        srv.close()
+    c = T.random_circuit(4, 5, 12, 21)
+    p = T.plan(T.build_network(c, [17, 18, 19]), max_log2_intermediate=12, search_trials=8, seed=1,
+               max_log2_cmac=1000.0)
+    info = p.info()
+    assert info["hash"] == st["plan_hash"]
+    ns = int(math.floor(2 ** cap / info["cmac_per_slice"]))
+    assert 1 <= ns < info["num_slices"] and st["slices"] == ns and st["status"] == 0
+    assert abs(st["slice_fraction"] - ns / info["num_slices"]) < 1e-12
+    assert math.log2(ns * info["cmac_per_slice"]) <= cap
+    ref = p.contract_amplitudes(req["bitstrings"], slice_count=ns)
+    assert np.linalg.norm(part - ref) <= 1e-6 * np.linalg.norm(ref)
