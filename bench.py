@@ -395,6 +395,9 @@ def run_ours(args):
             if mode in errs:
                 modes[mode]["rel_err_vs_fp64_sample"] = errs[mode]
         line["precision_modes"] = modes
+        if args.workload == "8x8" and not PLAN_CAP_AWARE:
+            line["plan_variants"] = {"width_cap_aware_rewrites": cap_aware_variant(T, args, words, open_q, dwords,
+                                                                                     out, stream, nout)}
         if args.workload == "8x8" and not args.no_6x6:
             line["workload_6x6"] = six_by_six_summary(T)
     if dist:
@@ -404,6 +407,31 @@ def run_ours(args):
         line["serving"] = serve_summary(args)
     if rank == 0:
         print(json.dumps(line))
+
+
+def cap_aware_variant(T, args, words, open_q, dwords, out, stream, nout):
+    """The same workload planned with width-cap-aware subtree rewrites (fewer
+    sliced indices under the 2^26 cap, more work per slice): one timed step
+    of the bench precision, its error against the FP64 oracle on slice 0."""
+    global PLAN_CAP_AWARE
+    keep = PLAN_CAP_AWARE
+    PLAN_CAP_AWARE = 1
+    try:
+        _, _, p, _, _, _ = make_workload(T, 0)
+    finally:
+        PLAN_CAP_AWARE = keep
+    info = p.info()
+    slices = min(SLICE_LIMIT, info["num_slices"])
+    e = time_mode(p, dwords, out, stream, args.precision, slices, 1, nout)
+    e.update({"plan_hash": hex(info["hash"]), "num_sliced": info["num_sliced"],
+              "fidelity_fraction_log2": round(float(np.log2(slices)) - info["num_sliced"], 3),
+              "cmac_per_slice_log2": round(float(np.log2(info["cmac_per_slice"])), 3),
+              "max_log2_intermediate": info["max_log2_intermediate"]})
+    if not args.no_cpu:
+        ref, _, _ = oracle_reference(p, words, open_q)
+        e["rel_err_vs_fp64_sample"] = mode_errors(p, words, ref, [args.precision])[args.precision]
+    del p
+    return e
 
 
 def six_by_six_summary(T):

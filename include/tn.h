@@ -491,7 +491,7 @@ tn_status tn_set_wait_limit(int64_t polls);
  * TN_PAIR_FUSED_TC and precision = TN_PREC_SPLIT_BF16 (M >= 128, N >= 16,
  * K >= 8).  Scratch comes from one static device array of 64 MiB per GPU
  * (kept until the process exits): the split operand planes,
- * 8 * (M + N) * max(K, 32) bytes, must fit, else TN_EINVAL before any work.
+ * 8 * (M + N) * K bytes, must fit, else TN_EINVAL before any work.
  * The first call on a device (that device current) looks up the array's
  * address with cudaGetSymbolAddress; make it before any stream capture.  All
  * calls on a device share the array: calls whose work overlaps on the GPU

@@ -549,7 +549,7 @@ tn_status run_step_in(Ctx& c, size_t s, const Geo& g) {
       size_t em = 0;
       tn_status r = c.event(em);
       if (r) return r;
-      const double K = std::ldexp(1.0, d.nk), kp = std::max(K, 32.0);
+      const double K = std::ldexp(1.0, d.nk), kp = K;
       const double nza = (d.a_lo ? d.units_lo : 1.0) * (d.a_hi ? (double)d.units / d.units_lo : 1.0);
       const double nzb = (d.b_lo ? d.units_lo : 1.0) * (d.b_hi ? (double)d.units / d.units_lo : 1.0);
       const double per = 8.0 + 2.0 * c.np;  // bytes read + written per complex element

@@ -1,7 +1,7 @@
 // Operand preparation for the TMA-fed tensor-core GEMM: gather a complex64
 // operand through its per-bit strides (the index permutation) and write it
-// once as four K-major 16-bit planes {re_hi, re_lo, im_hi, im_lo}, rows padded
-// to the tile and K padded to the stage width with zeros.
+// once as four K-major 16-bit planes {re_hi, re_lo, im_hi, im_lo} of K (>= 8)
+// values per row; the GEMM's TMA box reads past a short K as zeros.
 //
 // Paper: Sec. "Tensor Contraction Using Fused Permutation and Multiplication",
 // imbalanced case (TTGT: one permuted copy of each operand feeds the GEMM; the
@@ -181,7 +181,7 @@ void split_desc(int nrow, const int32_t* row_st, int nk, const int32_t* k_st, in
   sd.nrow = nrow;
   sd.nk = nk;
   sd.rows_pad = 1 << nrow;
-  sd.kp = std::max(1 << nk, 32);
+  sd.kp = 1 << nk;  // tensor-core shapes have K >= 8: whole 16-byte chunks, no padding
   sd.nlo = nlo;
   sd.lo = lo;
   sd.hi = hi;
@@ -230,7 +230,7 @@ bool planes_in_place(const float2* base, const GemmDesc& d, bool which_b, int np
   const int32_t* rs = which_b ? d.bn : d.am;
   const int32_t* ks = which_b ? d.bk : d.ak;
   const int64_t K = int64_t(1) << d.nk;
-  if (K < 32) return false;
+  if (K < 8) return false;
   for (int l = 0; l < d.nk; ++l)
     if (ks[l] != (int32_t(1) << l)) return false;
   for (int i = 0; i < nrow; ++i)

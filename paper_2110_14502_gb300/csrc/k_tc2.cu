@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     m0 = (g * GM + r % gm) * TM;
     n0 = (r / gm) * TN;
   }
-  const int nkt = kp / TKC;
+  const int nkt = (kp + TKC - 1) / TKC;  // a short K (8, 16) is one stage; TMA zero-fills past K
 
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int ntm = (int)((int64_t(1) << d.nm) / TM), ntn = (int)((int64_t(1) << d.nn) / TN);
   const int tiles = ntm * ntn;
   const int64_t items = (int64_t)tiles * d.units;
-  const int nkt = kp / TKC;
+  const int nkt = (kp + TKC - 1) / TKC;  // a short K (8, 16) is one stage; TMA zero-fills past K
   const int GM = d.group_m > 0 ? d.group_m : GROUP_M_DEFAULT;
   auto decode = [&](int64_t item, int& unit, int& m0, int& n0) {
     unit = (int)(item / tiles);
@@ -785,7 +785,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int ntm = (int)((int64_t(1) << d.nm) / TM), ntn = fold > 1 ? 1 : (int)((int64_t(1) << d.nn) / TN);
   const int tiles = ntm * ntn;
   const int64_t items = (int64_t)tiles * (d.units / fold);
-  const int nkt = kp / TKC;
+  const int nkt = (kp + TKC - 1) / TKC;  // a short K (8, 16) is one stage; TMA zero-fills past K
   const int nch = (nkt + chunk - 1) / chunk;
   const int GM = d.group_m > 0 ? d.group_m : GROUP_M_DEFAULT;
   auto decode = [&](int64_t item, int& unit, int& m0, int& n0) {
@@ -1081,7 +1081,10 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 5-D map over one operand's planes: [hi unit][lo unit][plane][row][k] of
 // 16-bit values; box = 32 k x box_rows x box_planes x 1 x 1 (box_planes 0:
-// all np planes).
+// all np planes).  A plane row holds K >= 8 values (16 bytes or more); when
+// K < 32 the box reaches past it and the copy fills those K positions with
+// zeros (the other operand's are zero as well, so the products vanish), and
+// the stage still receives the box's full byte count.
 bool encode_planes(CUtensorMap* map, const PlaneOperand& o, int box_rows, int box_planes = 0) {
   auto fn = encode_fn();
   if (!fn) return false;
@@ -1211,13 +1214,13 @@ int tma_tile_n(const GemmDesc& d) {
 }
 
 int64_t split_plane_elems(int nrow_bits, int nk_bits, int np) {
-  const int64_t kp = std::max<int64_t>(int64_t(1) << nk_bits, TKC);
+  const int64_t kp = int64_t(1) << nk_bits;  // K >= 8 (tensor-core shapes): rows of >= 16 bytes
   return np * (int64_t(1) << nrow_bits) * kp;
 }
 
 cudaError_t launch_gemm_tma(const PlaneOperand& a, const PlaneOperand& b, float2* C, bool c_planes, const GemmDesc& d,
                             bool bf16, const ScaleIO& sio, int* err, cudaStream_t s) {
-  if (!tc_shape_ok(d) || d.units > 65535 || a.kp != b.kp || a.kp % TKC || a.np != b.np ||
+  if (!tc_shape_ok(d) || d.units > 65535 || a.kp != b.kp || a.kp % 8 || a.np != b.np ||
       (a.np != 2 && a.np != 4))
     return cudaErrorInvalidValue;
   int TNv = tma_tile_n(d);

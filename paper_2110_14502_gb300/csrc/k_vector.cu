@@ -98,11 +98,13 @@ __global__ void __launch_bounds__(NT) vector_kernel(const float2* __restrict__ A
 }
 
 // Longer contracted index (K = 32..128) with a narrow B (N <= 8, N K <= 1024):
-// the same streaming layout, but each row's K values are consumed one at a
-// time into N running sums instead of being held in registers.
+// the same streaming layout, but each row's K values are consumed into N
+// running sums instead of being held in registers.  With pair_k (K bit 0 of A
+// has stride 1 and every pair starts on a 16-byte boundary) a row's K values
+// arrive two per 16-byte load.
 template <int NK, int NN>
 __global__ void __launch_bounds__(NT) vector_long_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
-                                                         float2* __restrict__ C, const GemmDesc d) {
+                                                         float2* __restrict__ C, const GemmDesc d, int pair_k) {
   constexpr int K = 1 << NK, N = 1 << NN;
   static_assert(K * N <= 1024, "B must fit in shared memory");
   const int64_t M = int64_t(1) << d.nm;
@@ -150,14 +152,30 @@ __global__ void __launch_bounds__(NT) vector_long_kernel(const float2* __restric
     float2 acc[N];
 #pragma unroll
     for (int n = 0; n < N; ++n) acc[n] = make_float2(0.f, 0.f);
-#pragma unroll 8
-    for (int k = 0; k < K; ++k) {
-      const float2 a = __ldg(A + (int64_t)oa + kA[k]);
+    if (pair_k) {
+#pragma unroll 4
+      for (int k = 0; k < K; k += 2) {
+        const float4 x = __ldg(reinterpret_cast<const float4*>(A + (int64_t)oa + kA[k]));
+        const float2 a0 = make_float2(x.x, x.y), a1 = make_float2(x.z, x.w);
 #pragma unroll
-      for (int n = 0; n < N; ++n) {
-        const float2 b = Bs[k * N + n];
-        acc[n].x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc[n].x));
-        acc[n].y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc[n].y));
+        for (int n = 0; n < N; ++n) {
+          const float2 b0 = Bs[k * N + n], b1 = Bs[(k + 1) * N + n];
+          acc[n].x = fmaf(a0.x, b0.x, fmaf(-a0.y, b0.y, acc[n].x));
+          acc[n].y = fmaf(a0.x, b0.y, fmaf(a0.y, b0.x, acc[n].y));
+          acc[n].x = fmaf(a1.x, b1.x, fmaf(-a1.y, b1.y, acc[n].x));
+          acc[n].y = fmaf(a1.x, b1.y, fmaf(a1.y, b1.x, acc[n].y));
+        }
+      }
+    } else {
+#pragma unroll 8
+      for (int k = 0; k < K; ++k) {
+        const float2 a = __ldg(A + (int64_t)oa + kA[k]);
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+          const float2 b = Bs[k * N + n];
+          acc[n].x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc[n].x));
+          acc[n].y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc[n].y));
+        }
       }
     }
 #pragma unroll
@@ -167,11 +185,16 @@ __global__ void __launch_bounds__(NT) vector_long_kernel(const float2* __restric
 
 template <int NK>
 cudaError_t launch_long(const float2* A, const float2* B, float2* C, const GemmDesc& d, dim3 g, cudaStream_t s) {
+  // pairs (k, k + 1), k even, are adjacent when A's K bit 0 has stride 1;
+  // every other stride of A is then even, so a pair starts on a 16-byte
+  // boundary once the base and the unit strides are even
+  const int pair_k = d.nk >= 1 && d.ak[0] == 1 && (reinterpret_cast<uintptr_t>(A) & 15) == 0 &&
+                     (d.a_lo & 1) == 0 && (d.a_hi & 1) == 0;
   switch (d.nn) {
-    case 0: vector_long_kernel<NK, 0><<<g, NT, 0, s>>>(A, B, C, d); break;
-    case 1: vector_long_kernel<NK, 1><<<g, NT, 0, s>>>(A, B, C, d); break;
-    case 2: vector_long_kernel<NK, 2><<<g, NT, 0, s>>>(A, B, C, d); break;
-    case 3: vector_long_kernel<NK, 3><<<g, NT, 0, s>>>(A, B, C, d); break;
+    case 0: vector_long_kernel<NK, 0><<<g, NT, 0, s>>>(A, B, C, d, pair_k); break;
+    case 1: vector_long_kernel<NK, 1><<<g, NT, 0, s>>>(A, B, C, d, pair_k); break;
+    case 2: vector_long_kernel<NK, 2><<<g, NT, 0, s>>>(A, B, C, d, pair_k); break;
+    case 3: vector_long_kernel<NK, 3><<<g, NT, 0, s>>>(A, B, C, d, pair_k); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -75,7 +75,7 @@ cudaError_t launch_gemm_tc(const float2* A, const float2* B, float2* C, const Ge
 // K run; element (r, k) at sum bit_i(r) row_st[i] + sum bit_l(k) k_st[l] of
 // the source tensor number z, whose base is src + (z % nlo) * lo + (z / nlo) * hi.
 // Output: per z four planes {re_hi, re_lo, im_hi, im_lo} of rows_pad x kp
-// 16-bit values (kp a multiple of 32, zero padded).
+// 16-bit values (kp = K >= 8; the GEMM's TMA copies read past a short K as zeros).
 struct SplitDesc {
   int nrow, nk;
   int rows_pad, kp;
@@ -133,7 +133,7 @@ cudaError_t split_operand(const float2* src, const GemmDesc& d, bool which_b, bo
                           unsigned* maxbits, int* e_out, float* m_out, uint16_t* scratch, PlaneOperand& out,
                           cudaStream_t s);
 // Plane operand of a tensor a producer epilogue already wrote as np planes
-// (layout [rows][K], K >= 32); false when the step's view does not match.
+// (layout [rows][K], K >= 8); false when the step's view does not match.
 bool planes_in_place(const float2* base, const GemmDesc& d, bool which_b, int np, PlaneOperand& out);
 // Split both operands of d into `scratch` (>= tc2_scratch_elems(d) 16-bit
 // values) and run the TMA GEMM.
