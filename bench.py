@@ -403,6 +403,11 @@ def run_ours(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+    # the workload's plan holds its arenas (most of the free HBM): release it
+    # before the serving run sizes its budget
+    del p
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_serve:
         line["serving"] = serve_summary(args)
     if rank == 0:
@@ -581,7 +586,7 @@ def run_stream(T, srv, reqs, gaps=None, rate=None, keep=()):
             while time.time() < target:
                 time.sleep(0.0002)
         tickets.append(srv.submit(**r))
-    lat, amps, refused, flops, kept, fractions = [], 0, 0, 0.0, {}, []
+    lat, amps, refused, flops, kept, fractions, failed = [], 0, 0, 0.0, {}, [], []
     for i, t in enumerate(tickets):
         try:
             o, st = srv.wait(t)
@@ -596,12 +601,15 @@ def run_stream(T, srv, reqs, gaps=None, rate=None, keep=()):
             if e.status in (3, 6):  # TN_EHBM, TN_ETOOBIG: counted, never dropped silently
                 refused += 1
             else:
-                raise
+                failed.append(str(e))
     dt = time.time() - t0
     res = {"seconds": round(dt, 3), "served": len(lat), "refused": refused,
            "amplitudes_per_s": round(amps / dt, 1), "tflops": round(flops / dt / 1e12, 3),
            "p50_ms": round(float(np.percentile(lat, 50)), 2) if lat else None,
            "p99_ms": round(float(np.percentile(lat, 99)), 2) if lat else None}
+    if failed:  # any other error is reported, with its first message
+        res["failed"] = len(failed)
+        res["first_error"] = failed[0]
     if fractions:
         lf = np.log2(fractions)
         res["partial_fidelity"] = {"requests": len(fractions), "log2_fraction_min": round(float(lf.min()), 2),

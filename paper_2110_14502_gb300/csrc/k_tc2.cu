@@ -721,6 +721,54 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
+// Staged output of the chunked kernel.  A warp's 32 x 16 sub-tile (lanes =
+// tile row bits 0..4, columns = tile column bits 0..3) covers 512 elements of
+// C; sorted by their C stride these 9 bits give each element a C-order index.
+// When the output's fastest indices interleave row and column bits (neither
+// the lanes nor a thread's columns form long contiguous runs), the warp writes
+// its values to shared memory at their C-order index and reads them back 16
+// consecutive C-order elements per lane: the first `run` sorted strides are
+// 1, 2, 4, .., so those 16 elements are one contiguous run (run >= 4) or two
+// runs of 8 (run == 3), stored with 16-byte vector stores.
+constexpr int STAGE_SLOTS = 512 + 32;  // 8-byte slots per warp; 16 bytes of padding after every 16 slots
+constexpr int EPI_STAGE_BYTES = 4 * STAGE_SLOTS * 8;
+
+struct StageMap {
+  bool on;
+  int32_t second;   // C offset of the lane's second 8-element half relative to its first
+  int lane_idx;     // this lane's bits of its elements' C-order index
+  int rank_c[4];    // C-order rank of column bits 0..3
+  int32_t rd_off;   // C offset of this lane's read-back run from the sub-tile's first element
+};
+
+__device__ __forceinline__ StageMap stage_map(const GemmDesc& d, int lane, int vb) {
+  StageMap m;
+  int32_t st[9], sst[9];
+  int rnk[9];
+  for (int b = 0; b < 5; ++b) st[b] = d.cm[b];
+  for (int b = 0; b < 4; ++b) st[5 + b] = d.cn[b];
+  for (int b = 0; b < 9; ++b) {  // the strides of C's indices are distinct powers of two
+    int r = 0;
+    for (int o = 0; o < 9; ++o) r += st[o] < st[b];
+    rnk[b] = r;
+    sst[r] = st[b];
+  }
+  int run = 0;
+  while (run < 9 && sst[run] == (1 << run)) ++run;
+  int lane_run = 0;
+  while (lane_run < 5 && d.cm[lane_run] == (1 << lane_run)) ++lane_run;
+  m.on = run >= 3 && lane_run < 5 && vb < 4 && run > lane_run && run > vb;
+  m.second = run >= 4 ? 8 : sst[3];
+  m.lane_idx = 0;
+  for (int b = 0; b < 5; ++b) m.lane_idx |= ((lane >> b) & 1) << rnk[b];
+  for (int b = 0; b < 4; ++b) m.rank_c[b] = rnk[5 + b];
+  m.rd_off = 0;
+  for (int k = 4; k < 9; ++k) m.rd_off += ((lane >> (k - 4)) & 1) * sst[k];
+  return m;
+}
+
+__device__ __forceinline__ int stage_slot(int idx) { return idx + ((idx >> 4) << 1); }
+
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
@@ -925,6 +973,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int q = warp & 3;
     const int tq = tid - 128;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    const StageMap sm = stage_map(d, lane, vec_bits(d));
+    float2* const slots = reinterpret_cast<float2*>(smem + NS * CF::STAGE) + q * STAGE_SLOTS;
     int64_t t = 0;
     uint32_t seen[2] = {0u, 0u};
     for (int64_t it = first; it < items; it += stride, ++t) {
@@ -1033,7 +1083,60 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             split16<BF16>(vr[jj], h[0][jj], h[1][jj]);
             split16<BF16>(vi[jj], h[2][jj], h[3][jj]);
           }
-          store_planes<NP>(Pl, plane, ro, &colC[c0], vb, h);
+          if (sm.on) {
+            // planes of one element packed in one 8-byte slot, in C order
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              int idx = sm.lane_idx;
+#pragma unroll
+              for (int b = 0; b < 4; ++b) idx |= ((jj >> b) & 1) << sm.rank_c[b];
+              reinterpret_cast<uint2*>(slots)[stage_slot(idx)] =
+                  make_uint2((uint32_t)h[0][jj] | ((uint32_t)h[1][jj] << 16), (uint32_t)h[2][jj] | ((uint32_t)h[3][jj] << 16));
+            }
+            __syncwarp();
+            uint2 v[16];
+#pragma unroll
+            for (int t = 0; t < 16; t += 2) {
+              const uint4 x = reinterpret_cast<const uint4*>(slots + 18 * lane)[t >> 1];
+              v[t] = make_uint2(x.x, x.y);
+              v[t + 1] = make_uint2(x.z, x.w);
+            }
+            __syncwarp();
+            const int64_t o0 = (int64_t)__shfl_sync(0xffffffffu, ro, 0) + colC[c0] + sm.rd_off;
+#pragma unroll
+            for (int pl = 0; pl < NP; ++pl) {
+              auto half = [&](int t0) {
+                auto g = [&](int t) { return (pl & 1) ? (pl < 2 ? v[t].x >> 16 : v[t].y >> 16) : (pl < 2 ? v[t].x : v[t].y) & 0xffffu; };
+                return make_uint4(g(t0) | (g(t0 + 1) << 16), g(t0 + 2) | (g(t0 + 3) << 16), g(t0 + 4) | (g(t0 + 5) << 16),
+                                  g(t0 + 6) | (g(t0 + 7) << 16));
+              };
+              *reinterpret_cast<uint4*>(Pl + pl * plane + o0) = half(0);
+              *reinterpret_cast<uint4*>(Pl + pl * plane + o0 + sm.second) = half(8);
+            }
+          } else {
+            store_planes<NP>(Pl, plane, ro, &colC[c0], vb, h);
+          }
+        } else if (sm.on) {
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            int idx = sm.lane_idx;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) idx |= ((jj >> b) & 1) << sm.rank_c[b];
+            slots[stage_slot(idx)] = make_float2(vr[jj], vi[jj]);
+          }
+          __syncwarp();
+          float4 v[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) v[t] = reinterpret_cast<const float4*>(slots + 18 * lane)[t];
+          __syncwarp();
+          const int64_t o0 = (int64_t)__shfl_sync(0xffffffffu, ro, 0) + colC[c0] + sm.rd_off;
+          float4* c0p = reinterpret_cast<float4*>(C + o0);
+          float4* c1p = reinterpret_cast<float4*>(C + o0 + sm.second);
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            c0p[t] = v[t];
+            c1p[t] = v[4 + t];
+          }
         } else {
           store_c64(C, ro, &colC[c0], vb, vr, vi);
         }
@@ -1152,7 +1255,7 @@ cudaError_t launch_chunked(const CUtensorMap& ma, const CUtensorMap& mb, float2*
   static int sms = 0;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(gemm_tma_chunked<TN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg2<TN, 4>::SMEM);
+                                         Cfg2<TN, 4>::SMEM + EPI_STAGE_BYTES);
     if (e != cudaSuccess) return e;
     sms = sm_count();
     attr = true;
@@ -1161,8 +1264,8 @@ cudaError_t launch_chunked(const CUtensorMap& ma, const CUtensorMap& mb, float2*
   const int64_t items = (M / TM) * (fold > 1 ? 1 : N / TN) * (d.units / fold);
   const int chunk = split_chunk();
   const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
-  gemm_tma_chunked<TN, BF16><<<grid, NTHREADS, Cfg2<TN, 4>::SMEM, s>>>(ma, mb, C, d, kp, z[0], z[1], z[2], z[3],
-                                                                     c_planes, sio, chunk, fold, err);
+  gemm_tma_chunked<TN, BF16><<<grid, NTHREADS, Cfg2<TN, 4>::SMEM + EPI_STAGE_BYTES, s>>>(
+      ma, mb, C, d, kp, z[0], z[1], z[2], z[3], c_planes, sio, chunk, fold, err);
   return cudaGetLastError();
 }
 

@@ -196,10 +196,16 @@ tn_status plan_request(Server& S, Request& R) {
   R.k = (int)P.net.open_qubits.size();
   R.words = std::max(1, (P.net.n + 63) / 64);
   const int64_t gb = std::min<int64_t>(std::max<int64_t>(R.params.nb, 1), 256);
-  const int64_t arena = 8 * R.q * (P.slice_arena_elems + gb * P.unit_arena_elems);
-  // arenas + operand planes (bounded by the arenas) + leaves, invariants, I/O
-  R.footprint = arena + arena / 2 + 8 * (P.invariant_elems + P.leaf_store_elems) +
-                16 * (R.params.nb << R.k) + (int64_t(32) << 20);
+  // arenas + operand planes (bounded by the arenas) of one quantum, leaves,
+  // invariants, I/O; a request whose quantum would not fit in a quarter of
+  // the budget runs smaller quanta (down to one slice), so that several
+  // requests still fit side by side
+  const int64_t per_slice = 12 * (P.slice_arena_elems + gb * P.unit_arena_elems);
+  const int64_t fixed = 8 * (P.invariant_elems + P.leaf_store_elems) + 16 * (R.params.nb << R.k) + (int64_t(32) << 20);
+  const int64_t share = S.budget / 4 - fixed;
+  if (share > per_slice) R.q = std::min<int64_t>(R.q, share / per_slice);
+  else R.q = 1;
+  R.footprint = per_slice * R.q + fixed;
   return TN_OK;
 }
 

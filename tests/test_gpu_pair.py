@@ -231,3 +231,30 @@ def test_rank_30_operand_sampled_outputs():
         assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref), (algo, np.linalg.norm(got - ref) / np.linalg.norm(ref))
     del dA, dB, dC
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("nm,nn,nk", [(9, 7, 6), (12, 8, 9), (14, 7, 5)])
+@pytest.mark.parametrize("precision", ["split_bf16", "split_fp16"])
+def test_output_layout_interleaving_rows_and_columns(nm, nn, nk, precision):
+    """An output whose fastest indices alternate between the GEMM's row and
+    column indices (stride 1 a row index, strides 2, 4, 8 column indices):
+    the chunked kernel stages each warp's sub-tile in shared memory in the
+    output's own order and stores contiguous runs.  Against FP64 einsum."""
+    T = tnlib()
+    import torch
+    M, N, K = list(range(nm)), list(range(nm, nm + nn)), list(range(nm + nn, nm + nn + nk))
+    la, lb = M + K, N + K                      # row bit 0 = M[-1], column bit j = N[-1 - j]
+    fast = [N[-3], N[-2], N[-1], M[-1]]        # C's four fastest indices, slowest of them first
+    lc = [x for x in M + N if x not in fast] + fast
+    A = I.random_tensor(len(la), 61).astype(np.complex64)
+    B = I.random_tensor(len(lb), 62).astype(np.complex64)
+    sub = lambda ls: "".join(LETTERS[x] for x in ls)
+    ref = np.einsum(f"{sub(la)},{sub(lb)}->{sub(lc)}", A.astype(np.complex128).reshape((2,) * len(la)),
+                    B.astype(np.complex128).reshape((2,) * len(lb))).reshape(-1)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.full((1 << len(lc),), float("nan"), dtype=torch.complex64, device="cuda")
+    T.contract_pair(dA, la, dB, lb, dC, lc, precision=precision, algo="fused_tc")
+    torch.cuda.synchronize()
+    got = dC.cpu().numpy().astype(np.complex128)
+    assert np.isfinite(got).all()
+    assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
