@@ -407,6 +407,10 @@ typedef struct {
                                     request's first slice quantum was reached on its stream */
   double gpu_end_ms;             /* device time at which its last quantum had finished */
   int64_t quanta;                /* slice quanta it was served in (one per scheduler turn) */
+  int64_t batched_requests;      /* requests served by the same contraction (1 = alone): requests for the
+                                    same circuit, open qubits, precision and slices that wait for
+                                    admission together are merged, their bitstrings units of the same
+                                    launches (at most 256 bitstrings in all) */
 } tn_request_stats;
 
 /* Creates a server on the current CUDA device with planner threads and a

@@ -84,7 +84,7 @@ class RequestStats(C.Structure):
                 ("flops", C.c_double), ("slices", C.c_int64), ("status", C.c_int32), ("num_open", C.c_int32),
                 ("nb", C.c_int64), ("plan_hash", C.c_uint64), ("planned_here", C.c_int32), ("stem_reused", C.c_int32),
                 ("slice_fraction", C.c_double), ("gpu_begin_ms", C.c_double), ("gpu_end_ms", C.c_double),
-                ("quanta", C.c_int64)]
+                ("quanta", C.c_int64), ("batched_requests", C.c_int64)]
 
 
 class PrecisionReport(C.Structure):

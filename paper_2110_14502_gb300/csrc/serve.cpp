@@ -13,7 +13,10 @@
 // request on that request's own CUDA stream, so the requests' work overlaps on
 // the device.  A request whose slices are all queued gets its amplitudes copied
 // back; when that copy has completed it is done, its slot and budget are freed
-// and the next requests are admitted.  The FP64 sum of a request runs in slice
+// and the next requests are admitted.  Requests for the same circuit, open
+// qubits, precision and slice range that wait for admission together are
+// served as one contraction: their bitstrings become units of the same
+// launches, and each gets its own rows of the result.  The FP64 sum of a request runs in slice
 // order whatever else is in flight, so a result is bit-identical alone and in
 // the mix.  Requests whose plan exceeds the cost cap fail with TN_ETOOBIG, and
 // ones that could never fit the budget with TN_EHBM; neither is dropped silently.
@@ -42,6 +45,17 @@ using Clock = std::chrono::steady_clock;
 
 enum ReqState { RS_PENDING, RS_READY, RS_ACTIVE, RS_FINISHING, RS_DONE };
 
+struct PlanKey {
+  int rows, cols, depth, open;
+  uint64_t seed;
+  int trials, width;
+  double cap;
+  bool operator<(const PlanKey& o) const {
+    return std::tie(rows, cols, depth, open, seed, trials, width, cap) <
+           std::tie(o.rows, o.cols, o.depth, o.open, o.seed, o.trials, o.width, o.cap);
+  }
+};
+
 struct Request {
   int64_t ticket = 0;
   tn_request params{};
@@ -67,24 +81,23 @@ struct Request {
   double gpu_begin_ms = 0, gpu_end_ms = 0;
   Clock::time_point t_submit, t_admit, t_done;
   bool planned_here = false;
+  PlanKey key{};
+  int64_t nb_own = 0;  // this request's bitstrings (the first rows of the contraction it leads)
+  // requests served in this one's contraction (their bitstrings follow its own)
+  std::vector<std::shared_ptr<Request>> members;
+  int64_t batched = 1;  // requests in the contraction that served this one
+  bool member = false;  // served in another request's contraction
 };
 
-struct PlanKey {
-  int rows, cols, depth, open;
-  uint64_t seed;
-  int trials, width;
-  double cap;
-  bool operator<(const PlanKey& o) const {
-    return std::tie(rows, cols, depth, open, seed, trials, width, cap) <
-           std::tie(o.rows, o.cols, o.depth, o.open, o.seed, o.trials, o.width, o.cap);
-  }
-};
+
 
 // Plans are pure functions of the circuit and the planning options, so one
 // cache serves every server of the process (host memory only: copies of a
 // cached plan own their device state).  It holds the kPlanCacheSize most
 // recently used plans.
 constexpr size_t kPlanCacheSize = 256;
+// bitstrings of requests merged into one contraction (one launch group)
+constexpr int64_t kMergeBits = 256;
 struct CachedPlan {
   std::shared_ptr<tn_plan_s> plan;
   uint64_t last = 0;
@@ -117,6 +130,16 @@ struct Server {
 
 namespace {
 
+// Device memory of a request (nb = params.nb bitstrings) running quanta of q
+// slices: arenas and operand planes (bounded by half the arenas) of one
+// quantum, leaves, invariants, I/O.
+int64_t footprint(const Request& R, int64_t q) {
+  const Plan& P = R.plan->plan;
+  const int64_t gb = std::min<int64_t>(std::max<int64_t>(R.params.nb, 1), 256);
+  return 12 * q * (P.slice_arena_elems + gb * P.unit_arena_elems) + 8 * (P.invariant_elems + P.leaf_store_elems) +
+         16 * (R.params.nb << R.k) + (int64_t(32) << 20);
+}
+
 tn_status plan_request(Server& S, Request& R) {
   const tn_request& p = R.params;
   // the cost cap bounds the work served: a request of fidelity f runs a
@@ -127,6 +150,7 @@ tn_status plan_request(Server& S, Request& R) {
   const bool fit = S.opts.over_cap_policy == 1 && !partial;
   const double cap = fit ? 1000.0 : S.opts.max_log2_cmac + (partial ? -std::log2(f) : 0.0);
   PlanKey key{p.rows, p.cols, p.depth, p.num_open, p.seed, S.opts.plan_trials, S.opts.max_log2_intermediate, cap};
+  R.key = key;
   std::shared_ptr<tn_plan_s> cached;
   {
     std::lock_guard<std::mutex> g(g_plan_mu);
@@ -195,17 +219,14 @@ tn_status plan_request(Server& S, Request& R) {
   R.q = std::min<int64_t>(R.ns, std::max(1, S.opts.slices_per_quantum));
   R.k = (int)P.net.open_qubits.size();
   R.words = std::max(1, (P.net.n + 63) / 64);
-  const int64_t gb = std::min<int64_t>(std::max<int64_t>(R.params.nb, 1), 256);
-  // arenas + operand planes (bounded by the arenas) of one quantum, leaves,
-  // invariants, I/O; a request whose quantum would not fit in a quarter of
-  // the budget runs smaller quanta (down to one slice), so that several
-  // requests still fit side by side
-  const int64_t per_slice = 12 * (P.slice_arena_elems + gb * P.unit_arena_elems);
-  const int64_t fixed = 8 * (P.invariant_elems + P.leaf_store_elems) + 16 * (R.params.nb << R.k) + (int64_t(32) << 20);
-  const int64_t share = S.budget / 4 - fixed;
+  // a request whose quantum would not fit in a quarter of the budget runs
+  // smaller quanta (down to one slice), so that several requests still fit
+  // side by side
+  const int64_t per_slice = footprint(R, 1) - footprint(R, 0);
+  const int64_t share = S.budget / 4 - footprint(R, 0);
   if (share > per_slice) R.q = std::min<int64_t>(R.q, share / per_slice);
   else R.q = 1;
-  R.footprint = per_slice * R.q + fixed;
+  R.footprint = footprint(R, R.q);
   return TN_OK;
 }
 
@@ -314,6 +335,40 @@ tn_status step_request(Request& R) {
   return TN_OK;
 }
 
+// A contraction that served several requests is done: each member gets its
+// rows of the result (after the leader's own), the leader's timings and
+// status.  Called with the server's mutex held.
+void finish_members(Request& R) {
+  int64_t row = R.nb_own;
+  const int64_t per = int64_t(1) << R.k;
+  R.batched = 1 + (int64_t)R.members.size();
+  for (auto& X : R.members) {
+    X->status = R.status;
+    X->error = R.error;
+    X->t_admit = R.t_admit;
+    X->t_done = R.t_done;
+    X->gpu_begin_ms = R.gpu_begin_ms;
+    X->gpu_end_ms = R.gpu_end_ms;
+    X->nquanta = R.nquanta;
+    X->k = R.k;
+    X->batched = R.batched;
+    X->member = true;
+    if (R.status == TN_OK && R.h_out) {
+      const int64_t n = X->nb_own * per;
+      if (cudaMallocHost(&X->h_out, std::max<int64_t>(n, 1) * 16) == cudaSuccess) {
+        std::memcpy(X->h_out, R.h_out + 2 * row * per, n * 16);
+      } else {
+        X->h_out = nullptr;
+        X->status = TN_ENOMEM;
+        X->error = "serving: pinned host memory for a merged request's result";
+      }
+    }
+    row += X->nb_own;
+    X->state = RS_DONE;
+  }
+  R.members.clear();
+}
+
 void scheduler_loop(Server* S) {
   cudaSetDevice(S->device);
   std::vector<char> slot_busy(S->streams.size(), 0);
@@ -330,12 +385,35 @@ void scheduler_loop(Server* S) {
         for (size_t i = 0; i < slot_busy.size(); ++i)
           if (!slot_busy[i]) { slot = (int)i; break; }
         if (slot < 0 || S->in_use + R->footprint > S->budget) break;
+        // requests of the same circuit, precision and slices waiting behind
+        // this one join its contraction while its bitstrings fit one group
+        for (auto it = S->ready.begin() + 1; it != S->ready.end();) {
+          Request& X = **it;
+          const bool same = X.key.rows == R->key.rows && X.key.cols == R->key.cols && X.key.depth == R->key.depth &&
+                            X.key.open == R->key.open && X.key.seed == R->key.seed && X.key.trials == R->key.trials &&
+                            X.key.width == R->key.width && X.key.cap == R->key.cap && X.precision == R->precision &&
+                            X.ns == R->ns;
+          if (!same || R->params.nb + X.params.nb > kMergeBits) { ++it; continue; }
+          R->params.nb += X.params.nb;
+          const int64_t fp = footprint(*R, R->q);
+          if (S->in_use + fp > S->budget) {
+            R->params.nb -= X.params.nb;
+            ++it;
+            continue;
+          }
+          R->footprint = fp;
+          R->bits.insert(R->bits.end(), X.bits.begin(), X.bits.end());
+          X.state = RS_ACTIVE;
+          R->members.push_back(*it);
+          it = S->ready.erase(it);
+        }
         tn_status st = guarded("serving: admission", [&] { return admit(*S, *R, S->streams[slot]); });
         if (st != TN_OK) {
           R->status = st;
           R->error = tn_last_error();
           R->state = RS_DONE;
           R->t_done = Clock::now();
+          finish_members(*R);
           S->ready.pop_front();
           S->cv.notify_all();
           continue;
@@ -371,6 +449,7 @@ void scheduler_loop(Server* S) {
             R->error = tn_last_error();
             R->state = RS_DONE;
             R->t_done = Clock::now();
+            finish_members(*R);
             release(*S, *R);
             slot_busy[slot_of[R.get()]] = 0;
             slot_of.erase(R.get());
@@ -388,6 +467,7 @@ void scheduler_loop(Server* S) {
         }
         R->t_done = Clock::now();
         R->state = RS_DONE;
+        finish_members(*R);
         release(*S, *R);
         slot_busy[slot_of[R.get()]] = 0;
         slot_of.erase(R.get());
@@ -484,6 +564,7 @@ extern "C" tn_status tn_submit(tn_server* h, const tn_request* req, int64_t* tic
   return guarded("tn_submit", [&]() -> tn_status {
   auto R = std::make_shared<Request>();
   R->params = *req;
+  R->nb_own = req->nb;
   R->precision = prec;
   const int words = std::max(1, (n + 63) / 64);
   R->bits.assign(req->bitstrings, req->bitstrings + req->nb * words);
@@ -527,7 +608,7 @@ extern "C" tn_status tn_wait(tn_server* h, int64_t ticket, double* out, int64_t 
     }
     S.reqs.erase(ticket);
   }
-  const int64_t nout = R->params.nb << R->k;
+  const int64_t nout = R->nb_own << R->k;
   if (stats) {
     std::memset(stats, 0, sizeof *stats);
     auto ms = [](Clock::time_point a, Clock::time_point b) {
@@ -540,11 +621,13 @@ extern "C" tn_status tn_wait(tn_server* h, int64_t ticket, double* out, int64_t 
     if (R->plan) stats->slice_fraction = (double)R->ns / std::ldexp(1.0, (int)R->plan->plan.sliced.size());
     stats->status = R->status;
     stats->num_open = R->k;
-    stats->nb = R->params.nb;
+    stats->nb = R->nb_own;
+    stats->batched_requests = R->batched;
     if (R->plan) {
       const Plan& P = R->plan->plan;
-      stats->flops = 8.0 * ((double)R->ns * P.cmac_slice_only + (double)R->params.nb * R->ns *
-                                                                     (P.cmac_per_slice - P.cmac_slice_only));
+      // the slice-only work of a merged contraction is counted with its leader
+      stats->flops = 8.0 * ((R->member ? 0.0 : (double)R->ns * P.cmac_slice_only) +
+                            (double)R->nb_own * R->ns * (P.cmac_per_slice - P.cmac_slice_only));
       stats->plan_hash = P.hash;
     }
     stats->planned_here = R->planned_here;

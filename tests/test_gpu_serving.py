@@ -261,3 +261,35 @@ def test_over_cap_requests_are_served_at_partial_fidelity_when_asked():
     assert math.log2(ns * info["cmac_per_slice"]) <= cap
     ref = p.contract_amplitudes(req["bitstrings"], slice_count=ns)
     assert np.linalg.norm(part - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def test_requests_for_one_circuit_share_a_contraction():
+    """Requests for the same circuit, open qubits and precision that wait for
+    admission together are served by one contraction (their bitstrings are
+    units of the same launches): each gets exactly what it gets alone, and
+    its statistics say how many requests shared the contraction."""
+    T = tnlib()
+    blocker = _req(4, 5, 12, 77, 2, 1)  # 256 one-slice quanta in front of the others
+    target = [_req(4, 5, 12, 21, 3, 1 + i % 2) for i in range(4)]
+    for i, r in enumerate(target):  # same circuit, different bitstrings
+        r["bitstrings"] = I.bitstrings(20, r["bitstrings"].shape[0], 500 + i)
+    srv = T.Server(max_inflight=1, slices_per_quantum=1, precision="split_bf16", plan_trials=8,
+                   max_log2_intermediate=12)
+    try:
+        tb = srv.submit(**blocker)
+        tickets = [srv.submit(**r) for r in target]
+        together = [srv.wait(t) for t in tickets]
+        srv.wait(tb)
+        alone = [srv.wait(srv.submit(**r)) for r in target]
+    finally:
+        srv.close()
+    assert max(st["batched_requests"] for _, st in together) >= 2, [st["batched_requests"] for _, st in together]
+    assert all(st["batched_requests"] == 1 for _, st in alone)
+    n = 20
+    gates = OC.random_circuit(4, 5, 12, 21)
+    psi = SV.simulate(gates, n)
+    for r, (o, st), (a, _) in zip(target, together, alone):
+        assert st["status"] == 0 and st["nb"] == r["bitstrings"].shape[0]
+        assert np.array_equal(o, a)
+        ref = SV.amplitudes(psi, n, [I.bits_of(w, n) for w in r["bitstrings"]], (17, 18, 19))
+        assert np.linalg.norm(o - ref) <= 1e-4 * np.linalg.norm(ref)
