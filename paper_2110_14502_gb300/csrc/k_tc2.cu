@@ -730,7 +730,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // consecutive C-order elements per lane: the first `run` sorted strides are
 // 1, 2, 4, .., so those 16 elements are one contiguous run (run >= 4) or two
 // runs of 8 (run == 3), stored with 16-byte vector stores.
-constexpr int STAGE_SLOTS = 512 + 32;  // 8-byte slots per warp; 16 bytes of padding after every 16 slots
+constexpr int STAGE_SLOTS = 512 + 64;  // 8-byte slots per warp: 512 elements, 2 padding slots after every 16
 constexpr int EPI_STAGE_BYTES = 4 * STAGE_SLOTS * 8;
 
 struct StageMap {
@@ -768,6 +768,7 @@ __device__ __forceinline__ StageMap stage_map(const GemmDesc& d, int lane, int v
 }
 
 __device__ __forceinline__ int stage_slot(int idx) { return idx + ((idx >> 4) << 1); }
+static_assert(511 + (511 >> 4) * 2 < STAGE_SLOTS, "the last element's slot lies inside the warp's slots");
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
   asm volatile(
