@@ -87,6 +87,7 @@ struct Request {
   std::vector<std::shared_ptr<Request>> members;
   int64_t batched = 1;  // requests in the contraction that served this one
   bool member = false;  // served in another request's contraction
+  int stem_reused = 0;  // a member: whether the contraction that served it reused a resident stem
 };
 
 
@@ -353,6 +354,7 @@ void finish_members(Request& R) {
     X->k = R.k;
     X->batched = R.batched;
     X->member = true;
+    X->stem_reused = R.plan && stem_reused(R.plan->plan) ? 1 : 0;
     if (R.status == TN_OK && R.h_out) {
       const int64_t n = X->nb_own * per;
       if (cudaMallocHost(&X->h_out, std::max<int64_t>(n, 1) * 16) == cudaSuccess) {
@@ -631,7 +633,7 @@ extern "C" tn_status tn_wait(tn_server* h, int64_t ticket, double* out, int64_t 
       stats->plan_hash = P.hash;
     }
     stats->planned_here = R->planned_here;
-    stats->stem_reused = R->plan && stem_reused(R->plan->plan) ? 1 : 0;
+    stats->stem_reused = R->member ? R->stem_reused : (R->plan && stem_reused(R->plan->plan) ? 1 : 0);
     stats->gpu_begin_ms = R->gpu_begin_ms;
     stats->gpu_end_ms = R->gpu_end_ms;
     stats->quanta = R->nquanta;

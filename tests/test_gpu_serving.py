@@ -68,7 +68,7 @@ def test_over_cap_and_over_budget_requests_fail_loudly():
 def test_stems_stay_resident_for_later_requests_of_a_circuit():
     """The second and later requests for a circuit reuse its resident stem
     (leaf tensors and phase-0 intermediates) instead of rebuilding it, also
-    while several of them are in flight at once; their amplitudes are
+    when they arrive together (and share a contraction); their amplitudes are
     bit-identical to those of a server that builds the stem afresh, and match
     the state vector."""
     T = tnlib()
