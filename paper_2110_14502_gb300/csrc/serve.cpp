@@ -382,7 +382,9 @@ void scheduler_loop(Server* S) {
       if (S->stop) return;
       // admission: arrival order, a free slot and room in the budget
       while (!S->ready.empty()) {
-        auto& R = S->ready.front();
+        // a copy: erasing merged requests from the deque below invalidates
+        // references into it
+        const std::shared_ptr<Request> R = S->ready.front();
         int slot = -1;
         for (size_t i = 0; i < slot_busy.size(); ++i)
           if (!slot_busy[i]) { slot = (int)i; break; }
