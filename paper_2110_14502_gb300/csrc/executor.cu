@@ -285,9 +285,33 @@ static tn_status acquire_stem(const Plan& P, int device, std::shared_ptr<Stem>& 
   st->device = device;
   st->hash = P.hash;
   st->data_hash = dh;
+  // resident stems that no plan holds are only a cache: when the device has
+  // no room for a new stem they all go, and the allocation is tried once more
+  auto evict_unused = [&] {
+    for (auto j = C.m.begin(); j != C.m.end();) {
+      if (j->second.stem.use_count() == 1) {
+        C.bytes -= j->second.stem->bytes;
+        j = C.m.erase(j);
+      } else {
+        ++j;
+      }
+    }
+  };
   tn_status r = upload_leaves(P, &st->store);
+  if (r != TN_OK) {
+    cudaGetLastError();
+    cudaFree(st->store);
+    st->store = nullptr;
+    evict_unused();
+    r = upload_leaves(P, &st->store);
+  }
   if (r != TN_OK) return r;
-  CK(dev_alloc(&st->inv, std::max<int64_t>(P.invariant_elems, 1) * sizeof(float2)));
+  const size_t inv_bytes = std::max<int64_t>(P.invariant_elems, 1) * sizeof(float2);
+  if (dev_alloc(&st->inv, inv_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    evict_unused();
+    CK(dev_alloc(&st->inv, inv_bytes));
+  }
   CK(cudaEventCreateWithFlags(&st->ready, cudaEventDisableTiming));
   st->bytes = 8 * (std::max<int64_t>(P.leaf_store_elems, 1) + std::max<int64_t>(P.invariant_elems, 1));
   ++C.misses;

@@ -726,22 +726,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // C; sorted by their C stride these 9 bits give each element a C-order index.
 // When the output's fastest indices interleave row and column bits (neither
 // the lanes nor a thread's columns form long contiguous runs), the warp writes
-// its values to shared memory at their C-order index and reads them back 16
-// consecutive C-order elements per lane: the first `run` sorted strides are
-// 1, 2, 4, .., so those 16 elements are one contiguous run (run >= 4) or two
-// runs of 8 (run == 3), stored with 16-byte vector stores.
+// its values to shared memory at their C-order index and reads them back in
+// C order, consecutive lanes taking consecutive 16-byte pieces (2 complex64
+// values, or 8 values of one 16-bit plane): the first `run` sorted strides
+// are 1, 2, 4, .., so each store instruction writes runs of 2^run values.
+// For 16-bit plane output the same staging also serves layouts whose
+// contiguous run lies along the lanes (rows fastest), where each thread would
+// otherwise store its values two bytes at a time.
 constexpr int STAGE_SLOTS = 512 + 64;  // 8-byte slots per warp: 512 elements, 2 padding slots after every 16
 constexpr int EPI_STAGE_BYTES = 4 * STAGE_SLOTS * 8;
 
 struct StageMap {
   bool on;
-  int32_t second;   // C offset of the lane's second 8-element half relative to its first
-  int lane_idx;     // this lane's bits of its elements' C-order index
-  int rank_c[4];    // C-order rank of column bits 0..3
-  int32_t rd_off;   // C offset of this lane's read-back run from the sub-tile's first element
+  int lane_idx;        // this lane's bits of its elements' C-order index
+  int rank_c[4];       // C-order rank of column bits 0..3
+  int32_t off_c64;     // C offset of this lane's pair (C-order index 2 lane) in read-back step 0
+  int32_t step_c64[3]; // C offset added by bits 0..2 of the complex64 read-back step
+  int32_t off_pl;      // C offset of this lane's 8 values (C-order index 8 lane) in read-back step 0
+  int32_t step_pl;     // C offset added by the second plane read-back step
 };
 
-__device__ __forceinline__ StageMap stage_map(const GemmDesc& d, int lane, int vb) {
+__device__ __forceinline__ StageMap stage_map(const GemmDesc& d, int lane, int vb, bool planes) {
   StageMap m;
   int32_t st[9], sst[9];
   int rnk[9];
@@ -757,13 +762,24 @@ __device__ __forceinline__ StageMap stage_map(const GemmDesc& d, int lane, int v
   while (run < 9 && sst[run] == (1 << run)) ++run;
   int lane_run = 0;
   while (lane_run < 5 && d.cm[lane_run] == (1 << lane_run)) ++lane_run;
-  m.on = run >= 3 && lane_run < 5 && vb < 4 && run > lane_run && run > vb;
-  m.second = run >= 4 ? 8 : sst[3];
+  // complex64: staged only where it lengthens the contiguous runs; planes
+  // (2-byte values): also where it merely turns 2-, 4- or 8-byte stores into
+  // 16-byte ones (a thread's columns give fewer than 8 contiguous values)
+  m.on = planes ? run >= 3 && vb < 3 : run >= 3 && lane_run < 5 && vb < 4 && run > lane_run && run > vb;
   m.lane_idx = 0;
   for (int b = 0; b < 5; ++b) m.lane_idx |= ((lane >> b) & 1) << rnk[b];
   for (int b = 0; b < 4; ++b) m.rank_c[b] = rnk[5 + b];
-  m.rd_off = 0;
-  for (int k = 4; k < 9; ++k) m.rd_off += ((lane >> (k - 4)) & 1) * sst[k];
+  // read-back step t, lane l: complex64 pair l + 32 t (C-order index bits
+  // 1..5 from the lane, 6..8 from t); plane group of 8 values l + 32 t (bits
+  // 3..7 from the lane, bit 8 from t)
+  m.off_c64 = 0;
+  m.off_pl = 0;
+  for (int b = 0; b < 5; ++b) {
+    m.off_c64 += ((lane >> b) & 1) * sst[1 + b];
+    m.off_pl += ((lane >> b) & 1) * sst[3 + b];
+  }
+  for (int b = 0; b < 3; ++b) m.step_c64[b] = sst[6 + b];
+  m.step_pl = sst[8];
   return m;
 }
 
@@ -974,7 +990,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int q = warp & 3;
     const int tq = tid - 128;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    const StageMap sm = stage_map(d, lane, vec_bits(d));
+    const StageMap sm = stage_map(d, lane, vec_bits(d), c_planes != 0);
     float2* const slots = reinterpret_cast<float2*>(smem + NS * CF::STAGE) + q * STAGE_SLOTS;
     int64_t t = 0;
     uint32_t seen[2] = {0u, 0u};
@@ -1095,25 +1111,30 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                   make_uint2((uint32_t)h[0][jj] | ((uint32_t)h[1][jj] << 16), (uint32_t)h[2][jj] | ((uint32_t)h[3][jj] << 16));
             }
             __syncwarp();
-            uint2 v[16];
+            const int64_t ob = (int64_t)__shfl_sync(0xffffffffu, ro, 0) + colC[c0] + sm.off_pl;
 #pragma unroll
-            for (int t = 0; t < 16; t += 2) {
-              const uint4 x = reinterpret_cast<const uint4*>(slots + 18 * lane)[t >> 1];
-              v[t] = make_uint2(x.x, x.y);
-              v[t + 1] = make_uint2(x.z, x.w);
+            for (int t = 0; t < 2; ++t) {
+              // C-order values 8 (lane + 32 t) .. + 7, one uint2 slot (4 planes) each
+              const uint4* src = reinterpret_cast<const uint4*>(slots) + stage_slot(8 * (lane + 32 * t)) / 2;
+              uint2 v[8];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const uint4 x = src[u];
+                v[2 * u] = make_uint2(x.x, x.y);
+                v[2 * u + 1] = make_uint2(x.z, x.w);
+              }
+              const int64_t o = ob + (t ? sm.step_pl : 0);
+#pragma unroll
+              for (int pl = 0; pl < NP; ++pl) {
+                auto g = [&](int e) {
+                  const uint32_t w = pl < 2 ? v[e].x : v[e].y;
+                  return (pl & 1) ? w >> 16 : w & 0xffffu;
+                };
+                *reinterpret_cast<uint4*>(Pl + pl * plane + o) =
+                    make_uint4(g(0) | (g(1) << 16), g(2) | (g(3) << 16), g(4) | (g(5) << 16), g(6) | (g(7) << 16));
+              }
             }
             __syncwarp();
-            const int64_t o0 = (int64_t)__shfl_sync(0xffffffffu, ro, 0) + colC[c0] + sm.rd_off;
-#pragma unroll
-            for (int pl = 0; pl < NP; ++pl) {
-              auto half = [&](int t0) {
-                auto g = [&](int t) { return (pl & 1) ? (pl < 2 ? v[t].x >> 16 : v[t].y >> 16) : (pl < 2 ? v[t].x : v[t].y) & 0xffffu; };
-                return make_uint4(g(t0) | (g(t0 + 1) << 16), g(t0 + 2) | (g(t0 + 3) << 16), g(t0 + 4) | (g(t0 + 5) << 16),
-                                  g(t0 + 6) | (g(t0 + 7) << 16));
-              };
-              *reinterpret_cast<uint4*>(Pl + pl * plane + o0) = half(0);
-              *reinterpret_cast<uint4*>(Pl + pl * plane + o0 + sm.second) = half(8);
-            }
           } else {
             store_planes<NP>(Pl, plane, ro, &colC[c0], vb, h);
           }
@@ -1126,18 +1147,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             slots[stage_slot(idx)] = make_float2(vr[jj], vi[jj]);
           }
           __syncwarp();
-          float4 v[8];
+          const int64_t ob = (int64_t)__shfl_sync(0xffffffffu, ro, 0) + colC[c0] + sm.off_c64;
 #pragma unroll
-          for (int t = 0; t < 8; ++t) v[t] = reinterpret_cast<const float4*>(slots + 18 * lane)[t];
-          __syncwarp();
-          const int64_t o0 = (int64_t)__shfl_sync(0xffffffffu, ro, 0) + colC[c0] + sm.rd_off;
-          float4* c0p = reinterpret_cast<float4*>(C + o0);
-          float4* c1p = reinterpret_cast<float4*>(C + o0 + sm.second);
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            c0p[t] = v[t];
-            c1p[t] = v[4 + t];
+          for (int t = 0; t < 8; ++t) {
+            // C-order values 2 (lane + 32 t) and the next one: two adjacent slots
+            const float4 x = reinterpret_cast<const float4*>(slots)[stage_slot(2 * (lane + 32 * t)) / 2];
+            const int32_t o = ((t & 1) ? sm.step_c64[0] : 0) + ((t & 2) ? sm.step_c64[1] : 0) +
+                              ((t & 4) ? sm.step_c64[2] : 0);
+            *reinterpret_cast<float4*>(C + ob + o) = x;
           }
+          __syncwarp();
         } else {
           store_c64(C, ro, &colC[c0], vb, vr, vi);
         }

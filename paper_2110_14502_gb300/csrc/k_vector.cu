@@ -183,6 +183,157 @@ __global__ void __launch_bounds__(NT) vector_long_kernel(const float2* __restric
   }
 }
 
+// Rows whose K values are contiguous (A's K bit i has stride 2^i, K >= 8):
+// a warp copies 32 rows' next KC = min(K, 16) values into shared memory with
+// 16-byte cp.async (every load instruction reads whole 128-byte lines, where a
+// thread-per-row load touches 32 lines a few bytes at a time), double-buffered
+// per warp, and each lane then runs its own row from shared memory into N
+// running sums.  Row pitch KC + 2 complex keeps the lanes' 16-byte reads of a
+// quarter-warp on distinct banks.  A CTA of SW warps owns 1024 consecutive
+// rows (M >= 32: every warp group of 32 rows is full).
+constexpr int SW = 4;
+constexpr int SNT = SW * 32;
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <int NK, int NN>
+__global__ void __launch_bounds__(SNT) vector_staged_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
+                                                            float2* __restrict__ C, const GemmDesc d) {
+  constexpr int K = 1 << NK, N = 1 << NN;
+  constexpr int KC = K < 16 ? K : 16;    // K values per stage
+  constexpr int PITCH = KC + 2;          // complex per staged row
+  constexpr int LPR = KC / 2;            // lanes per row in a copy (16 bytes each)
+  constexpr int RPI = 32 / LPR;          // rows per copy instruction
+  constexpr int NCH = K / KC;            // stages per row group
+  static_assert(K * N <= 1024, "B must fit in shared memory");
+  const int64_t M = int64_t(1) << d.nm;
+  const int64_t ulo = blockIdx.y % d.units_lo, uhi = blockIdx.y / d.units_lo;
+  A += ulo * d.a_lo + uhi * d.a_hi;
+  B += ulo * d.b_lo + uhi * d.b_hi;
+  C += ulo * d.c_lo + uhi * d.c_hi;
+  __shared__ __align__(16) float2 Bs[K * N];
+  __shared__ __align__(16) float2 stage[SW][2][32 * PITCH];
+  __shared__ int32_t nC[N];
+  __shared__ int32_t tAlo[32], tAhi[32], tClo[32], tChi[32];
+  __shared__ int32_t baseA, baseC;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t base = (int64_t)blockIdx.x * CH;
+  for (int e = tid; e < K * N; e += SNT) {
+    const int k = e / N, n = e % N;
+    Bs[e] = B[bit_offset(k, NK, d.bk) + bit_offset(n, NN, d.bn)];
+  }
+  if (tid < N) nC[tid] = bit_offset(tid, NN, d.cn);
+  const int lb = d.nm < CH_BITS ? d.nm : CH_BITS;
+  if (tid >= 32 && tid < 64) {
+    const int x = tid - 32;
+    tAlo[x] = bit_offset(x, 5, d.am);  // lb >= 5
+    tClo[x] = bit_offset(x, 5, d.cm);
+  }
+  if (tid >= 64 && tid < 96) {
+    const int x = tid - 64, b1 = lb - 5;
+    tAhi[x] = x < (1 << b1) ? bit_offset(x, b1, d.am + 5) : 0;
+    tChi[x] = x < (1 << b1) ? bit_offset(x, b1, d.cm + 5) : 0;
+  }
+  if (tid == 96) {
+    int32_t oa = 0, oc = 0;
+    for (int i = CH_BITS; i < d.nm; ++i)
+      if ((base >> i) & 1) { oa += d.am[i]; oc += d.cm[i]; }
+    baseA = oa;
+    baseC = oc;
+  }
+  __syncthreads();
+  const int64_t rows = M - base < CH ? M - base : CH;
+  const int ngroups = (int)(rows >> 5);
+  const int nitems = ngroups > warp ? ((ngroups - 1 - warp) / SW + 1) * NCH : 0;
+  float2* st = stage[warp][0];
+  // copy of item i = (row group warp + SW (i / NCH), K chunk i % NCH) into buffer i & 1
+  auto issue = [&](int i) {
+    const int g = warp + SW * (i / NCH), c = i % NCH;
+    const float2* src = A + baseA + tAhi[g] + (int64_t)c * KC + (lane % LPR) * 2;
+    float2* dst = st + (i & 1) * 32 * PITCH + (lane % LPR) * 2;
+#pragma unroll
+    for (int q = 0; q < LPR; ++q) {
+      const int r = q * RPI + lane / LPR;
+      cp_async16(dst + r * PITCH, src + tAlo[r]);
+    }
+  };
+  float2 acc[N];
+#pragma unroll
+  for (int n = 0; n < N; ++n) acc[n] = make_float2(0.f, 0.f);
+  if (nitems > 0) issue(0);
+  cp_async_commit();
+#pragma unroll 1
+  for (int i = 0; i < nitems; ++i) {
+    if (i + 1 < nitems) issue(i + 1);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncwarp();
+    const int c = i % NCH;
+    const float2* row = st + (i & 1) * 32 * PITCH + lane * PITCH;
+#pragma unroll
+    for (int kk = 0; kk < KC; kk += 2) {
+      const float4 x = *reinterpret_cast<const float4*>(row + kk);
+      const float2 a0 = make_float2(x.x, x.y), a1 = make_float2(x.z, x.w);
+      const int k = c * KC + kk;
+#pragma unroll
+      for (int n = 0; n < N; ++n) {
+        const float2 b0 = Bs[k * N + n], b1 = Bs[(k + 1) * N + n];
+        acc[n].x = fmaf(a0.x, b0.x, fmaf(-a0.y, b0.y, acc[n].x));
+        acc[n].y = fmaf(a0.x, b0.y, fmaf(a0.y, b0.x, acc[n].y));
+        acc[n].x = fmaf(a1.x, b1.x, fmaf(-a1.y, b1.y, acc[n].x));
+        acc[n].y = fmaf(a1.x, b1.y, fmaf(a1.y, b1.x, acc[n].y));
+      }
+    }
+    __syncwarp();  // every lane is done with this buffer before it is refilled
+    if (c == NCH - 1) {
+      const int g = warp + SW * (i / NCH);
+      const int32_t oc = baseC + tChi[g] + tClo[lane];
+#pragma unroll
+      for (int n = 0; n < N; ++n) {
+        C[(int64_t)oc + nC[n]] = acc[n];
+        acc[n] = make_float2(0.f, 0.f);
+      }
+    }
+  }
+}
+
+// The staged kernel applies when A's K values of a row are contiguous, every
+// copied 16-byte piece is aligned, and M >= 32.
+bool staged_ok(const float2* A, const GemmDesc& d) {
+  if (d.nk < 3 || d.nk > 7 || d.nm < 5 || (d.nk > 4 && d.nn > 3) || d.nn > 4) return false;
+  if ((reinterpret_cast<uintptr_t>(A) & 15) != 0 || (d.a_lo & 1) != 0 || (d.a_hi & 1) != 0) return false;
+  for (int i = 0; i < d.nk; ++i)
+    if (d.ak[i] != (int32_t(1) << i)) return false;
+  for (int i = 0; i < d.nm; ++i)
+    if (d.am[i] & 1) return false;
+  return true;
+}
+
+template <int NK>
+cudaError_t launch_staged(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s) {
+  const dim3 g((unsigned)(((int64_t(1) << d.nm) + CH - 1) / CH), (unsigned)d.units);
+  switch (d.nn) {
+    case 0: vector_staged_kernel<NK, 0><<<g, SNT, 0, s>>>(A, B, C, d); break;
+    case 1: vector_staged_kernel<NK, 1><<<g, SNT, 0, s>>>(A, B, C, d); break;
+    case 2: vector_staged_kernel<NK, 2><<<g, SNT, 0, s>>>(A, B, C, d); break;
+    case 3: vector_staged_kernel<NK, 3><<<g, SNT, 0, s>>>(A, B, C, d); break;
+    case 4:
+      if constexpr (NK <= 4) {
+        vector_staged_kernel<NK, 4><<<g, SNT, 0, s>>>(A, B, C, d);
+        break;
+      }
+      return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 template <int NK>
 cudaError_t launch_long(const float2* A, const float2* B, float2* C, const GemmDesc& d, dim3 g, cudaStream_t s) {
   // pairs (k, k + 1), k even, are adjacent when A's K bit 0 has stride 1;
@@ -221,6 +372,15 @@ cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const Gem
   if (!vector_shape_ok(d) || d.units > 65535) return cudaErrorInvalidValue;
   int64_t M = int64_t(1) << d.nm;
   dim3 g((unsigned)((M + CH - 1) / CH), (unsigned)d.units);
+  if (staged_ok(A, d)) {
+    switch (d.nk) {
+      case 3: return launch_staged<3>(A, B, C, d, s);
+      case 4: return launch_staged<4>(A, B, C, d, s);
+      case 5: return launch_staged<5>(A, B, C, d, s);
+      case 6: return launch_staged<6>(A, B, C, d, s);
+      default: return launch_staged<7>(A, B, C, d, s);
+    }
+  }
   if (d.nk > 4) {
     switch (d.nk) {
       case 5: return launch_long<5>(A, B, C, d, g, s);

@@ -65,6 +65,31 @@ def test_vector_kernel_matches_fp64(nm, nn, nk):
         assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref), algo
 
 
+@pytest.mark.parametrize("nm,nn,nk", [(5, 3, 5), (9, 4, 3), (11, 3, 5), (12, 4, 4), (13, 2, 6), (10, 1, 6),
+                                      (16, 3, 7), (18, 3, 5), (7, 0, 7), (6, 4, 3), (14, 0, 3)])
+def test_vector_kernel_contiguous_rows(nm, nn, nk):
+    """Planner-style layouts (the contracted indices innermost, in one order
+    in both operands): the rows of A are contiguous K runs, which the
+    streaming kernel stages through shared memory; M from one 32-row group to
+    several 1024-row CTAs, free index orders random."""
+    T = tnlib()
+    rng = np.random.default_rng(300 + 10 * nm + nk)
+    labels = list(range(nm + nn + nk))
+    M, N, K = labels[:nm], labels[nm:nm + nn], labels[nm + nn:]
+    kk = [int(x) for x in rng.permutation(K)]
+    la = [int(x) for x in rng.permutation(M)] + kk
+    lb = [int(x) for x in rng.permutation(N)] + kk
+    lc = [int(x) for x in rng.permutation(M + N)]
+    A = I.random_tensor(len(la), 61 + nm).astype(np.complex64)
+    B = I.random_tensor(len(lb), 62 + nk).astype(np.complex64)
+    sub = lambda ls: "".join(LETTERS[x] for x in ls)
+    ref = np.einsum(f"{sub(la)},{sub(lb)}->{sub(lc)}", A.astype(np.complex128).reshape((2,) * len(la)),
+                    B.astype(np.complex128).reshape((2,) * len(lb))).reshape(-1)
+    for algo in ("vector", "auto"):
+        got = _run(T, la, lb, lc, A, B, algo)
+        assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref), algo
+
+
 @pytest.mark.parametrize("nm,nn,nk", [(0, 0, 8), (4, 2, 12), (2, 4, 9), (6, 0, 10), (0, 6, 8), (3, 3, 14),
                                       (1, 2, 16)])
 def test_reduction_kernel_matches_fp64(nm, nn, nk):
