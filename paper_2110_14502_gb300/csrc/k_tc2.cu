@@ -160,6 +160,28 @@ __device__ __forceinline__ void split16(float x, uint16_t& hi, uint16_t& lo) {
   }
 }
 
+// Both parts of re and im at once: x = hi + lo, hi = rn16(x), lo = rn16(x - hi)
+// (the same roundings as split16), packed as the four planes of one element:
+// .x = re_hi | re_lo << 16, .y = im_hi | im_lo << 16.
+template <bool BF16>
+__device__ __forceinline__ uint2 split_pair(float re, float im) {
+  uint32_t hu, lu;
+  if (BF16) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(re - hf.x, im - hf.y);
+    hu = *reinterpret_cast<const uint32_t*>(&h);
+    lu = *reinterpret_cast<const uint32_t*>(&l);
+  } else {
+    const __half2 h = __floats2half2_rn(re, im);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(re - hf.x, im - hf.y);
+    hu = *reinterpret_cast<const uint32_t*>(&h);
+    lu = *reinterpret_cast<const uint32_t*>(&l);
+  }
+  return make_uint2(__byte_perm(hu, lu, 0x5410), __byte_perm(hu, lu, 0x7632));
+}
+
 template <bool BF16>
 __device__ __forceinline__ uint16_t to16(float x) {
   if (BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
@@ -227,6 +249,50 @@ __device__ __forceinline__ void store_planes(uint16_t* P, int64_t plane, int64_t
       const int64_t o = ro + col[j];
 #pragma unroll
       for (int p = 0; p < NP; ++p) P[p * plane + o] = h[p][j];
+    }
+  }
+}
+
+// The same stores from 16 packed elements (split_pair): plane 0 re_hi, 1 re_lo,
+// 2 im_hi, 3 im_lo.
+__device__ __forceinline__ uint32_t plane_pair(const uint2 (&e)[16], int p, int j) {
+  const uint32_t a = p < 2 ? e[j].x : e[j].y, b = p < 2 ? e[j + 1].x : e[j + 1].y;
+  return __byte_perm(a, b, (p & 1) ? 0x7632 : 0x5410);
+}
+__device__ __forceinline__ void store_planes4(uint16_t* P, int64_t plane, int64_t ro, const int32_t* col, int vb,
+                                              const uint2 (&e)[16]) {
+  if (vb >= 3) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int64_t o = ro + col[8 * r];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+        *reinterpret_cast<uint4*>(P + p * plane + o) = make_uint4(plane_pair(e, p, 8 * r), plane_pair(e, p, 8 * r + 2),
+                                                                  plane_pair(e, p, 8 * r + 4), plane_pair(e, p, 8 * r + 6));
+    }
+  } else if (vb == 2) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int64_t o = ro + col[4 * r];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+        *reinterpret_cast<uint2*>(P + p * plane + o) = make_uint2(plane_pair(e, p, 4 * r), plane_pair(e, p, 4 * r + 2));
+    }
+  } else if (vb == 1) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int64_t o = ro + col[2 * r];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) *reinterpret_cast<uint32_t*>(P + p * plane + o) = plane_pair(e, p, 2 * r);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int64_t o = ro + col[j];
+      P[o] = (uint16_t)(e[j].x & 0xffffu);
+      P[plane + o] = (uint16_t)(e[j].x >> 16);
+      P[2 * plane + o] = (uint16_t)(e[j].y & 0xffffu);
+      P[3 * plane + o] = (uint16_t)(e[j].y >> 16);
     }
   }
 }
@@ -838,6 +904,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ uint64_t full[NS], empty[NS], acc_full[2], acc_empty[2], mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int32_t colC[TN];
+  __shared__ int32_t col_slot[16];  // staging slot offset of a thread's column jj (same for every lane)
   __shared__ volatile int abort_flag;
   __shared__ volatile int epi_fail;
 
@@ -992,6 +1059,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const StageMap sm = stage_map(d, lane, vec_bits(d), c_planes != 0);
     float2* const slots = reinterpret_cast<float2*>(smem + NS * CF::STAGE) + q * STAGE_SLOTS;
+    // the C-order index of (lane, jj) is lane_idx | (jj's bits at their ranks);
+    // the two parts have disjoint bits, so their slots add
+    const int lane_slot = stage_slot(sm.lane_idx);
+    if (tq < 16) {
+      int idx = 0;
+      for (int b = 0; b < 4; ++b) idx |= ((tq >> b) & 1) << sm.rank_c[b];
+      col_slot[tq] = stage_slot(idx);
+    }
+    // scaling and the maximum / filter tracking only where the formats need them
+    const bool track = sio.mc != nullptr || sio.flag != nullptr;
     int64_t t = 0;
     uint32_t seen[2] = {0u, 0u};
     for (int64_t it = first; it < items; it += stride, ++t) {
@@ -1084,32 +1161,36 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tmem_ld<16>(R + (uint32_t)(TN + c0), ui);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         float vr[16], vi[16];
+        if (sc.direct && sc.f == 1.f) {
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          vr[jj] = sc(__uint_as_float(ur[jj]));
-          vi[jj] = sc(__uint_as_float(ui[jj]));
+          for (int jj = 0; jj < 16; ++jj) {
+            vr[jj] = __uint_as_float(ur[jj]);
+            vi[jj] = __uint_as_float(ui[jj]);
+          }
+        } else {
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            vr[jj] = sc(__uint_as_float(ur[jj]));
+            vi[jj] = sc(__uint_as_float(ui[jj]));
+          }
         }
         if (c_planes) {
           uint16_t* Pl = reinterpret_cast<uint16_t*>(C);
           const int64_t plane = int64_t(1) << (d.nm + d.nn);
-          uint16_t h[NP][16];
+          if (track) {
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            vmax = fmaxf(vmax, fmaxf(fabsf(vr[jj]), fabsf(vi[jj])));
-            bad |= !isfinite(vr[jj]) || !isfinite(vi[jj]);
-            split16<BF16>(vr[jj], h[0][jj], h[1][jj]);
-            split16<BF16>(vi[jj], h[2][jj], h[3][jj]);
+            for (int jj = 0; jj < 16; ++jj) {
+              vmax = fmaxf(vmax, fmaxf(fabsf(vr[jj]), fabsf(vi[jj])));
+              bad |= !isfinite(vr[jj]) || !isfinite(vi[jj]);
+            }
           }
+          uint2 e[16];
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) e[jj] = split_pair<BF16>(vr[jj], vi[jj]);
           if (sm.on) {
             // planes of one element packed in one 8-byte slot, in C order
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              int idx = sm.lane_idx;
-#pragma unroll
-              for (int b = 0; b < 4; ++b) idx |= ((jj >> b) & 1) << sm.rank_c[b];
-              reinterpret_cast<uint2*>(slots)[stage_slot(idx)] =
-                  make_uint2((uint32_t)h[0][jj] | ((uint32_t)h[1][jj] << 16), (uint32_t)h[2][jj] | ((uint32_t)h[3][jj] << 16));
-            }
+            for (int jj = 0; jj < 16; ++jj) reinterpret_cast<uint2*>(slots)[lane_slot + col_slot[jj]] = e[jj];
             __syncwarp();
             const int64_t ob = (int64_t)__shfl_sync(0xffffffffu, ro, 0) + colC[c0] + sm.off_pl;
 #pragma unroll
@@ -1126,26 +1207,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               const int64_t o = ob + (t ? sm.step_pl : 0);
 #pragma unroll
               for (int pl = 0; pl < NP; ++pl) {
-                auto g = [&](int e) {
-                  const uint32_t w = pl < 2 ? v[e].x : v[e].y;
-                  return (pl & 1) ? w >> 16 : w & 0xffffu;
+                auto pp = [&](int e0) {
+                  const uint32_t a = pl < 2 ? v[e0].x : v[e0].y, b = pl < 2 ? v[e0 + 1].x : v[e0 + 1].y;
+                  return __byte_perm(a, b, (pl & 1) ? 0x7632 : 0x5410);
                 };
-                *reinterpret_cast<uint4*>(Pl + pl * plane + o) =
-                    make_uint4(g(0) | (g(1) << 16), g(2) | (g(3) << 16), g(4) | (g(5) << 16), g(6) | (g(7) << 16));
+                *reinterpret_cast<uint4*>(Pl + pl * plane + o) = make_uint4(pp(0), pp(2), pp(4), pp(6));
               }
             }
             __syncwarp();
           } else {
-            store_planes<NP>(Pl, plane, ro, &colC[c0], vb, h);
+            store_planes4(Pl, plane, ro, &colC[c0], vb, e);
           }
         } else if (sm.on) {
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            int idx = sm.lane_idx;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) idx |= ((jj >> b) & 1) << sm.rank_c[b];
-            slots[stage_slot(idx)] = make_float2(vr[jj], vi[jj]);
-          }
+          for (int jj = 0; jj < 16; ++jj) slots[lane_slot + col_slot[jj]] = make_float2(vr[jj], vi[jj]);
           __syncwarp();
           const int64_t ob = (int64_t)__shfl_sync(0xffffffffu, ro, 0) + colC[c0] + sm.off_c64;
 #pragma unroll

@@ -132,12 +132,13 @@ struct Server {
 namespace {
 
 // Device memory of a request (nb = params.nb bitstrings) running quanta of q
-// slices: arenas and operand planes (bounded by half the arenas) of one
-// quantum, leaves, invariants, I/O.
+// slices: arenas (8 bytes per complex64 element) and the operand planes of a
+// split pass (at most 8 bytes per element of the step's two operands, which
+// the arena holds side by side) of one quantum, leaves, invariants, I/O.
 int64_t footprint(const Request& R, int64_t q) {
   const Plan& P = R.plan->plan;
   const int64_t gb = std::min<int64_t>(std::max<int64_t>(R.params.nb, 1), 256);
-  return 12 * q * (P.slice_arena_elems + gb * P.unit_arena_elems) + 8 * (P.invariant_elems + P.leaf_store_elems) +
+  return 16 * q * (P.slice_arena_elems + gb * P.unit_arena_elems) + 8 * (P.invariant_elems + P.leaf_store_elems) +
          16 * (R.params.nb << R.k) + (int64_t(32) << 20);
 }
 
