@@ -904,7 +904,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ uint64_t full[NS], empty[NS], acc_full[2], acc_empty[2], mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int32_t colC[TN];
-  __shared__ int32_t col_slot[16];  // staging slot offset of a thread's column jj (same for every lane)
   __shared__ volatile int abort_flag;
   __shared__ volatile int epi_fail;
 
@@ -920,9 +919,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int nkt = (kp + TKC - 1) / TKC;  // a short K (8, 16) is one stage; TMA zero-fills past K
   const int nch = (nkt + chunk - 1) / chunk;
   const int GM = d.group_m > 0 ? d.group_m : GROUP_M_DEFAULT;
+  const bool items32 = items < (int64_t(1) << 31);
   auto decode = [&](int64_t item, int& unit, int& m0, int& n0) {
-    unit = (int)(item / tiles);
-    const int t = (int)(item % tiles);
+    int t;
+    if (items32) {  // 32-bit division: a 64-bit one is a long dependent sequence
+      unit = (int)((uint32_t)item / (uint32_t)tiles);
+      t = (int)((uint32_t)item - (uint32_t)unit * (uint32_t)tiles);
+    } else {
+      unit = (int)(item / tiles);
+      t = (int)(item % tiles);
+    }
     const int per_group = GM * ntn;
     const int g = t / per_group, r = t % per_group;
     const int gm = min(GM, ntm - g * GM);
@@ -1062,11 +1068,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // the C-order index of (lane, jj) is lane_idx | (jj's bits at their ranks);
     // the two parts have disjoint bits, so their slots add
     const int lane_slot = stage_slot(sm.lane_idx);
-    if (tq < 16) {
-      int idx = 0;
-      for (int b = 0; b < 4; ++b) idx |= ((tq >> b) & 1) << sm.rank_c[b];
-      col_slot[tq] = stage_slot(idx);
-    }
+    int cs[4];  // slot offset of column bit b alone
+    for (int b = 0; b < 4; ++b) cs[b] = stage_slot(1 << sm.rank_c[b]);
+    auto col_slot = [&](int jj) {
+      return ((jj & 1) ? cs[0] : 0) + ((jj & 2) ? cs[1] : 0) + ((jj & 4) ? cs[2] : 0) + ((jj & 8) ? cs[3] : 0);
+    };
+    // C offset of the thread's row: its bits 0..6 (q * 32 + lane) once, the
+    // tile's bits 7.. per item as a warp sum (lane b holds row bit b's stride)
+    const int32_t ro_lo = bit_offset(q * 32 + lane, min(7, d.nm), d.cm);
+    const int32_t my_cm = lane >= 7 && lane < d.nm ? d.cm[lane] : 0;
+    int last_n0 = -1;
     // scaling and the maximum / filter tracking only where the formats need them
     const bool track = sio.mc != nullptr || sio.flag != nullptr;
     int64_t t = 0;
@@ -1075,8 +1086,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int unit, m0, n0;
       decode(it, unit, m0, n0);
       const int ulo = unit % d.units_lo, uhi = (unit / d.units_lo) * fold;
-      for (int jj = tq; jj < TN; jj += 128) colC[jj] = bit_offset(fold > 1 ? (jj & (nsub - 1)) : n0 + jj, d.nn, d.cn);
-      const int32_t ro = bit_offset(m0 + q * 32 + lane, d.nm, d.cm);
+      // the column offsets change with the tile's first column only (the
+      // barriers around each item order these writes against every read)
+      if (n0 != last_n0) {
+        for (int jj = tq; jj < TN; jj += 128) colC[jj] = bit_offset(fold > 1 ? (jj & (nsub - 1)) : n0 + jj, d.nn, d.cn);
+        last_n0 = n0;
+      }
+      const int32_t ro = ro_lo + (int32_t)__reduce_add_sync(0xffffffffu, (uint32_t)(((m0 >> lane) & 1) ? my_cm : 0));
       float2* Cu = C0 + (int64_t)ulo * d.c_lo + (int64_t)uhi * d.c_hi;
       // Scaled formats: exponents of the operands of the tile's f-th unit (a
       // folded tile holds `fold` hi units side by side, f = column / 2^nn,
@@ -1190,7 +1206,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (sm.on) {
             // planes of one element packed in one 8-byte slot, in C order
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) reinterpret_cast<uint2*>(slots)[lane_slot + col_slot[jj]] = e[jj];
+            for (int jj = 0; jj < 16; ++jj) reinterpret_cast<uint2*>(slots)[lane_slot + col_slot(jj)] = e[jj];
             __syncwarp();
             const int64_t ob = (int64_t)__shfl_sync(0xffffffffu, ro, 0) + colC[c0] + sm.off_pl;
 #pragma unroll
@@ -1220,7 +1236,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         } else if (sm.on) {
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) slots[lane_slot + col_slot[jj]] = make_float2(vr[jj], vi[jj]);
+          for (int jj = 0; jj < 16; ++jj) slots[lane_slot + col_slot(jj)] = make_float2(vr[jj], vi[jj]);
           __syncwarp();
           const int64_t ob = (int64_t)__shfl_sync(0xffffffffu, ro, 0) + colC[c0] + sm.off_c64;
 #pragma unroll

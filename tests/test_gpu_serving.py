@@ -293,3 +293,31 @@ def test_requests_for_one_circuit_share_a_contraction():
         assert np.array_equal(o, a)
         ref = SV.amplitudes(psi, n, [I.bits_of(w, n) for w in r["bitstrings"]], (17, 18, 19))
         assert np.linalg.norm(o - ref) <= 1e-4 * np.linalg.norm(ref)
+
+
+def test_a_stem_that_does_not_fit_evicts_the_cached_ones(monkeypatch):
+    """A new circuit's stem whose device allocation fails (host-side fault
+    injection: TN_FAULT_ALLOC=1 fails the next allocation) evicts the cached
+    stems that no request holds and is allocated once more: the request is
+    served correctly, and the evicted circuit's stem is rebuilt when it
+    comes back."""
+    T = tnlib()
+    first, second = _req(4, 5, 14, 71, 4, 2), _req(4, 5, 14, 72, 4, 2)
+    srv = T.Server(max_inflight=1, slices_per_quantum=16, precision="c64", plan_trials=8, max_log2_intermediate=15)
+    try:
+        a, sa = srv.wait(srv.submit(**first))
+        monkeypatch.setenv("TN_FAULT_ALLOC", "1")
+        b, sb = srv.wait(srv.submit(**second))
+        monkeypatch.delenv("TN_FAULT_ALLOC")
+        a2, sa2 = srv.wait(srv.submit(**first))
+    finally:
+        srv.close()
+    assert sa["status"] == 0 and sb["status"] == 0 and sa2["status"] == 0
+    assert sa2["stem_reused"] == 0  # evicted to make room for the second circuit's stem
+    assert np.array_equal(a2, a)
+    n = 20
+    for r, out in ((first, a), (second, b)):
+        gates = OC.random_circuit(r["rows"], r["cols"], r["depth"], r["seed"])
+        ref = SV.amplitudes(SV.simulate(gates, n), n, [I.bits_of(w, n) for w in r["bitstrings"]],
+                            tuple(range(n - 4, n)))
+        assert np.linalg.norm(out - ref) <= 1e-5 * np.linalg.norm(ref)
