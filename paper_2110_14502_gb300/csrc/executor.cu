@@ -375,8 +375,13 @@ static tn_status setup(Plan& P, Executor& E) {
   CK(dev_alloc(&E.perm, P.root_perm.size() * sizeof(int64_t)));
   CK(cudaMemcpy(E.perm, P.root_perm.data(), P.root_perm.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
   E.desc.resize(P.steps.size());
-  for (size_t s = 0; s < P.steps.size(); ++s)
+  for (size_t s = 0; s < P.steps.size(); ++s) {
+    // a GEMM-class step too narrow for the tensor cores whose shape the
+    // streaming kernels take (K <= 4, N <= 256) runs as one of them
     make_gemm_desc(P.steps[s].la, P.steps[s].lb, P.steps[s].lc, E.desc[s], P.steps[s].klass == SC_VECTOR);
+    if (P.steps[s].klass != SC_VECTOR && !tc_shape_ok(E.desc[s]) && vector_shape_ok(E.desc[s]))
+      make_gemm_desc(P.steps[s].la, P.steps[s].lb, P.steps[s].lc, E.desc[s], true);
+  }
   CK(cudaEventCreate(&E.ev0));
   CK(cudaEventCreate(&E.ev1));
   CK(dev_alloc(&E.err, sizeof(int)));
@@ -507,6 +512,7 @@ tn_status run_step_in(Ctx& c, size_t s, const Geo& g) {
   cudaError_t e;
   int klass = S.klass == SC_VECTOR ? TN_KCLASS_VECTOR : TN_KCLASS_GEMM_SIMT;
   if (S.klass != SC_VECTOR && c.tc && tc_shape_ok(d)) klass = TN_KCLASS_GEMM_TC;
+  else if (klass == TN_KCLASS_GEMM_SIMT && !tc_shape_ok(d) && vector_shape_ok(d)) klass = TN_KCLASS_VECTOR;
   // few outputs with a long contracted index: the bandwidth-bound reduction
   const bool reduce = klass == TN_KCLASS_GEMM_SIMT && reduce_shape_ok(d);
   if (reduce) klass = TN_KCLASS_VECTOR;

@@ -108,6 +108,27 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// One contiguous run of global memory into shared memory (16-byte aligned
+// addresses, a multiple of 16 bytes), completing on the stage's barrier.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// K-major operand without swizzle: core matrices of 8 rows x 16 bytes, each
+// 128 contiguous bytes; `lbo` bytes between the two core matrices of a 16-K
+// step, `sbo` bytes between 8-row groups; swizzle mode 0.
+__device__ __forceinline__ uint64_t plain_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
 // K-major, 64-byte swizzled operand: stride byte offset 512 (8 rows x 64 B),
 // descriptor version 1 (bits 46-47), swizzle mode 4 = 64 B (bits 61-63).
 __device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
@@ -887,11 +908,20 @@ int split_chunk() {
   return c;
 }
 
+// Planes of one operand for K = 8 (16-byte rows): byte address of plane p,
+// row r of the unit (zlo, zhi) = base + zlo st_lo + zhi st_hi + p plane + 16 r.
+// A null base selects the tensor-map loads.
+struct BulkPlanes {
+  const uint8_t* base;
+  int64_t st_lo, st_hi, plane;
+};
+
 template <int TN, bool BF16>
 __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_tma_chunked(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                      float2* __restrict__ C0, const GemmDesc d, int kp, int a_zlo, int a_zhi, int b_zlo, int b_zhi,
-                     int c_planes, const ScaleIO sio, int chunk, int fold, int* __restrict__ err) {
+                     int c_planes, const ScaleIO sio, int chunk, int fold, int* __restrict__ err,
+                     const BulkPlanes ba, const BulkPlanes bb) {
   constexpr int NP = 4;
   using CF = Cfg2<TN, NP>;
   constexpr int NS = CF::NSTAGE;
@@ -946,6 +976,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
   }
+  // K = 8: each operand plane sits in a stage as its 16-byte rows (one bulk
+  // copy) followed by as many zero bytes, the second core matrix of every
+  // 16-K MMA step; the zeros are written once here
+  const bool k8 = ba.base != nullptr;  // set by the host only for K = 8
+  constexpr int A_PLANE8 = 2 * TM * 16, B_PLANE8 = 2 * TN * 16;
+  if (k8) {
+    for (int s = 0; s < NS; ++s) {
+      uint8_t* st = smem + s * CF::STAGE;
+      for (int i = tid; i < 4 * (TM * 16 / 16); i += NTHREADS) {
+        const int p = i / (TM * 16 / 16), o = i % (TM * 16 / 16);
+        reinterpret_cast<uint4*>(st + p * A_PLANE8 + TM * 16)[o] = make_uint4(0u, 0u, 0u, 0u);
+      }
+      for (int i = tid; i < 4 * (TN * 16 / 16); i += NTHREADS) {
+        const int p = i / (TN * 16 / 16), o = i % (TN * 16 / 16);
+        reinterpret_cast<uint4*>(st + A_STAGE + p * B_PLANE8 + TN * 16)[o] = make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor core's reads
+  }
   if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(COLS));
@@ -973,6 +1022,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           break;
         }
         uint8_t* st = smem + s * CF::STAGE;
+        if (k8) {
+          // four 2 KB runs of A's planes and four runs of B's (per folded unit)
+          mbar_expect_tx(&full[s], 4 * TM * 16 + 4 * TN * 16);
+          const uint8_t* ga = ba.base + za_lo * ba.st_lo + za_hi * ba.st_hi + (int64_t)m0 * 16;
+#pragma unroll
+          for (int p = 0; p < 4; ++p) bulk_load(st + p * A_PLANE8, ga + p * ba.plane, TM * 16, &full[s]);
+          for (int f = 0; f < fold; ++f) {
+            const uint8_t* gb = bb.base + zb_lo * bb.st_lo + (fold > 1 ? uhi + f : zb_hi) * bb.st_hi +
+                                (int64_t)(fold > 1 ? 0 : n0) * 16;
+            const int rows = fold > 1 ? nsub : TN;
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+              bulk_load(st + A_STAGE + p * B_PLANE8 + f * rows * 16, gb + p * bb.plane, rows * 16, &full[s]);
+          }
+          continue;
+        }
         mbar_expect_tx(&full[s], CF::STAGE);
         tma_load_5d(st, &mapA, &full[s], kt * TKC, m0, 0, za_lo, za_hi);
         if (fold == 1) {
@@ -1021,14 +1086,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t a = smem_u32(smem + s * CF::STAGE);
-          const uint32_t bb = a + A_STAGE;
-#pragma unroll
-          for (int kk = 0; kk < TKC / 16; ++kk) {
+          const uint32_t b0 = a + A_STAGE;
+          const int nkk = k8 ? 1 : TKC / 16;  // K = 8: one 16-K step, its upper half zeros
+#pragma unroll 2
+          for (int kk = 0; kk < nkk; ++kk) {
             uint64_t A_[NP], B_[NP];
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
-              A_[p] = sw64_desc(a + p * (TM * 64) + kk * 32);
-              B_[p] = sw64_desc(bb + p * (TN * 64) + kk * 32);
+              if (k8) {
+                A_[p] = plain_desc(a + p * A_PLANE8, TM * 16, 128);
+                B_[p] = plain_desc(b0 + p * B_PLANE8, TN * 16, 128);
+              } else {
+                A_[p] = sw64_desc(a + p * (TM * 64) + kk * 32);
+                B_[p] = sw64_desc(b0 + p * (TN * 64) + kk * 32);
+              }
             }
             const uint32_t acc = (kt > k0 || kk) ? 1u : 0u;
             // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo; the chunk is short,
@@ -1361,7 +1432,8 @@ cudaError_t launch_persistent(const CUtensorMap& ma, const CUtensorMap& mb, floa
 
 template <int TN, bool BF16>
 cudaError_t launch_chunked(const CUtensorMap& ma, const CUtensorMap& mb, float2* C, const GemmDesc& d, int kp,
-                           const int z[4], int c_planes, const ScaleIO& sio, int fold, int* err, cudaStream_t s) {
+                           const int z[4], int c_planes, const ScaleIO& sio, int fold, int* err, cudaStream_t s,
+                           const BulkPlanes& ba, const BulkPlanes& bb) {
   static bool attr = false;
   static int sms = 0;
   if (!attr) {
@@ -1376,22 +1448,22 @@ cudaError_t launch_chunked(const CUtensorMap& ma, const CUtensorMap& mb, float2*
   const int chunk = split_chunk();
   const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
   gemm_tma_chunked<TN, BF16><<<grid, NTHREADS, Cfg2<TN, 4>::SMEM + EPI_STAGE_BYTES, s>>>(
-      ma, mb, C, d, kp, z[0], z[1], z[2], z[3], c_planes, sio, chunk, fold, err);
+      ma, mb, C, d, kp, z[0], z[1], z[2], z[3], c_planes, sio, chunk, fold, err, ba, bb);
   return cudaGetLastError();
 }
 
 template <bool BF16, int NP>
 cudaError_t launch_tn(int TNv, bool persistent, const CUtensorMap& ma, const CUtensorMap& mb, float2* C,
                       const GemmDesc& d, int kp, const int z[4], int cp, const ScaleIO& sio, int fold, int* err,
-                      cudaStream_t s) {
+                      cudaStream_t s, const BulkPlanes& ba = BulkPlanes{}, const BulkPlanes& bb = BulkPlanes{}) {
   if constexpr (NP == 4) {
     // split precision always runs the chunked persistent kernel (accuracy)
     (void)persistent;
     switch (TNv) {
-      case 128: return launch_chunked<128, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s);
-      case 64: return launch_chunked<64, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s);
-      case 32: return launch_chunked<32, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s);
-      case 16: return launch_chunked<16, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s);
+      case 128: return launch_chunked<128, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s, ba, bb);
+      case 64: return launch_chunked<64, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s, ba, bb);
+      case 32: return launch_chunked<32, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s, ba, bb);
+      case 16: return launch_chunked<16, BF16>(ma, mb, C, d, kp, z, cp, sio, fold, err, s, ba, bb);
       default: return cudaErrorInvalidValue;
     }
   } else {
@@ -1462,9 +1534,27 @@ cudaError_t launch_gemm_tma(const PlaneOperand& a, const PlaneOperand& b, float2
   const int kpi = (int)a.kp;
   const int z[4] = {a.nlo > 1, a.nhi > 1, b.nlo > 1, b.nhi > 1};
   const int cp = c_planes ? 1 : 0;
-  if (a.np == 4)
-    return bf16 ? launch_tn<true, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, fold, err, s)
-                : launch_tn<false, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, fold, err, s);
+  if (a.np == 4) {
+    // K = 8: the operands' 16-byte rows go by contiguous bulk copies (one per
+    // plane) instead of tensor-map boxes of 16-byte rows; every address and
+    // size must be a multiple of 16 bytes, else the tensor maps serve
+    auto bulk = [](const PlaneOperand& o) {
+      BulkPlanes q;
+      q.base = reinterpret_cast<const uint8_t*>(o.base);
+      q.st_lo = o.nlo > 1 ? o.st_lo : 0;
+      q.st_hi = o.nhi > 1 ? o.st_hi : 0;
+      q.plane = o.rows * o.kp * 2;
+      return q;
+    };
+    BulkPlanes qa = bulk(a), qb = bulk(b);
+    auto aligned = [](const BulkPlanes& q) {
+      return (reinterpret_cast<uintptr_t>(q.base) % 16) == 0 && q.st_lo % 16 == 0 && q.st_hi % 16 == 0 &&
+             q.plane % 16 == 0;
+    };
+    if (kpi != 8 || !aligned(qa) || !aligned(qb)) qa = qb = BulkPlanes{};
+    return bf16 ? launch_tn<true, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, fold, err, s, qa, qb)
+                : launch_tn<false, 4>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, fold, err, s, qa, qb);
+  }
   return bf16 ? launch_tn<true, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, 1, err, s)
               : launch_tn<false, 2>(TNv, persistent, ma, mb, C, d, kpi, z, cp, sio, 1, err, s);
 }

@@ -1,5 +1,5 @@
-// Bandwidth-bound contraction for vector-like steps (N <= 16 and K <= 16, or
-// N <= 8 and K <= 128).
+// Bandwidth-bound contraction for vector-like steps (N <= 16 and K <= 16,
+// N <= 8 and K <= 128, or N <= 256 and K <= 4).
 //
 // Paper: Sec. "Tensor Contraction Using Fused Permutation and
 // Multiplication", imbalanced case (a high-rank tensor against a rank-4 one):
@@ -87,6 +87,76 @@ __global__ void __launch_bounds__(NT) vector_kernel(const float2* __restrict__ A
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         float2 b = Bs[k * N + n];
+        acc.x = fmaf(a[k].x, b.x, acc.x);
+        acc.x = fmaf(-a[k].y, b.y, acc.x);
+        acc.y = fmaf(a[k].x, b.y, acc.y);
+        acc.y = fmaf(a[k].y, b.x, acc.y);
+      }
+      C[(int64_t)oc + nC[n]] = acc;
+    }
+  }
+}
+
+// Wide B with a very short contracted index (K <= 4, N = 32..256): the
+// outer-product-like steps that expand a tensor.  The row's K values stay in
+// registers while the thread walks the N columns, so the registers do not grow
+// with N; B (K N <= 1024 complex) sits in shared memory.
+template <int NK, int NN>
+__global__ void __launch_bounds__(NT) vector_wide_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
+                                                         float2* __restrict__ C, const GemmDesc d) {
+  constexpr int K = 1 << NK, N = 1 << NN;
+  static_assert(K * N <= 1024, "B must fit in shared memory");
+  const int64_t M = int64_t(1) << d.nm;
+  const int64_t ulo = blockIdx.y % d.units_lo, uhi = blockIdx.y / d.units_lo;
+  A += ulo * d.a_lo + uhi * d.a_hi;
+  B += ulo * d.b_lo + uhi * d.b_hi;
+  C += ulo * d.c_lo + uhi * d.c_hi;
+  __shared__ float2 Bs[K * N];
+  __shared__ int32_t kA[K], nC[N];
+  __shared__ int32_t tAlo[32], tAhi[32], tClo[32], tChi[32];
+  __shared__ int32_t baseA, baseC;
+  const int tid = threadIdx.x;
+  const int64_t base = (int64_t)blockIdx.x * CH;
+  for (int e = tid; e < K * N; e += NT) {
+    const int k = e / N, n = e % N;
+    Bs[e] = B[bit_offset(k, NK, d.bk) + bit_offset(n, NN, d.bn)];
+  }
+  if (tid < K) kA[tid] = bit_offset(tid, NK, d.ak);
+  for (int n = tid; n < N; n += NT) nC[n] = bit_offset(n, NN, d.cn);
+  const int lb = d.nm < CH_BITS ? d.nm : CH_BITS;
+  if (tid >= 128 && tid < 160) {
+    const int x = tid - 128, b0 = lb < 5 ? lb : 5;
+    tAlo[x] = x < (1 << b0) ? bit_offset(x, b0, d.am) : 0;
+    tClo[x] = x < (1 << b0) ? bit_offset(x, b0, d.cm) : 0;
+  }
+  if (tid >= 160 && tid < 192) {
+    const int x = tid - 160, b1 = lb > 5 ? lb - 5 : 0;
+    tAhi[x] = x < (1 << b1) ? bit_offset(x, b1, d.am + 5) : 0;
+    tChi[x] = x < (1 << b1) ? bit_offset(x, b1, d.cm + 5) : 0;
+  }
+  if (tid == 192) {
+    int32_t oa = 0, oc = 0;
+    for (int i = CH_BITS; i < d.nm; ++i)
+      if ((base >> i) & 1) { oa += d.am[i]; oc += d.cm[i]; }
+    baseA = oa;
+    baseC = oc;
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int r = 0; r < PER; ++r) {
+    const int loc = tid + r * NT;
+    if (base + loc >= M) break;
+    const int32_t oa = baseA + tAlo[loc & 31] + tAhi[loc >> 5];
+    const int32_t oc = baseC + tClo[loc & 31] + tChi[loc >> 5];
+    float2 a[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] = __ldg(A + (int64_t)oa + kA[k]);
+#pragma unroll 8
+    for (int n = 0; n < N; ++n) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float2 b = Bs[k * N + n];
         acc.x = fmaf(a[k].x, b.x, acc.x);
         acc.x = fmaf(-a[k].y, b.y, acc.x);
         acc.y = fmaf(a[k].x, b.y, acc.y);
@@ -366,12 +436,33 @@ cudaError_t launch_nn(const float2* A, const float2* B, float2* C, const GemmDes
 
 }  // namespace
 
-bool vector_shape_ok(const GemmDesc& d) { return (d.nn <= 4 && d.nk <= 4) || (d.nn <= 3 && d.nk <= 7); }
+bool vector_shape_ok(const GemmDesc& d) {
+  return (d.nn <= 4 && d.nk <= 4) || (d.nn <= 3 && d.nk <= 7) || (d.nn <= 8 && d.nk <= 2);
+}
+
+template <int NK>
+cudaError_t launch_wide(const float2* A, const float2* B, float2* C, const GemmDesc& d, dim3 g, cudaStream_t s) {
+  switch (d.nn) {
+    case 5: vector_wide_kernel<NK, 5><<<g, NT, 0, s>>>(A, B, C, d); break;
+    case 6: vector_wide_kernel<NK, 6><<<g, NT, 0, s>>>(A, B, C, d); break;
+    case 7: vector_wide_kernel<NK, 7><<<g, NT, 0, s>>>(A, B, C, d); break;
+    case 8: vector_wide_kernel<NK, 8><<<g, NT, 0, s>>>(A, B, C, d); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s) {
   if (!vector_shape_ok(d) || d.units > 65535) return cudaErrorInvalidValue;
   int64_t M = int64_t(1) << d.nm;
   dim3 g((unsigned)((M + CH - 1) / CH), (unsigned)d.units);
+  if (d.nn > 4) {  // K <= 2 (vector_shape_ok)
+    switch (d.nk) {
+      case 0: return launch_wide<0>(A, B, C, d, g, s);
+      case 1: return launch_wide<1>(A, B, C, d, g, s);
+      default: return launch_wide<2>(A, B, C, d, g, s);
+    }
+  }
   if (staged_ok(A, d)) {
     switch (d.nk) {
       case 3: return launch_staged<3>(A, B, C, d, s);

@@ -146,7 +146,8 @@ cudaError_t run_gemm_tc2(const float2* A, const float2* B, float2* C, const Gemm
 // aux: 24 bytes of device memory (maxima, exponents, stored maxima).
 cudaError_t run_gemm_tc2_scaled(const float2* A, const float2* B, float2* C, const GemmDesc& d, bool bf16, int np,
                                 uint16_t* scratch, void* aux, int* err, cudaStream_t s);
-// Vector-like steps: N <= 16 and K <= 16, or N <= 8 and K <= 128 (k_vector.cu).
+// Vector-like steps: N <= 16 and K <= 16, N <= 8 and K <= 128, or N <= 256 and
+// K <= 4 (k_vector.cu).
 bool vector_shape_ok(const GemmDesc& d);
 cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s);
 // Few outputs (M N <= 64), long contracted index (K >= 256): one CTA per

@@ -53,11 +53,12 @@ def test_pair_c64_matches_fp64(nm, nn, nk, algo):
 
 
 @pytest.mark.parametrize("nm,nn,nk", [(0, 0, 0), (5, 1, 3), (12, 4, 4), (18, 2, 2), (20, 4, 2),
-                                      (3, 3, 5), (11, 3, 5), (13, 2, 6), (9, 0, 7), (16, 3, 7), (10, 1, 6)])
+                                      (3, 3, 5), (11, 3, 5), (13, 2, 6), (9, 0, 7), (16, 3, 7), (10, 1, 6),
+                                      (13, 5, 2), (10, 8, 1), (9, 6, 2), (3, 8, 2), (12, 7, 0), (11, 5, 1)])
 def test_vector_kernel_matches_fp64(nm, nn, nk):
-    """Streaming kernel: N, K <= 16 with the row's K values in registers, and
-    N <= 8 with K up to 128 consumed into running sums; ragged M below one
-    CTA's 1024 rows included."""
+    """Streaming kernel: N, K <= 16 with the row's K values in registers,
+    N <= 8 with K up to 128 consumed into running sums, and N up to 256 with
+    K <= 4; ragged M below one CTA's 1024 rows included."""
     T = tnlib()
     la, lb, lc, A, B, ref = _case(nm, nn, nk, seed=7 + nm + nk)
     for algo in ("vector", "auto"):
@@ -146,7 +147,8 @@ def test_pair_rejects_bad_labels():
 
 TC_SHAPES = [(7, 4, 3), (7, 6, 5), (8, 7, 6), (10, 6, 9), (9, 9, 4), (12, 8, 10), (14, 7, 7), (7, 5, 4), (8, 8, 12),
              (15, 8, 6), (16, 7, 5), (13, 9, 8),  # >= 296 tiles: persistent CTAs
-             (7, 4, 14), (7, 5, 16)]               # long K: chunked accumulation keeps the error flat
+             (7, 4, 14), (7, 5, 16),              # long K: chunked accumulation keeps the error flat
+             (12, 5, 3), (16, 7, 3), (10, 6, 3)]  # K = 8: operand rows by bulk copies, zero upper K half
 
 
 @pytest.mark.parametrize("nm,nn,nk", TC_SHAPES)
@@ -191,7 +193,7 @@ PAIR_BOUND = {"split_fp16": 2e-5, "scaled_fp16": 2e-3, "scaled_bf16": 1.5e-2}
 
 
 @pytest.mark.parametrize("mode", list(PAIR_BOUND))
-@pytest.mark.parametrize("nm,nn,nk", [(7, 4, 3), (8, 7, 6), (9, 5, 11), (13, 9, 8)])
+@pytest.mark.parametrize("nm,nn,nk", [(7, 4, 3), (8, 7, 6), (9, 5, 11), (13, 9, 8), (14, 5, 3)])
 def test_tensor_core_precisions_vs_fp64(mode, nm, nn, nk):
     """The TMA tensor-core kernel in the precisions that scale operands by
     their exact maxima: split fp16 (four planes, chunked accumulation) and one
