@@ -87,7 +87,7 @@ struct Request {
   std::vector<std::shared_ptr<Request>> members;
   int64_t batched = 1;  // requests in the contraction that served this one
   bool member = false;  // served in another request's contraction
-  int stem_reused = 0;  // a member: whether the contraction that served it reused a resident stem
+  int stem_reused = 0;  // whether the contraction that served it reused a resident stem (set when done)
 };
 
 
@@ -277,7 +277,13 @@ void release(Server& S, Request& R) {
   if (R.ev_end) cudaEventDestroy(R.ev_end);
   R.ev_begin = R.ev_end = nullptr;
   S.in_use -= R.footprint;
-  // the request's plan copy keeps its arenas until the request is released by tn_wait
+  // the device memory goes with the budget share: the plan copy's executor
+  // (arenas, operand planes, graphs) is freed now, not when the client waits
+  R.stem_reused = R.plan && stem_reused(R.plan->plan) ? 1 : 0;
+  if (R.plan && R.plan->plan.exec) {
+    destroy_executor(R.plan->plan.exec);
+    R.plan->plan.exec = nullptr;
+  }
 }
 
 tn_status admit(Server&, Request& R, cudaStream_t stream) {
@@ -636,7 +642,7 @@ extern "C" tn_status tn_wait(tn_server* h, int64_t ticket, double* out, int64_t 
       stats->plan_hash = P.hash;
     }
     stats->planned_here = R->planned_here;
-    stats->stem_reused = R->member ? R->stem_reused : (R->plan && stem_reused(R->plan->plan) ? 1 : 0);
+    stats->stem_reused = R->stem_reused;
     stats->gpu_begin_ms = R->gpu_begin_ms;
     stats->gpu_end_ms = R->gpu_end_ms;
     stats->quanta = R->nquanta;
@@ -653,7 +659,7 @@ extern "C" tn_status tn_wait(tn_server* h, int64_t ticket, double* out, int64_t 
   }
   if (R->h_out) cudaFreeHost(R->h_out);
   R->h_out = nullptr;
-  R->plan.reset();  // frees the request's device state
+  R->plan.reset();  // the host copy of the plan (its device state went when the request completed)
   return st;
 }
 
