@@ -159,11 +159,11 @@ __global__ void __launch_bounds__(NT) split_kernel(const float2* __restrict__ sr
 }  // namespace
 
 cudaError_t launch_split(const float2* src, uint16_t* dst, const SplitDesc& d, int nz, bool bf16, int np,
-                         unsigned* maxbits, int* e_out, float* m_out, cudaStream_t s) {
+                         unsigned* maxbits, int* e_out, float* m_out, cudaStream_t s, bool max_ready) {
   if (nz < 1 || nz > 65535 || d.kp % 8 != 0 || (np != 2 && np != 4)) return cudaErrorInvalidValue;
   const int64_t total = (int64_t)d.rows_pad * (d.kp / 8);
   const int64_t blocks = std::min<int64_t>((total + NT - 1) / NT, 152 * 8);
-  if (maxbits) {
+  if (maxbits && !max_ready) {
     max_kernel<<<dim3((unsigned)blocks, (unsigned)nz), NT, 0, s>>>(src, d, maxbits);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -206,13 +206,13 @@ int64_t tc2_scratch_elems(const GemmDesc& d) { return split_scratch_elems(d, fal
 
 cudaError_t split_operand(const float2* src, const GemmDesc& d, bool which_b, bool bf16, int np, bool scaled,
                           unsigned* maxbits, int* e_out, float* m_out, uint16_t* scratch, PlaneOperand& out,
-                          cudaStream_t s) {
+                          cudaStream_t s, bool max_ready) {
   const int64_t lo = which_b ? d.b_lo : d.a_lo, hi = which_b ? d.b_hi : d.a_hi;
   const int nrow = which_b ? d.nn : d.nm;
   SplitDesc sd;
   split_desc(nrow, which_b ? d.bn : d.am, d.nk, which_b ? d.bk : d.ak, lo ? d.units_lo : 1, lo, hi, sd);
   const int nz = distinct(d, lo, hi);
-  cudaError_t e = launch_split(src, scratch, sd, nz, bf16, np, scaled ? maxbits : nullptr, e_out, m_out, s);
+  cudaError_t e = launch_split(src, scratch, sd, nz, bf16, np, scaled ? maxbits : nullptr, e_out, m_out, s, max_ready);
   const int64_t set = (int64_t)np * (int64_t(1) << nrow) * sd.kp * 2;
   out.base = scratch;
   out.np = np;

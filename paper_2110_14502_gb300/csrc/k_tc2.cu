@@ -821,7 +821,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // contiguous run lies along the lanes (rows fastest), where each thread would
 // otherwise store its values two bytes at a time.
 constexpr int STAGE_SLOTS = 512 + 64;  // 8-byte slots per warp: 512 elements, 2 padding slots after every 16
-constexpr int EPI_STAGE_BYTES = 4 * STAGE_SLOTS * 8;
 
 struct StageMap {
   bool on;
@@ -908,6 +907,21 @@ int split_chunk() {
   return c;
 }
 
+// Chunked kernel with EW epilogue warps (4 or 8): 128 + 32 EW threads.  Eight
+// epilogue warps (two per TMEM lane quarter, taking alternate 16-column
+// chunks) double the epilogue's latency hiding for output-bound steps; their
+// staging buffers leave room for fewer operand stages.
+template <int TN, int EW>
+struct ChunkCfg {
+  static constexpr int THREADS = 128 + 32 * EW;
+  static constexpr int STAGE_BYTES = EW * STAGE_SLOTS * 8;
+  static constexpr int BUDGET = EW == 4 ? SMEM_BUDGET : 227 * 1024 - STAGE_BYTES - 1024 - 4096;
+  static constexpr int STAGE = Cfg2<TN, 4>::STAGE;
+  static constexpr int NS = (BUDGET / STAGE) < 6 ? (BUDGET / STAGE) : 6;
+  static constexpr int SMEM = NS * STAGE + 1024 + STAGE_BYTES;
+  static_assert(NS >= 2, "at least two operand stages");
+};
+
 // Planes of one operand for K = 8 (16-byte rows): byte address of plane p,
 // row r of the unit (zlo, zhi) = base + zlo st_lo + zhi st_hi + p plane + 16 r.
 // A null base selects the tensor-map loads.
@@ -916,15 +930,17 @@ struct BulkPlanes {
   int64_t st_lo, st_hi, plane;
 };
 
-template <int TN, bool BF16>
-__global__ void __launch_bounds__(NTHREADS, 1)
+template <int TN, bool BF16, int EW>
+__global__ void __launch_bounds__(ChunkCfg<TN, EW>::THREADS, 1)
     gemm_tma_chunked(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                      float2* __restrict__ C0, const GemmDesc d, int kp, int a_zlo, int a_zhi, int b_zlo, int b_zhi,
                      int c_planes, const ScaleIO sio, int chunk, int fold, int* __restrict__ err,
                      const BulkPlanes ba, const BulkPlanes bb) {
   constexpr int NP = 4;
   using CF = Cfg2<TN, NP>;
-  constexpr int NS = CF::NSTAGE;
+  constexpr int NS = ChunkCfg<TN, EW>::NS;
+  constexpr int NT = ChunkCfg<TN, EW>::THREADS;
+  constexpr int ET = 32 * EW;  // epilogue threads
   constexpr int A_STAGE = CF::A_STAGE;
   constexpr uint32_t BUF = 2 * TN;  // columns of one buffer
   constexpr uint32_t COLS = 2 * BUF < 32 ? 32 : 2 * BUF;
@@ -968,7 +984,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 128); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], ET); }
     mbar_init(&mma_done, 1);
     abort_flag = 0;
     epi_fail = 0;
@@ -984,11 +1000,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (k8) {
     for (int s = 0; s < NS; ++s) {
       uint8_t* st = smem + s * CF::STAGE;
-      for (int i = tid; i < 4 * (TM * 16 / 16); i += NTHREADS) {
+      for (int i = tid; i < 4 * (TM * 16 / 16); i += NT) {
         const int p = i / (TM * 16 / 16), o = i % (TM * 16 / 16);
         reinterpret_cast<uint4*>(st + p * A_PLANE8 + TM * 16)[o] = make_uint4(0u, 0u, 0u, 0u);
       }
-      for (int i = tid; i < 4 * (TN * 16 / 16); i += NTHREADS) {
+      for (int i = tid; i < 4 * (TN * 16 / 16); i += NT) {
         const int p = i / (TN * 16 / 16), o = i % (TN * 16 / 16);
         reinterpret_cast<uint4*>(st + A_STAGE + p * B_PLANE8 + TN * 16)[o] = make_uint4(0u, 0u, 0u, 0u);
       }
@@ -1130,12 +1146,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     __syncwarp();
   } else if (warp >= 4) {
-    // ---- epilogue: fold chunks 1.. into R; after the last one, store R
-    const int q = warp & 3;
+    // ---- epilogue: fold chunks 1.. into R; after the last one, store R.
+    // Warp 4 + e reads TMEM lane quarter q = warp % 4 (the hardware's rule)
+    // and, with eight epilogue warps, every other 16-column chunk (h).
+    const int e = warp - 4, q = warp & 3, h = e >> 2;
+    constexpr int CS = 16 * (EW / 4);  // column stride between a warp's chunks
     const int tq = tid - 128;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const StageMap sm = stage_map(d, lane, vec_bits(d), c_planes != 0);
-    float2* const slots = reinterpret_cast<float2*>(smem + NS * CF::STAGE) + q * STAGE_SLOTS;
+    float2* const slots = reinterpret_cast<float2*>(smem + NS * CF::STAGE) + e * STAGE_SLOTS;
     // the C-order index of (lane, jj) is lane_idx | (jj's bits at their ranks);
     // the two parts have disjoint bits, so their slots add
     const int lane_slot = stage_slot(sm.lane_idx);
@@ -1160,7 +1179,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // the column offsets change with the tile's first column only (the
       // barriers around each item order these writes against every read)
       if (n0 != last_n0) {
-        for (int jj = tq; jj < TN; jj += 128) colC[jj] = bit_offset(fold > 1 ? (jj & (nsub - 1)) : n0 + jj, d.nn, d.cn);
+        for (int jj = tq; jj < TN; jj += ET) colC[jj] = bit_offset(fold > 1 ? (jj & (nsub - 1)) : n0 + jj, d.nn, d.cn);
         last_n0 = n0;
       }
       const int32_t ro = ro_lo + (int32_t)__reduce_add_sync(0xffffffffu, (uint32_t)(((m0 >> lane) & 1) ? my_cm : 0));
@@ -1200,13 +1219,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           abort_flag = 1;
           epi_fail = 1;
         }
-        // colC of this item and any failure visible to all 4 epilogue warps
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+        // colC of this item and any failure visible to every epilogue warp
+        asm volatile("bar.sync 1, %0;" ::"r"(ET) : "memory");
         if (epi_fail) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (c == 0) continue;  // the first chunk accumulated in R itself
 #pragma unroll 1
-        for (int c0 = 0; c0 < TN; c0 += 16) {
+        for (int c0 = 16 * h; c0 < TN; c0 += CS) {
           uint32_t pr[16], pi[16], rr[16], ri[16];
           tmem_ld<16>(P + (uint32_t)c0, pr);
           tmem_ld<16>(P + (uint32_t)(TN + c0), pi);
@@ -1232,11 +1251,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int ea = 0, eb = 0, r = 0;
       Pow2 sc(0);
 #pragma unroll 1
-      for (int c0 = 0; c0 < TN; c0 += 16) {
+      for (int c0 = 16 * h; c0 < TN; c0 += CS) {
         // columns of a folded tile belong to hi unit uhi + c0 / 2^nn (N >= 16:
-        // a 16-column chunk never straddles two units)
+        // a 16-column chunk never straddles two units); the warp's first and
+        // last chunks among a unit's gw columns open and close its records
         const int f = fold > 1 ? (c0 >> d.nn) : 0;
-        if (c0 % gw == 0) {
+        if (c0 % gw < CS) {
           unit_scale(f, ea, eb, r, weak);
           sc = Pow2(c_planes ? -r : ea + eb);
           vmax = 0.f;
@@ -1322,7 +1342,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         } else {
           store_c64(C, ro, &colC[c0], vb, vr, vi);
         }
-        if ((c0 + 16) % gw == 0 && (sio.mc || sio.flag)) {
+        if (c0 % gw + CS >= gw && (sio.mc || sio.flag)) {
           // the unit's columns are done: its largest stored component,
           // exponent and filter flag (launch unit ulo + (uhi + f) units_lo)
           const int un = fold > 1 ? ulo + (uhi + f) * d.units_lo : unit;
@@ -1339,7 +1359,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[rb])) : "memory");
       // every epilogue thread is done with colC before the next item rewrites it
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"r"(ET) : "memory");
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1430,15 +1450,16 @@ cudaError_t launch_persistent(const CUtensorMap& ma, const CUtensorMap& mb, floa
   return cudaGetLastError();
 }
 
-template <int TN, bool BF16>
-cudaError_t launch_chunked(const CUtensorMap& ma, const CUtensorMap& mb, float2* C, const GemmDesc& d, int kp,
-                           const int z[4], int c_planes, const ScaleIO& sio, int fold, int* err, cudaStream_t s,
-                           const BulkPlanes& ba, const BulkPlanes& bb) {
+template <int TN, bool BF16, int EW>
+cudaError_t launch_chunked_ew(const CUtensorMap& ma, const CUtensorMap& mb, float2* C, const GemmDesc& d, int kp,
+                              const int z[4], int c_planes, const ScaleIO& sio, int fold, int* err, cudaStream_t s,
+                              const BulkPlanes& ba, const BulkPlanes& bb) {
+  using CC = ChunkCfg<TN, EW>;
   static bool attr = false;
   static int sms = 0;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tma_chunked<TN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg2<TN, 4>::SMEM + EPI_STAGE_BYTES);
+    cudaError_t e =
+        cudaFuncSetAttribute(gemm_tma_chunked<TN, BF16, EW>, cudaFuncAttributeMaxDynamicSharedMemorySize, CC::SMEM);
     if (e != cudaSuccess) return e;
     sms = sm_count();
     attr = true;
@@ -1447,9 +1468,22 @@ cudaError_t launch_chunked(const CUtensorMap& ma, const CUtensorMap& mb, float2*
   const int64_t items = (M / TM) * (fold > 1 ? 1 : N / TN) * (d.units / fold);
   const int chunk = split_chunk();
   const unsigned grid = (unsigned)std::min<int64_t>(items, sms);
-  gemm_tma_chunked<TN, BF16><<<grid, NTHREADS, Cfg2<TN, 4>::SMEM + EPI_STAGE_BYTES, s>>>(
-      ma, mb, C, d, kp, z[0], z[1], z[2], z[3], c_planes, sio, chunk, fold, err, ba, bb);
+  gemm_tma_chunked<TN, BF16, EW><<<grid, CC::THREADS, CC::SMEM, s>>>(ma, mb, C, d, kp, z[0], z[1], z[2], z[3],
+                                                                      c_planes, sio, chunk, fold, err, ba, bb);
   return cudaGetLastError();
+}
+
+// Eight epilogue warps where the epilogue dominates a tile (a short K: at
+// most 4 operand stages, or 8 for tiles up to 64 columns wide), four where the
+// main loop does and the extra operand stage matters.
+template <int TN, bool BF16>
+cudaError_t launch_chunked(const CUtensorMap& ma, const CUtensorMap& mb, float2* C, const GemmDesc& d, int kp,
+                           const int z[4], int c_planes, const ScaleIO& sio, int fold, int* err, cudaStream_t s,
+                           const BulkPlanes& ba, const BulkPlanes& bb) {
+  const int nkt = (kp + TKC - 1) / TKC;
+  if (nkt <= 4 || (TN <= 64 && nkt <= 8))
+    return launch_chunked_ew<TN, BF16, 8>(ma, mb, C, d, kp, z, c_planes, sio, fold, err, s, ba, bb);
+  return launch_chunked_ew<TN, BF16, 4>(ma, mb, C, d, kp, z, c_planes, sio, fold, err, s, ba, bb);
 }
 
 template <bool BF16, int NP>

@@ -84,8 +84,10 @@ struct SplitDesc {
   int64_t lo, hi;
   int32_t row_st[kMaxBits], k_st[kMaxBits];
 };
+// max_ready: maxbits already holds each operand tensor's largest |component|
+// (recorded by its producer), so the maximum pass is skipped.
 cudaError_t launch_split(const float2* src, uint16_t* dst, const SplitDesc& d, int nz, bool bf16, int np,
-                         unsigned* maxbits, int* e_out, float* m_out, cudaStream_t s);
+                         unsigned* maxbits, int* e_out, float* m_out, cudaStream_t s, bool max_ready = false);
 // One GEMM operand stored as four K-major 16-bit planes {re_hi, re_lo, im_hi,
 // im_lo}, each rows x kp; consecutive units are st_lo / st_hi bytes apart
 // along the two unit dimensions (extent 1 = one tensor shared by all units).
@@ -131,7 +133,7 @@ cudaError_t launch_gemm_tma(const PlaneOperand& a, const PlaneOperand& b, float2
 int64_t split_scratch_elems(const GemmDesc& d, bool which_b, int np);
 cudaError_t split_operand(const float2* src, const GemmDesc& d, bool which_b, bool bf16, int np, bool scaled,
                           unsigned* maxbits, int* e_out, float* m_out, uint16_t* scratch, PlaneOperand& out,
-                          cudaStream_t s);
+                          cudaStream_t s, bool max_ready = false);
 // Plane operand of a tensor a producer epilogue already wrote as np planes
 // (layout [rows][K], K >= 8); false when the step's view does not match.
 bool planes_in_place(const float2* base, const GemmDesc& d, bool which_b, int np, PlaneOperand& out);
@@ -149,7 +151,10 @@ cudaError_t run_gemm_tc2_scaled(const float2* A, const float2* B, float2* C, con
 // Vector-like steps: N <= 16 and K <= 16, N <= 8 and K <= 128, or N <= 256 and
 // K <= 4 (k_vector.cu).
 bool vector_shape_ok(const GemmDesc& d);
-cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s);
+// maxbits (may be null): per launch unit, the largest |component| written, as
+// float bits by atomicMax (cleared by the caller).
+cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s,
+                          unsigned* maxbits = nullptr);
 // Few outputs (M N <= 64), long contracted index (K >= 256): one CTA per
 // unit, K spread over the threads, warp-shuffle reduction (k_reduce.cu).
 bool reduce_shape_ok(const GemmDesc& d);
