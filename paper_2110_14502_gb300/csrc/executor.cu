@@ -423,6 +423,7 @@ struct Ctx {
   int* flag1 = nullptr;          // [Gs] slice-only units
   int* flag2 = nullptr;          // [U] (bitstring, slice) units
   std::vector<char> planes_out;  // per step: output written as 16-bit planes for a tensor-core consumer
+  std::vector<char> max_out;     // per step: a streaming step records its output's maxima for a scaled split
   const int8_t* step_prec = nullptr;  // per-step precision override (TN_PREC_*, -1 = the call's)
   int call_precision = TN_PREC_C64;
   bool tuning = false;           // time the tile choices of each tensor-core step
@@ -518,7 +519,15 @@ tn_status run_step_in(Ctx& c, size_t s, const Geo& g) {
   if (reduce) klass = TN_KCLASS_VECTOR;
   if (c.sizing && klass != TN_KCLASS_GEMM_TC) return TN_OK;
   if (reduce) e = launch_reduce(A, B, C, d, c.st);
-  else if (klass == TN_KCLASS_VECTOR) e = launch_vector(A, B, C, d, c.st);
+  else if (klass == TN_KCLASS_VECTOR) {
+    unsigned* mb = nullptr;
+    e = cudaSuccess;
+    if (s < c.max_out.size() && c.max_out[s]) {
+      mb = c.mc_all + s * c.U;
+      e = cudaMemsetAsync(mb, 0, c.U * sizeof(unsigned), c.st);
+    }
+    if (e == cudaSuccess) e = launch_vector(A, B, C, d, c.st, mb);
+  }
   else if (klass == TN_KCLASS_GEMM_TC) {
     const int L = (int)P.net.leaves.size();
     PlaneOperand pa{}, pb{};
@@ -542,11 +551,15 @@ tn_status run_step_in(Ctx& c, size_t s, const Geo& g) {
     ScaleIO sio{};
     e = cudaSuccess;
     const int64_t U = c.U;
+    // a streaming producer already recorded its output's maxima for the split
+    auto recorded = [&](int x) { return x >= L && x - L < (int)c.max_out.size() && c.max_out[x - L]; };
     if (!a_in) {
-      if (c.scaled) e = cudaMemsetAsync(c.mb[0], 0, U * sizeof(unsigned), c.st);
+      const bool ready = c.scaled && recorded(S.a);
+      unsigned* mx = ready ? c.mc_all + (S.a - L) * U : c.mb[0];
+      if (c.scaled && !ready) e = cudaMemsetAsync(c.mb[0], 0, U * sizeof(unsigned), c.st);
       if (e == cudaSuccess)
-        e = split_operand(A, d, false, c.bf16, c.np, c.scaled, c.mb[0], c.es[0], c.ms[0], E.scratch, pa, c.st);
-      c.launches += c.scaled ? 2 : 1;
+        e = split_operand(A, d, false, c.bf16, c.np, c.scaled, mx, c.es[0], c.ms[0], E.scratch, pa, c.st, ready);
+      c.launches += c.scaled && !ready ? 2 : 1;
       sio.ea = c.es[0];
       sio.ma = c.ms[0];
     } else {
@@ -554,10 +567,13 @@ tn_status run_step_in(Ctx& c, size_t s, const Geo& g) {
       sio.ma = reinterpret_cast<const float*>(c.mc_all + (S.a - L) * U);
     }
     if (!b_in) {
-      if (e == cudaSuccess && c.scaled) e = cudaMemsetAsync(c.mb[1], 0, U * sizeof(unsigned), c.st);
+      const bool ready = c.scaled && recorded(S.b);
+      unsigned* mx = ready ? c.mc_all + (S.b - L) * U : c.mb[1];
+      if (e == cudaSuccess && c.scaled && !ready) e = cudaMemsetAsync(c.mb[1], 0, U * sizeof(unsigned), c.st);
       if (e == cudaSuccess)
-        e = split_operand(B, d, true, c.bf16, c.np, c.scaled, c.mb[1], c.es[1], c.ms[1], E.scratch + need_a, pb, c.st);
-      c.launches += c.scaled ? 2 : 1;
+        e = split_operand(B, d, true, c.bf16, c.np, c.scaled, mx, c.es[1], c.ms[1], E.scratch + need_a, pb, c.st,
+                          ready);
+      c.launches += c.scaled && !ready ? 2 : 1;
       sio.eb = c.es[1];
       sio.mb = c.ms[1];
     } else {
@@ -816,6 +832,20 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
         if (tc[p] && P.steps[p].phase != 0 && prec_of(p) == prec_of(t) &&
             planes_in_place(nullptr, E.desc[t], role == 1, np_t, probe))
           c.planes_out[p] = 1;
+      }
+    }
+    // A streaming step (complex64 output) feeding a tensor-core step in a
+    // scaled format records its output's maxima as it writes, and the split
+    // pass skips its maximum pass.
+    c.max_out.assign(P.steps.size(), 0);
+    for (size_t t = 0; t < P.steps.size(); ++t) {
+      if (!tc[t] || !is_scaled(prec_of(t))) continue;
+      const Step& S = P.steps[t];
+      for (int x : {S.a, S.b}) {
+        if (x < L) continue;
+        const int p = x - L;
+        const bool streams = P.steps[p].klass == SC_VECTOR || (!tc_shape_ok(E.desc[p]) && vector_shape_ok(E.desc[p]));
+        if (P.steps[p].phase != 0 && !c.planes_out[p] && streams) c.max_out[p] = 1;
       }
     }
   }

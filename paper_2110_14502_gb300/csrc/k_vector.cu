@@ -29,9 +29,20 @@ __device__ __forceinline__ int32_t bit_offset(int64_t x, int nb, const int32_t* 
   return o;
 }
 
+__device__ __forceinline__ float cmax(float m, float2 v) { return fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y))); }
+
+// The largest |component| this warp wrote, into the launch unit's slot (a
+// scaled split of the output then needs no pass of its own for it).
+__device__ __forceinline__ void record_max(unsigned* maxbits, float m) {
+  if (!maxbits) return;
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxbits + blockIdx.y, __float_as_uint(m));
+}
+
 template <int NK, int NN>
 __global__ void __launch_bounds__(NT) vector_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
-                                                    float2* __restrict__ C, const GemmDesc d) {
+                                                    float2* __restrict__ C, const GemmDesc d,
+                                                    unsigned* __restrict__ maxbits) {
   constexpr int K = 1 << NK, N = 1 << NN;
   const int64_t M = int64_t(1) << d.nm;
   const int64_t ulo = blockIdx.y % d.units_lo, uhi = blockIdx.y / d.units_lo;
@@ -72,6 +83,7 @@ __global__ void __launch_bounds__(NT) vector_kernel(const float2* __restrict__ A
     baseC = oc;
   }
   __syncthreads();
+  float mx = 0.f;
 #pragma unroll
   for (int r = 0; r < PER; ++r) {
     int loc = tid + r * NT;
@@ -93,8 +105,10 @@ __global__ void __launch_bounds__(NT) vector_kernel(const float2* __restrict__ A
         acc.y = fmaf(a[k].y, b.x, acc.y);
       }
       C[(int64_t)oc + nC[n]] = acc;
+      mx = cmax(mx, acc);
     }
   }
+  record_max(maxbits, mx);
 }
 
 // Wide B with a very short contracted index (K <= 4, N = 32..256): the
@@ -103,7 +117,8 @@ __global__ void __launch_bounds__(NT) vector_kernel(const float2* __restrict__ A
 // with N; B (K N <= 1024 complex) sits in shared memory.
 template <int NK, int NN>
 __global__ void __launch_bounds__(NT) vector_wide_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
-                                                         float2* __restrict__ C, const GemmDesc d) {
+                                                         float2* __restrict__ C, const GemmDesc d,
+                                                         unsigned* __restrict__ maxbits) {
   constexpr int K = 1 << NK, N = 1 << NN;
   static_assert(K * N <= 1024, "B must fit in shared memory");
   const int64_t M = int64_t(1) << d.nm;
@@ -142,6 +157,7 @@ __global__ void __launch_bounds__(NT) vector_wide_kernel(const float2* __restric
     baseC = oc;
   }
   __syncthreads();
+  float mx = 0.f;
 #pragma unroll 1
   for (int r = 0; r < PER; ++r) {
     const int loc = tid + r * NT;
@@ -163,8 +179,10 @@ __global__ void __launch_bounds__(NT) vector_wide_kernel(const float2* __restric
         acc.y = fmaf(a[k].y, b.x, acc.y);
       }
       C[(int64_t)oc + nC[n]] = acc;
+      mx = cmax(mx, acc);
     }
   }
+  record_max(maxbits, mx);
 }
 
 // Longer contracted index (K = 32..128) with a narrow B (N <= 8, N K <= 1024):
@@ -174,7 +192,8 @@ __global__ void __launch_bounds__(NT) vector_wide_kernel(const float2* __restric
 // arrive two per 16-byte load.
 template <int NK, int NN>
 __global__ void __launch_bounds__(NT) vector_long_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
-                                                         float2* __restrict__ C, const GemmDesc d, int pair_k) {
+                                                         float2* __restrict__ C, const GemmDesc d, int pair_k,
+                                                         unsigned* __restrict__ maxbits) {
   constexpr int K = 1 << NK, N = 1 << NN;
   static_assert(K * N <= 1024, "B must fit in shared memory");
   const int64_t M = int64_t(1) << d.nm;
@@ -213,6 +232,7 @@ __global__ void __launch_bounds__(NT) vector_long_kernel(const float2* __restric
     baseC = oc;
   }
   __syncthreads();
+  float mx = 0.f;
 #pragma unroll 1
   for (int r = 0; r < PER; ++r) {
     const int loc = tid + r * NT;
@@ -249,8 +269,12 @@ __global__ void __launch_bounds__(NT) vector_long_kernel(const float2* __restric
       }
     }
 #pragma unroll
-    for (int n = 0; n < N; ++n) C[(int64_t)oc + nC[n]] = acc[n];
+    for (int n = 0; n < N; ++n) {
+      C[(int64_t)oc + nC[n]] = acc[n];
+      mx = cmax(mx, acc[n]);
+    }
   }
+  record_max(maxbits, mx);
 }
 
 // Rows whose K values are contiguous (A's K bit i has stride 2^i, K >= 8):
@@ -274,7 +298,8 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 
 template <int NK, int NN>
 __global__ void __launch_bounds__(SNT) vector_staged_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
-                                                            float2* __restrict__ C, const GemmDesc d) {
+                                                            float2* __restrict__ C, const GemmDesc d,
+                                                            unsigned* __restrict__ maxbits) {
   constexpr int K = 1 << NK, N = 1 << NN;
   constexpr int KC = K < 16 ? K : 16;    // K values per stage
   constexpr int PITCH = KC + 2;          // complex per staged row
@@ -336,6 +361,7 @@ __global__ void __launch_bounds__(SNT) vector_staged_kernel(const float2* __rest
   float2 acc[N];
 #pragma unroll
   for (int n = 0; n < N; ++n) acc[n] = make_float2(0.f, 0.f);
+  float mx = 0.f;
   if (nitems > 0) issue(0);
   cp_async_commit();
 #pragma unroll 1
@@ -367,10 +393,12 @@ __global__ void __launch_bounds__(SNT) vector_staged_kernel(const float2* __rest
 #pragma unroll
       for (int n = 0; n < N; ++n) {
         C[(int64_t)oc + nC[n]] = acc[n];
+        mx = cmax(mx, acc[n]);
         acc[n] = make_float2(0.f, 0.f);
       }
     }
   }
+  record_max(maxbits, mx);
 }
 
 // The staged kernel applies when A's K values of a row are contiguous, every
@@ -386,16 +414,17 @@ bool staged_ok(const float2* A, const GemmDesc& d) {
 }
 
 template <int NK>
-cudaError_t launch_staged(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s) {
+cudaError_t launch_staged(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s,
+                          unsigned* mb) {
   const dim3 g((unsigned)(((int64_t(1) << d.nm) + CH - 1) / CH), (unsigned)d.units);
   switch (d.nn) {
-    case 0: vector_staged_kernel<NK, 0><<<g, SNT, 0, s>>>(A, B, C, d); break;
-    case 1: vector_staged_kernel<NK, 1><<<g, SNT, 0, s>>>(A, B, C, d); break;
-    case 2: vector_staged_kernel<NK, 2><<<g, SNT, 0, s>>>(A, B, C, d); break;
-    case 3: vector_staged_kernel<NK, 3><<<g, SNT, 0, s>>>(A, B, C, d); break;
+    case 0: vector_staged_kernel<NK, 0><<<g, SNT, 0, s>>>(A, B, C, d, mb); break;
+    case 1: vector_staged_kernel<NK, 1><<<g, SNT, 0, s>>>(A, B, C, d, mb); break;
+    case 2: vector_staged_kernel<NK, 2><<<g, SNT, 0, s>>>(A, B, C, d, mb); break;
+    case 3: vector_staged_kernel<NK, 3><<<g, SNT, 0, s>>>(A, B, C, d, mb); break;
     case 4:
       if constexpr (NK <= 4) {
-        vector_staged_kernel<NK, 4><<<g, SNT, 0, s>>>(A, B, C, d);
+        vector_staged_kernel<NK, 4><<<g, SNT, 0, s>>>(A, B, C, d, mb);
         break;
       }
       return cudaErrorInvalidValue;
@@ -405,30 +434,32 @@ cudaError_t launch_staged(const float2* A, const float2* B, float2* C, const Gem
 }
 
 template <int NK>
-cudaError_t launch_long(const float2* A, const float2* B, float2* C, const GemmDesc& d, dim3 g, cudaStream_t s) {
+cudaError_t launch_long(const float2* A, const float2* B, float2* C, const GemmDesc& d, dim3 g, cudaStream_t s,
+                        unsigned* mb) {
   // pairs (k, k + 1), k even, are adjacent when A's K bit 0 has stride 1;
   // every other stride of A is then even, so a pair starts on a 16-byte
   // boundary once the base and the unit strides are even
   const int pair_k = d.nk >= 1 && d.ak[0] == 1 && (reinterpret_cast<uintptr_t>(A) & 15) == 0 &&
                      (d.a_lo & 1) == 0 && (d.a_hi & 1) == 0;
   switch (d.nn) {
-    case 0: vector_long_kernel<NK, 0><<<g, NT, 0, s>>>(A, B, C, d, pair_k); break;
-    case 1: vector_long_kernel<NK, 1><<<g, NT, 0, s>>>(A, B, C, d, pair_k); break;
-    case 2: vector_long_kernel<NK, 2><<<g, NT, 0, s>>>(A, B, C, d, pair_k); break;
-    case 3: vector_long_kernel<NK, 3><<<g, NT, 0, s>>>(A, B, C, d, pair_k); break;
+    case 0: vector_long_kernel<NK, 0><<<g, NT, 0, s>>>(A, B, C, d, pair_k, mb); break;
+    case 1: vector_long_kernel<NK, 1><<<g, NT, 0, s>>>(A, B, C, d, pair_k, mb); break;
+    case 2: vector_long_kernel<NK, 2><<<g, NT, 0, s>>>(A, B, C, d, pair_k, mb); break;
+    case 3: vector_long_kernel<NK, 3><<<g, NT, 0, s>>>(A, B, C, d, pair_k, mb); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 template <int NK>
-cudaError_t launch_nn(const float2* A, const float2* B, float2* C, const GemmDesc& d, dim3 g, cudaStream_t s) {
+cudaError_t launch_nn(const float2* A, const float2* B, float2* C, const GemmDesc& d, dim3 g, cudaStream_t s,
+                      unsigned* mb) {
   switch (d.nn) {
-    case 0: vector_kernel<NK, 0><<<g, NT, 0, s>>>(A, B, C, d); break;
-    case 1: vector_kernel<NK, 1><<<g, NT, 0, s>>>(A, B, C, d); break;
-    case 2: vector_kernel<NK, 2><<<g, NT, 0, s>>>(A, B, C, d); break;
-    case 3: vector_kernel<NK, 3><<<g, NT, 0, s>>>(A, B, C, d); break;
-    case 4: vector_kernel<NK, 4><<<g, NT, 0, s>>>(A, B, C, d); break;
+    case 0: vector_kernel<NK, 0><<<g, NT, 0, s>>>(A, B, C, d, mb); break;
+    case 1: vector_kernel<NK, 1><<<g, NT, 0, s>>>(A, B, C, d, mb); break;
+    case 2: vector_kernel<NK, 2><<<g, NT, 0, s>>>(A, B, C, d, mb); break;
+    case 3: vector_kernel<NK, 3><<<g, NT, 0, s>>>(A, B, C, d, mb); break;
+    case 4: vector_kernel<NK, 4><<<g, NT, 0, s>>>(A, B, C, d, mb); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -441,50 +472,52 @@ bool vector_shape_ok(const GemmDesc& d) {
 }
 
 template <int NK>
-cudaError_t launch_wide(const float2* A, const float2* B, float2* C, const GemmDesc& d, dim3 g, cudaStream_t s) {
+cudaError_t launch_wide(const float2* A, const float2* B, float2* C, const GemmDesc& d, dim3 g, cudaStream_t s,
+                        unsigned* mb) {
   switch (d.nn) {
-    case 5: vector_wide_kernel<NK, 5><<<g, NT, 0, s>>>(A, B, C, d); break;
-    case 6: vector_wide_kernel<NK, 6><<<g, NT, 0, s>>>(A, B, C, d); break;
-    case 7: vector_wide_kernel<NK, 7><<<g, NT, 0, s>>>(A, B, C, d); break;
-    case 8: vector_wide_kernel<NK, 8><<<g, NT, 0, s>>>(A, B, C, d); break;
+    case 5: vector_wide_kernel<NK, 5><<<g, NT, 0, s>>>(A, B, C, d, mb); break;
+    case 6: vector_wide_kernel<NK, 6><<<g, NT, 0, s>>>(A, B, C, d, mb); break;
+    case 7: vector_wide_kernel<NK, 7><<<g, NT, 0, s>>>(A, B, C, d, mb); break;
+    case 8: vector_wide_kernel<NK, 8><<<g, NT, 0, s>>>(A, B, C, d, mb); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s) {
+cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s,
+                          unsigned* maxbits) {
   if (!vector_shape_ok(d) || d.units > 65535) return cudaErrorInvalidValue;
   int64_t M = int64_t(1) << d.nm;
   dim3 g((unsigned)((M + CH - 1) / CH), (unsigned)d.units);
   if (d.nn > 4) {  // K <= 2 (vector_shape_ok)
     switch (d.nk) {
-      case 0: return launch_wide<0>(A, B, C, d, g, s);
-      case 1: return launch_wide<1>(A, B, C, d, g, s);
-      default: return launch_wide<2>(A, B, C, d, g, s);
+      case 0: return launch_wide<0>(A, B, C, d, g, s, maxbits);
+      case 1: return launch_wide<1>(A, B, C, d, g, s, maxbits);
+      default: return launch_wide<2>(A, B, C, d, g, s, maxbits);
     }
   }
   if (staged_ok(A, d)) {
     switch (d.nk) {
-      case 3: return launch_staged<3>(A, B, C, d, s);
-      case 4: return launch_staged<4>(A, B, C, d, s);
-      case 5: return launch_staged<5>(A, B, C, d, s);
-      case 6: return launch_staged<6>(A, B, C, d, s);
-      default: return launch_staged<7>(A, B, C, d, s);
+      case 3: return launch_staged<3>(A, B, C, d, s, maxbits);
+      case 4: return launch_staged<4>(A, B, C, d, s, maxbits);
+      case 5: return launch_staged<5>(A, B, C, d, s, maxbits);
+      case 6: return launch_staged<6>(A, B, C, d, s, maxbits);
+      default: return launch_staged<7>(A, B, C, d, s, maxbits);
     }
   }
   if (d.nk > 4) {
     switch (d.nk) {
-      case 5: return launch_long<5>(A, B, C, d, g, s);
-      case 6: return launch_long<6>(A, B, C, d, g, s);
-      default: return launch_long<7>(A, B, C, d, g, s);
+      case 5: return launch_long<5>(A, B, C, d, g, s, maxbits);
+      case 6: return launch_long<6>(A, B, C, d, g, s, maxbits);
+      default: return launch_long<7>(A, B, C, d, g, s, maxbits);
     }
   }
   switch (d.nk) {
-    case 0: return launch_nn<0>(A, B, C, d, g, s);
-    case 1: return launch_nn<1>(A, B, C, d, g, s);
-    case 2: return launch_nn<2>(A, B, C, d, g, s);
-    case 3: return launch_nn<3>(A, B, C, d, g, s);
-    default: return launch_nn<4>(A, B, C, d, g, s);
+    case 0: return launch_nn<0>(A, B, C, d, g, s, maxbits);
+    case 1: return launch_nn<1>(A, B, C, d, g, s, maxbits);
+    case 2: return launch_nn<2>(A, B, C, d, g, s, maxbits);
+    case 3: return launch_nn<3>(A, B, C, d, g, s, maxbits);
+    default: return launch_nn<4>(A, B, C, d, g, s, maxbits);
   }
 }
 
