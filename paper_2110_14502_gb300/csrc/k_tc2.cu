@@ -1473,15 +1473,16 @@ cudaError_t launch_chunked_ew(const CUtensorMap& ma, const CUtensorMap& mb, floa
   return cudaGetLastError();
 }
 
-// Eight epilogue warps where the epilogue dominates a tile (a short K: at
-// most 4 operand stages, or 8 for tiles up to 64 columns wide), four where the
-// main loop does and the extra operand stage matters.
+// Eight epilogue warps where the epilogue dominates a tile (a short K, at
+// most four operand stages, and tiles of 64 or 128 columns: each warp then
+// still has two or more column chunks per tile), four where the main loop
+// does and the extra operand stage matters.
 template <int TN, bool BF16>
 cudaError_t launch_chunked(const CUtensorMap& ma, const CUtensorMap& mb, float2* C, const GemmDesc& d, int kp,
                            const int z[4], int c_planes, const ScaleIO& sio, int fold, int* err, cudaStream_t s,
                            const BulkPlanes& ba, const BulkPlanes& bb) {
   const int nkt = (kp + TKC - 1) / TKC;
-  if (nkt <= 4 || (TN <= 64 && nkt <= 8))
+  if (TN >= 64 && nkt <= 4)
     return launch_chunked_ew<TN, BF16, 8>(ma, mb, C, d, kp, z, c_planes, sio, fold, err, s, ba, bb);
   return launch_chunked_ew<TN, BF16, 4>(ma, mb, C, d, kp, z, c_planes, sio, fold, err, s, ba, bb);
 }
