@@ -31,6 +31,28 @@ __device__ __forceinline__ int32_t bit_offset(int64_t x, int nb, const int32_t* 
 
 __device__ __forceinline__ float cmax(float m, float2 v) { return fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y))); }
 
+// acc[n] += a0 B[k][n] + a1 B[k+1][n] for every n (rows Bk0, Bk1 of B in
+// shared memory), B read two columns per 16-byte load.
+__device__ __forceinline__ void cmac2(float2& c, float2 a0, float2 a1, float2 b0, float2 b1) {
+  c.x = fmaf(a0.x, b0.x, fmaf(-a0.y, b0.y, c.x));
+  c.y = fmaf(a0.x, b0.y, fmaf(a0.y, b0.x, c.y));
+  c.x = fmaf(a1.x, b1.x, fmaf(-a1.y, b1.y, c.x));
+  c.y = fmaf(a1.x, b1.y, fmaf(a1.y, b1.x, c.y));
+}
+template <int N>
+__device__ __forceinline__ void mac_pair(float2 (&acc)[N], const float2* Bk0, const float2* Bk1, float2 a0, float2 a1) {
+  if constexpr (N >= 2) {
+#pragma unroll
+    for (int n = 0; n < N; n += 2) {
+      const float4 p0 = *reinterpret_cast<const float4*>(Bk0 + n), p1 = *reinterpret_cast<const float4*>(Bk1 + n);
+      cmac2(acc[n], a0, a1, make_float2(p0.x, p0.y), make_float2(p1.x, p1.y));
+      cmac2(acc[n + 1], a0, a1, make_float2(p0.z, p0.w), make_float2(p1.z, p1.w));
+    }
+  } else {
+    cmac2(acc[0], a0, a1, Bk0[0], Bk1[0]);
+  }
+}
+
 // The largest |component| this warp wrote, into the launch unit's slot (a
 // scaled split of the output then needs no pass of its own for it).
 __device__ __forceinline__ void record_max(unsigned* maxbits, float m) {
@@ -201,7 +223,7 @@ __global__ void __launch_bounds__(NT) vector_long_kernel(const float2* __restric
   A += ulo * d.a_lo + uhi * d.a_hi;
   B += ulo * d.b_lo + uhi * d.b_hi;
   C += ulo * d.c_lo + uhi * d.c_hi;
-  __shared__ float2 Bs[K * N];
+  __shared__ __align__(16) float2 Bs[K * N];
   __shared__ int32_t kA[K], nC[N];
   __shared__ int32_t tAlo[32], tAhi[32], tClo[32], tChi[32];
   __shared__ int32_t baseA, baseC;
@@ -246,15 +268,7 @@ __global__ void __launch_bounds__(NT) vector_long_kernel(const float2* __restric
 #pragma unroll 4
       for (int k = 0; k < K; k += 2) {
         const float4 x = __ldg(reinterpret_cast<const float4*>(A + (int64_t)oa + kA[k]));
-        const float2 a0 = make_float2(x.x, x.y), a1 = make_float2(x.z, x.w);
-#pragma unroll
-        for (int n = 0; n < N; ++n) {
-          const float2 b0 = Bs[k * N + n], b1 = Bs[(k + 1) * N + n];
-          acc[n].x = fmaf(a0.x, b0.x, fmaf(-a0.y, b0.y, acc[n].x));
-          acc[n].y = fmaf(a0.x, b0.y, fmaf(a0.y, b0.x, acc[n].y));
-          acc[n].x = fmaf(a1.x, b1.x, fmaf(-a1.y, b1.y, acc[n].x));
-          acc[n].y = fmaf(a1.x, b1.y, fmaf(a1.y, b1.x, acc[n].y));
-        }
+        mac_pair<N>(acc, Bs + k * N, Bs + (k + 1) * N, make_float2(x.x, x.y), make_float2(x.z, x.w));
       }
     } else {
 #pragma unroll 8
@@ -375,16 +389,8 @@ __global__ void __launch_bounds__(SNT) vector_staged_kernel(const float2* __rest
 #pragma unroll
     for (int kk = 0; kk < KC; kk += 2) {
       const float4 x = *reinterpret_cast<const float4*>(row + kk);
-      const float2 a0 = make_float2(x.x, x.y), a1 = make_float2(x.z, x.w);
       const int k = c * KC + kk;
-#pragma unroll
-      for (int n = 0; n < N; ++n) {
-        const float2 b0 = Bs[k * N + n], b1 = Bs[(k + 1) * N + n];
-        acc[n].x = fmaf(a0.x, b0.x, fmaf(-a0.y, b0.y, acc[n].x));
-        acc[n].y = fmaf(a0.x, b0.y, fmaf(a0.y, b0.x, acc[n].y));
-        acc[n].x = fmaf(a1.x, b1.x, fmaf(-a1.y, b1.y, acc[n].x));
-        acc[n].y = fmaf(a1.x, b1.y, fmaf(a1.y, b1.x, acc[n].y));
-      }
+      mac_pair<N>(acc, Bs + k * N, Bs + (k + 1) * N, make_float2(x.x, x.y), make_float2(x.z, x.w));
     }
     __syncwarp();  // every lane is done with this buffer before it is refilled
     if (c == NCH - 1) {
