@@ -119,6 +119,9 @@ struct Server {
   std::map<int64_t, std::shared_ptr<Request>> reqs;
   std::deque<std::shared_ptr<Request>> to_plan, ready;
   std::vector<std::shared_ptr<Request>> active;
+  // done requests whose executors (device memory) still count against the
+  // budget until the client waits for them or admission needs the room
+  std::deque<std::shared_ptr<Request>> held;
   int64_t budget = 0, in_use = 0;
   // stems (leaf store + phase-0 outputs) of recent circuits, resident for
   // later requests of the same circuit; its capacity is taken off the budget
@@ -276,13 +279,24 @@ void release(Server& S, Request& R) {
   if (R.ev_begin) cudaEventDestroy(R.ev_begin);
   if (R.ev_end) cudaEventDestroy(R.ev_end);
   R.ev_begin = R.ev_end = nullptr;
-  S.in_use -= R.footprint;
-  // the device memory goes with the budget share: the plan copy's executor
-  // (arenas, operand planes, graphs) is freed now, not when the client waits
   R.stem_reused = R.plan && stem_reused(R.plan->plan) ? 1 : 0;
-  if (R.plan && R.plan->plan.exec) {
-    destroy_executor(R.plan->plan.exec);
-    R.plan->plan.exec = nullptr;
+  // The plan copy's executor (arenas, operand planes, graphs) keeps its device
+  // memory, and its budget share, until the client waits for the request or
+  // admission needs the room (reclaim); freeing device memory synchronises the
+  // device, so it is not done on every completion.
+}
+
+// Frees the executors of held requests, oldest first, until `need` more
+// bytes fit the budget (or none is left).  Called with the server's mutex held.
+void reclaim(Server& S, int64_t need) {
+  while (!S.held.empty() && S.in_use + need > S.budget) {
+    std::shared_ptr<Request> R = S.held.front();
+    S.held.pop_front();
+    if (R->plan && R->plan->plan.exec) {
+      destroy_executor(R->plan->plan.exec);
+      R->plan->plan.exec = nullptr;
+    }
+    S.in_use -= R->footprint;
   }
 }
 
@@ -395,6 +409,7 @@ void scheduler_loop(Server* S) {
         int slot = -1;
         for (size_t i = 0; i < slot_busy.size(); ++i)
           if (!slot_busy[i]) { slot = (int)i; break; }
+        if (slot >= 0 && S->in_use + R->footprint > S->budget) reclaim(*S, R->footprint);
         if (slot < 0 || S->in_use + R->footprint > S->budget) break;
         // requests of the same circuit, precision and slices waiting behind
         // this one join its contraction while its bitstrings fit one group
@@ -407,6 +422,7 @@ void scheduler_loop(Server* S) {
           if (!same || R->params.nb + X.params.nb > kMergeBits) { ++it; continue; }
           R->params.nb += X.params.nb;
           const int64_t fp = footprint(*R, R->q);
+          if (S->in_use + fp > S->budget) reclaim(*S, fp);
           if (S->in_use + fp > S->budget) {
             R->params.nb -= X.params.nb;
             ++it;
@@ -462,6 +478,7 @@ void scheduler_loop(Server* S) {
             R->t_done = Clock::now();
             finish_members(*R);
             release(*S, *R);
+            S->held.push_back(R);
             slot_busy[slot_of[R.get()]] = 0;
             slot_of.erase(R.get());
             S->active.erase(std::find(S->active.begin(), S->active.end(), R));
@@ -480,6 +497,7 @@ void scheduler_loop(Server* S) {
         R->state = RS_DONE;
         finish_members(*R);
         release(*S, *R);
+        S->held.push_back(R);
         slot_busy[slot_of[R.get()]] = 0;
         slot_of.erase(R.get());
         S->active.erase(std::find(S->active.begin(), S->active.end(), R));
@@ -605,6 +623,7 @@ extern "C" tn_status tn_wait(tn_server* h, int64_t ticket, double* out, int64_t 
   if (!h) return fail(TN_EINVAL, "tn_wait: NULL server");
   Server& S = h->s;
   std::shared_ptr<Request> R;
+  bool charged = false;
   {
     std::unique_lock<std::mutex> g(S.mu);
     auto it = S.reqs.find(ticket);
@@ -618,6 +637,19 @@ extern "C" tn_status tn_wait(tn_server* h, int64_t ticket, double* out, int64_t 
       S.cv.wait(g, pred);
     }
     S.reqs.erase(ticket);
+    auto hit = std::find(S.held.begin(), S.held.end(), R);
+    charged = hit != S.held.end();
+    if (charged) S.held.erase(hit);
+  }
+  if (charged) {
+    // the executor's device memory, then its budget share
+    if (R->plan && R->plan->plan.exec) {
+      destroy_executor(R->plan->plan.exec);
+      R->plan->plan.exec = nullptr;
+    }
+    std::lock_guard<std::mutex> g(S.mu);
+    S.in_use -= R->footprint;
+    S.cv.notify_all();
   }
   const int64_t nout = R->nb_own << R->k;
   if (stats) {
@@ -659,7 +691,7 @@ extern "C" tn_status tn_wait(tn_server* h, int64_t ticket, double* out, int64_t 
   }
   if (R->h_out) cudaFreeHost(R->h_out);
   R->h_out = nullptr;
-  R->plan.reset();  // the host copy of the plan (its device state went when the request completed)
+  R->plan.reset();
   return st;
 }
 
