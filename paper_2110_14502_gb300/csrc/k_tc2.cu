@@ -943,15 +943,11 @@ __global__ void __launch_bounds__(ChunkCfg<TN, EW>::THREADS, 1)
   constexpr int ET = 32 * EW;  // epilogue threads
   constexpr int A_STAGE = CF::A_STAGE;
   constexpr uint32_t BUF = 2 * TN;  // columns of one buffer
-  // accumulator buffers in TMEM (all 512 columns): a tile whose K is one chunk
-  // needs one, so the MMA warp may run NBMAX - 1 tiles ahead of the epilogue;
-  // tiles of several chunks use two (the running sum and the chunk)
-  constexpr int NBMAX = 512 / BUF;
-  constexpr uint32_t COLS = 512;
-  static_assert(NBMAX >= 2 && NBMAX <= 16, "accumulator buffers");
+  constexpr uint32_t COLS = 2 * BUF < 32 ? 32 : 2 * BUF;
+  static_assert(2 * BUF <= 512, "two accumulator buffers must fit in TMEM");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t full[NS], empty[NS], acc_full[NBMAX], acc_empty[NBMAX], mma_done;
+  __shared__ uint64_t full[NS], empty[NS], acc_full[2], acc_empty[2], mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int32_t colC[TN];
   __shared__ volatile int abort_flag;
@@ -968,7 +964,6 @@ __global__ void __launch_bounds__(ChunkCfg<TN, EW>::THREADS, 1)
   const int64_t items = (int64_t)tiles * (d.units / fold);
   const int nkt = (kp + TKC - 1) / TKC;  // a short K (8, 16) is one stage; TMA zero-fills past K
   const int nch = (nkt + chunk - 1) / chunk;
-  const int nb = nch == 1 ? NBMAX : 2;  // buffers in use
   const int GM = d.group_m > 0 ? d.group_m : GROUP_M_DEFAULT;
   const bool items32 = items < (int64_t(1) << 31);
   auto decode = [&](int64_t item, int& unit, int& m0, int& n0) {
@@ -989,7 +984,7 @@ __global__ void __launch_bounds__(ChunkCfg<TN, EW>::THREADS, 1)
 
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int b = 0; b < NBMAX; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], ET); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], ET); }
     mbar_init(&mma_done, 1);
     abort_flag = 0;
     epi_fail = 0;
@@ -1076,28 +1071,24 @@ __global__ void __launch_bounds__(ChunkCfg<TN, EW>::THREADS, 1)
     if (lane == 0) drain_loads(full, NS, g, err);  // g = stages issued
     __syncwarp();
   } else if (warp == 1) {
-    // ---- MMA issuer.  Chunk 0 of the t-th tile goes to buffer t % nb, later
-    // chunks (nb = 2) to the other one; every use of a buffer after its first
-    // waits for the epilogue's release of the previous one (parity bits per
-    // buffer: `started`, and `epar` the parity of the next wait).
+    // ---- MMA issuer.  Chunk 0 of the t-th tile goes to buffer t & 1, later
+    // chunks to the other one; the n-th use of a buffer (n >= 1) waits for
+    // the epilogue's (n-1)-th release of it.
     constexpr uint32_t I = idesc2(BF16, TM, TN, false), IN = idesc2(BF16, TM, TN, true);
     int64_t g = 0, t = 0;
-    uint32_t started = 0u, epar = 0u;
+    uint32_t used[2] = {0u, 0u};
     bool ok = true;
     for (int64_t it = first; lane == 0 && ok && it < items && !abort_flag; it += stride, ++t) {
-      const int rb = (int)(t % nb);
+      const int rb = (int)(t & 1);
       for (int c = 0; c < nch && ok; ++c) {
         const int b = c == 0 ? rb : 1 - rb;
-        if ((started >> b) & 1u) {
-          if (!mbar_wait(&acc_empty[b], (epar >> b) & 1u, wl)) {
-            atomicExch(err, 32);
-            abort_flag = 1;
-            ok = false;
-            break;
-          }
-          epar ^= 1u << b;
+        if (used[b] >= 1 && !mbar_wait(&acc_empty[b], (used[b] - 1) & 1, wl)) {
+          atomicExch(err, 32);
+          abort_flag = 1;
+          ok = false;
+          break;
         }
-        started |= 1u << b;
+        ++used[b];
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dr = tmem + (uint32_t)b * BUF, di = dr + TN;
         const int k0 = c * chunk, k1 = min(nkt, k0 + chunk);
@@ -1180,7 +1171,7 @@ __global__ void __launch_bounds__(ChunkCfg<TN, EW>::THREADS, 1)
     // scaling and the maximum / filter tracking only where the formats need them
     const bool track = sio.mc != nullptr || sio.flag != nullptr;
     int64_t t = 0;
-    uint32_t fpar = 0u;  // per buffer: parity of the next acc_full wait
+    uint32_t seen[2] = {0u, 0u};
     for (int64_t it = first; it < items; it += stride, ++t) {
       int unit, m0, n0;
       decode(it, unit, m0, n0);
@@ -1216,12 +1207,12 @@ __global__ void __launch_bounds__(ChunkCfg<TN, EW>::THREADS, 1)
       };
       const int vb = vec_bits(d);
       const int gw = fold > 1 ? nsub : TN;  // tile columns of one unit
-      const int rb = (int)(t % nb);
+      const int rb = (int)(t & 1);
       const uint32_t R = tmem + lane_off + (uint32_t)rb * BUF, P = tmem + lane_off + (uint32_t)(1 - rb) * BUF;
       for (int c = 0; c < nch; ++c) {
         const int b = c == 0 ? rb : 1 - rb;
-        bool ok = mbar_wait(&acc_full[b], (fpar >> b) & 1u, wl);
-        fpar ^= 1u << b;
+        bool ok = mbar_wait(&acc_full[b], seen[b] & 1, wl);
+        ++seen[b];
         ok = __all_sync(0xffffffffu, ok);
         if (!ok && lane == 0) {
           atomicExch(err, 34);
