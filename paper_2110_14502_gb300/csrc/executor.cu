@@ -379,7 +379,8 @@ static tn_status setup(Plan& P, Executor& E) {
     // a GEMM-class step too narrow for the tensor cores whose shape the
     // streaming kernels take (K <= 4, N <= 256) runs as one of them
     make_gemm_desc(P.steps[s].la, P.steps[s].lb, P.steps[s].lc, E.desc[s], P.steps[s].klass == SC_VECTOR);
-    if (P.steps[s].klass != SC_VECTOR && !tc_shape_ok(E.desc[s]) && vector_shape_ok(E.desc[s]))
+    if (P.steps[s].klass != SC_VECTOR && (!tc_shape_ok(E.desc[s]) || stream_preferred(E.desc[s])) &&
+        vector_shape_ok(E.desc[s]))
       make_gemm_desc(P.steps[s].la, P.steps[s].lb, P.steps[s].lc, E.desc[s], true);
   }
   CK(cudaEventCreate(&E.ev0));
@@ -512,8 +513,9 @@ tn_status run_step_in(Ctx& c, size_t s, const Geo& g) {
   if (c.profile && !c.sizing) { tn_status r = c.event(e0); if (r) return r; }
   cudaError_t e;
   int klass = S.klass == SC_VECTOR ? TN_KCLASS_VECTOR : TN_KCLASS_GEMM_SIMT;
-  if (S.klass != SC_VECTOR && c.tc && tc_shape_ok(d)) klass = TN_KCLASS_GEMM_TC;
-  else if (klass == TN_KCLASS_GEMM_SIMT && !tc_shape_ok(d) && vector_shape_ok(d)) klass = TN_KCLASS_VECTOR;
+  if (S.klass != SC_VECTOR && c.tc && tc_shape_ok(d) && !stream_preferred(d)) klass = TN_KCLASS_GEMM_TC;
+  else if (klass == TN_KCLASS_GEMM_SIMT && (!tc_shape_ok(d) || stream_preferred(d)) && vector_shape_ok(d))
+    klass = TN_KCLASS_VECTOR;
   // few outputs with a long contracted index: the bandwidth-bound reduction
   const bool reduce = klass == TN_KCLASS_GEMM_SIMT && reduce_shape_ok(d);
   if (reduce) klass = TN_KCLASS_VECTOR;
@@ -819,7 +821,8 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
     const int L = (int)P.net.leaves.size();
     std::vector<char> tc(P.steps.size(), 0);
     for (size_t s = 0; s < P.steps.size(); ++s)
-      tc[s] = P.steps[s].klass != SC_VECTOR && tc_shape_ok(E.desc[s]) && prec_of(s) != TN_PREC_C64;
+      tc[s] = P.steps[s].klass != SC_VECTOR && tc_shape_ok(E.desc[s]) && !stream_preferred(E.desc[s]) &&
+              prec_of(s) != TN_PREC_C64;
     for (size_t t = 0; t < P.steps.size(); ++t) {
       if (!tc[t] || !handover_of(prec_of(t))) continue;
       const Step& S = P.steps[t];
@@ -844,7 +847,9 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
       for (int x : {S.a, S.b}) {
         if (x < L) continue;
         const int p = x - L;
-        const bool streams = P.steps[p].klass == SC_VECTOR || (!tc_shape_ok(E.desc[p]) && vector_shape_ok(E.desc[p]));
+        const GemmDesc& dp = E.desc[p];
+        const bool streams = P.steps[p].klass == SC_VECTOR ||
+                             ((!tc_shape_ok(dp) || stream_preferred(dp)) && vector_shape_ok(dp));
         if (P.steps[p].phase != 0 && !c.planes_out[p] && streams) c.max_out[p] = 1;
       }
     }

@@ -10,6 +10,8 @@
 // order (bit 0 = most contiguous index) both the stream of A and the store of
 // C coalesce.  The row offsets come from two 32-entry position tables per
 // CTA plus one CTA base (the bits of m are disjoint, so offsets add).
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace tn {
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(NT) vector_kernel(const float2* __restrict__ A
 template <int NK, int NN>
 __global__ void __launch_bounds__(NT) vector_wide_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
                                                          float2* __restrict__ C, const GemmDesc d,
-                                                         unsigned* __restrict__ maxbits) {
+                                                         unsigned* __restrict__ maxbits, int pair_k) {
   constexpr int K = 1 << NK, N = 1 << NN;
   static_assert(K * N <= 1024, "B must fit in shared memory");
   const int64_t M = int64_t(1) << d.nm;
@@ -187,8 +189,17 @@ __global__ void __launch_bounds__(NT) vector_wide_kernel(const float2* __restric
     const int32_t oa = baseA + tAlo[loc & 31] + tAhi[loc >> 5];
     const int32_t oc = baseC + tClo[loc & 31] + tChi[loc >> 5];
     float2 a[K];
+    if (K >= 2 && pair_k) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) a[k] = __ldg(A + (int64_t)oa + kA[k]);
+      for (int k = 0; k < K; k += 2) {
+        const float4 x = __ldg(reinterpret_cast<const float4*>(A + (int64_t)oa + kA[k]));
+        a[k] = make_float2(x.x, x.y);
+        a[k + 1 < K ? k + 1 : k] = make_float2(x.z, x.w);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k) a[k] = __ldg(A + (int64_t)oa + kA[k]);
+    }
 #pragma unroll 8
     for (int n = 0; n < N; ++n) {
       float2 acc = make_float2(0.f, 0.f);
@@ -474,20 +485,39 @@ cudaError_t launch_nn(const float2* A, const float2* B, float2* C, const GemmDes
 }  // namespace
 
 bool vector_shape_ok(const GemmDesc& d) {
-  return (d.nn <= 4 && d.nk <= 4) || (d.nn <= 3 && d.nk <= 7) || (d.nn <= 8 && d.nk <= 2);
+  return (d.nn <= 4 && d.nk <= 4) || (d.nn <= 3 && d.nk <= 7) || (d.nn <= 8 && d.nk <= 2) ||
+         (d.nn == 5 && d.nk == 3);
 }
+
+// K = 8, N = 32: the tensor-core tile is 128 x 32 with one 16-K step (its upper
+// half zeros), a few hundred cycles of MMA against an epilogue and pipeline
+// round trip per tile; the streaming kernel does the 256 complex products per
+// row on the FP32 cores at about the memory rate instead.
+bool stream_preferred(const GemmDesc& d) { return d.nn == 5 && d.nk == 3; }
 
 template <int NK>
 cudaError_t launch_wide(const float2* A, const float2* B, float2* C, const GemmDesc& d, dim3 g, cudaStream_t s,
                         unsigned* mb) {
+  // pairs (k, k + 1), k even, adjacent and 16-byte aligned: A's K bit 0 has
+  // stride 1 (every other stride of A is then even), even unit strides
+  const int pair_k = NK >= 1 && d.ak[0] == 1 && (reinterpret_cast<uintptr_t>(A) & 15) == 0 && (d.a_lo & 1) == 0 &&
+                     (d.a_hi & 1) == 0;
+  auto one = [&](auto nn) -> cudaError_t {
+    constexpr int NN = decltype(nn)::value;
+    if constexpr (((1 << NK) << NN) <= 1024) {
+      vector_wide_kernel<NK, NN><<<g, NT, 0, s>>>(A, B, C, d, mb, pair_k);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  };
   switch (d.nn) {
-    case 5: vector_wide_kernel<NK, 5><<<g, NT, 0, s>>>(A, B, C, d, mb); break;
-    case 6: vector_wide_kernel<NK, 6><<<g, NT, 0, s>>>(A, B, C, d, mb); break;
-    case 7: vector_wide_kernel<NK, 7><<<g, NT, 0, s>>>(A, B, C, d, mb); break;
-    case 8: vector_wide_kernel<NK, 8><<<g, NT, 0, s>>>(A, B, C, d, mb); break;
+    case 5: return one(std::integral_constant<int, 5>{});
+    case 6: return one(std::integral_constant<int, 6>{});
+    case 7: return one(std::integral_constant<int, 7>{});
+    case 8: return one(std::integral_constant<int, 8>{});
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s,
@@ -495,6 +525,7 @@ cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const Gem
   if (!vector_shape_ok(d) || d.units > 65535) return cudaErrorInvalidValue;
   int64_t M = int64_t(1) << d.nm;
   dim3 g((unsigned)((M + CH - 1) / CH), (unsigned)d.units);
+  if (d.nn == 5 && d.nk == 3) return launch_wide<3>(A, B, C, d, g, s, maxbits);
   if (d.nn > 4) {  // K <= 2 (vector_shape_ok)
     switch (d.nk) {
       case 0: return launch_wide<0>(A, B, C, d, g, s, maxbits);

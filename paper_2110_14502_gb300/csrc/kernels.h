@@ -148,9 +148,11 @@ cudaError_t run_gemm_tc2(const float2* A, const float2* B, float2* C, const Gemm
 // aux: 24 bytes of device memory (maxima, exponents, stored maxima).
 cudaError_t run_gemm_tc2_scaled(const float2* A, const float2* B, float2* C, const GemmDesc& d, bool bf16, int np,
                                 uint16_t* scratch, void* aux, int* err, cudaStream_t s);
-// Vector-like steps: N <= 16 and K <= 16, N <= 8 and K <= 128, or N <= 256 and
-// K <= 4 (k_vector.cu).
+// Vector-like steps: N <= 16 and K <= 16, N <= 8 and K <= 128, N <= 256 and
+// K <= 4, or N = 32 and K = 8 (k_vector.cu).
 bool vector_shape_ok(const GemmDesc& d);
+// Shapes the tensor cores could take that run faster on the streaming kernel.
+bool stream_preferred(const GemmDesc& d);
 // maxbits (may be null): per launch unit, the largest |component| written, as
 // float bits by atomicMax (cleared by the caller).
 cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s,

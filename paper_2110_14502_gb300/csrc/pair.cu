@@ -133,7 +133,7 @@ static bool d_is_vector(const std::vector<int>& la, const std::vector<int>& lb, 
   for (int l : la)
     if (std::find(lb.begin(), lb.end(), l) != lb.end()) ++nk;
   const int nn = (int)lb.size() - nk;
-  return (nn <= 4 && nk <= 4) || (nn <= 3 && nk <= 7) || (nn <= 8 && nk <= 2);
+  return (nn <= 4 && nk <= 4) || (nn <= 3 && nk <= 7) || (nn <= 8 && nk <= 2) || (nn == 5 && nk == 3);
 }
 
 extern "C" tn_status tn_set_wait_limit(int64_t polls) {
@@ -177,7 +177,8 @@ extern "C" tn_status tn_contract_pair(const void* A, const int32_t* a_labels, in
     case TN_PAIR_FUSED_SIMT: e = launch_gemm_simt(a, b, c, d, s); break;
     case TN_PAIR_VECTOR:
       if (!vector_shape_ok(d))
-        return fail(TN_EINVAL, "tn_contract_pair: the vector kernel needs N, K <= 16, N <= 8 and K <= 128, or N <= 256 and K <= 4");
+        return fail(TN_EINVAL, "tn_contract_pair: the vector kernel needs N, K <= 16, N <= 8 and K <= 128, N <= 256 "
+                               "and K <= 4, or N = 32 and K = 8");
       e = launch_vector(a, b, c, d, s);
       break;
     case TN_PAIR_UNFUSED: return unfused(a, b, c, d, s);

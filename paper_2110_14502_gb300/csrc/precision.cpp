@@ -70,7 +70,7 @@ extern "C" tn_status tn_precision_analysis(tn_plan_t* p, const uint64_t* bitstri
       if (P.steps[s].phase == 0 || P.steps[s].klass == SC_VECTOR) continue;
       GemmDesc d;
       make_gemm_desc(P.steps[s].la, P.steps[s].lb, P.steps[s].lc, d);
-      if (tc_shape_ok(d)) cand.push_back((int)s);
+      if (tc_shape_ok(d) && !stream_preferred(d)) cand.push_back((int)s);
     }
     int runs = 0;
     auto contract = [&](int prec, const int8_t* sp, std::vector<double>& out) -> tn_status {

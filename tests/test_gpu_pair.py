@@ -54,11 +54,12 @@ def test_pair_c64_matches_fp64(nm, nn, nk, algo):
 
 @pytest.mark.parametrize("nm,nn,nk", [(0, 0, 0), (5, 1, 3), (12, 4, 4), (18, 2, 2), (20, 4, 2),
                                       (3, 3, 5), (11, 3, 5), (13, 2, 6), (9, 0, 7), (16, 3, 7), (10, 1, 6),
-                                      (13, 5, 2), (10, 8, 1), (9, 6, 2), (3, 8, 2), (12, 7, 0), (11, 5, 1)])
+                                      (13, 5, 2), (10, 8, 1), (9, 6, 2), (3, 8, 2), (12, 7, 0), (11, 5, 1),
+                                      (13, 5, 3), (6, 5, 3)])
 def test_vector_kernel_matches_fp64(nm, nn, nk):
     """Streaming kernel: N, K <= 16 with the row's K values in registers,
-    N <= 8 with K up to 128 consumed into running sums, and N up to 256 with
-    K <= 4; ragged M below one CTA's 1024 rows included."""
+    N <= 8 with K up to 128 consumed into running sums, N up to 256 with
+    K <= 4, and N = 32 with K = 8; ragged M below one CTA's 1024 rows included."""
     T = tnlib()
     la, lb, lc, A, B, ref = _case(nm, nn, nk, seed=7 + nm + nk)
     for algo in ("vector", "auto"):
@@ -67,7 +68,7 @@ def test_vector_kernel_matches_fp64(nm, nn, nk):
 
 
 @pytest.mark.parametrize("nm,nn,nk", [(5, 3, 5), (9, 4, 3), (11, 3, 5), (12, 4, 4), (13, 2, 6), (10, 1, 6),
-                                      (16, 3, 7), (18, 3, 5), (7, 0, 7), (6, 4, 3), (14, 0, 3)])
+                                      (16, 3, 7), (18, 3, 5), (7, 0, 7), (6, 4, 3), (14, 0, 3), (15, 5, 3)])
 def test_vector_kernel_contiguous_rows(nm, nn, nk):
     """Planner-style layouts (the contracted indices innermost, in one order
     in both operands): the rows of A are contiguous K runs, which the
