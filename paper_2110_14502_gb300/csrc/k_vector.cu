@@ -10,6 +10,9 @@
 // order (bit 0 = most contiguous index) both the stream of A and the store of
 // C coalesce.  The row offsets come from two 32-entry position tables per
 // CTA plus one CTA base (the bits of m are disjoint, so offsets add).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <type_traits>
 
 #include "kernels.h"
@@ -63,10 +66,55 @@ __device__ __forceinline__ void record_max(unsigned* maxbits, float m) {
   if ((threadIdx.x & 31) == 0) atomicMax(maxbits + blockIdx.y, __float_as_uint(m));
 }
 
+__device__ __forceinline__ uint16_t h16(float x, int bf16) {
+  return bf16 ? __bfloat16_as_ushort(__float2bfloat16_rn(x)) : __half_as_ushort(__float2half_rn(x));
+}
+__device__ __forceinline__ float f16(uint16_t h, int bf16) {
+  return bf16 ? __bfloat162float(__ushort_as_bfloat16(h)) : __half2float(__ushort_as_half(h));
+}
+
+// The launch unit's exponent for plane output: the stored values are x 2^-e
+// with the unit's largest |component| in [2^13, 2^14) (the split pass's
+// rule); 0 without maxima.  Block (0, unit) thread 0 records e and the stored
+// maximum for the consumer.
+__device__ __forceinline__ int unit_exponent(const VecOut& o) {
+  if (o.mode != 2 || !o.raw) return 0;
+  const float m = __uint_as_float(o.raw[blockIdx.y]);
+  int e = 0;
+  if (m > 0.f && isfinite(m)) {
+    int x;
+    frexpf(m, &x);
+    e = x - 14;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && o.ec) {
+    o.ec[blockIdx.y] = e;
+    o.mc[blockIdx.y] = __float_as_uint(ldexpf(m, -e));
+  }
+  return e;
+}
+
+// One output value: complex64 (mode 0), its maximum only (mode 1), or the four
+// 16-bit planes re_hi, re_lo, im_hi, im_lo of x 2^-e (mode 2; hi = rn16(x),
+// lo = rn16(x - hi), the split pass's roundings) at the same element offset.
+__device__ __forceinline__ void emit(const VecOut& o, float2* C, int64_t off, float2 v, float& mx, int e) {
+  mx = cmax(mx, v);
+  if (o.mode == 0) {
+    C[off] = v;
+  } else if (o.mode == 2) {
+    uint16_t* P = reinterpret_cast<uint16_t*>(C);
+    const float re = ldexpf(v.x, -e), im = ldexpf(v.y, -e);
+    const uint16_t rh = h16(re, o.bf16), ih = h16(im, o.bf16);
+    P[off] = rh;
+    P[o.plane + off] = h16(re - f16(rh, o.bf16), o.bf16);
+    P[2 * o.plane + off] = ih;
+    P[3 * o.plane + off] = h16(im - f16(ih, o.bf16), o.bf16);
+  }
+}
+
 template <int NK, int NN>
 __global__ void __launch_bounds__(NT) vector_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
                                                     float2* __restrict__ C, const GemmDesc d,
-                                                    unsigned* __restrict__ maxbits) {
+                                                    const VecOut o) {
   constexpr int K = 1 << NK, N = 1 << NN;
   const int64_t M = int64_t(1) << d.nm;
   const int64_t ulo = blockIdx.y % d.units_lo, uhi = blockIdx.y / d.units_lo;
@@ -108,6 +156,7 @@ __global__ void __launch_bounds__(NT) vector_kernel(const float2* __restrict__ A
   }
   __syncthreads();
   float mx = 0.f;
+  const int e = unit_exponent(o);
 #pragma unroll
   for (int r = 0; r < PER; ++r) {
     int loc = tid + r * NT;
@@ -128,11 +177,10 @@ __global__ void __launch_bounds__(NT) vector_kernel(const float2* __restrict__ A
         acc.y = fmaf(a[k].x, b.y, acc.y);
         acc.y = fmaf(a[k].y, b.x, acc.y);
       }
-      C[(int64_t)oc + nC[n]] = acc;
-      mx = cmax(mx, acc);
+      emit(o, C, (int64_t)oc + nC[n], acc, mx, e);
     }
   }
-  record_max(maxbits, mx);
+  record_max(o.maxbits, mx);
 }
 
 // Wide B with a very short contracted index (K <= 4, N = 32..256): the
@@ -142,7 +190,7 @@ __global__ void __launch_bounds__(NT) vector_kernel(const float2* __restrict__ A
 template <int NK, int NN>
 __global__ void __launch_bounds__(NT) vector_wide_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
                                                          float2* __restrict__ C, const GemmDesc d,
-                                                         unsigned* __restrict__ maxbits, int pair_k) {
+                                                         const VecOut o, int pair_k) {
   constexpr int K = 1 << NK, N = 1 << NN;
   static_assert(K * N <= 1024, "B must fit in shared memory");
   const int64_t M = int64_t(1) << d.nm;
@@ -182,6 +230,7 @@ __global__ void __launch_bounds__(NT) vector_wide_kernel(const float2* __restric
   }
   __syncthreads();
   float mx = 0.f;
+  const int e = unit_exponent(o);
 #pragma unroll 1
   for (int r = 0; r < PER; ++r) {
     const int loc = tid + r * NT;
@@ -211,11 +260,10 @@ __global__ void __launch_bounds__(NT) vector_wide_kernel(const float2* __restric
         acc.y = fmaf(a[k].x, b.y, acc.y);
         acc.y = fmaf(a[k].y, b.x, acc.y);
       }
-      C[(int64_t)oc + nC[n]] = acc;
-      mx = cmax(mx, acc);
+      emit(o, C, (int64_t)oc + nC[n], acc, mx, e);
     }
   }
-  record_max(maxbits, mx);
+  record_max(o.maxbits, mx);
 }
 
 // Longer contracted index (K = 32..128) with a narrow B (N <= 8, N K <= 1024):
@@ -226,7 +274,7 @@ __global__ void __launch_bounds__(NT) vector_wide_kernel(const float2* __restric
 template <int NK, int NN>
 __global__ void __launch_bounds__(NT) vector_long_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
                                                          float2* __restrict__ C, const GemmDesc d, int pair_k,
-                                                         unsigned* __restrict__ maxbits) {
+                                                         const VecOut o) {
   constexpr int K = 1 << NK, N = 1 << NN;
   static_assert(K * N <= 1024, "B must fit in shared memory");
   const int64_t M = int64_t(1) << d.nm;
@@ -266,6 +314,7 @@ __global__ void __launch_bounds__(NT) vector_long_kernel(const float2* __restric
   }
   __syncthreads();
   float mx = 0.f;
+  const int e = unit_exponent(o);
 #pragma unroll 1
   for (int r = 0; r < PER; ++r) {
     const int loc = tid + r * NT;
@@ -295,11 +344,10 @@ __global__ void __launch_bounds__(NT) vector_long_kernel(const float2* __restric
     }
 #pragma unroll
     for (int n = 0; n < N; ++n) {
-      C[(int64_t)oc + nC[n]] = acc[n];
-      mx = cmax(mx, acc[n]);
+      emit(o, C, (int64_t)oc + nC[n], acc[n], mx, e);
     }
   }
-  record_max(maxbits, mx);
+  record_max(o.maxbits, mx);
 }
 
 // Rows whose K values are contiguous (A's K bit i has stride 2^i, K >= 8):
@@ -324,7 +372,7 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 template <int NK, int NN>
 __global__ void __launch_bounds__(SNT) vector_staged_kernel(const float2* __restrict__ A, const float2* __restrict__ B,
                                                             float2* __restrict__ C, const GemmDesc d,
-                                                            unsigned* __restrict__ maxbits) {
+                                                            const VecOut o) {
   constexpr int K = 1 << NK, N = 1 << NN;
   constexpr int KC = K < 16 ? K : 16;    // K values per stage
   constexpr int PITCH = KC + 2;          // complex per staged row
@@ -387,6 +435,7 @@ __global__ void __launch_bounds__(SNT) vector_staged_kernel(const float2* __rest
 #pragma unroll
   for (int n = 0; n < N; ++n) acc[n] = make_float2(0.f, 0.f);
   float mx = 0.f;
+  const int e = unit_exponent(o);
   if (nitems > 0) issue(0);
   cp_async_commit();
 #pragma unroll 1
@@ -409,13 +458,12 @@ __global__ void __launch_bounds__(SNT) vector_staged_kernel(const float2* __rest
       const int32_t oc = baseC + tChi[g] + tClo[lane];
 #pragma unroll
       for (int n = 0; n < N; ++n) {
-        C[(int64_t)oc + nC[n]] = acc[n];
-        mx = cmax(mx, acc[n]);
+        emit(o, C, (int64_t)oc + nC[n], acc[n], mx, e);
         acc[n] = make_float2(0.f, 0.f);
       }
     }
   }
-  record_max(maxbits, mx);
+  record_max(o.maxbits, mx);
 }
 
 // The staged kernel applies when A's K values of a row are contiguous, every
@@ -432,7 +480,7 @@ bool staged_ok(const float2* A, const GemmDesc& d) {
 
 template <int NK>
 cudaError_t launch_staged(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s,
-                          unsigned* mb) {
+                          const VecOut& mb) {
   const dim3 g((unsigned)(((int64_t(1) << d.nm) + CH - 1) / CH), (unsigned)d.units);
   switch (d.nn) {
     case 0: vector_staged_kernel<NK, 0><<<g, SNT, 0, s>>>(A, B, C, d, mb); break;
@@ -452,7 +500,7 @@ cudaError_t launch_staged(const float2* A, const float2* B, float2* C, const Gem
 
 template <int NK>
 cudaError_t launch_long(const float2* A, const float2* B, float2* C, const GemmDesc& d, dim3 g, cudaStream_t s,
-                        unsigned* mb) {
+                        const VecOut& mb) {
   // pairs (k, k + 1), k even, are adjacent when A's K bit 0 has stride 1;
   // every other stride of A is then even, so a pair starts on a 16-byte
   // boundary once the base and the unit strides are even
@@ -470,7 +518,7 @@ cudaError_t launch_long(const float2* A, const float2* B, float2* C, const GemmD
 
 template <int NK>
 cudaError_t launch_nn(const float2* A, const float2* B, float2* C, const GemmDesc& d, dim3 g, cudaStream_t s,
-                      unsigned* mb) {
+                      const VecOut& mb) {
   switch (d.nn) {
     case 0: vector_kernel<NK, 0><<<g, NT, 0, s>>>(A, B, C, d, mb); break;
     case 1: vector_kernel<NK, 1><<<g, NT, 0, s>>>(A, B, C, d, mb); break;
@@ -497,7 +545,7 @@ bool stream_preferred(const GemmDesc& d) { return d.nn == 5 && d.nk == 3; }
 
 template <int NK>
 cudaError_t launch_wide(const float2* A, const float2* B, float2* C, const GemmDesc& d, dim3 g, cudaStream_t s,
-                        unsigned* mb) {
+                        const VecOut& mb) {
   // pairs (k, k + 1), k even, adjacent and 16-byte aligned: A's K bit 0 has
   // stride 1 (every other stride of A is then even), even unit strides
   const int pair_k = NK >= 1 && d.ak[0] == 1 && (reinterpret_cast<uintptr_t>(A) & 15) == 0 && (d.a_lo & 1) == 0 &&
@@ -521,7 +569,7 @@ cudaError_t launch_wide(const float2* A, const float2* B, float2* C, const GemmD
 }
 
 cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s,
-                          unsigned* maxbits) {
+                          const VecOut& maxbits) {
   if (!vector_shape_ok(d) || d.units > 65535) return cudaErrorInvalidValue;
   int64_t M = int64_t(1) << d.nm;
   dim3 g((unsigned)((M + CH - 1) / CH), (unsigned)d.units);
