@@ -529,23 +529,10 @@ tn_status run_step_in(Ctx& c, size_t s, const Geo& g) {
       e = cudaMemsetAsync(o.maxbits, 0, c.U * sizeof(unsigned), c.st);
     }
     if (s < c.planes_out.size() && c.planes_out[s]) {
-      // planes for a tensor-core consumer; in a scaled format a first pass
-      // takes each unit's maxima (into the split roles' scratch slots) for
-      // the exponents
+      // split planes for a tensor-core consumer (unscaled formats only)
       o.mode = 2;
       o.bf16 = c.bf16 ? 1 : 0;
       o.plane = int64_t(1) << (d.nm + d.nn);
-      if (c.scaled) {
-        VecOut m{};
-        m.mode = 1;
-        m.maxbits = c.mb[0];
-        e = cudaMemsetAsync(c.mb[0], 0, c.U * sizeof(unsigned), c.st);
-        if (e == cudaSuccess) e = launch_vector(A, B, C, d, c.st, m);
-        ++c.launches;
-        o.raw = c.mb[0];
-        o.ec = c.ec_all + s * c.U;
-        o.mc = c.mc_all + s * c.U;
-      }
     }
     if (e == cudaSuccess) e = launch_vector(A, B, C, d, c.st, o);
   }
@@ -854,14 +841,15 @@ static tn_status contract_core(Plan& P, const uint64_t* bits, int64_t nb, double
         if (P.steps[p].phase == 0 || prec_of(p) != prec_of(t) ||
             !planes_in_place(nullptr, E.desc[t], role == 1, np_t, probe))
           continue;
-        // A streaming producer writes split planes too: in one pass, or in a
-        // scaled format in two (maxima, then planes), which pays when its
-        // output (2^(M+N)) is at least half its input (2^(M+K)): the split
-        // pass it replaces reads and writes the output once more.
+        // A streaming producer writes split planes too, in an unscaled format
+        // (split bf16).  In a scaled one the exponents need the unit's maxima
+        // first: a second pass over the input, plus four 2-byte stores per
+        // value, cost as much as the split pass they replace (measured on the
+        // 8x8 plan), so there the producer records the maxima for the split.
         const GemmDesc& dp = E.desc[p];
         const bool streams = P.steps[p].klass == SC_VECTOR ||
                              ((!tc_shape_ok(dp) || stream_preferred(dp)) && vector_shape_ok(dp));
-        if (tc[p] || (streams && np_t == 4 && (!is_scaled(prec_of(t)) || dp.nn >= dp.nk))) c.planes_out[p] = 1;
+        if (tc[p] || (streams && np_t == 4 && !is_scaled(prec_of(t)))) c.planes_out[p] = 1;
       }
     }
     // A streaming step (complex64 output) feeding a tensor-core step in a

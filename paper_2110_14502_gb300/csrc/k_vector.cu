@@ -73,36 +73,16 @@ __device__ __forceinline__ float f16(uint16_t h, int bf16) {
   return bf16 ? __bfloat162float(__ushort_as_bfloat16(h)) : __half2float(__ushort_as_half(h));
 }
 
-// The launch unit's exponent for plane output: the stored values are x 2^-e
-// with the unit's largest |component| in [2^13, 2^14) (the split pass's
-// rule); 0 without maxima.  Block (0, unit) thread 0 records e and the stored
-// maximum for the consumer.
-__device__ __forceinline__ int unit_exponent(const VecOut& o) {
-  if (o.mode != 2 || !o.raw) return 0;
-  const float m = __uint_as_float(o.raw[blockIdx.y]);
-  int e = 0;
-  if (m > 0.f && isfinite(m)) {
-    int x;
-    frexpf(m, &x);
-    e = x - 14;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && o.ec) {
-    o.ec[blockIdx.y] = e;
-    o.mc[blockIdx.y] = __float_as_uint(ldexpf(m, -e));
-  }
-  return e;
-}
-
-// One output value: complex64 (mode 0), its maximum only (mode 1), or the four
-// 16-bit planes re_hi, re_lo, im_hi, im_lo of x 2^-e (mode 2; hi = rn16(x),
-// lo = rn16(x - hi), the split pass's roundings) at the same element offset.
-__device__ __forceinline__ void emit(const VecOut& o, float2* C, int64_t off, float2 v, float& mx, int e) {
+// One output value: complex64 (mode 0), or the four 16-bit planes re_hi,
+// re_lo, im_hi, im_lo (mode 2; hi = rn16(x), lo = rn16(x - hi), the split
+// pass's roundings) at the same element offset.
+__device__ __forceinline__ void emit(const VecOut& o, float2* C, int64_t off, float2 v, float& mx) {
   mx = cmax(mx, v);
   if (o.mode == 0) {
     C[off] = v;
-  } else if (o.mode == 2) {
+  } else {
     uint16_t* P = reinterpret_cast<uint16_t*>(C);
-    const float re = ldexpf(v.x, -e), im = ldexpf(v.y, -e);
+    const float re = v.x, im = v.y;
     const uint16_t rh = h16(re, o.bf16), ih = h16(im, o.bf16);
     P[off] = rh;
     P[o.plane + off] = h16(re - f16(rh, o.bf16), o.bf16);
@@ -156,7 +136,6 @@ __global__ void __launch_bounds__(NT) vector_kernel(const float2* __restrict__ A
   }
   __syncthreads();
   float mx = 0.f;
-  const int e = unit_exponent(o);
 #pragma unroll
   for (int r = 0; r < PER; ++r) {
     int loc = tid + r * NT;
@@ -177,7 +156,7 @@ __global__ void __launch_bounds__(NT) vector_kernel(const float2* __restrict__ A
         acc.y = fmaf(a[k].x, b.y, acc.y);
         acc.y = fmaf(a[k].y, b.x, acc.y);
       }
-      emit(o, C, (int64_t)oc + nC[n], acc, mx, e);
+      emit(o, C, (int64_t)oc + nC[n], acc, mx);
     }
   }
   record_max(o.maxbits, mx);
@@ -230,7 +209,6 @@ __global__ void __launch_bounds__(NT) vector_wide_kernel(const float2* __restric
   }
   __syncthreads();
   float mx = 0.f;
-  const int e = unit_exponent(o);
 #pragma unroll 1
   for (int r = 0; r < PER; ++r) {
     const int loc = tid + r * NT;
@@ -260,7 +238,7 @@ __global__ void __launch_bounds__(NT) vector_wide_kernel(const float2* __restric
         acc.y = fmaf(a[k].x, b.y, acc.y);
         acc.y = fmaf(a[k].y, b.x, acc.y);
       }
-      emit(o, C, (int64_t)oc + nC[n], acc, mx, e);
+      emit(o, C, (int64_t)oc + nC[n], acc, mx);
     }
   }
   record_max(o.maxbits, mx);
@@ -314,7 +292,6 @@ __global__ void __launch_bounds__(NT) vector_long_kernel(const float2* __restric
   }
   __syncthreads();
   float mx = 0.f;
-  const int e = unit_exponent(o);
 #pragma unroll 1
   for (int r = 0; r < PER; ++r) {
     const int loc = tid + r * NT;
@@ -344,7 +321,7 @@ __global__ void __launch_bounds__(NT) vector_long_kernel(const float2* __restric
     }
 #pragma unroll
     for (int n = 0; n < N; ++n) {
-      emit(o, C, (int64_t)oc + nC[n], acc[n], mx, e);
+      emit(o, C, (int64_t)oc + nC[n], acc[n], mx);
     }
   }
   record_max(o.maxbits, mx);
@@ -435,7 +412,6 @@ __global__ void __launch_bounds__(SNT) vector_staged_kernel(const float2* __rest
 #pragma unroll
   for (int n = 0; n < N; ++n) acc[n] = make_float2(0.f, 0.f);
   float mx = 0.f;
-  const int e = unit_exponent(o);
   if (nitems > 0) issue(0);
   cp_async_commit();
 #pragma unroll 1
@@ -458,7 +434,7 @@ __global__ void __launch_bounds__(SNT) vector_staged_kernel(const float2* __rest
       const int32_t oc = baseC + tChi[g] + tClo[lane];
 #pragma unroll
       for (int n = 0; n < N; ++n) {
-        emit(o, C, (int64_t)oc + nC[n], acc[n], mx, e);
+        emit(o, C, (int64_t)oc + nC[n], acc[n], mx);
         acc[n] = make_float2(0.f, 0.f);
       }
     }

@@ -153,22 +153,16 @@ cudaError_t run_gemm_tc2_scaled(const float2* A, const float2* B, float2* C, con
 bool vector_shape_ok(const GemmDesc& d);
 // Shapes the tensor cores could take that run faster on the streaming kernel.
 bool stream_preferred(const GemmDesc& d);
-// Output of a streaming step.  mode 0: complex64 C; 1: no output, only the
-// maxima; 2: four 16-bit planes {re_hi, re_lo, im_hi, im_lo} (bf16 or fp16,
-// each `plane` elements, at C's element offsets: a tensor-core consumer's
-// operand) of x 2^-e, e per launch unit from raw[unit] (the unit's largest
-// |component|; raw null: e = 0), with e and the stored maximum (float bits)
-// written to ec[unit] and mc[unit] when ec is set.  maxbits (may be null):
-// per launch unit, the largest |component| computed, as float bits by
-// atomicMax (cleared by the caller).
+// Output of a streaming step.  mode 0: complex64 C; 2: four 16-bit planes
+// {re_hi, re_lo, im_hi, im_lo} (bf16 or fp16, each `plane` elements, at C's
+// element offsets: a tensor-core consumer's operand, unscaled).  maxbits (may
+// be null): per launch unit, the largest |component| computed, as float bits
+// by atomicMax (cleared by the caller).
 struct VecOut {
   unsigned* maxbits;
   int mode;
   int bf16;
   int64_t plane;
-  const unsigned* raw;
-  int* ec;
-  unsigned* mc;
 };
 cudaError_t launch_vector(const float2* A, const float2* B, float2* C, const GemmDesc& d, cudaStream_t s,
                           const VecOut& out = VecOut{});
