@@ -267,7 +267,10 @@ void planner_loop(Server* S) {
   }
 }
 
-void release(Server& S, Request& R) {
+// A done request gives back its stream-ordered buffers and events and waits
+// in S.held for its executor to be freed.  Called with the server's mutex held.
+void release(Server& S, const std::shared_ptr<Request>& Rp) {
+  Request& R = *Rp;
   cudaFreeAsync(R.d_bits, R.stream);
   cudaFreeAsync(R.d_acc, R.stream);
   R.d_bits = nullptr;
@@ -284,6 +287,7 @@ void release(Server& S, Request& R) {
   // memory, and its budget share, until the client waits for the request or
   // admission needs the room (reclaim); freeing device memory synchronises the
   // device, so it is not done on every completion.
+  S.held.push_back(Rp);
 }
 
 // Frees the executors of held requests, oldest first, until `need` more
@@ -477,8 +481,7 @@ void scheduler_loop(Server* S) {
             R->state = RS_DONE;
             R->t_done = Clock::now();
             finish_members(*R);
-            release(*S, *R);
-            S->held.push_back(R);
+            release(*S, R);
             slot_busy[slot_of[R.get()]] = 0;
             slot_of.erase(R.get());
             S->active.erase(std::find(S->active.begin(), S->active.end(), R));
@@ -496,8 +499,7 @@ void scheduler_loop(Server* S) {
         R->t_done = Clock::now();
         R->state = RS_DONE;
         finish_members(*R);
-        release(*S, *R);
-        S->held.push_back(R);
+        release(*S, R);
         slot_busy[slot_of[R.get()]] = 0;
         slot_of.erase(R.get());
         S->active.erase(std::find(S->active.begin(), S->active.end(), R));
