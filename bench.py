@@ -408,6 +408,8 @@ def run_ours(args):
     del p
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.no_micro:
+        line["pair_micro"] = pair_micro_summary(args)
     if rank == 0 and world == 1 and not args.no_serve:
         line["serving"] = serve_summary(args)
     if rank == 0:
@@ -503,13 +505,13 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_micro(args):
-    """Pairwise contraction microbenchmark: fused kernels vs permute + cuBLAS."""
+def micro_rows(shapes, precision, steps, warmup, random_layout, verbose=True):
+    """Pairwise contraction microbenchmark rows: the fused tensor-core kernel
+    (`precision`, its operand split included), the fused FP32 kernel and
+    permute + cuBLAS cgemm on the same complex64 operands."""
     import torch
     import paper_2110_14502_gb300 as T
     import tn_inputs as I
-    shapes = [tuple(int(x) for x in args.shape.split(","))] if args.shape else \
-        [(14, 12, 10), (12, 12, 12), (13, 13, 13), (19, 11, 11), (17, 13, 9), (26, 2, 2)]
     res = []
     for nm, nn, nk in shapes:
         rng = np.random.default_rng(3)
@@ -520,36 +522,63 @@ def run_micro(args):
         la = [int(x) for x in rng.permutation(M)] + perm_k
         lb = [int(x) for x in rng.permutation(N)] + perm_k
         lc = [int(x) for x in rng.permutation(M + N)]
-        if args.random_layout:
+        if random_layout:
             la = [int(x) for x in rng.permutation(M + K)]
             lb = [int(x) for x in rng.permutation(K + N)]
         A = torch.from_numpy(I.random_tensor(len(la), 31, np.complex64)).cuda()
         B = torch.from_numpy(I.random_tensor(len(lb), 32, np.complex64)).cuda()
         Cc = torch.empty(1 << len(lc), dtype=torch.complex64, device="cuda")
         flops = 8.0 * 2.0 ** (nm + nn + nk)
-        row = {"shape": [nm, nn, nk], "tc_precision": args.precision if args.precision != "c64" else "split_bf16"}
+        tcp = precision if precision != "c64" else "split_bf16"
+        row = {"shape": [nm, nn, nk], "tc_precision": tcp}
         algos = ["vector"] if (nn <= 4 and nk <= 4) else ["fused_tc", "gather_tc", "fused_simt", "unfused"]
         for algo in algos:
             prec = "c64"
             if algo == "fused_tc":
-                prec = args.precision if args.precision != "c64" else "split_bf16"
+                prec = tcp
             elif algo == "gather_tc":
                 prec = "split_bf16"
-            for _ in range(args.warmup):
+            for _ in range(warmup):
                 T.contract_pair(A, la, B, lb, Cc, lc, precision=prec, algo=algo)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            for _ in range(args.steps):
+            for _ in range(steps):
                 T.contract_pair(A, la, B, lb, Cc, lc, precision=prec, algo=algo)
             e1.record()
             torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / args.steps
+            ms = e0.elapsed_time(e1) / steps
             row[algo] = {"ms": round(ms, 4), "tflops": round(flops / ms / 1e9, 2),
                          "gbs": round(8.0 * (2 ** len(la) + 2 ** len(lb) + 2 ** len(lc)) / ms / 1e6, 1)}
         res.append(row)
-        print(json.dumps(row), flush=True)
+        if verbose:
+            print(json.dumps(row), flush=True)
+        del A, B, Cc
+        torch.cuda.empty_cache()
     return res
+
+
+def run_micro(args):
+    """Pairwise contraction microbenchmark: fused kernels vs permute + cuBLAS."""
+    shapes = [tuple(int(x) for x in args.shape.split(","))] if args.shape else \
+        [(14, 12, 10), (12, 12, 12), (13, 13, 13), (19, 11, 11), (17, 13, 9), (26, 2, 2)]
+    return micro_rows(shapes, args.precision, args.steps, args.warmup, args.random_layout)
+
+
+# Pairwise microbenchmark of the bench line: complex64 operands of rank 20-30
+# (2^20-2^30 elements), 4-14 contracted indices, random index orders on both
+# operands and the output (log2 M, N, K).
+PAIR_SHAPES = [(12, 12, 10), (14, 14, 12), (16, 6, 14), (15, 15, 5)]
+
+
+def pair_micro_summary(args):
+    rows = micro_rows(PAIR_SHAPES, args.precision, 2, 1, True, verbose=False)
+    return {"operands": "complex64, rank 20-30, random index orders on both operands and the output, "
+                        "N(0,1) entries; per tn_contract_pair call (the tensor-core arm includes its operand split)",
+            "fused_tc": "tensor-core kernel in the bench precision", "fused_simt": "fused FP32 kernel (complex64)",
+            "gather_tc": "tensor-core kernel gathering operands in its main loop (split bf16)",
+            "unfused": "permute both operands, cuBLAS cgemm, permute the output (complex64)",
+            "rows": rows}
 
 
 def serve_workload(nreq, seed=5):
@@ -707,6 +736,7 @@ def main():
                     help="sum only the first N slices of the workload (profiling captures; 0: the workload's count)")
     ap.add_argument("--no-modes", action="store_true")
     ap.add_argument("--no-6x6", action="store_true")
+    ap.add_argument("--no-micro", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--autotune", action="store_true",
