@@ -1,5 +1,6 @@
 // Bandwidth-bound contraction for vector-like steps (N <= 16 and K <= 16,
-// N <= 8 and K <= 128, or N <= 256 and K <= 4).
+// N <= 8 and K <= 128, N <= 256 and K <= 4, or N = 32 and K = 8).  The output
+// is complex64, or a tensor-core consumer's four 16-bit split planes.
 //
 // Paper: Sec. "Tensor Contraction Using Fused Permutation and
 // Multiplication", imbalanced case (a high-rank tensor against a rank-4 one):
