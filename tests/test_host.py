@@ -634,3 +634,22 @@ def test_planner_seed_2_plan_of_the_8x8_network():
     assert two["cmac_per_slice"] < one["cmac_per_slice"]
     assert two["log2_cmac_total"] <= one["log2_cmac_total"] - 9
     assert two["max_log2_intermediate"] <= 26
+
+
+def test_bench_plan_search_over_seeds_keeps_the_cheapest_per_slice():
+    """bench.py --plan-seeds: of the plans from several planner seeds the one
+    with the least work per slice is kept (the benchmark sums a fixed number
+    of slices).  On the 8x8 network, seeds 20-27 include seed 25's plan, the
+    cheapest per slice of seeds 1-40 (74 sliced indices, 2^35.362 per slice;
+    259.6 amplitudes/s on the GPU against 196 for the default seed-1 plan)."""
+    import bench
+    T = tnlib()
+    bench.use_workload("8x8")
+    c = T.random_circuit(bench.ROWS, bench.COLS, bench.DEPTH, bench.CSEED)
+    n = bench.ROWS * bench.COLS
+    net = T.build_network(c, list(range(n - bench.NOPEN, n)))
+    best = bench.best_plan_of_seeds(T, net, range(20, 28)).info()
+    assert hex(best["hash"]) == "0x85af835ff396f738"
+    assert best["num_sliced"] == 74 and round(float(np.log2(best["cmac_per_slice"])), 3) == 35.362
+    one = bench.best_plan_of_seeds(T, net, [1]).info()
+    assert hex(one["hash"]) == "0x5973de292b52ff33"
